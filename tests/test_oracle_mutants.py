@@ -1,0 +1,78 @@
+"""Plant plausible mistakes in copies of the oracle and check the pins catch each one.
+
+Each mutant is the oracle's C source with one edit (a dropped term, a wrong
+sign, index or comparison, a swapped operand), compiled on the CPU into a
+temporary library. The pin suite must report at least one failure for every
+mutant; a mutant that every pin accepts would be a blind spot of the pins.
+"""
+import os
+import subprocess
+
+import pytest
+
+from oracle import build as obuild
+from oracle.oracle import Oracle
+from tests import oracle_pins
+
+MUTANTS = {
+    "idf_drop_plus_one": ("(1.0 + (double)df[t])) + 1.0;", "(1.0 + (double)df[t]));"),
+    "idf_unsmoothed": ("log((1.0 + (double)n_docs) / (1.0 + (double)df[t]))",
+                       "log((double)n_docs / (1.0 + (double)df[t]))"),
+    "weights_ignore_idf": ("(double)counts[e] * (idf ? idf[terms[e]] : 1.0)", "(double)counts[e]"),
+    "ref_norm_no_sqrt": ("rnorm[p] = sqrt(rnorm[p]);", "rnorm[p] = rnorm[p];"),
+    "ref_weight_one": ("double r = idf ? idf[t] : 1.0;", "double r = 1.0;"),
+    "sig_no_doc_norm": ("s[p] / (nrm * rnorm[p])", "s[p] / rnorm[p]"),
+    "sig_numerator_squared": ("s[p] += w[e] * (idf ? idf[terms[e]] : 1.0);", "s[p] += w[e] * w[e];"),
+    "rank_df_ascending": ("return (x->df < y->df) - (x->df > y->df);", "return (x->df > y->df) - (x->df < y->df);"),
+    "rank_tiebreak_desc": ("return (x->t > y->t) - (x->t < y->t);", "return (x->t < y->t) - (x->t > y->t);"),
+    "partition_cut_off_by_one": ("int64_t hi = ((int64_t)(p + 1) * n_sel) / k;",
+                                 "int64_t hi = ((int64_t)(p + 1) * n_sel + 1) / k;"),
+    "region_default_strict": ("(double)r[q].df <= (double)n_docs / 100.0", "(double)r[q].df < (double)n_docs / 100.0"),
+    "df1_means_df2": ("if (df[t] == 1) sel[n_sel++] = t;", "if (df[t] == 2) sel[n_sel++] = t;"),
+    "cos_dense_no_sqrt": ("return ab / (sqrt(aa) * sqrt(bb));\n}\n\n/* Exact", "return ab / (aa * bb);\n}\n\n/* Exact"),
+    "cosine_merge_wrong_advance": ("else if (ti[x] < tj[y]) ++x;", "else if (ti[x] < tj[y]) ++y;"),
+    "cosine_norm_uses_other_row": ("for (int64_t y = 0; y < nj; ++y) bb += wj[y] * wj[y];",
+                                   "for (int64_t y = 0; y < nj; ++y) bb += wi[y] * wj[y];"),
+    "counts_off_by_one": ("counts[out] = (int32_t)(y - x);", "counts[out] = (int32_t)(y - x + 1);"),
+    "simhash_tie_to_one": ("if (col[b] > 0) f |= (1ULL << b);", "if (col[b] >= 0) f |= (1ULL << b);"),
+    "simhash_bit_order": ("col[b] += ((h >> b) & 1ULL) ? 1 : -1;", "col[b] += ((h >> (63 - b)) & 1ULL) ? 1 : -1;"),
+    "simhash_no_minus_one": ("col[b] += ((h >> b) & 1ULL) ? 1 : -1;", "col[b] += ((h >> b) & 1ULL) ? 1 : 0;"),
+    "splitmix_shift": ("z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;", "z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ULL;"),
+    "term_hash_no_seed": ("orc_splitmix64((uint64_t)(uint32_t)t ^ seed)", "orc_splitmix64((uint64_t)(uint32_t)t)"),
+    "hamming_counts_equal_bits": ("c += (int32_t)((x >> bit) & 1ULL);", "c += (int32_t)(((x >> bit) & 1ULL) ^ 1ULL);"),
+    "pairs_include_self": ("for (int64_t j = i + 1; j < n; ++j) {\n            double c = orc_cos_dense",
+                           "for (int64_t j = i; j < n; ++j) {\n            double c = orc_cos_dense"),
+    "pairs_strict_threshold": ("double c = orc_cos_dense(S + i * k, S + j * k, k);\n            if (c >= tau)",
+                               "double c = orc_cos_dense(S + i * k, S + j * k, k);\n            if (c > tau)"),
+    "hamming_pairs_strict": ("if (h <= hmax)", "if (h < hmax)"),
+    "error_stats_signed": ("sa += fabs(e);", "sa += e;"),
+}
+
+
+@pytest.fixture(scope="module")
+def src():
+    with open(obuild.SRC) as f:
+        return f.read()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, src, name):
+    old, new = MUTANTS[name]
+    assert src.count(old) == 1, f"mutation site for {name} not unique/absent"
+    path = tmp_path / f"mut_{name}.c"
+    path.write_text(src.replace(old, new))
+    lib = tmp_path / f"libmut_{name}.so"
+    try:
+        obuild.build(str(path), str(lib), force=True)
+    except subprocess.CalledProcessError:
+        pytest.fail(f"mutant {name} did not compile")
+    failures = oracle_pins.run_all(Oracle(str(lib)))
+    assert failures, f"no pin caught mutant {name}"
+
+
+def test_unmutated_copy_passes(tmp_path, src):
+    path = tmp_path / "copy.c"
+    path.write_text(src)
+    lib = tmp_path / "libcopy.so"
+    obuild.build(str(path), str(lib), force=True)
+    assert oracle_pins.run_all(Oracle(str(lib))) == []
