@@ -1,0 +1,203 @@
+/*
+ * mrc.h -- C ABI of the GB300 (sm_103a) Multi-reference Cosine library.
+ *
+ * Multi-reference Cosine (Mohammadi & Nikoukaran, arXiv 1810.03099) gives each
+ * document a short signature: the cosine (Eq. 1) between the document's term
+ * vector and each of k reference partitions (Section IV). Near-duplicate pairs
+ * are then found by comparing signatures instead of whole documents. The
+ * library also runs the two methods the paper measures against (Section V,
+ * Table 1): exact cosine on the full term vectors, and 64-bit Simhash with
+ * Hamming distance (Section III).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Documents are a token CSR: offsets[n_docs + 1] (int64, offsets[0] == 0,
+ *   non-decreasing) and tokens[offsets[n_docs]] (int32 term ids in [0, vocab)).
+ *   A term id stands for one character 3-gram of Section III.
+ * - Every array argument may live in device memory or in host memory (pinned or
+ *   pageable); the library inspects each pointer. Host inputs are copied to the
+ *   device and host outputs are filled from the device inside the call.
+ * - The caller owns every argument buffer. The library owns mrc_ctx, mrc_index
+ *   and all device memory they hold.
+ * - All work is issued on the stream given to mrc_ctx_create. Calls that return
+ *   a pair count (mrc_match, cosine_allpairs, simhash_match) synchronise that
+ *   stream before returning; the other calls are stream-ordered and their
+ *   device outputs are valid once the stream reaches them.
+ * - Pairs: all-pairs calls emit each unordered pair once with i < j; query
+ *   calls emit (query index i, index/database position j). Self-pairs are never
+ *   emitted. Pair order in the output is unspecified. *n_pairs always receives
+ *   the total number found; when it exceeds `capacity`, `capacity` of them are
+ *   written and the call returns MRC_ERR_CAPACITY (retry with more room).
+ * - No exception crosses the ABI. A failing call returns a status and leaves a
+ *   message for mrc_last_error(). One context per host thread.
+ */
+#ifndef MRC_H_
+#define MRC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mrc_status;
+#define MRC_OK 0
+#define MRC_ERR_INVALID 1     /* bad argument (sizes, ids out of range, NULL)      */
+#define MRC_ERR_OOM 2         /* device allocation failed                           */
+#define MRC_ERR_CAPACITY 3    /* more pairs than `capacity`; *n_pairs is the total  */
+#define MRC_ERR_CUDA 4        /* a CUDA call failed; see mrc_last_error             */
+#define MRC_ERR_TIMEOUT 5     /* a bounded device-side wait gave up                 */
+#define MRC_ERR_UNSUPPORTED 6 /* valid request outside what this build implements   */
+
+/* Reference selection modes (Section IV). */
+#define MRC_SELECT_ALL 0    /* every term of non-zero document frequency              */
+#define MRC_SELECT_REGION 1 /* L consecutive ranks of the df-sorted list from region_start */
+#define MRC_SELECT_DF1 2    /* the first L terms (id order) that occur in one document */
+
+/* Term weighting. The paper counts N-grams (Section III); TF-IDF is the
+ * weighted vector space model its Section VI names as future work. */
+#define MRC_WEIGHT_COUNT 0 /* w(d,t) = c(d,t)                                    */
+#define MRC_WEIGHT_TFIDF 1 /* w(d,t) = c(d,t) * (ln((1+N)/(1+df(t))) + 1)       */
+
+/* Arithmetic of the signature comparison. */
+#define MRC_PREC_FP32 0     /* FP32-accurate compare (fp16 hi/lo split on tensor cores) */
+#define MRC_PREC_BF16_FP8 1 /* BF16 weights, FP8 E4M3 compare, FP32 rescoring near tau  */
+#define MRC_PREC_FP16 2     /* FP16 signatures, FP16 compare, FP32 rescoring near tau   */
+
+#define MRC_MAX_K 256               /* longest signature                                */
+#define MRC_MAX_DOC_TOKENS 65536    /* longest document (exact per-document sums)       */
+
+typedef struct mrc_ctx mrc_ctx;
+typedef struct mrc_index mrc_index;
+
+typedef struct {
+  int32_t i;   /* first document (query) index                          */
+  int32_t j;   /* second document (index position) index                */
+  float score; /* signature or exact cosine; Hamming distance for Simhash */
+} mrc_pair;
+
+typedef struct {
+  int64_t n_docs;
+  const int64_t* offsets; /* [n_docs + 1] */
+  const int32_t* tokens;  /* [offsets[n_docs]] */
+} mrc_docs;
+
+typedef struct {
+  int32_t k;            /* signature length = number of reference partitions, 1..MRC_MAX_K */
+  int32_t L;            /* reference terms selected; < 0 selects 32 * k                     */
+  int32_t select_mode;  /* MRC_SELECT_*                                                     */
+  int32_t region_start; /* REGION: first rank; < 0 = first rank with df <= n_docs / 100     */
+  int32_t weighting;    /* MRC_WEIGHT_*                                                     */
+  int32_t precision;    /* MRC_PREC_*                                                       */
+  float tau;            /* similarity threshold (inclusive), e.g. 0.9                       */
+  float margin;         /* reduced precision: candidates >= tau - margin are rescored       */
+  int32_t hamming_max;  /* Simhash: pairs with Hamming distance <= hamming_max              */
+  int32_t reserved;     /* must be 0                                                        */
+  uint64_t seed;        /* seed of the 64-bit Simhash feature hash                          */
+} mrc_params;
+
+typedef struct {
+  int64_t n_docs;
+  int32_t vocab;
+  int32_t k;
+  int64_t L_used;     /* reference terms actually selected                      */
+  int32_t precision;
+  int32_t weighting;
+  int32_t kp;         /* padded signature row length of the compare operands     */
+  int32_t reserved;
+} mrc_index_info;
+
+/* Fill *p with the library defaults: k = 8, L = 32k, REGION from the default
+ * start, TF-IDF, FP32, tau = 0.9, margin = 0.02, hamming_max = 3, seed 0x1810030990. */
+void mrc_params_default(mrc_params* p);
+
+/* Create a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+mrc_status mrc_ctx_create(void* cuda_stream, mrc_ctx** out);
+void mrc_ctx_destroy(mrc_ctx* ctx);
+/* Message of the last failing call on this context (never NULL). */
+const char* mrc_last_error(const mrc_ctx* ctx);
+
+/*
+ * Build a device-resident signature index over `corpus` (Sections III-IV):
+ * term counts per document, document frequencies, idf (frozen for later
+ * queries), reference selection and partitioning (a host-side sort of the
+ * vocabulary by df inside this call), then every document's signature
+ * s_p(d) = cos(v(d), v(R_p)) (Eq. 1 against partition p), its unit-length
+ * packed form for comparison, and its 64-bit Simhash (Section III).
+ * vocab: number of term ids. The returned index must be freed with
+ * mrc_index_free. Errors: MRC_ERR_INVALID for bad sizes/params/term ids,
+ * MRC_ERR_UNSUPPORTED for documents longer than MRC_MAX_DOC_TOKENS.
+ */
+mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, const mrc_params* params,
+                           mrc_index** out);
+
+/*
+ * Signatures (and Simhash) of new documents against a built index, with the
+ * index's idf and references (Section IV; the paper compares each new page
+ * with the signature database, Section I). sig: [n_docs * k] float32 raw
+ * cosines (row-major); simhash: [n_docs] uint64 or NULL.
+ */
+mrc_status mrc_signature(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float* sig,
+                         uint64_t* simhash);
+
+/*
+ * Signature comparison with a fused threshold: the cosine of two signatures
+ * (the "multi reference cosine" of Eq. 2) >= tau. query_sig == NULL compares
+ * all index pairs i < j; otherwise query_sig holds nq raw float32 signatures
+ * ([nq * k], e.g. from mrc_signature) compared against every index document.
+ * The index's precision decides the arithmetic (see MRC_PREC_*): in the
+ * reduced-precision forms every candidate >= tau - margin is rescored in FP32
+ * and kept iff its FP32 cosine >= tau.
+ */
+mrc_status mrc_match(mrc_ctx* ctx, const mrc_index* index, const float* query_sig, int64_t nq, float tau,
+                     mrc_pair* pairs, int64_t capacity, int64_t* n_pairs);
+
+/*
+ * Exact cosine (Eq. 1) of the weighted term vectors of every pair i < j of
+ * `docs` (the ground truth of Section V), emitting pairs with cosine >= tau.
+ * Weights use the index's idf and weighting. FP32-accurate: frequent terms go
+ * through a tensor-core GEMM in fp16 hi/lo split arithmetic, the remaining
+ * terms through sparse postings, summed before the threshold.
+ */
+mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float tau,
+                           mrc_pair* pairs, int64_t capacity, int64_t* n_pairs);
+
+/*
+ * Simhash matching (Section III): Hamming distance popcount(a_i XOR b_j) <=
+ * hamming_max. b == NULL compares all pairs i < j of a; otherwise every
+ * (i in a, j in b). score = the Hamming distance.
+ */
+mrc_status simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
+                         int32_t hamming_max, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs);
+
+/* Index introspection and export (for checks and persistence). Each output
+ * pointer may be NULL to skip it; sizes follow mrc_index_info. */
+mrc_status mrc_index_get_info(const mrc_index* index, mrc_index_info* info);
+mrc_status mrc_index_export(mrc_ctx* ctx, const mrc_index* index, float* sig /*[n*k]*/, uint64_t* simhash /*[n]*/,
+                            int32_t* df /*[vocab]*/, float* idf /*[vocab]*/, int32_t* part /*[vocab]*/,
+                            double* rnorm /*[k]*/);
+
+/* Persist an index (params, idf, references, signatures, Simhashes) to a
+ * versioned binary file, and load it back onto ctx's device. */
+mrc_status mrc_index_save(mrc_ctx* ctx, const mrc_index* index, const char* path);
+mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out);
+void mrc_index_free(mrc_index* index);
+
+/*
+ * Per-kernel timing. With timing on, every kernel the context launches is
+ * bracketed by CUDA events on the context's stream; mrc_ctx_kernel_stat
+ * returns, for kernel slot `slot` (0..count-1), its name, launches, summed
+ * device time and the algorithmic bytes and flops its launches account for.
+ * Returns the number of kernel slots, or -1 when `slot` is out of range.
+ */
+mrc_status mrc_ctx_set_timing(mrc_ctx* ctx, int32_t on);
+int32_t mrc_ctx_kernel_stat(mrc_ctx* ctx, int32_t slot, char* name /*[64]*/, int64_t* launches,
+                            double* total_ms, double* bytes, double* flops);
+void mrc_ctx_reset_stats(mrc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRC_H_ */

@@ -1,0 +1,957 @@
+// api.cu -- the C ABI declared in include/mrc.h: contexts, indexes and the five entry points.
+//
+// Host-side logic only; every per-document and per-pair step runs in the
+// kernels of ingest.cu, compare_tc.cu, simhash_match.cu and tail.cu. The one
+// host computation on the data path is the reference selection of Section IV
+// (a sort of the vocabulary by document frequency, once per index build).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+
+using mrc::Buffer;
+
+namespace mrc {
+
+mrc_status fail(mrc_ctx* ctx, mrc_status st, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return st;
+}
+
+mrc_status cuda_fail(mrc_ctx* ctx, cudaError_t e, const char* what) {
+  cudaGetLastError();
+  const mrc_status st = (e == cudaErrorMemoryAllocation) ? MRC_ERR_OOM : MRC_ERR_CUDA;
+  return fail(ctx, st, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void* ws_get(mrc_ctx* ctx, const char* slot, size_t bytes, mrc_status* st) {
+  Buffer& b = ctx->ws[slot];
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return b.ptr;
+  if (b.ptr) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+  }
+  // grow geometrically so that slowly growing requests do not reallocate every call
+  size_t want = std::max(bytes + bytes / 8, (size_t)256);
+  void* p = nullptr;
+  if (cudaMalloc(&p, want) != cudaSuccess) {
+    cudaGetLastError();
+    if (st) *st = MRC_ERR_OOM;
+    ctx->last_error = std::string("device allocation of ") + std::to_string(want) + " bytes for " + slot + " failed";
+    return nullptr;
+  }
+  b.ptr = p;
+  b.bytes = want;
+  return p;
+}
+
+void timing_begin(mrc_ctx* ctx, const char* name, double bytes, double flops, cudaEvent_t* ev_out) {
+  *ev_out = nullptr;
+  if (!ctx->timing) return;
+  auto get = [&]() {
+    cudaEvent_t e;
+    if (!ctx->free_events.empty()) {
+      e = ctx->free_events.back();
+      ctx->free_events.pop_back();
+    } else {
+      cudaEventCreate(&e);
+    }
+    return e;
+  };
+  PendingTiming pt;
+  pt.name = name;
+  pt.start = get();
+  pt.stop = get();
+  pt.bytes = bytes;
+  pt.flops = flops;
+  cudaEventRecord(pt.start, ctx->stream);
+  ctx->pending.push_back(pt);
+  *ev_out = pt.start;
+}
+
+void timing_end(mrc_ctx* ctx, cudaEvent_t start) {
+  if (!start) return;
+  for (auto it = ctx->pending.rbegin(); it != ctx->pending.rend(); ++it)
+    if (it->start == start) {
+      cudaEventRecord(it->stop, ctx->stream);
+      return;
+    }
+}
+
+static void collect_timings(mrc_ctx* ctx) {
+  for (auto& pt : ctx->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(pt.stop) == cudaSuccess) cudaEventElapsedTime(&ms, pt.start, pt.stop);
+    cudaGetLastError();
+    KernelStat* ks = nullptr;
+    for (auto& s : ctx->stats)
+      if (s.first == pt.name) ks = &s.second;
+    if (!ks) {
+      ctx->stats.emplace_back(pt.name, KernelStat{});
+      ks = &ctx->stats.back().second;
+    }
+    ks->launches += 1;
+    ks->ms += ms;
+    ks->bytes += pt.bytes;
+    ks->flops += pt.flops;
+    ctx->free_events.push_back(pt.start);
+    ctx->free_events.push_back(pt.stop);
+  }
+  ctx->pending.clear();
+}
+
+}  // namespace mrc
+
+using namespace mrc;
+
+namespace {
+
+constexpr uint64_t kDefaultSeed = 0x1810030990ull;
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device copy of a caller buffer (the buffer itself when it already lives on the device).
+const void* stage_in(mrc_ctx* ctx, const char* slot, const void* p, size_t bytes, mrc_status* st) {
+  if (!p || is_device_ptr(p)) return p;
+  void* d = ws_get(ctx, slot, bytes, st);
+  if (!d) return nullptr;
+  if (bytes && cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+    *st = cuda_fail(ctx, cudaGetLastError(), "host-to-device copy");
+    return nullptr;
+  }
+  return d;
+}
+
+struct Scope {
+  explicit Scope(mrc_ctx* c) : ctx(c) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    prev = cur;
+    if (cur != ctx->device) cudaSetDevice(ctx->device);
+  }
+  ~Scope() {
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+  }
+  mrc_ctx* ctx;
+  int prev;
+};
+
+mrc_status check_err_word(mrc_ctx* ctx, int32_t* d_err) {
+  int32_t h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel execution");
+  if (h & kErrTimeout) return fail(ctx, MRC_ERR_TIMEOUT, "a bounded device wait expired");
+  if (h & kErrBadOffsets) return fail(ctx, MRC_ERR_INVALID, "offsets must start at 0 and be non-decreasing");
+  if (h & kErrTooLong)
+    return fail(ctx, MRC_ERR_UNSUPPORTED, "a document is longer than MRC_MAX_DOC_TOKENS tokens");
+  if (h & kErrBadToken) return fail(ctx, MRC_ERR_INVALID, "a token id is outside [0, vocab)");
+  if (h & kErrTable) return fail(ctx, MRC_ERR_CUDA, "internal: per-document term table overflow");
+  return MRC_OK;
+}
+
+int32_t* call_err(mrc_ctx* ctx, mrc_status* st) {
+  int32_t* e = (int32_t*)ws_get(ctx, "call.err", sizeof(int32_t), st);
+  if (e) cudaMemsetAsync(e, 0, sizeof(int32_t), ctx->stream);
+  return e;
+}
+
+// Docs on the device: host arrays are copied in; returns MRC_OK or an error.
+mrc_status stage_docs(mrc_ctx* ctx, const mrc_docs* docs, const char* tag, DocsDev* out, int32_t* d_err) {
+  if (!docs || docs->n_docs < 0 || (docs->n_docs > 0 && (!docs->offsets)))
+    return fail(ctx, MRC_ERR_INVALID, "docs: NULL or negative n_docs");
+  if (docs->n_docs >= (1ll << 31) - 1) return fail(ctx, MRC_ERR_UNSUPPORTED, "more than 2^31 - 2 documents");
+  const int64_t n = docs->n_docs;
+  mrc_status st = MRC_OK;
+  int64_t T = 0;
+  const bool off_dev = is_device_ptr(docs->offsets);
+  if (off_dev) {
+    if (cudaMemcpy(&T, docs->offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return cuda_fail(ctx, cudaGetLastError(), "reading offsets[n_docs]");
+  } else {
+    T = docs->offsets[n];
+  }
+  if (T < 0) return fail(ctx, MRC_ERR_INVALID, "offsets[n_docs] < 0");
+  if (T > 0 && !docs->tokens) return fail(ctx, MRC_ERR_INVALID, "tokens is NULL");
+  std::string s1 = std::string(tag) + ".offsets", s2 = std::string(tag) + ".tokens";
+  out->n_docs = n;
+  out->offsets = (const int64_t*)stage_in(ctx, s1.c_str(), docs->offsets, sizeof(int64_t) * (size_t)(n + 1), &st);
+  if (st != MRC_OK) return st;
+  out->tokens = (const int32_t*)stage_in(ctx, s2.c_str(), docs->tokens, sizeof(int32_t) * (size_t)T, &st);
+  if (st != MRC_OK) return st;
+  if (T == 0) {
+    out->tokens = (const int32_t*)ws_get(ctx, "empty.tokens", 16, &st);
+    if (st != MRC_OK) return st;
+  }
+  out->n_tokens = T;
+  out->err = d_err;
+  return MRC_OK;
+}
+
+bool valid_params(const mrc_params* p, std::string* why) {
+  if (!p) return *why = "params is NULL", false;
+  if (p->k < 1 || p->k > MRC_MAX_K) return *why = "k must be in [1, MRC_MAX_K]", false;
+  if (p->select_mode < MRC_SELECT_ALL || p->select_mode > MRC_SELECT_DF1) return *why = "bad select_mode", false;
+  if (p->weighting != MRC_WEIGHT_COUNT && p->weighting != MRC_WEIGHT_TFIDF) return *why = "bad weighting", false;
+  if (p->precision < MRC_PREC_FP32 || p->precision > MRC_PREC_FP16) return *why = "bad precision", false;
+  if (!(p->margin >= 0.f)) return *why = "margin must be >= 0", false;
+  return true;
+}
+
+int32_t round_up(int32_t x, int32_t m) { return (x + m - 1) / m * m; }
+
+// Reference selection (Section IV): rank terms by df descending, ties by id;
+// zero-df terms dropped; REGION / ALL / DF1 pick the selection; partition p
+// holds selection positions [floor(pL/k), floor((p+1)L/k)).
+int64_t select_references(const std::vector<int32_t>& df, int64_t n_docs, const mrc_params& p,
+                          std::vector<int32_t>* part) {
+  const int32_t V = (int32_t)df.size();
+  part->assign(V, -1);
+  const int64_t L = p.L < 0 ? 32ll * p.k : p.L;
+  std::vector<int32_t> sel;
+  if (p.select_mode == MRC_SELECT_DF1) {
+    for (int32_t t = 0; t < V && (int64_t)sel.size() < L; ++t)
+      if (df[t] == 1) sel.push_back(t);
+  } else {
+    std::vector<int32_t> ranked;
+    ranked.reserve(V);
+    for (int32_t t = 0; t < V; ++t)
+      if (df[t] > 0) ranked.push_back(t);
+    std::stable_sort(ranked.begin(), ranked.end(), [&](int32_t a, int32_t b) { return df[a] > df[b]; });
+    if (p.select_mode == MRC_SELECT_ALL) {
+      sel = ranked;
+    } else {
+      int64_t start = p.region_start;
+      if (start < 0) {
+        start = (int64_t)ranked.size();
+        for (size_t q = 0; q < ranked.size(); ++q)
+          if ((double)df[ranked[q]] <= (double)n_docs / 100.0) {
+            start = (int64_t)q;
+            break;
+          }
+      }
+      for (int64_t q = start; q < (int64_t)ranked.size() && q < start + L; ++q) sel.push_back(ranked[q]);
+    }
+  }
+  const int64_t n = (int64_t)sel.size();
+  for (int32_t q = 0; q < p.k; ++q)
+    for (int64_t x = (int64_t)q * n / p.k; x < (int64_t)(q + 1) * n / p.k; ++x) (*part)[sel[x]] = q;
+  return n;
+}
+
+template <typename T>
+mrc_status dev_alloc(mrc_ctx* ctx, T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc((void**)p, sizeof(T) * count) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, MRC_ERR_OOM, std::string("device allocation failed: ") + what);
+  }
+  return MRC_OK;
+}
+
+void free_index_arrays(mrc_index* x) {
+  void* ptrs[] = {x->df,    x->idf,   x->tinfo, x->rinv,    x->sig,  x->sig_unit,
+                  x->simhash, x->op_hi, x->op_lo, x->op_e4m3, x->qnorm};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+// Uploads term info (idf under the weighting, partition) and 1/|R_p|.
+mrc_status upload_references(mrc_ctx* ctx, mrc_index* x) {
+  const int32_t V = x->vocab;
+  std::vector<TermInfo> ti(V);
+  for (int32_t t = 0; t < V; ++t) {
+    ti[t].idf = x->params.weighting == MRC_WEIGHT_TFIDF ? x->h_idf[t] : 1.0f;
+    ti[t].code = x->h_part[t];
+  }
+  // |R_p| from the same float idf the kernels use: each reference term weighs 1 * idf(t)
+  x->h_rnorm.assign(x->k, 0.0);
+  for (int32_t t = 0; t < V; ++t)
+    if (x->h_part[t] >= 0) {
+      const double r = ti[t].idf;
+      x->h_rnorm[x->h_part[t]] += r * r;
+    }
+  std::vector<float> rinv(x->k);
+  for (int32_t q = 0; q < x->k; ++q) {
+    x->h_rnorm[q] = std::sqrt(x->h_rnorm[q]);
+    rinv[q] = x->h_rnorm[q] > 0 ? (float)(1.0 / x->h_rnorm[q]) : 0.f;
+  }
+  cudaError_t e = cudaMemcpyAsync(x->tinfo, ti.data(), sizeof(TermInfo) * V, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(x->rinv, rinv.data(), sizeof(float) * x->k, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "uploading references");
+  return MRC_OK;
+}
+
+mrc_status alloc_signature_arrays(mrc_ctx* ctx, mrc_index* x) {
+  const size_t n = (size_t)std::max<int64_t>(x->n_docs, 1);
+  mrc_status st;
+  if ((st = dev_alloc(ctx, &x->sig, n * x->k, "signatures")) != MRC_OK) return st;
+  if ((st = dev_alloc(ctx, &x->sig_unit, n * x->k, "unit signatures")) != MRC_OK) return st;
+  if ((st = dev_alloc(ctx, &x->simhash, n, "simhash")) != MRC_OK) return st;
+  if (x->params.precision == MRC_PREC_FP32 || x->params.precision == MRC_PREC_FP16) {
+    uint16_t* h = nullptr;
+    if ((st = dev_alloc(ctx, &h, n * x->kp, "fp16 operands")) != MRC_OK) return st;
+    x->op_hi = h;
+  }
+  if (x->params.precision == MRC_PREC_FP32) {
+    uint16_t* l = nullptr;
+    if ((st = dev_alloc(ctx, &l, n * x->kp, "fp16 low operands")) != MRC_OK) return st;
+    x->op_lo = l;
+  }
+  if (x->params.precision == MRC_PREC_BF16_FP8) {
+    uint8_t* q = nullptr;
+    if ((st = dev_alloc(ctx, &q, n * x->kp8, "e4m3 operands")) != MRC_OK) return st;
+    x->op_e4m3 = q;
+    if ((st = dev_alloc(ctx, &x->qnorm, n, "e4m3 row norms")) != MRC_OK) return st;
+  }
+  return MRC_OK;
+}
+
+SigOut index_sig_out(mrc_index* x) {
+  SigOut o{};
+  o.sig = x->sig;
+  o.sig_unit = x->sig_unit;
+  o.simhash = x->simhash;
+  o.op_hi = x->op_hi;
+  o.op_lo = x->op_lo;
+  o.op_e4m3 = x->op_e4m3;
+  o.qnorm = x->qnorm;
+  o.kp = x->op_hi ? x->kp : 0;
+  o.kp8 = x->op_e4m3 ? x->kp8 : 0;
+  return o;
+}
+
+// Copies device pairs to a host destination (when `pairs` is host memory).
+mrc_status finish_pairs(mrc_ctx* ctx, mrc_pair* user, mrc_pair* dev, unsigned long long* d_count, int64_t capacity,
+                        int64_t* n_pairs) {
+  unsigned long long* hc = (unsigned long long*)ctx->pinned;
+  cudaError_t e = cudaMemcpyAsync(hc, d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reading pair count");
+  const int64_t total = (int64_t)*hc;
+  if (n_pairs) *n_pairs = total;
+  const int64_t m = std::min<int64_t>(total, capacity);
+  if (user != dev && m > 0) {
+    e = cudaMemcpyAsync(user, dev, sizeof(mrc_pair) * (size_t)m, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copying pairs to host");
+  }
+  if (total > capacity)
+    return fail(ctx, MRC_ERR_CAPACITY, "more pairs than capacity; *n_pairs holds the total");
+  return MRC_OK;
+}
+
+mrc_pair* pair_dest(mrc_ctx* ctx, mrc_pair* user, int64_t capacity, mrc_status* st) {
+  if (capacity <= 0) return (mrc_pair*)ws_get(ctx, "pairs.none", sizeof(mrc_pair), st);
+  if (user && is_device_ptr(user)) return user;
+  if (!user) {
+    *st = fail(ctx, MRC_ERR_INVALID, "pairs is NULL with capacity > 0");
+    return nullptr;
+  }
+  return (mrc_pair*)ws_get(ctx, "pairs.staging", sizeof(mrc_pair) * (size_t)capacity, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+void mrc_params_default(mrc_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->k = 8;
+  p->L = -1;
+  p->select_mode = MRC_SELECT_REGION;
+  p->region_start = -1;
+  p->weighting = MRC_WEIGHT_TFIDF;
+  p->precision = MRC_PREC_FP32;
+  p->tau = 0.9f;
+  p->margin = 0.02f;
+  p->hamming_max = 3;
+  p->seed = kDefaultSeed;
+}
+
+mrc_status mrc_ctx_create(void* cuda_stream, mrc_ctx** out) {
+  if (!out) return MRC_ERR_INVALID;
+  *out = nullptr;
+  mrc_ctx* c = new (std::nothrow) mrc_ctx();
+  if (!c) return MRC_ERR_OOM;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return MRC_ERR_CUDA;
+  }
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c->device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, c->device);
+  if (major != 10) {
+    delete c;
+    return MRC_ERR_UNSUPPORTED;  // built for sm_103a (Blackwell Ultra) only
+  }
+  c->stream = (cudaStream_t)cuda_stream;
+  if (cudaMallocHost(&c->pinned, 4096) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return MRC_ERR_OOM;
+  }
+  *out = c;
+  return MRC_OK;
+}
+
+void mrc_ctx_destroy(mrc_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->ws)
+    if (kv.second.ptr) cudaFree(kv.second.ptr);
+  for (auto& pt : ctx->pending) {
+    cudaEventDestroy(pt.start);
+    cudaEventDestroy(pt.stop);
+  }
+  for (auto e : ctx->free_events) cudaEventDestroy(e);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  delete ctx;
+}
+
+const char* mrc_last_error(const mrc_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, const mrc_params* params,
+                           mrc_index** out) {
+  if (!ctx || !out) return MRC_ERR_INVALID;
+  *out = nullptr;
+  Scope scope(ctx);
+  std::string why;
+  if (!valid_params(params, &why)) return fail(ctx, MRC_ERR_INVALID, why);
+  if (vocab < 1) return fail(ctx, MRC_ERR_INVALID, "vocab must be >= 1");
+  if (!corpus || corpus->n_docs < 1) return fail(ctx, MRC_ERR_INVALID, "the index corpus needs >= 1 document");
+  mrc_status st = MRC_OK;
+  int32_t* d_err = call_err(ctx, &st);
+  if (!d_err) return st;
+  DocsDev d;
+  if ((st = stage_docs(ctx, corpus, "build", &d, d_err)) != MRC_OK) return st;
+
+  mrc_index* x = new mrc_index();
+  x->device = ctx->device;
+  x->params = *params;
+  x->n_docs = d.n_docs;
+  x->vocab = vocab;
+  x->k = params->k;
+  x->kp = round_up(params->k, 64);
+  x->kp8 = round_up(params->k, 128);
+  auto bail = [&](mrc_status s) {
+    cudaStreamSynchronize(ctx->stream);
+    free_index_arrays(x);
+    delete x;
+    return s;
+  };
+  if ((st = dev_alloc(ctx, &x->df, vocab, "df")) != MRC_OK) return bail(st);
+  if ((st = dev_alloc(ctx, &x->idf, vocab, "idf")) != MRC_OK) return bail(st);
+  if ((st = dev_alloc(ctx, &x->tinfo, vocab, "term info")) != MRC_OK) return bail(st);
+  if ((st = dev_alloc(ctx, &x->rinv, x->k, "reference norms")) != MRC_OK) return bail(st);
+  cudaError_t e = cudaMemsetAsync(x->df, 0, sizeof(int32_t) * vocab, ctx->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
+
+  // a1: document frequencies, then idf
+  e = launch_df(ctx, d, x->df, vocab);
+  if (e != cudaSuccess && e != cudaErrorInvalidValue) return bail(cuda_fail(ctx, e, "df pass"));
+  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);
+  e = launch_idf(ctx, d.n_docs, x->df, vocab, params->weighting, x->idf, nullptr);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "idf"));
+  x->h_df.resize(vocab);
+  x->h_idf.resize(vocab);
+  e = cudaMemcpyAsync(x->h_df.data(), x->df, sizeof(int32_t) * vocab, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(x->h_idf.data(), x->idf, sizeof(float) * vocab, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "reading df"));
+
+  // references (host sort of the vocabulary), then their device tables
+  x->L_used = select_references(x->h_df, d.n_docs, *params, &x->h_part);
+  if ((st = upload_references(ctx, x)) != MRC_OK) return bail(st);
+
+  // a2-a4: signatures, Simhash, packed compare operands
+  if ((st = alloc_signature_arrays(ctx, x)) != MRC_OK) return bail(st);
+  if (x->op_hi) cudaMemsetAsync(x->op_hi, 0, sizeof(uint16_t) * (size_t)x->n_docs * x->kp, ctx->stream);
+  if (x->op_lo) cudaMemsetAsync(x->op_lo, 0, sizeof(uint16_t) * (size_t)x->n_docs * x->kp, ctx->stream);
+  if (x->op_e4m3) cudaMemsetAsync(x->op_e4m3, 0, (size_t)x->n_docs * x->kp8, ctx->stream);
+  e = launch_signature(ctx, d, vocab, x->tinfo, x->rinv, x->k, params->precision == MRC_PREC_BF16_FP8, params->seed,
+                       index_sig_out(x));
+  if (e != cudaSuccess && e != cudaErrorInvalidValue) return bail(cuda_fail(ctx, e, "signature pass"));
+  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);
+  *out = x;
+  return MRC_OK;
+}
+
+mrc_status mrc_signature(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float* sig, uint64_t* simhash) {
+  if (!ctx || !index) return MRC_ERR_INVALID;
+  Scope scope(ctx);
+  if (!docs) return fail(ctx, MRC_ERR_INVALID, "docs is NULL");
+  if (docs->n_docs == 0) return MRC_OK;
+  if (!sig && !simhash) return fail(ctx, MRC_ERR_INVALID, "no output requested");
+  mrc_status st = MRC_OK;
+  int32_t* d_err = call_err(ctx, &st);
+  if (!d_err) return st;
+  DocsDev d;
+  if ((st = stage_docs(ctx, docs, "sig", &d, d_err)) != MRC_OK) return st;
+  const int64_t n = d.n_docs;
+  const bool sig_host = sig && !is_device_ptr(sig), sh_host = simhash && !is_device_ptr(simhash);
+  SigOut o{};
+  o.sig = sig_host ? (float*)ws_get(ctx, "sig.out", sizeof(float) * (size_t)n * index->k, &st) : sig;
+  o.simhash = sh_host ? (uint64_t*)ws_get(ctx, "sig.simhash", sizeof(uint64_t) * (size_t)n, &st) : simhash;
+  if (st != MRC_OK) return st;
+  cudaError_t e = launch_signature(ctx, d, index->vocab, index->tinfo, index->rinv, index->k,
+                                   index->params.precision == MRC_PREC_BF16_FP8, index->params.seed, o);
+  if (e != cudaSuccess && e != cudaErrorInvalidValue) return cuda_fail(ctx, e, "signature pass");
+  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;
+  if (sig_host) e = cudaMemcpyAsync(sig, o.sig, sizeof(float) * (size_t)n * index->k, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess && sh_host)
+    e = cudaMemcpyAsync(simhash, o.simhash, sizeof(uint64_t) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess && (sig_host || sh_host)) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "copying signatures");
+  return MRC_OK;
+}
+
+mrc_status mrc_match(mrc_ctx* ctx, const mrc_index* index, const float* query_sig, int64_t nq, float tau,
+                     mrc_pair* pairs, int64_t capacity, int64_t* n_pairs) {
+  if (!ctx || !index) return MRC_ERR_INVALID;
+  Scope scope(ctx);
+  if (capacity < 0) return fail(ctx, MRC_ERR_INVALID, "capacity < 0");
+  if (query_sig && nq < 0) return fail(ctx, MRC_ERR_INVALID, "nq < 0");
+  if (n_pairs) *n_pairs = 0;
+  mrc_status st = MRC_OK;
+  int32_t* d_err = call_err(ctx, &st);
+  if (!d_err) return st;
+  const int64_t N = index->n_docs;
+  const int32_t prec = index->params.precision;
+  unsigned long long* d_count = (unsigned long long*)ws_get(ctx, "match.count", 2 * sizeof(unsigned long long), &st);
+  mrc_pair* dst = pair_dest(ctx, pairs, capacity, &st);
+  if (st != MRC_OK) return st;
+  cudaMemsetAsync(d_count, 0, 2 * sizeof(unsigned long long), ctx->stream);
+  if ((query_sig && nq == 0) || (!query_sig && N < 2)) return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
+
+  // query operands (packed unit signatures) or the index itself
+  const void *a_hi = index->op_hi, *a_lo = index->op_lo, *a8 = index->op_e4m3;
+  const float* a_unit = index->sig_unit;
+  const float* a_norm = index->qnorm;
+  int64_t na = N;
+  if (query_sig) {
+    const float* q = (const float*)stage_in(ctx, "match.q", query_sig, sizeof(float) * (size_t)nq * index->k, &st);
+    if (st != MRC_OK) return st;
+    float* qu = (float*)ws_get(ctx, "match.qunit", sizeof(float) * (size_t)nq * index->k, &st);
+    void* qh = prec != MRC_PREC_BF16_FP8 ? ws_get(ctx, "match.qhi", 2 * (size_t)nq * index->kp, &st) : nullptr;
+    void* ql = prec == MRC_PREC_FP32 ? ws_get(ctx, "match.qlo", 2 * (size_t)nq * index->kp, &st) : nullptr;
+    void* q8 = prec == MRC_PREC_BF16_FP8 ? ws_get(ctx, "match.q8", (size_t)nq * index->kp8, &st) : nullptr;
+    float* qn = prec == MRC_PREC_BF16_FP8 ? (float*)ws_get(ctx, "match.qnorm", sizeof(float) * (size_t)nq, &st)
+                                          : nullptr;
+    if (st != MRC_OK) return st;
+    cudaError_t e =
+        launch_pack(ctx, q, nq, index->k, 1, qh, ql, q8, qn, qu, qh ? index->kp : 0, q8 ? index->kp8 : 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "packing queries");
+    a_hi = qh;
+    a_lo = ql;
+    a8 = q8;
+    a_unit = qu;
+    a_norm = qn;
+    na = nq;
+  }
+
+  GemmArgs g{};
+  g.na = na;
+  g.nb = N;
+  g.triangle = query_sig ? 0 : 1;
+  g.err = d_err;
+  g.capacity = capacity;
+  g.out_scale = 1.0f;
+  if (prec == MRC_PREC_FP32) {
+    g.fmt = OP_SPLIT16;
+    g.a_hi = a_hi;
+    g.a_lo = a_lo;
+    g.b_hi = index->op_hi;
+    g.b_lo = index->op_lo;
+    g.kbytes = index->kp * 2;
+    g.thresh = tau;
+    g.pairs = dst;
+    g.count = d_count;
+    cudaError_t e = launch_gemm_compare(ctx, g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "signature compare");
+  } else {
+    // reduced precision: candidates at tau - margin, then FP32 rescoring
+    g.fmt = prec == MRC_PREC_FP16 ? OP_F16 : OP_E4M3;
+    g.a_hi = prec == MRC_PREC_FP16 ? a_hi : a8;
+    g.b_hi = prec == MRC_PREC_FP16 ? index->op_hi : index->op_e4m3;
+    g.kbytes = prec == MRC_PREC_FP16 ? index->kp * 2 : index->kp8;
+    g.out_scale = prec == MRC_PREC_FP16 ? 1.0f : 1.0f / (kE4M3Scale * kE4M3Scale);
+    g.a_norm = a_norm;
+    g.b_norm = index->qnorm;
+    g.thresh = tau - index->params.margin;
+    int64_t cand_cap = std::max<int64_t>(4 * capacity, 1 << 20);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      mrc_pair* cand = (mrc_pair*)ws_get(ctx, "match.cand", sizeof(mrc_pair) * (size_t)cand_cap, &st);
+      if (st != MRC_OK) return st;
+      cudaMemsetAsync(d_count, 0, 2 * sizeof(unsigned long long), ctx->stream);
+      g.pairs = cand;
+      g.count = d_count + 1;
+      g.capacity = cand_cap;
+      cudaError_t e = launch_gemm_compare(ctx, g);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "signature compare");
+      unsigned long long* hc = (unsigned long long*)ctx->pinned;
+      e = cudaMemcpyAsync(hc, d_count + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "reading candidate count");
+      const int64_t nc = (int64_t)*hc;
+      if (nc <= cand_cap) {
+        e = launch_rescore(ctx, cand, d_count + 1, cand_cap, a_unit, index->sig_unit, index->k, tau, dst, d_count,
+                           capacity);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "rescoring");
+        break;
+      }
+      cand_cap = nc + nc / 8 + 1024;
+    }
+  }
+  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;
+  return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
+}
+
+mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float tau, mrc_pair* pairs,
+                           int64_t capacity, int64_t* n_pairs) {
+  if (!ctx || !index) return MRC_ERR_INVALID;
+  Scope scope(ctx);
+  if (capacity < 0) return fail(ctx, MRC_ERR_INVALID, "capacity < 0");
+  if (n_pairs) *n_pairs = 0;
+  mrc_status st = MRC_OK;
+  int32_t* d_err = call_err(ctx, &st);
+  if (!d_err) return st;
+  DocsDev d;
+  if ((st = stage_docs(ctx, docs, "cos", &d, d_err)) != MRC_OK) return st;
+  const int64_t N = d.n_docs;
+  const int32_t V = index->vocab;
+  unsigned long long* d_count = (unsigned long long*)ws_get(ctx, "cos.count", sizeof(unsigned long long), &st);
+  mrc_pair* dst = pair_dest(ctx, pairs, capacity, &st);
+  if (st != MRC_OK) return st;
+  cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), ctx->stream);
+  if (N < 2) return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
+
+  // document frequencies within these documents decide the head/tail split
+  int32_t* df = (int32_t*)ws_get(ctx, "cos.df", sizeof(int32_t) * V, &st);
+  if (st != MRC_OK) return st;
+  cudaMemsetAsync(df, 0, sizeof(int32_t) * V, ctx->stream);
+  cudaError_t e = launch_df(ctx, d, df, V);
+  if (e != cudaSuccess && e != cudaErrorInvalidValue) return cuda_fail(ctx, e, "df pass");
+  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;
+  std::vector<int32_t> hdf(V);
+  e = cudaMemcpy(hdf.data(), df, sizeof(int32_t) * V, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reading df");
+
+  // head = terms whose postings are dense enough that a tensor-core column beats
+  // sparse products: df >= max(32, N / 48); tail = the other terms with df >= 2
+  const int64_t cut = std::max<int64_t>(32, N / 48);
+  std::vector<int32_t> head;
+  for (int32_t t = 0; t < V; ++t)
+    if (hdf[t] >= cut) head.push_back(t);
+  std::stable_sort(head.begin(), head.end(), [&](int32_t a, int32_t b) { return hdf[a] > hdf[b]; });
+  const int32_t kd = std::max<int32_t>(64, round_up((int32_t)head.size(), 64));
+  std::vector<int32_t> colmap(V, -1);
+  for (size_t c = 0; c < head.size(); ++c) colmap[head[c]] = (int32_t)c;
+  std::vector<int64_t> tstart(V, 0);
+  int64_t n_post = 0;
+  double tail_work = 0.0;
+  for (int32_t t = 0; t < V; ++t)
+    if (colmap[t] < 0 && hdf[t] >= 2) {
+      colmap[t] = -2;
+      tstart[t] = n_post;
+      n_post += hdf[t];
+      tail_work += (double)hdf[t] * (double)(hdf[t] - 1) / 2.0;
+    }
+  const int64_t ldh = (N + 3) / 4 * 4;
+  if ((double)N * (double)ldh * 4.0 > 64e9)
+    return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more documents than the 64 GB score buffer allows");
+
+  int32_t* d_colmap = (int32_t*)ws_get(ctx, "cos.colmap", sizeof(int32_t) * V, &st);
+  int64_t* d_tstart = (int64_t*)ws_get(ctx, "cos.tstart", sizeof(int64_t) * V, &st);
+  int32_t* d_tfill = (int32_t*)ws_get(ctx, "cos.tfill", sizeof(int32_t) * V, &st);
+  int32_t* d_pdoc = (int32_t*)ws_get(ctx, "cos.pdoc", sizeof(int32_t) * (size_t)std::max<int64_t>(n_post, 1), &st);
+  float* d_pw = (float*)ws_get(ctx, "cos.pw", sizeof(float) * (size_t)std::max<int64_t>(n_post, 1), &st);
+  int32_t* d_rcnt = (int32_t*)ws_get(ctx, "cos.rcnt", sizeof(int32_t) * (size_t)N, &st);
+  int32_t* d_rterm = (int32_t*)ws_get(ctx, "cos.rterm", sizeof(int32_t) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
+  float* d_rw = (float*)ws_get(ctx, "cos.rw", sizeof(float) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
+  void* d_hhi = ws_get(ctx, "cos.hhi", 2 * (size_t)N * kd, &st);
+  void* d_hlo = ws_get(ctx, "cos.hlo", 2 * (size_t)N * kd, &st);
+  float* d_H = (float*)ws_get(ctx, "cos.H", sizeof(float) * (size_t)N * ldh, &st);
+  if (st != MRC_OK) return st;
+  e = cudaMemcpyAsync(d_colmap, colmap.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_tstart, tstart.data(), sizeof(int64_t) * V, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_tfill, 0, sizeof(int32_t) * V, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_hhi, 0, 2 * (size_t)N * kd, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_hlo, 0, 2 * (size_t)N * kd, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cosine set-up");
+
+  // unit weights: dense head operands and tail postings
+  DenseOut o{};
+  o.colmap = d_colmap;
+  o.kd = kd;
+  o.head_hi = d_hhi;
+  o.head_lo = d_hlo;
+  o.tail_start = d_tstart;
+  o.tail_fill = d_tfill;
+  o.post_doc = d_pdoc;
+  o.post_w = d_pw;
+  o.row_cnt = d_rcnt;
+  o.row_term = d_rterm;
+  o.row_w = d_rw;
+  e = launch_densify(ctx, d, V, index->tinfo, o);
+  if (e != cudaSuccess && e != cudaErrorInvalidValue) return cuda_fail(ctx, e, "densify");
+
+  // head: tensor-core GEMM of the unit head columns (FP32-accurate split), stored
+  GemmArgs g{};
+  g.fmt = OP_SPLIT16;
+  g.a_hi = g.b_hi = d_hhi;
+  g.a_lo = g.b_lo = d_hlo;
+  g.na = g.nb = N;
+  g.kbytes = kd * 2;
+  g.triangle = 1;
+  g.out_scale = 1.0f;
+  g.store = d_H;
+  g.ld = ldh;
+  g.err = d_err;
+  e = launch_gemm_compare(ctx, g);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "head GEMM");
+
+  // tail: postings products added to the head scores, threshold, compaction
+  e = launch_cosine_tail(ctx, N, d_H, ldh, d.offsets, d_rcnt, d_rterm, d_rw, d_tstart, d_tfill, d_pdoc, d_pw, tau,
+                         dst, d_count, capacity, tail_work);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tail pass");
+  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;
+  return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
+}
+
+mrc_status simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
+                         int32_t hamming_max, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs) {
+  if (!ctx) return MRC_ERR_INVALID;
+  Scope scope(ctx);
+  if (na < 0 || (b && nb < 0) || capacity < 0 || (na > 0 && !a))
+    return fail(ctx, MRC_ERR_INVALID, "simhash_match: bad sizes or NULL input");
+  if (na >= (1ll << 31) || nb >= (1ll << 31)) return fail(ctx, MRC_ERR_UNSUPPORTED, "more than 2^31 fingerprints");
+  if (n_pairs) *n_pairs = 0;
+  mrc_status st = MRC_OK;
+  unsigned long long* d_count = (unsigned long long*)ws_get(ctx, "sh.count", sizeof(unsigned long long), &st);
+  mrc_pair* dst = pair_dest(ctx, pairs, capacity, &st);
+  if (st != MRC_OK) return st;
+  cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), ctx->stream);
+  const uint64_t* da = (const uint64_t*)stage_in(ctx, "sh.a", a, sizeof(uint64_t) * (size_t)na, &st);
+  const uint64_t* db = b ? (const uint64_t*)stage_in(ctx, "sh.b", b, sizeof(uint64_t) * (size_t)nb, &st) : nullptr;
+  if (st != MRC_OK) return st;
+  if (na > 0 && (!b || nb > 0)) {
+    cudaError_t e = launch_simhash_match(ctx, da, na, db, b ? nb : 0, hamming_max, dst, d_count, capacity);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "simhash match");
+  }
+  return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
+}
+
+mrc_status mrc_index_get_info(const mrc_index* x, mrc_index_info* info) {
+  if (!x || !info) return MRC_ERR_INVALID;
+  std::memset(info, 0, sizeof(*info));
+  info->n_docs = x->n_docs;
+  info->vocab = x->vocab;
+  info->k = x->k;
+  info->L_used = x->L_used;
+  info->precision = x->params.precision;
+  info->weighting = x->params.weighting;
+  info->kp = x->kp;
+  return MRC_OK;
+}
+
+mrc_status mrc_index_export(mrc_ctx* ctx, const mrc_index* x, float* sig, uint64_t* simhash, int32_t* df, float* idf,
+                            int32_t* part, double* rnorm) {
+  if (!ctx || !x) return MRC_ERR_INVALID;
+  Scope scope(ctx);
+  const size_t n = (size_t)x->n_docs;
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream);
+  };
+  cudaError_t e = cudaSuccess;
+  if (sig) e = cp(sig, x->sig, sizeof(float) * n * x->k);
+  if (e == cudaSuccess && simhash) e = cp(simhash, x->simhash, sizeof(uint64_t) * n);
+  if (e == cudaSuccess && df) e = cp(df, x->df, sizeof(int32_t) * x->vocab);
+  if (e == cudaSuccess && idf) e = cp(idf, x->idf, sizeof(float) * x->vocab);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "index export");
+  if (part) std::memcpy(part, x->h_part.data(), sizeof(int32_t) * x->vocab);
+  if (rnorm) std::memcpy(rnorm, x->h_rnorm.data(), sizeof(double) * x->k);
+  return MRC_OK;
+}
+
+void mrc_index_free(mrc_index* x) {
+  if (!x) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != x->device) cudaSetDevice(x->device);
+  cudaDeviceSynchronize();
+  free_index_arrays(x);
+  if (cur >= 0 && cur != x->device) cudaSetDevice(cur);
+  delete x;
+}
+
+// ---- persistence -------------------------------------------------------------------------
+static const char kMagic[8] = {'M', 'R', 'C', 'I', 'D', 'X', '0', '1'};
+
+mrc_status mrc_index_save(mrc_ctx* ctx, const mrc_index* x, const char* path) {
+  if (!ctx || !x || !path) return MRC_ERR_INVALID;
+  Scope scope(ctx);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(ctx, MRC_ERR_INVALID, std::string("cannot open ") + path);
+  const size_t n = (size_t)x->n_docs;
+  std::vector<float> sig(n * x->k), unit(n * x->k);
+  std::vector<uint64_t> sh(n);
+  cudaError_t e = cudaMemcpy(sig.data(), x->sig, sizeof(float) * sig.size(), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(unit.data(), x->sig_unit, sizeof(float) * unit.size(), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(sh.data(), x->simhash, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    std::fclose(f);
+    return cuda_fail(ctx, e, "index save");
+  }
+  const int32_t version = 1;
+  bool ok = std::fwrite(kMagic, 1, 8, f) == 8;
+  ok = ok && std::fwrite(&version, sizeof(version), 1, f) == 1;
+  ok = ok && std::fwrite(&x->params, sizeof(mrc_params), 1, f) == 1;
+  ok = ok && std::fwrite(&x->n_docs, sizeof(int64_t), 1, f) == 1;
+  ok = ok && std::fwrite(&x->vocab, sizeof(int32_t), 1, f) == 1;
+  ok = ok && std::fwrite(&x->L_used, sizeof(int64_t), 1, f) == 1;
+  ok = ok && std::fwrite(x->h_df.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
+  ok = ok && std::fwrite(x->h_idf.data(), sizeof(float), x->vocab, f) == (size_t)x->vocab;
+  ok = ok && std::fwrite(x->h_part.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
+  ok = ok && std::fwrite(sig.data(), sizeof(float), sig.size(), f) == sig.size();
+  ok = ok && std::fwrite(unit.data(), sizeof(float), unit.size(), f) == unit.size();
+  ok = ok && std::fwrite(sh.data(), sizeof(uint64_t), n, f) == n;
+  std::fclose(f);
+  if (!ok) return fail(ctx, MRC_ERR_INVALID, std::string("write failed: ") + path);
+  return MRC_OK;
+}
+
+mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
+  if (!ctx || !path || !out) return MRC_ERR_INVALID;
+  *out = nullptr;
+  Scope scope(ctx);
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(ctx, MRC_ERR_INVALID, std::string("cannot open ") + path);
+  char magic[8];
+  int32_t version = 0;
+  mrc_index* x = new mrc_index();
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0;
+  ok = ok && std::fread(&version, sizeof(version), 1, f) == 1 && version == 1;
+  ok = ok && std::fread(&x->params, sizeof(mrc_params), 1, f) == 1;
+  ok = ok && std::fread(&x->n_docs, sizeof(int64_t), 1, f) == 1;
+  ok = ok && std::fread(&x->vocab, sizeof(int32_t), 1, f) == 1;
+  ok = ok && std::fread(&x->L_used, sizeof(int64_t), 1, f) == 1;
+  std::string why;
+  ok = ok && valid_params(&x->params, &why) && x->vocab > 0 && x->n_docs > 0;
+  std::vector<float> sig, unit;
+  std::vector<uint64_t> sh;
+  if (ok) {
+    x->k = x->params.k;
+    x->kp = round_up(x->k, 64);
+    x->kp8 = round_up(x->k, 128);
+    x->device = ctx->device;
+    const size_t n = (size_t)x->n_docs;
+    x->h_df.resize(x->vocab);
+    x->h_idf.resize(x->vocab);
+    x->h_part.resize(x->vocab);
+    sig.resize(n * x->k);
+    unit.resize(n * x->k);
+    sh.resize(n);
+    ok = std::fread(x->h_df.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
+    ok = ok && std::fread(x->h_idf.data(), sizeof(float), x->vocab, f) == (size_t)x->vocab;
+    ok = ok && std::fread(x->h_part.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
+    ok = ok && std::fread(sig.data(), sizeof(float), sig.size(), f) == sig.size();
+    ok = ok && std::fread(unit.data(), sizeof(float), unit.size(), f) == unit.size();
+    ok = ok && std::fread(sh.data(), sizeof(uint64_t), n, f) == n;
+  }
+  std::fclose(f);
+  if (!ok) {
+    delete x;
+    return fail(ctx, MRC_ERR_INVALID, std::string("not a valid index file: ") + path);
+  }
+  mrc_status st;
+  auto bail = [&](mrc_status s) {
+    cudaStreamSynchronize(ctx->stream);
+    free_index_arrays(x);
+    delete x;
+    return s;
+  };
+  if ((st = dev_alloc(ctx, &x->df, x->vocab, "df")) != MRC_OK) return bail(st);
+  if ((st = dev_alloc(ctx, &x->idf, x->vocab, "idf")) != MRC_OK) return bail(st);
+  if ((st = dev_alloc(ctx, &x->tinfo, x->vocab, "term info")) != MRC_OK) return bail(st);
+  if ((st = dev_alloc(ctx, &x->rinv, x->k, "reference norms")) != MRC_OK) return bail(st);
+  if ((st = alloc_signature_arrays(ctx, x)) != MRC_OK) return bail(st);
+  const size_t n = (size_t)x->n_docs;
+  cudaError_t e = cudaMemcpy(x->df, x->h_df.data(), sizeof(int32_t) * x->vocab, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(x->idf, x->h_idf.data(), sizeof(float) * x->vocab, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(x->sig, sig.data(), sizeof(float) * sig.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(x->sig_unit, unit.data(), sizeof(float) * unit.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(x->simhash, sh.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "index load"));
+  if ((st = upload_references(ctx, x)) != MRC_OK) return bail(st);
+  // compare operands are re-packed from the unit signatures
+  if (x->op_hi) cudaMemsetAsync(x->op_hi, 0, 2 * n * x->kp, ctx->stream);
+  if (x->op_lo) cudaMemsetAsync(x->op_lo, 0, 2 * n * x->kp, ctx->stream);
+  if (x->op_e4m3) cudaMemsetAsync(x->op_e4m3, 0, n * x->kp8, ctx->stream);
+  e = launch_pack(ctx, x->sig_unit, x->n_docs, x->k, 0, x->op_hi, x->op_lo, x->op_e4m3, x->qnorm, nullptr,
+                  x->op_hi ? x->kp : 0, x->op_e4m3 ? x->kp8 : 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "index load packing"));
+  *out = x;
+  return MRC_OK;
+}
+
+// ---- timing --------------------------------------------------------------------------------
+mrc_status mrc_ctx_set_timing(mrc_ctx* ctx, int32_t on) {
+  if (!ctx) return MRC_ERR_INVALID;
+  ctx->timing = on != 0;
+  return MRC_OK;
+}
+
+int32_t mrc_ctx_kernel_stat(mrc_ctx* ctx, int32_t slot, char* name, int64_t* launches, double* total_ms,
+                            double* bytes, double* flops) {
+  if (!ctx) return -1;
+  collect_timings(ctx);
+  const int32_t count = (int32_t)ctx->stats.size();
+  if (slot < 0) return count;
+  if (slot >= count) return -1;
+  const auto& s = ctx->stats[slot];
+  if (name) {
+    std::strncpy(name, s.first.c_str(), 63);
+    name[63] = 0;
+  }
+  if (launches) *launches = s.second.launches;
+  if (total_ms) *total_ms = s.second.ms;
+  if (bytes) *bytes = s.second.bytes;
+  if (flops) *flops = s.second.flops;
+  return count;
+}
+
+void mrc_ctx_reset_stats(mrc_ctx* ctx) {
+  if (!ctx) return;
+  collect_timings(ctx);
+  ctx->stats.clear();
+}
+
+}  // extern "C"

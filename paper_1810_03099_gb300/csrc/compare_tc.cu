@@ -1,0 +1,533 @@
+// compare_tc.cu -- tensor-core comparison of unit vectors with a fused epilogue (rows a5 and a8).
+//
+// Computes scores S = A B^T (A, B row-major with a padded K; rows are unit
+// signatures for the signature comparison of Eq. 2, or unit TF-IDF vectors
+// restricted to frequent terms for the exact cosine of Eq. 1), one 128 x BN
+// output tile at a time, and either keeps the pairs with score >= threshold
+// (warp-ballot compaction into a global list with an atomic cursor) or
+// stores the tile as FP32 (the exact-cosine head, completed by tail.cu).
+//
+// Blackwell (sm_103a) structure, one persistent CTA per SM, warp-specialised:
+//   warp 0     : TMA producer (cp.async.bulk.tensor, 128-byte swizzle) into a
+//                ring of shared-memory stages guarded by mbarriers;
+//   warp 1     : allocates the 512 TMEM columns; one lane issues tcgen05.mma
+//                (cta_group::1, M = 128) into double-buffered TMEM accumulators
+//                and tcgen05.commit's the stage / accumulator barriers;
+//   warps 2..5 : epilogue, tcgen05.ld 32 columns at a time from their 32-lane
+//                TMEM quarter, threshold / store, then hand the buffer back.
+// Operand formats:
+//   SPLIT16: x = hi + lo * 2^-12 with hi, lo fp16; S = Ahi Bhi + 2^-12 (Ahi Blo + Alo Bhi)
+//            in two FP32 accumulators (error ~2^-22 relative: FP32-accurate scores);
+//   F16    : one fp16 operand pair, one accumulator;
+//   E4M3   : fp8 operands (unit vectors scaled by 256), kind::f8f6f4, score = acc / 65536.
+// Every wait is bounded (4 s): on expiry the kernel records kErrTimeout,
+// drains its own copies and MMAs (bounded), frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace mrc {
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kThreads = 192;
+constexpr int kRowBytes = 128;  // K bytes per stage per row (one 128B swizzle atom)
+constexpr uint64_t kTimeoutNs = 4000000000ull;
+constexpr float kNormLo = 0.93f;  // lower bound of |e4m3(x * 256)| / 256 for unit x (1 - 2^-4 = 0.9375)
+
+template <int FMT>
+struct Cfg;
+template <>
+struct Cfg<OP_SPLIT16> {
+  static constexpr int BN = 128, NOPS = 2, STAGES = 3, ACCS = 2;
+};
+template <>
+struct Cfg<OP_F16> {
+  static constexpr int BN = 256, NOPS = 1, STAGES = 4, ACCS = 1;
+};
+template <>
+struct Cfg<OP_E4M3> {
+  static constexpr int BN = 256, NOPS = 1, STAGES = 4, ACCS = 1;
+};
+
+struct GemmParams {
+  int64_t na, nb;
+  int32_t kblocks;
+  int32_t triangle;
+  int64_t tiles_m, tiles_n, super_rows, n_tiles;
+  float thresh, out_scale;
+  const float* a_norm;
+  const float* b_norm;
+  mrc_pair* pairs;
+  unsigned long long* count;
+  int64_t capacity;
+  float* store;
+  int64_t ld;
+  int32_t* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false on abort (another role gave up) or timeout (records it).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort, int32_t* err) {
+  if (mbar_try(b, parity)) return true;
+  const uint64_t t0 = gtime();
+  while (true) {
+#pragma unroll 1
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try(b, parity)) return true;
+    if (*abort) return false;
+    if (gtime() - t0 > kTimeoutNs) {
+      *abort = 1;
+      set_err(err, kErrTimeout);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B type code 0 (F16 for kind::f16,
+// E4M3 for kind::f8f6f4), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+template <int FMT>
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  if (FMT == OP_E4M3) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(
+            d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  }
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
+      "19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Tile t -> (row block bi in units of 128, column block bj in units of BN).
+template <int BN>
+__device__ __forceinline__ bool decode_tile(const GemmParams& p, int64_t t, int64_t& bi, int64_t& bj) {
+  if (!p.triangle) {
+    bi = t % p.tiles_m;
+    bj = t / p.tiles_m;
+    return true;
+  }
+  constexpr int H = BN / kBM;
+  const int64_t s = t / H;
+  const int64_t h = t % H;
+  const int64_t R = p.super_rows;
+  // row-major upper triangle of R x R super tiles: row I starts at I*R - I*(I-1)/2
+  const double b = 2.0 * (double)R + 1.0;
+  int64_t I = (int64_t)((b - sqrt(fmax(b * b - 8.0 * (double)s, 0.0))) * 0.5);
+  if (I < 0) I = 0;
+  if (I > R - 1) I = R - 1;
+  while (I > 0 && I * R - I * (I - 1) / 2 > s) --I;
+  while (I + 1 < R && (I + 1) * R - (I + 1) * I / 2 <= s) ++I;
+  const int64_t J = I + (s - (I * R - I * (I - 1) / 2));
+  bi = I * H + h;
+  bj = J;
+  return bi * kBM < p.na;
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_compare(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+                   const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1, GemmParams p) {
+  using C = Cfg<FMT>;
+  constexpr int BN = C::BN;
+  constexpr uint32_t A_BYTES = kBM * kRowBytes;
+  constexpr uint32_t B_BYTES = BN * kRowBytes;
+  constexpr uint32_t STAGE_BYTES = C::NOPS * (A_BYTES + B_BYTES);
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* acc_full = empty + C::STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0;
+      int32_t armed[C::STAGES];
+      for (int s = 0; s < C::STAGES; ++s) armed[s] = -1;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
+        int64_t bi, bj;
+        if (!decode_tile<BN>(p, t, bi, bj)) continue;
+        for (int kb = 0; kb < p.kblocks; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sbase = smem + stage * STAGE_BYTES;
+          mbar_expect_tx(&full[stage], STAGE_BYTES);
+          armed[stage] = (int32_t)phase;
+          const int x = kb * (FMT == OP_E4M3 ? kRowBytes : kRowBytes / 2);
+          tma_load_2d(sbase, &tA0, x, (int)(bi * kBM), &full[stage]);
+          tma_load_2d(sbase + A_BYTES, &tB0, x, (int)(bj * BN), &full[stage]);
+          if (C::NOPS == 2) {
+            tma_load_2d(sbase + A_BYTES + B_BYTES, &tA1, x, (int)(bi * kBM), &full[stage]);
+            tma_load_2d(sbase + 2 * A_BYTES + B_BYTES, &tB1, x, (int)(bj * BN), &full[stage]);
+          }
+          if (++stage == C::STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      // drain: the last copy armed on each stage lands before the CTA may exit
+      for (int s = 0; s < C::STAGES; ++s) {
+        if (armed[s] < 0) continue;
+        const uint64_t t0 = gtime();
+        while (!mbar_try(&full[s], (uint32_t)armed[s]) && gtime() - t0 < 100000000ull) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0;
+      int64_t it = 0;
+      bool ok = true;
+      const uint32_t id = idesc(BN);
+      for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
+        int64_t bi, bj;
+        if (!decode_tile<BN>(p, t, bi, bj)) continue;
+        const uint32_t ab = (uint32_t)(it & 1);
+        if (!mbar_wait(&acc_empty[ab], (uint32_t)((it >> 1) & 1) ^ 1u, abort_flag, p.err)) break;
+        tc_fence_after();
+        const uint32_t d0 = tmem + ab * 256u;
+        const uint32_t d1 = d0 + 128u;
+        for (int kb = 0; kb < p.kblocks; ++kb) {
+          if (!mbar_wait(&full[stage], phase, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
+          const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+            const uint64_t ad = sdesc(sa + kk * 32), bd = sdesc(sb + kk * 32);
+            umma<FMT>(d0, ad, bd, id, first);
+            if (C::NOPS == 2) {
+              const uint32_t sa1 = sa + A_BYTES + B_BYTES, sb1 = sa + 2 * A_BYTES + B_BYTES;
+              umma<FMT>(d1, ad, sdesc(sb1 + kk * 32), id, first);
+              umma<FMT>(d1, sdesc(sa1 + kk * 32), bd, id, 1u);
+            }
+          }
+          umma_commit(&empty[stage]);
+          if (++stage == C::STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&acc_full[ab]);
+        ++it;
+      }
+      // wait for every MMA issued so far before TMEM can be released
+      umma_commit(drain);
+      const uint64_t t0 = gtime();
+      while (!mbar_try(drain, 0) && gtime() - t0 < 100000000ull) {
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    int64_t it = 0;
+    for (int64_t t = blockIdx.x; t < p.n_tiles; t += gridDim.x) {
+      int64_t bi, bj;
+      if (!decode_tile<BN>(p, t, bi, bj)) continue;
+      const uint32_t ab = (uint32_t)(it & 1);
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(&acc_full[ab], (uint32_t)((it >> 1) & 1), abort_flag, p.err) ? 1 : 0;
+      ok = __shfl_sync(kFull, ok, 0);
+      if (!ok) break;
+      tc_fence_after();
+      const int64_t i = bi * kBM + q * 32 + lane;
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + ab * 256u;
+      // E4M3: the score is the cosine of the quantized vectors, acc * out_scale / (|q_i| |q_j|).
+      // Every non-zero quantized unit row has norm >= 1 - 2^-4 > kNormLo, so raw accumulators
+      // below thresh * |q_i| * kNormLo / out_scale cannot reach the threshold (fast path).
+      float row_norm = 1.f, fast_thresh = p.thresh;
+      if (FMT == OP_E4M3) {
+        row_norm = i < p.na ? p.a_norm[i] : 0.f;
+        if (p.thresh > 0.f)
+          fast_thresh = row_norm > 0.f ? p.thresh * row_norm * kNormLo / p.out_scale : __int_as_float(0x7f800000);
+        else
+          fast_thresh = -__int_as_float(0x7f800000);
+      }
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        float v[32];
+        tmem_ld32(trow + c * 32, v);
+        if (C::ACCS == 2) {
+          float x[32];
+          tmem_ld32(trow + 128 + c * 32, x);
+          tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 32; ++e) v[e] = fmaf(x[e], 1.0f / kSplitLoScale, v[e]);
+        } else {
+          tmem_wait_ld();
+        }
+        const int64_t j0 = bj * BN + c * 32;
+        if (p.store) {
+          if (i < p.na) {
+            float* dst = p.store + i * p.ld + j0;
+            if (j0 + 32 <= p.nb && (p.ld & 3) == 0) {
+#pragma unroll
+              for (int e = 0; e < 32; e += 4)
+                *reinterpret_cast<float4*>(dst + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+            } else {
+#pragma unroll
+              for (int e = 0; e < 32; ++e)
+                if (j0 + e < p.nb) dst[e] = v[e];
+            }
+          }
+        } else {
+          float m = v[0];
+#pragma unroll
+          for (int e = 1; e < 32; ++e) m = fmaxf(m, v[e]);
+          if (__any_sync(kFull, m >= fast_thresh)) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const int64_t j = j0 + e;
+              if (FMT == OP_E4M3) {
+                const float nn = row_norm * (j < p.nb ? p.b_norm[j] : 0.f);
+                v[e] = nn > 0.f ? v[e] * p.out_scale / nn : 0.f;
+              }
+              const bool hit = v[e] >= p.thresh && i < p.na && j < p.nb && (!p.triangle || j > i);
+              const unsigned bal = __ballot_sync(kFull, hit);
+              if (bal) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(p.count, (unsigned long long)__popc(bal));
+                base = __shfl_sync(kFull, base, 0);
+                if (hit) {
+                  const unsigned long long at = base + __popc(bal & ((1u << lane) - 1u));
+                  if (at < (unsigned long long)p.capacity) {
+                    mrc_pair pr;
+                    pr.i = (int32_t)i;
+                    pr.j = (int32_t)j;
+                    pr.score = v[e];
+                    p.pairs[at] = pr;
+                  }
+                }
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[ab]);
+      ++it;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+// 2D K-major operand map: rows x row_bytes, box = 128 bytes x box_rows, 128B swizzle, zero fill.
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t row_bytes, int box_rows, bool fp8) {
+  auto fn = encode_fn();
+  if (!fn || rows <= 0) return false;
+  const int eb = fp8 ? 1 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)(row_bytes / eb), (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / eb), (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r =
+      fn(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims,
+         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int FMT>
+cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
+  using C = Cfg<FMT>;
+  constexpr int BN = C::BN;
+  const bool fp8 = FMT == OP_E4M3;
+  CUtensorMap tA0, tA1, tB0, tB1;
+  if (!make_map(&tA0, g.a_hi, g.na, g.kbytes, kBM, fp8) || !make_map(&tB0, g.b_hi, g.nb, g.kbytes, BN, fp8))
+    return cudaErrorInvalidValue;
+  if (C::NOPS == 2) {
+    if (!make_map(&tA1, g.a_lo, g.na, g.kbytes, kBM, fp8) || !make_map(&tB1, g.b_lo, g.nb, g.kbytes, BN, fp8))
+      return cudaErrorInvalidValue;
+  } else {
+    tA1 = tA0;
+    tB1 = tB0;
+  }
+  GemmParams p{};
+  p.na = g.na;
+  p.nb = g.nb;
+  p.kblocks = g.kbytes / kRowBytes;
+  p.triangle = g.triangle;
+  p.tiles_m = (g.na + kBM - 1) / kBM;
+  p.tiles_n = (g.nb + BN - 1) / BN;
+  p.super_rows = (g.na + BN - 1) / BN;
+  p.n_tiles = g.triangle ? p.super_rows * (p.super_rows + 1) / 2 * (BN / kBM) : p.tiles_m * p.tiles_n;
+  p.thresh = g.thresh;
+  p.out_scale = g.out_scale;
+  p.a_norm = g.a_norm;
+  p.b_norm = g.b_norm;
+  if (FMT == OP_E4M3 && (!g.a_norm || !g.b_norm) && !g.store) return cudaErrorInvalidValue;
+  p.pairs = g.pairs;
+  p.count = g.count;
+  p.capacity = g.capacity;
+  p.store = g.store;
+  p.ld = g.ld;
+  p.err = g.err;
+  const size_t smem = 1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256;
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_compare<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int64_t grid = ctx->num_sms;
+  if (p.n_tiles < grid) grid = p.n_tiles;
+  if (grid <= 0) return cudaSuccess;
+  // algorithmic work: 2 K flops per evaluated pair (the triangle counts i < j only)
+  const double k_elems = (double)g.kbytes / (fp8 ? 1.0 : 2.0);
+  const double pairs = g.triangle ? (double)g.na * (double)(g.na - 1) / 2.0 : (double)g.na * (double)g.nb;
+  const double flops = 2.0 * k_elems * pairs * (C::NOPS == 2 ? 3.0 : 1.0);
+  const char* name = FMT == OP_SPLIT16 ? (g.store ? "gemm_split16_store" : "gemm_split16_thresh")
+                                        : (FMT == OP_F16 ? "gemm_f16_thresh" : "gemm_e4m3_thresh");
+  const double bytes = (double)C::NOPS * (double)(g.na + (g.triangle ? 0 : g.nb)) * g.kbytes;
+  cudaEvent_t ev = nullptr;
+  timing_begin(ctx, name, bytes, flops, &ev);
+  k_gemm_compare<FMT><<<(unsigned)grid, kThreads, smem, ctx->stream>>>(tA0, tA1, tB0, tB1, p);
+  timing_end(ctx, ev);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g) {
+  if (g.kbytes <= 0 || g.kbytes % kRowBytes != 0 || g.na <= 0 || g.nb <= 0) return cudaErrorInvalidValue;
+  if (g.na >= (1ll << 31) || g.nb >= (1ll << 31)) return cudaErrorInvalidValue;
+  switch (g.fmt) {
+    case OP_SPLIT16:
+      return run_gemm<OP_SPLIT16>(ctx, g);
+    case OP_F16:
+      return run_gemm<OP_F16>(ctx, g);
+    case OP_E4M3:
+      return run_gemm<OP_E4M3>(ctx, g);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace mrc

@@ -1,0 +1,573 @@
+// ingest.cu -- per-document passes over a token CSR (rows a1-a4 of the hot path).
+//
+// Every pass first turns a document's tokens into its bag of terms: the
+// vector space model of Section III counts each term (3-gram id) of the
+// document. The bag is built in shared memory as an open-addressing hash
+// table (term -> count), by one warp for short documents and by one CTA for
+// long ones; documents whose distinct terms could exceed half the CTA table
+// are split into several passes by a second hash of the term id.
+//
+// Then, per distinct term t with count c, one of three things happens:
+//   DF   : df[t] += 1                             (index build, Section IV ranking)
+//   SIG  : w = c * idf(t);  |d|^2 += w^2;  num[part(t)] += w * r_t  (Eq. 1 against
+//          each reference partition, Section IV), and the Simhash column sums of
+//          Section III: sum over the term's occurrences of (+1 bit set, -1 clear)
+//   DENSE: w/|d| goes to the exact-cosine operands (dense head columns or sparse
+//          tail postings; see cosine_allpairs)
+//
+// Determinism: per-term contributions are computed in FP32 (a function of the
+// term and its count only) and summed as 2^-22 fixed-point integers, so the
+// result does not depend on the order in which threads meet the terms. Every
+// contribution is >= 1 (counts >= 1, idf >= 1), so the rounding to the grid
+// costs at most 2^-23 relative.
+//
+// Simhash column sums use a bit transpose: a warp holds 32 terms' 64-bit
+// hashes, transposes them so that lane j holds bit j (and j+32) of all 32, and
+// adds popc(bits & count-bit-plane) << plane. A column is positive iff
+// 2 * (sum of counts whose hash bit is set) > document length.
+#include <cuda_bf16.h>
+#include <algorithm>
+#include <string>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace mrc {
+namespace {
+
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr int kShortMax = 512;      // documents up to this length take the warp path
+constexpr int kShortSlots = 1024;   // per-warp table (load <= 1/2)
+constexpr int kWarpsShort = 8;      // warps per CTA in the warp path
+constexpr int kLongThreads = 512;   // CTA size of the long-document path
+constexpr int kLongSlots = 16384;   // per-CTA table
+constexpr float kFix = 4194304.0f;  // 2^22
+constexpr float kInvFix = 1.0f / 4194304.0f;
+
+enum Mode { kDF = 0, kSIG = 1, kDENSE = 2 };
+
+__device__ __forceinline__ uint32_t slot_of(uint32_t t, int log2ts) { return (t * 0x9E3779B1u) >> (32 - log2ts); }
+__device__ __forceinline__ uint32_t pass_of(uint32_t t, uint32_t passes) {
+  return ((t * 0x85EBCA77u) >> 7) % passes;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014), one step from state (t XOR seed).
+__device__ __forceinline__ uint64_t feature_hash(uint32_t t, uint64_t seed) {
+  uint64_t z = ((uint64_t)t ^ seed) + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// 32x32 bit-matrix transpose across a warp: on entry lane r holds row r
+// (bit c = element (r, c)); on exit lane r holds column r of the input.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int s = 16 >> i;
+    const uint32_t m = masks[i];
+    const uint32_t y = __shfl_xor_sync(kFull, x, s);
+    x = (lane & s) ? ((x & ~m) | ((y & ~m) >> s)) : ((x & m) | ((y & m) << s));
+  }
+  return x;
+}
+
+__device__ __forceinline__ unsigned long long to_fix(float x) { return __float2ull_rn(x * kFix); }
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ bool table_insert(uint32_t* keys, uint32_t* cnts, int log2ts, uint32_t t) {
+  const uint32_t mask = (1u << log2ts) - 1u;
+  uint32_t s = slot_of(t, log2ts);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const uint32_t prev = atomicCAS(&keys[s], kEmpty, t);
+    if (prev == kEmpty || prev == t) {
+      atomicAdd(&cnts[s], 1u);
+      return true;
+    }
+    s = (s + 1u) & mask;
+  }
+  return false;
+}
+
+__device__ __forceinline__ int log2_slots(int64_t len, int max_log2) {
+  int l = 6;  // at least 64 slots
+  while (l < max_log2 && (1ll << l) < 2 * len) ++l;
+  return l;
+}
+
+struct IngestParams {
+  const int64_t* offsets;
+  const int32_t* tokens;
+  int32_t vocab;
+  const int32_t* short_list;
+  const int32_t* long_list;
+  const int32_t* list_counts;  // [0] short, [1] long
+  int32_t* long_cursor;        // dynamic grab of long documents
+  int32_t* err;
+  // DF
+  int32_t* df;
+  // SIG
+  const TermInfo* tinfo;
+  const float* rinv;
+  int32_t k;
+  int32_t bf16w;
+  uint64_t seed;
+  SigOut sig;
+  // DENSE
+  DenseOut dense;
+};
+
+// Per-group accumulators of the SIG and DENSE modes.
+struct Acc {
+  unsigned long long norm;
+  uint32_t plo, phi;
+};
+
+// Process one warp-chunk of 32 table slots [s0, s0 + 32).
+template <int MODE>
+__device__ __forceinline__ void chunk(const IngestParams& p, const uint32_t* keys, const uint32_t* cnts, int s0,
+                                      int lane, unsigned long long* num_q, Acc& a, int dense_phase, int64_t doc,
+                                      float inv_norm, int32_t* row_cnt_s, int64_t row_base) {
+  const uint32_t key = keys[s0 + lane];
+  const bool valid = key != kEmpty;
+  const unsigned any = __ballot_sync(kFull, valid);
+  if (any == 0u) return;
+  const uint32_t c = valid ? cnts[s0 + lane] : 0u;
+  if (MODE == kDF) {
+    if (valid) atomicAdd(&p.df[key], 1);
+    return;
+  }
+  if (MODE == kSIG) {
+    if (p.sig.simhash) {
+      const uint64_t h = valid ? feature_hash(key, p.seed) : 0ull;
+      const uint32_t hl = transpose32((uint32_t)h, lane);
+      const uint32_t hh = transpose32((uint32_t)(h >> 32), lane);
+      const uint32_t cmax = __reduce_max_sync(kFull, c);
+      for (uint32_t b = 0; (cmax >> b) != 0u; ++b) {
+        const uint32_t plane = __ballot_sync(kFull, (c >> b) & 1u);
+        a.plo += (uint32_t)__popc(hl & plane) << b;
+        a.phi += (uint32_t)__popc(hh & plane) << b;
+      }
+    }
+    if (valid) {
+      const int2 ti = __ldg(reinterpret_cast<const int2*>(p.tinfo) + key);
+      float w = (float)c * __int_as_float(ti.x);
+      float r = __int_as_float(ti.x);
+      if (p.bf16w) {
+        w = bf16_round(w);
+        r = bf16_round(r);
+      }
+      a.norm += to_fix(w * w);
+      if (ti.y >= 0) atomicAdd(&num_q[ti.y], to_fix(w * r));
+    }
+    return;
+  }
+  // DENSE
+  if (!valid) return;
+  const float w = (float)c * p.tinfo[key].idf;
+  if (dense_phase == 0) {
+    a.norm += to_fix(w * w);
+    return;
+  }
+  const float u = w * inv_norm;
+  const int32_t code = p.dense.colmap[key];
+  if (code >= 0) {
+    const __half hi = __float2half_rn(u);
+    const __half lo = __float2half_rn((u - __half2float(hi)) * kSplitLoScale);
+    const int64_t at = doc * (int64_t)p.dense.kd + code;
+    reinterpret_cast<__half*>(p.dense.head_hi)[at] = hi;
+    reinterpret_cast<__half*>(p.dense.head_lo)[at] = lo;
+  } else if (code == -2) {
+    const int64_t pos = p.dense.tail_start[key] + atomicAdd(&p.dense.tail_fill[key], 1);
+    p.dense.post_doc[pos] = (int32_t)doc;
+    p.dense.post_w[pos] = u;
+    const int32_t r = atomicAdd(row_cnt_s, 1);
+    p.dense.row_term[row_base + r] = (int32_t)key;
+    p.dense.row_w[row_base + r] = u;
+  }
+}
+
+// Writes the SIG outputs of one document; called by one full warp.
+__device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsigned long long norm_q,
+                             const unsigned long long* num_q, uint32_t plo, uint32_t phi, int lane) {
+  const float nrm = sqrtf((float)norm_q * kInvFix);
+  float tt = 0.f;
+  for (int q = lane; q < p.k; q += 32) {
+    const float t = (float)num_q[q] * kInvFix * p.rinv[q];
+    tt += t * t;
+  }
+  tt = warp_sum(tt);
+  const float tn = sqrtf(tt);
+  const int width = max(p.k, max(p.sig.kp, p.sig.kp8));
+  float q2 = 0.f;  // squared norm of the E4M3-quantized unit signature
+  for (int q = lane; q < width; q += 32) {
+    const float t = q < p.k ? (float)num_q[q] * kInvFix * p.rinv[q] : 0.f;
+    const float u = tn > 0.f ? t / tn : 0.f;
+    if (q < p.k) {
+      if (p.sig.sig) p.sig.sig[d * p.k + q] = nrm > 0.f ? t / nrm : 0.f;
+      if (p.sig.sig_unit) p.sig.sig_unit[d * p.k + q] = u;
+    }
+    if (q < p.sig.kp && p.sig.op_hi) {
+      const __half hi = __float2half_rn(u);
+      reinterpret_cast<__half*>(p.sig.op_hi)[d * p.sig.kp + q] = hi;
+      if (p.sig.op_lo)
+        reinterpret_cast<__half*>(p.sig.op_lo)[d * p.sig.kp + q] =
+            __float2half_rn((u - __half2float(hi)) * kSplitLoScale);
+    }
+    if (q < p.sig.kp8 && p.sig.op_e4m3) {
+      const __nv_fp8_storage_t e = __nv_cvt_float_to_fp8(u * kE4M3Scale, __NV_SATFINITE, __NV_E4M3);
+      reinterpret_cast<uint8_t*>(p.sig.op_e4m3)[d * p.sig.kp8 + q] = (uint8_t)e;
+      const float v = __half2float(__half(__nv_cvt_fp8_to_halfraw(e, __NV_E4M3))) * (1.0f / kE4M3Scale);
+      q2 += v * v;
+    }
+  }
+  if (p.sig.qnorm) {
+    q2 = warp_sum(q2);
+    if (lane == 0) p.sig.qnorm[d] = sqrtf(q2);
+  }
+  if (p.sig.simhash) {
+    const unsigned lo = __ballot_sync(kFull, 2ll * (long long)plo > len);
+    const unsigned hi = __ballot_sync(kFull, 2ll * (long long)phi > len);
+    if (lane == 0) p.sig.simhash[d] = (uint64_t)lo | ((uint64_t)hi << 32);
+  }
+}
+
+// ---------------------------------------------------------------- warp path
+template <int MODE>
+__global__ void __launch_bounds__(kWarpsShort * 32) k_ingest_short(IngestParams p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kq = MODE == kSIG ? p.k : 0;
+  const size_t per_warp = (size_t)kShortSlots * 8 + (size_t)kq * 8 + 16;
+  uint8_t* base = smem + per_warp * warp;
+  unsigned long long* num_q = reinterpret_cast<unsigned long long*>(base);
+  uint32_t* keys = reinterpret_cast<uint32_t*>(base + (size_t)kq * 8);
+  uint32_t* cnts = keys + kShortSlots;
+  int32_t* row_cnt_s = reinterpret_cast<int32_t*>(cnts + kShortSlots);
+
+  const int32_t n_short = p.list_counts[0];
+  for (int32_t it = blockIdx.x * kWarpsShort + warp; it < n_short; it += gridDim.x * kWarpsShort) {
+    const int64_t d = p.short_list[it];
+    const int64_t o0 = p.offsets[d], len = p.offsets[d + 1] - o0;
+    const int l2 = log2_slots(len, 10);
+    const int ts = 1 << l2;
+    for (int s = lane; s < ts; s += 32) {
+      keys[s] = kEmpty;
+      cnts[s] = 0u;
+    }
+    for (int q = lane; q < kq; q += 32) num_q[q] = 0ull;
+    if (lane == 0) *row_cnt_s = 0;
+    __syncwarp();
+    for (int64_t x = lane; x < len; x += 32) {
+      const int32_t t = p.tokens[o0 + x];
+      if ((uint32_t)t >= (uint32_t)p.vocab) {
+        set_err(p.err, kErrBadToken);
+        continue;
+      }
+      if (!table_insert(keys, cnts, l2, (uint32_t)t)) set_err(p.err, kErrTable);
+    }
+    __syncwarp();
+    Acc a{0ull, 0u, 0u};
+    float inv_norm = 0.f;
+    const int phases = MODE == kDENSE ? 2 : 1;
+    for (int ph = 0; ph < phases; ++ph) {
+      for (int s0 = 0; s0 < ts; s0 += 32)
+        chunk<MODE>(p, keys, cnts, s0, lane, num_q, a, ph, d, inv_norm, row_cnt_s, o0);
+      if (MODE == kDENSE && ph == 0) {
+        const unsigned long long nq = warp_sum(a.norm);
+        const float n2 = (float)nq * kInvFix;
+        inv_norm = n2 > 0.f ? 1.0f / sqrtf(n2) : 0.f;
+      }
+    }
+    __syncwarp();
+    if (MODE == kSIG) finalize_sig(p, d, len, warp_sum(a.norm), num_q, a.plo, a.phi, lane);
+    if (MODE == kDENSE && lane == 0) p.dense.row_cnt[d] = *row_cnt_s;
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------- CTA path
+template <int MODE>
+__global__ void __launch_bounds__(kLongThreads) k_ingest_long(IngestParams p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int nwarps = kLongThreads / 32;
+  const int kq = MODE == kSIG ? p.k : 0;
+  unsigned long long* num_q = reinterpret_cast<unsigned long long*>(smem);
+  unsigned long long* norm_s = num_q + kq;
+  uint32_t* P = reinterpret_cast<uint32_t*>(norm_s + 1);  // [64]
+  int32_t* misc = reinterpret_cast<int32_t*>(P + 64);     // [0] doc slot, [1] row count
+  uint32_t* keys = reinterpret_cast<uint32_t*>(misc + 4);
+  uint32_t* cnts = keys + kLongSlots;
+
+  const int32_t n_long = p.list_counts[1];
+  while (true) {
+    if (threadIdx.x == 0) misc[0] = atomicAdd(p.long_cursor, 1);
+    __syncthreads();
+    const int32_t it = misc[0];
+    if (it >= n_long) break;
+    const int64_t d = p.long_list[it];
+    const int64_t o0 = p.offsets[d], len = p.offsets[d + 1] - o0;
+    const int l2 = log2_slots(len, 14);
+    const int ts = 1 << l2;
+    const uint32_t passes = (uint32_t)((len + (kLongSlots / 2) - 1) / (kLongSlots / 2));
+    for (int q = threadIdx.x; q < kq; q += kLongThreads) num_q[q] = 0ull;
+    if (threadIdx.x < 64) P[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) {
+      *norm_s = 0ull;
+      misc[1] = 0;
+    }
+    Acc a{0ull, 0u, 0u};
+    float inv_norm = 0.f;
+    const int phases = MODE == kDENSE ? 2 : 1;
+    for (int ph = 0; ph < phases; ++ph) {
+      for (uint32_t pass = 0; pass < passes; ++pass) {
+        __syncthreads();
+        for (int s = threadIdx.x; s < ts; s += kLongThreads) {
+          keys[s] = kEmpty;
+          cnts[s] = 0u;
+        }
+        __syncthreads();
+        for (int64_t x = threadIdx.x; x < len; x += kLongThreads) {
+          const int32_t t = p.tokens[o0 + x];
+          if ((uint32_t)t >= (uint32_t)p.vocab) {
+            if (pass == 0 && ph == 0) set_err(p.err, kErrBadToken);
+            continue;
+          }
+          if (passes > 1 && pass_of((uint32_t)t, passes) != pass) continue;
+          if (!table_insert(keys, cnts, l2, (uint32_t)t)) set_err(p.err, kErrTable);
+        }
+        __syncthreads();
+        for (int s0 = warp * 32; s0 < ts; s0 += nwarps * 32)
+          chunk<MODE>(p, keys, cnts, s0, lane, num_q, a, ph, d, inv_norm, &misc[1], o0);
+      }
+      if (MODE == kDENSE && ph == 0) {
+        const unsigned long long nq = warp_sum(a.norm);
+        if (lane == 0) atomicAdd(norm_s, nq);
+        __syncthreads();
+        const float n2 = (float)(*norm_s) * kInvFix;
+        inv_norm = n2 > 0.f ? 1.0f / sqrtf(n2) : 0.f;
+      }
+    }
+    if (MODE == kSIG) {
+      const unsigned long long nq = warp_sum(a.norm);
+      if (lane == 0) atomicAdd(norm_s, nq);
+      atomicAdd(&P[lane], a.plo);
+      atomicAdd(&P[lane + 32], a.phi);
+    }
+    __syncthreads();
+    if (MODE == kSIG && warp == 0) finalize_sig(p, d, len, *norm_s, num_q, P[lane], P[lane + 32], lane);
+    if (MODE == kDENSE && threadIdx.x == 0) p.dense.row_cnt[d] = misc[1];
+    __syncthreads();
+  }
+}
+
+// Splits documents into the warp path and the CTA path; validates offsets.
+__global__ void k_classify(const int64_t* off, int64_t n, int32_t* short_list, int32_t* long_list, int32_t* counts,
+                           int32_t* max_len, int32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && off[0] != 0) set_err(err, kErrBadOffsets);
+  if (i >= n) return;
+  const int64_t len = off[i + 1] - off[i];
+  if (len < 0) {
+    set_err(err, kErrBadOffsets);
+    return;
+  }
+  if (len > MRC_MAX_DOC_TOKENS) {
+    set_err(err, kErrTooLong);
+    return;
+  }
+  atomicMax(max_len, (int32_t)len);
+  if (len <= kShortMax)
+    short_list[atomicAdd(&counts[0], 1)] = (int32_t)i;
+  else
+    long_list[atomicAdd(&counts[1], 1)] = (int32_t)i;
+}
+
+__global__ void k_idf(int64_t n_docs, const int32_t* df, int32_t vocab, int32_t weighting, float* idf,
+                      TermInfo* tinfo) {
+  const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= vocab) return;
+  // idf(t) = ln((1 + N) / (1 + df(t))) + 1, evaluated in double
+  const double v = log((1.0 + (double)n_docs) / (1.0 + (double)df[t])) + 1.0;
+  idf[t] = (float)v;
+  if (tinfo) {
+    tinfo[t].idf = weighting == MRC_WEIGHT_TFIDF ? (float)v : 1.0f;
+    tinfo[t].code = -1;
+  }
+}
+
+// Unit-length packing of raw signatures (query signatures handed to mrc_match).
+__global__ void k_pack(const float* sig, int64_t n, int32_t k, int32_t normalize, void* hi, void* lo, void* e4m3,
+                       float* qnorm, float* unit, int32_t kp, int32_t kp8) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const int64_t d = warp;
+  float ss = 0.f;
+  for (int q = lane; q < k; q += 32) {
+    const float v = sig[d * k + q];
+    ss += v * v;
+  }
+  ss = warp_sum(ss);
+  const float nrm = sqrtf(ss);
+  const int width = max(k, max(kp, kp8));
+  float q2 = 0.f;
+  for (int q = lane; q < width; q += 32) {
+    const float u = q < k ? (normalize ? (nrm > 0.f ? sig[d * k + q] / nrm : 0.f) : sig[d * k + q]) : 0.f;
+    if (unit && q < k) unit[d * k + q] = u;
+    if (hi && q < kp) {
+      const __half h = __float2half_rn(u);
+      reinterpret_cast<__half*>(hi)[d * kp + q] = h;
+      if (lo) reinterpret_cast<__half*>(lo)[d * kp + q] = __float2half_rn((u - __half2float(h)) * kSplitLoScale);
+    }
+    if (e4m3 && q < kp8) {
+      const __nv_fp8_storage_t e = __nv_cvt_float_to_fp8(u * kE4M3Scale, __NV_SATFINITE, __NV_E4M3);
+      reinterpret_cast<uint8_t*>(e4m3)[d * kp8 + q] = (uint8_t)e;
+      const float v = __half2float(__half(__nv_cvt_fp8_to_halfraw(e, __NV_E4M3))) * (1.0f / kE4M3Scale);
+      q2 += v * v;
+    }
+  }
+  if (qnorm) {
+    q2 = warp_sum(q2);
+    if (lane == 0) qnorm[d] = sqrtf(q2);
+  }
+}
+
+size_t short_smem(int kq) { return (size_t)kWarpsShort * ((size_t)kShortSlots * 8 + (size_t)kq * 8 + 16); }
+size_t long_smem(int kq) { return (size_t)kq * 8 + 8 + 64 * 4 + 16 + (size_t)kLongSlots * 8; }
+
+struct Lists {
+  int32_t* short_list;
+  int32_t* long_list;
+  int32_t* counts;  // [0] short [1] long [2] max_len [3] long cursor
+  int32_t* err;     // the call's device error word
+  int32_t h[5];
+};
+
+// Classifies documents and reads back the list sizes (one small sync).
+cudaError_t classify(mrc_ctx* ctx, const DocsDev& d, Lists* L) {
+  mrc_status st = MRC_OK;
+  L->short_list = (int32_t*)ws_get(ctx, "ingest.short", sizeof(int32_t) * (size_t)std::max<int64_t>(d.n_docs, 1), &st);
+  L->long_list = (int32_t*)ws_get(ctx, "ingest.long", sizeof(int32_t) * (size_t)std::max<int64_t>(d.n_docs, 1), &st);
+  L->counts = (int32_t*)ws_get(ctx, "ingest.counts", sizeof(int32_t) * 8, &st);
+  L->err = d.err;
+  if (st != MRC_OK) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMemsetAsync(L->counts, 0, sizeof(int32_t) * 8, ctx->stream);
+  if (e != cudaSuccess) return e;
+  if (d.n_docs > 0) {
+    const int64_t blocks = (d.n_docs + 255) / 256;
+    k_classify<<<(unsigned)blocks, 256, 0, ctx->stream>>>(d.offsets, d.n_docs, L->short_list, L->long_list,
+                                                          L->counts, L->counts + 2, L->err);
+  }
+  e = cudaMemcpyAsync(L->h, L->counts, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(L->h + 4, L->err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const char* name, double bytes_per_token,
+                       double bytes_per_doc) {
+  Lists L;
+  cudaError_t e = classify(ctx, d, &L);
+  if (e != cudaSuccess) return e;
+  if (L.h[4] != 0) return cudaErrorInvalidValue;  // reported by the caller as MRC_ERR_INVALID
+  p.short_list = L.short_list;
+  p.long_list = L.long_list;
+  p.list_counts = L.counts;
+  p.long_cursor = L.counts + 3;
+  p.err = L.err;
+  const int kq = MODE == kSIG ? p.k : 0;
+  const size_t s_smem = short_smem(kq), l_smem = long_smem(kq);
+  e = cudaFuncSetAttribute(k_ingest_short<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_ingest_long<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l_smem);
+  if (e != cudaSuccess) return e;
+  const double tokens = (double)d.n_tokens;
+  cudaEvent_t ev = nullptr;
+  if (L.h[0] > 0) {
+    const int per_sm = 2;
+    int grid = ctx->num_sms * per_sm;
+    const int need = (L.h[0] + kWarpsShort - 1) / kWarpsShort;
+    if (need < grid) grid = need;
+    std::string nm = std::string(name) + ".short";
+    timing_begin(ctx, nm.c_str(), tokens * bytes_per_token + bytes_per_doc * d.n_docs, 0.0, &ev);
+    k_ingest_short<MODE><<<grid, kWarpsShort * 32, s_smem, ctx->stream>>>(p);
+    timing_end(ctx, ev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (L.h[1] > 0) {
+    int grid = ctx->num_sms;
+    if (L.h[1] < grid) grid = L.h[1];
+    std::string nm = std::string(name) + ".long";
+    timing_begin(ctx, nm.c_str(), 0.0, 0.0, &ev);
+    k_ingest_long<MODE><<<grid, kLongThreads, l_smem, ctx->stream>>>(p);
+    timing_end(ctx, ev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+IngestParams base_params(const DocsDev& d) {
+  IngestParams p{};
+  p.offsets = d.offsets;
+  p.tokens = d.tokens;
+  return p;
+}
+
+}  // namespace
+
+cudaError_t launch_df(mrc_ctx* ctx, const DocsDev& d, int32_t* df, int32_t vocab) {
+  IngestParams p = base_params(d);
+  p.vocab = vocab;
+  p.df = df;
+  return run_ingest<kDF>(ctx, d, p, "ingest_df", 4.0, 8.0);
+}
+
+cudaError_t launch_idf(mrc_ctx* ctx, int64_t n_docs, const int32_t* df, int32_t vocab, int32_t weighting, float* idf,
+                       TermInfo* tinfo) {
+  k_idf<<<(vocab + 255) / 256, 256, 0, ctx->stream>>>(n_docs, df, vocab, weighting, idf, tinfo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_signature(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo,
+                                     const float* rinv, int32_t k, int32_t bf16_weights, uint64_t seed,
+                                     const SigOut& out) {
+  IngestParams p = base_params(d);
+  p.vocab = vocab;
+  p.tinfo = tinfo;
+  p.rinv = rinv;
+  p.k = k;
+  p.bf16w = bf16_weights;
+  p.seed = seed;
+  p.sig = out;
+  return run_ingest<kSIG>(ctx, d, p, "signature", 4.0, 8.0 + 4.0 * k + 8.0);
+}
+
+cudaError_t launch_pack(mrc_ctx* ctx, const float* sig, int64_t n, int32_t k, int32_t normalize, void* hi, void* lo,
+                        void* e4m3, float* qnorm, float* unit, int32_t kp, int32_t kp8) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t threads = n * 32;
+  k_pack<<<(unsigned)((threads + 255) / 256), 256, 0, ctx->stream>>>(sig, n, k, normalize, hi, lo, e4m3, qnorm,
+                                                                      unit, kp, kp8);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_densify(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo,
+                           const DenseOut& out) {
+  IngestParams p = base_params(d);
+  p.vocab = vocab;
+  p.tinfo = tinfo;
+  p.dense = out;
+  return run_ingest<kDENSE>(ctx, d, p, "densify", 4.0, 8.0);
+}
+
+}  // namespace mrc

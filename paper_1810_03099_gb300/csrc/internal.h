@@ -1,0 +1,183 @@
+// internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "mrc.h"
+
+namespace mrc {
+
+// Per-document term information looked up while streaming a document:
+// x = idf(t) as float (1.0 under count weighting), y = partition of t or -1.
+// For the exact-cosine densify pass y is the column code instead (see ingest.cu).
+struct TermInfo {
+  float idf;
+  int32_t code;
+};
+
+// Operand formats of the tensor-core compare.
+enum OperandFormat : int32_t { OP_SPLIT16 = 0, OP_F16 = 1, OP_E4M3 = 2 };
+
+// Scale of the low half of the fp16 hi/lo split: lo = fp16((x - hi) * 2^12).
+constexpr float kSplitLoScale = 4096.0f;
+// Global scale of unit signatures stored as E4M3 (max element 1.0 -> 256 <= 448).
+constexpr float kE4M3Scale = 256.0f;
+
+struct KernelStat {
+  int64_t launches = 0;
+  double ms = 0.0;
+  double bytes = 0.0;
+  double flops = 0.0;
+};
+
+struct PendingTiming {
+  std::string name;
+  cudaEvent_t start, stop;
+  double bytes, flops;
+};
+
+struct Buffer {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace mrc
+
+struct mrc_ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  std::string last_error;
+  std::map<std::string, mrc::Buffer> ws;  // grow-only scratch, by purpose
+  bool timing = false;
+  std::vector<mrc::PendingTiming> pending;
+  std::vector<std::pair<std::string, mrc::KernelStat>> stats;
+  std::vector<cudaEvent_t> free_events;
+  void* pinned = nullptr;  // small pinned host scratch (counters)
+};
+
+struct mrc_index {
+  int device = 0;
+  mrc_params params{};
+  int64_t n_docs = 0;
+  int32_t vocab = 0;
+  int32_t k = 0;
+  int32_t kp = 0;       // padded row length (elements) of fp16 compare operands
+  int32_t kp8 = 0;      // padded row length (bytes) of E4M3 compare operands
+  int64_t L_used = 0;
+  // host copies
+  std::vector<int32_t> h_df, h_part;
+  std::vector<float> h_idf;
+  std::vector<double> h_rnorm;
+  // device arrays
+  int32_t* df = nullptr;          // [vocab]
+  float* idf = nullptr;           // [vocab]
+  mrc::TermInfo* tinfo = nullptr; // [vocab]
+  float* rinv = nullptr;          // [k] 1 / |R_p| (0 for empty partitions)
+  float* sig = nullptr;           // [n * k] raw signatures
+  float* sig_unit = nullptr;      // [n * k] unit signatures (FP32 rescoring)
+  uint64_t* simhash = nullptr;    // [n]
+  void* op_hi = nullptr;          // [n * kp] fp16 (hi or the single fp16 operand)
+  void* op_lo = nullptr;          // [n * kp] fp16 (lo of the split)
+  void* op_e4m3 = nullptr;        // [n * kp8] e4m3
+  float* qnorm = nullptr;         // [n] norms of the e4m3 rows
+};
+
+namespace mrc {
+
+// ---- error / workspace helpers (api.cu) ----
+mrc_status fail(mrc_ctx* ctx, mrc_status st, const std::string& msg);
+mrc_status cuda_fail(mrc_ctx* ctx, cudaError_t e, const char* what);
+void* ws_get(mrc_ctx* ctx, const char* slot, size_t bytes, mrc_status* st);
+
+// ---- timing helpers (api.cu) ----
+void timing_begin(mrc_ctx* ctx, const char* name, double bytes, double flops, cudaEvent_t* ev_out);
+void timing_end(mrc_ctx* ctx, cudaEvent_t start);
+
+// ---- launchers ----
+struct DocsDev {
+  int64_t n_docs;
+  const int64_t* offsets;  // device
+  const int32_t* tokens;   // device
+  int64_t n_tokens;
+  int32_t* err;            // the call's device error word (kErr* bits)
+};
+
+// ingest.cu
+cudaError_t launch_df(mrc_ctx* ctx, const DocsDev& d, int32_t* df, int32_t vocab);
+cudaError_t launch_idf(mrc_ctx* ctx, int64_t n_docs, const int32_t* df, int32_t vocab, int32_t weighting,
+                       float* idf, TermInfo* tinfo);
+struct SigOut {
+  float* sig;          // [n*k] raw (may be null)
+  float* sig_unit;     // [n*k] unit (may be null)
+  uint64_t* simhash;   // [n] (may be null)
+  void* op_hi;         // [n*kp] fp16 (may be null)
+  void* op_lo;         // [n*kp] fp16 (may be null)
+  void* op_e4m3;       // [n*kp8] (may be null)
+  float* qnorm;        // [n] norm of the quantized E4M3 unit signature (may be null)
+  int32_t kp, kp8;
+};
+cudaError_t launch_signature(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo, const float* rinv,
+                             int32_t k, int32_t bf16_weights, uint64_t seed, const SigOut& out);
+// Packs rows of `sig` (normalised to unit length first when `normalize`) into compare operands.
+cudaError_t launch_pack(mrc_ctx* ctx, const float* sig, int64_t n, int32_t k, int32_t normalize, void* hi, void* lo,
+                        void* e4m3, float* qnorm, float* unit, int32_t kp, int32_t kp8);
+struct DenseOut {
+  const int32_t* colmap;  // [vocab] head column, -2 tail term, -1 skipped
+  int32_t kd;             // padded head width (elements)
+  void* head_hi;          // [n*kd] fp16
+  void* head_lo;          // [n*kd] fp16
+  const int64_t* tail_start;  // [vocab] start of the term's postings
+  int32_t* tail_fill;         // [vocab] fill cursors (zeroed)
+  int32_t* post_doc;          // [n_post]
+  float* post_w;              // [n_post]
+  int32_t* row_cnt;           // [n] tail terms of each doc
+  int32_t* row_term;          // [n_tokens] at the doc's token offsets
+  float* row_w;               // [n_tokens]
+};
+cudaError_t launch_densify(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo, const DenseOut& out);
+
+// compare_tc.cu
+struct GemmArgs {
+  int32_t fmt;          // OperandFormat
+  const void* a_hi;     // [na * kpad] (rows of A)
+  const void* a_lo;
+  const void* b_hi;     // [nb * kpad] (rows of B); == A for the triangle
+  const void* b_lo;
+  int64_t na, nb;
+  int32_t kbytes;       // bytes per row of one operand (padded)
+  int32_t triangle;     // 1: A == B, only pairs i < j
+  float thresh;         // epilogue threshold (score >= thresh)
+  float out_scale;      // score = acc * out_scale (E4M3), 1 otherwise
+  const float* a_norm;  // E4M3: norms of the quantized rows of A and B; the score is the
+  const float* b_norm;  //   cosine of the quantized vectors, acc * out_scale / (|qa| |qb|)
+  // epilogue: pairs (thresh) or dense store
+  mrc_pair* pairs;
+  unsigned long long* count;
+  int64_t capacity;
+  float* store;         // non-null: write the score tile to store[i * ld + j] instead of thresholding
+  int64_t ld;
+  int32_t* err;         // device error word
+};
+cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g);
+
+// simhash_match.cu
+cudaError_t launch_simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
+                                 int32_t hmax, mrc_pair* pairs, unsigned long long* count, int64_t capacity);
+
+// tail.cu
+cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const float* H, int64_t ldh, const int64_t* row_off,
+                               const int32_t* row_cnt, const int32_t* row_term, const float* row_w,
+                               const int64_t* tail_start, const int32_t* post_cnt, const int32_t* post_doc,
+                               const float* post_w, float tau, mrc_pair* pairs, unsigned long long* count,
+                               int64_t capacity, double work_pairs);
+cudaError_t launch_rescore(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand, int64_t cand_cap,
+                           const float* qunit, const float* xunit, int32_t k, float tau, mrc_pair* pairs,
+                           unsigned long long* count, int64_t capacity);
+
+}  // namespace mrc

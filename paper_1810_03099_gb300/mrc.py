@@ -1,0 +1,349 @@
+"""Python binding of the C ABI in include/mrc.h (argument marshalling only).
+
+Every function here converts arguments (torch tensors on the GPU, or numpy
+arrays / pinned host tensors) to plain pointers and sizes and calls the
+library of the same name; all computation happens in the CUDA kernels behind
+it. There is no fallback: if libmrc.so is missing or the GPU is absent the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmrc.so")
+
+MRC_OK, MRC_ERR_INVALID, MRC_ERR_OOM, MRC_ERR_CAPACITY = 0, 1, 2, 3
+MRC_ERR_CUDA, MRC_ERR_TIMEOUT, MRC_ERR_UNSUPPORTED = 4, 5, 6
+SELECT_ALL, SELECT_REGION, SELECT_DF1 = 0, 1, 2
+WEIGHT_COUNT, WEIGHT_TFIDF = 0, 1
+PREC_FP32, PREC_BF16_FP8, PREC_FP16 = 0, 1, 2
+MAX_K = 256
+
+
+class MrcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"mrc status {status}: {message}")
+        self.status = status
+        self.message = message
+
+
+class Params(C.Structure):
+    _fields_ = [("k", C.c_int32), ("L", C.c_int32), ("select_mode", C.c_int32), ("region_start", C.c_int32),
+                ("weighting", C.c_int32), ("precision", C.c_int32), ("tau", C.c_float), ("margin", C.c_float),
+                ("hamming_max", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64)]
+
+
+class Pair(C.Structure):
+    _fields_ = [("i", C.c_int32), ("j", C.c_int32), ("score", C.c_float)]
+
+
+class Docs(C.Structure):
+    _fields_ = [("n_docs", C.c_int64), ("offsets", C.c_void_p), ("tokens", C.c_void_p)]
+
+
+class IndexInfo(C.Structure):
+    _fields_ = [("n_docs", C.c_int64), ("vocab", C.c_int32), ("k", C.c_int32), ("L_used", C.c_int64),
+                ("precision", C.c_int32), ("weighting", C.c_int32), ("kp", C.c_int32), ("reserved", C.c_int32)]
+
+
+PAIR_DTYPE = np.dtype([("i", np.int32), ("j", np.int32), ("score", np.float32)])
+
+# name -> (restype, argtypes); the exported symbols of include/mrc.h
+_SIGNATURES = {
+    "mrc_params_default": (None, [C.POINTER(Params)]),
+    "mrc_ctx_create": (C.c_int32, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "mrc_ctx_destroy": (None, [C.c_void_p]),
+    "mrc_last_error": (C.c_char_p, [C.c_void_p]),
+    "mrc_build_index": (C.c_int32, [C.c_void_p, C.POINTER(Docs), C.c_int32, C.POINTER(Params), C.POINTER(C.c_void_p)]),
+    "mrc_signature": (C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(Docs), C.c_void_p, C.c_void_p]),
+    "mrc_match": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_void_p, C.c_int64,
+                              C.POINTER(C.c_int64)]),
+    "cosine_allpairs": (C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(Docs), C.c_float, C.c_void_p, C.c_int64,
+                                    C.POINTER(C.c_int64)]),
+    "simhash_match": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
+                                  C.c_int64, C.POINTER(C.c_int64)]),
+    "mrc_index_get_info": (C.c_int32, [C.c_void_p, C.POINTER(IndexInfo)]),
+    "mrc_index_export": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p]),
+    "mrc_index_save": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_char_p]),
+    "mrc_index_load": (C.c_int32, [C.c_void_p, C.c_char_p, C.POINTER(C.c_void_p)]),
+    "mrc_index_free": (None, [C.c_void_p]),
+    "mrc_ctx_set_timing": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "mrc_ctx_kernel_stat": (C.c_int32, [C.c_void_p, C.c_int32, C.c_char_p, C.POINTER(C.c_int64),
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "mrc_ctx_reset_stats": (None, [C.c_void_p]),
+}
+
+_LIB = None
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load libmrc.so (built by ``__graft_entry__.build()``); raises if it is absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def exported_symbols():
+    return sorted(_SIGNATURES)
+
+
+# ---------------------------------------------------------------------------- marshalling
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _check_dtype(x, np_dtype, torch_name):
+    if x is None:
+        return
+    if _is_torch(x):
+        if str(x.dtype) != f"torch.{torch_name}":
+            raise TypeError(f"expected torch.{torch_name}, got {x.dtype}")
+    elif x.dtype != np_dtype:
+        raise TypeError(f"expected {np_dtype}, got {x.dtype}")
+
+
+def _docs(offsets, tokens):
+    _check_dtype(offsets, np.int64, "int64")
+    _check_dtype(tokens, np.int32, "int32")
+    n = int(offsets.shape[0]) - 1
+    return Docs(n, _ptr(offsets), _ptr(tokens))
+
+
+def _on_device(x):
+    return _is_torch(x) and x.is_cuda
+
+
+class Context:
+    """A library context bound to the current device and a CUDA stream (torch's current stream by default)."""
+
+    def __init__(self, stream=None):
+        self.lib = load_library()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = C.c_void_p()
+        st = self.lib.mrc_ctx_create(C.c_void_p(stream), C.byref(h))
+        if st != MRC_OK:
+            raise MrcError(st, "mrc_ctx_create failed (needs a Blackwell sm_103a device)")
+        self.handle = h
+        self.stream = stream
+
+    def check(self, st):
+        if st != MRC_OK:
+            raise MrcError(st, self.last_error())
+
+    def last_error(self) -> str:
+        return self.lib.mrc_last_error(self.handle).decode()
+
+    def set_timing(self, on: bool = True):
+        self.check(self.lib.mrc_ctx_set_timing(self.handle, 1 if on else 0))
+
+    def kernel_stats(self):
+        out = []
+        n = self.lib.mrc_ctx_kernel_stat(self.handle, -1, None, None, None, None, None)
+        for s in range(max(n, 0)):
+            name = C.create_string_buffer(64)
+            la, ms, by, fl = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
+            self.lib.mrc_ctx_kernel_stat(self.handle, s, name, C.byref(la), C.byref(ms), C.byref(by), C.byref(fl))
+            out.append({"name": name.value.decode(), "launches": la.value, "ms": ms.value, "bytes": by.value,
+                        "flops": fl.value})
+        return out
+
+    def reset_stats(self):
+        self.lib.mrc_ctx_reset_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.mrc_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+class Index:
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.handle = handle
+        info = IndexInfo()
+        ctx.check(ctx.lib.mrc_index_get_info(handle, C.byref(info)))
+        self.n_docs, self.vocab, self.k = info.n_docs, info.vocab, info.k
+        self.L_used, self.precision, self.weighting, self.kp = info.L_used, info.precision, info.weighting, info.kp
+
+    def free(self):
+        if self.handle:
+            self.ctx.lib.mrc_index_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def params_default(**kw) -> Params:
+    p = Params()
+    load_library().mrc_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def mrc_build_index(ctx: Context, offsets, tokens, vocab: int, params: Params | None = None) -> Index:
+    params = params or params_default()
+    d = _docs(offsets, tokens)
+    h = C.c_void_p()
+    ctx.check(ctx.lib.mrc_build_index(ctx.handle, C.byref(d), int(vocab), C.byref(params), C.byref(h)))
+    return Index(ctx, h)
+
+
+def mrc_signature(ctx: Context, index: Index, offsets, tokens, sig=None, simhash=None, want_simhash=True):
+    """Signatures [n, k] float32 (and Simhash [n] uint64) of new documents; outputs on the inputs' side."""
+    n = int(offsets.shape[0]) - 1
+    if sig is None:
+        if _on_device(tokens):
+            import torch
+            sig = torch.empty((n, index.k), dtype=torch.float32, device=tokens.device)
+            simhash = torch.empty(n, dtype=torch.int64, device=tokens.device) if want_simhash else None
+        else:
+            sig = np.empty((n, index.k), np.float32)
+            simhash = np.empty(n, np.uint64) if want_simhash else None
+    d = _docs(offsets, tokens)
+    ctx.check(ctx.lib.mrc_signature(ctx.handle, index.handle, C.byref(d), _ptr(sig), _ptr(simhash)))
+    return sig, simhash
+
+
+def _pairs_buf(capacity, device):
+    if device is not None:
+        import torch
+        return torch.empty((max(capacity, 1), 3), dtype=torch.int32, device=device)
+    return np.empty(max(capacity, 1), PAIR_DTYPE)
+
+
+def _pair_call(ctx, fn, capacity, device, grow):
+    while True:
+        buf = _pairs_buf(capacity, device)
+        total = C.c_int64()
+        st = fn(buf, capacity, total)
+        if st == MRC_ERR_CAPACITY and grow:
+            capacity = int(total.value)
+            continue
+        if st not in (MRC_OK, MRC_ERR_CAPACITY):
+            ctx.check(st)
+        m = min(int(total.value), capacity)
+        return buf[:m], int(total.value)
+
+
+def pairs_to_numpy(buf):
+    """Pairs from a device [m, 3] int32 tensor or a host structured array -> structured numpy array."""
+    if isinstance(buf, np.ndarray):
+        return buf
+    arr = buf.cpu().numpy()
+    out = np.empty(arr.shape[0], PAIR_DTYPE)
+    out["i"] = arr[:, 0]
+    out["j"] = arr[:, 1]
+    out["score"] = arr[:, 2].view(np.float32)
+    return out
+
+
+def mrc_match(ctx: Context, index: Index, query_sig=None, tau: float = 0.9, capacity: int = 1 << 20,
+              device="cuda", grow=True):
+    """Signature pairs with cosine >= tau: all index pairs (query_sig None) or queries x index."""
+    nq = 0 if query_sig is None else int(query_sig.shape[0])
+    if query_sig is not None:
+        _check_dtype(query_sig, np.float32, "float32")
+
+    def fn(buf, cap, total):
+        return ctx.lib.mrc_match(ctx.handle, index.handle, _ptr(query_sig), nq, float(tau), _ptr(buf), cap,
+                                 C.byref(total))
+    return _pair_call(ctx, fn, capacity, device, grow)
+
+
+def cosine_allpairs(ctx: Context, index: Index, offsets, tokens, tau: float = 0.9, capacity: int = 1 << 20,
+                    device="cuda", grow=True):
+    """Exact TF-IDF cosine pairs >= tau over all pairs of the given documents."""
+    d = _docs(offsets, tokens)
+
+    def fn(buf, cap, total):
+        return ctx.lib.cosine_allpairs(ctx.handle, index.handle, C.byref(d), float(tau), _ptr(buf), cap,
+                                       C.byref(total))
+    return _pair_call(ctx, fn, capacity, device, grow)
+
+
+def simhash_match(ctx: Context, a, b=None, hamming_max: int = 3, capacity: int = 1 << 20, device="cuda", grow=True):
+    """Fingerprint pairs with Hamming distance <= hamming_max (all pairs of a, or a x b)."""
+    na = int(a.shape[0])
+    nb = 0 if b is None else int(b.shape[0])
+
+    def fn(buf, cap, total):
+        return ctx.lib.simhash_match(ctx.handle, _ptr(a), na, _ptr(b), nb, int(hamming_max), _ptr(buf), cap,
+                                     C.byref(total))
+    return _pair_call(ctx, fn, capacity, device, grow)
+
+
+def mrc_index_export(ctx: Context, index: Index):
+    """Host copies of the index: raw signatures, Simhash, df, idf, partitions, reference norms."""
+    n, k, V = index.n_docs, index.k, index.vocab
+    sig = np.empty((n, k), np.float32)
+    sh = np.empty(n, np.uint64)
+    df = np.empty(V, np.int32)
+    idf = np.empty(V, np.float32)
+    part = np.empty(V, np.int32)
+    rnorm = np.empty(k, np.float64)
+    ctx.check(ctx.lib.mrc_index_export(ctx.handle, index.handle, _ptr(sig), _ptr(sh), _ptr(df), _ptr(idf),
+                                       _ptr(part), _ptr(rnorm)))
+    return {"sig": sig, "simhash": sh, "df": df, "idf": idf, "part": part, "rnorm": rnorm}
+
+
+def index_simhash(ctx: Context, index: Index, out):
+    """The index's Simhash fingerprints copied into ``out`` (device or host, 8 bytes per document)."""
+    ctx.check(ctx.lib.mrc_index_export(ctx.handle, index.handle, None, _ptr(out), None, None, None, None))
+    return out
+
+
+def mrc_index_save(ctx: Context, index: Index, path: str):
+    ctx.check(ctx.lib.mrc_index_save(ctx.handle, index.handle, path.encode()))
+
+
+def mrc_index_load(ctx: Context, path: str) -> Index:
+    h = C.c_void_p()
+    ctx.check(ctx.lib.mrc_index_load(ctx.handle, path.encode(), C.byref(h)))
+    return Index(ctx, h)

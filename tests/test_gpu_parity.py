@@ -1,0 +1,263 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: raw signature entries within 2e-6 (FP32 contributions, exact
+fixed-point sums); every cosine (signature cosine of Eq. 2, exact cosine of
+Eq. 1) within 1e-5 absolute in the FP32 form; Simhash fingerprints and
+Hamming pair sets bit-exact; pair sets equal to the oracle's except pairs
+whose oracle score lies within 1e-5 of the threshold. Reduced-precision forms:
+recall and precision >= 0.99 against the FP64 pair set.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle.oracle import MODE_ALL, MODE_DF1, MODE_REGION, Oracle, Params, build_index, signature
+from paper_1810_03099_gb300 import synth
+from tests.gpu_common import compare_pairs, concat, csr, cuda_or_skip, edge_docs, mixed_corpus, pair_dict
+
+pytestmark = pytest.mark.gpu
+
+SIG_TOL = 2e-6
+COS_TOL = 1e-5
+BAND = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return cuda_or_skip()
+
+
+@pytest.fixture(scope="module")
+def M(torch):
+    from paper_1810_03099_gb300 import mrc
+    return mrc
+
+
+@pytest.fixture(scope="module")
+def ctx(M):
+    c = M.Context()
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def orc():
+    return Oracle()
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def mrc_params(M, p: Params, precision=0):
+    return M.params_default(k=p.k, L=p.L, select_mode=p.mode, region_start=p.region_start, weighting=p.weighting,
+                            precision=precision, tau=p.tau, hamming_max=p.hamming_max, seed=p.seed)
+
+
+PARAM_CASES = [
+    Params(k=8),
+    Params(k=16, mode=MODE_ALL, weighting=0),
+    Params(k=64, mode=MODE_DF1, L=200),
+    Params(k=200, mode=MODE_ALL),
+    Params(k=33, mode=MODE_REGION, L=500, region_start=40, seed=7),
+]
+
+
+@pytest.fixture(scope="module")
+def corpus():
+    return mixed_corpus()
+
+
+@pytest.mark.parametrize("case", range(len(PARAM_CASES)))
+def test_index_build_matches_oracle(torch, M, ctx, orc, corpus, case):
+    p = PARAM_CASES[case]
+    offs, toks = corpus
+    V = 5000
+    ref = build_index(offs, toks, V, p, orc)
+    idx = M.mrc_build_index(ctx, dev(torch, offs), dev(torch, toks), V, mrc_params(M, p))
+    ex = M.mrc_index_export(ctx, idx)
+    assert np.array_equal(ex["df"].astype(np.int64), ref.df)
+    assert np.max(np.abs(ex["idf"] - ref.idf_values) / ref.idf_values) < 1e-6
+    assert np.array_equal(ex["part"], ref.part) and idx.L_used == ref.L_used
+    assert np.max(np.abs(ex["rnorm"] - ref.rnorm) / np.maximum(ref.rnorm, 1e-300)) < 1e-6
+    err = np.abs(ex["sig"].astype(np.float64) - ref.S)
+    assert err.max() <= SIG_TOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
+    assert np.array_equal(ex["simhash"], ref.F)
+    idx.free()
+
+
+def test_signature_of_new_documents(torch, M, ctx, orc, corpus):
+    offs, toks = corpus
+    V = 5000
+    p = Params(k=24, mode=MODE_ALL)
+    ref = build_index(offs, toks, V, p, orc)
+    idx = M.mrc_build_index(ctx, dev(torch, offs), dev(torch, toks), V, mrc_params(M, p))
+    # queries: a different seed, plus terms the index never saw (df = 0)
+    q = synth.make_corpus(synth.SPECS["tiny"].with_(n_docs=300, vocab=V, seed=99))
+    qo, qt = concat((q.offsets, q.tokens), csr(edge_docs(V, seed=5)))
+    S_ref, F_ref, _ = signature(ref, qo, qt, orc)
+    sig, sh = M.mrc_signature(ctx, idx, dev(torch, qo), dev(torch, qt))
+    assert np.abs(sig.cpu().numpy().astype(np.float64) - S_ref).max() <= SIG_TOL
+    assert np.array_equal(sh.cpu().numpy().view(np.uint64), F_ref)
+    # host buffers give the same bits
+    sig_h, sh_h = M.mrc_signature(ctx, idx, qo, qt)
+    assert np.array_equal(sig_h, sig.cpu().numpy()) and np.array_equal(sh_h, sh.cpu().numpy().view(np.uint64))
+    idx.free()
+
+
+@pytest.mark.parametrize("k,tau", [(8, 0.9), (64, 0.9), (64, 0.6), (130, 0.8)])
+def test_match_allpairs_fp32(torch, M, ctx, orc, k, tau):
+    c = synth.make_corpus("tiny")
+    V = c.vocab
+    p = Params(k=k, mode=MODE_ALL if k > 64 else MODE_REGION)
+    ref = build_index(c.offsets, c.tokens, V, p, orc)
+    idx = M.mrc_build_index(ctx, dev(torch, c.offsets), dev(torch, c.tokens), V, mrc_params(M, p))
+    buf, total = M.mrc_match(ctx, idx, None, tau)
+    got = M.pairs_to_numpy(buf)
+    assert total == got.shape[0]
+    assert np.all(got["i"] < got["j"])
+    tot, pi, pj, ps = orc.sig_pairs(ref.S, tau)
+    rep = compare_pairs(pair_dict(got["i"], got["j"], got["score"]), pair_dict(pi, pj, ps), tau, BAND, COS_TOL,
+                        lambda i, j: orc.cos_dense(ref.S[i], ref.S[j]))
+    assert rep["n"] == tot
+    idx.free()
+
+
+def test_match_query_fp32(torch, M, ctx, orc):
+    c = synth.make_corpus("tiny")
+    V = c.vocab
+    p = Params(k=16)
+    ref = build_index(c.offsets, c.tokens, V, p, orc)
+    idx = M.mrc_build_index(ctx, dev(torch, c.offsets), dev(torch, c.tokens), V, mrc_params(M, p))
+    # arbitrary non-negative query vectors with exact zeros, and real document signatures
+    Q = np.concatenate([synth.random_signatures(300, 16, 11, density=0.3), ref.S[:50].astype(np.float32)])
+    Q[7] = 0.0  # an all-zero query matches nothing
+    for tau in (0.9, 0.5):
+        buf, total = M.mrc_match(ctx, idx, dev(torch, Q), tau)
+        got = M.pairs_to_numpy(buf)
+        Q64 = Q.astype(np.float64)
+        tot, pi, pj, ps = orc.sig_match(Q64, ref.S, tau)
+        compare_pairs(pair_dict(got["i"], got["j"], got["score"]), pair_dict(pi, pj, ps), tau, BAND, COS_TOL,
+                      lambda i, j: orc.cos_dense(Q64[i], ref.S[j]))
+        assert not np.any(got["i"] == 7)
+    idx.free()
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_match_reduced_precision(torch, M, ctx, orc, precision):
+    c = synth.make_corpus("tiny")
+    V = c.vocab
+    p = Params(k=64)
+    ref = build_index(c.offsets, c.tokens, V, p, orc)
+    idx = M.mrc_build_index(ctx, dev(torch, c.offsets), dev(torch, c.tokens), V, mrc_params(M, p, precision))
+    tau = 0.9
+    buf, total = M.mrc_match(ctx, idx, None, tau)
+    got = M.pairs_to_numpy(buf)
+    tot, pi, pj, ps = orc.sig_pairs(ref.S, tau)
+    g = set(zip(got["i"].tolist(), got["j"].tolist()))
+    o = set(zip(pi.tolist(), pj.tolist()))
+    inter = len(g & o)
+    recall = inter / max(len(o), 1)
+    prec = inter / max(len(g), 1)
+    assert recall >= 0.99 and prec >= 0.99, (recall, prec, len(g), len(o))
+    # rescored scores are FP32 cosines of the index's own unit signatures
+    oscore = pair_dict(pi, pj, ps)
+    err = [abs(s - oscore[(i, j)]) for i, j, s in zip(got["i"], got["j"], got["score"]) if (i, j) in oscore]
+    assert max(err) < (1e-5 if precision == 2 else 2e-2)
+    idx.free()
+
+
+@pytest.mark.parametrize("tau,weighting", [(0.5, 1), (0.9, 1), (0.7, 0)])
+def test_cosine_allpairs(torch, M, ctx, orc, tau, weighting):
+    offs, toks = mixed_corpus(n_tiny=1500, n_long=12)
+    V = 5000
+    p = Params(k=8, weighting=weighting)
+    ref = build_index(offs, toks, V, p, orc)
+    idx = M.mrc_build_index(ctx, dev(torch, offs), dev(torch, toks), V, mrc_params(M, p))
+    buf, total = M.cosine_allpairs(ctx, idx, dev(torch, offs), dev(torch, toks), tau)
+    got = M.pairs_to_numpy(buf)
+    tot, pi, pj, ps = orc.cosine_pairs(ref.row_ptr, ref.terms, ref.w, tau)
+    rep = compare_pairs(pair_dict(got["i"], got["j"], got["score"]), pair_dict(pi, pj, ps), tau, BAND, COS_TOL,
+                        lambda i, j: orc.cosine_pair(ref.row_ptr, ref.terms, ref.w, i, j))
+    assert rep["n"] == tot and tot > 0
+    idx.free()
+
+
+def test_simhash_match_bit_exact(torch, M, ctx, orc):
+    c = synth.make_corpus("tiny")
+    ref_F = orc.simhash(c.offsets, c.tokens, 0x1810030990)
+    for hmax in (0, 3, 6):
+        buf, total = M.simhash_match(ctx, dev(torch, ref_F.view(np.int64)), None, hmax)
+        got = M.pairs_to_numpy(buf)
+        tot, pi, pj, ph = orc.hamming_pairs(ref_F, None, hmax)
+        assert total == tot
+        assert sorted(zip(got["i"].tolist(), got["j"].tolist(), got["score"].astype(int).tolist())) == sorted(
+            zip(pi.tolist(), pj.tolist(), ph.tolist()))
+    # query x index with planted near copies, ragged sizes
+    X = synth.random_fingerprints(5003, 21, n_near=800, max_flip=4)
+    Q = np.concatenate([X[-300:], synth.random_fingerprints(77, 22)])
+    buf, total = M.simhash_match(ctx, dev(torch, Q.view(np.int64)), dev(torch, X.view(np.int64)), 4)
+    got = M.pairs_to_numpy(buf)
+    tot, pi, pj, ph = orc.hamming_pairs(Q, X, 4)
+    assert total == tot and tot >= 300
+    assert sorted(zip(got["i"].tolist(), got["j"].tolist())) == sorted(zip(pi.tolist(), pj.tolist()))
+
+
+def test_host_buffers_same_results(torch, M, ctx):
+    c = synth.make_corpus("tiny", n_docs=700)
+    V = c.vocab
+    p = M.params_default(k=16)
+    a = M.mrc_build_index(ctx, dev(torch, c.offsets), dev(torch, c.tokens), V, p)
+    b = M.mrc_build_index(ctx, c.offsets, c.tokens, V, p)
+    ea, eb = M.mrc_index_export(ctx, a), M.mrc_index_export(ctx, b)
+    assert np.array_equal(ea["sig"], eb["sig"]) and np.array_equal(ea["simhash"], eb["simhash"])
+    ga = M.pairs_to_numpy(M.mrc_match(ctx, a, None, 0.8)[0])
+    gb = M.mrc_match(ctx, b, None, 0.8, device=None)[0]
+    assert sorted(ga.tolist()) == sorted(gb.tolist())
+    ca = M.pairs_to_numpy(M.cosine_allpairs(ctx, a, dev(torch, c.offsets), dev(torch, c.tokens), 0.6)[0])
+    cb = M.cosine_allpairs(ctx, b, c.offsets, c.tokens, 0.6, device=None)[0]
+    assert sorted(ca.tolist()) == sorted(cb.tolist())
+    a.free()
+    b.free()
+
+
+def test_errors_and_capacity(torch, M, ctx):
+    c = synth.make_corpus("tiny", n_docs=300)
+    V = c.vocab
+    bad = c.tokens.copy()
+    bad[17] = V + 3
+    with pytest.raises(M.MrcError) as e:
+        M.mrc_build_index(ctx, dev(torch, c.offsets), dev(torch, bad), V, M.params_default())
+    assert e.value.status == M.MRC_ERR_INVALID
+    with pytest.raises(M.MrcError) as e:
+        M.mrc_build_index(ctx, c.offsets, c.tokens, V, M.params_default(k=0))
+    assert e.value.status == M.MRC_ERR_INVALID
+    idx = M.mrc_build_index(ctx, dev(torch, c.offsets), dev(torch, c.tokens), V, M.params_default(k=8))
+    full, total = M.mrc_match(ctx, idx, None, 0.5)
+    assert total > 10
+    part, total2 = M.mrc_match(ctx, idx, None, 0.5, capacity=10, grow=False)
+    assert total2 == total and part.shape[0] == 10
+    fullset = {tuple(r) for r in M.pairs_to_numpy(full)[["i", "j"]].tolist()}
+    assert {tuple(r) for r in M.pairs_to_numpy(part)[["i", "j"]].tolist()} <= fullset
+    idx.free()
+
+
+def test_save_load_roundtrip(torch, M, ctx, tmp_path):
+    c = synth.make_corpus("tiny", n_docs=500)
+    for prec in (0, 1, 2):
+        idx = M.mrc_build_index(ctx, dev(torch, c.offsets), dev(torch, c.tokens), c.vocab,
+                                M.params_default(k=32, precision=prec))
+        path = str(tmp_path / f"idx{prec}.bin")
+        M.mrc_index_save(ctx, idx, path)
+        idx2 = M.mrc_index_load(ctx, path)
+        e1, e2 = M.mrc_index_export(ctx, idx), M.mrc_index_export(ctx, idx2)
+        for key in ("sig", "simhash", "df", "idf", "part"):
+            assert np.array_equal(e1[key], e2[key]), key
+        p1 = sorted(M.pairs_to_numpy(M.mrc_match(ctx, idx, None, 0.9)[0]).tolist())
+        p2 = sorted(M.pairs_to_numpy(M.mrc_match(ctx, idx2, None, 0.9)[0]).tolist())
+        assert p1 == p2
+        q, _ = M.mrc_signature(ctx, idx2, dev(torch, c.offsets), dev(torch, c.tokens))
+        assert np.array_equal(q.cpu().numpy(), e1["sig"])
+        idx.free()
+        idx2.free()
