@@ -142,6 +142,31 @@ mrc_status mrc_signature(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* d
                          uint64_t* simhash);
 
 /*
+ * mrc_signature for callers that cannot allocate device memory on the call
+ * path: for example a serving process whose memory manager has already
+ * reserved the GPU's free memory for its own pools and admission control, or
+ * a request path that must not call cudaMalloc/cudaFree because they
+ * synchronise the device and can fail under memory pressure. The paper has no
+ * counterpart; this is a service of the library.
+ *
+ * Same results as mrc_signature (same kernels). Differences:
+ * - it allocates nothing: its scratch is a fixed array of about 512 KB that
+ *   the library keeps on every device that loads it, until the process exits;
+ * - at most MRC_NOALLOC_MAX_DOCS documents per call (more: MRC_ERR_INVALID);
+ * - offsets, tokens, sig and simhash must all be device memory (it copies
+ *   nothing; host pointers: MRC_ERR_INVALID);
+ * - the first call on a device looks up the array's device address (one
+ *   runtime call, which also loads the library's device code if it is not
+ *   loaded yet); make that first call before any stream capture;
+ * - all calls on a device share the array: calls whose work overlaps on the
+ *   GPU (other streams, other host threads) race and must be serialised.
+ * The call synchronises the context's stream.
+ */
+#define MRC_NOALLOC_MAX_DOCS 65536
+mrc_status mrc_signature_noalloc(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float* sig,
+                                 uint64_t* simhash);
+
+/*
  * Signature comparison with a fused threshold: the cosine of two signatures
  * (the "multi reference cosine" of Eq. 2) >= tau. query_sig == NULL compares
  * all index pairs i < j; otherwise query_sig holds nq raw float32 signatures

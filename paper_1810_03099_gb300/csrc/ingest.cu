@@ -571,3 +571,72 @@ cudaError_t launch_densify(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const 
 }
 
 }  // namespace mrc
+
+namespace mrc {
+
+// Signature pass whose scratch (document lists, counters, error word) is supplied by the
+// caller instead of the context's workspace. lists: [2 * cap] int32; counts: [8] int32;
+// err: [1] int32; all device memory, n_docs <= cap. *host_err receives the error word.
+cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo,
+                                     const float* rinv, int32_t k, int32_t bf16_weights, uint64_t seed,
+                                     const SigOut& out, int32_t* lists, int64_t cap, int32_t* counts, int32_t* err,
+                                     int32_t* host_err) {
+  *host_err = 0;
+  if (d.n_docs > cap || d.n_docs < 0) return cudaErrorInvalidValue;
+  IngestParams p = base_params(d);
+  p.vocab = vocab;
+  p.tinfo = tinfo;
+  p.rinv = rinv;
+  p.k = k;
+  p.bf16w = bf16_weights;
+  p.seed = seed;
+  p.sig = out;
+  int32_t* short_list = lists;
+  int32_t* long_list = lists + cap;
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * 8, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int32_t), ctx->stream);
+  if (e != cudaSuccess) return e;
+  if (d.n_docs > 0)
+    k_classify<<<(unsigned)((d.n_docs + 255) / 256), 256, 0, ctx->stream>>>(d.offsets, d.n_docs, short_list,
+                                                                            long_list, counts, counts + 2, err);
+  int32_t h[5] = {0, 0, 0, 0, 0};
+  e = cudaMemcpyAsync(h, counts, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h + 4, err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (h[4] != 0) {
+    *host_err = h[4];
+    return cudaSuccess;
+  }
+  p.short_list = short_list;
+  p.long_list = long_list;
+  p.list_counts = counts;
+  p.long_cursor = counts + 3;
+  p.err = err;
+  const size_t s_smem = short_smem(k), l_smem = long_smem(k);
+  e = cudaFuncSetAttribute(k_ingest_short<kSIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ingest_long<kSIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l_smem);
+  if (e != cudaSuccess) return e;
+  if (h[0] > 0) {
+    int grid = ctx->num_sms * 2;
+    const int need = (h[0] + kWarpsShort - 1) / kWarpsShort;
+    if (need < grid) grid = need;
+    k_ingest_short<kSIG><<<grid, kWarpsShort * 32, s_smem, ctx->stream>>>(p);
+  }
+  if (h[1] > 0) {
+    int grid = ctx->num_sms;
+    if (h[1] < grid) grid = h[1];
+    k_ingest_long<kSIG><<<grid, kLongThreads, l_smem, ctx->stream>>>(p);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(h + 4, err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return e;
+  *host_err = h[4];
+  return cudaSuccess;
+}
+
+}  // namespace mrc

@@ -60,6 +60,7 @@ _SIGNATURES = {
     "mrc_last_error": (C.c_char_p, [C.c_void_p]),
     "mrc_build_index": (C.c_int32, [C.c_void_p, C.POINTER(Docs), C.c_int32, C.POINTER(Params), C.POINTER(C.c_void_p)]),
     "mrc_signature": (C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(Docs), C.c_void_p, C.c_void_p]),
+    "mrc_signature_noalloc": (C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(Docs), C.c_void_p, C.c_void_p]),
     "mrc_match": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_void_p, C.c_int64,
                               C.POINTER(C.c_int64)]),
     "cosine_allpairs": (C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(Docs), C.c_float, C.c_void_p, C.c_int64,
@@ -249,6 +250,17 @@ def mrc_signature(ctx: Context, index: Index, offsets, tokens, sig=None, simhash
     d = _docs(offsets, tokens)
     ctx.check(ctx.lib.mrc_signature(ctx.handle, index.handle, C.byref(d), _ptr(sig), _ptr(simhash)))
     return sig, simhash
+
+
+def mrc_signature_noalloc(ctx: Context, index: Index, offsets, tokens, sig, simhash=None):
+    """Signatures into caller-provided device tensors without any device allocation
+    (at most NOALLOC_MAX_DOCS documents; every buffer must be device memory)."""
+    d = _docs(offsets, tokens)
+    ctx.check(ctx.lib.mrc_signature_noalloc(ctx.handle, index.handle, C.byref(d), _ptr(sig), _ptr(simhash)))
+    return sig, simhash
+
+
+NOALLOC_MAX_DOCS = 65536
 
 
 def _pairs_buf(capacity, device):
