@@ -207,6 +207,8 @@ mrc_status mrc_index_export(mrc_ctx* ctx, const mrc_index* index, float* sig /*[
  * versioned binary file, and load it back onto ctx's device. */
 mrc_status mrc_index_save(mrc_ctx* ctx, const mrc_index* index, const char* path);
 mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out);
+/* Release an index. Its memory is returned in order on the stream of the context that
+ * built (or loaded) it, so that stream must still exist. */
 void mrc_index_free(mrc_index* index);
 
 /*

@@ -230,11 +230,21 @@ int64_t select_references(const std::vector<int32_t>& df, int64_t n_docs, const 
     for (int32_t t = 0; t < V && (int64_t)sel.size() < L; ++t)
       if (df[t] == 1) sel.push_back(t);
   } else {
-    std::vector<int32_t> ranked;
-    ranked.reserve(V);
+    // counting sort: df descending, ids ascending within equal df
+    int32_t maxdf = 0;
+    for (int32_t t = 0; t < V; ++t) maxdf = std::max(maxdf, df[t]);
+    std::vector<int64_t> pos((size_t)maxdf + 2, 0);
     for (int32_t t = 0; t < V; ++t)
-      if (df[t] > 0) ranked.push_back(t);
-    std::stable_sort(ranked.begin(), ranked.end(), [&](int32_t a, int32_t b) { return df[a] > df[b]; });
+      if (df[t] > 0) pos[df[t]] += 1;
+    int64_t acc = 0;
+    for (int32_t v = maxdf; v >= 1; --v) {
+      const int64_t c = pos[v];
+      pos[v] = acc;
+      acc += c;
+    }
+    std::vector<int32_t> ranked((size_t)acc);
+    for (int32_t t = 0; t < V; ++t)
+      if (df[t] > 0) ranked[pos[df[t]]++] = t;
     if (p.select_mode == MRC_SELECT_ALL) {
       sel = ranked;
     } else {
@@ -256,11 +266,13 @@ int64_t select_references(const std::vector<int32_t>& df, int64_t n_docs, const 
   return n;
 }
 
+// Index arrays come from the device's stream-ordered memory pool (kept, not returned to the
+// driver, between builds), so building and freeing indexes does not synchronise the device.
 template <typename T>
 mrc_status dev_alloc(mrc_ctx* ctx, T** p, size_t count, const char* what) {
   *p = nullptr;
   if (count == 0) count = 1;
-  if (cudaMalloc((void**)p, sizeof(T) * count) != cudaSuccess) {
+  if (cudaMallocAsync((void**)p, sizeof(T) * count, ctx->stream) != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, MRC_ERR_OOM, std::string("device allocation failed: ") + what);
   }
@@ -271,7 +283,7 @@ void free_index_arrays(mrc_index* x) {
   void* ptrs[] = {x->df,    x->idf,   x->tinfo, x->rinv,    x->sig,  x->sig_unit,
                   x->simhash, x->op_hi, x->op_lo, x->op_e4m3, x->qnorm};
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, x->stream);
 }
 
 // Uploads term info (idf under the weighting, partition) and 1/|R_p|.
@@ -409,6 +421,12 @@ mrc_status mrc_ctx_create(void* cuda_stream, mrc_ctx** out) {
     return MRC_ERR_UNSUPPORTED;  // built for sm_103a (Blackwell Ultra) only
   }
   c->stream = (cudaStream_t)cuda_stream;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;  // freed index memory stays in this process's pool for reuse
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
   if (cudaMallocHost(&c->pinned, 4096) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -451,6 +469,7 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
 
   mrc_index* x = new mrc_index();
   x->device = ctx->device;
+  x->stream = ctx->stream;
   x->params = *params;
   x->n_docs = d.n_docs;
   x->vocab = vocab;
@@ -472,8 +491,7 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
 
   // a1: document frequencies, then idf
   e = launch_df(ctx, d, x->df, vocab);
-  if (e != cudaSuccess && e != cudaErrorInvalidValue) return bail(cuda_fail(ctx, e, "df pass"));
-  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "df pass"));
   e = launch_idf(ctx, d.n_docs, x->df, vocab, params->weighting, x->idf, nullptr);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "idf"));
   x->h_df.resize(vocab);
@@ -481,8 +499,8 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   e = cudaMemcpyAsync(x->h_df.data(), x->df, sizeof(int32_t) * vocab, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(x->h_idf.data(), x->idf, sizeof(float) * vocab, cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "reading df"));
+  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);  // synchronises the stream
 
   // references (host sort of the vocabulary), then their device tables
   x->L_used = select_references(x->h_df, d.n_docs, *params, &x->h_part);
@@ -495,7 +513,7 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   if (x->op_e4m3) cudaMemsetAsync(x->op_e4m3, 0, (size_t)x->n_docs * x->kp8, ctx->stream);
   e = launch_signature(ctx, d, vocab, x->tinfo, x->rinv, x->k, params->precision == MRC_PREC_BF16_FP8, params->seed,
                        index_sig_out(x));
-  if (e != cudaSuccess && e != cudaErrorInvalidValue) return bail(cuda_fail(ctx, e, "signature pass"));
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "signature pass"));
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);
   *out = x;
   return MRC_OK;
@@ -520,7 +538,7 @@ mrc_status mrc_signature(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* d
   if (st != MRC_OK) return st;
   cudaError_t e = launch_signature(ctx, d, index->vocab, index->tinfo, index->rinv, index->k,
                                    index->params.precision == MRC_PREC_BF16_FP8, index->params.seed, o);
-  if (e != cudaSuccess && e != cudaErrorInvalidValue) return cuda_fail(ctx, e, "signature pass");
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "signature pass");
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;
   if (sig_host) e = cudaMemcpyAsync(sig, o.sig, sizeof(float) * (size_t)n * index->k, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess && sh_host)
@@ -655,15 +673,15 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   if (st != MRC_OK) return st;
   cudaMemsetAsync(df, 0, sizeof(int32_t) * V, ctx->stream);
   cudaError_t e = launch_df(ctx, d, df, V);
-  if (e != cudaSuccess && e != cudaErrorInvalidValue) return cuda_fail(ctx, e, "df pass");
-  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "df pass");
   std::vector<int32_t> hdf(V);
-  e = cudaMemcpy(hdf.data(), df, sizeof(int32_t) * V, cudaMemcpyDeviceToHost);
+  e = cudaMemcpyAsync(hdf.data(), df, sizeof(int32_t) * V, cudaMemcpyDeviceToHost, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "reading df");
+  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;  // synchronises the stream
 
   // head = terms whose postings are dense enough that a tensor-core column beats
   // sparse products: df >= max(32, N / 48); tail = the other terms with df >= 2
-  const int64_t cut = std::max<int64_t>(32, N / 48);
+  const int64_t cut = std::min<int64_t>(std::max<int64_t>(32, N / 48), 4097);  // tail lists stay <= 4096
   std::vector<int32_t> head;
   for (int32_t t = 0; t < V; ++t)
     if (hdf[t] >= cut) head.push_back(t);
@@ -672,6 +690,7 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   std::vector<int32_t> colmap(V, -1);
   for (size_t c = 0; c < head.size(); ++c) colmap[head[c]] = (int32_t)c;
   std::vector<int64_t> tstart(V, 0);
+  std::vector<int64_t> cstart(1, 0);  // postings start of each tail term, in term-id order
   int64_t n_post = 0;
   double tail_work = 0.0;
   for (int32_t t = 0; t < V; ++t)
@@ -679,8 +698,25 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
       colmap[t] = -2;
       tstart[t] = n_post;
       n_post += hdf[t];
+      cstart.push_back(n_post);
       tail_work += (double)hdf[t] * (double)(hdf[t] - 1) / 2.0;
     }
+  // sort groups: consecutive tail terms holding <= 4096 postings together
+  const int32_t n_tail = (int32_t)cstart.size() - 1;
+  std::vector<int32_t> gterm(1, 0);
+  {
+    int64_t in_group = 0;
+    for (int32_t c = 0; c < n_tail; ++c) {
+      const int64_t len = cstart[c + 1] - cstart[c];
+      if (in_group > 0 && in_group + len > 4096) {
+        gterm.push_back(c);
+        in_group = 0;
+      }
+      in_group += len;
+    }
+    if (n_tail > 0) gterm.push_back(n_tail);
+  }
+  const int32_t n_groups = (int32_t)gterm.size() - 1;
   const int64_t ldh = (N + 3) / 4 * 4;
   if ((double)N * (double)ldh * 4.0 > 64e9)
     return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more documents than the 64 GB score buffer allows");
@@ -690,6 +726,12 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   int32_t* d_tfill = (int32_t*)ws_get(ctx, "cos.tfill", sizeof(int32_t) * V, &st);
   int32_t* d_pdoc = (int32_t*)ws_get(ctx, "cos.pdoc", sizeof(int32_t) * (size_t)std::max<int64_t>(n_post, 1), &st);
   float* d_pw = (float*)ws_get(ctx, "cos.pw", sizeof(float) * (size_t)std::max<int64_t>(n_post, 1), &st);
+  int32_t* d_pr = (int32_t*)ws_get(ctx, "cos.pr", sizeof(int32_t) * (size_t)std::max<int64_t>(n_post, 1), &st);
+  int32_t* d_sdoc = (int32_t*)ws_get(ctx, "cos.sdoc", sizeof(int32_t) * (size_t)std::max<int64_t>(n_post, 1), &st);
+  float* d_sw = (float*)ws_get(ctx, "cos.sw", sizeof(float) * (size_t)std::max<int64_t>(n_post, 1), &st);
+  int64_t* d_rpos = (int64_t*)ws_get(ctx, "cos.rpos", sizeof(int64_t) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
+  int64_t* d_cstart = (int64_t*)ws_get(ctx, "cos.cstart", sizeof(int64_t) * cstart.size(), &st);
+  int32_t* d_gterm = (int32_t*)ws_get(ctx, "cos.gterm", sizeof(int32_t) * gterm.size(), &st);
   int32_t* d_rcnt = (int32_t*)ws_get(ctx, "cos.rcnt", sizeof(int32_t) * (size_t)N, &st);
   int32_t* d_rterm = (int32_t*)ws_get(ctx, "cos.rterm", sizeof(int32_t) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
   float* d_rw = (float*)ws_get(ctx, "cos.rw", sizeof(float) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
@@ -700,6 +742,10 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   e = cudaMemcpyAsync(d_colmap, colmap.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_tstart, tstart.data(), sizeof(int64_t) * V, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_cstart, cstart.data(), sizeof(int64_t) * cstart.size(), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_gterm, gterm.data(), sizeof(int32_t) * gterm.size(), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_tfill, 0, sizeof(int32_t) * V, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_hhi, 0, 2 * (size_t)N * kd, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_hlo, 0, 2 * (size_t)N * kd, ctx->stream);
@@ -715,11 +761,14 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   o.tail_fill = d_tfill;
   o.post_doc = d_pdoc;
   o.post_w = d_pw;
+  o.post_r = d_pr;
   o.row_cnt = d_rcnt;
   o.row_term = d_rterm;
   o.row_w = d_rw;
   e = launch_densify(ctx, d, V, index->tinfo, o);
-  if (e != cudaSuccess && e != cudaErrorInvalidValue) return cuda_fail(ctx, e, "densify");
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "densify");
+  e = launch_sort_postings(ctx, d_cstart, d_gterm, n_groups, d_pdoc, d_pw, d_pr, d.offsets, d_sdoc, d_sw, d_rpos);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sorting postings");
 
   // head: tensor-core GEMM of the unit head columns (FP32-accurate split), stored
   GemmArgs g{};
@@ -737,8 +786,8 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   if (e != cudaSuccess) return cuda_fail(ctx, e, "head GEMM");
 
   // tail: postings products added to the head scores, threshold, compaction
-  e = launch_cosine_tail(ctx, N, d_H, ldh, d.offsets, d_rcnt, d_rterm, d_rw, d_tstart, d_tfill, d_pdoc, d_pw, tau,
-                         dst, d_count, capacity, tail_work);
+  e = launch_cosine_tail(ctx, N, d_H, ldh, d.offsets, d_rcnt, d_rterm, d_rw, d_rpos, d_tstart, d_tfill, d_sdoc, d_sw,
+                         tau, dst, d_count, capacity, tail_work);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tail pass");
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;
   return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
@@ -805,7 +854,6 @@ void mrc_index_free(mrc_index* x) {
   int cur = -1;
   cudaGetDevice(&cur);
   if (cur != x->device) cudaSetDevice(x->device);
-  cudaDeviceSynchronize();
   free_index_arrays(x);
   if (cur >= 0 && cur != x->device) cudaSetDevice(cur);
   delete x;
@@ -871,6 +919,7 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
     x->kp = round_up(x->k, 64);
     x->kp8 = round_up(x->k, 128);
     x->device = ctx->device;
+    x->stream = ctx->stream;
     const size_t n = (size_t)x->n_docs;
     x->h_df.resize(x->vocab);
     x->h_idf.resize(x->vocab);
@@ -903,7 +952,8 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
   if ((st = dev_alloc(ctx, &x->rinv, x->k, "reference norms")) != MRC_OK) return bail(st);
   if ((st = alloc_signature_arrays(ctx, x)) != MRC_OK) return bail(st);
   const size_t n = (size_t)x->n_docs;
-  cudaError_t e = cudaMemcpy(x->df, x->h_df.data(), sizeof(int32_t) * x->vocab, cudaMemcpyHostToDevice);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);  // stream-ordered allocations before plain copies
+  if (e == cudaSuccess) e = cudaMemcpy(x->df, x->h_df.data(), sizeof(int32_t) * x->vocab, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(x->idf, x->h_idf.data(), sizeof(float) * x->vocab, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(x->sig, sig.data(), sizeof(float) * sig.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(x->sig_unit, unit.data(), sizeof(float) * unit.size(), cudaMemcpyHostToDevice);

@@ -171,27 +171,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Tile t -> (row block bi in units of 128, column block bj in units of BN).
+// Tile t -> (row block bi in units of 128, column block bj in units of BN). 32-bit integer
+// and FP32 arithmetic only (the host guarantees n_tiles < 2^31 and super_rows^2 < 2^31).
 template <int BN>
-__device__ __forceinline__ bool decode_tile(const GemmParams& p, int64_t t, int64_t& bi, int64_t& bj) {
+__device__ __forceinline__ bool decode_tile(const GemmParams& p, int64_t t64, int64_t& bi, int64_t& bj) {
+  const int32_t t = (int32_t)t64;
   if (!p.triangle) {
-    bi = t % p.tiles_m;
-    bj = t / p.tiles_m;
+    const int32_t tm = (int32_t)p.tiles_m;
+    bi = t % tm;
+    bj = t / tm;
     return true;
   }
-  constexpr int H = BN / kBM;
-  const int64_t s = t / H;
-  const int64_t h = t % H;
-  const int64_t R = p.super_rows;
+  constexpr int H = BN / kBM;  // 1 or 2 row blocks per super tile
+  const int32_t s = t / H;
+  const int32_t h = t - s * H;
+  const int32_t R = (int32_t)p.super_rows;
   // row-major upper triangle of R x R super tiles: row I starts at I*R - I*(I-1)/2
-  const double b = 2.0 * (double)R + 1.0;
-  int64_t I = (int64_t)((b - sqrt(fmax(b * b - 8.0 * (double)s, 0.0))) * 0.5);
-  if (I < 0) I = 0;
-  if (I > R - 1) I = R - 1;
+  const float b = 2.0f * (float)R + 1.0f;
+  int32_t I = (int32_t)((b - sqrtf(fmaxf(b * b - 8.0f * (float)s, 0.0f))) * 0.5f);
+  I = I < 0 ? 0 : (I > R - 1 ? R - 1 : I);
   while (I > 0 && I * R - I * (I - 1) / 2 > s) --I;
   while (I + 1 < R && (I + 1) * R - (I + 1) * I / 2 <= s) ++I;
-  const int64_t J = I + (s - (I * R - I * (I - 1) / 2));
-  bi = I * H + h;
+  const int32_t J = I + (s - (I * R - I * (I - 1) / 2));
+  bi = (int64_t)I * H + h;
   bj = J;
   return bi * kBM < p.na;
 }
@@ -482,6 +484,7 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   p.tiles_n = (g.nb + BN - 1) / BN;
   p.super_rows = (g.na + BN - 1) / BN;
   p.n_tiles = g.triangle ? p.super_rows * (p.super_rows + 1) / 2 * (BN / kBM) : p.tiles_m * p.tiles_n;
+  if (p.n_tiles >= (1ll << 31) || p.super_rows * p.super_rows >= (1ll << 31)) return cudaErrorInvalidValue;
   p.thresh = g.thresh;
   p.out_scale = g.out_scale;
   p.a_norm = g.a_norm;

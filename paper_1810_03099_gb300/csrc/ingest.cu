@@ -129,9 +129,9 @@ struct Acc {
 // Process one warp-chunk of 32 table slots [s0, s0 + 32).
 template <int MODE>
 __device__ __forceinline__ void chunk(const IngestParams& p, const uint32_t* keys, const uint32_t* cnts, int s0,
-                                      int lane, unsigned long long* num_q, Acc& a, int dense_phase, int64_t doc,
-                                      float inv_norm, int32_t* row_cnt_s, int64_t row_base) {
-  const uint32_t key = keys[s0 + lane];
+                                      int limit, int lane, unsigned long long* num_q, Acc& a, int dense_phase,
+                                      int64_t doc, float inv_norm, int32_t* row_cnt_s, int64_t row_base) {
+  const uint32_t key = s0 + lane < limit ? keys[s0 + lane] : kEmpty;
   const bool valid = key != kEmpty;
   const unsigned any = __ballot_sync(kFull, valid);
   if (any == 0u) return;
@@ -182,9 +182,10 @@ __device__ __forceinline__ void chunk(const IngestParams& p, const uint32_t* key
     reinterpret_cast<__half*>(p.dense.head_lo)[at] = lo;
   } else if (code == -2) {
     const int64_t pos = p.dense.tail_start[key] + atomicAdd(&p.dense.tail_fill[key], 1);
+    const int32_t r = atomicAdd(row_cnt_s, 1);
     p.dense.post_doc[pos] = (int32_t)doc;
     p.dense.post_w[pos] = u;
-    const int32_t r = atomicAdd(row_cnt_s, 1);
+    p.dense.post_r[pos] = r;
     p.dense.row_term[row_base + r] = (int32_t)key;
     p.dense.row_w[row_base + r] = u;
   }
@@ -270,12 +271,27 @@ __global__ void __launch_bounds__(kWarpsShort * 32) k_ingest_short(IngestParams 
       if (!table_insert(keys, cnts, l2, (uint32_t)t)) set_err(p.err, kErrTable);
     }
     __syncwarp();
+    // compact the occupied slots to the front, in place (a write never passes an unread slot)
+    int nnz = 0;
+    for (int s0 = 0; s0 < ts; s0 += 32) {
+      const uint32_t key = keys[s0 + lane], c = cnts[s0 + lane];
+      const bool valid = key != kEmpty;
+      const unsigned bal = __ballot_sync(kFull, valid);
+      __syncwarp();
+      if (valid) {
+        const int at = nnz + __popc(bal & ((1u << lane) - 1u));
+        keys[at] = key;
+        cnts[at] = c;
+      }
+      nnz += __popc(bal);
+      __syncwarp();
+    }
     Acc a{0ull, 0u, 0u};
     float inv_norm = 0.f;
     const int phases = MODE == kDENSE ? 2 : 1;
     for (int ph = 0; ph < phases; ++ph) {
-      for (int s0 = 0; s0 < ts; s0 += 32)
-        chunk<MODE>(p, keys, cnts, s0, lane, num_q, a, ph, d, inv_norm, row_cnt_s, o0);
+      for (int s0 = 0; s0 < nnz; s0 += 32)
+        chunk<MODE>(p, keys, cnts, s0, nnz, lane, num_q, a, ph, d, inv_norm, row_cnt_s, o0);
       if (MODE == kDENSE && ph == 0) {
         const unsigned long long nq = warp_sum(a.norm);
         const float n2 = (float)nq * kInvFix;
@@ -342,7 +358,7 @@ __global__ void __launch_bounds__(kLongThreads) k_ingest_long(IngestParams p) {
         }
         __syncthreads();
         for (int s0 = warp * 32; s0 < ts; s0 += nwarps * 32)
-          chunk<MODE>(p, keys, cnts, s0, lane, num_q, a, ph, d, inv_norm, &misc[1], o0);
+          chunk<MODE>(p, keys, cnts, s0, ts, lane, num_q, a, ph, d, inv_norm, &misc[1], o0);
       }
       if (MODE == kDENSE && ph == 0) {
         const unsigned long long nq = warp_sum(a.norm);
@@ -439,50 +455,27 @@ __global__ void k_pack(const float* sig, int64_t n, int32_t k, int32_t normalize
 size_t short_smem(int kq) { return (size_t)kWarpsShort * ((size_t)kShortSlots * 8 + (size_t)kq * 8 + 16); }
 size_t long_smem(int kq) { return (size_t)kq * 8 + 8 + 64 * 4 + 16 + (size_t)kLongSlots * 8; }
 
-struct Lists {
-  int32_t* short_list;
-  int32_t* long_list;
-  int32_t* counts;  // [0] short [1] long [2] max_len [3] long cursor
-  int32_t* err;     // the call's device error word
-  int32_t h[5];
-};
-
-// Classifies documents and reads back the list sizes (one small sync).
-cudaError_t classify(mrc_ctx* ctx, const DocsDev& d, Lists* L) {
-  mrc_status st = MRC_OK;
-  L->short_list = (int32_t*)ws_get(ctx, "ingest.short", sizeof(int32_t) * (size_t)std::max<int64_t>(d.n_docs, 1), &st);
-  L->long_list = (int32_t*)ws_get(ctx, "ingest.long", sizeof(int32_t) * (size_t)std::max<int64_t>(d.n_docs, 1), &st);
-  L->counts = (int32_t*)ws_get(ctx, "ingest.counts", sizeof(int32_t) * 8, &st);
-  L->err = d.err;
-  if (st != MRC_OK) return cudaErrorMemoryAllocation;
-  cudaError_t e = cudaMemsetAsync(L->counts, 0, sizeof(int32_t) * 8, ctx->stream);
-  if (e != cudaSuccess) return e;
-  if (d.n_docs > 0) {
-    const int64_t blocks = (d.n_docs + 255) / 256;
-    k_classify<<<(unsigned)blocks, 256, 0, ctx->stream>>>(d.offsets, d.n_docs, L->short_list, L->long_list,
-                                                          L->counts, L->counts + 2, L->err);
-  }
-  e = cudaMemcpyAsync(L->h, L->counts, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, ctx->stream);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(L->h + 4, L->err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
-}
-
 template <int MODE>
 cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const char* name, double bytes_per_token,
                        double bytes_per_doc) {
-  Lists L;
-  cudaError_t e = classify(ctx, d, &L);
+  // Lists and counters stay on the device: both paths read their list sizes there, so no
+  // host round trip is needed. Offsets/length errors land in the call's error word.
+  mrc_status st = MRC_OK;
+  const size_t list_bytes = sizeof(int32_t) * (size_t)std::max<int64_t>(d.n_docs, 1);
+  int32_t* short_list = (int32_t*)ws_get(ctx, "ingest.short", list_bytes, &st);
+  int32_t* long_list = (int32_t*)ws_get(ctx, "ingest.long", list_bytes, &st);
+  int32_t* counts = (int32_t*)ws_get(ctx, "ingest.counts", sizeof(int32_t) * 8, &st);
+  if (st != MRC_OK) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * 8, ctx->stream);
   if (e != cudaSuccess) return e;
-  if (L.h[4] != 0) return cudaErrorInvalidValue;  // reported by the caller as MRC_ERR_INVALID
-  p.short_list = L.short_list;
-  p.long_list = L.long_list;
-  p.list_counts = L.counts;
-  p.long_cursor = L.counts + 3;
-  p.err = L.err;
+  if (d.n_docs <= 0) return cudaSuccess;
+  k_classify<<<(unsigned)((d.n_docs + 255) / 256), 256, 0, ctx->stream>>>(d.offsets, d.n_docs, short_list, long_list,
+                                                                          counts, counts + 2, d.err);
+  p.short_list = short_list;
+  p.long_list = long_list;
+  p.list_counts = counts;
+  p.long_cursor = counts + 3;
+  p.err = d.err;
   const int kq = MODE == kSIG ? p.k : 0;
   const size_t s_smem = short_smem(kq), l_smem = long_smem(kq);
   e = cudaFuncSetAttribute(k_ingest_short<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_smem);
@@ -491,11 +484,10 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   if (e != cudaSuccess) return e;
   const double tokens = (double)d.n_tokens;
   cudaEvent_t ev = nullptr;
-  if (L.h[0] > 0) {
-    const int per_sm = 2;
-    int grid = ctx->num_sms * per_sm;
-    const int need = (L.h[0] + kWarpsShort - 1) / kWarpsShort;
-    if (need < grid) grid = need;
+  {
+    int grid = ctx->num_sms * 2;
+    const int64_t need = (d.n_docs + kWarpsShort - 1) / kWarpsShort;
+    if (need < grid) grid = (int)need;
     std::string nm = std::string(name) + ".short";
     timing_begin(ctx, nm.c_str(), tokens * bytes_per_token + bytes_per_doc * d.n_docs, 0.0, &ev);
     k_ingest_short<MODE><<<grid, kWarpsShort * 32, s_smem, ctx->stream>>>(p);
@@ -503,9 +495,9 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (L.h[1] > 0) {
+  {
     int grid = ctx->num_sms;
-    if (L.h[1] < grid) grid = L.h[1];
+    if (d.n_docs < grid) grid = (int)d.n_docs;
     std::string nm = std::string(name) + ".long";
     timing_begin(ctx, nm.c_str(), 0.0, 0.0, &ev);
     k_ingest_long<MODE><<<grid, kLongThreads, l_smem, ctx->stream>>>(p);

@@ -63,6 +63,7 @@ struct mrc_ctx {
 
 struct mrc_index {
   int device = 0;
+  cudaStream_t stream = nullptr;  // stream of the building context (frees are ordered on it)
   mrc_params params{};
   int64_t n_docs = 0;
   int32_t vocab = 0;
@@ -136,6 +137,7 @@ struct DenseOut {
   int32_t* tail_fill;         // [vocab] fill cursors (zeroed)
   int32_t* post_doc;          // [n_post]
   float* post_w;              // [n_post]
+  int32_t* post_r;            // [n_post] index of the posting's term in its document's tail list
   int32_t* row_cnt;           // [n] tail terms of each doc
   int32_t* row_term;          // [n_tokens] at the doc's token offsets
   float* row_w;               // [n_tokens]
@@ -171,11 +173,17 @@ cudaError_t launch_simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, co
                                  int32_t hmax, mrc_pair* pairs, unsigned long long* count, int64_t capacity);
 
 // tail.cu
+// Sorts every tail term's postings by document (groups of consecutive tail terms holding
+// <= 4096 postings each) into sdoc/sw and records, for each (document, tail term) entry of
+// the per-document lists, the position of that document in the term's sorted postings.
+cudaError_t launch_sort_postings(mrc_ctx* ctx, const int64_t* cstart, const int32_t* gterm, int32_t n_groups,
+                                 const int32_t* post_doc, const float* post_w, const int32_t* post_r,
+                                 const int64_t* doc_off, int32_t* sdoc, float* sw, int64_t* row_pos);
 cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const float* H, int64_t ldh, const int64_t* row_off,
                                const int32_t* row_cnt, const int32_t* row_term, const float* row_w,
-                               const int64_t* tail_start, const int32_t* post_cnt, const int32_t* post_doc,
-                               const float* post_w, float tau, mrc_pair* pairs, unsigned long long* count,
-                               int64_t capacity, double work_pairs);
+                               const int64_t* row_pos, const int64_t* tail_start, const int32_t* post_cnt,
+                               const int32_t* sdoc, const float* sw, float tau, mrc_pair* pairs,
+                               unsigned long long* count, int64_t capacity, double work_pairs);
 cudaError_t launch_rescore(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand, int64_t cand_cap,
                            const float* qunit, const float* xunit, int32_t k, float tau, mrc_pair* pairs,
                            unsigned long long* count, int64_t capacity);
