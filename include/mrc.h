@@ -60,7 +60,8 @@ typedef int32_t mrc_status;
 #define MRC_WEIGHT_TFIDF 1 /* w(d,t) = c(d,t) * (ln((1+N)/(1+df(t))) + 1)       */
 
 /* Arithmetic of the signature comparison. */
-#define MRC_PREC_FP32 0     /* FP32-accurate compare (fp16 hi/lo split on tensor cores) */
+#define MRC_PREC_FP32 0     /* FP32-accurate: fp16 tensor-core candidates within a proven
+                               bound of tau, every candidate rescored in FP32 */
 #define MRC_PREC_BF16_FP8 1 /* BF16 weights, FP8 E4M3 compare, FP32 rescoring near tau  */
 #define MRC_PREC_FP16 2     /* FP16 signatures, FP16 compare, FP32 rescoring near tau   */
 

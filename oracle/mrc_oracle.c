@@ -73,6 +73,25 @@ void orc_idf(int64_t n_docs, int32_t vocab, const int64_t* df, double* idf) {
         idf[t] = log((1.0 + (double)n_docs) / (1.0 + (double)df[t])) + 1.0;
 }
 
+/*
+ * Reduced-precision storage of the per-term weights (the precision form): a
+ * value is rounded to FP32, then to bfloat16 (8 significant bits, round to
+ * nearest, ties to even). out[t] = that value, for every term.
+ */
+double orc_round_bf16(double x) {
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, sizeof(u));
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  u &= 0xFFFF0000u;
+  memcpy(&f, &u, sizeof(f));
+  return (double)f;
+}
+
+void orc_idf_bf16(int32_t vocab, const double* idf, double* out) {
+  for (int32_t t = 0; t < vocab; ++t) out[t] = orc_round_bf16(idf[t]);
+}
+
 /* w(d,t) = c(d,t) * idf(t); with idf == NULL, w = c (the paper's plain counts). */
 void orc_weights(int64_t nnz, const int32_t* terms, const int32_t* counts, const double* idf, double* w) {
     for (int64_t e = 0; e < nnz; ++e) w[e] = (double)counts[e] * (idf ? idf[terms[e]] : 1.0);

@@ -51,6 +51,8 @@ def _sig(lib):
         "orc_hamming": (i32, [u64, u64]),
         "orc_hamming_pairs": (i64, [_u64p, i64, _vp, i64, i32, _i32p, _i32p, _i32p, i64]),
         "orc_error_stats": (None, [_f64p, _f64p, i64, _f64p]),
+        "orc_round_bf16": (f64, [f64]),
+        "orc_idf_bf16": (None, [i32, _f64p, _f64p]),
     }
     for name, (res, args) in spec.items():
         f = getattr(lib, name)
@@ -107,6 +109,15 @@ class Oracle:
         df = np.ascontiguousarray(df, np.int64)
         out = np.zeros(df.shape[0], np.float64)
         self.lib.orc_idf(n_docs, df.shape[0], df, out)
+        return out
+
+    def round_bf16(self, x):
+        return self.lib.orc_round_bf16(float(x))
+
+    def idf_bf16(self, idf):
+        idf = _c64(idf)
+        out = np.zeros_like(idf)
+        self.lib.orc_idf_bf16(idf.shape[0], idf, out)
         return out
 
     def weights(self, terms, counts, idf=None):
@@ -226,6 +237,7 @@ class Params:
     tau: float = 0.9
     hamming_max: int = 3
     seed: int = 0x1810030990
+    bf16: bool = False  # precision form: per-term weights stored as bfloat16
 
     @property
     def L_eff(self) -> int:
@@ -261,6 +273,8 @@ def build_index(offsets, tokens, vocab, params: Params | None = None, orc: Oracl
     df = o.df(row_ptr, terms, vocab)
     idf_values = o.idf(n, df)
     idf = idf_values if p.weighting == WEIGHT_TFIDF else None
+    if idf is not None and p.bf16:
+        idf = o.idf_bf16(idf)  # the stored weight table of the precision form
     w = o.weights(terms, counts, idf)
     part, used = o.select_refs(df, n, p.mode, p.L_eff, p.region_start, p.k)
     rnorm = o.ref_norms(part, p.k, idf)

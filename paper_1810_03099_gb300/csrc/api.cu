@@ -116,6 +116,7 @@ using namespace mrc;
 namespace {
 
 constexpr uint64_t kDefaultSeed = 0x1810030990ull;
+constexpr float kF16CompareBound = 2e-3f;  // > max |fp16 cosine - cosine| of unit vectors (~1e-3)
 
 bool is_device_ptr(const void* p) {
   if (!p) return false;
@@ -217,6 +218,11 @@ bool valid_params(const mrc_params* p, std::string* why) {
 
 int32_t round_up(int32_t x, int32_t m) { return (x + m - 1) / m * m; }
 
+// Padded operand rows: 64-byte rows (one 64B swizzle atom) when they fit, else multiples
+// of 128 bytes. kp counts fp16 elements, kp8 counts E4M3 bytes.
+int32_t padded_kp(int32_t k) { return k <= 32 ? 32 : round_up(k, 64); }
+int32_t padded_kp8(int32_t k) { return k <= 64 ? 64 : round_up(k, 128); }
+
 // Reference selection (Section IV): rank terms by df descending, ties by id;
 // zero-df terms dropped; REGION / ALL / DF1 pick the selection; partition p
 // holds selection positions [floor(pL/k), floor((p+1)L/k)).
@@ -286,12 +292,24 @@ void free_index_arrays(mrc_index* x) {
     if (p) cudaFreeAsync(p, x->stream);
 }
 
-// Uploads term info (idf under the weighting, partition) and 1/|R_p|.
+// Round to the nearest bfloat16 (8 significant bits), ties to even.
+float bf16_round(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, sizeof(u));
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  u &= 0xFFFF0000u;
+  std::memcpy(&f, &u, sizeof(f));
+  return f;
+}
+
+// Uploads term info (idf under the weighting, partition) and 1/|R_p|. In the precision
+// form the stored per-term weights (document and reference) are bfloat16 values.
 mrc_status upload_references(mrc_ctx* ctx, mrc_index* x) {
   const int32_t V = x->vocab;
   std::vector<TermInfo> ti(V);
+  const bool bf16 = x->params.precision == MRC_PREC_BF16_FP8;
   for (int32_t t = 0; t < V; ++t) {
-    ti[t].idf = x->params.weighting == MRC_WEIGHT_TFIDF ? x->h_idf[t] : 1.0f;
+    ti[t].idf = x->params.weighting == MRC_WEIGHT_TFIDF ? (bf16 ? bf16_round(x->h_idf[t]) : x->h_idf[t]) : 1.0f;
     ti[t].code = x->h_part[t];
   }
   // |R_p| from the same float idf the kernels use: each reference term weighs 1 * idf(t)
@@ -324,11 +342,6 @@ mrc_status alloc_signature_arrays(mrc_ctx* ctx, mrc_index* x) {
     uint16_t* h = nullptr;
     if ((st = dev_alloc(ctx, &h, n * x->kp, "fp16 operands")) != MRC_OK) return st;
     x->op_hi = h;
-  }
-  if (x->params.precision == MRC_PREC_FP32) {
-    uint16_t* l = nullptr;
-    if ((st = dev_alloc(ctx, &l, n * x->kp, "fp16 low operands")) != MRC_OK) return st;
-    x->op_lo = l;
   }
   if (x->params.precision == MRC_PREC_BF16_FP8) {
     uint8_t* q = nullptr;
@@ -474,8 +487,8 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   x->n_docs = d.n_docs;
   x->vocab = vocab;
   x->k = params->k;
-  x->kp = round_up(params->k, 64);
-  x->kp8 = round_up(params->k, 128);
+  x->kp = padded_kp(params->k);
+  x->kp8 = padded_kp8(params->k);
   auto bail = [&](mrc_status s) {
     cudaStreamSynchronize(ctx->stream);
     free_index_arrays(x);
@@ -567,7 +580,7 @@ mrc_status mrc_match(mrc_ctx* ctx, const mrc_index* index, const float* query_si
   if ((query_sig && nq == 0) || (!query_sig && N < 2)) return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
 
   // query operands (packed unit signatures) or the index itself
-  const void *a_hi = index->op_hi, *a_lo = index->op_lo, *a8 = index->op_e4m3;
+  const void *a_hi = index->op_hi, *a8 = index->op_e4m3;
   const float* a_unit = index->sig_unit;
   const float* a_norm = index->qnorm;
   int64_t na = N;
@@ -576,74 +589,62 @@ mrc_status mrc_match(mrc_ctx* ctx, const mrc_index* index, const float* query_si
     if (st != MRC_OK) return st;
     float* qu = (float*)ws_get(ctx, "match.qunit", sizeof(float) * (size_t)nq * index->k, &st);
     void* qh = prec != MRC_PREC_BF16_FP8 ? ws_get(ctx, "match.qhi", 2 * (size_t)nq * index->kp, &st) : nullptr;
-    void* ql = prec == MRC_PREC_FP32 ? ws_get(ctx, "match.qlo", 2 * (size_t)nq * index->kp, &st) : nullptr;
     void* q8 = prec == MRC_PREC_BF16_FP8 ? ws_get(ctx, "match.q8", (size_t)nq * index->kp8, &st) : nullptr;
     float* qn = prec == MRC_PREC_BF16_FP8 ? (float*)ws_get(ctx, "match.qnorm", sizeof(float) * (size_t)nq, &st)
                                           : nullptr;
     if (st != MRC_OK) return st;
     cudaError_t e =
-        launch_pack(ctx, q, nq, index->k, 1, qh, ql, q8, qn, qu, qh ? index->kp : 0, q8 ? index->kp8 : 0);
+        launch_pack(ctx, q, nq, index->k, 1, qh, nullptr, q8, qn, qu, qh ? index->kp : 0, q8 ? index->kp8 : 0);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "packing queries");
     a_hi = qh;
-    a_lo = ql;
     a8 = q8;
     a_unit = qu;
     a_norm = qn;
     na = nq;
   }
 
+  // Candidates from the tensor cores at a lowered threshold, then FP32 rescoring of every
+  // candidate. FP32 form: fp16 unit vectors; |fp16 cosine - cosine| <= 2^-10 sum|x_p y_p| +
+  // subnormal and FP32-accumulation terms <= ~1e-3 (Cauchy-Schwarz), so tau - 2e-3 loses no
+  // pair and the rescored scores are FP32-accurate. FP16 / E4M3 forms: tau - margin.
   GemmArgs g{};
   g.na = na;
   g.nb = N;
   g.triangle = query_sig ? 0 : 1;
   g.err = d_err;
-  g.capacity = capacity;
   g.out_scale = 1.0f;
-  if (prec == MRC_PREC_FP32) {
-    g.fmt = OP_SPLIT16;
-    g.a_hi = a_hi;
-    g.a_lo = a_lo;
-    g.b_hi = index->op_hi;
-    g.b_lo = index->op_lo;
-    g.kbytes = index->kp * 2;
-    g.thresh = tau;
-    g.pairs = dst;
-    g.count = d_count;
-    cudaError_t e = launch_gemm_compare(ctx, g);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "signature compare");
-  } else {
-    // reduced precision: candidates at tau - margin, then FP32 rescoring
-    g.fmt = prec == MRC_PREC_FP16 ? OP_F16 : OP_E4M3;
-    g.a_hi = prec == MRC_PREC_FP16 ? a_hi : a8;
-    g.b_hi = prec == MRC_PREC_FP16 ? index->op_hi : index->op_e4m3;
-    g.kbytes = prec == MRC_PREC_FP16 ? index->kp * 2 : index->kp8;
-    g.out_scale = prec == MRC_PREC_FP16 ? 1.0f : 1.0f / (kE4M3Scale * kE4M3Scale);
+  g.fmt = prec == MRC_PREC_BF16_FP8 ? OP_E4M3 : OP_F16;
+  g.a_hi = prec == MRC_PREC_BF16_FP8 ? a8 : a_hi;
+  g.b_hi = prec == MRC_PREC_BF16_FP8 ? index->op_e4m3 : index->op_hi;
+  g.kbytes = prec == MRC_PREC_BF16_FP8 ? index->kp8 : index->kp * 2;
+  if (prec == MRC_PREC_BF16_FP8) {
+    g.out_scale = 1.0f / (kE4M3Scale * kE4M3Scale);
     g.a_norm = a_norm;
     g.b_norm = index->qnorm;
-    g.thresh = tau - index->params.margin;
-    int64_t cand_cap = std::max<int64_t>(4 * capacity, 1 << 20);
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      mrc_pair* cand = (mrc_pair*)ws_get(ctx, "match.cand", sizeof(mrc_pair) * (size_t)cand_cap, &st);
-      if (st != MRC_OK) return st;
-      cudaMemsetAsync(d_count, 0, 2 * sizeof(unsigned long long), ctx->stream);
-      g.pairs = cand;
-      g.count = d_count + 1;
-      g.capacity = cand_cap;
-      cudaError_t e = launch_gemm_compare(ctx, g);
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "signature compare");
-      unsigned long long* hc = (unsigned long long*)ctx->pinned;
-      e = cudaMemcpyAsync(hc, d_count + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "reading candidate count");
-      const int64_t nc = (int64_t)*hc;
-      if (nc <= cand_cap) {
-        e = launch_rescore(ctx, cand, d_count + 1, cand_cap, a_unit, index->sig_unit, index->k, tau, dst, d_count,
-                           capacity);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "rescoring");
-        break;
-      }
-      cand_cap = nc + nc / 8 + 1024;
+  }
+  g.thresh = tau - (prec == MRC_PREC_FP32 ? kF16CompareBound : index->params.margin);
+  int64_t cand_cap = std::max<int64_t>(4 * capacity, 1 << 20);
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    mrc_pair* cand = (mrc_pair*)ws_get(ctx, "match.cand", sizeof(mrc_pair) * (size_t)cand_cap, &st);
+    if (st != MRC_OK) return st;
+    cudaMemsetAsync(d_count, 0, 2 * sizeof(unsigned long long), ctx->stream);
+    g.pairs = cand;
+    g.count = d_count + 1;
+    g.capacity = cand_cap;
+    cudaError_t e = launch_gemm_compare(ctx, g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "signature compare");
+    unsigned long long* hc = (unsigned long long*)ctx->pinned;
+    e = cudaMemcpyAsync(hc, d_count + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reading candidate count");
+    const int64_t nc = (int64_t)*hc;
+    if (nc <= cand_cap) {
+      e = launch_rescore(ctx, cand, d_count + 1, cand_cap, a_unit, index->sig_unit, index->k, tau, dst, d_count,
+                         capacity);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "rescoring");
+      break;
     }
+    cand_cap = nc + nc / 8 + 1024;
   }
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;
   return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
@@ -753,6 +754,7 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
 
   // unit weights: dense head operands and tail postings
   DenseOut o{};
+  o.idf = index->params.weighting == MRC_WEIGHT_TFIDF ? index->idf : nullptr;
   o.colmap = d_colmap;
   o.kd = kd;
   o.head_hi = d_hhi;
@@ -916,8 +918,8 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
   std::vector<uint64_t> sh;
   if (ok) {
     x->k = x->params.k;
-    x->kp = round_up(x->k, 64);
-    x->kp8 = round_up(x->k, 128);
+    x->kp = padded_kp(x->k);
+    x->kp8 = padded_kp8(x->k);
     x->device = ctx->device;
     x->stream = ctx->stream;
     const size_t n = (size_t)x->n_docs;

@@ -25,6 +25,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "device.cuh"
@@ -431,6 +432,299 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Small-K variant (one K block per row: 64- or 128-byte operand rows). Each CTA walks a
+// contiguous, row-major range of tiles, so consecutive tiles share their A rows: A is
+// loaded once per row block into one of two resident buffers and only B streams through
+// a 4-stage ring. Eight epilogue warps (two per TMEM lane quarter) split the columns.
+constexpr int kResThreads = 320;  // warp 0 TMA, warp 1 MMA + TMEM, warps 2..9 epilogue
+constexpr int kResStagesB = 4;
+
+// 64-byte-swizzle descriptor (8-row groups 512 bytes apart) or the 128-byte one.
+template <int RB>
+__device__ __forceinline__ uint64_t sdesc_rb(uint32_t saddr) {
+  if (RB == 128) return sdesc(saddr);
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+// Row-major tile order: row block bi (units of 128), column block bj (units of BN).
+// Triangle: row bi holds column blocks floor(bi / H) .. C - 1 (H = BN / 128).
+template <int BN>
+__device__ __forceinline__ bool decode_rowmajor(const GemmParams& p, int64_t t64, int64_t& bi, int64_t& bj) {
+  const int32_t t = (int32_t)t64;
+  if (!p.triangle) {
+    const int32_t tn = (int32_t)p.tiles_n;
+    bi = t / tn;
+    bj = t - (int32_t)bi * tn;
+    return true;
+  }
+  constexpr int H = BN / kBM;
+  const int32_t C = (int32_t)p.super_rows;
+  // super row I (H row blocks, C - I tiles each) starts at H * (I*C - I*(I-1)/2)
+  const float b = 2.0f * (float)C + 1.0f;
+  const float s = (float)t / (float)H;
+  int32_t I = (int32_t)((b - sqrtf(fmaxf(b * b - 8.0f * s, 0.0f))) * 0.5f);
+  I = I < 0 ? 0 : (I > C - 1 ? C - 1 : I);
+  while (I > 0 && H * (I * C - I * (I - 1) / 2) > t) --I;
+  while (I + 1 < C && H * ((I + 1) * C - (I + 1) * I / 2) <= t) ++I;
+  const int32_t r = t - H * (I * C - I * (I - 1) / 2);
+  const int32_t w = C - I;
+  const int32_t h = r / w;
+  bj = I + (r - h * w);
+  bi = (int64_t)I * H + h;
+  return bi * kBM < p.na;
+}
+
+template <int FMT, int RB>
+__global__ void __launch_bounds__(kResThreads, 1)
+    k_gemm_resident(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+                    const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1, GemmParams p) {
+  using C = Cfg<FMT>;
+  constexpr int BN = C::BN;
+  constexpr uint32_t A_BYTES = kBM * RB, B_BYTES = BN * RB;
+  constexpr uint32_t A_STAGE = C::NOPS * A_BYTES, B_STAGE = C::NOPS * B_BYTES;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* abuf = smem;                    // [2][A_STAGE]
+  uint8_t* bbuf = smem + 2 * A_STAGE;      // [kResStagesB][B_STAGE]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(bbuf + kResStagesB * B_STAGE);
+  uint64_t* a_full = bar;
+  uint64_t* a_empty = bar + 2;
+  uint64_t* b_full = bar + 4;
+  uint64_t* b_empty = b_full + kResStagesB;
+  uint64_t* acc_full = b_empty + kResStagesB;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
+  float* stage_all = reinterpret_cast<float*>(drain + 4);  // [8 warps][32 x 33]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* stage = stage_all + (warp >= 2 ? warp - 2 : 0) * (32 * 33);
+  const int64_t t_begin = p.n_tiles * blockIdx.x / gridDim.x;
+  const int64_t t_end = p.n_tiles * (blockIdx.x + 1) / gridDim.x;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&a_full[b], 1);
+      mbar_init(&a_empty[b], 1);
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 8);
+    }
+    for (int s = 0; s < kResStagesB; ++s) {
+      mbar_init(&b_full[s], 1);
+      mbar_init(&b_empty[s], 1);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ TMA producer
+      int32_t a_armed[2] = {-1, -1};
+      int32_t b_armed[kResStagesB];
+      for (int s = 0; s < kResStagesB; ++s) b_armed[s] = -1;
+      uint32_t stage = 0, phase = 0, a_use = 0;
+      int64_t last_bi = -1;
+      for (int64_t t = t_begin; t < t_end; ++t) {
+        int64_t bi, bj;
+        if (!decode_rowmajor<BN>(p, t, bi, bj)) continue;
+        if (bi != last_bi) {
+          const uint32_t ab = a_use & 1u;
+          if (!mbar_wait(&a_empty[ab], ((a_use >> 1) & 1u) ^ 1u, abort_flag, p.err)) break;
+          mbar_expect_tx(&a_full[ab], A_STAGE);
+          a_armed[ab] = (int32_t)((a_use >> 1) & 1u);
+          uint8_t* dst = abuf + ab * A_STAGE;
+          tma_load_2d(dst, &tA0, 0, (int)(bi * kBM), &a_full[ab]);
+          if (C::NOPS == 2) tma_load_2d(dst + A_BYTES, &tA1, 0, (int)(bi * kBM), &a_full[ab]);
+          last_bi = bi;
+          ++a_use;
+        }
+        if (!mbar_wait(&b_empty[stage], phase ^ 1u, abort_flag, p.err)) break;
+        mbar_expect_tx(&b_full[stage], B_STAGE);
+        b_armed[stage] = (int32_t)phase;
+        uint8_t* dst = bbuf + stage * B_STAGE;
+        tma_load_2d(dst, &tB0, 0, (int)(bj * BN), &b_full[stage]);
+        if (C::NOPS == 2) tma_load_2d(dst + B_BYTES, &tB1, 0, (int)(bj * BN), &b_full[stage]);
+        if (++stage == kResStagesB) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+      // drain: every armed copy lands before the CTA may exit
+      for (int b = 0; b < 2; ++b) {
+        if (a_armed[b] < 0) continue;
+        const uint64_t t0 = gtime();
+        while (!mbar_try(&a_full[b], (uint32_t)a_armed[b]) && gtime() - t0 < 100000000ull) {
+        }
+      }
+      for (int s = 0; s < kResStagesB; ++s) {
+        if (b_armed[s] < 0) continue;
+        const uint64_t t0 = gtime();
+        while (!mbar_try(&b_full[s], (uint32_t)b_armed[s]) && gtime() - t0 < 100000000ull) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ MMA issuer
+      const uint32_t id = idesc(BN);
+      uint32_t stage = 0, phase = 0, a_use = 0, ab_a = 0;
+      int64_t last_bi = -1, it = 0;
+      for (int64_t t = t_begin; t < t_end; ++t) {
+        int64_t bi, bj;
+        if (!decode_rowmajor<BN>(p, t, bi, bj)) continue;
+        if (bi != last_bi) {
+          if (last_bi >= 0) umma_commit(&a_empty[ab_a]);  // previous row's MMAs release its A buffer
+          ab_a = a_use & 1u;
+          if (!mbar_wait(&a_full[ab_a], (a_use >> 1) & 1u, abort_flag, p.err)) break;
+          last_bi = bi;
+          ++a_use;
+        }
+        const uint32_t ab = (uint32_t)(it & 1);
+        if (!mbar_wait(&acc_empty[ab], (uint32_t)((it >> 1) & 1) ^ 1u, abort_flag, p.err)) break;
+        if (!mbar_wait(&b_full[stage], phase, abort_flag, p.err)) break;
+        tc_fence_after();
+        const uint32_t d0 = tmem + ab * 256u, d1 = d0 + 128u;
+        const uint32_t sa = smem_u32(abuf + ab_a * A_STAGE), sb = smem_u32(bbuf + stage * B_STAGE);
+        // descriptors built once per tile; a 32-byte K step adds 2 to the start-address field
+        const uint64_t ad0 = sdesc_rb<RB>(sa), bd0 = sdesc_rb<RB>(sb);
+        const uint64_t al0 = sdesc_rb<RB>(sa + A_BYTES), bl0 = sdesc_rb<RB>(sb + B_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < RB / 32; ++kk) {
+          const uint32_t first = kk == 0 ? 0u : 1u;
+          umma<FMT>(d0, ad0 + 2 * kk, bd0 + 2 * kk, id, first);
+          if (C::NOPS == 2) {
+            umma<FMT>(d1, ad0 + 2 * kk, bl0 + 2 * kk, id, first);
+            umma<FMT>(d1, al0 + 2 * kk, bd0 + 2 * kk, id, 1u);
+          }
+        }
+        umma_commit(&b_empty[stage]);
+        umma_commit(&acc_full[ab]);
+        if (++stage == kResStagesB) {
+          stage = 0;
+          phase ^= 1u;
+        }
+        ++it;
+      }
+      umma_commit(drain);
+      const uint64_t t0 = gtime();
+      while (!mbar_try(drain, 0) && gtime() - t0 < 100000000ull) {
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue (8 warps)
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    int64_t it = 0;
+    for (int64_t t = t_begin; t < t_end; ++t) {
+      int64_t bi, bj;
+      if (!decode_rowmajor<BN>(p, t, bi, bj)) continue;
+      const uint32_t ab = (uint32_t)(it & 1);
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(&acc_full[ab], (uint32_t)((it >> 1) & 1), abort_flag, p.err) ? 1 : 0;
+      ok = __shfl_sync(kFull, ok, 0);
+      if (!ok) break;
+      tc_fence_after();
+      const int64_t i = bi * kBM + q * 32 + lane;
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + ab * 256u;
+      float row_norm = 1.f, fast_thresh = p.thresh;
+      if (FMT == OP_E4M3) {
+        row_norm = i < p.na ? p.a_norm[i] : 0.f;
+        if (p.thresh > 0.f)
+          fast_thresh = row_norm > 0.f ? p.thresh * row_norm * kNormLo / p.out_scale : __int_as_float(0x7f800000);
+        else
+          fast_thresh = -__int_as_float(0x7f800000);
+      }
+      // all of this warp's TMEM loads are issued before one wait, so they overlap
+      constexpr int CH = BN / 64;  // 32-column chunks per warp (half of the tile)
+      float v[CH][32];
+#pragma unroll
+      for (int c = 0; c < CH; ++c) tmem_ld32(trow + (half * CH + c) * 32, v[c]);
+      if (C::ACCS == 2) {
+        float x[CH][32];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) tmem_ld32(trow + 128 + (half * CH + c) * 32, x[c]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int e = 0; e < 32; ++e) v[c][e] = fmaf(x[c][e], 1.0f / kSplitLoScale, v[c][e]);
+      } else {
+        tmem_wait_ld();
+      }
+      // the accumulators are in registers: hand the TMEM buffer back before thresholding
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[ab]);
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int64_t j0 = bj * BN + (half * CH + c) * 32;
+        float m = v[c][0];
+#pragma unroll
+        for (int e = 1; e < 32; ++e) m = fmaxf(m, v[c][e]);
+        if (__any_sync(kFull, m >= fast_thresh)) {
+          // rare: stage the chunk in this warp's shared-memory slab and walk it compactly
+#pragma unroll
+          for (int e = 0; e < 32; ++e) stage[lane * 33 + e] = v[c][e];
+          __syncwarp();
+#pragma unroll 1
+          for (int e = 0; e < 32; ++e) {
+            const int64_t j = j0 + e;
+            float sc = stage[lane * 33 + e];
+            if (FMT == OP_E4M3) {
+              const float nn = row_norm * (j < p.nb ? p.b_norm[j] : 0.f);
+              sc = nn > 0.f ? sc * p.out_scale / nn : 0.f;
+            }
+            const bool hit = sc >= p.thresh && i < p.na && j < p.nb && (!p.triangle || j > i);
+            const unsigned bal = __ballot_sync(kFull, hit);
+            if (bal) {
+              unsigned long long base = 0;
+              if (lane == 0) base = atomicAdd(p.count, (unsigned long long)__popc(bal));
+              base = __shfl_sync(kFull, base, 0);
+              if (hit) {
+                const unsigned long long at = base + __popc(bal & ((1u << lane) - 1u));
+                if (at < (unsigned long long)p.capacity) {
+                  mrc_pair pr;
+                  pr.i = (int32_t)i;
+                  pr.j = (int32_t)j;
+                  pr.score = sc;
+                  p.pairs[at] = pr;
+                }
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+      ++it;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -444,20 +738,78 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D K-major operand map: rows x row_bytes, box = 128 bytes x box_rows, 128B swizzle, zero fill.
-bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t row_bytes, int box_rows, bool fp8) {
+// 2D K-major operand map: rows x row_bytes, box = box_bytes (64 or 128) x box_rows,
+// swizzle of the same width, zero fill out of bounds.
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t row_bytes, int box_rows, bool fp8,
+              int box_bytes = kRowBytes) {
   auto fn = encode_fn();
   if (!fn || rows <= 0) return false;
   const int eb = fp8 ? 1 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)(row_bytes / eb), (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
-  cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / eb), (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)(box_bytes / eb), (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  const CUresult r =
-      fn(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims,
-         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUtensorMapSwizzle sw = box_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  const CUresult r = fn(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                        const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+template <int FMT, int RB>
+cudaError_t run_gemm_resident(mrc_ctx* ctx, const GemmArgs& g) {
+  using C = Cfg<FMT>;
+  constexpr int BN = C::BN;
+  const bool fp8 = FMT == OP_E4M3;
+  CUtensorMap tA0, tA1, tB0, tB1;
+  if (!make_map(&tA0, g.a_hi, g.na, g.kbytes, kBM, fp8, RB) || !make_map(&tB0, g.b_hi, g.nb, g.kbytes, BN, fp8, RB))
+    return cudaErrorInvalidValue;
+  if (C::NOPS == 2) {
+    if (!make_map(&tA1, g.a_lo, g.na, g.kbytes, kBM, fp8, RB) || !make_map(&tB1, g.b_lo, g.nb, g.kbytes, BN, fp8, RB))
+      return cudaErrorInvalidValue;
+  } else {
+    tA1 = tA0;
+    tB1 = tB0;
+  }
+  GemmParams p{};
+  p.na = g.na;
+  p.nb = g.nb;
+  p.kblocks = 1;
+  p.triangle = g.triangle;
+  p.tiles_m = (g.na + kBM - 1) / kBM;
+  p.tiles_n = (g.nb + BN - 1) / BN;
+  p.super_rows = (g.na + BN - 1) / BN;
+  p.n_tiles = g.triangle ? p.super_rows * (p.super_rows + 1) / 2 * (BN / kBM) : p.tiles_m * p.tiles_n;
+  if (p.n_tiles >= (1ll << 31) || p.super_rows * p.super_rows >= (1ll << 31)) return cudaErrorInvalidValue;
+  p.thresh = g.thresh;
+  p.out_scale = g.out_scale;
+  p.a_norm = g.a_norm;
+  p.b_norm = g.b_norm;
+  if (FMT == OP_E4M3 && (!g.a_norm || !g.b_norm)) return cudaErrorInvalidValue;
+  p.pairs = g.pairs;
+  p.count = g.count;
+  p.capacity = g.capacity;
+  p.err = g.err;
+  // at least 120 KB, so that one CTA (which owns all 512 TMEM columns) runs per SM
+  const size_t smem =
+      std::max<size_t>(1024 + 2 * (size_t)C::NOPS * kBM * RB + (size_t)kResStagesB * C::NOPS * BN * RB + 256 +
+                           8 * 32 * 33 * sizeof(float),
+                       120 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_resident<FMT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int64_t grid = ctx->num_sms;
+  if (p.n_tiles < grid) grid = p.n_tiles;
+  if (grid <= 0) return cudaSuccess;
+  const double k_elems = (double)g.kbytes / (fp8 ? 1.0 : 2.0);
+  const double pairs = g.triangle ? (double)g.na * (double)(g.na - 1) / 2.0 : (double)g.na * (double)g.nb;
+  const double flops = 2.0 * k_elems * pairs * (C::NOPS == 2 ? 3.0 : 1.0);
+  const char* name = FMT == OP_SPLIT16 ? "gemm_split16_thresh" : (FMT == OP_F16 ? "gemm_f16_thresh" : "gemm_e4m3_thresh");
+  const double bytes = (double)C::NOPS * (double)(g.na + (g.triangle ? 0 : g.nb)) * g.kbytes;
+  cudaEvent_t ev = nullptr;
+  timing_begin(ctx, name, bytes, flops, &ev);
+  k_gemm_resident<FMT, RB><<<(unsigned)grid, kResThreads, smem, ctx->stream>>>(tA0, tA1, tB0, tB1, p);
+  timing_end(ctx, ev);
+  return cudaGetLastError();
 }
 
 template <int FMT>
@@ -519,8 +871,21 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
 }  // namespace
 
 cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g) {
-  if (g.kbytes <= 0 || g.kbytes % kRowBytes != 0 || g.na <= 0 || g.nb <= 0) return cudaErrorInvalidValue;
+  if (g.na <= 0 || g.nb <= 0) return cudaErrorInvalidValue;
   if (g.na >= (1ll << 31) || g.nb >= (1ll << 31)) return cudaErrorInvalidValue;
+  if (!g.store && (g.kbytes == 64 || g.kbytes == 128)) {
+    // one K block: resident-A kernel
+    switch (g.fmt * 2 + (g.kbytes == 128 ? 1 : 0)) {
+      case OP_SPLIT16 * 2: return run_gemm_resident<OP_SPLIT16, 64>(ctx, g);
+      case OP_SPLIT16 * 2 + 1: return run_gemm_resident<OP_SPLIT16, 128>(ctx, g);
+      case OP_F16 * 2: return run_gemm_resident<OP_F16, 64>(ctx, g);
+      case OP_F16 * 2 + 1: return run_gemm_resident<OP_F16, 128>(ctx, g);
+      case OP_E4M3 * 2: return run_gemm_resident<OP_E4M3, 64>(ctx, g);
+      case OP_E4M3 * 2 + 1: return run_gemm_resident<OP_E4M3, 128>(ctx, g);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (g.kbytes <= 0 || g.kbytes % kRowBytes != 0) return cudaErrorInvalidValue;
   switch (g.fmt) {
     case OP_SPLIT16:
       return run_gemm<OP_SPLIT16>(ctx, g);

@@ -76,7 +76,6 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 }
 
 __device__ __forceinline__ unsigned long long to_fix(float x) { return __float2ull_rn(x * kFix); }
-__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 __device__ __forceinline__ bool table_insert(uint32_t* keys, uint32_t* cnts, int log2ts, uint32_t t) {
   const uint32_t mask = (1u << log2ts) - 1u;
@@ -153,13 +152,11 @@ __device__ __forceinline__ void chunk(const IngestParams& p, const uint32_t* key
       }
     }
     if (valid) {
+      // the term table holds idf (or 1 under count weighting; bfloat16-rounded idf in the
+      // precision form); c * idf is exact in FP32 for bfloat16 idf (c < 2^16)
       const int2 ti = __ldg(reinterpret_cast<const int2*>(p.tinfo) + key);
-      float w = (float)c * __int_as_float(ti.x);
-      float r = __int_as_float(ti.x);
-      if (p.bf16w) {
-        w = bf16_round(w);
-        r = bf16_round(r);
-      }
+      const float r = __int_as_float(ti.x);
+      const float w = (float)c * r;
       a.norm += to_fix(w * w);
       if (ti.y >= 0) atomicAdd(&num_q[ti.y], to_fix(w * r));
     }
@@ -167,7 +164,7 @@ __device__ __forceinline__ void chunk(const IngestParams& p, const uint32_t* key
   }
   // DENSE
   if (!valid) return;
-  const float w = (float)c * p.tinfo[key].idf;
+  const float w = p.dense.idf ? (float)c * __ldg(p.dense.idf + key) : (float)c;
   if (dense_phase == 0) {
     a.norm += to_fix(w * w);
     return;

@@ -129,6 +129,7 @@ cudaError_t launch_signature(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, cons
 cudaError_t launch_pack(mrc_ctx* ctx, const float* sig, int64_t n, int32_t k, int32_t normalize, void* hi, void* lo,
                         void* e4m3, float* qnorm, float* unit, int32_t kp, int32_t kp8);
 struct DenseOut {
+  const float* idf;       // [vocab] FP32 idf under TF-IDF weighting, NULL for counts
   const int32_t* colmap;  // [vocab] head column, -2 tail term, -1 skipped
   int32_t kd;             // padded head width (elements)
   void* head_hi;          // [n*kd] fp16

@@ -131,13 +131,14 @@ class _Alias:
         for s in small:
             prob[s] = 1.0
         self.prob = prob
+        self.prob32 = prob.astype(np.float32)
         self.alias = alias
         self.n = n
 
     def draw(self, rng: np.random.Generator, size: int) -> np.ndarray:
-        i = rng.integers(0, self.n, size=size)
-        u = rng.random(size)
-        return np.where(u < self.prob[i], i, self.alias[i])
+        i = rng.integers(0, self.n, size=size, dtype=np.int64)
+        u = rng.random(size, dtype=np.float32)
+        return np.where(u < self.prob32[i], i, self.alias[i])
 
 
 def _lengths(spec: CorpusSpec, rng: np.random.Generator, n: int) -> np.ndarray:
@@ -152,7 +153,7 @@ def _lengths(spec: CorpusSpec, rng: np.random.Generator, n: int) -> np.ndarray:
 
 def _draw_terms(rng, zipf: _Alias, perms: np.ndarray, topics: np.ndarray) -> np.ndarray:
     ranks = zipf.draw(rng, topics.shape[0])
-    return perms[topics, ranks].astype(np.int32)
+    return perms.reshape(-1)[topics.astype(np.int64) * perms.shape[1] + ranks]
 
 
 def make_corpus(spec: CorpusSpec | str, n_docs: int | None = None, seed: int | None = None) -> Corpus:
@@ -188,20 +189,21 @@ def make_corpus(spec: CorpusSpec | str, n_docs: int | None = None, seed: int | N
     T = int(offsets[-1])
     tokens = np.empty(T, dtype=np.int32)
 
-    # base documents, in chunks of about 2^25 tokens
-    chunk = 1 << 25
+    # base documents, in chunks of about 2^24 tokens: every token draws its topic from its
+    # document's mixture (inverse CDF over the mixture) and then its term from that topic
+    chunk = 1 << 24
+    cum = np.cumsum(theta, axis=1).astype(np.float32)
+    cum[:, -1] = 2.0  # every draw falls at or below the last topic
     d0 = 0
     while d0 < N:
-        d1 = int(np.searchsorted(offsets, offsets[d0] + chunk, side="right"))
-        d1 = max(d1 - 1, d0 + 1)
-        d1 = min(d1, N)
-        counts = rng.multinomial(lens[d0:d1], theta[d0:d1])  # [docs, topics]
-        topics = np.repeat(np.tile(np.arange(K, dtype=np.int64), d1 - d0), counts.ravel())
-        terms = _draw_terms(rng, zipf, perms, topics)
-        # topic blocks are contiguous within a document: shuffle inside each document
-        doc_of = np.repeat(np.arange(d0, d1, dtype=np.int64), lens[d0:d1])
-        order = np.lexsort((rng.random(terms.shape[0]), doc_of))
-        tokens[offsets[d0]:offsets[d1]] = terms[order]
+        d1 = int(np.searchsorted(offsets, offsets[d0] + chunk, side="right")) - 1
+        d1 = min(max(d1, d0 + 1), N)
+        ln = lens[d0:d1]
+        u = rng.random(int(offsets[d1] - offsets[d0]), dtype=np.float32)
+        topics = np.zeros(u.shape[0], dtype=np.int32)
+        for z in range(K - 1):
+            topics += u > np.repeat(cum[d0:d1, z], ln)
+        tokens[offsets[d0]:offsets[d1]] = _draw_terms(rng, zipf, perms, topics)
         d0 = d1
 
     edits = np.zeros(N, dtype=np.int32)

@@ -118,6 +118,20 @@ def pin_error_stats_by_hand(o: Oracle):
     assert abs(st["var"] - 1 / 24) < 1e-15 and abs(st["mse"] - 1 / 24) < 1e-15
 
 
+def pin_bf16_rounding_matches_library(o: Oracle):
+    """bfloat16 rounding (RNE after FP32) against torch's CPU float32 -> bfloat16 conversion."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(9))
+    xs = np.concatenate([rng.uniform(0.5, 20.0, 4000), rng.lognormal(0, 3, 4000),
+                         [1.0, 1.00390625, 1.005859375, 1.0078125, 2.0 ** -20, 3.0, 17.123456]])
+    want = torch.tensor(xs.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    got = np.array([o.round_bf16(x) for x in xs])
+    assert np.array_equal(got, want)
+    # ties go to even: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7
+    assert o.round_bf16(1.0 + 2.0 ** -8) == 1.0
+    assert o.round_bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+
+
 # ---------------------------------------------------------------- invariants of the definitions
 def pin_reference_doc_is_one_hot(o: Oracle):
     """A document made of exactly the terms of partition p has signature e_p

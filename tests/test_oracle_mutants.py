@@ -46,6 +46,8 @@ MUTANTS = {
                                "double c = orc_cos_dense(S + i * k, S + j * k, k);\n            if (c > tau)"),
     "hamming_pairs_strict": ("if (h <= hmax)", "if (h < hmax)"),
     "error_stats_signed": ("sa += fabs(e);", "sa += e;"),
+    "bf16_truncates": ("u += 0x7FFFu + ((u >> 16) & 1u);", "u += 0u;"),
+    "bf16_ties_away": ("u += 0x7FFFu + ((u >> 16) & 1u);", "u += 0x8000u;"),
 }
 
 
