@@ -197,6 +197,37 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
 mrc_status simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
                          int32_t hamming_max, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs);
 
+/*
+ * Batched queries, captured once as a CUDA graph (one graph launch per batch).
+ * The paper signatures each new page and compares it with the signature
+ * database (Section I, Section IV); a batch does that for up to max_docs new
+ * documents at once against every document of `index`: signature pass,
+ * tensor-core compare at a lowered threshold (tau - 2e-3 in the FP32 form, a
+ * proven bound; tau - margin in the reduced forms), FP32 rescoring. Pairs are
+ * (query position i in the batch, index document j).
+ *   mrc_batch_create : allocates the pipeline's device buffers (inputs, outputs,
+ *     workspace) and its own non-blocking stream, runs the pipeline once and
+ *     captures it. max_tokens bounds the tokens of one batch; capacity bounds
+ *     the pairs of one batch; tile_n is the compare tile width (0 = default,
+ *     128 or 256; see the autotuner). The batch keeps `index` (not owned).
+ *   mrc_batch_launch : asynchronous. Copies the batch's offsets/tokens (host or
+ *     device memory) into the pipeline, pads it to max_docs with empty documents
+ *     and launches the graph. At most one launch in flight per batch object; use
+ *     several objects to overlap batches on the device.
+ *   mrc_batch_poll   : 1 when the last launch has finished (or none is pending), else 0.
+ *   mrc_batch_wait   : waits for the last launch and copies min(total, capacity)
+ *     pairs to `pairs` (host or device); *n_pairs = total. MRC_ERR_CAPACITY when
+ *     the pairs (or the internal candidate list) overflowed.
+ */
+typedef struct mrc_batch mrc_batch;
+mrc_status mrc_batch_create(mrc_ctx* ctx, const mrc_index* index, int64_t max_docs, int64_t max_tokens, float tau,
+                            int64_t capacity, int32_t tile_n, mrc_batch** out);
+mrc_status mrc_batch_launch(mrc_batch* batch, const mrc_docs* docs);
+int32_t mrc_batch_poll(mrc_batch* batch);
+mrc_status mrc_batch_wait(mrc_batch* batch, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs);
+const char* mrc_batch_last_error(const mrc_batch* batch);
+void mrc_batch_free(mrc_batch* batch);
+
 /* Index introspection and export (for checks and persistence). Each output
  * pointer may be NULL to skip it; sizes follow mrc_index_info. */
 mrc_status mrc_index_get_info(const mrc_index* index, mrc_index_info* info);

@@ -1,0 +1,289 @@
+// batch.cu -- graph-captured query batches against a resident signature index.
+//
+// A batch pipeline compares new documents with every document of an index, the way
+// the method is meant to be served (each new page is signatured and compared with
+// the signature database, Section I / Section IV):
+//   signature pass (bag of terms, TF-IDF, cosine to each reference partition; unit
+//   signature and compare operands written directly) -> tensor-core compare of the
+//   batch against the whole index at a lowered threshold -> FP32 rescoring.
+// The whole pipeline is captured once into a CUDA graph on the batch's own stream, for
+// exactly max_docs documents; a batch of fewer documents is padded with empty ones
+// (zero signatures, which match nothing). Each batch is then one graph launch, after
+// the copies of its offsets and tokens.
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "device.cuh"
+#include "internal.h"
+
+using namespace mrc;
+
+struct mrc_batch {
+  mrc_ctx* ctx = nullptr;  // private context: its own stream and workspace
+  const mrc_index* index = nullptr;
+  int64_t max_docs = 0, max_tokens = 0, capacity = 0, cand_cap = 0;
+  float tau = 0.f;
+  int32_t tile_n = 0;
+  int64_t* d_offsets = nullptr;
+  int32_t* d_tokens = nullptr;
+  float* d_unit = nullptr;
+  void* d_op = nullptr;
+  float* d_qnorm = nullptr;
+  mrc_pair* d_cand = nullptr;
+  mrc_pair* d_pairs = nullptr;
+  unsigned long long* d_counts = nullptr;  // [0] pairs, [1] candidates
+  int32_t* d_err = nullptr;
+  unsigned long long* h_counts = nullptr;  // pinned: [0] pairs [1] candidates [2] error word
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+};
+
+namespace {
+
+constexpr float kF16Bound = 2e-3f;  // > max |fp16 cosine - cosine| of unit vectors
+
+__global__ void k_pad_offsets(int64_t* off, int64_t n, int64_t max_docs) {
+  const int64_t i = n + 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= max_docs) off[i] = off[n];
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// The stream-ordered work of one batch (captured into the graph).
+cudaError_t record(mrc_batch* b) {
+  mrc_ctx* ctx = b->ctx;
+  const mrc_index* x = b->index;
+  const int32_t prec = x->params.precision;
+  cudaError_t e = cudaMemsetAsync(b->d_counts, 0, 2 * sizeof(unsigned long long), ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int32_t), ctx->stream);
+  if (e != cudaSuccess) return e;
+  DocsDev d{};
+  d.n_docs = b->max_docs;
+  d.offsets = b->d_offsets;
+  d.tokens = b->d_tokens;
+  d.n_tokens = b->max_tokens;
+  d.err = b->d_err;
+  SigOut o{};
+  o.sig_unit = b->d_unit;
+  if (prec == MRC_PREC_BF16_FP8) {
+    o.op_e4m3 = b->d_op;
+    o.qnorm = b->d_qnorm;
+    o.kp8 = x->kp8;
+  } else {
+    o.op_hi = b->d_op;
+    o.kp = x->kp;
+  }
+  e = launch_signature(ctx, d, x->vocab, x->tinfo, x->rinv, x->k, 0, x->params.seed, o);
+  if (e != cudaSuccess) return e;
+  GemmArgs g{};
+  g.na = b->max_docs;
+  g.nb = x->n_docs;
+  g.triangle = 0;
+  g.err = b->d_err;
+  g.out_scale = 1.0f;
+  g.tile_n = b->tile_n;
+  g.fmt = prec == MRC_PREC_BF16_FP8 ? OP_E4M3 : OP_F16;
+  g.a_hi = b->d_op;
+  g.b_hi = prec == MRC_PREC_BF16_FP8 ? x->op_e4m3 : x->op_hi;
+  g.kbytes = prec == MRC_PREC_BF16_FP8 ? x->kp8 : x->kp * 2;
+  if (prec == MRC_PREC_BF16_FP8) {
+    g.out_scale = 1.0f / (kE4M3Scale * kE4M3Scale);
+    g.a_norm = b->d_qnorm;
+    g.b_norm = x->qnorm;
+  }
+  g.thresh = b->tau - (prec == MRC_PREC_FP32 ? kF16Bound : x->params.margin);
+  g.pairs = b->d_cand;
+  g.count = b->d_counts + 1;
+  g.capacity = b->cand_cap;
+  e = launch_gemm_compare(ctx, g);
+  if (e != cudaSuccess) return e;
+  return launch_rescore(ctx, b->d_cand, b->d_counts + 1, b->cand_cap, b->d_unit, x->sig_unit, x->k, b->tau,
+                        b->d_pairs, b->d_counts, b->capacity);
+}
+
+void release(mrc_batch* b) {
+  if (!b) return;
+  if (b->ctx) cudaStreamSynchronize(b->ctx->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->done) cudaEventDestroy(b->done);
+  void* ptrs[] = {b->d_offsets, b->d_tokens, b->d_unit, b->d_op, b->d_qnorm, b->d_cand, b->d_pairs, b->d_counts,
+                  b->d_err};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (b->h_counts) cudaFreeHost(b->h_counts);
+  if (b->ctx) {
+    cudaStream_t s = b->ctx->stream;
+    mrc_ctx_destroy(b->ctx);
+    cudaStreamDestroy(s);
+  }
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+mrc_status mrc_batch_create(mrc_ctx* ctx, const mrc_index* index, int64_t max_docs, int64_t max_tokens, float tau,
+                            int64_t capacity, int32_t tile_n, mrc_batch** out) {
+  if (!ctx || !index || !out) return MRC_ERR_INVALID;
+  *out = nullptr;
+  if (max_docs < 1 || max_docs > (1 << 24) || max_tokens < 1 || capacity < 1)
+    return fail(ctx, MRC_ERR_INVALID, "mrc_batch_create: max_docs in [1, 2^24], max_tokens and capacity >= 1");
+  if (tile_n != 0 && tile_n != 128 && tile_n != 256)
+    return fail(ctx, MRC_ERR_INVALID, "mrc_batch_create: tile_n must be 0, 128 or 256");
+  cudaSetDevice(ctx->device);
+  mrc_batch* b = new mrc_batch();
+  b->index = index;
+  b->max_docs = max_docs;
+  b->max_tokens = max_tokens;
+  b->capacity = capacity;
+  b->cand_cap = std::max<int64_t>(4 * capacity, 1 << 16);
+  b->tau = tau;
+  b->tile_n = tile_n;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return cuda_fail(ctx, cudaGetLastError(), "creating the batch stream");
+  }
+  mrc_ctx* bc = nullptr;
+  if (mrc_ctx_create(s, &bc) != MRC_OK) {
+    cudaStreamDestroy(s);
+    delete b;
+    return fail(ctx, MRC_ERR_CUDA, "creating the batch context");
+  }
+  b->ctx = bc;
+  const int32_t prec = index->params.precision;
+  const size_t op_bytes = prec == MRC_PREC_BF16_FP8 ? (size_t)max_docs * index->kp8 : 2 * (size_t)max_docs * index->kp;
+  cudaError_t e = cudaMalloc(&b->d_offsets, sizeof(int64_t) * (size_t)(max_docs + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_tokens, sizeof(int32_t) * (size_t)max_tokens);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_unit, sizeof(float) * (size_t)max_docs * index->k);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_op, op_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_qnorm, sizeof(float) * (size_t)max_docs);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_cand, sizeof(mrc_pair) * (size_t)b->cand_cap);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_pairs, sizeof(mrc_pair) * (size_t)capacity);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_counts, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_offsets, 0, sizeof(int64_t) * (size_t)(max_docs + 1), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_op, 0, op_bytes, s);
+  if (e != cudaSuccess) {
+    mrc_status st = cuda_fail(ctx, e, "mrc_batch_create allocations");
+    release(b);
+    return st;
+  }
+  // one uncaptured run sizes every workspace buffer; then the same work is captured
+  e = record(b);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaGraph_t graph = nullptr;
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    const cudaError_t er = record(b);
+    e = cudaStreamEndCapture(s, &graph);
+    if (er != cudaSuccess) e = er;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    mrc_status st = cuda_fail(ctx, e, "capturing the batch pipeline");
+    release(b);
+    return st;
+  }
+  *out = b;
+  return MRC_OK;
+}
+
+mrc_status mrc_batch_launch(mrc_batch* b, const mrc_docs* docs) {
+  if (!b || !docs) return MRC_ERR_INVALID;
+  mrc_ctx* ctx = b->ctx;
+  cudaSetDevice(ctx->device);
+  if (b->pending) return fail(ctx, MRC_ERR_INVALID, "mrc_batch_launch: the previous launch was not waited for");
+  const int64_t n = docs->n_docs;
+  if (n < 0 || n > b->max_docs || (n > 0 && !docs->offsets))
+    return fail(ctx, MRC_ERR_INVALID, "mrc_batch_launch: n_docs outside [0, max_docs]");
+  const bool dev = n > 0 && on_device(docs->offsets);
+  int64_t T = 0;
+  cudaError_t e = cudaSuccess;
+  if (n > 0) {
+    if (dev)
+      e = cudaMemcpy(&T, docs->offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost);
+    else
+      T = docs->offsets[n];
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reading offsets[n_docs]");
+    if (T < 0 || T > b->max_tokens) return fail(ctx, MRC_ERR_INVALID, "mrc_batch_launch: more tokens than max_tokens");
+    e = cudaMemcpyAsync(b->d_offsets, docs->offsets, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyDefault,
+                        ctx->stream);
+    if (e == cudaSuccess && T > 0)
+      e = cudaMemcpyAsync(b->d_tokens, docs->tokens, sizeof(int32_t) * (size_t)T, cudaMemcpyDefault, ctx->stream);
+  } else {
+    e = cudaMemsetAsync(b->d_offsets, 0, sizeof(int64_t), ctx->stream);
+  }
+  if (e == cudaSuccess && n < b->max_docs) {
+    const int64_t m = b->max_docs - n;
+    k_pad_offsets<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(b->d_offsets, n, b->max_docs);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->h_counts, b->d_counts, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->h_counts + 2, b->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b->done, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "mrc_batch_launch");
+  b->pending = true;
+  return MRC_OK;
+}
+
+int32_t mrc_batch_poll(mrc_batch* b) {
+  if (!b || !b->pending) return 1;
+  const cudaError_t e = cudaEventQuery(b->done);
+  if (e == cudaErrorNotReady) {
+    cudaGetLastError();
+    return 0;
+  }
+  return 1;
+}
+
+mrc_status mrc_batch_wait(mrc_batch* b, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs) {
+  if (!b) return MRC_ERR_INVALID;
+  mrc_ctx* ctx = b->ctx;
+  if (n_pairs) *n_pairs = 0;
+  if (!b->pending) return fail(ctx, MRC_ERR_INVALID, "mrc_batch_wait: nothing launched");
+  cudaError_t e = cudaEventSynchronize(b->done);
+  b->pending = false;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "mrc_batch_wait");
+  const int64_t total = (int64_t)b->h_counts[0];
+  const int64_t cand = (int64_t)b->h_counts[1];
+  int32_t err = 0;
+  std::memcpy(&err, b->h_counts + 2, sizeof(int32_t));
+  if (err & kErrTimeout) return fail(ctx, MRC_ERR_TIMEOUT, "a bounded device wait expired");
+  if (err & kErrBadToken) return fail(ctx, MRC_ERR_INVALID, "a token id is outside [0, vocab)");
+  if (err & kErrBadOffsets) return fail(ctx, MRC_ERR_INVALID, "offsets must start at 0 and be non-decreasing");
+  if (err & kErrTooLong) return fail(ctx, MRC_ERR_UNSUPPORTED, "a document is longer than MRC_MAX_DOC_TOKENS tokens");
+  if (n_pairs) *n_pairs = total;
+  if (cand > b->cand_cap)
+    return fail(ctx, MRC_ERR_CAPACITY, "candidate list overflowed: create the batch with a larger capacity");
+  const int64_t m = std::min<int64_t>(std::min<int64_t>(total, b->capacity), capacity);
+  if (m > 0 && pairs) {
+    e = cudaMemcpy(pairs, b->d_pairs, sizeof(mrc_pair) * (size_t)m, cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copying batch pairs");
+  }
+  if (total > std::min(capacity, b->capacity))
+    return fail(ctx, MRC_ERR_CAPACITY, "more pairs than capacity; *n_pairs holds the total");
+  return MRC_OK;
+}
+
+const char* mrc_batch_last_error(const mrc_batch* b) { return b ? b->ctx->last_error.c_str() : "no batch"; }
+
+void mrc_batch_free(mrc_batch* b) { release(b); }
+
+}  // extern "C"

@@ -481,12 +481,12 @@ __device__ __forceinline__ bool decode_rowmajor(const GemmParams& p, int64_t t64
   return bi * kBM < p.na;
 }
 
-template <int FMT, int RB>
+template <int FMT, int RB, int BN>
 __global__ void __launch_bounds__(kResThreads, 1)
     k_gemm_resident(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
                     const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1, GemmParams p) {
   using C = Cfg<FMT>;
-  constexpr int BN = C::BN;
+  static_assert(C::ACCS * BN * 2 <= 512, "two accumulator buffers must fit in TMEM");
   constexpr uint32_t A_BYTES = kBM * RB, B_BYTES = BN * RB;
   constexpr uint32_t A_STAGE = C::NOPS * A_BYTES, B_STAGE = C::NOPS * B_BYTES;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -756,10 +756,9 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t row_bytes,
   return r == CUDA_SUCCESS;
 }
 
-template <int FMT, int RB>
+template <int FMT, int RB, int BN>
 cudaError_t run_gemm_resident(mrc_ctx* ctx, const GemmArgs& g) {
   using C = Cfg<FMT>;
-  constexpr int BN = C::BN;
   const bool fp8 = FMT == OP_E4M3;
   CUtensorMap tA0, tA1, tB0, tB1;
   if (!make_map(&tA0, g.a_hi, g.na, g.kbytes, kBM, fp8, RB) || !make_map(&tB0, g.b_hi, g.nb, g.kbytes, BN, fp8, RB))
@@ -795,7 +794,8 @@ cudaError_t run_gemm_resident(mrc_ctx* ctx, const GemmArgs& g) {
       std::max<size_t>(1024 + 2 * (size_t)C::NOPS * kBM * RB + (size_t)kResStagesB * C::NOPS * BN * RB + 256 +
                            8 * 32 * 33 * sizeof(float),
                        120 * 1024);
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_resident<FMT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_gemm_resident<FMT, RB, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int64_t grid = ctx->num_sms;
   if (p.n_tiles < grid) grid = p.n_tiles;
@@ -807,7 +807,7 @@ cudaError_t run_gemm_resident(mrc_ctx* ctx, const GemmArgs& g) {
   const double bytes = (double)C::NOPS * (double)(g.na + (g.triangle ? 0 : g.nb)) * g.kbytes;
   cudaEvent_t ev = nullptr;
   timing_begin(ctx, name, bytes, flops, &ev);
-  k_gemm_resident<FMT, RB><<<(unsigned)grid, kResThreads, smem, ctx->stream>>>(tA0, tA1, tB0, tB1, p);
+  k_gemm_resident<FMT, RB, BN><<<(unsigned)grid, kResThreads, smem, ctx->stream>>>(tA0, tA1, tB0, tB1, p);
   timing_end(ctx, ev);
   return cudaGetLastError();
 }
@@ -875,13 +875,19 @@ cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g) {
   if (g.na >= (1ll << 31) || g.nb >= (1ll << 31)) return cudaErrorInvalidValue;
   if (!g.store && (g.kbytes == 64 || g.kbytes == 128)) {
     // one K block: resident-A kernel
-    switch (g.fmt * 2 + (g.kbytes == 128 ? 1 : 0)) {
-      case OP_SPLIT16 * 2: return run_gemm_resident<OP_SPLIT16, 64>(ctx, g);
-      case OP_SPLIT16 * 2 + 1: return run_gemm_resident<OP_SPLIT16, 128>(ctx, g);
-      case OP_F16 * 2: return run_gemm_resident<OP_F16, 64>(ctx, g);
-      case OP_F16 * 2 + 1: return run_gemm_resident<OP_F16, 128>(ctx, g);
-      case OP_E4M3 * 2: return run_gemm_resident<OP_E4M3, 64>(ctx, g);
-      case OP_E4M3 * 2 + 1: return run_gemm_resident<OP_E4M3, 128>(ctx, g);
+    // tile width: 256 columns by default for single-accumulator formats, 128 on request
+    const int wide = (g.fmt != OP_SPLIT16 && g.tile_n != 128) ? 1 : 0;
+    switch ((g.fmt * 2 + (g.kbytes == 128 ? 1 : 0)) * 2 + wide) {
+      case (OP_SPLIT16 * 2) * 2: return run_gemm_resident<OP_SPLIT16, 64, 128>(ctx, g);
+      case (OP_SPLIT16 * 2 + 1) * 2: return run_gemm_resident<OP_SPLIT16, 128, 128>(ctx, g);
+      case (OP_F16 * 2) * 2: return run_gemm_resident<OP_F16, 64, 128>(ctx, g);
+      case (OP_F16 * 2) * 2 + 1: return run_gemm_resident<OP_F16, 64, 256>(ctx, g);
+      case (OP_F16 * 2 + 1) * 2: return run_gemm_resident<OP_F16, 128, 128>(ctx, g);
+      case (OP_F16 * 2 + 1) * 2 + 1: return run_gemm_resident<OP_F16, 128, 256>(ctx, g);
+      case (OP_E4M3 * 2) * 2: return run_gemm_resident<OP_E4M3, 64, 128>(ctx, g);
+      case (OP_E4M3 * 2) * 2 + 1: return run_gemm_resident<OP_E4M3, 64, 256>(ctx, g);
+      case (OP_E4M3 * 2 + 1) * 2: return run_gemm_resident<OP_E4M3, 128, 128>(ctx, g);
+      case (OP_E4M3 * 2 + 1) * 2 + 1: return run_gemm_resident<OP_E4M3, 128, 256>(ctx, g);
       default: return cudaErrorInvalidValue;
     }
   }

@@ -192,20 +192,24 @@ __device__ __forceinline__ void chunk(const IngestParams& p, const uint32_t* key
 __device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsigned long long norm_q,
                              const unsigned long long* num_q, uint32_t plo, uint32_t phi, int lane) {
   const float nrm = sqrtf((float)norm_q * kInvFix);
-  float tt = 0.f;
+  // raw signature s_p = t_p / |d|, t_p = num_p / |R_p|; the unit signature is s / |s|,
+  // computed exactly as the packing of stored raw signatures computes it
+  float ss = 0.f;
   for (int q = lane; q < p.k; q += 32) {
     const float t = (float)num_q[q] * kInvFix * p.rinv[q];
-    tt += t * t;
+    const float sv = nrm > 0.f ? t / nrm : 0.f;
+    ss += sv * sv;
   }
-  tt = warp_sum(tt);
-  const float tn = sqrtf(tt);
+  ss = warp_sum(ss);
+  const float sn = sqrtf(ss);
   const int width = max(p.k, max(p.sig.kp, p.sig.kp8));
   float q2 = 0.f;  // squared norm of the E4M3-quantized unit signature
   for (int q = lane; q < width; q += 32) {
     const float t = q < p.k ? (float)num_q[q] * kInvFix * p.rinv[q] : 0.f;
-    const float u = tn > 0.f ? t / tn : 0.f;
+    const float sv = nrm > 0.f ? t / nrm : 0.f;
+    const float u = (q < p.k && sn > 0.f) ? sv / sn : 0.f;
     if (q < p.k) {
-      if (p.sig.sig) p.sig.sig[d * p.k + q] = nrm > 0.f ? t / nrm : 0.f;
+      if (p.sig.sig) p.sig.sig[d * p.k + q] = sv;
       if (p.sig.sig_unit) p.sig.sig_unit[d * p.k + q] = u;
     }
     if (q < p.sig.kp && p.sig.op_hi) {

@@ -165,6 +165,7 @@ struct GemmArgs {
   int64_t capacity;
   float* store;         // non-null: write the score tile to store[i * ld + j] instead of thresholding
   int64_t ld;
+  int32_t tile_n;       // compare tile width for small K: 128, 256 or 0 (default)
   int32_t* err;         // device error word
 };
 cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g);

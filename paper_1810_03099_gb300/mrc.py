@@ -77,6 +77,13 @@ _SIGNATURES = {
     "mrc_ctx_kernel_stat": (C.c_int32, [C.c_void_p, C.c_int32, C.c_char_p, C.POINTER(C.c_int64),
                                         C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mrc_ctx_reset_stats": (None, [C.c_void_p]),
+    "mrc_batch_create": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_float, C.c_int64, C.c_int32,
+                                     C.POINTER(C.c_void_p)]),
+    "mrc_batch_launch": (C.c_int32, [C.c_void_p, C.POINTER(Docs)]),
+    "mrc_batch_poll": (C.c_int32, [C.c_void_p]),
+    "mrc_batch_wait": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "mrc_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "mrc_batch_free": (None, [C.c_void_p]),
 }
 
 _LIB = None
@@ -211,6 +218,54 @@ class Index:
     def free(self):
         if self.handle:
             self.ctx.lib.mrc_index_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+class Batch:
+    """A graph-captured query pipeline (mrc_batch_*): up to max_docs new documents per launch,
+    compared against every document of `index`."""
+
+    def __init__(self, ctx: Context, index: Index, max_docs: int, max_tokens: int, tau: float = 0.9,
+                 capacity: int = 1 << 18, tile_n: int = 0):
+        self.ctx, self.index = ctx, index
+        self.max_docs, self.max_tokens, self.capacity, self.tile_n = max_docs, max_tokens, capacity, tile_n
+        h = C.c_void_p()
+        ctx.check(ctx.lib.mrc_batch_create(ctx.handle, index.handle, int(max_docs), int(max_tokens), float(tau),
+                                           int(capacity), int(tile_n), C.byref(h)))
+        self.handle = h
+        self._keep = None
+
+    def _check(self, st):
+        if st != MRC_OK:
+            raise MrcError(st, self.ctx.lib.mrc_batch_last_error(self.handle).decode())
+
+    def launch(self, offsets, tokens):
+        """Asynchronous: copy the batch in (host or device buffers) and launch the graph."""
+        d = _docs(offsets, tokens)
+        self._keep = (offsets, tokens)  # the copies are stream-ordered: keep the inputs alive
+        self._check(self.ctx.lib.mrc_batch_launch(self.handle, C.byref(d)))
+
+    def poll(self) -> bool:
+        return bool(self.ctx.lib.mrc_batch_poll(self.handle))
+
+    def wait(self, out=None):
+        """Wait for the last launch; returns (pairs as a structured numpy array, total)."""
+        buf = out if out is not None else np.empty(self.capacity, PAIR_DTYPE)
+        total = C.c_int64()
+        st = self.ctx.lib.mrc_batch_wait(self.handle, _ptr(buf), int(buf.shape[0]), C.byref(total))
+        self._keep = None
+        self._check(st)
+        return buf[:min(int(total.value), buf.shape[0])], int(total.value)
+
+    def free(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.mrc_batch_free(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -1,0 +1,123 @@
+"""Continuous-batching server over a device-resident signature index (the serving form).
+
+New documents arrive one by one (Poisson arrivals in the benchmark). A single
+host loop
+  * admits arrived requests into a queue;
+  * dispatches a micro-batch (up to ``micro_batch`` documents, or whatever has
+    waited ``deadline_s``) to any free pipeline slot: each slot is a
+    graph-captured ``mrc_batch`` with its own stream, so batches launched while
+    others are still on the GPU overlap on the device;
+  * completes slots as their GPU work finishes (non-blocking polls) and stamps
+    every request's latency (completion minus arrival).
+The number of slots is admitted against free HBM at start-up: a slot is only
+created while its device footprint fits in ``hbm_fraction`` of the free memory.
+Each document's result does not depend on the other documents of its batch
+(per-document signature pass, per-pair compare and rescoring), so a request's
+pairs are the same alone and in the mix.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import mrc
+
+
+@dataclass
+class Request:
+    rid: int
+    tokens: np.ndarray
+    arrival: float
+    done: float = -1.0
+    pairs: list = field(default_factory=list)
+
+
+def slot_footprint(index, max_docs: int, max_tokens: int, capacity: int) -> int:
+    """Device bytes of one pipeline slot (inputs, operands, candidates, pairs, workspace)."""
+    k = index.k
+    op = max_docs * (64 if k <= 64 else k) * 2
+    cand = max(4 * capacity, 1 << 16) * 12
+    ws = max_docs * 8 * 4 + 64 * 1024
+    return 8 * (max_docs + 1) + 4 * max_tokens + 4 * max_docs * k + op + 4 * max_docs + cand + 12 * capacity + ws
+
+
+class Server:
+    def __init__(self, ctx, index, tau: float = 0.9, micro_batch: int = 128, deadline_s: float = 1e-3,
+                 slots: int = 4, max_doc_tokens: int = 10000, capacity: int = 1 << 16, hbm_fraction: float = 0.5,
+                 tile_n: int = 0, free_bytes: int | None = None):
+        import torch
+        self.ctx, self.index, self.tau = ctx, index, tau
+        self.micro_batch, self.deadline_s = micro_batch, deadline_s
+        self.max_tokens = micro_batch * max_doc_tokens
+        self.capacity = capacity
+        free = torch.cuda.mem_get_info()[0] if free_bytes is None else free_bytes
+        foot = slot_footprint(index, micro_batch, self.max_tokens, capacity)
+        self.admitted_slots = int(max(0, min(slots, (hbm_fraction * free) // foot)))
+        if self.admitted_slots < 1:
+            raise MemoryError("not enough free device memory for one pipeline slot")
+        self.slots = [mrc.Batch(ctx, index, micro_batch, self.max_tokens, tau, capacity, tile_n)
+                      for _ in range(self.admitted_slots)]
+        self.busy: list[list[Request] | None] = [None] * len(self.slots)
+        # pinned staging per slot (stream-ordered copies read them until the batch finishes)
+        self.h_off = [torch.empty(micro_batch + 1, dtype=torch.int64).pin_memory() for _ in self.slots]
+        self.h_tok = [torch.empty(self.max_tokens, dtype=torch.int32).pin_memory() for _ in self.slots]
+
+    def _launch(self, s: int, reqs: list[Request]):
+        lens = np.array([r.tokens.shape[0] for r in reqs], np.int64)
+        off = self.h_off[s].numpy()[:len(reqs) + 1]
+        off[0] = 0
+        np.cumsum(lens, out=off[1:])
+        tok = self.h_tok[s].numpy()
+        if off[-1]:
+            tok[:off[-1]] = np.concatenate([r.tokens for r in reqs])
+        self.slots[s].launch(self.h_off[s][:len(reqs) + 1], self.h_tok[s][:int(off[-1])])
+        self.busy[s] = reqs
+
+    def _complete(self, s: int, now: float):
+        pairs, _ = self.slots[s].wait()
+        reqs = self.busy[s]
+        for r in reqs:
+            r.done = now
+        for i, j, sc in zip(pairs["i"].tolist(), pairs["j"].tolist(), pairs["score"].tolist()):
+            reqs[i].pairs.append((j, sc))
+        self.busy[s] = None
+
+    def run(self, docs: list[np.ndarray], arrivals: np.ndarray) -> list[Request]:
+        """Serve documents arriving at the given times (seconds from start); returns the requests."""
+        reqs = [Request(i, d, float(a)) for i, (d, a) in enumerate(zip(docs, arrivals))]
+        queue: list[Request] = []
+        nxt = 0
+        finished = 0
+        t0 = time.perf_counter()
+        while finished < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and reqs[nxt].arrival <= now:
+                queue.append(reqs[nxt])
+                nxt += 1
+            for s in range(len(self.slots)):
+                if self.busy[s] is not None and self.slots[s].poll():
+                    n = len(self.busy[s])
+                    self._complete(s, time.perf_counter() - t0)
+                    finished += n
+            if queue:
+                due = len(queue) >= self.micro_batch or (now - queue[0].arrival) >= self.deadline_s or nxt == len(reqs)
+                if due:
+                    for s in range(len(self.slots)):
+                        if self.busy[s] is None and queue:
+                            take, queue = queue[:self.micro_batch], queue[self.micro_batch:]
+                            self._launch(s, take)
+        self.wall_s = time.perf_counter() - t0
+        return reqs
+
+    def free(self):
+        for b in self.slots:
+            b.free()
+
+
+def latency_report(reqs: list[Request], wall_s: float) -> dict:
+    lat = np.array([r.done - r.arrival for r in reqs])
+    return {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3),
+            "docs_per_s": len(reqs) / wall_s}

@@ -1,0 +1,129 @@
+"""Batching and serving forms, through the C ABI.
+
+* A graph-captured batch gives the pair set of the oracle (query x index, FP32 form:
+  equal except within 1e-5 of tau) and exactly what the eager path (mrc_signature then
+  mrc_match) gives, padded or not, with either compare tile width.
+* A served request's pairs are bit-identical alone and in the mix of a continuous batch.
+* Admission by free device memory: a fake low free-memory figure admits fewer slots.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle, Params, build_index, signature
+from paper_1810_03099_gb300 import synth
+from tests.gpu_common import cuda_or_skip, pair_dict
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = cuda_or_skip()
+    from paper_1810_03099_gb300 import mrc
+    c = synth.make_corpus(synth.SPECS["tiny"].with_(n_docs=3000))
+    ctx = mrc.Context()
+    orc = Oracle()
+    yield {"torch": torch, "mrc": mrc, "c": c, "ctx": ctx, "orc": orc}
+    ctx.close()
+
+
+def _queries(c, n, seed):
+    q = synth.make_corpus(synth.SPECS["tiny"].with_(n_docs=n, vocab=c.vocab, seed=seed, dup_frac=0.0))
+    # half of the queries are copies (with edits) of index documents, so that matches exist
+    rng = np.random.Generator(np.random.PCG64(seed))
+    docs = [q.doc(i).copy() for i in range(n)]
+    for i in range(0, n, 2):
+        src = c.doc(int(rng.integers(0, c.n_docs))).copy()
+        if src.size > 4:
+            src[rng.integers(0, src.size)] = int(rng.integers(0, c.vocab))
+        docs[i] = src
+    offs = np.zeros(n + 1, np.int64)
+    offs[1:] = np.cumsum([d.size for d in docs])
+    return offs, np.concatenate(docs).astype(np.int32)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_matches_oracle_and_eager(env, precision):
+    mrc, ctx, c, orc, torch = env["mrc"], env["ctx"], env["c"], env["orc"], env["torch"]
+    p = Params(k=32, bf16=precision == 1)
+    ref = build_index(c.offsets, c.tokens, c.vocab, p, orc)
+    idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, mrc.params_default(k=32, precision=precision))
+    qo, qt = _queries(c, 100, 5)
+    tau = 0.9
+    # eager path
+    sig, _ = mrc.mrc_signature(ctx, idx, qo, qt)
+    eager = mrc.pairs_to_numpy(mrc.mrc_match(ctx, idx, sig, tau, device=None)[0])
+    eset = sorted(eager.tolist())
+    Sq, _, _ = signature(ref, qo, qt, orc)
+    tot, pi, pj, ps = orc.sig_match(Sq, ref.S, tau)
+    od = pair_dict(pi, pj, ps)
+    assert tot > 20
+    for max_docs, tile in ((100, 0), (128, 128), (256, 256)):
+        b = mrc.Batch(ctx, idx, max_docs, 200000, tau, capacity=1 << 16, tile_n=tile)
+        for _ in range(2):  # replays are repeatable
+            b.launch(qo, qt)
+            got, total = b.wait()
+            assert total == got.shape[0]
+            assert sorted(got.tolist()) == eset
+        b.free()
+    gd = pair_dict(eager["i"], eager["j"], eager["score"])
+    for pr, sc in gd.items():
+        o = od.get(pr, orc.cos_dense(Sq[pr[0]], ref.S[pr[1]]))
+        assert o >= tau - 1e-5 and abs(sc - o) <= 1e-5
+    missed = [pr for pr, o in od.items() if pr not in gd and o > tau + 1e-5]
+    assert len(missed) <= (0 if precision == 0 else 0.01 * len(od))
+    idx.free()
+
+
+def test_batch_runner_buckets_and_autotune(env, tmp_path):
+    mrc, ctx, c = env["mrc"], env["ctx"], env["c"]
+    from paper_1810_03099_gb300 import batching
+    idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, mrc.params_default(k=32))
+    qo, qt = _queries(c, 300, 9)
+    batches = batching.make_batches(qo, qt, [1, 7, 64, 200, 33], seed=3)
+    tn = batching.autotune_tile(ctx, idx, 64, 64 * 5000, batches[2][:2], reps=2, cache=str(tmp_path / "t.json"))
+    assert tn in (128, 256)
+    assert batching.autotune_tile(ctx, idx, 64, 64 * 5000, batches[2][:2], cache=str(tmp_path / "t.json")) == tn
+    runner = batching.BatchRunner(ctx, idx, 0.9, max_docs=256, max_doc_tokens=5000, autotune=False)
+    for offs, toks, pick in batches:
+        got, total = runner.run(offs, toks)
+        sig, _ = mrc.mrc_signature(ctx, idx, offs, toks)
+        want = mrc.pairs_to_numpy(mrc.mrc_match(ctx, idx, sig, 0.9, device=None)[0])
+        assert sorted(got.tolist()) == sorted(want.tolist())
+    runner.free()
+    idx.free()
+
+
+def test_serving_alone_equals_mix(env):
+    mrc, ctx, c = env["mrc"], env["ctx"], env["c"]
+    from paper_1810_03099_gb300 import serving
+    idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, mrc.params_default(k=32))
+    qo, qt = _queries(c, 400, 13)
+    docs = [qt[qo[i]:qo[i + 1]] for i in range(400)]
+    arrivals = synth.poisson_arrivals(200000.0, 400, seed=21)
+    srv = serving.Server(ctx, idx, 0.9, micro_batch=32, deadline_s=2e-4, slots=3, max_doc_tokens=5000)
+    mixed = srv.run(docs, arrivals)
+    rep = serving.latency_report(mixed, srv.wall_s)
+    assert rep["requests"] == 400 and rep["p99_ms"] >= rep["p50_ms"] > 0
+    alone = serving.Server(ctx, idx, 0.9, micro_batch=1, deadline_s=0.0, slots=1, max_doc_tokens=5000)
+    single = alone.run(docs[:120], np.zeros(120))
+    for a, b in zip(mixed[:120], single):
+        assert sorted(a.pairs) == sorted(b.pairs)  # bit-identical scores
+    assert sum(len(r.pairs) for r in mixed) > 50
+    srv.free()
+    alone.free()
+    idx.free()
+
+
+def test_serving_admission_by_free_memory(env):
+    mrc, ctx, c = env["mrc"], env["ctx"], env["c"]
+    from paper_1810_03099_gb300 import serving
+    idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, mrc.params_default(k=32))
+    foot = serving.slot_footprint(idx, 32, 32 * 5000, 1 << 16)
+    s = serving.Server(ctx, idx, micro_batch=32, slots=8, max_doc_tokens=5000, hbm_fraction=1.0,
+                       free_bytes=3 * foot + 1)
+    assert s.admitted_slots == 3
+    s.free()
+    with pytest.raises(MemoryError):
+        serving.Server(ctx, idx, micro_batch=32, slots=8, max_doc_tokens=5000, hbm_fraction=1.0, free_bytes=foot - 1)
+    idx.free()
