@@ -151,6 +151,155 @@ def cpu_baseline_leg(c):
             "sample": f"first {n} of {N} documents, one pass; per-document time x N/n, all-pairs time x (N/n)^2"}
 
 
+def _timed(fn, reps=1):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1) / 1e3 / reps
+
+
+def form_precision(args):
+    """Precision form on the one-million-document corpus: bf16 weight table, FP8 E4M3 compare,
+    FP32 rescoring; against the FP32 form on the same corpus; error vs the FP64 oracle on a
+    seeded 10,000-document subset."""
+    import torch
+    from oracle.oracle import Oracle, Params, build_index
+    from paper_1810_03099_gb300 import mrc, synth
+    c = synth.make_corpus_device("precision")
+    ctx = mrc.Context()
+    res = {}
+    for name, prec in (("bf16_fp8", mrc.PREC_BF16_FP8), ("fp32", mrc.PREC_FP32)):
+        p = mrc.params_default(k=64, precision=prec)
+        build = lambda: mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, p)  # noqa: E731
+        idx, _ = _timed(build)
+        idx.free()
+        idx, t_build = _timed(build)
+        mrc.mrc_match(ctx, idx, None, TAU, capacity=1 << 24)
+        ctx.reset_stats()
+        ctx.set_timing(True)
+        (pairs, total), t_match = _timed(lambda: mrc.mrc_match(ctx, idx, None, TAU, capacity=1 << 24))
+        ctx.set_timing(False)
+        n = c.n_docs
+        res[name] = {"build_s": t_build, "match_s": t_match, "docs_per_s": n / (t_build + t_match),
+                     "pairs_per_s": n * (n - 1) / 2 / t_match, "pairs": total,
+                     "kernels_ms": {s["name"]: s["ms"] for s in ctx.kernel_stats()}}
+        idx.free()
+    # error vs FP64 on a subset (the index corpus is the subset)
+    sub = c.host_subset(np.sort(np.random.Generator(np.random.PCG64(7)).choice(c.n_docs, 10000, replace=False)))
+    orc = Oracle()
+    ref = build_index(sub.offsets, sub.tokens, c.vocab, Params(k=64), orc)
+    _, pi, pj, _ = orc.sig_pairs(ref.S, TAU)
+    want = set(zip(pi.tolist(), pj.tolist()))
+    idx = mrc.mrc_build_index(ctx, sub.offsets, sub.tokens, c.vocab, mrc.params_default(k=64, precision=1))
+    got = mrc.mrc_match(ctx, idx, None, TAU, device=None)[0]
+    have = set(zip(got["i"].tolist(), got["j"].tolist()))
+    ex = mrc.mrc_index_export(ctx, idx)
+    inter = len(have & want)
+    res["vs_fp64_subset"] = {"docs": 10000, "pairs_fp64": len(want), "pairs": len(have),
+                             "recall": inter / max(len(want), 1), "precision": inter / max(len(have), 1),
+                             "max_abs_sig_err": float(np.abs(ex["sig"] - ref.S).max())}
+    idx.free()
+    line = {"metric": "docs/s", "form": "precision", "value": res["bf16_fp8"]["docs_per_s"], "unit": "docs/s",
+            "vs_fp32_form": res["bf16_fp8"]["docs_per_s"] / res["fp32"]["docs_per_s"],
+            "config": {"workload": f"precision: {c.n_docs} docs, {c.n_tokens} tokens, V=2^18, k=64, all-pairs tau={TAU}"},
+            "detail": res}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def form_batching(args):
+    """Batching form: 4,096 batches of 1-512 documents (log-uniform 20-20,000 tokens) against the
+    one-million-document precision index, one graph launch per batch, autotuned tile width."""
+    import torch
+    from paper_1810_03099_gb300 import batching, mrc, synth
+    c = synth.make_corpus_device("precision")
+    ctx = mrc.Context()
+    idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, mrc.params_default(k=64, precision=1))
+    del c
+    torch.cuda.empty_cache()
+    sizes = synth.query_batch_sizes(args.batches)
+    q = synth.make_corpus_device(synth.SPECS["batch_queries"].with_(n_docs=int(sizes.sum())))
+    starts = np.concatenate([[0], np.cumsum(sizes)])
+    runner = batching.BatchRunner(ctx, idx, TAU, max_docs=512, max_doc_tokens=20000, capacity=1 << 18)
+    def batch(b):
+        s0, s1 = int(starts[b]), int(starts[b + 1])
+        o = q.offsets[s0:s1 + 1] - q.offsets[s0]
+        return o, q.tokens[q.offsets[s0]:q.offsets[s1]]
+    # capture (and tune) one pipeline per size bucket before timing
+    first = {}
+    for b, n in enumerate(sizes.tolist()):
+        first.setdefault(batching.bucket_of(int(n), 512), b)
+    runner.prepare([batch(b) for b in first.values()])
+    lat = []
+    total_pairs = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for b in range(len(sizes)):
+        o, t = batch(b)
+        tb = time.perf_counter()
+        _, tot = runner.run(o, t)
+        lat.append(time.perf_counter() - tb)
+        total_pairs += tot
+    wall = time.perf_counter() - t0
+    docs = int(sizes.sum())
+    line = {"metric": "docs/s", "form": "batching", "value": docs / wall, "unit": "docs/s",
+            "config": {"workload": f"{len(sizes)} batches of 1-512 docs ({docs} docs, {q.n_tokens} tokens), "
+                                   f"log-uniform 20-20,000 tokens, vs 1M-doc bf16/FP8 index, k=64, tau={TAU}"},
+            "batch_latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3)},
+            "pairs": total_pairs, "tiles": {str(k): v for k, v in runner.tiles.items()}}
+    print(json.dumps(line), flush=True)
+    runner.free()
+    idx.free()
+    ctx.close()
+
+
+def form_serving(args):
+    """Serving form: Poisson arrivals of new documents against a device-resident index of ten
+    million FP16 signatures (k = 64) plus their Simhashes; continuous batching over pipeline
+    slots admitted by free HBM; p50/p99 latency and sustained docs/s per arrival rate."""
+    import torch
+    from paper_1810_03099_gb300 import mrc, serving, synth
+    n_index = args.serving_docs
+    c = synth.make_corpus_device("serving", n_docs=n_index)
+    ctx = mrc.Context()
+    idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, mrc.params_default(k=64, precision=2))
+    n_tok = c.n_tokens
+    del c
+    torch.cuda.empty_cache()
+    pool = synth.make_corpus_device(synth.SPECS["precision"].with_(n_docs=20000, seed=BASE_QUERY_SEED))
+    pool = pool.host_subset(np.arange(20000))
+    docs = [pool.doc(i) for i in range(pool.n_docs)]
+    srv = serving.Server(ctx, idx, TAU, micro_batch=128, deadline_s=1e-3, slots=4, max_doc_tokens=10000,
+                         capacity=1 << 21)
+    srv.run(docs[:2000], np.zeros(2000))  # warm-up
+    rows = []
+    for rate in (10000, 50000, 100000, 250000, 500000):
+        n_req = int(min(20000, max(4000, rate * 0.5)))
+        arr = synth.poisson_arrivals(float(rate), n_req)
+        reqs = srv.run(docs[:n_req], arr)
+        rep = serving.latency_report(reqs, srv.wall_s)
+        rep["rate"] = rate
+        rep["pairs_per_request"] = float(np.mean([len(r.pairs) for r in reqs]))
+        rows.append(rep)
+    line = {"metric": "p99 latency ms / sustained docs/s", "form": "serving", "value": max(r["docs_per_s"] for r in rows),
+            "unit": "docs/s", "config": {"workload": f"index {n_index} docs ({n_tok} tokens) FP16 k=64; micro-batch <= 128 "
+                                                     f"or 1 ms; {srv.admitted_slots} slots"},
+            "rates": rows}
+    print(json.dumps(line), flush=True)
+    srv.free()
+    idx.free()
+    ctx.close()
+
+
+BASE_QUERY_SEED = 1810031999
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -158,7 +307,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mrc", choices=["mrc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="news20", choices=["news20", "precision", "batching", "serving", "forms"],
+                    help="news20 (default): the headline step; the others measure the three forms")
+    ap.add_argument("--batches", type=int, default=4096)
+    ap.add_argument("--serving-docs", type=int, default=10_000_000)
     args = ap.parse_args()
+    if args.form != "news20" and args.impl == "mrc":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        for f in (["precision", "batching", "serving"] if args.form == "forms" else [args.form]):
+            {"precision": form_precision, "batching": form_batching, "serving": form_serving}[f](args)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -216,15 +216,18 @@ mrc_status simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint
  *     several objects to overlap batches on the device.
  *   mrc_batch_poll   : 1 when the last launch has finished (or none is pending), else 0.
  *   mrc_batch_wait   : waits for the last launch and copies min(total, capacity)
- *     pairs to `pairs` (host or device); *n_pairs = total. MRC_ERR_CAPACITY when
- *     the pairs (or the internal candidate list) overflowed.
+ *     pairs to `pairs` (host or device), grouped by query position i (order
+ *     within a query unspecified); *n_pairs = total; query_offsets (may be NULL,
+ *     [n_docs + 1] of the last launch) receives where each query's pairs start.
+ *     MRC_ERR_CAPACITY when the pairs (or the internal candidate list) overflowed.
  */
 typedef struct mrc_batch mrc_batch;
 mrc_status mrc_batch_create(mrc_ctx* ctx, const mrc_index* index, int64_t max_docs, int64_t max_tokens, float tau,
                             int64_t capacity, int32_t tile_n, mrc_batch** out);
 mrc_status mrc_batch_launch(mrc_batch* batch, const mrc_docs* docs);
 int32_t mrc_batch_poll(mrc_batch* batch);
-mrc_status mrc_batch_wait(mrc_batch* batch, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs);
+mrc_status mrc_batch_wait(mrc_batch* batch, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs,
+                          int64_t* query_offsets);
 const char* mrc_batch_last_error(const mrc_batch* batch);
 void mrc_batch_free(mrc_batch* batch);
 

@@ -218,10 +218,10 @@ bool valid_params(const mrc_params* p, std::string* why) {
 
 int32_t round_up(int32_t x, int32_t m) { return (x + m - 1) / m * m; }
 
-// Padded operand rows: 64-byte rows (one 64B swizzle atom) when they fit, else multiples
-// of 128 bytes. kp counts fp16 elements, kp8 counts E4M3 bytes.
-int32_t padded_kp(int32_t k) { return k <= 32 ? 32 : round_up(k, 64); }
-int32_t padded_kp8(int32_t k) { return k <= 64 ? 64 : round_up(k, 128); }
+// Padded operand rows: multiples of 128 bytes (one 128B swizzle atom). kp counts fp16
+// elements, kp8 counts E4M3 bytes.
+int32_t padded_kp(int32_t k) { return round_up(k, 64); }
+int32_t padded_kp8(int32_t k) { return round_up(k, 128); }
 
 // Reference selection (Section IV): rank terms by df descending, ties by id;
 // zero-df terms dropped; REGION / ALL / DF1 pick the selection; partition p
@@ -286,8 +286,8 @@ mrc_status dev_alloc(mrc_ctx* ctx, T** p, size_t count, const char* what) {
 }
 
 void free_index_arrays(mrc_index* x) {
-  void* ptrs[] = {x->df,    x->idf,   x->tinfo, x->rinv,    x->sig,  x->sig_unit,
-                  x->simhash, x->op_hi, x->op_lo, x->op_e4m3, x->qnorm};
+  void* ptrs[] = {x->df,    x->idf,   x->tinfo,    x->rinv,  x->sig,       x->sig_unit,
+                  x->simhash, x->op_hi, x->op_lo, x->op_e4m3, x->qnorm, x->qnorm_min};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, x->stream);
 }
@@ -348,6 +348,7 @@ mrc_status alloc_signature_arrays(mrc_ctx* ctx, mrc_index* x) {
     if ((st = dev_alloc(ctx, &q, n * x->kp8, "e4m3 operands")) != MRC_OK) return st;
     x->op_e4m3 = q;
     if ((st = dev_alloc(ctx, &x->qnorm, n, "e4m3 row norms")) != MRC_OK) return st;
+    if ((st = dev_alloc(ctx, &x->qnorm_min, (n + 127) / 128, "e4m3 block norm minima")) != MRC_OK) return st;
   }
   return MRC_OK;
 }
@@ -526,6 +527,7 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   if (x->op_e4m3) cudaMemsetAsync(x->op_e4m3, 0, (size_t)x->n_docs * x->kp8, ctx->stream);
   e = launch_signature(ctx, d, vocab, x->tinfo, x->rinv, x->k, params->precision == MRC_PREC_BF16_FP8, params->seed,
                        index_sig_out(x));
+  if (e == cudaSuccess && x->qnorm_min) e = launch_block_min(ctx, x->qnorm, x->n_docs, x->qnorm_min);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "signature pass"));
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);
   *out = x;
@@ -621,6 +623,7 @@ mrc_status mrc_match(mrc_ctx* ctx, const mrc_index* index, const float* query_si
     g.out_scale = 1.0f / (kE4M3Scale * kE4M3Scale);
     g.a_norm = a_norm;
     g.b_norm = index->qnorm;
+    g.b_norm_min = index->qnorm_min;
   }
   g.thresh = tau - (prec == MRC_PREC_FP32 ? kF16CompareBound : index->params.margin);
   int64_t cand_cap = std::max<int64_t>(4 * capacity, 1 << 20);
@@ -968,6 +971,7 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
   if (x->op_e4m3) cudaMemsetAsync(x->op_e4m3, 0, n * x->kp8, ctx->stream);
   e = launch_pack(ctx, x->sig_unit, x->n_docs, x->k, 0, x->op_hi, x->op_lo, x->op_e4m3, x->qnorm, nullptr,
                   x->op_hi ? x->kp : 0, x->op_e4m3 ? x->kp8 : 0);
+  if (e == cudaSuccess && x->qnorm_min) e = launch_block_min(ctx, x->qnorm, x->n_docs, x->qnorm_min);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "index load packing"));
   *out = x;

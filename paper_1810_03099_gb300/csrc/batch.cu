@@ -32,17 +32,64 @@ struct mrc_batch {
   float* d_qnorm = nullptr;
   mrc_pair* d_cand = nullptr;
   mrc_pair* d_pairs = nullptr;
+  mrc_pair* d_grouped = nullptr;           // pairs grouped by query
+  int64_t* d_qoff = nullptr;               // [max_docs + 1] start of each query's pairs
+  int32_t* d_qcnt = nullptr;               // [max_docs] pairs per query
+  int32_t* d_qfill = nullptr;              // [max_docs] scatter cursors
   unsigned long long* d_counts = nullptr;  // [0] pairs, [1] candidates
   int32_t* d_err = nullptr;
   unsigned long long* h_counts = nullptr;  // pinned: [0] pairs [1] candidates [2] error word
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t done = nullptr;
   bool pending = false;
+  int64_t last_n = 0;  // documents of the last launch
 };
 
 namespace {
 
 constexpr float kF16Bound = 2e-3f;  // > max |fp16 cosine - cosine| of unit vectors
+
+// Groups the batch's pairs by query: per-query counts, exclusive scan (one CTA), scatter.
+__global__ void k_group_count(const mrc_pair* pairs, const unsigned long long* n_pairs, int64_t cap, int32_t* cnt) {
+  const int64_t n = min((int64_t)*n_pairs, cap);
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[pairs[x].i], 1);
+}
+
+__global__ void k_group_scan(const int32_t* cnt, int64_t n_q, int64_t* qoff, int32_t* fill) {
+  __shared__ int64_t part[1024];
+  const int64_t per = (n_q + blockDim.x - 1) / blockDim.x;
+  const int64_t a = threadIdx.x * per, b = min(n_q, a + per);
+  int64_t s = 0;
+  for (int64_t q = a; q < b; ++q) s += cnt[q];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t run = 0;
+    for (unsigned t = 0; t < blockDim.x; ++t) {
+      const int64_t v = part[t];
+      part[t] = run;
+      run += v;
+    }
+    qoff[n_q] = run;
+  }
+  __syncthreads();
+  int64_t run = part[threadIdx.x];
+  for (int64_t q = a; q < b; ++q) {
+    qoff[q] = run;
+    fill[q] = 0;
+    run += cnt[q];
+  }
+}
+
+__global__ void k_group_scatter(const mrc_pair* pairs, const unsigned long long* n_pairs, int64_t cap,
+                                const int64_t* qoff, int32_t* fill, mrc_pair* out) {
+  const int64_t n = min((int64_t)*n_pairs, cap);
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+    const mrc_pair pr = pairs[x];
+    out[qoff[pr.i] + atomicAdd(&fill[pr.i], 1)] = pr;
+  }
+}
 
 __global__ void k_pad_offsets(int64_t* off, int64_t n, int64_t max_docs) {
   const int64_t i = n + 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -99,6 +146,7 @@ cudaError_t record(mrc_batch* b) {
     g.out_scale = 1.0f / (kE4M3Scale * kE4M3Scale);
     g.a_norm = b->d_qnorm;
     g.b_norm = x->qnorm;
+    g.b_norm_min = x->qnorm_min;
   }
   g.thresh = b->tau - (prec == MRC_PREC_FP32 ? kF16Bound : x->params.margin);
   g.pairs = b->d_cand;
@@ -106,8 +154,18 @@ cudaError_t record(mrc_batch* b) {
   g.capacity = b->cand_cap;
   e = launch_gemm_compare(ctx, g);
   if (e != cudaSuccess) return e;
-  return launch_rescore(ctx, b->d_cand, b->d_counts + 1, b->cand_cap, b->d_unit, x->sig_unit, x->k, b->tau,
-                        b->d_pairs, b->d_counts, b->capacity);
+  e = launch_rescore(ctx, b->d_cand, b->d_counts + 1, b->cand_cap, b->d_unit, x->sig_unit, x->k, b->tau,
+                     b->d_pairs, b->d_counts, b->capacity);
+  if (e != cudaSuccess) return e;
+  // group the pairs by query, so each query's pairs come back as one slice
+  e = cudaMemsetAsync(b->d_qcnt, 0, sizeof(int32_t) * (size_t)b->max_docs, ctx->stream);
+  if (e != cudaSuccess) return e;
+  const int grid = ctx->num_sms * 4;
+  k_group_count<<<grid, 256, 0, ctx->stream>>>(b->d_pairs, b->d_counts, b->capacity, b->d_qcnt);
+  k_group_scan<<<1, 1024, 0, ctx->stream>>>(b->d_qcnt, b->max_docs, b->d_qoff, b->d_qfill);
+  k_group_scatter<<<grid, 256, 0, ctx->stream>>>(b->d_pairs, b->d_counts, b->capacity, b->d_qoff, b->d_qfill,
+                                                 b->d_grouped);
+  return cudaGetLastError();
 }
 
 void release(mrc_batch* b) {
@@ -115,8 +173,8 @@ void release(mrc_batch* b) {
   if (b->ctx) cudaStreamSynchronize(b->ctx->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->done) cudaEventDestroy(b->done);
-  void* ptrs[] = {b->d_offsets, b->d_tokens, b->d_unit, b->d_op, b->d_qnorm, b->d_cand, b->d_pairs, b->d_counts,
-                  b->d_err};
+  void* ptrs[] = {b->d_offsets, b->d_tokens, b->d_unit,  b->d_op,  b->d_qnorm, b->d_cand,   b->d_pairs,
+                  b->d_grouped, b->d_qoff,   b->d_qcnt, b->d_qfill, b->d_counts, b->d_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->h_counts) cudaFreeHost(b->h_counts);
@@ -170,6 +228,10 @@ mrc_status mrc_batch_create(mrc_ctx* ctx, const mrc_index* index, int64_t max_do
   if (e == cudaSuccess) e = cudaMalloc(&b->d_qnorm, sizeof(float) * (size_t)max_docs);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_cand, sizeof(mrc_pair) * (size_t)b->cand_cap);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_pairs, sizeof(mrc_pair) * (size_t)capacity);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_grouped, sizeof(mrc_pair) * (size_t)capacity);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_qoff, sizeof(int64_t) * (size_t)(max_docs + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_qcnt, sizeof(int32_t) * (size_t)max_docs);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_qfill, sizeof(int32_t) * (size_t)max_docs);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_counts, 4 * sizeof(unsigned long long));
@@ -240,6 +302,7 @@ mrc_status mrc_batch_launch(mrc_batch* b, const mrc_docs* docs) {
   if (e == cudaSuccess) e = cudaEventRecord(b->done, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "mrc_batch_launch");
   b->pending = true;
+  b->last_n = n;
   return MRC_OK;
 }
 
@@ -253,7 +316,7 @@ int32_t mrc_batch_poll(mrc_batch* b) {
   return 1;
 }
 
-mrc_status mrc_batch_wait(mrc_batch* b, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs) {
+mrc_status mrc_batch_wait(mrc_batch* b, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs, int64_t* query_offsets) {
   if (!b) return MRC_ERR_INVALID;
   mrc_ctx* ctx = b->ctx;
   if (n_pairs) *n_pairs = 0;
@@ -274,8 +337,12 @@ mrc_status mrc_batch_wait(mrc_batch* b, mrc_pair* pairs, int64_t capacity, int64
     return fail(ctx, MRC_ERR_CAPACITY, "candidate list overflowed: create the batch with a larger capacity");
   const int64_t m = std::min<int64_t>(std::min<int64_t>(total, b->capacity), capacity);
   if (m > 0 && pairs) {
-    e = cudaMemcpy(pairs, b->d_pairs, sizeof(mrc_pair) * (size_t)m, cudaMemcpyDefault);
+    e = cudaMemcpy(pairs, b->d_grouped, sizeof(mrc_pair) * (size_t)m, cudaMemcpyDefault);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copying batch pairs");
+  }
+  if (query_offsets) {
+    e = cudaMemcpy(query_offsets, b->d_qoff, sizeof(int64_t) * (size_t)(b->last_n + 1), cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copying query offsets");
   }
   if (total > std::min(capacity, b->capacity))
     return fail(ctx, MRC_ERR_CAPACITY, "more pairs than capacity; *n_pairs holds the total");

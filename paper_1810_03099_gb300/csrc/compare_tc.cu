@@ -63,6 +63,7 @@ struct GemmParams {
   float thresh, out_scale;
   const float* a_norm;
   const float* b_norm;
+  const float* b_norm_min;  // [ceil(nb / 128)] smallest non-zero b_norm of each 128-column block
   mrc_pair* pairs;
   unsigned long long* count;
   int64_t capacity;
@@ -644,13 +645,16 @@ __global__ void __launch_bounds__(kResThreads, 1)
       tc_fence_after();
       const int64_t i = bi * kBM + q * 32 + lane;
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + ab * 256u;
-      float row_norm = 1.f, fast_thresh = p.thresh;
+      // E4M3: the score is the cosine of the quantized vectors, acc * out_scale / (|q_i| |q_j|);
+      // raw accumulators below thresh * |q_i| * min_j |q_j| / out_scale (minimum over the
+      // chunk's 128-column block) cannot reach the threshold (fast path)
+      float row_norm = 1.f, row_bound = p.thresh;
       if (FMT == OP_E4M3) {
         row_norm = i < p.na ? p.a_norm[i] : 0.f;
         if (p.thresh > 0.f)
-          fast_thresh = row_norm > 0.f ? p.thresh * row_norm * kNormLo / p.out_scale : __int_as_float(0x7f800000);
+          row_bound = row_norm > 0.f ? p.thresh * row_norm / p.out_scale : __int_as_float(0x7f800000);
         else
-          fast_thresh = -__int_as_float(0x7f800000);
+          row_bound = -__int_as_float(0x7f800000);
       }
       // all of this warp's TMEM loads are issued before one wait, so they overlap
       constexpr int CH = BN / 64;  // 32-column chunks per warp (half of the tile)
@@ -676,6 +680,8 @@ __global__ void __launch_bounds__(kResThreads, 1)
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
         const int64_t j0 = bj * BN + (half * CH + c) * 32;
+        float fast_thresh = row_bound;
+        if (FMT == OP_E4M3 && p.thresh > 0.f && j0 < p.nb) fast_thresh = row_bound * __ldg(p.b_norm_min + (j0 >> 7));
         float m = v[c][0];
 #pragma unroll
         for (int e = 1; e < 32; ++e) m = fmaxf(m, v[c][e]);
@@ -784,7 +790,8 @@ cudaError_t run_gemm_resident(mrc_ctx* ctx, const GemmArgs& g) {
   p.out_scale = g.out_scale;
   p.a_norm = g.a_norm;
   p.b_norm = g.b_norm;
-  if (FMT == OP_E4M3 && (!g.a_norm || !g.b_norm)) return cudaErrorInvalidValue;
+  p.b_norm_min = g.b_norm_min;
+  if (FMT == OP_E4M3 && (!g.a_norm || !g.b_norm || !g.b_norm_min)) return cudaErrorInvalidValue;
   p.pairs = g.pairs;
   p.count = g.count;
   p.capacity = g.capacity;

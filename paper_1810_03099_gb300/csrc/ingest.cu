@@ -554,6 +554,27 @@ cudaError_t launch_pack(mrc_ctx* ctx, const float* sig, int64_t n, int32_t k, in
   return cudaGetLastError();
 }
 
+__global__ void k_block_min(const float* norm, int64_t n, float* out) {
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b * 128 >= n) return;
+  float m = __int_as_float(0x7f800000);
+  for (int x = lane; x < 128; x += 32) {
+    const int64_t j = b * 128 + x;
+    if (j < n && norm[j] > 0.f) m = fminf(m, norm[j]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(kFull, m, o));
+  if (lane == 0) out[b] = m == __int_as_float(0x7f800000) ? 1.0f : m;
+}
+
+cudaError_t launch_block_min(mrc_ctx* ctx, const float* norm, int64_t n, float* out) {
+  const int64_t blocks = (n + 127) / 128;
+  if (blocks <= 0) return cudaSuccess;
+  k_block_min<<<(unsigned)((blocks * 32 + 255) / 256), 256, 0, ctx->stream>>>(norm, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_densify(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo,
                            const DenseOut& out) {
   IngestParams p = base_params(d);

@@ -87,6 +87,7 @@ struct mrc_index {
   void* op_lo = nullptr;          // [n * kp] fp16 (lo of the split)
   void* op_e4m3 = nullptr;        // [n * kp8] e4m3
   float* qnorm = nullptr;         // [n] norms of the e4m3 rows
+  float* qnorm_min = nullptr;     // [ceil(n / 128)] smallest non-zero qnorm of each 128-row block
 };
 
 namespace mrc {
@@ -128,6 +129,8 @@ cudaError_t launch_signature(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, cons
 // Packs rows of `sig` (normalised to unit length first when `normalize`) into compare operands.
 cudaError_t launch_pack(mrc_ctx* ctx, const float* sig, int64_t n, int32_t k, int32_t normalize, void* hi, void* lo,
                         void* e4m3, float* qnorm, float* unit, int32_t kp, int32_t kp8);
+// out[b] = smallest non-zero norm[128 b .. 128 b + 127] (1 when the block has none)
+cudaError_t launch_block_min(mrc_ctx* ctx, const float* norm, int64_t n, float* out);
 struct DenseOut {
   const float* idf;       // [vocab] FP32 idf under TF-IDF weighting, NULL for counts
   const int32_t* colmap;  // [vocab] head column, -2 tail term, -1 skipped
@@ -159,6 +162,7 @@ struct GemmArgs {
   float out_scale;      // score = acc * out_scale (E4M3), 1 otherwise
   const float* a_norm;  // E4M3: norms of the quantized rows of A and B; the score is the
   const float* b_norm;  //   cosine of the quantized vectors, acc * out_scale / (|qa| |qb|)
+  const float* b_norm_min;  // E4M3: smallest non-zero b_norm of each 128-row block of B
   // epilogue: pairs (thresh) or dense store
   mrc_pair* pairs;
   unsigned long long* count;

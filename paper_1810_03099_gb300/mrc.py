@@ -81,7 +81,7 @@ _SIGNATURES = {
                                      C.POINTER(C.c_void_p)]),
     "mrc_batch_launch": (C.c_int32, [C.c_void_p, C.POINTER(Docs)]),
     "mrc_batch_poll": (C.c_int32, [C.c_void_p]),
-    "mrc_batch_wait": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "mrc_batch_wait": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
     "mrc_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "mrc_batch_free": (None, [C.c_void_p]),
 }
@@ -254,14 +254,27 @@ class Batch:
     def poll(self) -> bool:
         return bool(self.ctx.lib.mrc_batch_poll(self.handle))
 
-    def wait(self, out=None):
-        """Wait for the last launch; returns (pairs as a structured numpy array, total)."""
-        buf = out if out is not None else np.empty(self.capacity, PAIR_DTYPE)
+    def wait(self, out=None, offsets=False):
+        """Wait for the last launch; returns (pairs grouped by query position, total) and, with
+        offsets=True, also the [n + 1] start of each query's pairs. Without `out` the pairs land
+        in a buffer owned by this object and a copy of them is returned."""
+        own = out is None
+        if own:
+            if getattr(self, "_out", None) is None:
+                self._out = np.empty(self.capacity, PAIR_DTYPE)
+            buf = self._out
+        else:
+            buf = out
+        n = 0 if self._keep is None else int(self._keep[0].shape[0]) - 1
+        qoff = np.zeros(n + 1, np.int64)
         total = C.c_int64()
-        st = self.ctx.lib.mrc_batch_wait(self.handle, _ptr(buf), int(buf.shape[0]), C.byref(total))
+        st = self.ctx.lib.mrc_batch_wait(self.handle, _ptr(buf), int(buf.shape[0]), C.byref(total),
+                                         qoff.ctypes.data if offsets else None)
         self._keep = None
         self._check(st)
-        return buf[:min(int(total.value), buf.shape[0])], int(total.value)
+        m = min(int(total.value), buf.shape[0])
+        pairs = buf[:m].copy() if own else buf[:m]
+        return (pairs, int(total.value), qoff) if offsets else (pairs, int(total.value))
 
     def free(self):
         if getattr(self, "handle", None):

@@ -31,7 +31,7 @@ class Request:
     tokens: np.ndarray
     arrival: float
     done: float = -1.0
-    pairs: list = field(default_factory=list)
+    pairs: np.ndarray = field(default_factory=lambda: np.empty(0, mrc.PAIR_DTYPE))  # (i, j, score) rows
 
 
 def slot_footprint(index, max_docs: int, max_tokens: int, capacity: int) -> int:
@@ -40,7 +40,8 @@ def slot_footprint(index, max_docs: int, max_tokens: int, capacity: int) -> int:
     op = max_docs * (64 if k <= 64 else k) * 2
     cand = max(4 * capacity, 1 << 16) * 12
     ws = max_docs * 8 * 4 + 64 * 1024
-    return 8 * (max_docs + 1) + 4 * max_tokens + 4 * max_docs * k + op + 4 * max_docs + cand + 12 * capacity + ws
+    grouped = 12 * capacity + 16 * max_docs + 8
+    return 8 * (max_docs + 1) + 4 * max_tokens + 4 * max_docs * k + op + 4 * max_docs + cand + 12 * capacity + ws + grouped
 
 
 class Server:
@@ -76,12 +77,12 @@ class Server:
         self.busy[s] = reqs
 
     def _complete(self, s: int, now: float):
-        pairs, _ = self.slots[s].wait()
+        # the pipeline returns the batch's pairs grouped by request, with each request's start
+        pairs, _, qoff = self.slots[s].wait(offsets=True)
         reqs = self.busy[s]
-        for r in reqs:
+        for q, r in enumerate(reqs):
             r.done = now
-        for i, j, sc in zip(pairs["i"].tolist(), pairs["j"].tolist(), pairs["score"].tolist()):
-            reqs[i].pairs.append((j, sc))
+            r.pairs = pairs[qoff[q]:qoff[q + 1]]
         self.busy[s] = None
 
     def run(self, docs: list[np.ndarray], arrivals: np.ndarray) -> list[Request]:

@@ -280,3 +280,127 @@ def random_fingerprints(n: int, seed: int, n_near: int = 0, max_flip: int = 4) -
             v ^= 1 << b
         x[t] = np.uint64(v)
     return x
+
+
+@dataclass
+class DeviceCorpus:
+    """A corpus whose token CSR lives on a CUDA device (torch tensors)."""
+    spec: CorpusSpec
+    offsets: "object"  # torch.int64 [N+1] on the device
+    tokens: "object"  # torch.int32 [T] on the device
+    dup_src: np.ndarray  # [N]: -1 or the original the near-duplicate was copied from
+
+    @property
+    def n_docs(self) -> int:
+        return int(self.offsets.shape[0] - 1)
+
+    @property
+    def vocab(self) -> int:
+        return int(self.spec.vocab)
+
+    @property
+    def n_tokens(self) -> int:
+        return int(self.tokens.shape[0])
+
+    def host_subset(self, idx) -> Corpus:
+        """Documents ``idx`` copied to the host as a ``Corpus`` (for CPU checks)."""
+        import torch
+        idx = np.asarray(idx, dtype=np.int64)
+        offs_h = self.offsets.cpu().numpy()
+        lens = offs_h[idx + 1] - offs_h[idx]
+        new = np.zeros(idx.shape[0] + 1, np.int64)
+        np.cumsum(lens, out=new[1:])
+        pos = torch.from_numpy(np.repeat(offs_h[idx] - new[:-1], lens) + np.arange(int(new[-1]))).to(self.tokens.device)
+        toks = self.tokens[pos].cpu().numpy()
+        return Corpus(self.spec, new, toks, np.full(idx.shape[0], -1, np.int64), np.zeros(idx.shape[0], np.int32))
+
+
+def make_corpus_device(spec: CorpusSpec | str, device="cuda", n_docs: int | None = None,
+                       seed: int | None = None) -> DeviceCorpus:
+    """Draw a large corpus directly into device memory.
+
+    Same recipe as ``make_corpus`` (topic mixtures, Zipf topics, lengths, near-duplicates),
+    with a different random stream: mixtures, lengths and the duplicate plan come from
+    the seeded NumPy generator; per-token topic and term draws and the duplicates' edits
+    from a seeded torch generator on the device. A near-duplicate copies its original's
+    root (the first document of a copy chain) before its own edits.
+    """
+    import torch
+    if isinstance(spec, str):
+        spec = SPECS[spec]
+    if n_docs is not None:
+        spec = spec.with_(n_docs=int(n_docs))
+    if seed is not None:
+        spec = spec.with_(seed=int(seed))
+    rng = np.random.Generator(np.random.PCG64(spec.seed))
+    N, V, K = spec.n_docs, spec.vocab, spec.n_topics
+    dev = torch.device(device)
+    ranks = np.arange(1, V + 1, dtype=np.float64)
+    zipf = _Alias(ranks ** (-spec.zipf_s))
+    perms = np.stack([rng.permutation(V) for _ in range(K)]).astype(np.int32)
+    theta = rng.dirichlet(np.full(K, spec.alpha), size=N).astype(np.float32)
+    lens = _lengths(spec, rng, N)
+    n_dup = int(round(spec.dup_frac * N)) if N > 1 else 0
+    dup_src = np.full(N, -1, dtype=np.int64)
+    edit_f = np.zeros(N, np.float32)
+    if n_dup:
+        dups = np.sort(rng.choice(np.arange(1, N), size=n_dup, replace=False))
+        dup_src[dups] = (rng.random(n_dup) * dups).astype(np.int64)
+        root = dup_src.copy()
+        while True:  # follow copy chains to their first document
+            nxt = np.where(root >= 0, dup_src[np.maximum(root, 0)], -1)
+            upd = (root >= 0) & (nxt >= 0)
+            if not upd.any():
+                break
+            root[upd] = nxt[upd]
+        lens[dups] = lens[root[dups]]
+        theta[dups] = theta[root[dups]]
+        edit_f[dups] = rng.uniform(spec.edit_lo, spec.edit_hi, size=n_dup)
+    offsets = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    T = int(offsets[-1])
+
+    g = torch.Generator(device=dev)
+    g.manual_seed(spec.seed)
+    d_perm = torch.from_numpy(perms.reshape(-1)).to(dev)
+    d_prob = torch.from_numpy(zipf.prob32).to(dev)
+    d_alias = torch.from_numpy(zipf.alias).to(dev)
+    d_cum = torch.from_numpy(np.cumsum(theta, axis=1)).to(dev)
+    d_cum[:, -1] = 2.0
+    d_lens = torch.from_numpy(lens).to(dev)
+    d_off = torch.from_numpy(offsets).to(dev)
+    tokens = torch.empty(T, dtype=torch.int32, device=dev)
+
+    def draw_terms(docs_of_tok):
+        u = torch.rand(docs_of_tok.shape[0], generator=g, device=dev)
+        topic = torch.zeros(docs_of_tok.shape[0], dtype=torch.int64, device=dev)
+        for z in range(K - 1):
+            topic += (u > d_cum[docs_of_tok, z]).to(torch.int64)
+        i = torch.randint(0, V, (docs_of_tok.shape[0],), generator=g, device=dev)
+        a = torch.rand(docs_of_tok.shape[0], generator=g, device=dev)
+        r = torch.where(a < d_prob[i], i, d_alias[i])
+        return d_perm[topic * V + r].to(torch.int32)
+
+    chunk = 1 << 27
+    d0 = 0
+    while d0 < N:
+        d1 = int(np.searchsorted(offsets, offsets[d0] + chunk, side="right")) - 1
+        d1 = min(max(d1, d0 + 1), N)
+        docs_of = torch.repeat_interleave(torch.arange(d0, d1, device=dev), d_lens[d0:d1])
+        tokens[offsets[d0]:offsets[d1]] = draw_terms(docs_of)
+        d0 = d1
+    if n_dup:
+        dd = torch.from_numpy(dups).to(dev)
+        rr = torch.from_numpy(root[dups]).to(dev)
+        dl = d_lens[dd]
+        within = torch.arange(int(dl.sum().item()), device=dev) - torch.repeat_interleave(
+            torch.cumsum(dl, 0) - dl, dl)
+        dst = torch.repeat_interleave(d_off[dd], dl) + within
+        src = torch.repeat_interleave(d_off[rr], dl) + within
+        tokens[dst] = tokens[src]
+        f = torch.repeat_interleave(torch.from_numpy(edit_f[dups]).to(dev), dl)
+        edit = torch.rand(dst.shape[0], generator=g, device=dev) < f
+        pos = dst[edit]
+        if pos.numel():
+            tokens[pos] = draw_terms(torch.repeat_interleave(dd, dl)[edit])
+    return DeviceCorpus(spec, d_off, tokens, dup_src)
