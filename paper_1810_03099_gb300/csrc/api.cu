@@ -721,8 +721,8 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
     if (n_tail > 0) gterm.push_back(n_tail);
   }
   const int32_t n_groups = (int32_t)gterm.size() - 1;
-  const int64_t ldh = (N + 3) / 4 * 4;
-  if ((double)N * (double)ldh * 4.0 > 64e9)
+  const int64_t ldh = (N + 7) / 8 * 8;
+  if ((double)N * (double)ldh * 2.0 > 64e9)
     return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more documents than the 64 GB score buffer allows");
 
   int32_t* d_colmap = (int32_t*)ws_get(ctx, "cos.colmap", sizeof(int32_t) * V, &st);
@@ -741,7 +741,7 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   float* d_rw = (float*)ws_get(ctx, "cos.rw", sizeof(float) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
   void* d_hhi = ws_get(ctx, "cos.hhi", 2 * (size_t)N * kd, &st);
   void* d_hlo = ws_get(ctx, "cos.hlo", 2 * (size_t)N * kd, &st);
-  float* d_H = (float*)ws_get(ctx, "cos.H", sizeof(float) * (size_t)N * ldh, &st);
+  void* d_H = ws_get(ctx, "cos.H16", 2 * (size_t)N * ldh, &st);
   if (st != MRC_OK) return st;
   e = cudaMemcpyAsync(d_colmap, colmap.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
@@ -775,24 +775,27 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   e = launch_sort_postings(ctx, d_cstart, d_gterm, n_groups, d_pdoc, d_pw, d_pr, d.offsets, d_sdoc, d_sw, d_rpos);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sorting postings");
 
-  // head: tensor-core GEMM of the unit head columns (FP32-accurate split), stored
+  // head: single-fp16 tensor-core GEMM of the unit head columns, stored as fp16. Its error
+  // against the exact head sum is at most: fp16 rounding of both operands, 2^-10 sum|w_i w_j|
+  // <= 2^-10 (unit vectors); FP32 accumulation over kd terms, kd 2^-23; the fp16 store of a
+  // value <= 1, 2^-12; plus 1e-4 for subnormal operands and the FP32 addition of the tail.
   GemmArgs g{};
-  g.fmt = OP_SPLIT16;
+  g.fmt = OP_F16;
   g.a_hi = g.b_hi = d_hhi;
-  g.a_lo = g.b_lo = d_hlo;
   g.na = g.nb = N;
   g.kbytes = kd * 2;
   g.triangle = 1;
   g.out_scale = 1.0f;
-  g.store = d_H;
+  g.store16 = d_H;
   g.ld = ldh;
   g.err = d_err;
   e = launch_gemm_compare(ctx, g);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "head GEMM");
+  const float delta = (float)(std::ldexp(1.0, -10) + std::ldexp(1.0, -12) + (double)kd * std::ldexp(1.0, -23) + 1e-4);
 
-  // tail: postings products added to the head scores, threshold, compaction
+  // tail: postings products, candidates against tau - delta, exact head for each candidate
   e = launch_cosine_tail(ctx, N, d_H, ldh, d.offsets, d_rcnt, d_rterm, d_rw, d_rpos, d_tstart, d_tfill, d_sdoc, d_sw,
-                         tau, dst, d_count, capacity, tail_work);
+                         d_hhi, d_hlo, kd, tau, delta, dst, d_count, capacity, tail_work);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tail pass");
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;
   return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);

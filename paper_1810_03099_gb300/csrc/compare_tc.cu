@@ -24,6 +24,7 @@
 // drains its own copies and MMAs (bounded), frees TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -68,6 +69,7 @@ struct GemmParams {
   unsigned long long* count;
   int64_t capacity;
   float* store;
+  __half* store16;
   int64_t ld;
   int32_t* err;
 };
@@ -200,6 +202,72 @@ __device__ __forceinline__ bool decode_tile(const GemmParams& p, int64_t t64, in
   return bi * kBM < p.na;
 }
 
+// Threshold one 32-column chunk held in registers (v[e] = score of column j0 + e for this
+// lane's row i) and append its pairs. Fast path: the chunk's maximum misses fast_thresh in
+// every lane. Otherwise each lane builds a 32-bit mask of candidate columns (bounds and the
+// triangle's j > i applied with bit arithmetic), tests the candidates exactly (E4M3: against
+// the column norms staged once per warp), and the warp appends all hits with one atomic.
+template <int FMT>
+__device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)[32], int64_t i, int64_t j0, int lane,
+                                           float fast_thresh, float row_norm, float* stage, float* nstage) {
+  float m = v[0];
+#pragma unroll
+  for (int e = 1; e < 32; ++e) m = fmaxf(m, v[e]);
+  if (!__any_sync(kFull, m >= fast_thresh)) return;
+#pragma unroll
+  for (int e = 0; e < 32; ++e) stage[lane * 33 + e] = v[e];
+  if (FMT == OP_E4M3) nstage[lane] = j0 + lane < p.nb ? __ldg(p.b_norm + j0 + lane) : 0.f;
+  __syncwarp();
+  uint32_t mask = 0;
+#pragma unroll
+  for (int e = 0; e < 32; ++e) mask |= (v[e] >= fast_thresh ? 1u : 0u) << e;
+  const int64_t lim = p.nb - j0;  // columns j0 + e < nb
+  if (lim < 32) mask &= lim <= 0 ? 0u : ((1u << lim) - 1u);
+  if (p.triangle) {  // j0 + e > i
+    const int64_t dlt = i - j0;
+    if (dlt >= 31) mask = 0u;
+    else if (dlt >= 0) mask &= ~((2u << dlt) - 1u);
+  }
+  if (i >= p.na) mask = 0u;
+  uint32_t hits = 0;
+  for (uint32_t mm = mask; mm; mm &= mm - 1u) {
+    const int e = __ffs(mm) - 1;
+    float sc = stage[lane * 33 + e];
+    if (FMT == OP_E4M3) {
+      const float nn = row_norm * nstage[e];
+      sc = nn > 0.f ? sc * p.out_scale / nn : 0.f;
+    }
+    if (sc >= p.thresh) hits |= 1u << e;
+  }
+  const int cnt = __popc(hits);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  if (total) {
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(p.count, (unsigned long long)total);
+    base = __shfl_sync(kFull, base, 31);
+    unsigned long long at = base + (unsigned long long)(incl - cnt);
+    for (uint32_t hh = hits; hh; hh &= hh - 1u, ++at) {
+      const int e = __ffs(hh) - 1;
+      float sc = stage[lane * 33 + e];
+      if (FMT == OP_E4M3) sc = sc * p.out_scale / (row_norm * nstage[e]);
+      if (at < (unsigned long long)p.capacity) {
+        mrc_pair pr;
+        pr.i = (int32_t)i;
+        pr.j = (int32_t)(j0 + e);
+        pr.score = sc;
+        p.pairs[at] = pr;
+      }
+    }
+  }
+  __syncwarp();
+}
+
 template <int FMT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_compare(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
@@ -218,8 +286,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* drain = acc_empty + 2;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
+  float* stage_all = reinterpret_cast<float*>(drain + 4);  // [4 epilogue warps][32 x 33 + 32]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* stage = stage_all + (warp >= 2 ? warp - 2 : 0) * (32 * 33 + 32);
+  float* nstage = stage + 32 * 33;
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -372,7 +443,28 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_wait_ld();
         }
         const int64_t j0 = bj * BN + c * 32;
-        if (p.store) {
+        if (p.store16) {
+          if (i < p.na) {
+            __half* dst = p.store16 + i * p.ld + j0;
+            if (j0 + 32 <= p.nb && (p.ld & 7) == 0) {
+#pragma unroll
+              for (int e = 0; e < 32; e += 8) {
+                uint4 w;
+                __half2 h0 = __floats2half2_rn(v[e], v[e + 1]), h1 = __floats2half2_rn(v[e + 2], v[e + 3]);
+                __half2 h2 = __floats2half2_rn(v[e + 4], v[e + 5]), h3 = __floats2half2_rn(v[e + 6], v[e + 7]);
+                w.x = *reinterpret_cast<uint32_t*>(&h0);
+                w.y = *reinterpret_cast<uint32_t*>(&h1);
+                w.z = *reinterpret_cast<uint32_t*>(&h2);
+                w.w = *reinterpret_cast<uint32_t*>(&h3);
+                *reinterpret_cast<uint4*>(dst + e) = w;
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < 32; ++e)
+                if (j0 + e < p.nb) dst[e] = __float2half_rn(v[e]);
+            }
+          }
+        } else if (p.store) {
           if (i < p.na) {
             float* dst = p.store + i * p.ld + j0;
             if (j0 + 32 <= p.nb && (p.ld & 3) == 0) {
@@ -386,36 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         } else {
-          float m = v[0];
-#pragma unroll
-          for (int e = 1; e < 32; ++e) m = fmaxf(m, v[e]);
-          if (__any_sync(kFull, m >= fast_thresh)) {
-#pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              const int64_t j = j0 + e;
-              if (FMT == OP_E4M3) {
-                const float nn = row_norm * (j < p.nb ? p.b_norm[j] : 0.f);
-                v[e] = nn > 0.f ? v[e] * p.out_scale / nn : 0.f;
-              }
-              const bool hit = v[e] >= p.thresh && i < p.na && j < p.nb && (!p.triangle || j > i);
-              const unsigned bal = __ballot_sync(kFull, hit);
-              if (bal) {
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(p.count, (unsigned long long)__popc(bal));
-                base = __shfl_sync(kFull, base, 0);
-                if (hit) {
-                  const unsigned long long at = base + __popc(bal & ((1u << lane) - 1u));
-                  if (at < (unsigned long long)p.capacity) {
-                    mrc_pair pr;
-                    pr.i = (int32_t)i;
-                    pr.j = (int32_t)j;
-                    pr.score = v[e];
-                    p.pairs[at] = pr;
-                  }
-                }
-              }
-            }
-          }
+          emit_chunk<FMT>(p, v, i, j0, lane, fast_thresh, row_norm, stage, nstage);
         }
       }
       tc_fence_before();
@@ -504,10 +567,11 @@ __global__ void __launch_bounds__(kResThreads, 1)
   uint64_t* drain = acc_empty + 2;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
-  float* stage_all = reinterpret_cast<float*>(drain + 4);  // [8 warps][32 x 33]
+  float* stage_all = reinterpret_cast<float*>(drain + 4);  // [8 warps][32 x 33 + 32]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* stage = stage_all + (warp >= 2 ? warp - 2 : 0) * (32 * 33);
+  float* stage = stage_all + (warp >= 2 ? warp - 2 : 0) * (32 * 33 + 32);
+  float* nstage = stage + 32 * 33;
   const int64_t t_begin = p.n_tiles * blockIdx.x / gridDim.x;
   const int64_t t_end = p.n_tiles * (blockIdx.x + 1) / gridDim.x;
   if (threadIdx.x == 0) {
@@ -648,9 +712,12 @@ __global__ void __launch_bounds__(kResThreads, 1)
       // E4M3: the score is the cosine of the quantized vectors, acc * out_scale / (|q_i| |q_j|);
       // raw accumulators below thresh * |q_i| * min_j |q_j| / out_scale (minimum over the
       // chunk's 128-column block) cannot reach the threshold (fast path)
-      float row_norm = 1.f, row_bound = p.thresh;
-      if (FMT == OP_E4M3) {
-        row_norm = i < p.na ? p.a_norm[i] : 0.f;
+      float row_norm = 1.f, row_bound = p.thresh, nmin0 = 1.f, nmin1 = 1.f;
+      if (FMT == OP_E4M3) {  // issued before the TMEM loads so that their latencies overlap
+        row_norm = i < p.na ? __ldg(p.a_norm + i) : 0.f;
+        const int64_t b0 = (bj * BN) >> 7, nbk = (p.nb + 127) >> 7;
+        nmin0 = b0 < nbk ? __ldg(p.b_norm_min + b0) : 1.f;
+        if (BN > 128) nmin1 = b0 + 1 < nbk ? __ldg(p.b_norm_min + b0 + 1) : 1.f;
         if (p.thresh > 0.f)
           row_bound = row_norm > 0.f ? p.thresh * row_norm / p.out_scale : __int_as_float(0x7f800000);
         else
@@ -681,43 +748,8 @@ __global__ void __launch_bounds__(kResThreads, 1)
       for (int c = 0; c < CH; ++c) {
         const int64_t j0 = bj * BN + (half * CH + c) * 32;
         float fast_thresh = row_bound;
-        if (FMT == OP_E4M3 && p.thresh > 0.f && j0 < p.nb) fast_thresh = row_bound * __ldg(p.b_norm_min + (j0 >> 7));
-        float m = v[c][0];
-#pragma unroll
-        for (int e = 1; e < 32; ++e) m = fmaxf(m, v[c][e]);
-        if (__any_sync(kFull, m >= fast_thresh)) {
-          // rare: stage the chunk in this warp's shared-memory slab and walk it compactly
-#pragma unroll
-          for (int e = 0; e < 32; ++e) stage[lane * 33 + e] = v[c][e];
-          __syncwarp();
-#pragma unroll 1
-          for (int e = 0; e < 32; ++e) {
-            const int64_t j = j0 + e;
-            float sc = stage[lane * 33 + e];
-            if (FMT == OP_E4M3) {
-              const float nn = row_norm * (j < p.nb ? p.b_norm[j] : 0.f);
-              sc = nn > 0.f ? sc * p.out_scale / nn : 0.f;
-            }
-            const bool hit = sc >= p.thresh && i < p.na && j < p.nb && (!p.triangle || j > i);
-            const unsigned bal = __ballot_sync(kFull, hit);
-            if (bal) {
-              unsigned long long base = 0;
-              if (lane == 0) base = atomicAdd(p.count, (unsigned long long)__popc(bal));
-              base = __shfl_sync(kFull, base, 0);
-              if (hit) {
-                const unsigned long long at = base + __popc(bal & ((1u << lane) - 1u));
-                if (at < (unsigned long long)p.capacity) {
-                  mrc_pair pr;
-                  pr.i = (int32_t)i;
-                  pr.j = (int32_t)j;
-                  pr.score = sc;
-                  p.pairs[at] = pr;
-                }
-              }
-            }
-          }
-          __syncwarp();
-        }
+        if (FMT == OP_E4M3 && p.thresh > 0.f) fast_thresh = row_bound * ((((half * CH + c) * 32) >> 7) ? nmin1 : nmin0);
+        emit_chunk<FMT>(p, v[c], i, j0, lane, fast_thresh, row_norm, stage, nstage);
       }
       ++it;
     }
@@ -799,7 +831,7 @@ cudaError_t run_gemm_resident(mrc_ctx* ctx, const GemmArgs& g) {
   // at least 120 KB, so that one CTA (which owns all 512 TMEM columns) runs per SM
   const size_t smem =
       std::max<size_t>(1024 + 2 * (size_t)C::NOPS * kBM * RB + (size_t)kResStagesB * C::NOPS * BN * RB + 256 +
-                           8 * 32 * 33 * sizeof(float),
+                           8 * (32 * 33 + 32) * sizeof(float),
                        120 * 1024);
   cudaError_t e =
       cudaFuncSetAttribute(k_gemm_resident<FMT, RB, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -848,14 +880,15 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   p.out_scale = g.out_scale;
   p.a_norm = g.a_norm;
   p.b_norm = g.b_norm;
-  if (FMT == OP_E4M3 && (!g.a_norm || !g.b_norm) && !g.store) return cudaErrorInvalidValue;
+  if (FMT == OP_E4M3 && (!g.a_norm || !g.b_norm) && !g.store && !g.store16) return cudaErrorInvalidValue;
   p.pairs = g.pairs;
   p.count = g.count;
   p.capacity = g.capacity;
   p.store = g.store;
+  p.store16 = reinterpret_cast<__half*>(g.store16);
   p.ld = g.ld;
   p.err = g.err;
-  const size_t smem = 1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256;
+  const size_t smem = 1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256 + 4 * (32 * 33 + 32) * 4;
   cudaError_t e = cudaFuncSetAttribute(k_gemm_compare<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int64_t grid = ctx->num_sms;
@@ -865,8 +898,10 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   const double k_elems = (double)g.kbytes / (fp8 ? 1.0 : 2.0);
   const double pairs = g.triangle ? (double)g.na * (double)(g.na - 1) / 2.0 : (double)g.na * (double)g.nb;
   const double flops = 2.0 * k_elems * pairs * (C::NOPS == 2 ? 3.0 : 1.0);
-  const char* name = FMT == OP_SPLIT16 ? (g.store ? "gemm_split16_store" : "gemm_split16_thresh")
-                                        : (FMT == OP_F16 ? "gemm_f16_thresh" : "gemm_e4m3_thresh");
+  const bool st = g.store || g.store16;
+  const char* name = FMT == OP_SPLIT16 ? (st ? "gemm_split16_store" : "gemm_split16_thresh")
+                                        : (FMT == OP_F16 ? (st ? "gemm_f16_store" : "gemm_f16_thresh")
+                                                         : "gemm_e4m3_thresh");
   const double bytes = (double)C::NOPS * (double)(g.na + (g.triangle ? 0 : g.nb)) * g.kbytes;
   cudaEvent_t ev = nullptr;
   timing_begin(ctx, name, bytes, flops, &ev);
@@ -880,7 +915,7 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
 cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g) {
   if (g.na <= 0 || g.nb <= 0) return cudaErrorInvalidValue;
   if (g.na >= (1ll << 31) || g.nb >= (1ll << 31)) return cudaErrorInvalidValue;
-  if (!g.store && (g.kbytes == 64 || g.kbytes == 128)) {
+  if (!g.store && !g.store16 && (g.kbytes == 64 || g.kbytes == 128)) {
     // one K block: resident-A kernel
     // tile width: 256 columns by default for single-accumulator formats, 128 on request
     const int wide = (g.fmt != OP_SPLIT16 && g.tile_n != 128) ? 1 : 0;

@@ -2,13 +2,17 @@
 //
 // Exact cosine (Eq. 1) of unit TF-IDF vectors splits over the vocabulary:
 // cos(i, j) = sum over frequent ("head") terms + sum over the other terms.
-// The head sums come from the tensor-core GEMM as an FP32 matrix H. This
-// kernel adds the remaining terms from postings lists and applies the
-// threshold (see k_cosine_tail).
+// The head sums come from a single-fp16 tensor-core GEMM as an fp16 matrix
+// H16 (an approximation with a proven error bound). This kernel adds the
+// remaining terms from postings lists, selects candidates against the
+// threshold lowered by that bound, and recomputes each candidate's head
+// exactly before the final test (see k_cosine_tail).
 //
 // Rescoring (reduced-precision forms): each candidate pair found with a
 // lowered threshold in FP8 or FP16 is recomputed as an FP32 dot product of the
 // two FP32 unit signatures and kept iff it reaches tau.
+#include <cuda_fp16.h>
+
 #include "device.cuh"
 #include "internal.h"
 
@@ -84,46 +88,72 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_postings(
   }
 }
 
-// One CTA per (row i, column window) work item, accumulating in a shared-memory row of
-// 2^-30 fixed-point integers (each product is < 1: rounding <= 2^-31; integer sums do not
-// depend on the order in which threads add them):
-//  1. acc[j] = H[i][j] for the window (independent loads, four per thread in flight);
+// Exact score of one candidate pair (i, j): the head part recomputed from the split head rows
+// (w = hi + lo / 4096 is exact in FP32: 22 significant bits), FP32 products summed by the
+// warp in a fixed order, plus the exact tail sum. Every lane returns the same value.
+__device__ __forceinline__ float exact_head(const __half* __restrict__ hhi, const __half* __restrict__ hlo,
+                                            int32_t kd, int64_t i, int64_t j, int lane) {
+  const __half* ai = hhi + i * kd;
+  const __half* bi = hlo + i * kd;
+  const __half* aj = hhi + j * kd;
+  const __half* bj = hlo + j * kd;
+  float s = 0.f;
+  for (int32_t c = 8 * lane; c < kd; c += 256) {
+    const uint4 xa = __ldg(reinterpret_cast<const uint4*>(ai + c));
+    const uint4 xb = __ldg(reinterpret_cast<const uint4*>(bi + c));
+    const uint4 ya = __ldg(reinterpret_cast<const uint4*>(aj + c));
+    const uint4 yb = __ldg(reinterpret_cast<const uint4*>(bj + c));
+    const __half2* pa = reinterpret_cast<const __half2*>(&xa);
+    const __half2* pb = reinterpret_cast<const __half2*>(&xb);
+    const __half2* qa = reinterpret_cast<const __half2*>(&ya);
+    const __half2* qb = reinterpret_cast<const __half2*>(&yb);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float2 h1 = __half22float2(pa[u]), l1 = __half22float2(pb[u]);
+      const float2 h2 = __half22float2(qa[u]), l2 = __half22float2(qb[u]);
+      const float x0 = fmaf(l1.x, 1.0f / kSplitLoScale, h1.x), x1 = fmaf(l1.y, 1.0f / kSplitLoScale, h1.y);
+      const float y0 = fmaf(l2.x, 1.0f / kSplitLoScale, h2.x), y1 = fmaf(l2.y, 1.0f / kSplitLoScale, h2.y);
+      s = fmaf(x0, y0, s);
+      s = fmaf(x1, y1, s);
+    }
+  }
+  return warp_sum(s);
+}
+
+// One CTA per (row i, column window) work item. The tail sums accumulate in a shared-memory
+// row of 2^-30 fixed-point integers (each product is < 1: rounding <= 2^-31; integer sums do
+// not depend on the order in which threads add them):
+//  1. acc[j] = 0 over the window;
 //  2. for every tail term t of document i, the postings after i's own position in t's
 //     sorted list are exactly the documents j > i sharing t: acc[j] += w_it * w_jt. Each
 //     warp takes 32 of the row's terms at a time (one lane per term holds its metadata),
 //     flattens their postings into one index range (warp prefix sum; a shuffle binary
 //     search maps an index back to its term) and walks it with four loads per lane in
 //     flight, so short lists do not leave lanes idle;
-//  3. threshold and warp-aggregated compaction.
+//  3. scan: H16[i][j] (the fp16 head score from the tensor cores, eight columns per 16-byte
+//     load) + tail >= tau - delta marks a candidate, where delta bounds the head's error;
+//     each candidate's head is recomputed exactly (exact_head) and the pair is kept iff
+//     head + tail >= tau.
 __global__ void __launch_bounds__(kTailThreads) k_cosine_tail(
-    int64_t n, const float* __restrict__ H, int64_t ldh, const int64_t* __restrict__ row_off,
+    int64_t n, const __half* __restrict__ H, int64_t ldh, const int64_t* __restrict__ row_off,
     const int32_t* __restrict__ row_cnt, const int32_t* __restrict__ row_term, const float* __restrict__ row_w,
     const int64_t* __restrict__ row_pos, const int64_t* __restrict__ tail_start, const int32_t* __restrict__ post_cnt,
-    const int32_t* __restrict__ sdoc, const float* __restrict__ sw, float tau, mrc_pair* pairs,
+    const int32_t* __restrict__ sdoc, const float* __restrict__ sw, const __half* __restrict__ hhi,
+    const __half* __restrict__ hlo, int32_t kd, float tau, float delta, mrc_pair* pairs,
     unsigned long long* count, int64_t capacity, int64_t window, int64_t n_windows, int64_t n_items) {
   extern __shared__ int32_t acc[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float cand_tau = tau - delta;
   for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int64_t i = item / n_windows;
     const int64_t w = item % n_windows;
-    const int64_t base = w * window;
+    const int64_t base = w * window;  // a multiple of 8 (window is)
     const int64_t lo = max(i + 1, base), hi = min(n, base + window);
     if (lo >= hi) continue;  // block-uniform
-    const float* hrow = H + i * ldh;
     __syncthreads();  // the previous item's scan is done with acc
-    for (int64_t j = lo + threadIdx.x; j < hi; j += 8 * kTailThreads) {
-      float v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int64_t jj = j + u * kTailThreads;
-        v[u] = jj < hi ? __ldcs(hrow + jj) : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int64_t jj = j + u * kTailThreads;
-        if (jj < hi) acc[jj - base] = __float2int_rn(v[u] * kTailFix);
-      }
-    }
+    const int64_t a0 = (lo - base) & ~7ll, a1 = hi - base;  // accumulator range touched, 8-aligned start
+    for (int64_t x = a0 + 4 * threadIdx.x; x < a1; x += 4 * kTailThreads)
+      *reinterpret_cast<int4*>(acc + x) = make_int4(0, 0, 0, 0);
     __syncthreads();
     const int32_t nt = row_cnt[i];
     const int64_t ro = row_off[i];
@@ -178,27 +208,55 @@ __global__ void __launch_bounds__(kTailThreads) k_cosine_tail(
       }
     }
     __syncthreads();
-    for (int64_t x0 = lo; x0 < hi; x0 += kTailThreads) {
-      const int64_t j = x0 + threadIdx.x;
-      float s = 0.f;
-      bool hit = false;
-      if (j < hi) {
-        s = (float)acc[j - base] * kTailInv;
-        hit = s >= tau;
+    // scan: each lane takes eight consecutive columns (one 16-byte load of H16, in the row's
+    // ldh >= round8(n) padding at the end, so never past the row)
+    const __half* hrow = H + i * ldh;
+    for (int64_t g0 = base + a0 + 8 * (int64_t)warp * 32; g0 < hi; g0 += 8 * kTailThreads) {
+      const int64_t g = g0 + 8 * lane;
+      uint32_t mask = 0;
+      float sv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (g < hi) {
+        const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(hrow + g));
+        const __half2* h2 = reinterpret_cast<const __half2*>(&raw);
+        const int4 t0 = *reinterpret_cast<const int4*>(acc + (g - base));
+        const int4 t1 = *reinterpret_cast<const int4*>(acc + (g - base) + 4);
+        const int32_t tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float2 hf = __half22float2(h2[u]);
+          sv[2 * u] = (float)tv[2 * u] * kTailInv;
+          sv[2 * u + 1] = (float)tv[2 * u + 1] * kTailInv;
+          const int64_t ja = g + 2 * u, jb = ja + 1;
+          if (ja >= lo && ja < hi && hf.x + sv[2 * u] >= cand_tau) mask |= 1u << (2 * u);
+          if (jb >= lo && jb < hi && hf.y + sv[2 * u + 1] >= cand_tau) mask |= 1u << (2 * u + 1);
+        }
       }
-      const unsigned bal = __ballot_sync(kFull, hit);
-      if (bal) {
-        unsigned long long at0 = 0;
-        if (lane == 0) at0 = atomicAdd(count, (unsigned long long)__popc(bal));
-        at0 = __shfl_sync(kFull, at0, 0);
-        if (hit) {
-          const unsigned long long at = at0 + __popc(bal & ((1u << lane) - 1u));
-          if (at < (unsigned long long)capacity) {
-            mrc_pair pr;
-            pr.i = (int32_t)i;
-            pr.j = (int32_t)j;
-            pr.score = s;
-            pairs[at] = pr;
+      unsigned todo = __ballot_sync(kFull, mask != 0);
+      while (todo) {  // rare: candidates of one lane at a time, the whole warp per candidate
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        uint32_t m = __shfl_sync(kFull, mask, src);
+        const int64_t gs = __shfl_sync(kFull, g, src);
+        while (m) {
+          const int e = __ffs(m) - 1;
+          m &= m - 1;
+          const int64_t j = gs + e;
+          float tail = 0.f;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float y = __shfl_sync(kFull, sv[u], src);
+            if (u == e) tail = y;
+          }
+          const float s = exact_head(hhi, hlo, kd, i, j, lane) + tail;
+          if (lane == 0 && s >= tau) {
+            const unsigned long long at = atomicAdd(count, 1ull);
+            if (at < (unsigned long long)capacity) {
+              mrc_pair pr;
+              pr.i = (int32_t)i;
+              pr.j = (int32_t)j;
+              pr.score = s;
+              pairs[at] = pr;
+            }
           }
         }
       }
@@ -247,13 +305,16 @@ cudaError_t launch_sort_postings(mrc_ctx* ctx, const int64_t* cstart, const int3
   return cudaGetLastError();
 }
 
-cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const float* H, int64_t ldh, const int64_t* row_off,
+cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t ldh, const int64_t* row_off,
                                const int32_t* row_cnt, const int32_t* row_term, const float* row_w,
                                const int64_t* row_pos, const int64_t* tail_start, const int32_t* post_cnt,
-                               const int32_t* sdoc, const float* sw, float tau, mrc_pair* pairs,
-                               unsigned long long* count, int64_t capacity, double work_pairs) {
+                               const int32_t* sdoc, const float* sw, const void* head_hi, const void* head_lo,
+                               int32_t kd, float tau, float delta, mrc_pair* pairs, unsigned long long* count,
+                               int64_t capacity, double work_pairs) {
   if (n <= 1) return cudaSuccess;
-  const int64_t window = n < kMaxWindow ? n : kMaxWindow;
+  if ((ldh & 7) || ldh < (n + 7) / 8 * 8 || (kd & 63) || kd <= 0) return cudaErrorInvalidValue;
+  const int64_t n8 = (n + 7) / 8 * 8;
+  const int64_t window = n8 < kMaxWindow ? n8 : kMaxWindow;  // a multiple of 8
   const int64_t n_windows = (n + window - 1) / window;
   const int64_t n_items = n * n_windows;
   const size_t smem = sizeof(int32_t) * (size_t)window;
@@ -264,12 +325,13 @@ cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const float* H, int64_t 
   int64_t grid = (int64_t)ctx->num_sms * (per_sm > 0 ? per_sm : 1);
   if (n_items < grid) grid = n_items;
   cudaEvent_t ev = nullptr;
-  // algorithmic bytes: the upper triangle of H read once; flops: 2 per tail posting product
-  timing_begin(ctx, "cosine_tail", 4.0 * (double)n * (double)(n - 1) / 2.0, 2.0 * work_pairs, &ev);
-  k_cosine_tail<<<(unsigned)grid, kTailThreads, smem, ctx->stream>>>(n, H, ldh, row_off, row_cnt, row_term, row_w,
-                                                                     row_pos, tail_start, post_cnt, sdoc, sw, tau,
-                                                                     pairs, count, capacity, window, n_windows,
-                                                                     n_items);
+  // algorithmic bytes: the upper triangle of the fp16 head scores read once; flops: 2 per
+  // tail posting product
+  timing_begin(ctx, "cosine_tail", 2.0 * (double)n * (double)(n - 1) / 2.0, 2.0 * work_pairs, &ev);
+  k_cosine_tail<<<(unsigned)grid, kTailThreads, smem, ctx->stream>>>(
+      n, reinterpret_cast<const __half*>(H16), ldh, row_off, row_cnt, row_term, row_w, row_pos, tail_start, post_cnt,
+      sdoc, sw, reinterpret_cast<const __half*>(head_hi), reinterpret_cast<const __half*>(head_lo), kd, tau, delta,
+      pairs, count, capacity, window, n_windows, n_items);
   timing_end(ctx, ev);
   return cudaGetLastError();
 }
