@@ -721,6 +721,8 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
     if (n_tail > 0) gterm.push_back(n_tail);
   }
   const int32_t n_groups = (int32_t)gterm.size() - 1;
+  if (n_post >= (1ll << 31) - 64)
+    return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more than 2^31 tail postings");
   const int64_t ldh = (N + 7) / 8 * 8;
   if ((double)N * (double)ldh * 2.0 > 64e9)
     return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more documents than the 64 GB score buffer allows");
@@ -733,7 +735,7 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   int32_t* d_pr = (int32_t*)ws_get(ctx, "cos.pr", sizeof(int32_t) * (size_t)std::max<int64_t>(n_post, 1), &st);
   int32_t* d_sdoc = (int32_t*)ws_get(ctx, "cos.sdoc", sizeof(int32_t) * (size_t)std::max<int64_t>(n_post, 1), &st);
   float* d_sw = (float*)ws_get(ctx, "cos.sw", sizeof(float) * (size_t)std::max<int64_t>(n_post, 1), &st);
-  int64_t* d_rpos = (int64_t*)ws_get(ctx, "cos.rpos", sizeof(int64_t) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
+  void* d_rwalk = ws_get(ctx, "cos.rwalk", 8 * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
   int64_t* d_cstart = (int64_t*)ws_get(ctx, "cos.cstart", sizeof(int64_t) * cstart.size(), &st);
   int32_t* d_gterm = (int32_t*)ws_get(ctx, "cos.gterm", sizeof(int32_t) * gterm.size(), &st);
   int32_t* d_rcnt = (int32_t*)ws_get(ctx, "cos.rcnt", sizeof(int32_t) * (size_t)N, &st);
@@ -742,6 +744,7 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   void* d_hhi = ws_get(ctx, "cos.hhi", 2 * (size_t)N * kd, &st);
   void* d_hlo = ws_get(ctx, "cos.hlo", 2 * (size_t)N * kd, &st);
   void* d_H = ws_get(ctx, "cos.H16", 2 * (size_t)N * ldh, &st);
+  unsigned long long* d_next = (unsigned long long*)ws_get(ctx, "cos.next", sizeof(unsigned long long), &st);
   if (st != MRC_OK) return st;
   e = cudaMemcpyAsync(d_colmap, colmap.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
@@ -772,7 +775,7 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   o.row_w = d_rw;
   e = launch_densify(ctx, d, V, index->tinfo, o);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "densify");
-  e = launch_sort_postings(ctx, d_cstart, d_gterm, n_groups, d_pdoc, d_pw, d_pr, d.offsets, d_sdoc, d_sw, d_rpos);
+  e = launch_sort_postings(ctx, d_cstart, d_gterm, n_groups, d_pdoc, d_pw, d_pr, d.offsets, d_sdoc, d_sw, d_rwalk);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sorting postings");
 
   // head: single-fp16 tensor-core GEMM of the unit head columns, stored as fp16. Its error
@@ -794,8 +797,8 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   const float delta = (float)(std::ldexp(1.0, -10) + std::ldexp(1.0, -12) + (double)kd * std::ldexp(1.0, -23) + 1e-4);
 
   // tail: postings products, candidates against tau - delta, exact head for each candidate
-  e = launch_cosine_tail(ctx, N, d_H, ldh, d.offsets, d_rcnt, d_rterm, d_rw, d_rpos, d_tstart, d_tfill, d_sdoc, d_sw,
-                         d_hhi, d_hlo, kd, tau, delta, dst, d_count, capacity, tail_work);
+  e = launch_cosine_tail(ctx, N, d_H, ldh, d.offsets, d_rcnt, d_rwalk, d_rw, d_sdoc, d_sw, n_post, d_hhi, d_hlo, kd,
+                         tau, delta, dst, d_count, capacity, tail_work, d_next);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tail pass");
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;
   return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);

@@ -41,8 +41,10 @@ constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr int kShortMax = 512;      // documents up to this length take the warp path
 constexpr int kShortSlots = 1024;   // per-warp table (load <= 1/2)
 constexpr int kWarpsShort = 8;      // warps per CTA in the warp path
+constexpr int kShortRegs = kShortMax / 32;  // tokens per lane held in registers (warp path)
 constexpr int kLongThreads = 512;   // CTA size of the long-document path
-constexpr int kLongSlots = 16384;   // per-CTA table
+constexpr int kLongSlots = 8192;    // per-CTA table: documents with > 4096 tokens take several passes
+constexpr int kLongUnroll = 4;      // token loads per thread in flight (CTA path)
 constexpr float kFix = 4194304.0f;  // 2^22
 constexpr float kInvFix = 1.0f / 4194304.0f;
 
@@ -105,6 +107,7 @@ struct IngestParams {
   const int32_t* long_list;
   const int32_t* list_counts;  // [0] short, [1] long
   int32_t* long_cursor;        // dynamic grab of long documents
+  int32_t* short_cursor;       // dynamic grab of short documents (one warp each)
   int32_t* err;
   // DF
   int32_t* df;
@@ -239,7 +242,7 @@ __device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsi
 
 // ---------------------------------------------------------------- warp path
 template <int MODE>
-__global__ void __launch_bounds__(kWarpsShort * 32) k_ingest_short(IngestParams p) {
+__global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kq = MODE == kSIG ? p.k : 0;
@@ -251,7 +254,14 @@ __global__ void __launch_bounds__(kWarpsShort * 32) k_ingest_short(IngestParams 
   int32_t* row_cnt_s = reinterpret_cast<int32_t*>(cnts + kShortSlots);
 
   const int32_t n_short = p.list_counts[0];
-  for (int32_t it = blockIdx.x * kWarpsShort + warp; it < n_short; it += gridDim.x * kWarpsShort) {
+  // documents are taken one at a time as warps free up (their lengths vary 100-fold); each
+  // warp asks for its next document while it works on the current one
+  int32_t it = 0;
+  if (lane == 0) it = atomicAdd(p.short_cursor, 1);
+  it = __shfl_sync(kFull, it, 0);
+  while (it < n_short) {
+    int32_t next = 0;
+    if (lane == 0) next = atomicAdd(p.short_cursor, 1);
     const int64_t d = p.short_list[it];
     const int64_t o0 = p.offsets[d], len = p.offsets[d + 1] - o0;
     const int l2 = log2_slots(len, 10);
@@ -262,14 +272,21 @@ __global__ void __launch_bounds__(kWarpsShort * 32) k_ingest_short(IngestParams 
     }
     for (int q = lane; q < kq; q += 32) num_q[q] = 0ull;
     if (lane == 0) *row_cnt_s = 0;
+    // all of the document's token loads in flight at once (len <= 512: 16 per lane)
+    int32_t tk[kShortRegs];
+#pragma unroll
+    for (int u = 0; u < kShortRegs; ++u) tk[u] = lane + 32 * u < len ? __ldcs(p.tokens + o0 + lane + 32 * u) : -1;
     __syncwarp();
-    for (int64_t x = lane; x < len; x += 32) {
-      const int32_t t = p.tokens[o0 + x];
-      if ((uint32_t)t >= (uint32_t)p.vocab) {
-        set_err(p.err, kErrBadToken);
-        continue;
+#pragma unroll
+    for (int u = 0; u < kShortRegs; ++u) {
+      if (32 * u >= len) break;  // warp-uniform
+      if (lane + 32 * u < len) {
+        const int32_t t = tk[u];
+        if ((uint32_t)t >= (uint32_t)p.vocab)
+          set_err(p.err, kErrBadToken);
+        else if (!table_insert(keys, cnts, l2, (uint32_t)t))
+          set_err(p.err, kErrTable);
       }
-      if (!table_insert(keys, cnts, l2, (uint32_t)t)) set_err(p.err, kErrTable);
     }
     __syncwarp();
     // compact the occupied slots to the front, in place (a write never passes an unread slot)
@@ -303,6 +320,7 @@ __global__ void __launch_bounds__(kWarpsShort * 32) k_ingest_short(IngestParams 
     if (MODE == kSIG) finalize_sig(p, d, len, warp_sum(a.norm), num_q, a.plo, a.phi, lane);
     if (MODE == kDENSE && lane == 0) p.dense.row_cnt[d] = *row_cnt_s;
     __syncwarp();
+    it = __shfl_sync(kFull, next, 0);
   }
 }
 
@@ -328,7 +346,7 @@ __global__ void __launch_bounds__(kLongThreads) k_ingest_long(IngestParams p) {
     if (it >= n_long) break;
     const int64_t d = p.long_list[it];
     const int64_t o0 = p.offsets[d], len = p.offsets[d + 1] - o0;
-    const int l2 = log2_slots(len, 14);
+    const int l2 = log2_slots(len, 13);
     const int ts = 1 << l2;
     const uint32_t passes = (uint32_t)((len + (kLongSlots / 2) - 1) / (kLongSlots / 2));
     for (int q = threadIdx.x; q < kq; q += kLongThreads) num_q[q] = 0ull;
@@ -343,19 +361,31 @@ __global__ void __launch_bounds__(kLongThreads) k_ingest_long(IngestParams p) {
     for (int ph = 0; ph < phases; ++ph) {
       for (uint32_t pass = 0; pass < passes; ++pass) {
         __syncthreads();
-        for (int s = threadIdx.x; s < ts; s += kLongThreads) {
-          keys[s] = kEmpty;
-          cnts[s] = 0u;
-        }
-        __syncthreads();
-        for (int64_t x = threadIdx.x; x < len; x += kLongThreads) {
-          const int32_t t = p.tokens[o0 + x];
-          if ((uint32_t)t >= (uint32_t)p.vocab) {
-            if (pass == 0 && ph == 0) set_err(p.err, kErrBadToken);
-            continue;
+        if (ph == 0 || passes > 1) {  // with one pass, the second DENSE phase reuses the table
+          for (int s = threadIdx.x; s < ts; s += kLongThreads) {
+            keys[s] = kEmpty;
+            cnts[s] = 0u;
           }
-          if (passes > 1 && pass_of((uint32_t)t, passes) != pass) continue;
-          if (!table_insert(keys, cnts, l2, (uint32_t)t)) set_err(p.err, kErrTable);
+          __syncthreads();
+          for (int64_t x0 = threadIdx.x; x0 < len; x0 += kLongUnroll * kLongThreads) {
+            int32_t tk[kLongUnroll];
+#pragma unroll
+            for (int u = 0; u < kLongUnroll; ++u) {
+              const int64_t x = x0 + u * kLongThreads;
+              tk[u] = x < len ? __ldcs(p.tokens + o0 + x) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kLongUnroll; ++u) {
+              if (x0 + u * kLongThreads >= len) break;
+              const int32_t t = tk[u];
+              if ((uint32_t)t >= (uint32_t)p.vocab) {
+                if (pass == 0 && ph == 0) set_err(p.err, kErrBadToken);
+                continue;
+              }
+              if (passes > 1 && pass_of((uint32_t)t, passes) != pass) continue;
+              if (!table_insert(keys, cnts, l2, (uint32_t)t)) set_err(p.err, kErrTable);
+            }
+          }
         }
         __syncthreads();
         for (int s0 = warp * 32; s0 < ts; s0 += nwarps * 32)
@@ -382,9 +412,21 @@ __global__ void __launch_bounds__(kLongThreads) k_ingest_long(IngestParams p) {
   }
 }
 
-// Splits documents into the warp path and the CTA path; validates offsets.
-__global__ void k_classify(const int64_t* off, int64_t n, int32_t* short_list, int32_t* long_list, int32_t* counts,
-                           int32_t* max_len, int32_t* err) {
+// Length classes of the CTA path: class c holds lengths in [2^(9+c), 2^(10+c)), c = 0..7.
+constexpr int kLenClasses = 8;
+__device__ __forceinline__ int len_class(int64_t len) {
+  int c = 0;
+  while (c < kLenClasses - 1 && len >= (2ll << (9 + c))) ++c;
+  return c;
+}
+
+// Counter words of one ingest call (int32).
+constexpr int kCntShort = 0, kCntLong = 1, kCntMaxLen = 2, kCntLongCursor = 3, kCntShortCursor = 4;
+constexpr int kCntClass = 8, kCntClassFill = 16, kCntWords = 32;
+
+// Splits documents into the warp path (appended to short_list) and the CTA path (counted per
+// length class); validates offsets.
+__global__ void k_classify(const int64_t* off, int64_t n, int32_t* short_list, int32_t* counts, int32_t* err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && off[0] != 0) set_err(err, kErrBadOffsets);
   if (i >= n) return;
@@ -397,11 +439,33 @@ __global__ void k_classify(const int64_t* off, int64_t n, int32_t* short_list, i
     set_err(err, kErrTooLong);
     return;
   }
-  atomicMax(max_len, (int32_t)len);
-  if (len <= kShortMax)
-    short_list[atomicAdd(&counts[0], 1)] = (int32_t)i;
-  else
-    long_list[atomicAdd(&counts[1], 1)] = (int32_t)i;
+  atomicMax(&counts[kCntMaxLen], (int32_t)len);
+  if (len <= kShortMax) {
+    short_list[atomicAdd(&counts[kCntShort], 1)] = (int32_t)i;
+  } else {
+    atomicAdd(&counts[kCntLong], 1);
+    atomicAdd(&counts[kCntClass + len_class(len)], 1);
+  }
+}
+
+// Places the CTA-path documents in long_list, longer length classes first, so that the
+// longest documents start first and the short ones fill in behind them.
+__global__ void k_place_long(const int64_t* off, int64_t n, int32_t* long_list, int32_t* counts) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t len = off[i + 1] - off[i];
+  if (len <= kShortMax || len > MRC_MAX_DOC_TOKENS) return;
+  const int c = len_class(len);
+  int32_t base = 0;
+  for (int q = kLenClasses - 1; q > c; --q) base += counts[kCntClass + q];
+  long_list[base + atomicAdd(&counts[kCntClassFill + c], 1)] = (int32_t)i;
+}
+
+void launch_classify(cudaStream_t stream, const int64_t* off, int64_t n, int32_t* short_list, int32_t* long_list,
+                     int32_t* counts, int32_t* err) {
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  k_classify<<<blocks, 256, 0, stream>>>(off, n, short_list, counts, err);
+  k_place_long<<<blocks, 256, 0, stream>>>(off, n, long_list, counts);
 }
 
 __global__ void k_idf(int64_t n_docs, const int32_t* df, int32_t vocab, int32_t weighting, float* idf,
@@ -453,6 +517,26 @@ __global__ void k_pack(const float* sig, int64_t n, int32_t k, int32_t normalize
   }
 }
 
+// Persistent grids: as many CTAs as fit on every SM at once.
+template <int MODE>
+int short_grid(const mrc_ctx* ctx, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ingest_short<MODE>, kWarpsShort * 32, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return ctx->num_sms * per_sm;
+}
+template <int MODE>
+int long_grid(const mrc_ctx* ctx, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ingest_long<MODE>, kLongThreads, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return ctx->num_sms * per_sm;
+}
+
 size_t short_smem(int kq) { return (size_t)kWarpsShort * ((size_t)kShortSlots * 8 + (size_t)kq * 8 + 16); }
 size_t long_smem(int kq) { return (size_t)kq * 8 + 8 + 64 * 4 + 16 + (size_t)kLongSlots * 8; }
 
@@ -465,17 +549,17 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   const size_t list_bytes = sizeof(int32_t) * (size_t)std::max<int64_t>(d.n_docs, 1);
   int32_t* short_list = (int32_t*)ws_get(ctx, "ingest.short", list_bytes, &st);
   int32_t* long_list = (int32_t*)ws_get(ctx, "ingest.long", list_bytes, &st);
-  int32_t* counts = (int32_t*)ws_get(ctx, "ingest.counts", sizeof(int32_t) * 8, &st);
+  int32_t* counts = (int32_t*)ws_get(ctx, "ingest.counts", sizeof(int32_t) * kCntWords, &st);
   if (st != MRC_OK) return cudaErrorMemoryAllocation;
-  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * 8, ctx->stream);
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * kCntWords, ctx->stream);
   if (e != cudaSuccess) return e;
   if (d.n_docs <= 0) return cudaSuccess;
-  k_classify<<<(unsigned)((d.n_docs + 255) / 256), 256, 0, ctx->stream>>>(d.offsets, d.n_docs, short_list, long_list,
-                                                                          counts, counts + 2, d.err);
+  launch_classify(ctx->stream, d.offsets, d.n_docs, short_list, long_list, counts, d.err);
   p.short_list = short_list;
   p.long_list = long_list;
   p.list_counts = counts;
-  p.long_cursor = counts + 3;
+  p.long_cursor = counts + kCntLongCursor;
+  p.short_cursor = counts + kCntShortCursor;
   p.err = d.err;
   const int kq = MODE == kSIG ? p.k : 0;
   const size_t s_smem = short_smem(kq), l_smem = long_smem(kq);
@@ -486,7 +570,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   const double tokens = (double)d.n_tokens;
   cudaEvent_t ev = nullptr;
   {
-    int grid = ctx->num_sms * 2;
+    int grid = short_grid<MODE>(ctx, s_smem);
     const int64_t need = (d.n_docs + kWarpsShort - 1) / kWarpsShort;
     if (need < grid) grid = (int)need;
     std::string nm = std::string(name) + ".short";
@@ -497,7 +581,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
     if (e != cudaSuccess) return e;
   }
   {
-    int grid = ctx->num_sms;
+    int grid = long_grid<MODE>(ctx, l_smem);
     if (d.n_docs < grid) grid = (int)d.n_docs;
     std::string nm = std::string(name) + ".long";
     timing_begin(ctx, nm.c_str(), 0.0, 0.0, &ev);
@@ -589,7 +673,7 @@ cudaError_t launch_densify(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const 
 namespace mrc {
 
 // Signature pass whose scratch (document lists, counters, error word) is supplied by the
-// caller instead of the context's workspace. lists: [2 * cap] int32; counts: [8] int32;
+// caller instead of the context's workspace. lists: [2 * cap] int32; counts: [32] int32;
 // err: [1] int32; all device memory, n_docs <= cap. *host_err receives the error word.
 cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo,
                                      const float* rinv, int32_t k, int32_t bf16_weights, uint64_t seed,
@@ -607,12 +691,10 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
   p.sig = out;
   int32_t* short_list = lists;
   int32_t* long_list = lists + cap;
-  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * 8, ctx->stream);
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * kCntWords, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int32_t), ctx->stream);
   if (e != cudaSuccess) return e;
-  if (d.n_docs > 0)
-    k_classify<<<(unsigned)((d.n_docs + 255) / 256), 256, 0, ctx->stream>>>(d.offsets, d.n_docs, short_list,
-                                                                            long_list, counts, counts + 2, err);
+  if (d.n_docs > 0) launch_classify(ctx->stream, d.offsets, d.n_docs, short_list, long_list, counts, err);
   int32_t h[5] = {0, 0, 0, 0, 0};
   e = cudaMemcpyAsync(h, counts, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h + 4, err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
@@ -626,7 +708,8 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
   p.short_list = short_list;
   p.long_list = long_list;
   p.list_counts = counts;
-  p.long_cursor = counts + 3;
+  p.long_cursor = counts + kCntLongCursor;
+  p.short_cursor = counts + kCntShortCursor;
   p.err = err;
   const size_t s_smem = short_smem(k), l_smem = long_smem(k);
   e = cudaFuncSetAttribute(k_ingest_short<kSIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_smem);
@@ -634,13 +717,13 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
     e = cudaFuncSetAttribute(k_ingest_long<kSIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l_smem);
   if (e != cudaSuccess) return e;
   if (h[0] > 0) {
-    int grid = ctx->num_sms * 2;
+    int grid = short_grid<kSIG>(ctx, s_smem);
     const int need = (h[0] + kWarpsShort - 1) / kWarpsShort;
     if (need < grid) grid = need;
     k_ingest_short<kSIG><<<grid, kWarpsShort * 32, s_smem, ctx->stream>>>(p);
   }
   if (h[1] > 0) {
-    int grid = ctx->num_sms;
+    int grid = long_grid<kSIG>(ctx, l_smem);
     if (h[1] < grid) grid = h[1];
     k_ingest_long<kSIG><<<grid, kLongThreads, l_smem, ctx->stream>>>(p);
   }

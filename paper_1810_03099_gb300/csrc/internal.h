@@ -185,15 +185,14 @@ cudaError_t launch_simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, co
 // the per-document lists, the position of that document in the term's sorted postings.
 cudaError_t launch_sort_postings(mrc_ctx* ctx, const int64_t* cstart, const int32_t* gterm, int32_t n_groups,
                                  const int32_t* post_doc, const float* post_w, const int32_t* post_r,
-                                 const int64_t* doc_off, int32_t* sdoc, float* sw, int64_t* row_pos);
+                                 const int64_t* doc_off, int32_t* sdoc, float* sw, void* row_walk);
 // Exact cosine completion: approximate fp16 head scores H plus exact tail products, candidates
 // >= tau - delta rescored exactly (head from the hi/lo split rows [n x kd], tail exact).
 cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t ldh, const int64_t* row_off,
-                               const int32_t* row_cnt, const int32_t* row_term, const float* row_w,
-                               const int64_t* row_pos, const int64_t* tail_start, const int32_t* post_cnt,
-                               const int32_t* sdoc, const float* sw, const void* head_hi, const void* head_lo,
+                               const int32_t* row_cnt, const void* row_walk, const float* row_w, const int32_t* sdoc,
+                               const float* sw, int64_t n_postings, const void* head_hi, const void* head_lo,
                                int32_t kd, float tau, float delta, mrc_pair* pairs, unsigned long long* count,
-                               int64_t capacity, double work_pairs);
+                               int64_t capacity, double work_pairs, unsigned long long* next_item);
 cudaError_t launch_rescore(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand, int64_t cand_cap,
                            const float* qunit, const float* xunit, int32_t k, float tau, mrc_pair* pairs,
                            unsigned long long* count, int64_t capacity);

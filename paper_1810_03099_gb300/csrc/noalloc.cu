@@ -36,7 +36,7 @@ namespace {
 constexpr int64_t kMaxDocs = MRC_NOALLOC_MAX_DOCS;
 constexpr int kMaxDevices = 64;
 // [0, kMaxDocs): warp-path list; [kMaxDocs, 2 kMaxDocs): CTA-path list;
-// then 8 counters and the error word.
+// then 32 counter words and the error word.
 constexpr int64_t kWords = 2 * kMaxDocs + 64;
 
 static __device__ __align__(256) int32_t g_signature_scratch[kWords];
@@ -100,7 +100,7 @@ extern "C" mrc_status mrc_signature_noalloc(mrc_ctx* ctx, const mrc_index* index
   if (st != MRC_OK) return st;
   int32_t* lists = scratch;
   int32_t* counts = scratch + 2 * kMaxDocs;
-  int32_t* err = counts + 8;
+  int32_t* err = counts + 32;
 
   mrc::DocsDev d{};
   d.n_docs = docs->n_docs;

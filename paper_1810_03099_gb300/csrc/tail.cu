@@ -26,16 +26,19 @@ constexpr float kTailFix = 1073741824.0f;              // 2^30: tail sums stay b
 constexpr float kTailInv = 1.0f / 1073741824.0f;
 constexpr int kSortMax = 4096;                         // postings per sorted group
 constexpr int kSortThreads = 512;
+constexpr int kWalkChunks = 4;                        // 32-posting chunks per lane in flight
 
 // Sorts the postings of each group of consecutive tail terms by (term, document) with a
 // bitonic sort of 64-bit keys in shared memory: key = term-in-group << 44 | doc << 12 |
 // original slot. Segments keep their places, so each term's postings come out sorted by
-// document. Then records row_pos[offsets[doc] + r] = sorted position of that posting.
+// document. Then records, for the posting of term t in slot r of document d,
+// row_walk[offsets[d] + r] = [sorted position + 1, end of t's list): the postings of the
+// documents after d that share t. Positions are 32-bit (fewer than 2^31 postings).
 __global__ void __launch_bounds__(kSortThreads) k_sort_postings(
     const int64_t* __restrict__ cstart, const int32_t* __restrict__ gterm, int32_t n_groups,
     const int32_t* __restrict__ post_doc, const float* __restrict__ post_w, const int32_t* __restrict__ post_r,
     const int64_t* __restrict__ doc_off, int32_t* __restrict__ sdoc, float* __restrict__ sw,
-    int64_t* __restrict__ row_pos) {
+    int2* __restrict__ row_walk) {
   __shared__ unsigned long long keys[kSortMax];
   __shared__ int32_t tst[kSortMax / 2 + 1];
   for (int32_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
@@ -78,14 +81,26 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_postings(
       }
     }
     for (int x = threadIdx.x; x < P; x += kSortThreads) {
-      const int64_t src = p0 + (int64_t)(keys[x] & 4095ull);
-      const int64_t dst = p0 + x;
+      const unsigned long long key = keys[x];
+      const int64_t src = p0 + (int64_t)(key & 4095ull);
+      const int32_t dst = (int32_t)(p0 + x);
       const int32_t d = post_doc[src];
       sdoc[dst] = d;
       sw[dst] = post_w[src];
-      row_pos[doc_off[d] + post_r[src]] = dst;
+      // the postings after this one in its term's list: the documents > d sharing the term
+      row_walk[doc_off[d] + post_r[src]] = make_int2(dst + 1, (int32_t)(p0 + tst[(int)(key >> 44) + 1]));
     }
   }
+}
+
+// Position of the (m+1)-th set bit of mask (which has more than m set bits): the smallest p with
+// popc(mask & bits 0..p) > m, by binary search.
+__device__ __forceinline__ int nth_set_bit(unsigned mask, int m) {
+  int p = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1)
+    if (__popc(mask & (0xffffffffu >> (31 - (p + step - 1)))) <= m) p += step;
+  return p;
 }
 
 // Exact score of one candidate pair (i, j): the head part recomputed from the split head rows
@@ -126,33 +141,46 @@ __device__ __forceinline__ float exact_head(const __half* __restrict__ hhi, cons
 //  1. acc[j] = 0 over the window;
 //  2. for every tail term t of document i, the postings after i's own position in t's
 //     sorted list are exactly the documents j > i sharing t: acc[j] += w_it * w_jt. Each
-//     warp takes 32 of the row's terms at a time (one lane per term holds its metadata),
-//     flattens their postings into one index range (warp prefix sum; a shuffle binary
-//     search maps an index back to its term) and walks it with four loads per lane in
-//     flight, so short lists do not leave lanes idle;
+//     warp takes 32 of the row's terms at a time (one lane per term holds its walk range),
+//     moves the non-empty ones to the low lanes and flattens their postings into one
+//     position range (warp prefix sum). A 32-position chunk finds each lane's term from a
+//     ballot and an OR-reduction of the term starts inside the chunk; four chunks' loads
+//     are in flight per lane, so short lists do not leave lanes idle;
 //  3. scan: H16[i][j] (the fp16 head score from the tensor cores, eight columns per 16-byte
 //     load) + tail >= tau - delta marks a candidate, where delta bounds the head's error;
 //     each candidate's head is recomputed exactly (exact_head) and the pair is kept iff
 //     head + tail >= tau.
-__global__ void __launch_bounds__(kTailThreads) k_cosine_tail(
-    int64_t n, const __half* __restrict__ H, int64_t ldh, const int64_t* __restrict__ row_off,
-    const int32_t* __restrict__ row_cnt, const int32_t* __restrict__ row_term, const float* __restrict__ row_w,
-    const int64_t* __restrict__ row_pos, const int64_t* __restrict__ tail_start, const int32_t* __restrict__ post_cnt,
+__global__ void __launch_bounds__(kTailThreads, 3) k_cosine_tail(
+    int32_t n, const __half* __restrict__ H, int64_t ldh, const int64_t* __restrict__ row_off,
+    const int32_t* __restrict__ row_cnt, const int2* __restrict__ row_walk, const float* __restrict__ row_w,
     const int32_t* __restrict__ sdoc, const float* __restrict__ sw, const __half* __restrict__ hhi,
     const __half* __restrict__ hlo, int32_t kd, float tau, float delta, mrc_pair* pairs,
-    unsigned long long* count, int64_t capacity, int64_t window, int64_t n_windows, int64_t n_items) {
+    unsigned long long* count, int64_t capacity, int32_t window, int32_t n_windows, int64_t n_items,
+    unsigned long long* next_item) {
   extern __shared__ int32_t acc[];
+  __shared__ long long s_item;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float cand_tau = tau - delta;
-  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-    const int64_t i = item / n_windows;
-    const int64_t w = item % n_windows;
-    const int64_t base = w * window;  // a multiple of 8 (window is)
-    const int64_t lo = max(i + 1, base), hi = min(n, base + window);
+  for (;;) {
+    // work items are taken in row order as CTAs free up: rows differ in cost by orders of
+    // magnitude (long documents, early rows), so a static split leaves CTAs idle
+    __syncthreads();  // the previous item's scan is done with acc and s_item
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(next_item, 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= n_items) break;  // block-uniform
+    const int32_t i = (int32_t)(item / n_windows);
+    const int32_t base = (int32_t)(item % n_windows) * window;  // a multiple of 8 (window is)
+    const int32_t lo = max(i + 1, base), hi = min(n, base + window);
     if (lo >= hi) continue;  // block-uniform
-    __syncthreads();  // the previous item's scan is done with acc
-    const int64_t a0 = (lo - base) & ~7ll, a1 = hi - base;  // accumulator range touched, 8-aligned start
-    for (int64_t x = a0 + 4 * threadIdx.x; x < a1; x += 4 * kTailThreads)
+    const __half* hrow = H + (int64_t)i * ldh;
+    {  // pull this item's head scores toward L2 while the tail sums are built (one 128-byte line
+       // per thread covers 32768 columns, the largest window)
+      const int32_t at = (lo & ~63) + 64 * (int32_t)threadIdx.x;
+      if (at < hi) asm volatile("prefetch.global.L2 [%0];" ::"l"(hrow + at));
+    }
+    const int32_t a0 = (lo - base) & ~7, a1 = hi - base;  // accumulator range touched, 8-aligned start
+    for (int32_t x = a0 + 4 * (int32_t)threadIdx.x; x < a1; x += 4 * kTailThreads)
       *reinterpret_cast<int4*>(acc + x) = make_int4(0, 0, 0, 0);
     __syncthreads();
     const int32_t nt = row_cnt[i];
@@ -160,61 +188,67 @@ __global__ void __launch_bounds__(kTailThreads) k_cosine_tail(
     for (int32_t b0 = warp; b0 < nt; b0 += 32 * kTailWarps) {
       // lane l holds term b0 + 16 l: its remaining postings [st, st + cnt) (documents > i)
       const int32_t r = b0 + kTailWarps * lane;
-      int64_t st = 0;
-      int32_t cnt = 0;
+      int32_t st = 0, cnt = 0;
       float wi = 0.f;
       if (r < nt) {
-        const int32_t t = row_term[ro + r];
+        const int2 wk = row_walk[ro + r];
+        st = wk.x;
+        cnt = wk.y - wk.x;
         wi = row_w[ro + r];
-        st = row_pos[ro + r] + 1;
-        cnt = (int32_t)(tail_start[t] + post_cnt[t] - st);
       }
-      // flatten the batch: posting f of the batch belongs to the last lane q with excl_q <= f
+      // move the terms with postings left to the low lanes, in order
+      const unsigned live = __ballot_sync(kFull, cnt > 0);
+      const int nlive = __popc(live);
+      if (nlive == 0) continue;  // warp-uniform
+      const int from = nth_set_bit(live, lane < nlive ? lane : 0);
+      st = __shfl_sync(kFull, st, from);
+      cnt = __shfl_sync(kFull, cnt, from);
+      wi = __shfl_sync(kFull, wi, from);
+      if (lane >= nlive) cnt = 0;
+      // flatten: live term k owns positions [ex_k, ex_k + cnt_k) of the warp's posting range
       int32_t incl = cnt;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int32_t y = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += y;
       }
-      const int32_t excl = incl - cnt;
       const int32_t total = __shfl_sync(kFull, incl, 31);
-      for (int32_t f0 = 0; f0 < total; f0 += 4 * 32) {
-        int32_t jd[4];
-        float wv[4];
+      const int32_t ex = lane < nlive ? incl - cnt : 0x7fffffff;  // strictly increasing over live lanes
+      for (int32_t f0 = 0; f0 < total; f0 += 32 * kWalkChunks) {
+        int32_t jd[kWalkChunks];
+        float wv[kWalkChunks];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int32_t f = f0 + 32 * u + lane;
-          int q = 0;
-#pragma unroll
-          for (int step = 16; step > 0; step >>= 1) {
-            const int cand = q + step;
-            const int32_t ex = __shfl_sync(kFull, excl, cand & 31);
-            if (cand < 32 && ex <= f) q = cand;
-          }
-          const int64_t sq = __shfl_sync(kFull, st, q);
-          const int32_t eq = __shfl_sync(kFull, excl, q);
-          const float wq = __shfl_sync(kFull, wi, q);
+        for (int u = 0; u < kWalkChunks; ++u) {
+          const int32_t cs = f0 + 32 * u;  // this chunk's first position (warp-uniform)
           jd[u] = -1;
           wv[u] = 0.f;
-          if (f < total) {
-            const int64_t x = sq + (f - eq);
-            jd[u] = sdoc[x];
-            wv[u] = wq * sw[x];
+          if (cs < total) {
+            // owner of position cs + lane: the owner of cs plus the terms starting in (cs, cs + lane]
+            const int kb = __popc(__ballot_sync(kFull, ex <= cs)) - 1;
+            const int32_t dlt = ex - cs;
+            const unsigned starts = __reduce_or_sync(kFull, (dlt > 0 && dlt < 32) ? (1u << dlt) : 0u);
+            const int k = kb + __popc(starts & (0xffffffffu >> (31 - lane)));
+            const int32_t sk = __shfl_sync(kFull, st, k), ek = __shfl_sync(kFull, ex, k);
+            const float wk = __shfl_sync(kFull, wi, k);
+            const int32_t f = cs + lane;
+            if (f < total) {
+              const int32_t x = sk + (f - ek);
+              jd[u] = sdoc[x];
+              wv[u] = wk * sw[x];
+            }
           }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < kWalkChunks; ++u)
           if (jd[u] >= lo && jd[u] < hi) atomicAdd(&acc[jd[u] - base], __float2int_rn(wv[u] * kTailFix));
       }
     }
     __syncthreads();
     // scan: each lane takes eight consecutive columns (one 16-byte load of H16, in the row's
     // ldh >= round8(n) padding at the end, so never past the row)
-    const __half* hrow = H + i * ldh;
-    for (int64_t g0 = base + a0 + 8 * (int64_t)warp * 32; g0 < hi; g0 += 8 * kTailThreads) {
-      const int64_t g = g0 + 8 * lane;
+    for (int32_t g0 = base + a0 + 256 * warp; g0 < hi; g0 += 8 * kTailThreads) {
+      const int32_t g = g0 + 8 * lane;
       uint32_t mask = 0;
-      float sv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (g < hi) {
         const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(hrow + g));
         const __half2* h2 = reinterpret_cast<const __half2*>(&raw);
@@ -224,11 +258,10 @@ __global__ void __launch_bounds__(kTailThreads) k_cosine_tail(
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const float2 hf = __half22float2(h2[u]);
-          sv[2 * u] = (float)tv[2 * u] * kTailInv;
-          sv[2 * u + 1] = (float)tv[2 * u + 1] * kTailInv;
-          const int64_t ja = g + 2 * u, jb = ja + 1;
-          if (ja >= lo && ja < hi && hf.x + sv[2 * u] >= cand_tau) mask |= 1u << (2 * u);
-          if (jb >= lo && jb < hi && hf.y + sv[2 * u + 1] >= cand_tau) mask |= 1u << (2 * u + 1);
+          const int32_t ja = g + 2 * u;
+          if (ja >= lo && ja < hi && hf.x + (float)tv[2 * u] * kTailInv >= cand_tau) mask |= 1u << (2 * u);
+          if (ja + 1 >= lo && ja + 1 < hi && hf.y + (float)tv[2 * u + 1] * kTailInv >= cand_tau)
+            mask |= 2u << (2 * u);
         }
       }
       unsigned todo = __ballot_sync(kFull, mask != 0);
@@ -236,24 +269,17 @@ __global__ void __launch_bounds__(kTailThreads) k_cosine_tail(
         const int src = __ffs(todo) - 1;
         todo &= todo - 1;
         uint32_t m = __shfl_sync(kFull, mask, src);
-        const int64_t gs = __shfl_sync(kFull, g, src);
+        const int32_t gs = __shfl_sync(kFull, g, src);
         while (m) {
-          const int e = __ffs(m) - 1;
+          const int32_t j = gs + __ffs(m) - 1;
           m &= m - 1;
-          const int64_t j = gs + e;
-          float tail = 0.f;
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const float y = __shfl_sync(kFull, sv[u], src);
-            if (u == e) tail = y;
-          }
-          const float s = exact_head(hhi, hlo, kd, i, j, lane) + tail;
+          const float s = exact_head(hhi, hlo, kd, i, j, lane) + (float)acc[j - base] * kTailInv;
           if (lane == 0 && s >= tau) {
             const unsigned long long at = atomicAdd(count, 1ull);
             if (at < (unsigned long long)capacity) {
               mrc_pair pr;
-              pr.i = (int32_t)i;
-              pr.j = (int32_t)j;
+              pr.i = i;
+              pr.j = j;
               pr.score = s;
               pairs[at] = pr;
             }
@@ -293,29 +319,33 @@ __global__ void k_rescore(const mrc_pair* __restrict__ cand, const unsigned long
 
 cudaError_t launch_sort_postings(mrc_ctx* ctx, const int64_t* cstart, const int32_t* gterm, int32_t n_groups,
                                  const int32_t* post_doc, const float* post_w, const int32_t* post_r,
-                                 const int64_t* doc_off, int32_t* sdoc, float* sw, int64_t* row_pos) {
+                                 const int64_t* doc_off, int32_t* sdoc, float* sw, void* row_walk) {
   if (n_groups <= 0) return cudaSuccess;
   int grid = ctx->num_sms * 3;
   if (n_groups < grid) grid = n_groups;
   cudaEvent_t ev = nullptr;
   timing_begin(ctx, "sort_postings", 0.0, 0.0, &ev);
   k_sort_postings<<<grid, kSortThreads, 0, ctx->stream>>>(cstart, gterm, n_groups, post_doc, post_w, post_r, doc_off,
-                                                           sdoc, sw, row_pos);
+                                                           sdoc, sw,
+                                                           reinterpret_cast<int2*>(row_walk));
   timing_end(ctx, ev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t ldh, const int64_t* row_off,
-                               const int32_t* row_cnt, const int32_t* row_term, const float* row_w,
-                               const int64_t* row_pos, const int64_t* tail_start, const int32_t* post_cnt,
-                               const int32_t* sdoc, const float* sw, const void* head_hi, const void* head_lo,
+                               const int32_t* row_cnt, const void* row_walk, const float* row_w, const int32_t* sdoc,
+                               const float* sw, int64_t n_postings, const void* head_hi, const void* head_lo,
                                int32_t kd, float tau, float delta, mrc_pair* pairs, unsigned long long* count,
-                               int64_t capacity, double work_pairs) {
+                               int64_t capacity, double work_pairs, unsigned long long* next_item) {
   if (n <= 1) return cudaSuccess;
-  if ((ldh & 7) || ldh < (n + 7) / 8 * 8 || (kd & 63) || kd <= 0) return cudaErrorInvalidValue;
+  if (!next_item) return cudaErrorInvalidValue;
+  // documents and postings are indexed in 32 bits
+  if ((ldh & 7) || ldh < (n + 7) / 8 * 8 || (kd & 63) || kd <= 0 || n >= (1ll << 31) - 64 ||
+      n_postings >= (1ll << 31) - 64)
+    return cudaErrorInvalidValue;
   const int64_t n8 = (n + 7) / 8 * 8;
-  const int64_t window = n8 < kMaxWindow ? n8 : kMaxWindow;  // a multiple of 8
-  const int64_t n_windows = (n + window - 1) / window;
+  const int32_t window = (int32_t)(n8 < kMaxWindow ? n8 : kMaxWindow);  // a multiple of 8
+  const int32_t n_windows = (int32_t)((n + window - 1) / window);
   const int64_t n_items = n * n_windows;
   const size_t smem = sizeof(int32_t) * (size_t)window;
   cudaError_t e = cudaFuncSetAttribute(k_cosine_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -324,14 +354,16 @@ cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cosine_tail, kTailThreads, smem);
   int64_t grid = (int64_t)ctx->num_sms * (per_sm > 0 ? per_sm : 1);
   if (n_items < grid) grid = n_items;
+  e = cudaMemsetAsync(next_item, 0, sizeof(unsigned long long), ctx->stream);
+  if (e != cudaSuccess) return e;
   cudaEvent_t ev = nullptr;
   // algorithmic bytes: the upper triangle of the fp16 head scores read once; flops: 2 per
   // tail posting product
   timing_begin(ctx, "cosine_tail", 2.0 * (double)n * (double)(n - 1) / 2.0, 2.0 * work_pairs, &ev);
   k_cosine_tail<<<(unsigned)grid, kTailThreads, smem, ctx->stream>>>(
-      n, reinterpret_cast<const __half*>(H16), ldh, row_off, row_cnt, row_term, row_w, row_pos, tail_start, post_cnt,
-      sdoc, sw, reinterpret_cast<const __half*>(head_hi), reinterpret_cast<const __half*>(head_lo), kd, tau, delta,
-      pairs, count, capacity, window, n_windows, n_items);
+      (int32_t)n, reinterpret_cast<const __half*>(H16), ldh, row_off, row_cnt, reinterpret_cast<const int2*>(row_walk),
+      row_w, sdoc, sw, reinterpret_cast<const __half*>(head_hi), reinterpret_cast<const __half*>(head_lo), kd, tau, delta,
+      pairs, count, capacity, window, n_windows, n_items, next_item);
   timing_end(ctx, ev);
   return cudaGetLastError();
 }
