@@ -674,9 +674,11 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
 
   // document frequencies within these documents decide the head/tail split
   int32_t* df = (int32_t*)ws_get(ctx, "cos.df", sizeof(int32_t) * V, &st);
+  unsigned long long* d_norm = (unsigned long long*)ws_get(ctx, "cos.norm", sizeof(unsigned long long) * N, &st);
   if (st != MRC_OK) return st;
   cudaMemsetAsync(df, 0, sizeof(int32_t) * V, ctx->stream);
-  cudaError_t e = launch_df(ctx, d, df, V);
+  const float* wid = index->params.weighting == MRC_WEIGHT_TFIDF ? index->idf : nullptr;
+  cudaError_t e = launch_df_norm(ctx, d, df, V, wid, d_norm);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "df pass");
   std::vector<int32_t> hdf(V);
   e = cudaMemcpyAsync(hdf.data(), df, sizeof(int32_t) * V, cudaMemcpyDeviceToHost, ctx->stream);
@@ -705,22 +707,19 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
       cstart.push_back(n_post);
       tail_work += (double)hdf[t] * (double)(hdf[t] - 1) / 2.0;
     }
-  // sort groups: consecutive tail terms holding <= 4096 postings together
   const int32_t n_tail = (int32_t)cstart.size() - 1;
-  std::vector<int32_t> gterm(1, 0);
-  {
-    int64_t in_group = 0;
-    for (int32_t c = 0; c < n_tail; ++c) {
-      const int64_t len = cstart[c + 1] - cstart[c];
-      if (in_group > 0 && in_group + len > 4096) {
-        gterm.push_back(c);
-        in_group = 0;
-      }
-      in_group += len;
+  // tail terms by list length: up to 32 postings (ranked by one warp's shuffles) and longer
+  std::vector<int32_t> rank_terms(std::max<int32_t>(n_tail, 1));
+  int32_t n_small = 0, max_m = 0;
+  for (int32_t c = 0; c < n_tail; ++c)
+    if (cstart[c + 1] - cstart[c] <= 32) rank_terms[n_small++] = c;
+  for (int32_t c = 0, b = n_small; c < n_tail; ++c) {
+    const int32_t m = (int32_t)(cstart[c + 1] - cstart[c]);
+    if (m > 32) {
+      rank_terms[b++] = c;
+      max_m = std::max(max_m, m);
     }
-    if (n_tail > 0) gterm.push_back(n_tail);
   }
-  const int32_t n_groups = (int32_t)gterm.size() - 1;
   if (n_post >= (1ll << 31) - 64)
     return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more than 2^31 tail postings");
   const int64_t ldh = (N + 7) / 8 * 8;
@@ -737,9 +736,8 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   float* d_sw = (float*)ws_get(ctx, "cos.sw", sizeof(float) * (size_t)std::max<int64_t>(n_post, 1), &st);
   void* d_rwalk = ws_get(ctx, "cos.rwalk", 8 * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
   int64_t* d_cstart = (int64_t*)ws_get(ctx, "cos.cstart", sizeof(int64_t) * cstart.size(), &st);
-  int32_t* d_gterm = (int32_t*)ws_get(ctx, "cos.gterm", sizeof(int32_t) * gterm.size(), &st);
+  int32_t* d_rank_terms = (int32_t*)ws_get(ctx, "cos.rterms", sizeof(int32_t) * rank_terms.size(), &st);
   int32_t* d_rcnt = (int32_t*)ws_get(ctx, "cos.rcnt", sizeof(int32_t) * (size_t)N, &st);
-  int32_t* d_rterm = (int32_t*)ws_get(ctx, "cos.rterm", sizeof(int32_t) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
   float* d_rw = (float*)ws_get(ctx, "cos.rw", sizeof(float) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
   void* d_hhi = ws_get(ctx, "cos.hhi", 2 * (size_t)N * kd, &st);
   void* d_hlo = ws_get(ctx, "cos.hlo", 2 * (size_t)N * kd, &st);
@@ -752,7 +750,8 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_cstart, cstart.data(), sizeof(int64_t) * cstart.size(), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_gterm, gterm.data(), sizeof(int32_t) * gterm.size(), cudaMemcpyHostToDevice, ctx->stream);
+    e = cudaMemcpyAsync(d_rank_terms, rank_terms.data(), sizeof(int32_t) * rank_terms.size(), cudaMemcpyHostToDevice,
+                        ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_tfill, 0, sizeof(int32_t) * V, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_hhi, 0, 2 * (size_t)N * kd, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_hlo, 0, 2 * (size_t)N * kd, ctx->stream);
@@ -760,7 +759,7 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
 
   // unit weights: dense head operands and tail postings
   DenseOut o{};
-  o.idf = index->params.weighting == MRC_WEIGHT_TFIDF ? index->idf : nullptr;
+  o.idf = wid;
   o.colmap = d_colmap;
   o.kd = kd;
   o.head_hi = d_hhi;
@@ -771,11 +770,12 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   o.post_w = d_pw;
   o.post_r = d_pr;
   o.row_cnt = d_rcnt;
-  o.row_term = d_rterm;
+  o.norm = d_norm;
   o.row_w = d_rw;
   e = launch_densify(ctx, d, V, index->tinfo, o);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "densify");
-  e = launch_sort_postings(ctx, d_cstart, d_gterm, n_groups, d_pdoc, d_pw, d_pr, d.offsets, d_sdoc, d_sw, d_rwalk);
+  e = launch_rank_postings(ctx, d_cstart, d_rank_terms, n_small, d_rank_terms + n_small, n_tail - n_small, max_m, d_pdoc,
+                           d_pw, d_pr, d.offsets, d_sdoc, d_sw, d_rwalk);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sorting postings");
 
   // head: single-fp16 tensor-core GEMM of the unit head columns, stored as fp16. Its error

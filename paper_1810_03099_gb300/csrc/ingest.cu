@@ -48,7 +48,7 @@ constexpr int kLongUnroll = 4;      // token loads per thread in flight (CTA pat
 constexpr float kFix = 4194304.0f;  // 2^22
 constexpr float kInvFix = 1.0f / 4194304.0f;
 
-enum Mode { kDF = 0, kSIG = 1, kDENSE = 2 };
+enum Mode { kDF = 0, kSIG = 1, kDENSE = 2, kDFN = 3 };
 
 __device__ __forceinline__ uint32_t slot_of(uint32_t t, int log2ts) { return (t * 0x9E3779B1u) >> (32 - log2ts); }
 __device__ __forceinline__ uint32_t pass_of(uint32_t t, uint32_t passes) {
@@ -78,6 +78,12 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 }
 
 __device__ __forceinline__ unsigned long long to_fix(float x) { return __float2ull_rn(x * kFix); }
+
+// 1 / |w| from the fixed-point squared norm (0 for an empty document).
+__device__ __forceinline__ float inv_norm_of(unsigned long long norm_q) {
+  const float n2 = (float)norm_q * kInvFix;
+  return n2 > 0.f ? 1.0f / sqrtf(n2) : 0.f;
+}
 
 __device__ __forceinline__ bool table_insert(uint32_t* keys, uint32_t* cnts, int log2ts, uint32_t t) {
   const uint32_t mask = (1u << log2ts) - 1u;
@@ -109,8 +115,10 @@ struct IngestParams {
   int32_t* long_cursor;        // dynamic grab of long documents
   int32_t* short_cursor;       // dynamic grab of short documents (one warp each)
   int32_t* err;
-  // DF
+  // DF (and DFN: df plus squared norms)
   int32_t* df;
+  const float* norm_idf;
+  unsigned long long* norm_out;
   // SIG
   const TermInfo* tinfo;
   const float* rinv;
@@ -131,15 +139,21 @@ struct Acc {
 // Process one warp-chunk of 32 table slots [s0, s0 + 32).
 template <int MODE>
 __device__ __forceinline__ void chunk(const IngestParams& p, const uint32_t* keys, const uint32_t* cnts, int s0,
-                                      int limit, int lane, unsigned long long* num_q, Acc& a, int dense_phase,
-                                      int64_t doc, float inv_norm, int32_t* row_cnt_s, int64_t row_base) {
+                                      int limit, int lane, unsigned long long* num_q, Acc& a, int64_t doc,
+                                      float inv_norm, int32_t* row_cnt_s, int64_t row_base) {
   const uint32_t key = s0 + lane < limit ? keys[s0 + lane] : kEmpty;
   const bool valid = key != kEmpty;
   const unsigned any = __ballot_sync(kFull, valid);
   if (any == 0u) return;
   const uint32_t c = valid ? cnts[s0 + lane] : 0u;
-  if (MODE == kDF) {
-    if (valid) atomicAdd(&p.df[key], 1);
+  if (MODE == kDF || MODE == kDFN) {
+    if (valid) {
+      atomicAdd(&p.df[key], 1);
+      if (MODE == kDFN) {
+        const float w = p.norm_idf ? (float)c * __ldg(p.norm_idf + key) : (float)c;
+        a.norm += to_fix(w * w);
+      }
+    }
     return;
   }
   if (MODE == kSIG) {
@@ -168,10 +182,6 @@ __device__ __forceinline__ void chunk(const IngestParams& p, const uint32_t* key
   // DENSE
   if (!valid) return;
   const float w = p.dense.idf ? (float)c * __ldg(p.dense.idf + key) : (float)c;
-  if (dense_phase == 0) {
-    a.norm += to_fix(w * w);
-    return;
-  }
   const float u = w * inv_norm;
   const int32_t code = p.dense.colmap[key];
   if (code >= 0) {
@@ -186,7 +196,6 @@ __device__ __forceinline__ void chunk(const IngestParams& p, const uint32_t* key
     p.dense.post_doc[pos] = (int32_t)doc;
     p.dense.post_w[pos] = u;
     p.dense.post_r[pos] = r;
-    p.dense.row_term[row_base + r] = (int32_t)key;
     p.dense.row_w[row_base + r] = u;
   }
 }
@@ -306,18 +315,14 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
     }
     Acc a{0ull, 0u, 0u};
     float inv_norm = 0.f;
-    const int phases = MODE == kDENSE ? 2 : 1;
-    for (int ph = 0; ph < phases; ++ph) {
-      for (int s0 = 0; s0 < nnz; s0 += 32)
-        chunk<MODE>(p, keys, cnts, s0, nnz, lane, num_q, a, ph, d, inv_norm, row_cnt_s, o0);
-      if (MODE == kDENSE && ph == 0) {
-        const unsigned long long nq = warp_sum(a.norm);
-        const float n2 = (float)nq * kInvFix;
-        inv_norm = n2 > 0.f ? 1.0f / sqrtf(n2) : 0.f;
-      }
-    }
+    if (MODE == kDENSE) inv_norm = inv_norm_of(p.dense.norm[d]);
+    for (int s0 = 0; s0 < nnz; s0 += 32) chunk<MODE>(p, keys, cnts, s0, nnz, lane, num_q, a, d, inv_norm, row_cnt_s, o0);
     __syncwarp();
     if (MODE == kSIG) finalize_sig(p, d, len, warp_sum(a.norm), num_q, a.plo, a.phi, lane);
+    if (MODE == kDFN) {
+      const unsigned long long nq = warp_sum(a.norm);
+      if (lane == 0) p.norm_out[d] = nq;
+    }
     if (MODE == kDENSE && lane == 0) p.dense.row_cnt[d] = *row_cnt_s;
     __syncwarp();
     it = __shfl_sync(kFull, next, 0);
@@ -357,47 +362,40 @@ __global__ void __launch_bounds__(kLongThreads) k_ingest_long(IngestParams p) {
     }
     Acc a{0ull, 0u, 0u};
     float inv_norm = 0.f;
-    const int phases = MODE == kDENSE ? 2 : 1;
-    for (int ph = 0; ph < phases; ++ph) {
-      for (uint32_t pass = 0; pass < passes; ++pass) {
-        __syncthreads();
-        if (ph == 0 || passes > 1) {  // with one pass, the second DENSE phase reuses the table
-          for (int s = threadIdx.x; s < ts; s += kLongThreads) {
-            keys[s] = kEmpty;
-            cnts[s] = 0u;
-          }
-          __syncthreads();
-          for (int64_t x0 = threadIdx.x; x0 < len; x0 += kLongUnroll * kLongThreads) {
-            int32_t tk[kLongUnroll];
+    if (MODE == kDENSE) inv_norm = inv_norm_of(p.dense.norm[d]);
+    for (uint32_t pass = 0; pass < passes; ++pass) {
+      __syncthreads();
+      for (int s = threadIdx.x; s < ts; s += kLongThreads) {
+        keys[s] = kEmpty;
+        cnts[s] = 0u;
+      }
+      __syncthreads();
+      for (int64_t x0 = threadIdx.x; x0 < len; x0 += kLongUnroll * kLongThreads) {
+        int32_t tk[kLongUnroll];  // kLongUnroll token loads in flight per thread
 #pragma unroll
-            for (int u = 0; u < kLongUnroll; ++u) {
-              const int64_t x = x0 + u * kLongThreads;
-              tk[u] = x < len ? __ldcs(p.tokens + o0 + x) : -1;
-            }
-#pragma unroll
-            for (int u = 0; u < kLongUnroll; ++u) {
-              if (x0 + u * kLongThreads >= len) break;
-              const int32_t t = tk[u];
-              if ((uint32_t)t >= (uint32_t)p.vocab) {
-                if (pass == 0 && ph == 0) set_err(p.err, kErrBadToken);
-                continue;
-              }
-              if (passes > 1 && pass_of((uint32_t)t, passes) != pass) continue;
-              if (!table_insert(keys, cnts, l2, (uint32_t)t)) set_err(p.err, kErrTable);
-            }
-          }
+        for (int u = 0; u < kLongUnroll; ++u) {
+          const int64_t x = x0 + u * kLongThreads;
+          tk[u] = x < len ? __ldcs(p.tokens + o0 + x) : -1;
         }
-        __syncthreads();
-        for (int s0 = warp * 32; s0 < ts; s0 += nwarps * 32)
-          chunk<MODE>(p, keys, cnts, s0, ts, lane, num_q, a, ph, d, inv_norm, &misc[1], o0);
+#pragma unroll
+        for (int u = 0; u < kLongUnroll; ++u) {
+          if (x0 + u * kLongThreads >= len) break;
+          const int32_t t = tk[u];
+          if ((uint32_t)t >= (uint32_t)p.vocab) {
+            if (pass == 0) set_err(p.err, kErrBadToken);
+            continue;
+          }
+          if (passes > 1 && pass_of((uint32_t)t, passes) != pass) continue;
+          if (!table_insert(keys, cnts, l2, (uint32_t)t)) set_err(p.err, kErrTable);
+        }
       }
-      if (MODE == kDENSE && ph == 0) {
-        const unsigned long long nq = warp_sum(a.norm);
-        if (lane == 0) atomicAdd(norm_s, nq);
-        __syncthreads();
-        const float n2 = (float)(*norm_s) * kInvFix;
-        inv_norm = n2 > 0.f ? 1.0f / sqrtf(n2) : 0.f;
-      }
+      __syncthreads();
+      for (int s0 = warp * 32; s0 < ts; s0 += nwarps * 32)
+        chunk<MODE>(p, keys, cnts, s0, ts, lane, num_q, a, d, inv_norm, &misc[1], o0);
+    }
+    if (MODE == kDFN) {
+      const unsigned long long nq = warp_sum(a.norm);
+      if (lane == 0) atomicAdd(norm_s, nq);
     }
     if (MODE == kSIG) {
       const unsigned long long nq = warp_sum(a.norm);
@@ -408,6 +406,7 @@ __global__ void __launch_bounds__(kLongThreads) k_ingest_long(IngestParams p) {
     __syncthreads();
     if (MODE == kSIG && warp == 0) finalize_sig(p, d, len, *norm_s, num_q, P[lane], P[lane + 32], lane);
     if (MODE == kDENSE && threadIdx.x == 0) p.dense.row_cnt[d] = misc[1];
+    if (MODE == kDFN && threadIdx.x == 0) p.norm_out[d] = *norm_s;
     __syncthreads();
   }
 }
@@ -607,6 +606,16 @@ cudaError_t launch_df(mrc_ctx* ctx, const DocsDev& d, int32_t* df, int32_t vocab
   p.vocab = vocab;
   p.df = df;
   return run_ingest<kDF>(ctx, d, p, "ingest_df", 4.0, 8.0);
+}
+
+cudaError_t launch_df_norm(mrc_ctx* ctx, const DocsDev& d, int32_t* df, int32_t vocab, const float* idf,
+                           unsigned long long* norm) {
+  IngestParams p = base_params(d);
+  p.vocab = vocab;
+  p.df = df;
+  p.norm_idf = idf;
+  p.norm_out = norm;
+  return run_ingest<kDFN>(ctx, d, p, "ingest_df_norm", 4.0, 16.0);
 }
 
 cudaError_t launch_idf(mrc_ctx* ctx, int64_t n_docs, const int32_t* df, int32_t vocab, int32_t weighting, float* idf,

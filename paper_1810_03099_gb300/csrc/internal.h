@@ -112,6 +112,10 @@ struct DocsDev {
 
 // ingest.cu
 cudaError_t launch_df(mrc_ctx* ctx, const DocsDev& d, int32_t* df, int32_t vocab);
+// The df pass plus each document's squared weight norm |w|^2 (w = count * idf, or count when
+// idf is NULL) as a 2^-22 fixed-point sum, written to norm[doc] for every document.
+cudaError_t launch_df_norm(mrc_ctx* ctx, const DocsDev& d, int32_t* df, int32_t vocab, const float* idf,
+                           unsigned long long* norm);
 cudaError_t launch_idf(mrc_ctx* ctx, int64_t n_docs, const int32_t* df, int32_t vocab, int32_t weighting,
                        float* idf, TermInfo* tinfo);
 struct SigOut {
@@ -143,8 +147,8 @@ struct DenseOut {
   float* post_w;              // [n_post]
   int32_t* post_r;            // [n_post] index of the posting's term in its document's tail list
   int32_t* row_cnt;           // [n] tail terms of each doc
-  int32_t* row_term;          // [n_tokens] at the doc's token offsets
-  float* row_w;               // [n_tokens]
+  float* row_w;               // [n_tokens] at the doc's token offsets: unit weight of its r-th tail term
+  const unsigned long long* norm;  // [n] squared norms, 2^-22 fixed point (from launch_df_norm)
 };
 cudaError_t launch_densify(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo, const DenseOut& out);
 
@@ -180,12 +184,14 @@ cudaError_t launch_simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, co
                                  int32_t hmax, mrc_pair* pairs, unsigned long long* count, int64_t capacity);
 
 // tail.cu
-// Sorts every tail term's postings by document (groups of consecutive tail terms holding
-// <= 4096 postings each) into sdoc/sw and records, for each (document, tail term) entry of
-// the per-document lists, the position of that document in the term's sorted postings.
-cudaError_t launch_sort_postings(mrc_ctx* ctx, const int64_t* cstart, const int32_t* gterm, int32_t n_groups,
-                                 const int32_t* post_doc, const float* post_w, const int32_t* post_r,
-                                 const int64_t* doc_off, int32_t* sdoc, float* sw, void* row_walk);
+// Orders every tail term's postings by document into sdoc/sw and records, for each
+// (document, tail term) entry of the per-document lists, the range of the term's postings that
+// follow that document. small_terms: tail terms (indices into cstart) with at most 32
+// postings; big_terms: the others, each with at most max_m postings.
+cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int32_t* small_terms, int32_t n_small,
+                                 const int32_t* big_terms, int32_t n_big, int32_t max_m, const int32_t* post_doc,
+                                 const float* post_w, const int32_t* post_r, const int64_t* doc_off, int32_t* sdoc,
+                                 float* sw, void* row_walk);
 // Exact cosine completion: approximate fp16 head scores H plus exact tail products, candidates
 // >= tau - delta rescored exactly (head from the hi/lo split rows [n x kd], tail exact).
 cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t ldh, const int64_t* row_off,

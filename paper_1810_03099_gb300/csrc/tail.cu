@@ -24,72 +24,85 @@ constexpr int kTailWarps = kTailThreads / 32;
 constexpr int kMaxWindow = 32768;                      // columns per work item (128 KB of accumulators)
 constexpr float kTailFix = 1073741824.0f;              // 2^30: tail sums stay below 2^31
 constexpr float kTailInv = 1.0f / 1073741824.0f;
-constexpr int kSortMax = 4096;                         // postings per sorted group
-constexpr int kSortThreads = 512;
+constexpr int kRankWarps = 8;                          // warps per CTA of the long-list ranking
 constexpr int kWalkChunks = 4;                        // 32-posting chunks per lane in flight
 
-// Sorts the postings of each group of consecutive tail terms by (term, document) with a
-// bitonic sort of 64-bit keys in shared memory: key = term-in-group << 44 | doc << 12 |
-// original slot. Segments keep their places, so each term's postings come out sorted by
-// document. Then records, for the posting of term t in slot r of document d,
-// row_walk[offsets[d] + r] = [sorted position + 1, end of t's list): the postings of the
-// documents after d that share t. Positions are 32-bit (fewer than 2^31 postings).
-__global__ void __launch_bounds__(kSortThreads) k_sort_postings(
-    const int64_t* __restrict__ cstart, const int32_t* __restrict__ gterm, int32_t n_groups,
+// Orders each tail term's postings by document: a posting's rank in its list is the number
+// of postings of the same term with a smaller document id (ids in one list are distinct, so
+// the ranks are a permutation). One warp per term. Then writes the sorted list and, for the
+// posting of term t in slot r of document d, row_walk[offsets[d] + r] = [sorted position + 1,
+// end of t's list): the postings of the documents after d that share t. Positions are 32-bit
+// (fewer than 2^31 postings).
+__device__ __forceinline__ void put_ranked(int32_t at, int32_t end, int32_t d, float w, int32_t r, int64_t off,
+                                           int32_t* __restrict__ sdoc, float* __restrict__ sw,
+                                           int2* __restrict__ row_walk) {
+  sdoc[at] = d;
+  sw[at] = w;
+  row_walk[off + r] = make_int2(at + 1, end);
+}
+
+// Lists of at most 32 postings: one posting per lane, ranks through shuffles. Every load of a
+// posting (document, weight, slot, the document's offset) is issued before the ranking.
+__global__ void __launch_bounds__(256) k_rank_small(const int64_t* __restrict__ cstart,
+                                                    const int32_t* __restrict__ terms, int32_t n_terms,
+                                                    const int32_t* __restrict__ post_doc,
+                                                    const float* __restrict__ post_w,
+                                                    const int32_t* __restrict__ post_r,
+                                                    const int64_t* __restrict__ doc_off, int32_t* __restrict__ sdoc,
+                                                    float* __restrict__ sw, int2* __restrict__ row_walk) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n_terms; x += nwarps) {
+    const int32_t c = terms[x];
+    const int32_t p0 = (int32_t)cstart[c];
+    const int32_t m = (int32_t)cstart[c + 1] - p0;
+    int32_t d = 0x7fffffff, r = 0;
+    float w = 0.f;
+    int64_t off = 0;
+    if (lane < m) {
+      d = post_doc[p0 + lane];
+      w = post_w[p0 + lane];
+      r = post_r[p0 + lane];
+      off = doc_off[d];
+    }
+    int32_t rank = 0;
+    for (int q = 0; q < m; ++q) rank += __shfl_sync(kFull, d, q) < d ? 1 : 0;
+    if (lane < m) put_ranked(p0 + rank, p0 + m, d, w, r, off, sdoc, sw, row_walk);
+  }
+}
+
+// Longer lists (up to max_m postings): staged in the warp's shared-memory buffer; each
+// posting counts the smaller ids there, four per 16-byte broadcast read.
+__global__ void __launch_bounds__(kRankWarps * 32) k_rank_big(
+    const int64_t* __restrict__ cstart, const int32_t* __restrict__ terms, int32_t n_terms, int32_t buf,
     const int32_t* __restrict__ post_doc, const float* __restrict__ post_w, const int32_t* __restrict__ post_r,
     const int64_t* __restrict__ doc_off, int32_t* __restrict__ sdoc, float* __restrict__ sw,
     int2* __restrict__ row_walk) {
-  __shared__ unsigned long long keys[kSortMax];
-  __shared__ int32_t tst[kSortMax / 2 + 1];
-  for (int32_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
-    const int32_t t0 = gterm[g], t1 = gterm[g + 1];
-    const int32_t nterm = t1 - t0;
-    const int64_t p0 = cstart[t0];
-    const int32_t P = (int32_t)(cstart[t1] - p0);
-    __syncthreads();
-    for (int x = threadIdx.x; x <= nterm; x += kSortThreads) tst[x] = (int32_t)(cstart[t0 + x] - p0);
-    int n2 = 2;
-    while (n2 < P) n2 <<= 1;
-    __syncthreads();
-    for (int x = threadIdx.x; x < n2; x += kSortThreads) {
-      unsigned long long k = ~0ull;
-      if (x < P) {
-        int a = 0, b = nterm;  // last term start <= x
-        while (b - a > 1) {
-          const int m = (a + b) >> 1;
-          if (tst[m] <= x) a = m; else b = m;
-        }
-        k = ((unsigned long long)a << 44) | ((unsigned long long)(uint32_t)post_doc[p0 + x] << 12) |
-            (unsigned long long)x;
+  extern __shared__ __align__(16) int32_t rbuf[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t* sd = rbuf + warp * buf;
+  const int64_t nwarps = (int64_t)gridDim.x * kRankWarps;
+  for (int64_t x = (int64_t)blockIdx.x * kRankWarps + warp; x < n_terms; x += nwarps) {
+    const int32_t c = terms[x];
+    const int32_t p0 = (int32_t)cstart[c];
+    const int32_t m = (int32_t)cstart[c + 1] - p0;
+    const int32_t m4 = (m + 3) & ~3;
+    if (m4 > buf) continue;  // excluded by the host
+    for (int32_t y = lane; y < m4; y += 32) sd[y] = y < m ? post_doc[p0 + y] : 0x7fffffff;
+    __syncwarp();
+    for (int32_t e = lane; e < m; e += 32) {
+      const int32_t d = sd[e];
+      const float w = post_w[p0 + e];
+      const int32_t r = post_r[p0 + e];
+      const int64_t off = doc_off[d];
+      int32_t rank = 0;
+      for (int32_t y = 0; y < m4; y += 4) {
+        const int4 v = *reinterpret_cast<const int4*>(sd + y);
+        rank += (v.x < d) + (v.y < d) + (v.z < d) + (v.w < d);
       }
-      keys[x] = k;
+      put_ranked(p0 + rank, p0 + m, d, w, r, off, sdoc, sw, row_walk);
     }
-    __syncthreads();
-    for (int k = 2; k <= n2; k <<= 1) {
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int x = threadIdx.x; x < n2; x += kSortThreads) {
-          const int y = x ^ j;
-          if (y > x) {
-            const unsigned long long a = keys[x], b = keys[y];
-            if ((a > b) == ((x & k) == 0)) {
-              keys[x] = b;
-              keys[y] = a;
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
-    for (int x = threadIdx.x; x < P; x += kSortThreads) {
-      const unsigned long long key = keys[x];
-      const int64_t src = p0 + (int64_t)(key & 4095ull);
-      const int32_t dst = (int32_t)(p0 + x);
-      const int32_t d = post_doc[src];
-      sdoc[dst] = d;
-      sw[dst] = post_w[src];
-      // the postings after this one in its term's list: the documents > d sharing the term
-      row_walk[doc_off[d] + post_r[src]] = make_int2(dst + 1, (int32_t)(p0 + tst[(int)(key >> 44) + 1]));
-    }
+    __syncwarp();
   }
 }
 
@@ -317,17 +330,35 @@ __global__ void k_rescore(const mrc_pair* __restrict__ cand, const unsigned long
 
 }  // namespace
 
-cudaError_t launch_sort_postings(mrc_ctx* ctx, const int64_t* cstart, const int32_t* gterm, int32_t n_groups,
-                                 const int32_t* post_doc, const float* post_w, const int32_t* post_r,
-                                 const int64_t* doc_off, int32_t* sdoc, float* sw, void* row_walk) {
-  if (n_groups <= 0) return cudaSuccess;
-  int grid = ctx->num_sms * 3;
-  if (n_groups < grid) grid = n_groups;
+cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int32_t* small_terms, int32_t n_small,
+                                 const int32_t* big_terms, int32_t n_big, int32_t max_m, const int32_t* post_doc,
+                                 const float* post_w, const int32_t* post_r, const int64_t* doc_off, int32_t* sdoc,
+                                 float* sw, void* row_walk) {
   cudaEvent_t ev = nullptr;
-  timing_begin(ctx, "sort_postings", 0.0, 0.0, &ev);
-  k_sort_postings<<<grid, kSortThreads, 0, ctx->stream>>>(cstart, gterm, n_groups, post_doc, post_w, post_r, doc_off,
-                                                           sdoc, sw,
-                                                           reinterpret_cast<int2*>(row_walk));
+  timing_begin(ctx, "rank_postings", 0.0, 0.0, &ev);
+  if (n_small > 0) {
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rank_small, 256, 0);
+    int64_t grid = (int64_t)ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t need = ((int64_t)n_small + 7) / 8;
+    if (need < grid) grid = need;
+    k_rank_small<<<(unsigned)grid, 256, 0, ctx->stream>>>(cstart, small_terms, n_small, post_doc, post_w, post_r,
+                                                           doc_off, sdoc, sw, reinterpret_cast<int2*>(row_walk));
+  }
+  if (n_big > 0) {
+    const int32_t buf = (max_m + 3) & ~3;
+    const size_t smem = sizeof(int32_t) * (size_t)kRankWarps * buf;
+    cudaError_t e = cudaFuncSetAttribute(k_rank_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rank_big, kRankWarps * 32, smem);
+    int64_t grid = (int64_t)ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t need = ((int64_t)n_big + kRankWarps - 1) / kRankWarps;
+    if (need < grid) grid = need;
+    k_rank_big<<<(unsigned)grid, kRankWarps * 32, smem, ctx->stream>>>(cstart, big_terms, n_big, buf, post_doc,
+                                                                       post_w, post_r, doc_off, sdoc, sw,
+                                                                       reinterpret_cast<int2*>(row_walk));
+  }
   timing_end(ctx, ev);
   return cudaGetLastError();
 }
