@@ -672,71 +672,48 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), ctx->stream);
   if (N < 2) return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
 
-  // document frequencies within these documents decide the head/tail split
+  // document frequencies within these documents decide the head/tail split: head = terms
+  // whose postings are dense enough that a tensor-core column beats sparse products,
+  // df >= max(32, N / 48) (capped so that tail lists stay <= 4096 postings); tail = the
+  // other terms with df >= 2. The split is computed on the device; only its totals come back.
+  const int32_t cut = (int32_t)std::min<int64_t>(std::max<int64_t>(32, N / 48), 4097);
+  const int64_t n_tblocks = ((int64_t)V + 1023) / 1024;
   int32_t* df = (int32_t*)ws_get(ctx, "cos.df", sizeof(int32_t) * V, &st);
   unsigned long long* d_norm = (unsigned long long*)ws_get(ctx, "cos.norm", sizeof(unsigned long long) * N, &st);
+  int32_t* d_colmap = (int32_t*)ws_get(ctx, "cos.colmap", sizeof(int32_t) * V, &st);
+  int64_t* d_tstart = (int64_t*)ws_get(ctx, "cos.tstart", sizeof(int64_t) * V, &st);
+  int32_t* d_tfill = (int32_t*)ws_get(ctx, "cos.tfill", sizeof(int32_t) * V, &st);
+  int64_t* d_cstart = (int64_t*)ws_get(ctx, "cos.cstart", sizeof(int64_t) * ((size_t)V + 1), &st);
+  int32_t* d_rank_terms = (int32_t*)ws_get(ctx, "cos.rterms", sizeof(int32_t) * (size_t)V, &st);
+  long long* d_tpart = (long long*)ws_get(ctx, "cos.tpart", sizeof(long long) * 8 * (size_t)n_tblocks, &st);
+  long long* d_tsum = (long long*)ws_get(ctx, "cos.tsum", sizeof(long long) * 8, &st);
   if (st != MRC_OK) return st;
   cudaMemsetAsync(df, 0, sizeof(int32_t) * V, ctx->stream);
+  cudaMemsetAsync(d_cstart, 0, sizeof(int64_t), ctx->stream);
   const float* wid = index->params.weighting == MRC_WEIGHT_TFIDF ? index->idf : nullptr;
   cudaError_t e = launch_df_norm(ctx, d, df, V, wid, d_norm);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "df pass");
-  std::vector<int32_t> hdf(V);
-  e = cudaMemcpyAsync(hdf.data(), df, sizeof(int32_t) * V, cudaMemcpyDeviceToHost, ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "reading df");
+  e = launch_cosine_terms(ctx, df, V, cut, d_tpart, d_tsum, d_colmap, d_tstart, d_cstart, d_rank_terms);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "head/tail split");
+  long long* h_tsum = (long long*)((char*)ctx->pinned + 1024);
+  e = cudaMemcpyAsync(h_tsum, d_tsum, sizeof(long long) * 6, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the head/tail split");
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;  // synchronises the stream
-
-  // head = terms whose postings are dense enough that a tensor-core column beats
-  // sparse products: df >= max(32, N / 48); tail = the other terms with df >= 2
-  const int64_t cut = std::min<int64_t>(std::max<int64_t>(32, N / 48), 4097);  // tail lists stay <= 4096
-  std::vector<int32_t> head;
-  for (int32_t t = 0; t < V; ++t)
-    if (hdf[t] >= cut) head.push_back(t);
-  std::stable_sort(head.begin(), head.end(), [&](int32_t a, int32_t b) { return hdf[a] > hdf[b]; });
-  const int32_t kd = std::max<int32_t>(64, round_up((int32_t)head.size(), 64));
-  std::vector<int32_t> colmap(V, -1);
-  for (size_t c = 0; c < head.size(); ++c) colmap[head[c]] = (int32_t)c;
-  std::vector<int64_t> tstart(V, 0);
-  std::vector<int64_t> cstart(1, 0);  // postings start of each tail term, in term-id order
-  int64_t n_post = 0;
-  double tail_work = 0.0;
-  for (int32_t t = 0; t < V; ++t)
-    if (colmap[t] < 0 && hdf[t] >= 2) {
-      colmap[t] = -2;
-      tstart[t] = n_post;
-      n_post += hdf[t];
-      cstart.push_back(n_post);
-      tail_work += (double)hdf[t] * (double)(hdf[t] - 1) / 2.0;
-    }
-  const int32_t n_tail = (int32_t)cstart.size() - 1;
-  // tail terms by list length: up to 32 postings (ranked by one warp's shuffles) and longer
-  std::vector<int32_t> rank_terms(std::max<int32_t>(n_tail, 1));
-  int32_t n_small = 0, max_m = 0;
-  for (int32_t c = 0; c < n_tail; ++c)
-    if (cstart[c + 1] - cstart[c] <= 32) rank_terms[n_small++] = c;
-  for (int32_t c = 0, b = n_small; c < n_tail; ++c) {
-    const int32_t m = (int32_t)(cstart[c + 1] - cstart[c]);
-    if (m > 32) {
-      rank_terms[b++] = c;
-      max_m = std::max(max_m, m);
-    }
-  }
+  const int64_t n_head = h_tsum[0], n_post = h_tsum[2];
+  const int32_t n_tail = (int32_t)h_tsum[1], n_small = (int32_t)h_tsum[3], max_m = (int32_t)h_tsum[4];
+  const double tail_work = (double)h_tsum[5];
+  const int32_t kd = std::max<int32_t>(64, round_up((int32_t)n_head, 64));
   if (n_post >= (1ll << 31) - 64)
     return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more than 2^31 tail postings");
   const int64_t ldh = (N + 7) / 8 * 8;
   if ((double)N * (double)ldh * 2.0 > 64e9)
     return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more documents than the 64 GB score buffer allows");
 
-  int32_t* d_colmap = (int32_t*)ws_get(ctx, "cos.colmap", sizeof(int32_t) * V, &st);
-  int64_t* d_tstart = (int64_t*)ws_get(ctx, "cos.tstart", sizeof(int64_t) * V, &st);
-  int32_t* d_tfill = (int32_t*)ws_get(ctx, "cos.tfill", sizeof(int32_t) * V, &st);
   int32_t* d_pdoc = (int32_t*)ws_get(ctx, "cos.pdoc", sizeof(int32_t) * (size_t)std::max<int64_t>(n_post, 1), &st);
   float* d_pw = (float*)ws_get(ctx, "cos.pw", sizeof(float) * (size_t)std::max<int64_t>(n_post, 1), &st);
   int32_t* d_pr = (int32_t*)ws_get(ctx, "cos.pr", sizeof(int32_t) * (size_t)std::max<int64_t>(n_post, 1), &st);
-  int32_t* d_sdoc = (int32_t*)ws_get(ctx, "cos.sdoc", sizeof(int32_t) * (size_t)std::max<int64_t>(n_post, 1), &st);
-  float* d_sw = (float*)ws_get(ctx, "cos.sw", sizeof(float) * (size_t)std::max<int64_t>(n_post, 1), &st);
+  void* d_spost = ws_get(ctx, "cos.spost", 8 * (size_t)std::max<int64_t>(n_post, 1), &st);
   void* d_rwalk = ws_get(ctx, "cos.rwalk", 8 * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
-  int64_t* d_cstart = (int64_t*)ws_get(ctx, "cos.cstart", sizeof(int64_t) * cstart.size(), &st);
-  int32_t* d_rank_terms = (int32_t*)ws_get(ctx, "cos.rterms", sizeof(int32_t) * rank_terms.size(), &st);
   int32_t* d_rcnt = (int32_t*)ws_get(ctx, "cos.rcnt", sizeof(int32_t) * (size_t)N, &st);
   float* d_rw = (float*)ws_get(ctx, "cos.rw", sizeof(float) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
   void* d_hhi = ws_get(ctx, "cos.hhi", 2 * (size_t)N * kd, &st);
@@ -744,15 +721,7 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   void* d_H = ws_get(ctx, "cos.H16", 2 * (size_t)N * ldh, &st);
   unsigned long long* d_next = (unsigned long long*)ws_get(ctx, "cos.next", sizeof(unsigned long long), &st);
   if (st != MRC_OK) return st;
-  e = cudaMemcpyAsync(d_colmap, colmap.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_tstart, tstart.data(), sizeof(int64_t) * V, cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_cstart, cstart.data(), sizeof(int64_t) * cstart.size(), cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_rank_terms, rank_terms.data(), sizeof(int32_t) * rank_terms.size(), cudaMemcpyHostToDevice,
-                        ctx->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_tfill, 0, sizeof(int32_t) * V, ctx->stream);
+  e = cudaMemsetAsync(d_tfill, 0, sizeof(int32_t) * V, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_hhi, 0, 2 * (size_t)N * kd, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_hlo, 0, 2 * (size_t)N * kd, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cosine set-up");
@@ -775,7 +744,7 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   e = launch_densify(ctx, d, V, index->tinfo, o);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "densify");
   e = launch_rank_postings(ctx, d_cstart, d_rank_terms, n_small, d_rank_terms + n_small, n_tail - n_small, max_m, d_pdoc,
-                           d_pw, d_pr, d.offsets, d_sdoc, d_sw, d_rwalk);
+                           d_pw, d_pr, d.offsets, d_spost, d_rwalk);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sorting postings");
 
   // head: single-fp16 tensor-core GEMM of the unit head columns, stored as fp16. Its error
@@ -797,7 +766,7 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   const float delta = (float)(std::ldexp(1.0, -10) + std::ldexp(1.0, -12) + (double)kd * std::ldexp(1.0, -23) + 1e-4);
 
   // tail: postings products, candidates against tau - delta, exact head for each candidate
-  e = launch_cosine_tail(ctx, N, d_H, ldh, d.offsets, d_rcnt, d_rwalk, d_rw, d_sdoc, d_sw, n_post, d_hhi, d_hlo, kd,
+  e = launch_cosine_tail(ctx, N, d_H, ldh, d.offsets, d_rcnt, d_rwalk, d_rw, d_spost, n_post, d_hhi, d_hlo, kd,
                          tau, delta, dst, d_count, capacity, tail_work, d_next);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tail pass");
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;

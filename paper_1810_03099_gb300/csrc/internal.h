@@ -183,20 +183,31 @@ cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g);
 cudaError_t launch_simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
                                  int32_t hmax, mrc_pair* pairs, unsigned long long* count, int64_t capacity);
 
+// Head/tail split of the vocabulary for the exact cosine: df >= cut -> head column (colmap =
+// column, in term-id order), 2 <= df < cut -> tail term (colmap = -2, tstart = start of its
+// postings; cstart[c], cstart[c + 1] bound the c-th tail list; rank_terms lists the tail
+// terms of at most 32 postings first), else colmap = -1. part: [8 * ceil(V / 1024)] int64
+// scratch. summary (int64): [0] head terms, [1] tail terms, [2] tail postings, [3] tail
+// terms of <= 32 postings, [4] longest tail list, [5] sum over tail terms of df (df - 1) / 2.
+cudaError_t launch_cosine_terms(mrc_ctx* ctx, const int32_t* df, int32_t V, int32_t cut, long long* part,
+                                long long* summary, int32_t* colmap, int64_t* tstart, int64_t* cstart,
+                                int32_t* rank_terms);
+
 // tail.cu
-// Orders every tail term's postings by document into sdoc/sw and records, for each
+// Orders every tail term's postings by document into spost ((document, weight bits) int32
+// pairs) and records, for each
 // (document, tail term) entry of the per-document lists, the range of the term's postings that
 // follow that document. small_terms: tail terms (indices into cstart) with at most 32
 // postings; big_terms: the others, each with at most max_m postings.
 cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int32_t* small_terms, int32_t n_small,
                                  const int32_t* big_terms, int32_t n_big, int32_t max_m, const int32_t* post_doc,
-                                 const float* post_w, const int32_t* post_r, const int64_t* doc_off, int32_t* sdoc,
-                                 float* sw, void* row_walk);
+                                 const float* post_w, const int32_t* post_r, const int64_t* doc_off, void* spost,
+                                 void* row_walk);
 // Exact cosine completion: approximate fp16 head scores H plus exact tail products, candidates
 // >= tau - delta rescored exactly (head from the hi/lo split rows [n x kd], tail exact).
 cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t ldh, const int64_t* row_off,
-                               const int32_t* row_cnt, const void* row_walk, const float* row_w, const int32_t* sdoc,
-                               const float* sw, int64_t n_postings, const void* head_hi, const void* head_lo,
+                               const int32_t* row_cnt, const void* row_walk, const float* row_w, const void* spost,
+                               int64_t n_postings, const void* head_hi, const void* head_lo,
                                int32_t kd, float tau, float delta, mrc_pair* pairs, unsigned long long* count,
                                int64_t capacity, double work_pairs, unsigned long long* next_item);
 cudaError_t launch_rescore(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand, int64_t cand_cap,

@@ -34,10 +34,8 @@ constexpr int kWalkChunks = 4;                        // 32-posting chunks per l
 // end of t's list): the postings of the documents after d that share t. Positions are 32-bit
 // (fewer than 2^31 postings).
 __device__ __forceinline__ void put_ranked(int32_t at, int32_t end, int32_t d, float w, int32_t r, int64_t off,
-                                           int32_t* __restrict__ sdoc, float* __restrict__ sw,
-                                           int2* __restrict__ row_walk) {
-  sdoc[at] = d;
-  sw[at] = w;
+                                           int2* __restrict__ spost, int2* __restrict__ row_walk) {
+  spost[at] = make_int2(d, __float_as_int(w));
   row_walk[off + r] = make_int2(at + 1, end);
 }
 
@@ -48,8 +46,8 @@ __global__ void __launch_bounds__(256) k_rank_small(const int64_t* __restrict__ 
                                                     const int32_t* __restrict__ post_doc,
                                                     const float* __restrict__ post_w,
                                                     const int32_t* __restrict__ post_r,
-                                                    const int64_t* __restrict__ doc_off, int32_t* __restrict__ sdoc,
-                                                    float* __restrict__ sw, int2* __restrict__ row_walk) {
+                                                    const int64_t* __restrict__ doc_off, int2* __restrict__ spost,
+                                                    int2* __restrict__ row_walk) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n_terms; x += nwarps) {
@@ -67,7 +65,7 @@ __global__ void __launch_bounds__(256) k_rank_small(const int64_t* __restrict__ 
     }
     int32_t rank = 0;
     for (int q = 0; q < m; ++q) rank += __shfl_sync(kFull, d, q) < d ? 1 : 0;
-    if (lane < m) put_ranked(p0 + rank, p0 + m, d, w, r, off, sdoc, sw, row_walk);
+    if (lane < m) put_ranked(p0 + rank, p0 + m, d, w, r, off, spost, row_walk);
   }
 }
 
@@ -76,8 +74,7 @@ __global__ void __launch_bounds__(256) k_rank_small(const int64_t* __restrict__ 
 __global__ void __launch_bounds__(kRankWarps * 32) k_rank_big(
     const int64_t* __restrict__ cstart, const int32_t* __restrict__ terms, int32_t n_terms, int32_t buf,
     const int32_t* __restrict__ post_doc, const float* __restrict__ post_w, const int32_t* __restrict__ post_r,
-    const int64_t* __restrict__ doc_off, int32_t* __restrict__ sdoc, float* __restrict__ sw,
-    int2* __restrict__ row_walk) {
+    const int64_t* __restrict__ doc_off, int2* __restrict__ spost, int2* __restrict__ row_walk) {
   extern __shared__ __align__(16) int32_t rbuf[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* sd = rbuf + warp * buf;
@@ -100,9 +97,158 @@ __global__ void __launch_bounds__(kRankWarps * 32) k_rank_big(
         const int4 v = *reinterpret_cast<const int4*>(sd + y);
         rank += (v.x < d) + (v.y < d) + (v.z < d) + (v.w < d);
       }
-      put_ranked(p0 + rank, p0 + m, d, w, r, off, sdoc, sw, row_walk);
+      put_ranked(p0 + rank, p0 + m, d, w, r, off, spost, row_walk);
     }
     __syncwarp();
+  }
+}
+
+// ---- head/tail split of the vocabulary (exact cosine set-up) ----------------------------
+// A term is a head term (a dense tensor-core column) when df >= cut, a tail term (sparse
+// postings) when 2 <= df < cut, and ignored otherwise (a term in one document joins no
+// pair). Head columns and tail lists follow term-id order. Three passes: per-block counts
+// over 1024-term blocks, one CTA turning them into block offsets, per-term placement.
+constexpr int kTermBlock = 1024;
+enum { kTcHead = 0, kTcTail, kTcPost, kTcSmall, kTcMaxM, kTcWork, kTcFields };
+
+struct TermFlags {
+  int32_t head, tail, post, small;
+};
+__device__ __forceinline__ TermFlags term_class(int32_t d, int32_t cut) {
+  TermFlags f;
+  f.head = d >= cut;
+  f.tail = d >= 2 && d < cut;
+  f.post = f.tail ? d : 0;
+  f.small = f.tail && d <= 32;
+  return f;
+}
+
+// Exclusive scan of v over the CTA (kTermBlock threads); *total receives the sum.
+// scratch: 33 words of shared memory.
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* scratch, long long* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  __syncthreads();  // scratch is free (a previous scan may still read it)
+  if (lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const long long w = scratch[lane];
+    long long wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(kFull, wi, o);
+      if (lane >= o) wi += y;
+    }
+    scratch[lane] = wi - w;
+    if (lane == 31) scratch[32] = wi;
+  }
+  __syncthreads();
+  *total = scratch[32];
+  return scratch[warp] + incl - v;
+}
+
+__device__ __forceinline__ long long block_max(long long v, long long* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    long long x = scratch[lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(kFull, x, o));
+    if (lane == 0) scratch[32] = x;
+  }
+  __syncthreads();
+  return scratch[32];
+}
+
+__global__ void __launch_bounds__(kTermBlock) k_term_count(const int32_t* __restrict__ df, int32_t V, int32_t cut,
+                                                           long long* __restrict__ part) {
+  __shared__ long long scratch[33];
+  const int64_t t = (int64_t)blockIdx.x * kTermBlock + threadIdx.x;
+  const int32_t d = t < V ? df[t] : 0;
+  const TermFlags f = term_class(d, cut);
+  const long long v[kTcFields] = {f.head, f.tail, f.post, f.small, f.tail ? d : 0,
+                                  f.tail ? (long long)d * (d - 1) / 2 : 0};
+  long long out[kTcFields];
+#pragma unroll
+  for (int q = 0; q < kTcFields; ++q) {
+    long long total = 0;
+    if (q == kTcMaxM)
+      total = block_max(v[q], scratch);
+    else
+      block_excl_scan(v[q], scratch, &total);
+    out[q] = total;
+  }
+  if (threadIdx.x < kTcFields) part[(int64_t)blockIdx.x * kTcFields + threadIdx.x] = out[threadIdx.x];
+}
+
+// One CTA: per-block counts -> exclusive per-block offsets (in place, except the maximum
+// field), and the totals into summary[kTcFields].
+__global__ void __launch_bounds__(kTermBlock) k_term_scan(long long* __restrict__ part, int64_t nb,
+                                                          long long* __restrict__ summary) {
+  __shared__ long long scratch[33];
+  const int64_t per = (nb + kTermBlock - 1) / kTermBlock;  // blocks per thread, contiguous
+  const int64_t b0 = threadIdx.x * per, b1 = min(nb, b0 + per);
+#pragma unroll 1
+  for (int q = 0; q < kTcFields; ++q) {
+    long long sum = 0;
+    for (int64_t b = b0; b < b1; ++b) {
+      const long long x = part[b * kTcFields + q];
+      sum = q == kTcMaxM ? max(sum, x) : sum + x;
+    }
+    if (q == kTcMaxM) {
+      const long long m = block_max(sum, scratch);
+      if (threadIdx.x == 0) summary[q] = m;
+      continue;
+    }
+    long long total = 0;
+    long long run = block_excl_scan(sum, scratch, &total);
+    for (int64_t b = b0; b < b1; ++b) {
+      const long long x = part[b * kTcFields + q];
+      part[b * kTcFields + q] = run;
+      run += x;
+    }
+    if (threadIdx.x == 0) summary[q] = total;
+  }
+}
+
+// Per term: head column, or tail list start; the tail-list boundaries (cstart), and the tail
+// lists split into those of at most 32 postings (rank_terms[0, n_small)) and the longer ones
+// (rank_terms[n_small, n_tail)).
+__global__ void __launch_bounds__(kTermBlock) k_term_place(const int32_t* __restrict__ df, int32_t V, int32_t cut,
+                                                           const long long* __restrict__ part,
+                                                           const long long* __restrict__ summary,
+                                                           int32_t* __restrict__ colmap, int64_t* __restrict__ tstart,
+                                                           int64_t* __restrict__ cstart,
+                                                           int32_t* __restrict__ rank_terms) {
+  __shared__ long long scratch[33];
+  const int64_t t = (int64_t)blockIdx.x * kTermBlock + threadIdx.x;
+  const int32_t d = t < V ? df[t] : 0;
+  const TermFlags f = term_class(d, cut);
+  const long long* off = part + (int64_t)blockIdx.x * kTcFields;
+  long long total;
+  const long long r_head = off[kTcHead] + block_excl_scan(f.head, scratch, &total);
+  const long long r_tail = off[kTcTail] + block_excl_scan(f.tail, scratch, &total);
+  const long long r_post = off[kTcPost] + block_excl_scan(f.post, scratch, &total);
+  const long long r_small = off[kTcSmall] + block_excl_scan(f.small, scratch, &total);
+  if (t >= V) return;
+  colmap[t] = f.head ? (int32_t)r_head : (f.tail ? -2 : -1);
+  tstart[t] = f.tail ? r_post : 0;
+  if (f.tail) {
+    cstart[r_tail] = r_post;
+    cstart[r_tail + 1] = r_post + d;  // the same value the next tail term writes as its start
+    if (f.small)
+      rank_terms[r_small] = (int32_t)r_tail;
+    else
+      rank_terms[summary[kTcSmall] + (r_tail - r_small)] = (int32_t)r_tail;
   }
 }
 
@@ -166,7 +312,7 @@ __device__ __forceinline__ float exact_head(const __half* __restrict__ hhi, cons
 __global__ void __launch_bounds__(kTailThreads, 3) k_cosine_tail(
     int32_t n, const __half* __restrict__ H, int64_t ldh, const int64_t* __restrict__ row_off,
     const int32_t* __restrict__ row_cnt, const int2* __restrict__ row_walk, const float* __restrict__ row_w,
-    const int32_t* __restrict__ sdoc, const float* __restrict__ sw, const __half* __restrict__ hhi,
+    const int2* __restrict__ spost, const __half* __restrict__ hhi,
     const __half* __restrict__ hlo, int32_t kd, float tau, float delta, mrc_pair* pairs,
     unsigned long long* count, int64_t capacity, int32_t window, int32_t n_windows, int64_t n_items,
     unsigned long long* next_item) {
@@ -246,8 +392,9 @@ __global__ void __launch_bounds__(kTailThreads, 3) k_cosine_tail(
             const int32_t f = cs + lane;
             if (f < total) {
               const int32_t x = sk + (f - ek);
-              jd[u] = sdoc[x];
-              wv[u] = wk * sw[x];
+              const int2 pv = spost[x];  // (document, weight) of the posting
+              jd[u] = pv.x;
+              wv[u] = wk * __int_as_float(pv.y);
             }
           }
         }
@@ -330,10 +477,26 @@ __global__ void k_rescore(const mrc_pair* __restrict__ cand, const unsigned long
 
 }  // namespace
 
+cudaError_t launch_cosine_terms(mrc_ctx* ctx, const int32_t* df, int32_t V, int32_t cut, long long* part,
+                                long long* summary, int32_t* colmap, int64_t* tstart, int64_t* cstart,
+                                int32_t* rank_terms) {
+  if (V <= 0) return cudaErrorInvalidValue;
+  const int64_t nb = ((int64_t)V + kTermBlock - 1) / kTermBlock;
+  if (nb > 0x7fffffff) return cudaErrorInvalidValue;
+  cudaEvent_t ev = nullptr;
+  timing_begin(ctx, "term_split", 0.0, 0.0, &ev);
+  k_term_count<<<(unsigned)nb, kTermBlock, 0, ctx->stream>>>(df, V, cut, part);
+  k_term_scan<<<1, kTermBlock, 0, ctx->stream>>>(part, nb, summary);
+  k_term_place<<<(unsigned)nb, kTermBlock, 0, ctx->stream>>>(df, V, cut, part, summary, colmap, tstart, cstart,
+                                                             rank_terms);
+  timing_end(ctx, ev);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int32_t* small_terms, int32_t n_small,
                                  const int32_t* big_terms, int32_t n_big, int32_t max_m, const int32_t* post_doc,
-                                 const float* post_w, const int32_t* post_r, const int64_t* doc_off, int32_t* sdoc,
-                                 float* sw, void* row_walk) {
+                                 const float* post_w, const int32_t* post_r, const int64_t* doc_off, void* spost,
+                                 void* row_walk) {
   cudaEvent_t ev = nullptr;
   timing_begin(ctx, "rank_postings", 0.0, 0.0, &ev);
   if (n_small > 0) {
@@ -343,7 +506,8 @@ cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int3
     const int64_t need = ((int64_t)n_small + 7) / 8;
     if (need < grid) grid = need;
     k_rank_small<<<(unsigned)grid, 256, 0, ctx->stream>>>(cstart, small_terms, n_small, post_doc, post_w, post_r,
-                                                           doc_off, sdoc, sw, reinterpret_cast<int2*>(row_walk));
+                                                           doc_off, reinterpret_cast<int2*>(spost),
+                                                           reinterpret_cast<int2*>(row_walk));
   }
   if (n_big > 0) {
     const int32_t buf = (max_m + 3) & ~3;
@@ -356,7 +520,8 @@ cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int3
     const int64_t need = ((int64_t)n_big + kRankWarps - 1) / kRankWarps;
     if (need < grid) grid = need;
     k_rank_big<<<(unsigned)grid, kRankWarps * 32, smem, ctx->stream>>>(cstart, big_terms, n_big, buf, post_doc,
-                                                                       post_w, post_r, doc_off, sdoc, sw,
+                                                                       post_w, post_r, doc_off,
+                                                                       reinterpret_cast<int2*>(spost),
                                                                        reinterpret_cast<int2*>(row_walk));
   }
   timing_end(ctx, ev);
@@ -364,8 +529,8 @@ cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int3
 }
 
 cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t ldh, const int64_t* row_off,
-                               const int32_t* row_cnt, const void* row_walk, const float* row_w, const int32_t* sdoc,
-                               const float* sw, int64_t n_postings, const void* head_hi, const void* head_lo,
+                               const int32_t* row_cnt, const void* row_walk, const float* row_w, const void* spost,
+                               int64_t n_postings, const void* head_hi, const void* head_lo,
                                int32_t kd, float tau, float delta, mrc_pair* pairs, unsigned long long* count,
                                int64_t capacity, double work_pairs, unsigned long long* next_item) {
   if (n <= 1) return cudaSuccess;
@@ -393,7 +558,7 @@ cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t
   timing_begin(ctx, "cosine_tail", 2.0 * (double)n * (double)(n - 1) / 2.0, 2.0 * work_pairs, &ev);
   k_cosine_tail<<<(unsigned)grid, kTailThreads, smem, ctx->stream>>>(
       (int32_t)n, reinterpret_cast<const __half*>(H16), ldh, row_off, row_cnt, reinterpret_cast<const int2*>(row_walk),
-      row_w, sdoc, sw, reinterpret_cast<const __half*>(head_hi), reinterpret_cast<const __half*>(head_lo), kd, tau, delta,
+      row_w, reinterpret_cast<const int2*>(spost), reinterpret_cast<const __half*>(head_hi), reinterpret_cast<const __half*>(head_lo), kd, tau, delta,
       pairs, count, capacity, window, n_windows, n_items, next_item);
   timing_end(ctx, ev);
   return cudaGetLastError();
