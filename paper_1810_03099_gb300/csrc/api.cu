@@ -226,12 +226,14 @@ int32_t padded_kp8(int32_t k) { return round_up(k, 128); }
 // Reference selection (Section IV): rank terms by df descending, ties by id;
 // zero-df terms dropped; REGION / ALL / DF1 pick the selection; partition p
 // holds selection positions [floor(pL/k), floor((p+1)L/k)).
-int64_t select_references(const std::vector<int32_t>& df, int64_t n_docs, const mrc_params& p,
+int64_t select_references(const int32_t* df, int32_t V, int64_t n_docs, const mrc_params& p,
                           std::vector<int32_t>* part) {
-  const int32_t V = (int32_t)df.size();
   part->assign(V, -1);
   const int64_t L = p.L < 0 ? 32ll * p.k : p.L;
-  std::vector<int32_t> sel;
+  // scratch kept across calls (fresh vocabulary-sized allocations cost page faults)
+  static thread_local std::vector<int32_t> sel, ranked;
+  static thread_local std::vector<int64_t> pos;
+  sel.clear();
   if (p.select_mode == MRC_SELECT_DF1) {
     for (int32_t t = 0; t < V && (int64_t)sel.size() < L; ++t)
       if (df[t] == 1) sel.push_back(t);
@@ -239,7 +241,7 @@ int64_t select_references(const std::vector<int32_t>& df, int64_t n_docs, const 
     // counting sort: df descending, ids ascending within equal df
     int32_t maxdf = 0;
     for (int32_t t = 0; t < V; ++t) maxdf = std::max(maxdf, df[t]);
-    std::vector<int64_t> pos((size_t)maxdf + 2, 0);
+    pos.assign((size_t)maxdf + 2, 0);
     for (int32_t t = 0; t < V; ++t)
       if (df[t] > 0) pos[df[t]] += 1;
     int64_t acc = 0;
@@ -248,11 +250,11 @@ int64_t select_references(const std::vector<int32_t>& df, int64_t n_docs, const 
       pos[v] = acc;
       acc += c;
     }
-    std::vector<int32_t> ranked((size_t)acc);
+    ranked.resize((size_t)acc);
     for (int32_t t = 0; t < V; ++t)
       if (df[t] > 0) ranked[pos[df[t]]++] = t;
     if (p.select_mode == MRC_SELECT_ALL) {
-      sel = ranked;
+      sel.assign(ranked.begin(), ranked.end());
     } else {
       int64_t start = p.region_start;
       if (start < 0) {
@@ -304,32 +306,52 @@ float bf16_round(float f) {
 
 // Uploads term info (idf under the weighting, partition) and 1/|R_p|. In the precision
 // form the stored per-term weights (document and reference) are bfloat16 values.
-mrc_status upload_references(mrc_ctx* ctx, mrc_index* x) {
+// Reference tables of the signature pass from the host partition (x->h_part) and the host
+// idf: |R_p| on the host (each reference term weighs 1 * idf(t), in the float the kernels
+// use), the term table on the device. The copies read pinned staging, so the caller keeps
+// the staging untouched until the stream has passed them.
+mrc_status upload_references(mrc_ctx* ctx, mrc_index* x, const float* h_idf, int32_t* part_stage,
+                             float* rinv_stage) {
   const int32_t V = x->vocab;
-  std::vector<TermInfo> ti(V);
+  const bool tfidf = x->params.weighting == MRC_WEIGHT_TFIDF;
   const bool bf16 = x->params.precision == MRC_PREC_BF16_FP8;
-  for (int32_t t = 0; t < V; ++t) {
-    ti[t].idf = x->params.weighting == MRC_WEIGHT_TFIDF ? (bf16 ? bf16_round(x->h_idf[t]) : x->h_idf[t]) : 1.0f;
-    ti[t].code = x->h_part[t];
-  }
-  // |R_p| from the same float idf the kernels use: each reference term weighs 1 * idf(t)
   x->h_rnorm.assign(x->k, 0.0);
   for (int32_t t = 0; t < V; ++t)
     if (x->h_part[t] >= 0) {
-      const double r = ti[t].idf;
+      const double r = tfidf ? (bf16 ? bf16_round(h_idf[t]) : h_idf[t]) : 1.0f;
       x->h_rnorm[x->h_part[t]] += r * r;
     }
-  std::vector<float> rinv(x->k);
   for (int32_t q = 0; q < x->k; ++q) {
     x->h_rnorm[q] = std::sqrt(x->h_rnorm[q]);
-    rinv[q] = x->h_rnorm[q] > 0 ? (float)(1.0 / x->h_rnorm[q]) : 0.f;
+    rinv_stage[q] = x->h_rnorm[q] > 0 ? (float)(1.0 / x->h_rnorm[q]) : 0.f;
   }
-  cudaError_t e = cudaMemcpyAsync(x->tinfo, ti.data(), sizeof(TermInfo) * V, cudaMemcpyHostToDevice, ctx->stream);
+  std::memcpy(part_stage, x->h_part.data(), sizeof(int32_t) * V);
+  mrc_status st = MRC_OK;
+  int32_t* d_part = (int32_t*)ws_get(ctx, "build.part", sizeof(int32_t) * V, &st);
+  if (st != MRC_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(d_part, part_stage, sizeof(int32_t) * V, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(x->rinv, rinv.data(), sizeof(float) * x->k, cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    e = cudaMemcpyAsync(x->rinv, rinv_stage, sizeof(float) * x->k, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = launch_term_info(ctx, x->idf, d_part, V, tfidf, bf16, x->tinfo);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "uploading references");
   return MRC_OK;
+}
+
+// Grow-only pinned host scratch of the context.
+void* host_ws(mrc_ctx* ctx, size_t bytes, mrc_status* st) {
+  if (bytes <= ctx->host_ws_bytes) return ctx->host_ws;
+  cudaStreamSynchronize(ctx->stream);  // nothing in flight may still read the old buffer
+  if (ctx->host_ws) cudaFreeHost(ctx->host_ws);
+  ctx->host_ws = nullptr;
+  ctx->host_ws_bytes = 0;
+  if (cudaMallocHost(&ctx->host_ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->host_ws = nullptr;
+    *st = fail(ctx, MRC_ERR_OOM, "pinned host allocation failed");
+    return nullptr;
+  }
+  ctx->host_ws_bytes = bytes;
+  return ctx->host_ws;
 }
 
 mrc_status alloc_signature_arrays(mrc_ctx* ctx, mrc_index* x) {
@@ -461,6 +483,7 @@ void mrc_ctx_destroy(mrc_ctx* ctx) {
   }
   for (auto e : ctx->free_events) cudaEventDestroy(e);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->host_ws) cudaFreeHost(ctx->host_ws);
   delete ctx;
 }
 
@@ -508,17 +531,21 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "df pass"));
   e = launch_idf(ctx, d.n_docs, x->df, vocab, params->weighting, x->idf, nullptr);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "idf"));
-  x->h_df.resize(vocab);
-  x->h_idf.resize(vocab);
-  e = cudaMemcpyAsync(x->h_df.data(), x->df, sizeof(int32_t) * vocab, cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(x->h_idf.data(), x->idf, sizeof(float) * vocab, cudaMemcpyDeviceToHost, ctx->stream);
+  // pinned staging: df and idf [vocab] each, then the partition [vocab] and 1 / |R_p| [k]
+  char* stage = (char*)host_ws(ctx, 12 * (size_t)vocab + 4 * (size_t)x->k + 64, &st);
+  if (!stage) return bail(st);
+  int32_t* h_df = (int32_t*)stage;
+  float* h_idf = (float*)(stage + 4 * (size_t)vocab);
+  e = cudaMemcpyAsync(h_df, x->df, sizeof(int32_t) * vocab, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_idf, x->idf, sizeof(float) * vocab, cudaMemcpyDeviceToHost, ctx->stream);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "reading df"));
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);  // synchronises the stream
 
   // references (host sort of the vocabulary), then their device tables
-  x->L_used = select_references(x->h_df, d.n_docs, *params, &x->h_part);
-  if ((st = upload_references(ctx, x)) != MRC_OK) return bail(st);
+  x->L_used = select_references(h_df, vocab, d.n_docs, *params, &x->h_part);
+  if ((st = upload_references(ctx, x, h_idf, (int32_t*)(stage + 8 * (size_t)vocab),
+                              (float*)(stage + 12 * (size_t)vocab))) != MRC_OK)
+    return bail(st);
 
   // a2-a4: signatures, Simhash, packed compare operands
   if ((st = alloc_signature_arrays(ctx, x)) != MRC_OK) return bail(st);
@@ -857,6 +884,13 @@ mrc_status mrc_index_save(mrc_ctx* ctx, const mrc_index* x, const char* path) {
     std::fclose(f);
     return cuda_fail(ctx, e, "index save");
   }
+  std::vector<int32_t> hdf(x->vocab);
+  std::vector<float> hidf(x->vocab);
+  if (cudaMemcpy(hdf.data(), x->df, sizeof(int32_t) * x->vocab, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(hidf.data(), x->idf, sizeof(float) * x->vocab, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    std::fclose(f);
+    return cuda_fail(ctx, cudaGetLastError(), "index save");
+  }
   const int32_t version = 1;
   bool ok = std::fwrite(kMagic, 1, 8, f) == 8;
   ok = ok && std::fwrite(&version, sizeof(version), 1, f) == 1;
@@ -864,8 +898,8 @@ mrc_status mrc_index_save(mrc_ctx* ctx, const mrc_index* x, const char* path) {
   ok = ok && std::fwrite(&x->n_docs, sizeof(int64_t), 1, f) == 1;
   ok = ok && std::fwrite(&x->vocab, sizeof(int32_t), 1, f) == 1;
   ok = ok && std::fwrite(&x->L_used, sizeof(int64_t), 1, f) == 1;
-  ok = ok && std::fwrite(x->h_df.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
-  ok = ok && std::fwrite(x->h_idf.data(), sizeof(float), x->vocab, f) == (size_t)x->vocab;
+  ok = ok && std::fwrite(hdf.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
+  ok = ok && std::fwrite(hidf.data(), sizeof(float), x->vocab, f) == (size_t)x->vocab;
   ok = ok && std::fwrite(x->h_part.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
   ok = ok && std::fwrite(sig.data(), sizeof(float), sig.size(), f) == sig.size();
   ok = ok && std::fwrite(unit.data(), sizeof(float), unit.size(), f) == unit.size();
@@ -892,7 +926,8 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
   ok = ok && std::fread(&x->L_used, sizeof(int64_t), 1, f) == 1;
   std::string why;
   ok = ok && valid_params(&x->params, &why) && x->vocab > 0 && x->n_docs > 0;
-  std::vector<float> sig, unit;
+  std::vector<float> sig, unit, hidf;
+  std::vector<int32_t> hdf;
   std::vector<uint64_t> sh;
   if (ok) {
     x->k = x->params.k;
@@ -901,14 +936,14 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
     x->device = ctx->device;
     x->stream = ctx->stream;
     const size_t n = (size_t)x->n_docs;
-    x->h_df.resize(x->vocab);
-    x->h_idf.resize(x->vocab);
+    hdf.resize(x->vocab);
+    hidf.resize(x->vocab);
     x->h_part.resize(x->vocab);
     sig.resize(n * x->k);
     unit.resize(n * x->k);
     sh.resize(n);
-    ok = std::fread(x->h_df.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
-    ok = ok && std::fread(x->h_idf.data(), sizeof(float), x->vocab, f) == (size_t)x->vocab;
+    ok = std::fread(hdf.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
+    ok = ok && std::fread(hidf.data(), sizeof(float), x->vocab, f) == (size_t)x->vocab;
     ok = ok && std::fread(x->h_part.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
     ok = ok && std::fread(sig.data(), sizeof(float), sig.size(), f) == sig.size();
     ok = ok && std::fread(unit.data(), sizeof(float), unit.size(), f) == unit.size();
@@ -933,13 +968,16 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
   if ((st = alloc_signature_arrays(ctx, x)) != MRC_OK) return bail(st);
   const size_t n = (size_t)x->n_docs;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);  // stream-ordered allocations before plain copies
-  if (e == cudaSuccess) e = cudaMemcpy(x->df, x->h_df.data(), sizeof(int32_t) * x->vocab, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(x->idf, x->h_idf.data(), sizeof(float) * x->vocab, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(x->df, hdf.data(), sizeof(int32_t) * x->vocab, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(x->idf, hidf.data(), sizeof(float) * x->vocab, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(x->sig, sig.data(), sizeof(float) * sig.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(x->sig_unit, unit.data(), sizeof(float) * unit.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(x->simhash, sh.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "index load"));
-  if ((st = upload_references(ctx, x)) != MRC_OK) return bail(st);
+  char* stage = (char*)host_ws(ctx, 4 * (size_t)x->vocab + 4 * (size_t)x->k + 64, &st);
+  if (!stage) return bail(st);
+  if ((st = upload_references(ctx, x, hidf.data(), (int32_t*)stage, (float*)(stage + 4 * (size_t)x->vocab))) != MRC_OK)
+    return bail(st);
   // compare operands are re-packed from the unit signatures
   if (x->op_hi) cudaMemsetAsync(x->op_hi, 0, 2 * n * x->kp, ctx->stream);
   if (x->op_lo) cudaMemsetAsync(x->op_lo, 0, 2 * n * x->kp, ctx->stream);

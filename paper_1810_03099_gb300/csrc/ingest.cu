@@ -618,6 +618,22 @@ cudaError_t launch_df_norm(mrc_ctx* ctx, const DocsDev& d, int32_t* df, int32_t 
   return run_ingest<kDFN>(ctx, d, p, "ingest_df_norm", 4.0, 16.0);
 }
 
+__global__ void k_term_info(const float* idf, const int32_t* part, int32_t vocab, int32_t tfidf, int32_t bf16,
+                            TermInfo* tinfo) {
+  const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= vocab) return;
+  float w = 1.0f;
+  if (tfidf) w = bf16 ? __bfloat162float(__float2bfloat16_rn(idf[t])) : idf[t];
+  tinfo[t].idf = w;
+  tinfo[t].code = part[t];
+}
+
+cudaError_t launch_term_info(mrc_ctx* ctx, const float* idf, const int32_t* part, int32_t vocab, int32_t tfidf,
+                             int32_t bf16, TermInfo* tinfo) {
+  k_term_info<<<(vocab + 255) / 256, 256, 0, ctx->stream>>>(idf, part, vocab, tfidf, bf16, tinfo);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_idf(mrc_ctx* ctx, int64_t n_docs, const int32_t* df, int32_t vocab, int32_t weighting, float* idf,
                        TermInfo* tinfo) {
   k_idf<<<(vocab + 255) / 256, 256, 0, ctx->stream>>>(n_docs, df, vocab, weighting, idf, tinfo);

@@ -59,6 +59,8 @@ struct mrc_ctx {
   std::vector<std::pair<std::string, mrc::KernelStat>> stats;
   std::vector<cudaEvent_t> free_events;
   void* pinned = nullptr;  // small pinned host scratch (counters)
+  void* host_ws = nullptr;  // grow-only pinned host scratch (vocabulary-sized tables)
+  size_t host_ws_bytes = 0;
 };
 
 struct mrc_index {
@@ -71,9 +73,8 @@ struct mrc_index {
   int32_t kp = 0;       // padded row length (elements) of fp16 compare operands
   int32_t kp8 = 0;      // padded row length (bytes) of E4M3 compare operands
   int64_t L_used = 0;
-  // host copies
-  std::vector<int32_t> h_df, h_part;
-  std::vector<float> h_idf;
+  // host copies (reference partition of each term, reference norms)
+  std::vector<int32_t> h_part;
   std::vector<double> h_rnorm;
   // device arrays
   int32_t* df = nullptr;          // [vocab]
@@ -116,6 +117,10 @@ cudaError_t launch_df(mrc_ctx* ctx, const DocsDev& d, int32_t* df, int32_t vocab
 // idf is NULL) as a 2^-22 fixed-point sum, written to norm[doc] for every document.
 cudaError_t launch_df_norm(mrc_ctx* ctx, const DocsDev& d, int32_t* df, int32_t vocab, const float* idf,
                            unsigned long long* norm);
+// Term table of the signature pass: tinfo[t] = {weight of t in a reference (idf under TF-IDF,
+// bfloat16-rounded when bf16 != 0; 1 under counts), reference partition of t or -1}.
+cudaError_t launch_term_info(mrc_ctx* ctx, const float* idf, const int32_t* part, int32_t vocab, int32_t tfidf,
+                             int32_t bf16, TermInfo* tinfo);
 cudaError_t launch_idf(mrc_ctx* ctx, int64_t n_docs, const int32_t* df, int32_t vocab, int32_t weighting,
                        float* idf, TermInfo* tinfo);
 struct SigOut {
