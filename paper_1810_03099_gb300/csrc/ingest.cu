@@ -85,18 +85,35 @@ __device__ __forceinline__ float inv_norm_of(unsigned long long norm_q) {
   return n2 > 0.f ? 1.0f / sqrtf(n2) : 0.f;
 }
 
-__device__ __forceinline__ bool table_insert(uint32_t* keys, uint32_t* cnts, int log2ts, uint32_t t) {
+// Inserts up to B terms (those whose bit is set in pend) with all of a round's
+// compare-and-swaps in flight: each round tries every pending term at its current probe
+// slot; a term is placed when its slot was empty or already holds it, otherwise it moves to
+// the next slot. Linear probing from the same start slot keeps the table consistent under
+// concurrent inserts (slots are never emptied). Returns false if a term found no slot.
+template <int B>
+__device__ __forceinline__ bool table_insert_batch(uint32_t* keys, uint32_t* cnts, int log2ts, const int32_t (&tk)[B],
+                                                   uint32_t pend) {
   const uint32_t mask = (1u << log2ts) - 1u;
-  uint32_t s = slot_of(t, log2ts);
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
-    const uint32_t prev = atomicCAS(&keys[s], kEmpty, t);
-    if (prev == kEmpty || prev == t) {
-      atomicAdd(&cnts[s], 1u);
-      return true;
-    }
-    s = (s + 1u) & mask;
+  uint32_t slot[B];
+#pragma unroll
+  for (int u = 0; u < B; ++u) slot[u] = slot_of((uint32_t)tk[u], log2ts);
+  for (uint32_t round = 0; pend != 0u && round <= mask; ++round) {
+    uint32_t prev[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if ((pend >> u) & 1u) prev[u] = atomicCAS(&keys[slot[u]], kEmpty, (uint32_t)tk[u]);
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if ((pend >> u) & 1u) {
+        if (prev[u] == kEmpty || prev[u] == (uint32_t)tk[u]) {
+          atomicAdd(&cnts[slot[u]], 1u);
+          pend &= ~(1u << u);
+        } else {
+          slot[u] = (slot[u] + 1u) & mask;
+        }
+      }
   }
-  return false;
+  return pend == 0u;
 }
 
 __device__ __forceinline__ int log2_slots(int64_t len, int max_log2) {
@@ -136,21 +153,41 @@ struct Acc {
   uint32_t plo, phi;
 };
 
-// Process one warp-chunk of 32 table slots [s0, s0 + 32).
+// Per-term table values a mode needs besides the term's count: SIG (reference weight, reference
+// partition), DENSE (idf or 1, head column / -2 tail / -1), DFN (idf or 1). Loading them is the
+// only global-memory read per term, so the warp path gathers them for a whole document at once.
+struct TermAux {
+  float w;
+  int32_t code;
+};
+
 template <int MODE>
-__device__ __forceinline__ void chunk(const IngestParams& p, const uint32_t* keys, const uint32_t* cnts, int s0,
-                                      int limit, int lane, unsigned long long* num_q, Acc& a, int64_t doc,
-                                      float inv_norm, int32_t* row_cnt_s, int64_t row_base) {
-  const uint32_t key = s0 + lane < limit ? keys[s0 + lane] : kEmpty;
+__device__ __forceinline__ TermAux load_aux(const IngestParams& p, uint32_t key) {
+  TermAux x{1.0f, 0};
+  if (MODE == kSIG) {
+    const int2 ti = __ldg(reinterpret_cast<const int2*>(p.tinfo) + key);
+    x.w = __int_as_float(ti.x);
+    x.code = ti.y;
+  } else if (MODE == kDENSE) {
+    if (p.dense.idf) x.w = __ldg(p.dense.idf + key);
+    x.code = __ldg(p.dense.colmap + key);
+  } else if (MODE == kDFN) {
+    if (p.norm_idf) x.w = __ldg(p.norm_idf + key);
+  }
+  return x;
+}
+
+// The work of one warp-chunk of 32 terms (key == kEmpty: no term in this lane).
+template <int MODE>
+__device__ __forceinline__ void chunk(const IngestParams& p, uint32_t key, uint32_t c, TermAux aux, int lane,
+                                      unsigned long long* num_q, Acc& a, int64_t doc, float inv_norm,
+                                      int32_t* row_cnt_s, int64_t row_base) {
   const bool valid = key != kEmpty;
-  const unsigned any = __ballot_sync(kFull, valid);
-  if (any == 0u) return;
-  const uint32_t c = valid ? cnts[s0 + lane] : 0u;
   if (MODE == kDF || MODE == kDFN) {
     if (valid) {
       atomicAdd(&p.df[key], 1);
       if (MODE == kDFN) {
-        const float w = p.norm_idf ? (float)c * __ldg(p.norm_idf + key) : (float)c;
+        const float w = (float)c * aux.w;
         a.norm += to_fix(w * w);
       }
     }
@@ -171,19 +208,18 @@ __device__ __forceinline__ void chunk(const IngestParams& p, const uint32_t* key
     if (valid) {
       // the term table holds idf (or 1 under count weighting; bfloat16-rounded idf in the
       // precision form); c * idf is exact in FP32 for bfloat16 idf (c < 2^16)
-      const int2 ti = __ldg(reinterpret_cast<const int2*>(p.tinfo) + key);
-      const float r = __int_as_float(ti.x);
+      const float r = aux.w;
       const float w = (float)c * r;
       a.norm += to_fix(w * w);
-      if (ti.y >= 0) atomicAdd(&num_q[ti.y], to_fix(w * r));
+      if (aux.code >= 0) atomicAdd(&num_q[aux.code], to_fix(w * r));
     }
     return;
   }
   // DENSE
   if (!valid) return;
-  const float w = p.dense.idf ? (float)c * __ldg(p.dense.idf + key) : (float)c;
+  const float w = (float)c * aux.w;
   const float u = w * inv_norm;
-  const int32_t code = p.dense.colmap[key];
+  const int32_t code = aux.code;
   if (code >= 0) {
     const __half hi = __float2half_rn(u);
     const __half lo = __float2half_rn((u - __half2float(hi)) * kSplitLoScale);
@@ -281,21 +317,28 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
     }
     for (int q = lane; q < kq; q += 32) num_q[q] = 0ull;
     if (lane == 0) *row_cnt_s = 0;
-    // all of the document's token loads in flight at once (len <= 512: 16 per lane)
+    // all of the document's token loads in flight at once (len <= 512: 16 per lane), then
+    // inserts in batches of 8 with their compare-and-swaps in flight together
     int32_t tk[kShortRegs];
 #pragma unroll
     for (int u = 0; u < kShortRegs; ++u) tk[u] = lane + 32 * u < len ? __ldcs(p.tokens + o0 + lane + 32 * u) : -1;
     __syncwarp();
 #pragma unroll
-    for (int u = 0; u < kShortRegs; ++u) {
-      if (32 * u >= len) break;  // warp-uniform
-      if (lane + 32 * u < len) {
-        const int32_t t = tk[u];
-        if ((uint32_t)t >= (uint32_t)p.vocab)
-          set_err(p.err, kErrBadToken);
-        else if (!table_insert(keys, cnts, l2, (uint32_t)t))
-          set_err(p.err, kErrTable);
+    for (int h = 0; h < kShortRegs; h += 8) {
+      if (32 * h >= len) break;  // warp-uniform
+      int32_t tb[8];
+      uint32_t pend = 0u;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        tb[u] = tk[h + u];
+        if (lane + 32 * (h + u) < len) {
+          if ((uint32_t)tb[u] >= (uint32_t)p.vocab)
+            set_err(p.err, kErrBadToken);
+          else
+            pend |= 1u << u;
+        }
       }
+      if (!table_insert_batch<8>(keys, cnts, l2, tb, pend)) set_err(p.err, kErrTable);
     }
     __syncwarp();
     // compact the occupied slots to the front, in place (a write never passes an unread slot)
@@ -313,10 +356,40 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
       nnz += __popc(bal);
       __syncwarp();
     }
+    // gather the terms' table values into the free upper half of the table (nnz <= ts / 2),
+    // eight loads per lane in flight
+    float* aux_w = reinterpret_cast<float*>(keys + ts / 2);
+    int32_t* aux_c = reinterpret_cast<int32_t*>(cnts + ts / 2);
+    if (MODE != kDF) {
+      for (int s0 = 0; s0 < nnz; s0 += 8 * 32) {
+        TermAux ax[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int sl = s0 + 32 * u + lane;
+          if (sl < nnz) ax[u] = load_aux<MODE>(p, keys[sl]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int sl = s0 + 32 * u + lane;
+          if (sl < nnz) {
+            aux_w[sl] = ax[u].w;
+            aux_c[sl] = ax[u].code;
+          }
+        }
+      }
+      __syncwarp();
+    }
     Acc a{0ull, 0u, 0u};
     float inv_norm = 0.f;
     if (MODE == kDENSE) inv_norm = inv_norm_of(p.dense.norm[d]);
-    for (int s0 = 0; s0 < nnz; s0 += 32) chunk<MODE>(p, keys, cnts, s0, nnz, lane, num_q, a, d, inv_norm, row_cnt_s, o0);
+    for (int s0 = 0; s0 < nnz; s0 += 32) {
+      const int sl = s0 + lane;
+      const uint32_t key = sl < nnz ? keys[sl] : kEmpty;
+      const uint32_t c = sl < nnz ? cnts[sl] : 0u;
+      TermAux ax{1.0f, 0};
+      if (MODE != kDF && sl < nnz) ax = TermAux{aux_w[sl], aux_c[sl]};
+      chunk<MODE>(p, key, c, ax, lane, num_q, a, d, inv_norm, row_cnt_s, o0);
+    }
     __syncwarp();
     if (MODE == kSIG) finalize_sig(p, d, len, warp_sum(a.norm), num_q, a.plo, a.phi, lane);
     if (MODE == kDFN) {
@@ -331,7 +404,7 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
 
 // ---------------------------------------------------------------- CTA path
 template <int MODE>
-__global__ void __launch_bounds__(kLongThreads) k_ingest_long(IngestParams p) {
+__global__ void __launch_bounds__(kLongThreads, 2) k_ingest_long(IngestParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int nwarps = kLongThreads / 32;
@@ -377,6 +450,7 @@ __global__ void __launch_bounds__(kLongThreads) k_ingest_long(IngestParams p) {
           const int64_t x = x0 + u * kLongThreads;
           tk[u] = x < len ? __ldcs(p.tokens + o0 + x) : -1;
         }
+        uint32_t pend = 0u;
 #pragma unroll
         for (int u = 0; u < kLongUnroll; ++u) {
           if (x0 + u * kLongThreads >= len) break;
@@ -386,12 +460,30 @@ __global__ void __launch_bounds__(kLongThreads) k_ingest_long(IngestParams p) {
             continue;
           }
           if (passes > 1 && pass_of((uint32_t)t, passes) != pass) continue;
-          if (!table_insert(keys, cnts, l2, (uint32_t)t)) set_err(p.err, kErrTable);
+          pend |= 1u << u;
         }
+        if (!table_insert_batch<kLongUnroll>(keys, cnts, l2, tk, pend)) set_err(p.err, kErrTable);
       }
       __syncthreads();
-      for (int s0 = warp * 32; s0 < ts; s0 += nwarps * 32)
-        chunk<MODE>(p, keys, cnts, s0, ts, lane, num_q, a, d, inv_norm, &misc[1], o0);
+      // each warp walks its chunks with the next chunk's table values already in flight
+      int s0 = warp * 32;
+      uint32_t key = s0 + lane < ts ? keys[s0 + lane] : kEmpty;
+      uint32_t c = key != kEmpty ? cnts[s0 + lane] : 0u;
+      TermAux ax{1.0f, 0};
+      if (MODE != kDF && key != kEmpty) ax = load_aux<MODE>(p, key);
+      while (s0 < ts) {
+        const int s1 = s0 + nwarps * 32;
+        const uint32_t key1 = s1 + lane < ts ? keys[s1 + lane] : kEmpty;
+        const uint32_t c1 = key1 != kEmpty ? cnts[s1 + lane] : 0u;
+        TermAux ax1{1.0f, 0};
+        if (MODE != kDF && key1 != kEmpty) ax1 = load_aux<MODE>(p, key1);
+        if (__ballot_sync(kFull, key != kEmpty) != 0u)
+          chunk<MODE>(p, key, c, ax, lane, num_q, a, d, inv_norm, &misc[1], o0);
+        s0 = s1;
+        key = key1;
+        c = c1;
+        ax = ax1;
+      }
     }
     if (MODE == kDFN) {
       const unsigned long long nq = warp_sum(a.norm);
