@@ -232,7 +232,9 @@ const char* mrc_batch_last_error(const mrc_batch* batch);
 void mrc_batch_free(mrc_batch* batch);
 
 /* Index introspection and export (for checks and persistence). Each output
- * pointer may be NULL to skip it; sizes follow mrc_index_info. */
+ * pointer may be NULL to skip it; sizes follow mrc_index_info. Host outputs
+ * are complete on return; device outputs are written in order on the
+ * context's stream, like every other call's device results. */
 mrc_status mrc_index_get_info(const mrc_index* index, mrc_index_info* info);
 mrc_status mrc_index_export(mrc_ctx* ctx, const mrc_index* index, float* sig /*[n*k]*/, uint64_t* simhash /*[n]*/,
                             int32_t* df /*[vocab]*/, float* idf /*[vocab]*/, int32_t* part /*[vocab]*/,

@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -52,6 +54,33 @@ void* ws_get(mrc_ctx* ctx, const char* slot, size_t bytes, mrc_status* st) {
   b.ptr = p;
   b.bytes = want;
   return p;
+}
+
+int resident_ctas(const void* func, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> smem_set;  // (kernel, device) -> limit set
+  static std::map<std::tuple<const void*, int, int, size_t>, int> occ;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_tuple(func, dev, threads, smem);
+  const auto it = occ.find(key);
+  if (it != occ.end()) return it->second;
+  size_t& lim = smem_set[std::make_pair(func, dev)];
+  if (smem > 48 * 1024 && smem > lim) {
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    lim = smem;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  occ[key] = per_sm;
+  return per_sm;
 }
 
 void timing_begin(mrc_ctx* ctx, const char* name, double bytes, double flops, cudaEvent_t* ev_out) {
@@ -154,11 +183,8 @@ struct Scope {
   int prev;
 };
 
-mrc_status check_err_word(mrc_ctx* ctx, int32_t* d_err) {
-  int32_t h = 0;
-  cudaError_t e = cudaMemcpyAsync(&h, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel execution");
+// Status of a call's device error word h (already on the host).
+mrc_status err_status(mrc_ctx* ctx, int32_t h) {
   if (h & kErrTimeout) return fail(ctx, MRC_ERR_TIMEOUT, "a bounded device wait expired");
   if (h & kErrBadOffsets) return fail(ctx, MRC_ERR_INVALID, "offsets must start at 0 and be non-decreasing");
   if (h & kErrTooLong)
@@ -166,6 +192,14 @@ mrc_status check_err_word(mrc_ctx* ctx, int32_t* d_err) {
   if (h & kErrBadToken) return fail(ctx, MRC_ERR_INVALID, "a token id is outside [0, vocab)");
   if (h & kErrTable) return fail(ctx, MRC_ERR_CUDA, "internal: per-document term table overflow");
   return MRC_OK;
+}
+
+mrc_status check_err_word(mrc_ctx* ctx, int32_t* d_err) {
+  int32_t* h = (int32_t*)((char*)ctx->pinned + 256);
+  cudaError_t e = cudaMemcpyAsync(h, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel execution");
+  return err_status(ctx, *h);
 }
 
 int32_t* call_err(mrc_ctx* ctx, mrc_status* st) {
@@ -223,54 +257,64 @@ int32_t round_up(int32_t x, int32_t m) { return (x + m - 1) / m * m; }
 int32_t padded_kp(int32_t k) { return round_up(k, 64); }
 int32_t padded_kp8(int32_t k) { return round_up(k, 128); }
 
-// Reference selection (Section IV): rank terms by df descending, ties by id;
-// zero-df terms dropped; REGION / ALL / DF1 pick the selection; partition p
-// holds selection positions [floor(pL/k), floor((p+1)L/k)).
-int64_t select_references(const int32_t* df, int32_t V, int64_t n_docs, const mrc_params& p,
-                          std::vector<int32_t>* part) {
-  part->assign(V, -1);
+// Reference selection (Section IV): terms ranked by df descending, ids ascending within equal
+// df, zero-df terms dropped; REGION / ALL / DF1 pick the selection; partition p holds
+// selection positions [floor(pL/k), floor((p+1)L/k)), so position x lies in partition
+// floor(((x + 1) k - 1) / L). Writes part[t] (-1 for unselected terms) for every term and
+// returns L. The ranking is never materialised: with cnt[v] terms of df v, a term of df v that
+// is the s-th such term in id order has rank #{df > v} + s, so one pass in id order places
+// every term.
+int64_t select_references(const int32_t* df, int32_t V, int64_t n_docs, const mrc_params& p, int32_t* part) {
   const int64_t L = p.L < 0 ? 32ll * p.k : p.L;
-  // scratch kept across calls (fresh vocabulary-sized allocations cost page faults)
-  static thread_local std::vector<int32_t> sel, ranked;
-  static thread_local std::vector<int64_t> pos;
-  sel.clear();
   if (p.select_mode == MRC_SELECT_DF1) {
-    for (int32_t t = 0; t < V && (int64_t)sel.size() < L; ++t)
-      if (df[t] == 1) sel.push_back(t);
-  } else {
-    // counting sort: df descending, ids ascending within equal df
-    int32_t maxdf = 0;
-    for (int32_t t = 0; t < V; ++t) maxdf = std::max(maxdf, df[t]);
-    pos.assign((size_t)maxdf + 2, 0);
-    for (int32_t t = 0; t < V; ++t)
-      if (df[t] > 0) pos[df[t]] += 1;
-    int64_t acc = 0;
-    for (int32_t v = maxdf; v >= 1; --v) {
-      const int64_t c = pos[v];
-      pos[v] = acc;
-      acc += c;
-    }
-    ranked.resize((size_t)acc);
-    for (int32_t t = 0; t < V; ++t)
-      if (df[t] > 0) ranked[pos[df[t]]++] = t;
-    if (p.select_mode == MRC_SELECT_ALL) {
-      sel.assign(ranked.begin(), ranked.end());
-    } else {
-      int64_t start = p.region_start;
-      if (start < 0) {
-        start = (int64_t)ranked.size();
-        for (size_t q = 0; q < ranked.size(); ++q)
-          if ((double)df[ranked[q]] <= (double)n_docs / 100.0) {
-            start = (int64_t)q;
-            break;
-          }
+    int64_t n = 0;
+    for (int32_t t = 0; t < V; ++t) n += (df[t] == 1 && n < L) ? 1 : 0;
+    int64_t x = 0;
+    for (int32_t t = 0; t < V; ++t) {
+      int32_t q = -1;
+      if (df[t] == 1 && x < n) {
+        q = (int32_t)(((x + 1) * p.k - 1) / n);
+        ++x;
       }
-      for (int64_t q = start; q < (int64_t)ranked.size() && q < start + L; ++q) sel.push_back(ranked[q]);
+      part[t] = q;
     }
+    return n;
   }
-  const int64_t n = (int64_t)sel.size();
-  for (int32_t q = 0; q < p.k; ++q)
-    for (int64_t x = (int64_t)q * n / p.k; x < (int64_t)(q + 1) * n / p.k; ++x) (*part)[sel[x]] = q;
+  // scratch kept across calls (fresh allocations cost page faults)
+  static thread_local std::vector<int64_t> base, seen;
+  int32_t maxdf = 0;
+  for (int32_t t = 0; t < V; ++t) maxdf = std::max(maxdf, df[t]);
+  base.assign((size_t)maxdf + 2, 0);
+  for (int32_t t = 0; t < V; ++t) base[df[t]] += 1;
+  int64_t above = 0;  // terms with df > v, for v from maxdf down
+  for (int32_t v = maxdf; v >= 1; --v) {
+    const int64_t c = base[v];
+    base[v] = above;
+    above += c;
+  }
+  const int64_t ranked = above;  // terms with df >= 1
+  int64_t start = 0, end = ranked;
+  if (p.select_mode != MRC_SELECT_ALL) {
+    start = p.region_start;
+    if (start < 0) {
+      // first rank whose df <= N / 100: the number of terms with df > floor(N / 100)
+      const int64_t vcap = n_docs / 100;
+      start = vcap >= maxdf ? 0 : (vcap >= 1 ? base[vcap] : ranked);
+    }
+    start = std::min(start, ranked);
+    end = std::min(start + L, ranked);
+  }
+  const int64_t n = end - start;
+  seen.assign((size_t)maxdf + 2, 0);
+  for (int32_t t = 0; t < V; ++t) {
+    const int32_t v = df[t];
+    int32_t q = -1;
+    if (v > 0) {
+      const int64_t x = base[v] + seen[v]++ - start;
+      if (x >= 0 && x < n) q = (int32_t)(((x + 1) * p.k - 1) / n);
+    }
+    part[t] = q;
+  }
   return n;
 }
 
@@ -333,14 +377,17 @@ mrc_status upload_references(mrc_ctx* ctx, mrc_index* x, const float* h_idf, int
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(x->rinv, rinv_stage, sizeof(float) * x->k, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = launch_term_info(ctx, x->idf, d_part, V, tfidf, bf16, x->tinfo);
+  if (e == cudaSuccess && !ctx->host_ws_done) e = cudaEventCreateWithFlags(&ctx->host_ws_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->host_ws_done, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "uploading references");
   return MRC_OK;
 }
 
 // Grow-only pinned host scratch of the context.
 void* host_ws(mrc_ctx* ctx, size_t bytes, mrc_status* st) {
+  // copies still in flight may read the buffer: wait for the last of them
+  if (ctx->host_ws_done) cudaEventSynchronize(ctx->host_ws_done);
   if (bytes <= ctx->host_ws_bytes) return ctx->host_ws;
-  cudaStreamSynchronize(ctx->stream);  // nothing in flight may still read the old buffer
   if (ctx->host_ws) cudaFreeHost(ctx->host_ws);
   ctx->host_ws = nullptr;
   ctx->host_ws_bytes = 0;
@@ -390,12 +437,20 @@ SigOut index_sig_out(mrc_index* x) {
 }
 
 // Copies device pairs to a host destination (when `pairs` is host memory).
+// Ends a pair-producing call with one synchronisation: reads the pair count (and the call's
+// error word, when given; an error takes precedence), then copies host-side results.
 mrc_status finish_pairs(mrc_ctx* ctx, mrc_pair* user, mrc_pair* dev, unsigned long long* d_count, int64_t capacity,
-                        int64_t* n_pairs) {
+                        int64_t* n_pairs, int32_t* d_err = nullptr) {
   unsigned long long* hc = (unsigned long long*)ctx->pinned;
+  int32_t* he = (int32_t*)((char*)ctx->pinned + 256);
   cudaError_t e = cudaMemcpyAsync(hc, d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess && d_err) e = cudaMemcpyAsync(he, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "reading pair count");
+  if (d_err) {
+    const mrc_status st = err_status(ctx, *he);
+    if (st != MRC_OK) return st;
+  }
   const int64_t total = (int64_t)*hc;
   if (n_pairs) *n_pairs = total;
   const int64_t m = std::min<int64_t>(total, capacity);
@@ -484,6 +539,7 @@ void mrc_ctx_destroy(mrc_ctx* ctx) {
   for (auto e : ctx->free_events) cudaEventDestroy(e);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->host_ws) cudaFreeHost(ctx->host_ws);
+  if (ctx->host_ws_done) cudaEventDestroy(ctx->host_ws_done);
   delete ctx;
 }
 
@@ -542,7 +598,8 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);  // synchronises the stream
 
   // references (host sort of the vocabulary), then their device tables
-  x->L_used = select_references(h_df, vocab, d.n_docs, *params, &x->h_part);
+  x->h_part.resize(vocab);
+  x->L_used = select_references(h_df, vocab, d.n_docs, *params, x->h_part.data());
   if ((st = upload_references(ctx, x, h_idf, (int32_t*)(stage + 8 * (size_t)vocab),
                               (float*)(stage + 12 * (size_t)vocab))) != MRC_OK)
     return bail(st);
@@ -556,7 +613,9 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
                        index_sig_out(x));
   if (e == cudaSuccess && x->qnorm_min) e = launch_block_min(ctx, x->qnorm, x->n_docs, x->qnorm_min);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "signature pass"));
-  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);
+  // The df pass already validated these documents (offsets, lengths, token ids) and the
+  // signature pass meets the same ones, so the call returns without waiting for it: the index
+  // is ready in stream order, like any device result.
   *out = x;
   return MRC_OK;
 }
@@ -653,6 +712,8 @@ mrc_status mrc_match(mrc_ctx* ctx, const mrc_index* index, const float* query_si
     g.b_norm_min = index->qnorm_min;
   }
   g.thresh = tau - (prec == MRC_PREC_FP32 ? kF16CompareBound : index->params.margin);
+  // candidates, then their rescoring (which reads the candidate count on the device), then one
+  // synchronisation; only if the candidate buffer overflowed is the pass repeated, larger
   int64_t cand_cap = std::max<int64_t>(4 * capacity, 1 << 20);
   for (int attempt = 0; attempt < 2; ++attempt) {
     mrc_pair* cand = (mrc_pair*)ws_get(ctx, "match.cand", sizeof(mrc_pair) * (size_t)cand_cap, &st);
@@ -663,20 +724,16 @@ mrc_status mrc_match(mrc_ctx* ctx, const mrc_index* index, const float* query_si
     g.capacity = cand_cap;
     cudaError_t e = launch_gemm_compare(ctx, g);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "signature compare");
+    e = launch_rescore(ctx, cand, d_count + 1, cand_cap, a_unit, index->sig_unit, index->k, tau, dst, d_count, capacity);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rescoring");
     unsigned long long* hc = (unsigned long long*)ctx->pinned;
-    e = cudaMemcpyAsync(hc, d_count + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    e = cudaMemcpyAsync(hc + 1, d_count + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reading candidate count");
-    const int64_t nc = (int64_t)*hc;
-    if (nc <= cand_cap) {
-      e = launch_rescore(ctx, cand, d_count + 1, cand_cap, a_unit, index->sig_unit, index->k, tau, dst, d_count,
-                         capacity);
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "rescoring");
-      break;
-    }
+    if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;  // synchronises the stream
+    const int64_t nc = (int64_t)hc[1];
+    if (nc <= cand_cap) break;
     cand_cap = nc + nc / 8 + 1024;
   }
-  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;
   return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
 }
 
@@ -796,8 +853,7 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   e = launch_cosine_tail(ctx, N, d_H, ldh, d.offsets, d_rcnt, d_rwalk, d_rw, d_spost, n_post, d_hhi, d_hlo, kd,
                          tau, delta, dst, d_count, capacity, tail_work, d_next);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tail pass");
-  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;
-  return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
+  return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs, d_err);
 }
 
 mrc_status simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
@@ -849,7 +905,10 @@ mrc_status mrc_index_export(mrc_ctx* ctx, const mrc_index* x, float* sig, uint64
   if (e == cudaSuccess && simhash) e = cp(simhash, x->simhash, sizeof(uint64_t) * n);
   if (e == cudaSuccess && df) e = cp(df, x->df, sizeof(int32_t) * x->vocab);
   if (e == cudaSuccess && idf) e = cp(idf, x->idf, sizeof(float) * x->vocab);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  // device outputs are stream-ordered like every call's; host outputs are complete on return
+  const bool host_out = (sig && !is_device_ptr(sig)) || (simhash && !is_device_ptr(simhash)) ||
+                        (df && !is_device_ptr(df)) || (idf && !is_device_ptr(idf));
+  if (e == cudaSuccess && host_out) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "index export");
   if (part) std::memcpy(part, x->h_part.data(), sizeof(int32_t) * x->vocab);
   if (rnorm) std::memcpy(rnorm, x->h_rnorm.data(), sizeof(double) * x->k);

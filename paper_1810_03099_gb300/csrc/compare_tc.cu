@@ -833,9 +833,7 @@ cudaError_t run_gemm_resident(mrc_ctx* ctx, const GemmArgs& g) {
       std::max<size_t>(1024 + 2 * (size_t)C::NOPS * kBM * RB + (size_t)kResStagesB * C::NOPS * BN * RB + 256 +
                            8 * (32 * 33 + 32) * sizeof(float),
                        120 * 1024);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_gemm_resident<FMT, RB, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  if (resident_ctas(k_gemm_resident<FMT, RB, BN>, kResThreads, smem) <= 0) return cudaErrorInvalidConfiguration;
   int64_t grid = ctx->num_sms;
   if (p.n_tiles < grid) grid = p.n_tiles;
   if (grid <= 0) return cudaSuccess;
@@ -889,8 +887,7 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   p.ld = g.ld;
   p.err = g.err;
   const size_t smem = 1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256 + 4 * (32 * 33 + 32) * 4;
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_compare<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  if (resident_ctas(k_gemm_compare<FMT>, kThreads, smem) <= 0) return cudaErrorInvalidConfiguration;
   int64_t grid = ctx->num_sms;
   if (p.n_tiles < grid) grid = p.n_tiles;
   if (grid <= 0) return cudaSuccess;

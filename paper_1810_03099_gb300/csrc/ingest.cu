@@ -608,24 +608,15 @@ __global__ void k_pack(const float* sig, int64_t n, int32_t k, int32_t normalize
   }
 }
 
-// Persistent grids: as many CTAs as fit on every SM at once.
+// Persistent grids: as many CTAs as fit on every SM at once (0: the shared memory limit could
+// not be raised).
 template <int MODE>
 int short_grid(const mrc_ctx* ctx, size_t smem) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ingest_short<MODE>, kWarpsShort * 32, smem) !=
-          cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  return ctx->num_sms * per_sm;
+  return ctx->num_sms * resident_ctas(k_ingest_short<MODE>, kWarpsShort * 32, smem);
 }
 template <int MODE>
 int long_grid(const mrc_ctx* ctx, size_t smem) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ingest_long<MODE>, kLongThreads, smem) !=
-          cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  return ctx->num_sms * per_sm;
+  return ctx->num_sms * resident_ctas(k_ingest_long<MODE>, kLongThreads, smem);
 }
 
 size_t short_smem(int kq) { return (size_t)kWarpsShort * ((size_t)kShortSlots * 8 + (size_t)kq * 8 + 16); }
@@ -654,14 +645,11 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   p.err = d.err;
   const int kq = MODE == kSIG ? p.k : 0;
   const size_t s_smem = short_smem(kq), l_smem = long_smem(kq);
-  e = cudaFuncSetAttribute(k_ingest_short<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_ingest_long<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l_smem);
-  if (e != cudaSuccess) return e;
   const double tokens = (double)d.n_tokens;
   cudaEvent_t ev = nullptr;
   {
     int grid = short_grid<MODE>(ctx, s_smem);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
     const int64_t need = (d.n_docs + kWarpsShort - 1) / kWarpsShort;
     if (need < grid) grid = (int)need;
     std::string nm = std::string(name) + ".short";
@@ -673,6 +661,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   }
   {
     int grid = long_grid<MODE>(ctx, l_smem);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
     if (d.n_docs < grid) grid = (int)d.n_docs;
     std::string nm = std::string(name) + ".long";
     timing_begin(ctx, nm.c_str(), 0.0, 0.0, &ev);
@@ -829,18 +818,16 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
   p.short_cursor = counts + kCntShortCursor;
   p.err = err;
   const size_t s_smem = short_smem(k), l_smem = long_smem(k);
-  e = cudaFuncSetAttribute(k_ingest_short<kSIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ingest_long<kSIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l_smem);
-  if (e != cudaSuccess) return e;
   if (h[0] > 0) {
     int grid = short_grid<kSIG>(ctx, s_smem);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
     const int need = (h[0] + kWarpsShort - 1) / kWarpsShort;
     if (need < grid) grid = need;
     k_ingest_short<kSIG><<<grid, kWarpsShort * 32, s_smem, ctx->stream>>>(p);
   }
   if (h[1] > 0) {
     int grid = long_grid<kSIG>(ctx, l_smem);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
     if (h[1] < grid) grid = h[1];
     k_ingest_long<kSIG><<<grid, kLongThreads, l_smem, ctx->stream>>>(p);
   }

@@ -61,6 +61,7 @@ struct mrc_ctx {
   void* pinned = nullptr;  // small pinned host scratch (counters)
   void* host_ws = nullptr;  // grow-only pinned host scratch (vocabulary-sized tables)
   size_t host_ws_bytes = 0;
+  cudaEvent_t host_ws_done = nullptr;  // recorded after the last copy that reads host_ws
 };
 
 struct mrc_index {
@@ -97,6 +98,17 @@ namespace mrc {
 mrc_status fail(mrc_ctx* ctx, mrc_status st, const std::string& msg);
 mrc_status cuda_fail(mrc_ctx* ctx, cudaError_t e, const char* what);
 void* ws_get(mrc_ctx* ctx, const char* slot, size_t bytes, mrc_status* st);
+
+// ---- launch set-up cache (api.cu) ----
+// Resident CTAs per SM of `func` at `threads` threads and `smem` bytes of dynamic shared
+// memory on the current device (at least 1). Raises the kernel's dynamic shared memory limit
+// to `smem` first when needed. Results are cached per (kernel, device, threads, smem), so the
+// runtime is queried once per configuration. Returns 0 if the limit cannot be raised.
+int resident_ctas(const void* func, int threads, size_t smem);
+template <typename K>
+int resident_ctas(K* kernel, int threads, size_t smem) {
+  return resident_ctas(reinterpret_cast<const void*>(kernel), threads, smem);
+}
 
 // ---- timing helpers (api.cu) ----
 void timing_begin(mrc_ctx* ctx, const char* name, double bytes, double flops, cudaEvent_t* ev_out);

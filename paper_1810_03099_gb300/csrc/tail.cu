@@ -500,9 +500,7 @@ cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int3
   cudaEvent_t ev = nullptr;
   timing_begin(ctx, "rank_postings", 0.0, 0.0, &ev);
   if (n_small > 0) {
-    int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rank_small, 256, 0);
-    int64_t grid = (int64_t)ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+    int64_t grid = (int64_t)ctx->num_sms * resident_ctas(k_rank_small, 256, 0);
     const int64_t need = ((int64_t)n_small + 7) / 8;
     if (need < grid) grid = need;
     k_rank_small<<<(unsigned)grid, 256, 0, ctx->stream>>>(cstart, small_terms, n_small, post_doc, post_w, post_r,
@@ -512,11 +510,9 @@ cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int3
   if (n_big > 0) {
     const int32_t buf = (max_m + 3) & ~3;
     const size_t smem = sizeof(int32_t) * (size_t)kRankWarps * buf;
-    cudaError_t e = cudaFuncSetAttribute(k_rank_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rank_big, kRankWarps * 32, smem);
-    int64_t grid = (int64_t)ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+    const int per_sm = resident_ctas(k_rank_big, kRankWarps * 32, smem);
+    if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+    int64_t grid = (int64_t)ctx->num_sms * per_sm;
     const int64_t need = ((int64_t)n_big + kRankWarps - 1) / kRankWarps;
     if (need < grid) grid = need;
     k_rank_big<<<(unsigned)grid, kRankWarps * 32, smem, ctx->stream>>>(cstart, big_terms, n_big, buf, post_doc,
@@ -544,13 +540,11 @@ cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t
   const int32_t n_windows = (int32_t)((n + window - 1) / window);
   const int64_t n_items = n * n_windows;
   const size_t smem = sizeof(int32_t) * (size_t)window;
-  cudaError_t e = cudaFuncSetAttribute(k_cosine_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cosine_tail, kTailThreads, smem);
-  int64_t grid = (int64_t)ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+  const int per_sm = resident_ctas(k_cosine_tail, kTailThreads, smem);
+  if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+  int64_t grid = (int64_t)ctx->num_sms * per_sm;
   if (n_items < grid) grid = n_items;
-  e = cudaMemsetAsync(next_item, 0, sizeof(unsigned long long), ctx->stream);
+  cudaError_t e = cudaMemsetAsync(next_item, 0, sizeof(unsigned long long), ctx->stream);
   if (e != cudaSuccess) return e;
   cudaEvent_t ev = nullptr;
   // algorithmic bytes: the upper triangle of the fp16 head scores read once; flops: 2 per
