@@ -257,6 +257,23 @@ int32_t round_up(int32_t x, int32_t m) { return (x + m - 1) / m * m; }
 int32_t padded_kp(int32_t k) { return round_up(k, 64); }
 int32_t padded_kp8(int32_t k) { return round_up(k, 128); }
 
+// Round to the nearest bfloat16 (8 significant bits), ties to even.
+float bf16_round(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, sizeof(u));
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  u &= 0xFFFF0000u;
+  std::memcpy(&f, &u, sizeof(f));
+  return f;
+}
+
+// The reference weight of term t: idf under TF-IDF (bfloat16-rounded in the precision form,
+// as the kernels use it), 1 under counts.
+double reference_weight(const mrc_params& p, const float* idf, int32_t t) {
+  if (p.weighting != MRC_WEIGHT_TFIDF) return 1.0;
+  return p.precision == MRC_PREC_BF16_FP8 ? bf16_round(idf[t]) : idf[t];
+}
+
 // Reference selection (Section IV): terms ranked by df descending, ids ascending within equal
 // df, zero-df terms dropped; REGION / ALL / DF1 pick the selection; partition p holds
 // selection positions [floor(pL/k), floor((p+1)L/k)), so position x lies in partition
@@ -264,8 +281,11 @@ int32_t padded_kp8(int32_t k) { return round_up(k, 128); }
 // returns L. The ranking is never materialised: with cnt[v] terms of df v, a term of df v that
 // is the s-th such term in id order has rank #{df > v} + s, so one pass in id order places
 // every term.
-int64_t select_references(const int32_t* df, int32_t V, int64_t n_docs, const mrc_params& p, int32_t* part) {
+// |R_p|^2 accumulates over the selected terms in term-id order.
+int64_t select_references(const int32_t* df, int32_t V, int64_t n_docs, const mrc_params& p, int32_t* part,
+                          const float* idf, std::vector<double>* rnorm2) {
   const int64_t L = p.L < 0 ? 32ll * p.k : p.L;
+  rnorm2->assign(p.k, 0.0);
   if (p.select_mode == MRC_SELECT_DF1) {
     int64_t n = 0;
     for (int32_t t = 0; t < V; ++t) n += (df[t] == 1 && n < L) ? 1 : 0;
@@ -275,6 +295,8 @@ int64_t select_references(const int32_t* df, int32_t V, int64_t n_docs, const mr
       if (df[t] == 1 && x < n) {
         q = (int32_t)(((x + 1) * p.k - 1) / n);
         ++x;
+        const double r = reference_weight(p, idf, t);
+        (*rnorm2)[q] += r * r;
       }
       part[t] = q;
     }
@@ -311,7 +333,11 @@ int64_t select_references(const int32_t* df, int32_t V, int64_t n_docs, const mr
     int32_t q = -1;
     if (v > 0) {
       const int64_t x = base[v] + seen[v]++ - start;
-      if (x >= 0 && x < n) q = (int32_t)(((x + 1) * p.k - 1) / n);
+      if (x >= 0 && x < n) {
+        q = (int32_t)(((x + 1) * p.k - 1) / n);
+        const double r = reference_weight(p, idf, t);
+        (*rnorm2)[q] += r * r;
+      }
     }
     part[t] = q;
   }
@@ -338,48 +364,43 @@ void free_index_arrays(mrc_index* x) {
     if (p) cudaFreeAsync(p, x->stream);
 }
 
-// Round to the nearest bfloat16 (8 significant bits), ties to even.
-float bf16_round(float f) {
-  uint32_t u;
-  std::memcpy(&u, &f, sizeof(u));
-  u += 0x7FFFu + ((u >> 16) & 1u);
-  u &= 0xFFFF0000u;
-  std::memcpy(&f, &u, sizeof(f));
-  return f;
-}
 
 // Uploads term info (idf under the weighting, partition) and 1/|R_p|. In the precision
 // form the stored per-term weights (document and reference) are bfloat16 values.
-// Reference tables of the signature pass from the host partition (x->h_part) and the host
-// idf: |R_p| on the host (each reference term weighs 1 * idf(t), in the float the kernels
-// use), the term table on the device. The copies read pinned staging, so the caller keeps
-// the staging untouched until the stream has passed them.
-mrc_status upload_references(mrc_ctx* ctx, mrc_index* x, const float* h_idf, int32_t* part_stage,
-                             float* rinv_stage) {
+// Reference tables of the signature pass: 1 / |R_p| from the squared norms in x->h_rnorm (which
+// become the norms), the term table built on the device from the partition of every term
+// (part_stage: pinned, [vocab]) and the device idf. The copies read pinned staging, so the
+// context's host_ws_done event marks when the staging may be reused.
+mrc_status upload_references(mrc_ctx* ctx, mrc_index* x, const int32_t* part_stage, float* rinv_stage) {
   const int32_t V = x->vocab;
-  const bool tfidf = x->params.weighting == MRC_WEIGHT_TFIDF;
-  const bool bf16 = x->params.precision == MRC_PREC_BF16_FP8;
-  x->h_rnorm.assign(x->k, 0.0);
-  for (int32_t t = 0; t < V; ++t)
-    if (x->h_part[t] >= 0) {
-      const double r = tfidf ? (bf16 ? bf16_round(h_idf[t]) : h_idf[t]) : 1.0f;
-      x->h_rnorm[x->h_part[t]] += r * r;
-    }
   for (int32_t q = 0; q < x->k; ++q) {
     x->h_rnorm[q] = std::sqrt(x->h_rnorm[q]);
     rinv_stage[q] = x->h_rnorm[q] > 0 ? (float)(1.0 / x->h_rnorm[q]) : 0.f;
   }
-  std::memcpy(part_stage, x->h_part.data(), sizeof(int32_t) * V);
   mrc_status st = MRC_OK;
   int32_t* d_part = (int32_t*)ws_get(ctx, "build.part", sizeof(int32_t) * V, &st);
   if (st != MRC_OK) return st;
   cudaError_t e = cudaMemcpyAsync(d_part, part_stage, sizeof(int32_t) * V, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(x->rinv, rinv_stage, sizeof(float) * x->k, cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess) e = launch_term_info(ctx, x->idf, d_part, V, tfidf, bf16, x->tinfo);
+  if (e == cudaSuccess)
+    e = launch_term_info(ctx, x->idf, d_part, V, x->params.weighting == MRC_WEIGHT_TFIDF,
+                         x->params.precision == MRC_PREC_BF16_FP8, x->tinfo);
   if (e == cudaSuccess && !ctx->host_ws_done) e = cudaEventCreateWithFlags(&ctx->host_ws_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->host_ws_done, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "uploading references");
+  return MRC_OK;
+}
+
+// Partition of every term, read back from the device term table.
+mrc_status read_partition(mrc_ctx* ctx, const mrc_index* x, std::vector<int32_t>* part) {
+  std::vector<TermInfo> ti(x->vocab);
+  const cudaError_t e =
+      cudaMemcpyAsync(ti.data(), x->tinfo, sizeof(TermInfo) * x->vocab, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+    return cuda_fail(ctx, cudaGetLastError(), "reading the reference partition");
+  part->resize(x->vocab);
+  for (int32_t t = 0; t < x->vocab; ++t) (*part)[t] = ti[t].code;
   return MRC_OK;
 }
 
@@ -598,11 +619,9 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);  // synchronises the stream
 
   // references (host sort of the vocabulary), then their device tables
-  x->h_part.resize(vocab);
-  x->L_used = select_references(h_df, vocab, d.n_docs, *params, x->h_part.data());
-  if ((st = upload_references(ctx, x, h_idf, (int32_t*)(stage + 8 * (size_t)vocab),
-                              (float*)(stage + 12 * (size_t)vocab))) != MRC_OK)
-    return bail(st);
+  int32_t* part_stage = (int32_t*)(stage + 8 * (size_t)vocab);
+  x->L_used = select_references(h_df, vocab, d.n_docs, *params, part_stage, h_idf, &x->h_rnorm);
+  if ((st = upload_references(ctx, x, part_stage, (float*)(stage + 12 * (size_t)vocab))) != MRC_OK) return bail(st);
 
   // a2-a4: signatures, Simhash, packed compare operands
   if ((st = alloc_signature_arrays(ctx, x)) != MRC_OK) return bail(st);
@@ -910,7 +929,12 @@ mrc_status mrc_index_export(mrc_ctx* ctx, const mrc_index* x, float* sig, uint64
                         (df && !is_device_ptr(df)) || (idf && !is_device_ptr(idf));
   if (e == cudaSuccess && host_out) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "index export");
-  if (part) std::memcpy(part, x->h_part.data(), sizeof(int32_t) * x->vocab);
+  if (part) {
+    std::vector<int32_t> hp;
+    const mrc_status st = read_partition(ctx, x, &hp);
+    if (st != MRC_OK) return st;
+    std::memcpy(part, hp.data(), sizeof(int32_t) * x->vocab);
+  }
   if (rnorm) std::memcpy(rnorm, x->h_rnorm.data(), sizeof(double) * x->k);
   return MRC_OK;
 }
@@ -943,8 +967,12 @@ mrc_status mrc_index_save(mrc_ctx* ctx, const mrc_index* x, const char* path) {
     std::fclose(f);
     return cuda_fail(ctx, e, "index save");
   }
-  std::vector<int32_t> hdf(x->vocab);
+  std::vector<int32_t> hdf(x->vocab), hpart;
   std::vector<float> hidf(x->vocab);
+  if (read_partition(ctx, x, &hpart) != MRC_OK) {
+    std::fclose(f);
+    return MRC_ERR_CUDA;
+  }
   if (cudaMemcpy(hdf.data(), x->df, sizeof(int32_t) * x->vocab, cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemcpy(hidf.data(), x->idf, sizeof(float) * x->vocab, cudaMemcpyDeviceToHost) != cudaSuccess) {
     std::fclose(f);
@@ -959,7 +987,7 @@ mrc_status mrc_index_save(mrc_ctx* ctx, const mrc_index* x, const char* path) {
   ok = ok && std::fwrite(&x->L_used, sizeof(int64_t), 1, f) == 1;
   ok = ok && std::fwrite(hdf.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
   ok = ok && std::fwrite(hidf.data(), sizeof(float), x->vocab, f) == (size_t)x->vocab;
-  ok = ok && std::fwrite(x->h_part.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
+  ok = ok && std::fwrite(hpart.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
   ok = ok && std::fwrite(sig.data(), sizeof(float), sig.size(), f) == sig.size();
   ok = ok && std::fwrite(unit.data(), sizeof(float), unit.size(), f) == unit.size();
   ok = ok && std::fwrite(sh.data(), sizeof(uint64_t), n, f) == n;
@@ -986,7 +1014,7 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
   std::string why;
   ok = ok && valid_params(&x->params, &why) && x->vocab > 0 && x->n_docs > 0;
   std::vector<float> sig, unit, hidf;
-  std::vector<int32_t> hdf;
+  std::vector<int32_t> hdf, hpart;
   std::vector<uint64_t> sh;
   if (ok) {
     x->k = x->params.k;
@@ -997,13 +1025,13 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
     const size_t n = (size_t)x->n_docs;
     hdf.resize(x->vocab);
     hidf.resize(x->vocab);
-    x->h_part.resize(x->vocab);
+    hpart.resize(x->vocab);
     sig.resize(n * x->k);
     unit.resize(n * x->k);
     sh.resize(n);
     ok = std::fread(hdf.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
     ok = ok && std::fread(hidf.data(), sizeof(float), x->vocab, f) == (size_t)x->vocab;
-    ok = ok && std::fread(x->h_part.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
+    ok = ok && std::fread(hpart.data(), sizeof(int32_t), x->vocab, f) == (size_t)x->vocab;
     ok = ok && std::fread(sig.data(), sizeof(float), sig.size(), f) == sig.size();
     ok = ok && std::fread(unit.data(), sizeof(float), unit.size(), f) == unit.size();
     ok = ok && std::fread(sh.data(), sizeof(uint64_t), n, f) == n;
@@ -1035,7 +1063,17 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "index load"));
   char* stage = (char*)host_ws(ctx, 4 * (size_t)x->vocab + 4 * (size_t)x->k + 64, &st);
   if (!stage) return bail(st);
-  if ((st = upload_references(ctx, x, hidf.data(), (int32_t*)stage, (float*)(stage + 4 * (size_t)x->vocab))) != MRC_OK)
+  x->h_rnorm.assign(x->k, 0.0);
+  for (int32_t t = 0; t < x->vocab; ++t) {
+    const int32_t q = hpart[t];
+    if (q >= x->k) return bail(fail(ctx, MRC_ERR_INVALID, std::string("not a valid index file: ") + path));
+    if (q >= 0) {
+      const double r = reference_weight(x->params, hidf.data(), t);
+      x->h_rnorm[q] += r * r;
+    }
+  }
+  std::memcpy(stage, hpart.data(), sizeof(int32_t) * x->vocab);
+  if ((st = upload_references(ctx, x, (int32_t*)stage, (float*)(stage + 4 * (size_t)x->vocab))) != MRC_OK)
     return bail(st);
   // compare operands are re-packed from the unit signatures
   if (x->op_hi) cudaMemsetAsync(x->op_hi, 0, 2 * n * x->kp, ctx->stream);

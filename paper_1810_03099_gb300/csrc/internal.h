@@ -74,8 +74,7 @@ struct mrc_index {
   int32_t kp = 0;       // padded row length (elements) of fp16 compare operands
   int32_t kp8 = 0;      // padded row length (bytes) of E4M3 compare operands
   int64_t L_used = 0;
-  // host copies (reference partition of each term, reference norms)
-  std::vector<int32_t> h_part;
+  // reference norms |R_p| (host copy; the partition of each term lives in the device term table)
   std::vector<double> h_rnorm;
   // device arrays
   int32_t* df = nullptr;          // [vocab]
