@@ -19,9 +19,10 @@
 namespace mrc {
 namespace {
 
-constexpr int kTailThreads = 512;
+constexpr int kTailThreads = 768;                      // two CTAs per SM
 constexpr int kTailWarps = kTailThreads / 32;
-constexpr int kMaxWindow = 32768;                      // columns per work item (128 KB of accumulators)
+constexpr int kMaxWindow = 24576;                      // columns per work item (96 KB of accumulators)
+constexpr int kTermBatch = kTailThreads;               // row terms whose postings are flattened together
 constexpr float kTailFix = 1073741824.0f;              // 2^30: tail sums stay below 2^31
 constexpr float kTailInv = 1.0f / 1073741824.0f;
 constexpr int kRankWarps = 8;                          // warps per CTA of the long-list ranking
@@ -252,14 +253,32 @@ __global__ void __launch_bounds__(kTermBlock) k_term_place(const int32_t* __rest
   }
 }
 
-// Position of the (m+1)-th set bit of mask (which has more than m set bits): the smallest p with
-// popc(mask & bits 0..p) > m, by binary search.
-__device__ __forceinline__ int nth_set_bit(unsigned mask, int m) {
-  int p = 0;
+// Exclusive scan of v over the CTA (kTailThreads threads); *total receives the sum. scratch:
+// 33 ints of shared memory. Synchronises the CTA.
+__device__ __forceinline__ int32_t cta_excl_scan(int32_t v, int32_t* scratch, int32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t incl = v;
 #pragma unroll
-  for (int step = 16; step > 0; step >>= 1)
-    if (__popc(mask & (0xffffffffu >> (31 - (p + step - 1)))) <= m) p += step;
-  return p;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int32_t w = lane < kTailWarps ? scratch[lane] : 0;
+    int32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(kFull, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < kTailWarps) scratch[lane] = wi - w;
+    if (lane == 31) scratch[32] = wi;
+  }
+  __syncthreads();
+  *total = scratch[32];
+  return scratch[warp] + incl - v;
 }
 
 // Exact score of one candidate pair (i, j): the head part recomputed from the split head rows
@@ -299,39 +318,48 @@ __device__ __forceinline__ float exact_head(const __half* __restrict__ hhi, cons
 // not depend on the order in which threads add them):
 //  1. acc[j] = 0 over the window;
 //  2. for every tail term t of document i, the postings after i's own position in t's
-//     sorted list are exactly the documents j > i sharing t: acc[j] += w_it * w_jt. Each
-//     warp takes 32 of the row's terms at a time (one lane per term holds its walk range),
-//     moves the non-empty ones to the low lanes and flattens their postings into one
-//     position range (warp prefix sum). A 32-position chunk finds each lane's term from a
-//     ballot and an OR-reduction of the term starts inside the chunk; four chunks' loads
-//     are in flight per lane, so short lists do not leave lanes idle;
+//     sorted list are exactly the documents j > i sharing t: acc[j] += w_it * w_jt. The
+//     CTA takes up to 768 of the row's terms at a time, flattens their postings into one
+//     position range (CTA prefix sum of the list lengths, term tables in shared memory)
+//     and gives every warp an equal slice of it, four loads per lane in flight, so neither
+//     short lists nor uneven terms leave warps idle;
 //  3. scan: H16[i][j] (the fp16 head score from the tensor cores, eight columns per 16-byte
 //     load) + tail >= tau - delta marks a candidate, where delta bounds the head's error;
 //     each candidate's head is recomputed exactly (exact_head) and the pair is kept iff
 //     head + tail >= tau.
-__global__ void __launch_bounds__(kTailThreads, 3) k_cosine_tail(
+__global__ void __launch_bounds__(kTailThreads, 2) k_cosine_tail(
     int32_t n, const __half* __restrict__ H, int64_t ldh, const int64_t* __restrict__ row_off,
     const int32_t* __restrict__ row_cnt, const int2* __restrict__ row_walk, const float* __restrict__ row_w,
     const int2* __restrict__ spost, const __half* __restrict__ hhi,
     const __half* __restrict__ hlo, int32_t kd, float tau, float delta, mrc_pair* pairs,
     unsigned long long* count, int64_t capacity, int32_t window, int32_t n_windows, int64_t n_items,
     unsigned long long* next_item) {
-  extern __shared__ int32_t acc[];
-  __shared__ long long s_item;
+  extern __shared__ int32_t acc[];  // [window] accumulators, then the term tables
+  int32_t* t_st = acc + window;       // [kTermBatch] first remaining posting of each term
+  int32_t* t_ex = t_st + kTermBatch;  // [kTermBatch + 1] flattened start of each term
+  float* t_w = reinterpret_cast<float*>(t_ex + kTermBatch + 1);  // [kTermBatch] the row's weight
+  __shared__ int32_t t_scan[33];
+  __shared__ long long s_item[2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float cand_tau = tau - delta;
-  for (;;) {
-    // work items are taken in row order as CTAs free up: rows differ in cost by orders of
-    // magnitude (long documents, early rows), so a static split leaves CTAs idle
-    __syncthreads();  // the previous item's scan is done with acc and s_item
-    if (threadIdx.x == 0) s_item = (long long)atomicAdd(next_item, 1ull);
-    __syncthreads();
-    const int64_t item = s_item;
+  const bool one_window = n_windows == 1;
+  // Work items are taken in row order as CTAs free up (rows differ in cost by orders of
+  // magnitude: long documents, early rows), one item ahead: the index of the next item is
+  // requested at the start of the current one and read after its first barrier.
+  if (threadIdx.x == 0) s_item[0] = (long long)atomicAdd(next_item, 1ull);
+  __syncthreads();
+  for (int k = 0;; ++k) {
+    const int64_t item = s_item[k & 1];
     if (item >= n_items) break;  // block-uniform
+    __syncthreads();  // every thread has read s_item[k & 1] before it is requested again
+    if (threadIdx.x == 0) s_item[(k + 1) & 1] = (long long)atomicAdd(next_item, 1ull);
     const int32_t i = (int32_t)(item / n_windows);
     const int32_t base = (int32_t)(item % n_windows) * window;  // a multiple of 8 (window is)
     const int32_t lo = max(i + 1, base), hi = min(n, base + window);
-    if (lo >= hi) continue;  // block-uniform
+    if (lo >= hi) {  // block-uniform
+      __syncthreads();  // publishes s_item[(k + 1) & 1]
+      continue;
+    }
     const __half* hrow = H + (int64_t)i * ldh;
     {  // pull this item's head scores toward L2 while the tail sums are built (one 128-byte line
        // per thread covers 32768 columns, the largest window)
@@ -344,9 +372,9 @@ __global__ void __launch_bounds__(kTailThreads, 3) k_cosine_tail(
     __syncthreads();
     const int32_t nt = row_cnt[i];
     const int64_t ro = row_off[i];
-    for (int32_t b0 = warp; b0 < nt; b0 += 32 * kTailWarps) {
-      // lane l holds term b0 + 16 l: its remaining postings [st, st + cnt) (documents > i)
-      const int32_t r = b0 + kTailWarps * lane;
+    for (int32_t b0 = 0; b0 < nt; b0 += kTermBatch) {
+      // term r = b0 + thread: its remaining postings [st, st + cnt) (documents > i)
+      const int32_t r = b0 + threadIdx.x;
       int32_t st = 0, cnt = 0;
       float wi = 0.f;
       if (r < nt) {
@@ -355,53 +383,52 @@ __global__ void __launch_bounds__(kTailThreads, 3) k_cosine_tail(
         cnt = wk.y - wk.x;
         wi = row_w[ro + r];
       }
-      // move the terms with postings left to the low lanes, in order
-      const unsigned live = __ballot_sync(kFull, cnt > 0);
-      const int nlive = __popc(live);
-      if (nlive == 0) continue;  // warp-uniform
-      const int from = nth_set_bit(live, lane < nlive ? lane : 0);
-      st = __shfl_sync(kFull, st, from);
-      cnt = __shfl_sync(kFull, cnt, from);
-      wi = __shfl_sync(kFull, wi, from);
-      if (lane >= nlive) cnt = 0;
-      // flatten: live term k owns positions [ex_k, ex_k + cnt_k) of the warp's posting range
-      int32_t incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
+      int32_t total;
+      const int32_t ex = cta_excl_scan(cnt, t_scan, &total);  // synchronises the CTA
+      const int32_t nterm = min(kTermBatch, nt - b0);
+      t_st[threadIdx.x] = st - ex;  // posting index = t_st[term] + flattened position
+      t_ex[threadIdx.x] = ex;
+      t_w[threadIdx.x] = wi * kTailFix;
+      if (threadIdx.x == 0) t_ex[nterm] = total;
+      __syncthreads();
+      // the batch's postings flattened into [0, total); each warp takes an equal slice. A
+      // lane finds the term of its first position by binary search (the last term whose
+      // start <= position is the non-empty one) and then only moves forward.
+      const int32_t s0 = (int32_t)((int64_t)total * warp / kTailWarps);
+      const int32_t s1 = (int32_t)((int64_t)total * (warp + 1) / kTailWarps);
+      int32_t own = 0;
+      {
+        const int32_t f = s0 + lane;
+        int32_t a = 0, c = nterm;  // t_ex[a] <= f < t_ex[c]
+        while (c - a > 1) {
+          const int32_t m = (a + c) >> 1;
+          if (t_ex[m] <= f) a = m; else c = m;
+        }
+        own = a;
       }
-      const int32_t total = __shfl_sync(kFull, incl, 31);
-      const int32_t ex = lane < nlive ? incl - cnt : 0x7fffffff;  // strictly increasing over live lanes
-      for (int32_t f0 = 0; f0 < total; f0 += 32 * kWalkChunks) {
-        int32_t jd[kWalkChunks];
+      for (int32_t f0 = s0; f0 < s1; f0 += 32 * kWalkChunks) {
+        int2 pv[kWalkChunks];
         float wv[kWalkChunks];
 #pragma unroll
         for (int u = 0; u < kWalkChunks; ++u) {
-          const int32_t cs = f0 + 32 * u;  // this chunk's first position (warp-uniform)
-          jd[u] = -1;
+          const int32_t f = f0 + 32 * u + lane;
+          pv[u] = make_int2(-1, 0);
           wv[u] = 0.f;
-          if (cs < total) {
-            // owner of position cs + lane: the owner of cs plus the terms starting in (cs, cs + lane]
-            const int kb = __popc(__ballot_sync(kFull, ex <= cs)) - 1;
-            const int32_t dlt = ex - cs;
-            const unsigned starts = __reduce_or_sync(kFull, (dlt > 0 && dlt < 32) ? (1u << dlt) : 0u);
-            const int k = kb + __popc(starts & (0xffffffffu >> (31 - lane)));
-            const int32_t sk = __shfl_sync(kFull, st, k), ek = __shfl_sync(kFull, ex, k);
-            const float wk = __shfl_sync(kFull, wi, k);
-            const int32_t f = cs + lane;
-            if (f < total) {
-              const int32_t x = sk + (f - ek);
-              const int2 pv = spost[x];  // (document, weight) of the posting
-              jd[u] = pv.x;
-              wv[u] = wk * __int_as_float(pv.y);
-            }
+          if (f < s1) {
+            while (t_ex[own + 1] <= f) ++own;
+            pv[u] = spost[t_st[own] + f];  // (document, weight) of the posting
+            wv[u] = t_w[own];
           }
         }
+        // with one window per row every posting after i lies in [i + 1, n)
 #pragma unroll
-        for (int u = 0; u < kWalkChunks; ++u)
-          if (jd[u] >= lo && jd[u] < hi) atomicAdd(&acc[jd[u] - base], __float2int_rn(wv[u] * kTailFix));
+        for (int u = 0; u < kWalkChunks; ++u) {
+          const int32_t j = pv[u].x;
+          if (one_window ? j >= 0 : (j >= lo && j < hi))
+            atomicAdd(&acc[j - base], __float2int_rn(wv[u] * __int_as_float(pv[u].y)));
+        }
       }
+      __syncthreads();  // the next batch rewrites the term tables
     }
     __syncthreads();
     // scan: each lane takes eight consecutive columns (one 16-byte load of H16, in the row's
@@ -415,13 +442,21 @@ __global__ void __launch_bounds__(kTailThreads, 3) k_cosine_tail(
         const int4 t0 = *reinterpret_cast<const int4*>(acc + (g - base));
         const int4 t1 = *reinterpret_cast<const int4*>(acc + (g - base) + 4);
         const int32_t tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+        float sv[8];  // head + tail (the 2^-30 scaling is exact)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const float2 hf = __half22float2(h2[u]);
-          const int32_t ja = g + 2 * u;
-          if (ja >= lo && ja < hi && hf.x + (float)tv[2 * u] * kTailInv >= cand_tau) mask |= 1u << (2 * u);
-          if (ja + 1 >= lo && ja + 1 < hi && hf.y + (float)tv[2 * u + 1] * kTailInv >= cand_tau)
-            mask |= 2u << (2 * u);
+          sv[2 * u] = fmaf((float)tv[2 * u], kTailInv, hf.x);
+          sv[2 * u + 1] = fmaf((float)tv[2 * u + 1], kTailInv, hf.y);
+        }
+        // one comparison for the eight columns; the bounds only matter for the rare hits
+        // (columns outside [lo, hi) hold stale values)
+        const float mx = fmaxf(fmaxf(fmaxf(sv[0], sv[1]), fmaxf(sv[2], sv[3])),
+                               fmaxf(fmaxf(sv[4], sv[5]), fmaxf(sv[6], sv[7])));
+        if (mx >= cand_tau) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (g + e >= lo && g + e < hi && sv[e] >= cand_tau) mask |= 1u << e;
         }
       }
       unsigned todo = __ballot_sync(kFull, mask != 0);
@@ -539,7 +574,7 @@ cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t
   const int32_t window = (int32_t)(n8 < kMaxWindow ? n8 : kMaxWindow);  // a multiple of 8
   const int32_t n_windows = (int32_t)((n + window - 1) / window);
   const int64_t n_items = n * n_windows;
-  const size_t smem = sizeof(int32_t) * (size_t)window;
+  const size_t smem = sizeof(int32_t) * ((size_t)window + 3 * kTermBatch + 1);
   const int per_sm = resident_ctas(k_cosine_tail, kTailThreads, smem);
   if (per_sm <= 0) return cudaErrorInvalidConfiguration;
   int64_t grid = (int64_t)ctx->num_sms * per_sm;
