@@ -15,6 +15,7 @@ and device->host copies of every pair list inside the timed region).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -34,6 +35,35 @@ HMAX = 3
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
+# the news20 step, valid only while the kernel's source file is unchanged since the capture.
+NCU_TRAFFIC = {
+    "cosine_tail": ("paper_1810_03099_gb300/csrc/tail.cu",
+                    "2ca969a90258090a3f42e445e7b26ec9e0fa34a6cbbdbf3735e81b2468f74037", 416108032),
+    "gemm_f16_store": ("paper_1810_03099_gb300/csrc/compare_tc.cu",
+                       "cfc6bb80e5563bfcceb64c7bf1cf6f7311a04e661ff2fa2d596671454a3713f0", 351628800),
+}
+KERNEL_NOTES = {
+    "cosine_tail": "algorithmic bytes = the fp16 head scores of the upper triangle; the postings it also walks "
+                   "are L2-resident. ncu: issue-active 66%, l1tex 53%: instruction/latency-bound, not HBM-bound",
+    "gemm_f16_store": "2 kd flops per pair of the triangle (kd = 1024 head columns); tensor pipe 60% active "
+                      "(ncu), L2 66% busy with operand reloads",
+}
+
+
+def ncu_traffic(name):
+    if name not in NCU_TRAFFIC:
+        return None
+    path, digest, nbytes = NCU_TRAFFIC[name]
+    try:
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
+    except OSError:
+        return None
+    return nbytes
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -45,7 +75,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -60,7 +90,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:  # noqa: BLE001
@@ -303,7 +333,7 @@ BASE_QUERY_SEED = 1810031999
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mrc", choices=["mrc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -410,20 +440,27 @@ def main():
         per = s["ms"] / max(s["launches"], 1)
         kernels.append({"name": s["name"], "launches": s["launches"], "ms_per_launch": per,
                         "share": s["ms"] / max(sum(x["ms"] for x in stats), 1e-9)})
-    if top:
-        per_launch_s = top["ms"] / top["launches"] / 1e3
-        if top["flops"] > 0 and top["name"].startswith("gemm"):
-            achieved = top["flops"] / top["launches"] / per_launch_s / 1e12
+    def kernel_roofline(s):
+        per_launch_s = s["ms"] / s["launches"] / 1e3
+        if s["flops"] > 0 and s["name"].startswith("gemm"):
+            achieved = s["flops"] / s["launches"] / per_launch_s / 1e12
             peak = peaks["bf16_tflops"]
-            roofline = {"bound": "tensor", "kernel": top["name"], "achieved": achieved, "peak": peak,
-                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                        "peak_source": peaks["source"] + " bf16 burst (fp16 same rate)",
-                        "note": "executed split-fp16 flops (3 products per term pair)"}
+            r = {"bound": "tensor", "kernel": s["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                 "frac": achieved / peak, "traffic": ncu_traffic(s["name"]),
+                 "peak_source": peaks["source"] + " bf16 burst (fp16 same rate)"}
         else:
-            achieved = top["bytes"] / top["launches"] / per_launch_s / 1e9
+            achieved = s["bytes"] / s["launches"] / per_launch_s / 1e9
             peak = peaks["hbm_gbs"]
-            roofline = {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": None, "peak_source": peaks["source"]}
+            r = {"bound": "hbm", "kernel": s["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                 "frac": achieved / peak, "traffic": ncu_traffic(s["name"]), "peak_source": peaks["source"]}
+        if s["name"] in KERNEL_NOTES:
+            r["note"] = KERNEL_NOTES[s["name"]]
+        return r
+
+    ranked = sorted(stats, key=lambda s: -s["ms"])
+    if top:
+        roofline = kernel_roofline(top)
+    others = [kernel_roofline(s) for s in ranked[1:3] if s["bytes"] > 0 or s["flops"] > 0]
     gpu_launches = int(sum(s["launches"] for s in stats))
 
     line = {
@@ -440,7 +477,8 @@ def main():
         "clocks": clk,
         "pairs": counts,
         "signature_pairs_per_s": None,
-        "kernels": kernels[:8],
+        "rooflines_next": others,
+        "kernels": kernels,
     }
     sig_k = [s for s in stats if s["name"] == "gemm_split16_thresh"]
     if sig_k:

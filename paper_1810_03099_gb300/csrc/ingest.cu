@@ -552,11 +552,15 @@ __global__ void k_place_long(const int64_t* off, int64_t n, int32_t* long_list, 
   long_list[base + atomicAdd(&counts[kCntClassFill + c], 1)] = (int32_t)i;
 }
 
-void launch_classify(cudaStream_t stream, const int64_t* off, int64_t n, int32_t* short_list, int32_t* long_list,
+void launch_classify(mrc_ctx* ctx, const int64_t* off, int64_t n, int32_t* short_list, int32_t* long_list,
                      int32_t* counts, int32_t* err) {
   const unsigned blocks = (unsigned)((n + 255) / 256);
-  k_classify<<<blocks, 256, 0, stream>>>(off, n, short_list, counts, err);
-  k_place_long<<<blocks, 256, 0, stream>>>(off, n, long_list, counts);
+  {
+    KernelTimer kt(ctx, "classify", 8.0 * (double)(n + 1));
+    k_classify<<<blocks, 256, 0, ctx->stream>>>(off, n, short_list, counts, err);
+  }
+  KernelTimer kt(ctx, "place_long", 8.0 * (double)(n + 1));
+  k_place_long<<<blocks, 256, 0, ctx->stream>>>(off, n, long_list, counts);
 }
 
 __global__ void k_idf(int64_t n_docs, const int32_t* df, int32_t vocab, int32_t weighting, float* idf,
@@ -636,7 +640,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * kCntWords, ctx->stream);
   if (e != cudaSuccess) return e;
   if (d.n_docs <= 0) return cudaSuccess;
-  launch_classify(ctx->stream, d.offsets, d.n_docs, short_list, long_list, counts, d.err);
+  launch_classify(ctx, d.offsets, d.n_docs, short_list, long_list, counts, d.err);
   p.short_list = short_list;
   p.long_list = long_list;
   p.list_counts = counts;
@@ -711,12 +715,14 @@ __global__ void k_term_info(const float* idf, const int32_t* part, int32_t vocab
 
 cudaError_t launch_term_info(mrc_ctx* ctx, const float* idf, const int32_t* part, int32_t vocab, int32_t tfidf,
                              int32_t bf16, TermInfo* tinfo) {
+  KernelTimer kt(ctx, "term_info", 16.0 * vocab);
   k_term_info<<<(vocab + 255) / 256, 256, 0, ctx->stream>>>(idf, part, vocab, tfidf, bf16, tinfo);
   return cudaGetLastError();
 }
 
 cudaError_t launch_idf(mrc_ctx* ctx, int64_t n_docs, const int32_t* df, int32_t vocab, int32_t weighting, float* idf,
                        TermInfo* tinfo) {
+  KernelTimer kt(ctx, "idf", 8.0 * vocab);
   k_idf<<<(vocab + 255) / 256, 256, 0, ctx->stream>>>(n_docs, df, vocab, weighting, idf, tinfo);
   return cudaGetLastError();
 }
@@ -739,6 +745,7 @@ cudaError_t launch_pack(mrc_ctx* ctx, const float* sig, int64_t n, int32_t k, in
                         void* e4m3, float* qnorm, float* unit, int32_t kp, int32_t kp8) {
   if (n <= 0) return cudaSuccess;
   const int64_t threads = n * 32;
+  KernelTimer kt(ctx, "pack", 8.0 * (double)n * k);
   k_pack<<<(unsigned)((threads + 255) / 256), 256, 0, ctx->stream>>>(sig, n, k, normalize, hi, lo, e4m3, qnorm,
                                                                       unit, kp, kp8);
   return cudaGetLastError();
@@ -761,6 +768,7 @@ __global__ void k_block_min(const float* norm, int64_t n, float* out) {
 cudaError_t launch_block_min(mrc_ctx* ctx, const float* norm, int64_t n, float* out) {
   const int64_t blocks = (n + 127) / 128;
   if (blocks <= 0) return cudaSuccess;
+  KernelTimer kt(ctx, "block_min", 4.0 * (double)n);
   k_block_min<<<(unsigned)((blocks * 32 + 255) / 256), 256, 0, ctx->stream>>>(norm, n, out);
   return cudaGetLastError();
 }
@@ -800,7 +808,7 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
   cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * kCntWords, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int32_t), ctx->stream);
   if (e != cudaSuccess) return e;
-  if (d.n_docs > 0) launch_classify(ctx->stream, d.offsets, d.n_docs, short_list, long_list, counts, err);
+  if (d.n_docs > 0) launch_classify(ctx, d.offsets, d.n_docs, short_list, long_list, counts, err);
   int32_t h[5] = {0, 0, 0, 0, 0};
   e = cudaMemcpyAsync(h, counts, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h + 4, err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);

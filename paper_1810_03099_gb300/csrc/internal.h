@@ -112,6 +112,17 @@ int resident_ctas(K* kernel, int threads, size_t smem) {
 // ---- timing helpers (api.cu) ----
 void timing_begin(mrc_ctx* ctx, const char* name, double bytes, double flops, cudaEvent_t* ev_out);
 void timing_end(mrc_ctx* ctx, cudaEvent_t start);
+// Times the launches made during its lifetime under `name` (when the context's timing is on).
+struct KernelTimer {
+  mrc_ctx* ctx;
+  cudaEvent_t ev = nullptr;
+  KernelTimer(mrc_ctx* c, const char* name, double bytes = 0.0, double flops = 0.0) : ctx(c) {
+    timing_begin(c, name, bytes, flops, &ev);
+  }
+  ~KernelTimer() { timing_end(ctx, ev); }
+  KernelTimer(const KernelTimer&) = delete;
+  KernelTimer& operator=(const KernelTimer&) = delete;
+};
 
 // ---- launchers ----
 struct DocsDev {

@@ -518,13 +518,17 @@ cudaError_t launch_cosine_terms(mrc_ctx* ctx, const int32_t* df, int32_t V, int3
   if (V <= 0) return cudaErrorInvalidValue;
   const int64_t nb = ((int64_t)V + kTermBlock - 1) / kTermBlock;
   if (nb > 0x7fffffff) return cudaErrorInvalidValue;
-  cudaEvent_t ev = nullptr;
-  timing_begin(ctx, "term_split", 0.0, 0.0, &ev);
-  k_term_count<<<(unsigned)nb, kTermBlock, 0, ctx->stream>>>(df, V, cut, part);
-  k_term_scan<<<1, kTermBlock, 0, ctx->stream>>>(part, nb, summary);
+  {
+    KernelTimer kt(ctx, "term_count", 4.0 * V);
+    k_term_count<<<(unsigned)nb, kTermBlock, 0, ctx->stream>>>(df, V, cut, part);
+  }
+  {
+    KernelTimer kt(ctx, "term_scan", 96.0 * nb);
+    k_term_scan<<<1, kTermBlock, 0, ctx->stream>>>(part, nb, summary);
+  }
+  KernelTimer kt(ctx, "term_place", 28.0 * V);
   k_term_place<<<(unsigned)nb, kTermBlock, 0, ctx->stream>>>(df, V, cut, part, summary, colmap, tstart, cstart,
                                                              rank_terms);
-  timing_end(ctx, ev);
   return cudaGetLastError();
 }
 
@@ -532,12 +536,11 @@ cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int3
                                  const int32_t* big_terms, int32_t n_big, int32_t max_m, const int32_t* post_doc,
                                  const float* post_w, const int32_t* post_r, const int64_t* doc_off, void* spost,
                                  void* row_walk) {
-  cudaEvent_t ev = nullptr;
-  timing_begin(ctx, "rank_postings", 0.0, 0.0, &ev);
   if (n_small > 0) {
     int64_t grid = (int64_t)ctx->num_sms * resident_ctas(k_rank_small, 256, 0);
     const int64_t need = ((int64_t)n_small + 7) / 8;
     if (need < grid) grid = need;
+    KernelTimer kt(ctx, "rank_small");
     k_rank_small<<<(unsigned)grid, 256, 0, ctx->stream>>>(cstart, small_terms, n_small, post_doc, post_w, post_r,
                                                            doc_off, reinterpret_cast<int2*>(spost),
                                                            reinterpret_cast<int2*>(row_walk));
@@ -550,12 +553,12 @@ cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int3
     int64_t grid = (int64_t)ctx->num_sms * per_sm;
     const int64_t need = ((int64_t)n_big + kRankWarps - 1) / kRankWarps;
     if (need < grid) grid = need;
+    KernelTimer kt(ctx, "rank_big");
     k_rank_big<<<(unsigned)grid, kRankWarps * 32, smem, ctx->stream>>>(cstart, big_terms, n_big, buf, post_doc,
                                                                        post_w, post_r, doc_off,
                                                                        reinterpret_cast<int2*>(spost),
                                                                        reinterpret_cast<int2*>(row_walk));
   }
-  timing_end(ctx, ev);
   return cudaGetLastError();
 }
 
