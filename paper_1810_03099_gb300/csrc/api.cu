@@ -208,6 +208,23 @@ int32_t* call_err(mrc_ctx* ctx, mrc_status* st) {
   return e;
 }
 
+// Attaches a bag-of-terms workspace to d when it fits (8 bytes per token, at most 16 GB), so
+// that a call's second pass over the same documents reads the bag instead of hashing again.
+void attach_bag(mrc_ctx* ctx, DocsDev* d) {
+  if (d->n_tokens <= 0 || 8.0 * (double)d->n_tokens > 16e9) return;
+  mrc_status st = MRC_OK;
+  int32_t* terms = (int32_t*)ws_get(ctx, "bag.terms", sizeof(int32_t) * (size_t)d->n_tokens, &st);
+  int32_t* cnts = (int32_t*)ws_get(ctx, "bag.cnts", sizeof(int32_t) * (size_t)d->n_tokens, &st);
+  int32_t* n = (int32_t*)ws_get(ctx, "bag.n", sizeof(int32_t) * (size_t)std::max<int64_t>(d->n_docs, 1), &st);
+  if (st != MRC_OK) {  // not enough memory for the bag: the second pass hashes again
+    ctx->last_error.clear();
+    return;
+  }
+  d->bag_terms = terms;
+  d->bag_cnts = cnts;
+  d->bag_n = n;
+}
+
 // Docs on the device: host arrays are copied in; returns MRC_OK or an error.
 mrc_status stage_docs(mrc_ctx* ctx, const mrc_docs* docs, const char* tag, DocsDev* out, int32_t* d_err) {
   if (!docs || docs->n_docs < 0 || (docs->n_docs > 0 && (!docs->offsets)))
@@ -603,8 +620,12 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   cudaError_t e = cudaMemsetAsync(x->df, 0, sizeof(int32_t) * vocab, ctx->stream);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
 
-  // a1: document frequencies, then idf
+  // a1: document frequencies (storing each document's bag of terms), then idf
+  attach_bag(ctx, &d);
+  d.bag_write = 1;
   e = launch_df(ctx, d, x->df, vocab);
+  d.bag_write = 0;
+  d.bag_read = 1;
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "df pass"));
   e = launch_idf(ctx, d.n_docs, x->df, vocab, params->weighting, x->idf, nullptr);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "idf"));
@@ -794,7 +815,11 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   cudaMemsetAsync(df, 0, sizeof(int32_t) * V, ctx->stream);
   cudaMemsetAsync(d_cstart, 0, sizeof(int64_t), ctx->stream);
   const float* wid = index->params.weighting == MRC_WEIGHT_TFIDF ? index->idf : nullptr;
+  attach_bag(ctx, &d);
+  d.bag_write = 1;
   cudaError_t e = launch_df_norm(ctx, d, df, V, wid, d_norm);
+  d.bag_write = 0;
+  d.bag_read = 1;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "df pass");
   e = launch_cosine_terms(ctx, df, V, cut, d_tpart, d_tsum, d_colmap, d_tstart, d_cstart, d_rank_terms);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "head/tail split");

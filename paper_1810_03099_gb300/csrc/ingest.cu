@@ -145,6 +145,13 @@ struct IngestParams {
   SigOut sig;
   // DENSE
   DenseOut dense;
+  // Bag of terms of every document, (term, count) pairs at the document's token offsets and
+  // the number of pairs per document: a pass with bag_write stores the bag it builds, a later
+  // pass over the same documents with bag_read takes it instead of hashing the tokens again.
+  int32_t* bag_terms;
+  int32_t* bag_cnts;
+  int32_t* bag_n;
+  int32_t bag_write, bag_read;
 };
 
 // Per-group accumulators of the SIG and DENSE modes.
@@ -285,6 +292,58 @@ __device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsi
   }
 }
 
+// Builds the bag of terms of one document (<= kShortMax tokens) in a warp's table of 2^l2
+// slots: clears the table, inserts every token (all of the document's token loads in flight
+// at once, 16 per lane; inserts in batches of 8 with their compare-and-swaps in flight
+// together), then compacts the occupied slots to the front. Returns the number of distinct
+// terms (<= 2^l2 / 2).
+__device__ __forceinline__ int warp_hash_doc(const IngestParams& p, uint32_t* keys, uint32_t* cnts, int l2, int64_t o0,
+                                             int64_t len, int lane) {
+  const int ts = 1 << l2;
+  for (int s = lane; s < ts; s += 32) {
+    keys[s] = kEmpty;
+    cnts[s] = 0u;
+  }
+  int32_t tk[kShortRegs];
+#pragma unroll
+  for (int u = 0; u < kShortRegs; ++u) tk[u] = lane + 32 * u < len ? __ldcs(p.tokens + o0 + lane + 32 * u) : -1;
+  __syncwarp();
+#pragma unroll
+  for (int h = 0; h < kShortRegs; h += 8) {
+    if (32 * h >= len) break;  // warp-uniform
+    int32_t tb[8];
+    uint32_t pend = 0u;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      tb[u] = tk[h + u];
+      if (lane + 32 * (h + u) < len) {
+        if ((uint32_t)tb[u] >= (uint32_t)p.vocab)
+          set_err(p.err, kErrBadToken);
+        else
+          pend |= 1u << u;
+      }
+    }
+    if (!table_insert_batch<8>(keys, cnts, l2, tb, pend)) set_err(p.err, kErrTable);
+  }
+  __syncwarp();
+  // compact the occupied slots to the front, in place (a write never passes an unread slot)
+  int nnz = 0;
+  for (int s0 = 0; s0 < ts; s0 += 32) {
+    const uint32_t key = keys[s0 + lane], c = cnts[s0 + lane];
+    const bool valid = key != kEmpty;
+    const unsigned bal = __ballot_sync(kFull, valid);
+    __syncwarp();
+    if (valid) {
+      const int at = nnz + __popc(bal & ((1u << lane) - 1u));
+      keys[at] = key;
+      cnts[at] = c;
+    }
+    nnz += __popc(bal);
+    __syncwarp();
+  }
+  return nnz;
+}
+
 // ---------------------------------------------------------------- warp path
 template <int MODE>
 __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestParams p) {
@@ -311,50 +370,39 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
     const int64_t o0 = p.offsets[d], len = p.offsets[d + 1] - o0;
     const int l2 = log2_slots(len, 10);
     const int ts = 1 << l2;
-    for (int s = lane; s < ts; s += 32) {
-      keys[s] = kEmpty;
-      cnts[s] = 0u;
-    }
     for (int q = lane; q < kq; q += 32) num_q[q] = 0ull;
     if (lane == 0) *row_cnt_s = 0;
-    // all of the document's token loads in flight at once (len <= 512: 16 per lane), then
-    // inserts in batches of 8 with their compare-and-swaps in flight together
-    int32_t tk[kShortRegs];
+    int nnz = 0;
+    if (p.bag_read) {
+      // the document's bag, built by an earlier pass: (term, count) pairs, four loads in flight
+      nnz = p.bag_n[d];
+      for (int s0 = 0; s0 < nnz; s0 += 4 * 32) {
+        int32_t bt[4], bc[4];
 #pragma unroll
-    for (int u = 0; u < kShortRegs; ++u) tk[u] = lane + 32 * u < len ? __ldcs(p.tokens + o0 + lane + 32 * u) : -1;
-    __syncwarp();
+        for (int u = 0; u < 4; ++u) {
+          const int sl = s0 + 32 * u + lane;
+          bt[u] = sl < nnz ? __ldcs(p.bag_terms + o0 + sl) : 0;
+          bc[u] = sl < nnz ? __ldcs(p.bag_cnts + o0 + sl) : 0;
+        }
 #pragma unroll
-    for (int h = 0; h < kShortRegs; h += 8) {
-      if (32 * h >= len) break;  // warp-uniform
-      int32_t tb[8];
-      uint32_t pend = 0u;
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        tb[u] = tk[h + u];
-        if (lane + 32 * (h + u) < len) {
-          if ((uint32_t)tb[u] >= (uint32_t)p.vocab)
-            set_err(p.err, kErrBadToken);
-          else
-            pend |= 1u << u;
+        for (int u = 0; u < 4; ++u) {
+          const int sl = s0 + 32 * u + lane;
+          if (sl < nnz) {
+            keys[sl] = (uint32_t)bt[u];
+            cnts[sl] = (uint32_t)bc[u];
+          }
         }
       }
-      if (!table_insert_batch<8>(keys, cnts, l2, tb, pend)) set_err(p.err, kErrTable);
-    }
-    __syncwarp();
-    // compact the occupied slots to the front, in place (a write never passes an unread slot)
-    int nnz = 0;
-    for (int s0 = 0; s0 < ts; s0 += 32) {
-      const uint32_t key = keys[s0 + lane], c = cnts[s0 + lane];
-      const bool valid = key != kEmpty;
-      const unsigned bal = __ballot_sync(kFull, valid);
       __syncwarp();
-      if (valid) {
-        const int at = nnz + __popc(bal & ((1u << lane) - 1u));
-        keys[at] = key;
-        cnts[at] = c;
+    } else {
+      nnz = warp_hash_doc(p, keys, cnts, l2, o0, len, lane);
+      if (p.bag_write) {
+        for (int sl = lane; sl < nnz; sl += 32) {
+          p.bag_terms[o0 + sl] = (int32_t)keys[sl];
+          p.bag_cnts[o0 + sl] = (int32_t)cnts[sl];
+        }
+        if (lane == 0) p.bag_n[d] = nnz;
       }
-      nnz += __popc(bal);
-      __syncwarp();
     }
     // gather the terms' table values into the free upper half of the table (nnz <= ts / 2),
     // eight loads per lane in flight
@@ -402,18 +450,57 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
   }
 }
 
+// The CTA's warps walk table slots [0, lim) in 32-slot chunks, each with the next chunk's
+// table values already in flight. With bag_cursor, the occupied slots of each chunk are also
+// appended to the document's bag (coalesced; the bag's order does not matter to any pass:
+// every sum over it is an integer sum).
+template <int MODE>
+__device__ __forceinline__ void cta_walk(const IngestParams& p, const uint32_t* keys, const uint32_t* cnts, int lim,
+                                         int warp, int lane, unsigned long long* num_q, Acc& a, int64_t d,
+                                         float inv_norm, int32_t* row_cnt_s, int64_t o0, int32_t* bag_cursor) {
+  constexpr int nwarps = kLongThreads / 32;
+  int s0 = warp * 32;
+  uint32_t key = s0 + lane < lim ? keys[s0 + lane] : kEmpty;
+  uint32_t c = key != kEmpty ? cnts[s0 + lane] : 0u;
+  TermAux ax{1.0f, 0};
+  if (MODE != kDF && key != kEmpty) ax = load_aux<MODE>(p, key);
+  while (s0 < lim) {
+    const int s1 = s0 + nwarps * 32;
+    const uint32_t key1 = s1 + lane < lim ? keys[s1 + lane] : kEmpty;
+    const uint32_t c1 = key1 != kEmpty ? cnts[s1 + lane] : 0u;
+    TermAux ax1{1.0f, 0};
+    if (MODE != kDF && key1 != kEmpty) ax1 = load_aux<MODE>(p, key1);
+    const unsigned occ = __ballot_sync(kFull, key != kEmpty);
+    if (occ != 0u) {
+      chunk<MODE>(p, key, c, ax, lane, num_q, a, d, inv_norm, row_cnt_s, o0);
+      if (bag_cursor) {
+        int32_t at = 0;
+        if (lane == 0) at = atomicAdd(bag_cursor, __popc(occ));
+        at = __shfl_sync(kFull, at, 0) + __popc(occ & ((1u << lane) - 1u));
+        if (key != kEmpty) {
+          p.bag_terms[o0 + at] = (int32_t)key;
+          p.bag_cnts[o0 + at] = (int32_t)c;
+        }
+      }
+    }
+    s0 = s1;
+    key = key1;
+    c = c1;
+    ax = ax1;
+  }
+}
+
 // ---------------------------------------------------------------- CTA path
 template <int MODE>
 __global__ void __launch_bounds__(kLongThreads, 2) k_ingest_long(IngestParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int nwarps = kLongThreads / 32;
   const int kq = MODE == kSIG ? p.k : 0;
   unsigned long long* num_q = reinterpret_cast<unsigned long long*>(smem);
   unsigned long long* norm_s = num_q + kq;
   uint32_t* P = reinterpret_cast<uint32_t*>(norm_s + 1);  // [64]
   int32_t* misc = reinterpret_cast<int32_t*>(P + 64);     // [0] doc slot, [1] row count
-  uint32_t* keys = reinterpret_cast<uint32_t*>(misc + 4);
+  uint32_t* keys = reinterpret_cast<uint32_t*>(misc + 4);  // misc: [0] doc slot, [1] row count, [2] bag size
   uint32_t* cnts = keys + kLongSlots;
 
   const int32_t n_long = p.list_counts[1];
@@ -436,53 +523,65 @@ __global__ void __launch_bounds__(kLongThreads, 2) k_ingest_long(IngestParams p)
     Acc a{0ull, 0u, 0u};
     float inv_norm = 0.f;
     if (MODE == kDENSE) inv_norm = inv_norm_of(p.dense.norm[d]);
-    for (uint32_t pass = 0; pass < passes; ++pass) {
-      __syncthreads();
-      for (int s = threadIdx.x; s < ts; s += kLongThreads) {
-        keys[s] = kEmpty;
-        cnts[s] = 0u;
-      }
-      __syncthreads();
-      for (int64_t x0 = threadIdx.x; x0 < len; x0 += kLongUnroll * kLongThreads) {
-        int32_t tk[kLongUnroll];  // kLongUnroll token loads in flight per thread
+    if (p.bag_read) {
+      // the document's bag, built by an earlier pass, in table-sized slices
+      const int32_t nb = p.bag_n[d];
+      for (int32_t b0 = 0; b0 < nb; b0 += kLongSlots) {
+        const int32_t m = min(kLongSlots, nb - b0);
+        __syncthreads();
+        for (int32_t x0 = threadIdx.x; x0 < m; x0 += 4 * kLongThreads) {
+          int32_t bt[4], bc[4];
 #pragma unroll
-        for (int u = 0; u < kLongUnroll; ++u) {
-          const int64_t x = x0 + u * kLongThreads;
-          tk[u] = x < len ? __ldcs(p.tokens + o0 + x) : -1;
-        }
-        uint32_t pend = 0u;
-#pragma unroll
-        for (int u = 0; u < kLongUnroll; ++u) {
-          if (x0 + u * kLongThreads >= len) break;
-          const int32_t t = tk[u];
-          if ((uint32_t)t >= (uint32_t)p.vocab) {
-            if (pass == 0) set_err(p.err, kErrBadToken);
-            continue;
+          for (int u = 0; u < 4; ++u) {
+            const int32_t x = x0 + u * kLongThreads;
+            bt[u] = x < m ? __ldcs(p.bag_terms + o0 + b0 + x) : 0;
+            bc[u] = x < m ? __ldcs(p.bag_cnts + o0 + b0 + x) : 0;
           }
-          if (passes > 1 && pass_of((uint32_t)t, passes) != pass) continue;
-          pend |= 1u << u;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int32_t x = x0 + u * kLongThreads;
+            if (x < m) {
+              keys[x] = (uint32_t)bt[u];
+              cnts[x] = (uint32_t)bc[u];
+            }
+          }
         }
-        if (!table_insert_batch<kLongUnroll>(keys, cnts, l2, tk, pend)) set_err(p.err, kErrTable);
+        __syncthreads();
+        cta_walk<MODE>(p, keys, cnts, m, warp, lane, num_q, a, d, inv_norm, &misc[1], o0, nullptr);
       }
-      __syncthreads();
-      // each warp walks its chunks with the next chunk's table values already in flight
-      int s0 = warp * 32;
-      uint32_t key = s0 + lane < ts ? keys[s0 + lane] : kEmpty;
-      uint32_t c = key != kEmpty ? cnts[s0 + lane] : 0u;
-      TermAux ax{1.0f, 0};
-      if (MODE != kDF && key != kEmpty) ax = load_aux<MODE>(p, key);
-      while (s0 < ts) {
-        const int s1 = s0 + nwarps * 32;
-        const uint32_t key1 = s1 + lane < ts ? keys[s1 + lane] : kEmpty;
-        const uint32_t c1 = key1 != kEmpty ? cnts[s1 + lane] : 0u;
-        TermAux ax1{1.0f, 0};
-        if (MODE != kDF && key1 != kEmpty) ax1 = load_aux<MODE>(p, key1);
-        if (__ballot_sync(kFull, key != kEmpty) != 0u)
-          chunk<MODE>(p, key, c, ax, lane, num_q, a, d, inv_norm, &misc[1], o0);
-        s0 = s1;
-        key = key1;
-        c = c1;
-        ax = ax1;
+    } else {
+      if (threadIdx.x == 0) misc[2] = 0;
+      for (uint32_t pass = 0; pass < passes; ++pass) {
+        __syncthreads();
+        for (int s = threadIdx.x; s < ts; s += kLongThreads) {
+          keys[s] = kEmpty;
+          cnts[s] = 0u;
+        }
+        __syncthreads();
+        for (int64_t x0 = threadIdx.x; x0 < len; x0 += kLongUnroll * kLongThreads) {
+          int32_t tk[kLongUnroll];  // kLongUnroll token loads in flight per thread
+#pragma unroll
+          for (int u = 0; u < kLongUnroll; ++u) {
+            const int64_t x = x0 + u * kLongThreads;
+            tk[u] = x < len ? __ldcs(p.tokens + o0 + x) : -1;
+          }
+          uint32_t pend = 0u;
+#pragma unroll
+          for (int u = 0; u < kLongUnroll; ++u) {
+            if (x0 + u * kLongThreads >= len) break;
+            const int32_t t = tk[u];
+            if ((uint32_t)t >= (uint32_t)p.vocab) {
+              if (pass == 0) set_err(p.err, kErrBadToken);
+              continue;
+            }
+            if (passes > 1 && pass_of((uint32_t)t, passes) != pass) continue;
+            pend |= 1u << u;
+          }
+          if (!table_insert_batch<kLongUnroll>(keys, cnts, l2, tk, pend)) set_err(p.err, kErrTable);
+        }
+        __syncthreads();
+        cta_walk<MODE>(p, keys, cnts, ts, warp, lane, num_q, a, d, inv_norm, &misc[1], o0,
+                       p.bag_write ? &misc[2] : nullptr);
       }
     }
     if (MODE == kDFN) {
@@ -499,6 +598,7 @@ __global__ void __launch_bounds__(kLongThreads, 2) k_ingest_long(IngestParams p)
     if (MODE == kSIG && warp == 0) finalize_sig(p, d, len, *norm_s, num_q, P[lane], P[lane + 32], lane);
     if (MODE == kDENSE && threadIdx.x == 0) p.dense.row_cnt[d] = misc[1];
     if (MODE == kDFN && threadIdx.x == 0) p.norm_out[d] = *norm_s;
+    if (p.bag_write && threadIdx.x == 0) p.bag_n[d] = misc[2];
     __syncthreads();
   }
 }
@@ -681,6 +781,13 @@ IngestParams base_params(const DocsDev& d) {
   IngestParams p{};
   p.offsets = d.offsets;
   p.tokens = d.tokens;
+  if (d.bag_terms && d.bag_cnts && d.bag_n) {
+    p.bag_terms = d.bag_terms;
+    p.bag_cnts = d.bag_cnts;
+    p.bag_n = d.bag_n;
+    p.bag_write = d.bag_write;
+    p.bag_read = d.bag_read && !d.bag_write;
+  }
   return p;
 }
 

@@ -131,6 +131,13 @@ struct DocsDev {
   const int32_t* tokens;   // device
   int64_t n_tokens;
   int32_t* err;            // the call's device error word (kErr* bits)
+  // Optional bag of terms of these documents (device, [n_tokens] (term, count) pairs at the
+  // documents' token offsets, [n_docs] pair counts): a pass with bag_write stores it, a later
+  // pass with bag_read reads it instead of hashing the tokens again.
+  int32_t* bag_terms = nullptr;
+  int32_t* bag_cnts = nullptr;
+  int32_t* bag_n = nullptr;
+  int32_t bag_write = 0, bag_read = 0;
 };
 
 // ingest.cu
