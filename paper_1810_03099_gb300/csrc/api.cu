@@ -321,8 +321,13 @@ int64_t select_references(const int32_t* df, int32_t V, int64_t n_docs, const mr
   }
   // scratch kept across calls (fresh allocations cost page faults)
   static thread_local std::vector<int64_t> base, seen;
-  int32_t maxdf = 0;
-  for (int32_t t = 0; t < V; ++t) maxdf = std::max(maxdf, df[t]);
+  // df <= n_docs bounds the histogram; a pass for the largest df pays off only when the
+  // vocabulary is small next to the collection
+  int32_t maxdf = (int32_t)std::min<int64_t>(n_docs, INT32_MAX - 2);
+  if (n_docs > 4 * (int64_t)V) {
+    maxdf = 0;
+    for (int32_t t = 0; t < V; ++t) maxdf = std::max(maxdf, df[t]);
+  }
   base.assign((size_t)maxdf + 2, 0);
   for (int32_t t = 0; t < V; ++t) base[df[t]] += 1;
   int64_t above = 0;  // terms with df > v, for v from maxdf down
@@ -363,27 +368,47 @@ int64_t select_references(const int32_t* df, int32_t V, int64_t n_docs, const mr
 
 // Index arrays come from the device's stream-ordered memory pool (kept, not returned to the
 // driver, between builds), so building and freeing indexes does not synchronise the device.
-template <typename T>
-mrc_status dev_alloc(mrc_ctx* ctx, T** p, size_t count, const char* what) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  if (cudaMallocAsync((void**)p, sizeof(T) * count, ctx->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(ctx, MRC_ERR_OOM, std::string("device allocation failed: ") + what);
+void free_index_arrays(mrc_index* x) {
+  if (x->block) cudaFreeAsync(x->block, x->stream);
+  x->block = nullptr;
+}
+
+// Every device array of an index in one stream-ordered allocation (256-byte aligned slices):
+// the term tables [vocab], the reference norms [k], the signatures and Simhashes [n_docs], and
+// the compare operands of the index's precision form.
+mrc_status alloc_index_arrays(mrc_ctx* ctx, mrc_index* x) {
+  const size_t n = (size_t)std::max<int64_t>(x->n_docs, 1), V = (size_t)x->vocab, k = (size_t)x->k;
+  const bool f16 = x->params.precision == MRC_PREC_FP32 || x->params.precision == MRC_PREC_FP16;
+  const bool e4m3 = x->params.precision == MRC_PREC_BF16_FP8;
+  const size_t sizes[] = {4 * V, 4 * V, 8 * V, 4 * k, 4 * n * k, 4 * n * k, 8 * n,
+                          f16 ? 2 * n * (size_t)x->kp : 0, e4m3 ? n * (size_t)x->kp8 : 0, e4m3 ? 4 * n : 0,
+                          e4m3 ? 4 * ((n + 127) / 128) : 0};
+  size_t off[11], total = 0;
+  for (int q = 0; q < 11; ++q) {
+    off[q] = total;
+    total += (sizes[q] + 255) / 256 * 256;
   }
+  char* b = nullptr;
+  if (cudaMallocAsync((void**)&b, total, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, MRC_ERR_OOM, "device allocation failed: index arrays");
+  }
+  x->block = b;
+  x->df = (int32_t*)(b + off[0]);
+  x->idf = (float*)(b + off[1]);
+  x->tinfo = (TermInfo*)(b + off[2]);
+  x->rinv = (float*)(b + off[3]);
+  x->sig = (float*)(b + off[4]);
+  x->sig_unit = (float*)(b + off[5]);
+  x->simhash = (uint64_t*)(b + off[6]);
+  x->op_hi = f16 ? (void*)(b + off[7]) : nullptr;
+  x->op_lo = nullptr;
+  x->op_e4m3 = e4m3 ? (void*)(b + off[8]) : nullptr;
+  x->qnorm = e4m3 ? (float*)(b + off[9]) : nullptr;
+  x->qnorm_min = e4m3 ? (float*)(b + off[10]) : nullptr;
   return MRC_OK;
 }
 
-void free_index_arrays(mrc_index* x) {
-  void* ptrs[] = {x->df,    x->idf,   x->tinfo,    x->rinv,  x->sig,       x->sig_unit,
-                  x->simhash, x->op_hi, x->op_lo, x->op_e4m3, x->qnorm, x->qnorm_min};
-  for (void* p : ptrs)
-    if (p) cudaFreeAsync(p, x->stream);
-}
-
-
-// Uploads term info (idf under the weighting, partition) and 1/|R_p|. In the precision
-// form the stored per-term weights (document and reference) are bfloat16 values.
 // Reference tables of the signature pass: 1 / |R_p| from the squared norms in x->h_rnorm (which
 // become the norms), the term table built on the device from the partition of every term
 // (part_stage: pinned, [vocab]) and the device idf. The copies read pinned staging, so the
@@ -437,27 +462,6 @@ void* host_ws(mrc_ctx* ctx, size_t bytes, mrc_status* st) {
   }
   ctx->host_ws_bytes = bytes;
   return ctx->host_ws;
-}
-
-mrc_status alloc_signature_arrays(mrc_ctx* ctx, mrc_index* x) {
-  const size_t n = (size_t)std::max<int64_t>(x->n_docs, 1);
-  mrc_status st;
-  if ((st = dev_alloc(ctx, &x->sig, n * x->k, "signatures")) != MRC_OK) return st;
-  if ((st = dev_alloc(ctx, &x->sig_unit, n * x->k, "unit signatures")) != MRC_OK) return st;
-  if ((st = dev_alloc(ctx, &x->simhash, n, "simhash")) != MRC_OK) return st;
-  if (x->params.precision == MRC_PREC_FP32 || x->params.precision == MRC_PREC_FP16) {
-    uint16_t* h = nullptr;
-    if ((st = dev_alloc(ctx, &h, n * x->kp, "fp16 operands")) != MRC_OK) return st;
-    x->op_hi = h;
-  }
-  if (x->params.precision == MRC_PREC_BF16_FP8) {
-    uint8_t* q = nullptr;
-    if ((st = dev_alloc(ctx, &q, n * x->kp8, "e4m3 operands")) != MRC_OK) return st;
-    x->op_e4m3 = q;
-    if ((st = dev_alloc(ctx, &x->qnorm, n, "e4m3 row norms")) != MRC_OK) return st;
-    if ((st = dev_alloc(ctx, &x->qnorm_min, (n + 127) / 128, "e4m3 block norm minima")) != MRC_OK) return st;
-  }
-  return MRC_OK;
 }
 
 SigOut index_sig_out(mrc_index* x) {
@@ -613,10 +617,7 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
     delete x;
     return s;
   };
-  if ((st = dev_alloc(ctx, &x->df, vocab, "df")) != MRC_OK) return bail(st);
-  if ((st = dev_alloc(ctx, &x->idf, vocab, "idf")) != MRC_OK) return bail(st);
-  if ((st = dev_alloc(ctx, &x->tinfo, vocab, "term info")) != MRC_OK) return bail(st);
-  if ((st = dev_alloc(ctx, &x->rinv, x->k, "reference norms")) != MRC_OK) return bail(st);
+  if ((st = alloc_index_arrays(ctx, x)) != MRC_OK) return bail(st);
   cudaError_t e = cudaMemsetAsync(x->df, 0, sizeof(int32_t) * vocab, ctx->stream);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
 
@@ -626,6 +627,7 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   e = launch_df(ctx, d, x->df, vocab);
   d.bag_write = 0;
   d.bag_read = 1;
+  d.lists_ready = 1;
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "df pass"));
   e = launch_idf(ctx, d.n_docs, x->df, vocab, params->weighting, x->idf, nullptr);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "idf"));
@@ -645,7 +647,6 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   if ((st = upload_references(ctx, x, part_stage, (float*)(stage + 12 * (size_t)vocab))) != MRC_OK) return bail(st);
 
   // a2-a4: signatures, Simhash, packed compare operands
-  if ((st = alloc_signature_arrays(ctx, x)) != MRC_OK) return bail(st);
   if (x->op_hi) cudaMemsetAsync(x->op_hi, 0, sizeof(uint16_t) * (size_t)x->n_docs * x->kp, ctx->stream);
   if (x->op_lo) cudaMemsetAsync(x->op_lo, 0, sizeof(uint16_t) * (size_t)x->n_docs * x->kp, ctx->stream);
   if (x->op_e4m3) cudaMemsetAsync(x->op_e4m3, 0, (size_t)x->n_docs * x->kp8, ctx->stream);
@@ -820,6 +821,7 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   cudaError_t e = launch_df_norm(ctx, d, df, V, wid, d_norm);
   d.bag_write = 0;
   d.bag_read = 1;
+  d.lists_ready = 1;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "df pass");
   e = launch_cosine_terms(ctx, df, V, cut, d_tpart, d_tsum, d_colmap, d_tstart, d_cstart, d_rank_terms);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "head/tail split");
@@ -1073,11 +1075,7 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
     delete x;
     return s;
   };
-  if ((st = dev_alloc(ctx, &x->df, x->vocab, "df")) != MRC_OK) return bail(st);
-  if ((st = dev_alloc(ctx, &x->idf, x->vocab, "idf")) != MRC_OK) return bail(st);
-  if ((st = dev_alloc(ctx, &x->tinfo, x->vocab, "term info")) != MRC_OK) return bail(st);
-  if ((st = dev_alloc(ctx, &x->rinv, x->k, "reference norms")) != MRC_OK) return bail(st);
-  if ((st = alloc_signature_arrays(ctx, x)) != MRC_OK) return bail(st);
+  if ((st = alloc_index_arrays(ctx, x)) != MRC_OK) return bail(st);
   const size_t n = (size_t)x->n_docs;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);  // stream-ordered allocations before plain copies
   if (e == cudaSuccess) e = cudaMemcpy(x->df, hdf.data(), sizeof(int32_t) * x->vocab, cudaMemcpyHostToDevice);

@@ -737,10 +737,16 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   int32_t* long_list = (int32_t*)ws_get(ctx, "ingest.long", list_bytes, &st);
   int32_t* counts = (int32_t*)ws_get(ctx, "ingest.counts", sizeof(int32_t) * kCntWords, &st);
   if (st != MRC_OK) return cudaErrorMemoryAllocation;
-  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * kCntWords, ctx->stream);
-  if (e != cudaSuccess) return e;
   if (d.n_docs <= 0) return cudaSuccess;
-  launch_classify(ctx, d.offsets, d.n_docs, short_list, long_list, counts, d.err);
+  cudaError_t e;
+  if (d.lists_ready) {  // the lists of the previous pass over these documents: reset the cursors
+    e = cudaMemsetAsync(counts + kCntLongCursor, 0, sizeof(int32_t) * 2, ctx->stream);
+    if (e != cudaSuccess) return e;
+  } else {
+    e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * kCntWords, ctx->stream);
+    if (e != cudaSuccess) return e;
+    launch_classify(ctx, d.offsets, d.n_docs, short_list, long_list, counts, d.err);
+  }
   p.short_list = short_list;
   p.long_list = long_list;
   p.list_counts = counts;

@@ -89,6 +89,7 @@ struct mrc_index {
   void* op_e4m3 = nullptr;        // [n * kp8] e4m3
   float* qnorm = nullptr;         // [n] norms of the e4m3 rows
   float* qnorm_min = nullptr;     // [ceil(n / 128)] smallest non-zero qnorm of each 128-row block
+  void* block = nullptr;          // one stream-ordered allocation holding every array above
 };
 
 namespace mrc {
@@ -138,6 +139,9 @@ struct DocsDev {
   int32_t* bag_cnts = nullptr;
   int32_t* bag_n = nullptr;
   int32_t bag_write = 0, bag_read = 0;
+  // Set after a pass over these documents: its split into warp-path and CTA-path lists (in
+  // the context's workspace) is still valid, so the next pass reuses it.
+  int32_t lists_ready = 0;
 };
 
 // ingest.cu
