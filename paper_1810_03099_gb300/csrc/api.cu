@@ -321,6 +321,8 @@ int64_t select_references(const int32_t* df, int32_t V, int64_t n_docs, const mr
   }
   // scratch kept across calls (fresh allocations cost page faults)
   static thread_local std::vector<int64_t> base, seen;
+  static thread_local std::vector<int32_t> cnt4;
+  static thread_local std::vector<uint8_t> band;
   // df <= n_docs bounds the histogram; a pass for the largest df pays off only when the
   // vocabulary is small next to the collection
   int32_t maxdf = (int32_t)std::min<int64_t>(n_docs, INT32_MAX - 2);
@@ -328,11 +330,15 @@ int64_t select_references(const int32_t* df, int32_t V, int64_t n_docs, const mr
     maxdf = 0;
     for (int32_t t = 0; t < V; ++t) maxdf = std::max(maxdf, df[t]);
   }
-  base.assign((size_t)maxdf + 2, 0);
-  for (int32_t t = 0; t < V; ++t) base[df[t]] += 1;
+  // histogram of df in four interleaved copies (a run of equal df values would otherwise
+  // chain every increment on the previous one)
+  const size_t M = (size_t)maxdf + 2;
+  cnt4.assign(4 * M, 0);
+  for (int32_t t = 0; t < V; ++t) cnt4[(size_t)(t & 3) * M + df[t]] += 1;
+  base.assign(M, 0);
   int64_t above = 0;  // terms with df > v, for v from maxdf down
   for (int32_t v = maxdf; v >= 1; --v) {
-    const int64_t c = base[v];
+    const int64_t c = (int64_t)cnt4[v] + cnt4[M + v] + cnt4[2 * M + v] + cnt4[3 * M + v];
     base[v] = above;
     above += c;
   }
@@ -349,11 +355,18 @@ int64_t select_references(const int32_t* df, int32_t V, int64_t n_docs, const mr
     end = std::min(start + L, ranked);
   }
   const int64_t n = end - start;
-  seen.assign((size_t)maxdf + 2, 0);
+  // df values whose ranks [base[v], base[v] + count) meet the selection [start, end): only
+  // their terms need a running rank
+  band.assign(M, 0);
+  for (int32_t v = maxdf; v >= 1; --v) {
+    const int64_t c = (v > 1 ? base[v - 1] : ranked) - base[v];
+    band[v] = base[v] < end && base[v] + c > start;
+  }
+  seen.assign(M, 0);
   for (int32_t t = 0; t < V; ++t) {
     const int32_t v = df[t];
     int32_t q = -1;
-    if (v > 0) {
+    if (band[v]) {
       const int64_t x = base[v] + seen[v]++ - start;
       if (x >= 0 && x < n) {
         q = (int32_t)(((x + 1) * p.k - 1) / n);
@@ -382,9 +395,9 @@ mrc_status alloc_index_arrays(mrc_ctx* ctx, mrc_index* x) {
   const bool e4m3 = x->params.precision == MRC_PREC_BF16_FP8;
   const size_t sizes[] = {4 * V, 4 * V, 8 * V, 4 * k, 4 * n * k, 4 * n * k, 8 * n,
                           f16 ? 2 * n * (size_t)x->kp : 0, e4m3 ? n * (size_t)x->kp8 : 0, e4m3 ? 4 * n : 0,
-                          e4m3 ? 4 * ((n + 127) / 128) : 0};
-  size_t off[11], total = 0;
-  for (int q = 0; q < 11; ++q) {
+                          e4m3 ? 4 * ((n + 127) / 128) : 0, 8 * k};
+  size_t off[12], total = 0;
+  for (int q = 0; q < 12; ++q) {
     off[q] = total;
     total += (sizes[q] + 255) / 256 * 256;
   }
@@ -406,6 +419,7 @@ mrc_status alloc_index_arrays(mrc_ctx* ctx, mrc_index* x) {
   x->op_e4m3 = e4m3 ? (void*)(b + off[8]) : nullptr;
   x->qnorm = e4m3 ? (float*)(b + off[9]) : nullptr;
   x->qnorm_min = e4m3 ? (float*)(b + off[10]) : nullptr;
+  x->rnorm = (double*)(b + off[11]);
   return MRC_OK;
 }
 
@@ -587,6 +601,18 @@ void mrc_ctx_destroy(mrc_ctx* ctx) {
 
 const char* mrc_last_error(const mrc_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
 
+// a2-a4 for an index: signatures, Simhash and packed compare operands of its documents.
+mrc_status launch_index_signatures(mrc_ctx* ctx, mrc_index* x, const DocsDev& d) {
+  if (x->op_hi) cudaMemsetAsync(x->op_hi, 0, sizeof(uint16_t) * (size_t)x->n_docs * x->kp, ctx->stream);
+  if (x->op_lo) cudaMemsetAsync(x->op_lo, 0, sizeof(uint16_t) * (size_t)x->n_docs * x->kp, ctx->stream);
+  if (x->op_e4m3) cudaMemsetAsync(x->op_e4m3, 0, (size_t)x->n_docs * x->kp8, ctx->stream);
+  cudaError_t e = launch_signature(ctx, d, x->vocab, x->tinfo, x->rinv, x->k,
+                                   x->params.precision == MRC_PREC_BF16_FP8, x->params.seed, index_sig_out(x));
+  if (e == cudaSuccess && x->qnorm_min) e = launch_block_min(ctx, x->qnorm, x->n_docs, x->qnorm_min);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "signature pass");
+  return MRC_OK;
+}
+
 mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, const mrc_params* params,
                            mrc_index** out) {
   if (!ctx || !out) return MRC_ERR_INVALID;
@@ -631,7 +657,43 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "df pass"));
   e = launch_idf(ctx, d.n_docs, x->df, vocab, params->weighting, x->idf, nullptr);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "idf"));
-  // pinned staging: df and idf [vocab] each, then the partition [vocab] and 1 / |R_p| [k]
+  // References: REGION selection on the device when its df histogram is small (no host round
+  // trip between the passes); otherwise, and when a tie group overflows the device sort, on
+  // the host.
+  const bool dev_select = params->select_mode == MRC_SELECT_REGION &&
+                          d.n_docs + 2 <= std::max<int64_t>(4 * (int64_t)vocab, 1 << 20);
+  if (dev_select) {
+    const size_t hb = sizeof(int32_t) * ((size_t)d.n_docs + 2);
+    int32_t* hist = (int32_t*)ws_get(ctx, "sel.hist", hb, &st);
+    int32_t* above = (int32_t*)ws_get(ctx, "sel.above", hb, &st);
+    long long* sstate = (long long*)ws_get(ctx, "sel.state", sizeof(long long) * device_selection_words(), &st);
+    unsigned long long* keys = (unsigned long long*)ws_get(ctx, "sel.keys", 8 * 8192, &st);
+    int32_t* d_part = (int32_t*)ws_get(ctx, "build.part", sizeof(int32_t) * vocab, &st);
+    if (st != MRC_OK) return bail(st);
+    const bool tfidf = params->weighting == MRC_WEIGHT_TFIDF, bf16 = params->precision == MRC_PREC_BF16_FP8;
+    const int64_t L = params->L < 0 ? 32ll * params->k : params->L;
+    e = launch_select_region(ctx, x->df, vocab, d.n_docs, L, params->region_start, tfidf ? x->idf : nullptr, bf16,
+                             x->k, hist, above, sstate, keys, d_part, x->rnorm, x->rinv);
+    if (e == cudaSuccess) e = launch_term_info(ctx, x->idf, d_part, vocab, tfidf, bf16, x->tinfo);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "reference selection"));
+    if ((st = launch_index_signatures(ctx, x, d)) != MRC_OK) return bail(st);
+    // one synchronisation: the error word, the selection state and |R_p|
+    char* hs = (char*)ctx->pinned + 1024;
+    e = cudaMemcpyAsync(hs, sstate, sizeof(long long) * device_selection_words(), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hs + 128, x->rnorm, sizeof(double) * x->k, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "reading the selection"));
+    if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);  // synchronises the stream
+    const long long* hss = (const long long*)hs;
+    if (hss[6] == 0) {
+      x->L_used = hss[1];
+      x->h_rnorm.assign((const double*)(hs + 128), (const double*)(hs + 128) + x->k);
+      *out = x;
+      return MRC_OK;
+    }
+  }
+  // host selection: df and idf read back to pinned staging, then the partition [vocab] and
+  // 1 / |R_p| [k] staged for the device tables
   char* stage = (char*)host_ws(ctx, 12 * (size_t)vocab + 4 * (size_t)x->k + 64, &st);
   if (!stage) return bail(st);
   int32_t* h_df = (int32_t*)stage;
@@ -640,20 +702,10 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_idf, x->idf, sizeof(float) * vocab, cudaMemcpyDeviceToHost, ctx->stream);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "reading df"));
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);  // synchronises the stream
-
-  // references (host sort of the vocabulary), then their device tables
   int32_t* part_stage = (int32_t*)(stage + 8 * (size_t)vocab);
   x->L_used = select_references(h_df, vocab, d.n_docs, *params, part_stage, h_idf, &x->h_rnorm);
   if ((st = upload_references(ctx, x, part_stage, (float*)(stage + 12 * (size_t)vocab))) != MRC_OK) return bail(st);
-
-  // a2-a4: signatures, Simhash, packed compare operands
-  if (x->op_hi) cudaMemsetAsync(x->op_hi, 0, sizeof(uint16_t) * (size_t)x->n_docs * x->kp, ctx->stream);
-  if (x->op_lo) cudaMemsetAsync(x->op_lo, 0, sizeof(uint16_t) * (size_t)x->n_docs * x->kp, ctx->stream);
-  if (x->op_e4m3) cudaMemsetAsync(x->op_e4m3, 0, (size_t)x->n_docs * x->kp8, ctx->stream);
-  e = launch_signature(ctx, d, vocab, x->tinfo, x->rinv, x->k, params->precision == MRC_PREC_BF16_FP8, params->seed,
-                       index_sig_out(x));
-  if (e == cudaSuccess && x->qnorm_min) e = launch_block_min(ctx, x->qnorm, x->n_docs, x->qnorm_min);
-  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "signature pass"));
+  if ((st = launch_index_signatures(ctx, x, d)) != MRC_OK) return bail(st);
   // The df pass already validated these documents (offsets, lengths, token ids) and the
   // signature pass meets the same ones, so the call returns without waiting for it: the index
   // is ready in stream order, like any device result.

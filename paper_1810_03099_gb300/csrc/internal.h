@@ -89,6 +89,7 @@ struct mrc_index {
   void* op_e4m3 = nullptr;        // [n * kp8] e4m3
   float* qnorm = nullptr;         // [n] norms of the e4m3 rows
   float* qnorm_min = nullptr;     // [ceil(n / 128)] smallest non-zero qnorm of each 128-row block
+  double* rnorm = nullptr;        // [k] |R_p| (written by the device reference selection)
   void* block = nullptr;          // one stream-ordered allocation holding every array above
 };
 
@@ -143,6 +144,19 @@ struct DocsDev {
   // the context's workspace) is still valid, so the next pass reuses it.
   int32_t lists_ready = 0;
 };
+
+// select.cu
+// REGION reference selection on the device from df [V]: partition of every term into part
+// [V] (-1 unselected), |R_p| into rnorm [k] (double) and 1 / |R_p| into rinv [k]; idf NULL
+// under count weighting, bf16: weights rounded to bfloat16 (precision form). Scratch: hist
+// and above [n_docs + 2] int32, state [device_selection_words()] int64, keys [8192] uint64.
+// state[5] = band size, state[6] = 1 if the band exceeded 8192 terms (part, rnorm and rinv
+// are then not written: select on the host), state[1] = L.
+int64_t device_selection_words();
+cudaError_t launch_select_region(mrc_ctx* ctx, const int32_t* df, int32_t V, int64_t n_docs, int64_t L,
+                                 int64_t region_start, const float* idf, int32_t bf16, int32_t k, int32_t* hist,
+                                 int32_t* above, long long* state, unsigned long long* keys, int32_t* part,
+                                 double* rnorm, float* rinv);
 
 // ingest.cu
 cudaError_t launch_df(mrc_ctx* ctx, const DocsDev& d, int32_t* df, int32_t vocab);

@@ -87,6 +87,27 @@ def test_index_build_matches_oracle(torch, M, ctx, orc, corpus, case):
     idx.free()
 
 
+def test_index_build_large_tie_group(torch, M, ctx, orc):
+    """20,000 terms that all share df = 5: the REGION selection's band is one tie group larger
+    than the device sort holds, so the build selects on the host; the index still matches."""
+    n_docs, V = 2000, 20000
+    rows = [[] for _ in range(n_docs)]
+    for t in range(V):
+        for j in range(5):
+            rows[(t * 5 + j) % n_docs].append(t)
+    offs = np.zeros(n_docs + 1, np.int64)
+    offs[1:] = np.cumsum([len(r) for r in rows])
+    toks = np.concatenate([np.array(r, np.int32) for r in rows])
+    p = Params(k=64)
+    ref = build_index(offs, toks, V, p, orc)
+    idx = M.mrc_build_index(ctx, dev(torch, offs), dev(torch, toks), V, mrc_params(M, p))
+    ex = M.mrc_index_export(ctx, idx)
+    assert np.array_equal(ex["part"], ref.part) and idx.L_used == ref.L_used == 2048
+    assert np.max(np.abs(ex["rnorm"] - ref.rnorm) / np.maximum(ref.rnorm, 1e-300)) < 1e-6
+    assert np.abs(ex["sig"].astype(np.float64) - ref.S).max() <= SIG_TOL
+    idx.free()
+
+
 def test_signature_of_new_documents(torch, M, ctx, orc, corpus):
     offs, toks = corpus
     V = 5000
