@@ -313,16 +313,43 @@ __device__ __forceinline__ float exact_head(const __half* __restrict__ hhi, cons
   return warp_sum(s);
 }
 
-// One CTA per (row i, column window) work item. The tail sums accumulate in a shared-memory
-// row of 2^-30 fixed-point integers (each product is < 1: rounding <= 2^-31; integer sums do
-// not depend on the order in which threads add them):
-//  1. acc[j] = 0 over the window;
-//  2. for every tail term t of document i, the postings after i's own position in t's
-//     sorted list are exactly the documents j > i sharing t: acc[j] += w_it * w_jt. The
-//     CTA takes up to 768 of the row's terms at a time, flattens their postings into one
-//     position range (CTA prefix sum of the list lengths, term tables in shared memory)
-//     and gives every warp an equal slice of it, four loads per lane in flight, so neither
-//     short lists nor uneven terms leave warps idle;
+// A work item is one or two segments; a segment is row `row`'s columns [c_lo, c_hi), their
+// accumulators at acc[off + (j - cb)] (cb = c_lo rounded down to 8; off a multiple of 8).
+struct TailSeg {
+  int32_t row, c_lo, c_hi, cb, off;
+};
+
+// Work item -> segments (number of non-empty segments returned). With one window per row,
+// rows pair up as (r, n-1-r): the pair's columns [r+1, n) and [n-r, n) fill one accumulator
+// row of about n entries, so every item costs about the same and the per-item fixed work is
+// halved. Otherwise an item is one row's columns within one window.
+__device__ __forceinline__ int tail_segments(int64_t item, int32_t n, int32_t window, int32_t n_windows, bool paired,
+                                             TailSeg& s0, TailSeg& s1) {
+  if (paired) {
+    const int32_t r0 = (int32_t)item, r1 = n - 1 - (int32_t)item;
+    s0 = TailSeg{r0, r0 + 1, n, (r0 + 1) & ~7, 0};
+    s1 = TailSeg{r1, r1 + 1, n, (r1 + 1) & ~7, (n - s0.cb + 7) & ~7};
+    const int k0 = s0.c_lo < s0.c_hi, k1 = r1 > r0 && s1.c_lo < s1.c_hi;
+    if (!k0) s0 = s1;  // (cannot happen for r0 < n - 1; kept for safety)
+    return k0 + k1;
+  }
+  const int32_t i = (int32_t)(item / n_windows);
+  const int32_t base = (int32_t)(item % n_windows) * window;  // a multiple of 8 (window is)
+  s0 = TailSeg{i, max(i + 1, base), min(n, base + window), base, 0};
+  s1 = s0;
+  return s0.c_lo < s0.c_hi ? 1 : 0;
+}
+
+// One CTA per work item (see tail_segments). The tail sums accumulate in a shared-memory row
+// of 2^-30 fixed-point integers (each product is < 1: rounding <= 2^-31; integer sums do not
+// depend on the order in which threads add them):
+//  1. acc = 0 over the item's segments;
+//  2. for every tail term t of a segment's document i, the postings after i's own position in
+//     t's sorted list are exactly the documents j > i sharing t: acc[j] += w_it * w_jt. The
+//     CTA takes up to 768 of the item's terms at a time, flattens their postings into one
+//     position range (CTA prefix sum of the list lengths, term tables in shared memory) and
+//     gives every warp an equal slice of it, four loads per lane in flight, so neither short
+//     lists nor uneven terms leave warps idle;
 //  3. scan: H16[i][j] (the fp16 head score from the tensor cores, eight columns per 16-byte
 //     load) + tail >= tau - delta marks a candidate, where delta bounds the head's error;
 //     each candidate's head is recomputed exactly (exact_head) and the pair is kept iff
@@ -332,56 +359,59 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_cosine_tail(
     const int32_t* __restrict__ row_cnt, const int2* __restrict__ row_walk, const float* __restrict__ row_w,
     const int2* __restrict__ spost, const __half* __restrict__ hhi,
     const __half* __restrict__ hlo, int32_t kd, float tau, float delta, mrc_pair* pairs,
-    unsigned long long* count, int64_t capacity, int32_t window, int32_t n_windows, int64_t n_items,
-    unsigned long long* next_item) {
-  extern __shared__ int32_t acc[];  // [window] accumulators, then the term tables
-  int32_t* t_st = acc + window;       // [kTermBatch] first remaining posting of each term
+    unsigned long long* count, int64_t capacity, int32_t window, int32_t acc_len, int32_t n_windows, int64_t n_items,
+    int32_t paired, unsigned long long* next_item) {
+  extern __shared__ int32_t acc[];    // [acc_len] accumulators, then the term tables
+  int32_t* t_st = acc + acc_len;      // [kTermBatch] posting index - flattened start, per term
   int32_t* t_ex = t_st + kTermBatch;  // [kTermBatch + 1] flattened start of each term
-  float* t_w = reinterpret_cast<float*>(t_ex + kTermBatch + 1);  // [kTermBatch] the row's weight
+  float* t_w = reinterpret_cast<float*>(t_ex + kTermBatch + 1);  // [kTermBatch] 2^30 x the row's weight
+  int32_t* t_sh = reinterpret_cast<int32_t*>(t_w + kTermBatch);   // [kTermBatch] accumulator shift
   __shared__ int32_t t_scan[33];
   __shared__ long long s_item[2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float cand_tau = tau - delta;
-  const bool one_window = n_windows == 1;
-  // Work items are taken in row order as CTAs free up (rows differ in cost by orders of
-  // magnitude: long documents, early rows), one item ahead: the index of the next item is
+  // Work items are taken in order as CTAs free up, one ahead: the index of the next item is
   // requested at the start of the current one and read after its first barrier.
   if (threadIdx.x == 0) s_item[0] = (long long)atomicAdd(next_item, 1ull);
   __syncthreads();
-  for (int k = 0;; ++k) {
-    const int64_t item = s_item[k & 1];
+  for (int it = 0;; ++it) {
+    const int64_t item = s_item[it & 1];
     if (item >= n_items) break;  // block-uniform
-    __syncthreads();  // every thread has read s_item[k & 1] before it is requested again
-    if (threadIdx.x == 0) s_item[(k + 1) & 1] = (long long)atomicAdd(next_item, 1ull);
-    const int32_t i = (int32_t)(item / n_windows);
-    const int32_t base = (int32_t)(item % n_windows) * window;  // a multiple of 8 (window is)
-    const int32_t lo = max(i + 1, base), hi = min(n, base + window);
-    if (lo >= hi) {  // block-uniform
-      __syncthreads();  // publishes s_item[(k + 1) & 1]
+    __syncthreads();  // every thread has read s_item[it & 1] before it is requested again
+    if (threadIdx.x == 0) s_item[(it + 1) & 1] = (long long)atomicAdd(next_item, 1ull);
+    TailSeg sa, sb;
+    const int nseg = tail_segments(item, n, window, n_windows, paired != 0, sa, sb);
+    if (nseg == 0) {  // block-uniform
+      __syncthreads();  // publishes s_item[(it + 1) & 1]
       continue;
     }
-    const __half* hrow = H + (int64_t)i * ldh;
-    {  // pull this item's head scores toward L2 while the tail sums are built (one 128-byte line
-       // per thread covers 32768 columns, the largest window)
-      const int32_t at = (lo & ~63) + 64 * (int32_t)threadIdx.x;
-      if (at < hi) asm volatile("prefetch.global.L2 [%0];" ::"l"(hrow + at));
+    // pull the segments' head scores toward L2 while the tail sums are built (one 128-byte
+    // line per thread and segment covers 49,152 columns)
+    {
+      const int32_t at = (sa.c_lo & ~63) + 64 * (int32_t)threadIdx.x;
+      if (at < sa.c_hi) asm volatile("prefetch.global.L2 [%0];" ::"l"(H + (int64_t)sa.row * ldh + at));
+      const int32_t bt = (sb.c_lo & ~63) + 64 * (int32_t)threadIdx.x;
+      if (nseg > 1 && bt < sb.c_hi) asm volatile("prefetch.global.L2 [%0];" ::"l"(H + (int64_t)sb.row * ldh + bt));
     }
-    const int32_t a0 = (lo - base) & ~7, a1 = hi - base;  // accumulator range touched, 8-aligned start
-    for (int32_t x = a0 + 4 * (int32_t)threadIdx.x; x < a1; x += 4 * kTailThreads)
+    const TailSeg& sl = nseg > 1 ? sb : sa;
+    const int32_t a1 = sl.off + (sl.c_hi - sl.cb);  // accumulators in use
+    for (int32_t x = 4 * (int32_t)threadIdx.x; x < a1; x += 4 * kTailThreads)
       *reinterpret_cast<int4*>(acc + x) = make_int4(0, 0, 0, 0);
     __syncthreads();
-    const int32_t nt = row_cnt[i];
-    const int64_t ro = row_off[i];
+    const int32_t nt0 = row_cnt[sa.row], nt = nt0 + (nseg > 1 ? row_cnt[sb.row] : 0);
     for (int32_t b0 = 0; b0 < nt; b0 += kTermBatch) {
-      // term r = b0 + thread: its remaining postings [st, st + cnt) (documents > i)
+      // term r = b0 + thread: its remaining postings [st, st + cnt) (documents > its row)
       const int32_t r = b0 + threadIdx.x;
-      int32_t st = 0, cnt = 0;
+      int32_t st = 0, cnt = 0, sh = 0;
       float wi = 0.f;
       if (r < nt) {
-        const int2 wk = row_walk[ro + r];
+        const bool q = r >= nt0;
+        const int64_t ro = row_off[q ? sb.row : sa.row] + (q ? r - nt0 : r);
+        const int2 wk = row_walk[ro];
         st = wk.x;
         cnt = wk.y - wk.x;
-        wi = row_w[ro + r];
+        wi = row_w[ro];
+        sh = q ? sb.off - sb.cb : sa.off - sa.cb;
       }
       int32_t total;
       const int32_t ex = cta_excl_scan(cnt, t_scan, &total);  // synchronises the CTA
@@ -389,6 +419,7 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_cosine_tail(
       t_st[threadIdx.x] = st - ex;  // posting index = t_st[term] + flattened position
       t_ex[threadIdx.x] = ex;
       t_w[threadIdx.x] = wi * kTailFix;
+      t_sh[threadIdx.x] = sh;
       if (threadIdx.x == 0) t_ex[nterm] = total;
       __syncthreads();
       // the batch's postings flattened into [0, total); each warp takes an equal slice. A
@@ -409,38 +440,47 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_cosine_tail(
       for (int32_t f0 = s0; f0 < s1; f0 += 32 * kWalkChunks) {
         int2 pv[kWalkChunks];
         float wv[kWalkChunks];
+        int32_t shv[kWalkChunks];
 #pragma unroll
         for (int u = 0; u < kWalkChunks; ++u) {
           const int32_t f = f0 + 32 * u + lane;
           pv[u] = make_int2(-1, 0);
           wv[u] = 0.f;
+          shv[u] = 0;
           if (f < s1) {
             while (t_ex[own + 1] <= f) ++own;
             pv[u] = spost[t_st[own] + f];  // (document, weight) of the posting
             wv[u] = t_w[own];
+            shv[u] = t_sh[own];
           }
         }
-        // with one window per row every posting after i lies in [i + 1, n)
+        // with one window per row every posting after a segment's row lies in its columns
 #pragma unroll
         for (int u = 0; u < kWalkChunks; ++u) {
           const int32_t j = pv[u].x;
-          if (one_window ? j >= 0 : (j >= lo && j < hi))
-            atomicAdd(&acc[j - base], __float2int_rn(wv[u] * __int_as_float(pv[u].y)));
+          if (n_windows == 1 ? j >= 0 : (j >= sa.c_lo && j < sa.c_hi))
+            atomicAdd(&acc[j + shv[u]], __float2int_rn(wv[u] * __int_as_float(pv[u].y)));
         }
       }
       __syncthreads();  // the next batch rewrites the term tables
     }
     __syncthreads();
-    // scan: each lane takes eight consecutive columns (one 16-byte load of H16, in the row's
-    // ldh >= round8(n) padding at the end, so never past the row)
-    for (int32_t g0 = base + a0 + 256 * warp; g0 < hi; g0 += 8 * kTailThreads) {
-      const int32_t g = g0 + 8 * lane;
+    // scan: each lane takes eight consecutive columns of one segment (one 16-byte load of H16,
+    // in the row's ldh >= round8(n) padding at the end, so never past the row)
+    const int32_t g_a = (sa.c_hi - sa.cb + 7) >> 3;  // 8-column groups of the first segment
+    const int32_t g_all = g_a + (nseg > 1 ? (sb.c_hi - sb.cb + 7) >> 3 : 0);
+    for (int32_t q0 = 32 * warp; q0 < g_all; q0 += kTailThreads) {
+      const int32_t q = q0 + lane;
+      const bool sq = q >= g_a;
+      const TailSeg& sg = sq ? sb : sa;
+      const int32_t g = sg.cb + 8 * (sq ? q - g_a : q);
+      const int32_t ai = sg.off + (g - sg.cb);
       uint32_t mask = 0;
-      if (g < hi) {
-        const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(hrow + g));
+      if (q < g_all) {
+        const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(H + (int64_t)sg.row * ldh + g));
         const __half2* h2 = reinterpret_cast<const __half2*>(&raw);
-        const int4 t0 = *reinterpret_cast<const int4*>(acc + (g - base));
-        const int4 t1 = *reinterpret_cast<const int4*>(acc + (g - base) + 4);
+        const int4 t0 = *reinterpret_cast<const int4*>(acc + ai);
+        const int4 t1 = *reinterpret_cast<const int4*>(acc + ai + 4);
         const int32_t tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
         float sv[8];  // head + tail (the 2^-30 scaling is exact)
 #pragma unroll
@@ -450,13 +490,13 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_cosine_tail(
           sv[2 * u + 1] = fmaf((float)tv[2 * u + 1], kTailInv, hf.y);
         }
         // one comparison for the eight columns; the bounds only matter for the rare hits
-        // (columns outside [lo, hi) hold stale values)
+        // (columns outside [c_lo, c_hi) hold stale values)
         const float mx = fmaxf(fmaxf(fmaxf(sv[0], sv[1]), fmaxf(sv[2], sv[3])),
                                fmaxf(fmaxf(sv[4], sv[5]), fmaxf(sv[6], sv[7])));
         if (mx >= cand_tau) {
 #pragma unroll
           for (int e = 0; e < 8; ++e)
-            if (g + e >= lo && g + e < hi && sv[e] >= cand_tau) mask |= 1u << e;
+            if (g + e >= sg.c_lo && g + e < sg.c_hi && sv[e] >= cand_tau) mask |= 1u << e;
         }
       }
       unsigned todo = __ballot_sync(kFull, mask != 0);
@@ -465,15 +505,18 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_cosine_tail(
         todo &= todo - 1;
         uint32_t m = __shfl_sync(kFull, mask, src);
         const int32_t gs = __shfl_sync(kFull, g, src);
+        const int32_t as = __shfl_sync(kFull, ai, src);
+        const int32_t row = __shfl_sync(kFull, sg.row, src);
         while (m) {
-          const int32_t j = gs + __ffs(m) - 1;
+          const int e = __ffs(m) - 1;
           m &= m - 1;
-          const float s = exact_head(hhi, hlo, kd, i, j, lane) + (float)acc[j - base] * kTailInv;
+          const int32_t j = gs + e;
+          const float s = exact_head(hhi, hlo, kd, row, j, lane) + (float)acc[as + e] * kTailInv;
           if (lane == 0 && s >= tau) {
             const unsigned long long at = atomicAdd(count, 1ull);
             if (at < (unsigned long long)capacity) {
               mrc_pair pr;
-              pr.i = i;
+              pr.i = row;
               pr.j = j;
               pr.score = s;
               pairs[at] = pr;
@@ -576,8 +619,11 @@ cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t
   const int64_t n8 = (n + 7) / 8 * 8;
   const int32_t window = (int32_t)(n8 < kMaxWindow ? n8 : kMaxWindow);  // a multiple of 8
   const int32_t n_windows = (int32_t)((n + window - 1) / window);
-  const int64_t n_items = n * n_windows;
-  const size_t smem = sizeof(int32_t) * ((size_t)window + 3 * kTermBatch + 1);
+  // one window per row: rows pair up, (n + 1) / 2 items over about n + 16 accumulators
+  const int32_t paired = n_windows == 1 ? 1 : 0;
+  const int64_t n_items = paired ? (n + 1) / 2 : n * n_windows;
+  const int32_t acc_len = paired ? window + 32 : window;
+  const size_t smem = sizeof(int32_t) * ((size_t)acc_len + 4 * kTermBatch + 1);
   const int per_sm = resident_ctas(k_cosine_tail, kTailThreads, smem);
   if (per_sm <= 0) return cudaErrorInvalidConfiguration;
   int64_t grid = (int64_t)ctx->num_sms * per_sm;
@@ -591,7 +637,7 @@ cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t
   k_cosine_tail<<<(unsigned)grid, kTailThreads, smem, ctx->stream>>>(
       (int32_t)n, reinterpret_cast<const __half*>(H16), ldh, row_off, row_cnt, reinterpret_cast<const int2*>(row_walk),
       row_w, reinterpret_cast<const int2*>(spost), reinterpret_cast<const __half*>(head_hi), reinterpret_cast<const __half*>(head_lo), kd, tau, delta,
-      pairs, count, capacity, window, n_windows, n_items, next_item);
+      pairs, count, capacity, window, acc_len, n_windows, n_items, paired, next_item);
   timing_end(ctx, ev);
   return cudaGetLastError();
 }
