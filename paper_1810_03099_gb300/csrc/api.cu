@@ -269,10 +269,10 @@ bool valid_params(const mrc_params* p, std::string* why) {
 
 int32_t round_up(int32_t x, int32_t m) { return (x + m - 1) / m * m; }
 
-// Padded operand rows: multiples of 128 bytes (one 128B swizzle atom). kp counts fp16
-// elements, kp8 counts E4M3 bytes.
+// Padded operand rows: kp counts fp16 elements (rows of a multiple of 128 bytes, one 128B
+// swizzle atom), kp8 counts E4M3 bytes (a multiple of 64: 64-byte rows use the 64B swizzle).
 int32_t padded_kp(int32_t k) { return round_up(k, 64); }
-int32_t padded_kp8(int32_t k) { return round_up(k, 128); }
+int32_t padded_kp8(int32_t k) { return round_up(k, 64); }
 
 // Round to the nearest bfloat16 (8 significant bits), ties to even.
 float bf16_round(float f) {

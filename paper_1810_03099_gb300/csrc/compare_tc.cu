@@ -39,6 +39,7 @@ constexpr int kBM = 128;
 constexpr int kThreads = 192;
 constexpr int kRowBytes = 128;  // K bytes per stage per row (one 128B swizzle atom)
 constexpr uint64_t kTimeoutNs = 4000000000ull;
+constexpr int kPairBuf = 64;  // pairs buffered per epilogue warp before one global atomic
 constexpr float kNormLo = 0.93f;  // lower bound of |e4m3(x * 256)| / 256 for unit x (1 - 2^-4 = 0.9375)
 
 template <int FMT>
@@ -202,14 +203,27 @@ __device__ __forceinline__ bool decode_tile(const GemmParams& p, int64_t t64, in
   return bi * kBM < p.na;
 }
 
+// Writes a warp's buffered pairs (nbuf of them, in buf) to the global list with one atomic.
+__device__ __forceinline__ void flush_pairs(const GemmParams& p, const mrc_pair* buf, int& nbuf, int lane) {
+  if (nbuf == 0) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(p.count, (unsigned long long)nbuf);
+  base = __shfl_sync(kFull, base, 0);
+  for (int x = lane; x < nbuf; x += 32)
+    if (base + x < (unsigned long long)p.capacity) p.pairs[base + x] = buf[x];
+  nbuf = 0;
+  __syncwarp();
+}
+
 // Threshold one 32-column chunk held in registers (v[e] = score of column j0 + e for this
 // lane's row i) and append its pairs. Fast path: the chunk's maximum misses fast_thresh in
 // every lane. Otherwise each lane builds a 32-bit mask of candidate columns (bounds and the
 // triangle's j > i applied with bit arithmetic), tests the candidates exactly (E4M3: against
-// the column norms staged once per warp), and the warp appends all hits with one atomic.
+// the column norms staged once per warp), and the warp appends its hits to its pair buffer.
 template <int FMT>
 __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)[32], int64_t i, int64_t j0, int lane,
-                                           float fast_thresh, float row_norm, float* stage, float* nstage) {
+                                           float fast_thresh, float row_norm, float* stage, float* nstage,
+                                           mrc_pair* buf, int& nbuf) {
   float m = v[0];
 #pragma unroll
   for (int e = 1; e < 32; ++e) m = fmaxf(m, v[e]);
@@ -248,22 +262,30 @@ __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)
   }
   const int total = __shfl_sync(kFull, incl, 31);
   if (total) {
+    // pairs go to the warp's buffer (one global atomic per flush instead of per chunk); a
+    // chunk with more pairs than the buffer holds goes out directly
+    if (nbuf + total > kPairBuf) flush_pairs(p, buf, nbuf, lane);
+    const bool direct = total > kPairBuf;
     unsigned long long base = 0;
-    if (lane == 31) base = atomicAdd(p.count, (unsigned long long)total);
-    base = __shfl_sync(kFull, base, 31);
-    unsigned long long at = base + (unsigned long long)(incl - cnt);
+    if (direct) {
+      if (lane == 31) base = atomicAdd(p.count, (unsigned long long)total);
+      base = __shfl_sync(kFull, base, 31);
+    }
+    int at = incl - cnt;
     for (uint32_t hh = hits; hh; hh &= hh - 1u, ++at) {
       const int e = __ffs(hh) - 1;
       float sc = stage[lane * 33 + e];
       if (FMT == OP_E4M3) sc = sc * p.out_scale / (row_norm * nstage[e]);
-      if (at < (unsigned long long)p.capacity) {
-        mrc_pair pr;
-        pr.i = (int32_t)i;
-        pr.j = (int32_t)(j0 + e);
-        pr.score = sc;
-        p.pairs[at] = pr;
-      }
+      mrc_pair pr;
+      pr.i = (int32_t)i;
+      pr.j = (int32_t)(j0 + e);
+      pr.score = sc;
+      if (!direct)
+        buf[nbuf + at] = pr;
+      else if (base + at < (unsigned long long)p.capacity)
+        p.pairs[base + at] = pr;
     }
+    if (!direct) nbuf += total;
   }
   __syncwarp();
 }
@@ -287,10 +309,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
   float* stage_all = reinterpret_cast<float*>(drain + 4);  // [4 epilogue warps][32 x 33 + 32]
+  mrc_pair* pbuf_all = reinterpret_cast<mrc_pair*>(stage_all + 4 * (32 * 33 + 32));  // [4][kPairBuf]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* stage = stage_all + (warp >= 2 ? warp - 2 : 0) * (32 * 33 + 32);
   float* nstage = stage + 32 * 33;
+  mrc_pair* pbuf = pbuf_all + (warp >= 2 ? warp - 2 : 0) * kPairBuf;
+  int nbuf = 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -478,7 +503,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         } else {
-          emit_chunk<FMT>(p, v, i, j0, lane, fast_thresh, row_norm, stage, nstage);
+          emit_chunk<FMT>(p, v, i, j0, lane, fast_thresh, row_norm, stage, nstage, pbuf, nbuf);
         }
       }
       tc_fence_before();
@@ -486,6 +511,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) mbar_arrive(&acc_empty[ab]);
       ++it;
     }
+    flush_pairs(p, pbuf, nbuf, lane);
   }
   tc_fence_before();
   __syncthreads();
@@ -568,10 +594,13 @@ __global__ void __launch_bounds__(kResThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
   float* stage_all = reinterpret_cast<float*>(drain + 4);  // [8 warps][32 x 33 + 32]
+  mrc_pair* pbuf_all = reinterpret_cast<mrc_pair*>(stage_all + 8 * (32 * 33 + 32));  // [8][kPairBuf]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* stage = stage_all + (warp >= 2 ? warp - 2 : 0) * (32 * 33 + 32);
   float* nstage = stage + 32 * 33;
+  mrc_pair* pbuf = pbuf_all + (warp >= 2 ? warp - 2 : 0) * kPairBuf;
+  int nbuf = 0;
   const int64_t t_begin = p.n_tiles * blockIdx.x / gridDim.x;
   const int64_t t_end = p.n_tiles * (blockIdx.x + 1) / gridDim.x;
   if (threadIdx.x == 0) {
@@ -749,10 +778,11 @@ __global__ void __launch_bounds__(kResThreads, 1)
         const int64_t j0 = bj * BN + (half * CH + c) * 32;
         float fast_thresh = row_bound;
         if (FMT == OP_E4M3 && p.thresh > 0.f) fast_thresh = row_bound * ((((half * CH + c) * 32) >> 7) ? nmin1 : nmin0);
-        emit_chunk<FMT>(p, v[c], i, j0, lane, fast_thresh, row_norm, stage, nstage);
+        emit_chunk<FMT>(p, v[c], i, j0, lane, fast_thresh, row_norm, stage, nstage, pbuf, nbuf);
       }
       ++it;
     }
+    flush_pairs(p, pbuf, nbuf, lane);
   }
   tc_fence_before();
   __syncthreads();
@@ -831,7 +861,7 @@ cudaError_t run_gemm_resident(mrc_ctx* ctx, const GemmArgs& g) {
   // at least 120 KB, so that one CTA (which owns all 512 TMEM columns) runs per SM
   const size_t smem =
       std::max<size_t>(1024 + 2 * (size_t)C::NOPS * kBM * RB + (size_t)kResStagesB * C::NOPS * BN * RB + 256 +
-                           8 * (32 * 33 + 32) * sizeof(float),
+                           8 * (32 * 33 + 32) * sizeof(float) + 8 * kPairBuf * sizeof(mrc_pair),
                        120 * 1024);
   if (resident_ctas(k_gemm_resident<FMT, RB, BN>, kResThreads, smem) <= 0) return cudaErrorInvalidConfiguration;
   int64_t grid = ctx->num_sms;
@@ -886,7 +916,8 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   p.store16 = reinterpret_cast<__half*>(g.store16);
   p.ld = g.ld;
   p.err = g.err;
-  const size_t smem = 1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256 + 4 * (32 * 33 + 32) * 4;
+  const size_t smem = 1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256 + 4 * (32 * 33 + 32) * 4 +
+                      4 * kPairBuf * sizeof(mrc_pair);
   if (resident_ctas(k_gemm_compare<FMT>, kThreads, smem) <= 0) return cudaErrorInvalidConfiguration;
   int64_t grid = ctx->num_sms;
   if (p.n_tiles < grid) grid = p.n_tiles;
