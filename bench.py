@@ -39,9 +39,9 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # the news20 step, valid only while the kernel's source file is unchanged since the capture.
 NCU_TRAFFIC = {
     "cosine_tail": ("paper_1810_03099_gb300/csrc/tail.cu",
-                    "2ca969a90258090a3f42e445e7b26ec9e0fa34a6cbbdbf3735e81b2468f74037", 416108032),
+                    "19bc835feb3fd7e07d1be0ed5c4ab051a9cc5e4dafc7804d229ee40319ffe20a", 416553984),
     "gemm_f16_store": ("paper_1810_03099_gb300/csrc/compare_tc.cu",
-                       "cfc6bb80e5563bfcceb64c7bf1cf6f7311a04e661ff2fa2d596671454a3713f0", 351628800),
+                       "86febfa900da6472714ddbacea36b2f5c93d9f7fff104bd1e6083945317581f7", 351744768),
 }
 KERNEL_NOTES = {
     "cosine_tail": "algorithmic bytes = the fp16 head scores of the upper triangle; the postings it also walks "
@@ -376,6 +376,9 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     caps = {"sig": 1 << 22, "cos": 1 << 22, "sh": 1 << 22}
     counts = {}
+    # device step: stream-ordered calls into preallocated device pair buffers, counts on the device
+    pbuf = {key: torch.empty((cap, 3), dtype=torch.int32, device="cuda") for key, cap in caps.items()}
+    dcount = torch.zeros(3, dtype=torch.int64, device="cuda")
 
     def step(host: bool):
         if host:
@@ -387,17 +390,27 @@ def main():
         else:
             idx = mrc.mrc_build_index(ctx, offs_d, toks_d, V, params)
             sh = mrc.index_simhash(ctx, idx, torch.empty(N, dtype=torch.int64, device="cuda"))
-            p1, n1 = mrc.mrc_match(ctx, idx, None, TAU, capacity=caps["sig"])
-            p2, n2 = mrc.simhash_match(ctx, sh, None, HMAX, capacity=caps["sh"])
-            p3, n3 = mrc.cosine_allpairs(ctx, idx, offs_d, toks_d, TAU, capacity=caps["cos"])
+            mrc.mrc_match_async(ctx, idx, pbuf["sig"], dcount[0:1], None, TAU)
+            mrc.simhash_match_async(ctx, sh, pbuf["sh"], dcount[1:2], None, HMAX)
+            mrc.cosine_allpairs_async(ctx, idx, offs_d, toks_d, pbuf["cos"], dcount[2:3], TAU)
+            idx.free()
+            return None
         idx.free()
         counts.update(sig_pairs=n1, simhash_pairs=n2, cosine_pairs=n3)
         return (p1, p2, p3)
+
+    def device_counts():
+        ctx.sync()  # raises a device-side error of the stream-ordered calls
+        n1, n2, n3 = (int(x) for x in dcount.tolist())
+        assert n1 <= caps["sig"] and n2 <= caps["sh"] and n3 <= caps["cos"], "pair buffers too small"
+        counts.update(sig_pairs=n1, simhash_pairs=n2, cosine_pairs=n3)
 
     def timed(host: bool, steps: int, warmup: int, with_timing: bool):
         for _ in range(warmup):
             step(host)
         torch.cuda.synchronize()
+        if not host:
+            device_counts()
         if dist:
             dist.barrier()
         ctx.reset_stats()
@@ -412,6 +425,8 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
             total_ms += e0.elapsed_time(e1)
+            if not host:
+                device_counts()
         ctx.set_timing(False)
         stats = ctx.kernel_stats()
         if dist:
@@ -485,7 +500,7 @@ def main():
         "kernel_events_region_ms_per_step": inst_ms / args.steps,
         "kernels": kernels,
     }
-    sig_k = [s for s in stats if s["name"] == "gemm_split16_thresh"]
+    sig_k = [s for s in stats if s["name"] == "gemm_f16_thresh"]
     if sig_k:
         per = sig_k[0]["ms"] / sig_k[0]["launches"] / 1e3
         line["signature_pairs_per_s"] = N * (N - 1) / 2 / per

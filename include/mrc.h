@@ -21,8 +21,9 @@
  *   and all device memory they hold.
  * - All work is issued on the stream given to mrc_ctx_create. Calls that return
  *   a pair count (mrc_match, cosine_allpairs, simhash_match) synchronise that
- *   stream before returning; the other calls are stream-ordered and their
- *   device outputs are valid once the stream reaches them.
+ *   stream before returning; their *_async forms and the other calls are
+ *   stream-ordered and their device outputs are valid once the stream reaches
+ *   them (mrc_ctx_sync waits for that and reports device-side errors).
  * - Pairs: all-pairs calls emit each unordered pair once with i < j; query
  *   calls emit (query index i, index/database position j). Self-pairs are never
  *   emitted. Pair order in the output is unspecified. *n_pairs always receives
@@ -196,6 +197,35 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
  */
 mrc_status simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
                          int32_t hamming_max, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs);
+
+/*
+ * Stream-ordered forms of the three pair calls: the same work and the same
+ * pairs, but nothing waits for the device. `pairs` (when capacity > 0) and
+ * d_n_pairs must be device memory; d_n_pairs receives the total pair count
+ * (int64) when the stream reaches the end of the call, and min(total,
+ * capacity) pairs are written. A total above `capacity` is not an error here:
+ * the caller reads *d_n_pairs and compares. Inputs may be host or device memory
+ * as everywhere; a host input is copied before the call returns.
+ * Device-side errors (a bounded wait that expired, a candidate buffer that
+ * overflowed -- the reduced-precision forms first collect candidates in a
+ * buffer of max(4 * capacity, 2^20) entries, which the synchronous form grows
+ * and repeats on overflow) are recorded in the context and returned by the
+ * next mrc_ctx_sync. cosine_allpairs_async still waits once, after its first
+ * pass, for the sizes of its head/tail split.
+ * Host-side argument errors return at once, as in the synchronous forms.
+ *
+ * mrc_ctx_sync waits for the context's stream and returns the first recorded
+ * device-side error of the stream-ordered calls since the previous
+ * mrc_ctx_sync (MRC_ERR_TIMEOUT, MRC_ERR_CAPACITY for a candidate overflow,
+ * ...), clearing it; MRC_OK otherwise.
+ */
+mrc_status mrc_match_async(mrc_ctx* ctx, const mrc_index* index, const float* query_sig, int64_t nq, float tau,
+                           mrc_pair* pairs, int64_t capacity, int64_t* d_n_pairs);
+mrc_status cosine_allpairs_async(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float tau,
+                                 mrc_pair* pairs, int64_t capacity, int64_t* d_n_pairs);
+mrc_status simhash_match_async(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
+                               int32_t hamming_max, mrc_pair* pairs, int64_t capacity, int64_t* d_n_pairs);
+mrc_status mrc_ctx_sync(mrc_ctx* ctx);
 
 /*
  * Batched queries, captured once as a CUDA graph (one graph launch per batch).

@@ -191,6 +191,9 @@ mrc_status err_status(mrc_ctx* ctx, int32_t h) {
     return fail(ctx, MRC_ERR_UNSUPPORTED, "a document is longer than MRC_MAX_DOC_TOKENS tokens");
   if (h & kErrBadToken) return fail(ctx, MRC_ERR_INVALID, "a token id is outside [0, vocab)");
   if (h & kErrTable) return fail(ctx, MRC_ERR_CUDA, "internal: per-document term table overflow");
+  if (h & kErrOverflow)
+    return fail(ctx, MRC_ERR_CAPACITY, "a candidate buffer overflowed: pairs may be missing; repeat the call with "
+                                       "its synchronous form");
   return MRC_OK;
 }
 
@@ -579,6 +582,14 @@ mrc_status mrc_ctx_create(void* cuda_stream, mrc_ctx** out) {
     delete c;
     return MRC_ERR_OOM;
   }
+  if (cudaMalloc(&c->async_err, sizeof(int32_t)) != cudaSuccess ||
+      cudaMemset(c->async_err, 0, sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->async_err) cudaFree(c->async_err);
+    cudaFreeHost(c->pinned);
+    delete c;
+    return MRC_ERR_OOM;
+  }
   *out = c;
   return MRC_OK;
 }
@@ -594,6 +605,7 @@ void mrc_ctx_destroy(mrc_ctx* ctx) {
   }
   for (auto e : ctx->free_events) cudaEventDestroy(e);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->async_err) cudaFree(ctx->async_err);
   if (ctx->host_ws) cudaFreeHost(ctx->host_ws);
   if (ctx->host_ws_done) cudaEventDestroy(ctx->host_ws_done);
   delete ctx;
@@ -742,15 +754,20 @@ mrc_status mrc_signature(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* d
   return MRC_OK;
 }
 
-mrc_status mrc_match(mrc_ctx* ctx, const mrc_index* index, const float* query_sig, int64_t nq, float tau,
-                     mrc_pair* pairs, int64_t capacity, int64_t* n_pairs) {
+// mrc_match, or with d_total its stream-ordered form: the pair count goes to *d_total (device),
+// errors to the context's stream-ordered error word, and nothing waits.
+static mrc_status match_impl(mrc_ctx* ctx, const mrc_index* index, const float* query_sig, int64_t nq, float tau,
+                      mrc_pair* pairs, int64_t capacity, int64_t* n_pairs, unsigned long long* d_total) {
   if (!ctx || !index) return MRC_ERR_INVALID;
   Scope scope(ctx);
   if (capacity < 0) return fail(ctx, MRC_ERR_INVALID, "capacity < 0");
   if (query_sig && nq < 0) return fail(ctx, MRC_ERR_INVALID, "nq < 0");
   if (n_pairs) *n_pairs = 0;
   mrc_status st = MRC_OK;
-  int32_t* d_err = call_err(ctx, &st);
+  const bool async = d_total != nullptr;
+  if (async && ((capacity > 0 && (!pairs || !is_device_ptr(pairs))) || !is_device_ptr(d_total)))
+    return fail(ctx, MRC_ERR_INVALID, "stream-ordered calls take device pairs and a device pair count");
+  int32_t* d_err = async ? ctx->async_err : call_err(ctx, &st);
   if (!d_err) return st;
   const int64_t N = index->n_docs;
   const int32_t prec = index->params.precision;
@@ -758,7 +775,10 @@ mrc_status mrc_match(mrc_ctx* ctx, const mrc_index* index, const float* query_si
   mrc_pair* dst = pair_dest(ctx, pairs, capacity, &st);
   if (st != MRC_OK) return st;
   cudaMemsetAsync(d_count, 0, 2 * sizeof(unsigned long long), ctx->stream);
-  if ((query_sig && nq == 0) || (!query_sig && N < 2)) return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
+  unsigned long long* pc = async ? d_total : d_count;  // the pair counter; d_count[1] counts candidates
+  if (async) cudaMemsetAsync(pc, 0, sizeof(unsigned long long), ctx->stream);
+  if ((query_sig && nq == 0) || (!query_sig && N < 2))
+    return async ? MRC_OK : finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
 
   // query operands (packed unit signatures) or the index itself
   const void *a_hi = index->op_hi, *a8 = index->op_e4m3;
@@ -812,13 +832,17 @@ mrc_status mrc_match(mrc_ctx* ctx, const mrc_index* index, const float* query_si
     mrc_pair* cand = (mrc_pair*)ws_get(ctx, "match.cand", sizeof(mrc_pair) * (size_t)cand_cap, &st);
     if (st != MRC_OK) return st;
     cudaMemsetAsync(d_count, 0, 2 * sizeof(unsigned long long), ctx->stream);
+    if (async) cudaMemsetAsync(pc, 0, sizeof(unsigned long long), ctx->stream);
     g.pairs = cand;
     g.count = d_count + 1;
     g.capacity = cand_cap;
     cudaError_t e = launch_gemm_compare(ctx, g);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "signature compare");
-    e = launch_rescore(ctx, cand, d_count + 1, cand_cap, a_unit, index->sig_unit, index->k, tau, dst, d_count, capacity);
+    // the synchronous form retries an overflow below; the stream-ordered form reports it
+    e = launch_rescore(ctx, cand, d_count + 1, cand_cap, a_unit, index->sig_unit, index->k, tau, dst, pc, capacity,
+                       async ? d_err : nullptr);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rescoring");
+    if (async) return MRC_OK;  // a candidate overflow is reported by mrc_ctx_sync
     unsigned long long* hc = (unsigned long long*)ctx->pinned;
     e = cudaMemcpyAsync(hc + 1, d_count + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reading candidate count");
@@ -830,24 +854,30 @@ mrc_status mrc_match(mrc_ctx* ctx, const mrc_index* index, const float* query_si
   return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
 }
 
-mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float tau, mrc_pair* pairs,
-                           int64_t capacity, int64_t* n_pairs) {
+// cosine_allpairs, or with d_total its stream-ordered form (see match_impl); the head/tail split
+// still waits once for its totals.
+static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float tau, mrc_pair* pairs,
+                       int64_t capacity, int64_t* n_pairs, unsigned long long* d_total) {
   if (!ctx || !index) return MRC_ERR_INVALID;
   Scope scope(ctx);
   if (capacity < 0) return fail(ctx, MRC_ERR_INVALID, "capacity < 0");
   if (n_pairs) *n_pairs = 0;
   mrc_status st = MRC_OK;
-  int32_t* d_err = call_err(ctx, &st);
+  const bool async = d_total != nullptr;
+  if (async && ((capacity > 0 && (!pairs || !is_device_ptr(pairs))) || !is_device_ptr(d_total)))
+    return fail(ctx, MRC_ERR_INVALID, "stream-ordered calls take device pairs and a device pair count");
+  int32_t* d_err = call_err(ctx, &st);  // checked at the split's synchronisation
   if (!d_err) return st;
   DocsDev d;
   if ((st = stage_docs(ctx, docs, "cos", &d, d_err)) != MRC_OK) return st;
   const int64_t N = d.n_docs;
   const int32_t V = index->vocab;
-  unsigned long long* d_count = (unsigned long long*)ws_get(ctx, "cos.count", sizeof(unsigned long long), &st);
+  unsigned long long* d_count =
+      async ? d_total : (unsigned long long*)ws_get(ctx, "cos.count", sizeof(unsigned long long), &st);
   mrc_pair* dst = pair_dest(ctx, pairs, capacity, &st);
   if (st != MRC_OK) return st;
   cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), ctx->stream);
-  if (N < 2) return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
+  if (N < 2) return async ? MRC_OK : finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
 
   // document frequencies within these documents decide the head/tail split: head = terms
   // whose postings are dense enough that a tensor-core column beats sparse products,
@@ -942,7 +972,7 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   g.out_scale = 1.0f;
   g.store16 = d_H;
   g.ld = ldh;
-  g.err = d_err;
+  g.err = async ? ctx->async_err : d_err;
   e = launch_gemm_compare(ctx, g);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "head GEMM");
   const float delta = (float)(std::ldexp(1.0, -10) + std::ldexp(1.0, -12) + (double)kd * std::ldexp(1.0, -23) + 1e-4);
@@ -951,11 +981,14 @@ mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs*
   e = launch_cosine_tail(ctx, N, d_H, ldh, d.offsets, d_rcnt, d_rwalk, d_rw, d_spost, n_post, d_hhi, d_hlo, kd,
                          tau, delta, dst, d_count, capacity, tail_work, d_next);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tail pass");
+  if (async) return MRC_OK;
   return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs, d_err);
 }
 
-mrc_status simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
-                         int32_t hamming_max, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs) {
+// simhash_match, or with d_total its stream-ordered form (see match_impl).
+static mrc_status simhash_impl(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
+                        int32_t hamming_max, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs,
+                        unsigned long long* d_total) {
   if (!ctx) return MRC_ERR_INVALID;
   Scope scope(ctx);
   if (na < 0 || (b && nb < 0) || capacity < 0 || (na > 0 && !a))
@@ -963,7 +996,11 @@ mrc_status simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint
   if (na >= (1ll << 31) || nb >= (1ll << 31)) return fail(ctx, MRC_ERR_UNSUPPORTED, "more than 2^31 fingerprints");
   if (n_pairs) *n_pairs = 0;
   mrc_status st = MRC_OK;
-  unsigned long long* d_count = (unsigned long long*)ws_get(ctx, "sh.count", sizeof(unsigned long long), &st);
+  const bool async = d_total != nullptr;
+  if (async && ((capacity > 0 && (!pairs || !is_device_ptr(pairs))) || !is_device_ptr(d_total)))
+    return fail(ctx, MRC_ERR_INVALID, "stream-ordered calls take device pairs and a device pair count");
+  unsigned long long* d_count =
+      async ? d_total : (unsigned long long*)ws_get(ctx, "sh.count", sizeof(unsigned long long), &st);
   mrc_pair* dst = pair_dest(ctx, pairs, capacity, &st);
   if (st != MRC_OK) return st;
   cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), ctx->stream);
@@ -974,7 +1011,52 @@ mrc_status simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint
     cudaError_t e = launch_simhash_match(ctx, da, na, db, b ? nb : 0, hamming_max, dst, d_count, capacity);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "simhash match");
   }
+  if (async) return MRC_OK;
   return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
+}
+
+mrc_status mrc_match(mrc_ctx* ctx, const mrc_index* index, const float* query_sig, int64_t nq, float tau,
+                     mrc_pair* pairs, int64_t capacity, int64_t* n_pairs) {
+  return match_impl(ctx, index, query_sig, nq, tau, pairs, capacity, n_pairs, nullptr);
+}
+
+mrc_status mrc_match_async(mrc_ctx* ctx, const mrc_index* index, const float* query_sig, int64_t nq, float tau,
+                           mrc_pair* pairs, int64_t capacity, int64_t* d_n_pairs) {
+  if (!d_n_pairs) return ctx ? fail(ctx, MRC_ERR_INVALID, "d_n_pairs is NULL") : MRC_ERR_INVALID;
+  return match_impl(ctx, index, query_sig, nq, tau, pairs, capacity, nullptr, (unsigned long long*)d_n_pairs);
+}
+
+mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float tau, mrc_pair* pairs,
+                           int64_t capacity, int64_t* n_pairs) {
+  return cosine_impl(ctx, index, docs, tau, pairs, capacity, n_pairs, nullptr);
+}
+
+mrc_status cosine_allpairs_async(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float tau,
+                                 mrc_pair* pairs, int64_t capacity, int64_t* d_n_pairs) {
+  if (!d_n_pairs) return ctx ? fail(ctx, MRC_ERR_INVALID, "d_n_pairs is NULL") : MRC_ERR_INVALID;
+  return cosine_impl(ctx, index, docs, tau, pairs, capacity, nullptr, (unsigned long long*)d_n_pairs);
+}
+
+mrc_status simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
+                         int32_t hamming_max, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs) {
+  return simhash_impl(ctx, a, na, b, nb, hamming_max, pairs, capacity, n_pairs, nullptr);
+}
+
+mrc_status simhash_match_async(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
+                               int32_t hamming_max, mrc_pair* pairs, int64_t capacity, int64_t* d_n_pairs) {
+  if (!d_n_pairs) return ctx ? fail(ctx, MRC_ERR_INVALID, "d_n_pairs is NULL") : MRC_ERR_INVALID;
+  return simhash_impl(ctx, a, na, b, nb, hamming_max, pairs, capacity, nullptr, (unsigned long long*)d_n_pairs);
+}
+
+mrc_status mrc_ctx_sync(mrc_ctx* ctx) {
+  if (!ctx) return MRC_ERR_INVALID;
+  Scope scope(ctx);
+  int32_t* h = (int32_t*)((char*)ctx->pinned + 256);
+  cudaError_t e = cudaMemcpyAsync(h, ctx->async_err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->async_err, 0, sizeof(int32_t), ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronising the context's stream");
+  return err_status(ctx, *h);
 }
 
 mrc_status mrc_index_get_info(const mrc_index* x, mrc_index_info* info) {

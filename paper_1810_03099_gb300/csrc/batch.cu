@@ -155,7 +155,7 @@ cudaError_t record(mrc_batch* b) {
   e = launch_gemm_compare(ctx, g);
   if (e != cudaSuccess) return e;
   e = launch_rescore(ctx, b->d_cand, b->d_counts + 1, b->cand_cap, b->d_unit, x->sig_unit, x->k, b->tau,
-                     b->d_pairs, b->d_counts, b->capacity);
+                     b->d_pairs, b->d_counts, b->capacity, b->d_err);
   if (e != cudaSuccess) return e;
   // group the pairs by query, so each query's pairs come back as one slice
   e = cudaMemsetAsync(b->d_qcnt, 0, sizeof(int32_t) * (size_t)b->max_docs, ctx->stream);

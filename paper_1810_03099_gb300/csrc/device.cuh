@@ -14,6 +14,7 @@ constexpr int32_t kErrBadOffsets = 2;  // offsets not non-decreasing from 0
 constexpr int32_t kErrTimeout = 4;     // a bounded wait gave up
 constexpr int32_t kErrTable = 8;       // a per-document table overflowed (cannot happen at load <= 1/2)
 constexpr int32_t kErrTooLong = 16;    // a document longer than the supported maximum
+constexpr int32_t kErrOverflow = 32;   // a candidate buffer overflowed (pairs may be missing)
 
 __device__ __forceinline__ void set_err(int32_t* err, int32_t bit) {
   if (err) atomicOr(err, bit);

@@ -62,6 +62,7 @@ struct mrc_ctx {
   void* host_ws = nullptr;  // grow-only pinned host scratch (vocabulary-sized tables)
   size_t host_ws_bytes = 0;
   cudaEvent_t host_ws_done = nullptr;  // recorded after the last copy that reads host_ws
+  int32_t* async_err = nullptr;  // device error word of the stream-ordered calls (until mrc_ctx_sync)
 };
 
 struct mrc_index {
@@ -264,6 +265,6 @@ cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t
                                int64_t capacity, double work_pairs, unsigned long long* next_item);
 cudaError_t launch_rescore(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand, int64_t cand_cap,
                            const float* qunit, const float* xunit, int32_t k, float tau, mrc_pair* pairs,
-                           unsigned long long* count, int64_t capacity);
+                           unsigned long long* count, int64_t capacity, int32_t* err);
 
 }  // namespace mrc

@@ -530,11 +530,12 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_cosine_tail(
 
 __global__ void k_rescore(const mrc_pair* __restrict__ cand, const unsigned long long* n_cand, int64_t cand_cap,
                           const float* __restrict__ qunit, const float* __restrict__ xunit, int32_t k, float tau,
-                          mrc_pair* pairs, unsigned long long* count, int64_t capacity) {
+                          mrc_pair* pairs, unsigned long long* count, int64_t capacity, int32_t* err) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t nc0 = (int64_t)*n_cand;
   const int64_t nc = nc0 < cand_cap ? nc0 : cand_cap;
+  if (err && nc0 > cand_cap && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, kErrOverflow);
   for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nc; c += nwarps) {
     const mrc_pair pc = cand[c];
     const float* qa = qunit + (int64_t)pc.i * k;
@@ -644,12 +645,12 @@ cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t
 
 cudaError_t launch_rescore(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand, int64_t cand_cap,
                            const float* qunit, const float* xunit, int32_t k, float tau, mrc_pair* pairs,
-                           unsigned long long* count, int64_t capacity) {
+                           unsigned long long* count, int64_t capacity, int32_t* err) {
   int64_t grid = (int64_t)ctx->num_sms * 8;
   cudaEvent_t ev = nullptr;
   timing_begin(ctx, "rescore", 0.0, 0.0, &ev);
   k_rescore<<<(unsigned)grid, 256, 0, ctx->stream>>>(cand, n_cand, cand_cap, qunit, xunit, k, tau, pairs, count,
-                                                     capacity);
+                                                     capacity, err);
   timing_end(ctx, ev);
   return cudaGetLastError();
 }

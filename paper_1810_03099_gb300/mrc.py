@@ -67,6 +67,13 @@ _SIGNATURES = {
                                     C.POINTER(C.c_int64)]),
     "simhash_match": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
                                   C.c_int64, C.POINTER(C.c_int64)]),
+    "mrc_match_async": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_void_p,
+                                    C.c_int64, C.c_void_p]),
+    "cosine_allpairs_async": (C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(Docs), C.c_float, C.c_void_p,
+                                          C.c_int64, C.c_void_p]),
+    "simhash_match_async": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
+                                        C.c_void_p, C.c_int64, C.c_void_p]),
+    "mrc_ctx_sync": (C.c_int32, [C.c_void_p]),
     "mrc_index_get_info": (C.c_int32, [C.c_void_p, C.POINTER(IndexInfo)]),
     "mrc_index_export": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p]),
@@ -167,6 +174,10 @@ class Context:
     def check(self, st):
         if st != MRC_OK:
             raise MrcError(st, self.last_error())
+
+    def sync(self):
+        """Wait for the context's stream; raise a device-side error of the stream-ordered calls."""
+        self.check(self.lib.mrc_ctx_sync(self.handle))
 
     def last_error(self) -> str:
         return self.lib.mrc_last_error(self.handle).decode()
@@ -397,6 +408,42 @@ def simhash_match(ctx: Context, a, b=None, hamming_max: int = 3, capacity: int =
         return ctx.lib.simhash_match(ctx.handle, _ptr(a), na, _ptr(b), nb, int(hamming_max), _ptr(buf), cap,
                                      C.byref(total))
     return _pair_call(ctx, fn, capacity, device, grow)
+
+
+def _async_out(pairs, count):
+    import torch
+    if not (_is_torch(pairs) and pairs.is_cuda and pairs.dtype == torch.int32 and pairs.dim() == 2
+            and pairs.shape[1] == 3 and pairs.is_contiguous()):
+        raise TypeError("pairs must be a contiguous CUDA int32 tensor of shape [capacity, 3]")
+    if not (_is_torch(count) and count.is_cuda and count.dtype == torch.int64 and count.numel() >= 1):
+        raise TypeError("count must be a CUDA int64 tensor")
+    return int(pairs.shape[0]), _ptr(count)
+
+
+def mrc_match_async(ctx: Context, index: Index, pairs, count, query_sig=None, tau: float = 0.9):
+    """Stream-ordered mrc_match: writes up to pairs.shape[0] pairs and count[0] = total; no wait."""
+    cap, pc = _async_out(pairs, count)
+    nq = 0 if query_sig is None else int(query_sig.shape[0])
+    if query_sig is not None:
+        _check_dtype(query_sig, np.float32, "float32")
+    ctx.check(ctx.lib.mrc_match_async(ctx.handle, index.handle, _ptr(query_sig), nq, float(tau), _ptr(pairs), cap,
+                                      pc))
+
+
+def cosine_allpairs_async(ctx: Context, index: Index, offsets, tokens, pairs, count, tau: float = 0.9):
+    """Stream-ordered cosine_allpairs (one wait, after the head/tail split is known)."""
+    cap, pc = _async_out(pairs, count)
+    d = _docs(offsets, tokens)
+    ctx.check(ctx.lib.cosine_allpairs_async(ctx.handle, index.handle, C.byref(d), float(tau), _ptr(pairs), cap, pc))
+
+
+def simhash_match_async(ctx: Context, a, pairs, count, b=None, hamming_max: int = 3):
+    """Stream-ordered simhash_match."""
+    cap, pc = _async_out(pairs, count)
+    na = int(a.shape[0])
+    nb = 0 if b is None else int(b.shape[0])
+    ctx.check(ctx.lib.simhash_match_async(ctx.handle, _ptr(a), na, _ptr(b), nb, int(hamming_max), _ptr(pairs), cap,
+                                          pc))
 
 
 def mrc_index_export(ctx: Context, index: Index):
