@@ -376,9 +376,15 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     caps = {"sig": 1 << 22, "cos": 1 << 22, "sh": 1 << 22}
     counts = {}
-    # device step: stream-ordered calls into preallocated device pair buffers, counts on the device
+    # device step: stream-ordered calls into preallocated device pair buffers, counts on the device;
+    # the signature and Simhash matches run on a second stream (their own context) beside the
+    # exact cosine, which needs the index only
     pbuf = {key: torch.empty((cap, 3), dtype=torch.int32, device="cuda") for key, cap in caps.items()}
     dcount = torch.zeros(3, dtype=torch.int64, device="cuda")
+    sh_dev = torch.empty(N, dtype=torch.int64, device="cuda")
+    stream2 = torch.cuda.Stream()
+    ctx2 = mrc.Context(stream2.cuda_stream)
+    built = torch.cuda.Event()
 
     def step(host: bool):
         if host:
@@ -389,17 +395,21 @@ def main():
             p3, n3 = mrc.cosine_allpairs(ctx, idx, offs_h, toks_h, TAU, capacity=caps["cos"], device=None)
         else:
             idx = mrc.mrc_build_index(ctx, offs_d, toks_d, V, params)
-            sh = mrc.index_simhash(ctx, idx, torch.empty(N, dtype=torch.int64, device="cuda"))
-            mrc.mrc_match_async(ctx, idx, pbuf["sig"], dcount[0:1], None, TAU)
-            mrc.simhash_match_async(ctx, sh, pbuf["sh"], dcount[1:2], None, HMAX)
+            sh = mrc.index_simhash(ctx, idx, sh_dev)
+            built.record(stream)
+            stream2.wait_event(built)
+            mrc.mrc_match_async(ctx2, idx, pbuf["sig"], dcount[0:1], None, TAU)
+            mrc.simhash_match_async(ctx2, sh, pbuf["sh"], dcount[1:2], None, HMAX)
             mrc.cosine_allpairs_async(ctx, idx, offs_d, toks_d, pbuf["cos"], dcount[2:3], TAU)
-            idx.free()
+            stream.wait_stream(stream2)
+            idx.free()  # in order on the index's stream, after both streams' uses
             return None
         idx.free()
         counts.update(sig_pairs=n1, simhash_pairs=n2, cosine_pairs=n3)
         return (p1, p2, p3)
 
     def device_counts():
+        ctx2.sync()
         ctx.sync()  # raises a device-side error of the stream-ordered calls
         n1, n2, n3 = (int(x) for x in dcount.tolist())
         assert n1 <= caps["sig"] and n2 <= caps["sh"] and n3 <= caps["cos"], "pair buffers too small"
@@ -413,8 +423,9 @@ def main():
             device_counts()
         if dist:
             dist.barrier()
-        ctx.reset_stats()
-        ctx.set_timing(with_timing)
+        for cx in (ctx, ctx2):
+            cx.reset_stats()
+            cx.set_timing(with_timing)
         total_ms = 0.0
         for _ in range(steps):
             flush.zero_()
@@ -427,8 +438,14 @@ def main():
             total_ms += e0.elapsed_time(e1)
             if not host:
                 device_counts()
-        ctx.set_timing(False)
-        stats = ctx.kernel_stats()
+        stats = {}
+        for cx in (ctx, ctx2):
+            cx.set_timing(False)
+            for st in cx.kernel_stats():
+                acc = stats.setdefault(st["name"], dict(st, launches=0, ms=0.0, bytes=0.0, flops=0.0))
+                for key in ("launches", "ms", "bytes", "flops"):
+                    acc[key] += st[key]
+        stats = list(stats.values())
         if dist:
             t = torch.tensor([total_ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -508,6 +525,7 @@ def main():
         line["cpu_baseline"] = cpu_baseline_leg(c)
     if rank == 0:
         print(json.dumps(line), flush=True)
+    ctx2.close()
     ctx.close()
     if dist:
         dist.destroy_process_group()

@@ -448,6 +448,9 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
     __syncwarp();
     it = __shfl_sync(kFull, next, 0);
   }
+  // This grid may start while the CTA path's grid (launched just before it) is still running;
+  // it completes only after that grid, so the next launch on the stream sees both.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // The CTA's warps walk table slots [0, lim) in 32-slot chunks, each with the next chunk's
@@ -504,6 +507,8 @@ __global__ void __launch_bounds__(kLongThreads, 2) k_ingest_long(IngestParams p)
   uint32_t* cnts = keys + kLongSlots;
 
   const int32_t n_long = p.list_counts[1];
+  // the warp path's grid may start on SMs this grid leaves (the two touch disjoint documents)
+  asm volatile("griddepcontrol.launch_dependents;");
   while (true) {
     if (threadIdx.x == 0) misc[0] = atomicAdd(p.long_cursor, 1);
     __syncthreads();
@@ -757,18 +762,12 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   const size_t s_smem = short_smem(kq), l_smem = long_smem(kq);
   const double tokens = (double)d.n_tokens;
   cudaEvent_t ev = nullptr;
-  {
-    int grid = short_grid<MODE>(ctx, s_smem);
-    if (grid <= 0) return cudaErrorInvalidConfiguration;
-    const int64_t need = (d.n_docs + kWarpsShort - 1) / kWarpsShort;
-    if (need < grid) grid = (int)need;
-    std::string nm = std::string(name) + ".short";
-    timing_begin(ctx, nm.c_str(), tokens * bytes_per_token + bytes_per_doc * d.n_docs, 0.0, &ev);
-    k_ingest_short<MODE><<<grid, kWarpsShort * 32, s_smem, ctx->stream>>>(p);
-    timing_end(ctx, ev);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+  // The CTA path (longest documents first) is launched first; the warp path follows as a
+  // programmatic dependent launch, so its CTAs fill SMs as the CTA path's grid drains instead
+  // of waiting for the whole grid. Not while the stream is being captured into a graph.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(ctx->stream, &cap);
+  const bool overlap = cap == cudaStreamCaptureStatusNone && !ctx->timing;
   {
     int grid = long_grid<MODE>(ctx, l_smem);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
@@ -778,6 +777,28 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
     k_ingest_long<MODE><<<grid, kLongThreads, l_smem, ctx->stream>>>(p);
     timing_end(ctx, ev);
     e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  {
+    int grid = short_grid<MODE>(ctx, s_smem);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    const int64_t need = (d.n_docs + kWarpsShort - 1) / kWarpsShort;
+    if (need < grid) grid = (int)need;
+    std::string nm = std::string(name) + ".short";
+    timing_begin(ctx, nm.c_str(), tokens * bytes_per_token + bytes_per_doc * d.n_docs, 0.0, &ev);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kWarpsShort * 32);
+    cfg.dynamicSmemBytes = s_smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = overlap ? 1 : 0;
+    e = cudaLaunchKernelEx(&cfg, k_ingest_short<MODE>, p);
+    timing_end(ctx, ev);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -6,16 +6,20 @@
 // [#{df > v}, #{df > v} + cnt[v]), so only the df values whose rank range meets the selection
 // matter: a contiguous band of values [v_lo, v_hi]. The device pass
 //   1. histograms df (k_df_hist),
-//   2. turns the histogram into #{df > v} and finds start, L and the band (one CTA,
-//      k_sel_band),
-//   3. collects the band's terms (k_band_collect) and
-//   4. sorts them by (df descending, id ascending) in shared memory, which gives their ranks,
-//      writes the partition of every selected term and the reference norms |R_p| (one CTA,
-//      k_band_place; each partition summed by one thread in rank order, in double).
-// A band of more than kBandMax terms (a tie group larger than the buffer) is reported in the
-// status word; the caller then selects on the host.
+//   2. turns the histogram into above[v] = #{df > v} and finds start, L and the band (one
+//      CTA, k_sel_band); the terms of df v hold the ranks [above[v], above[v - 1]),
+//   3. places each band term in its df group's rank range (k_band_group, order within a
+//      group arbitrary),
+//   4. sorts each group by id (one CTA per group, k_group_sort), which gives every band
+//      term its rank, and writes the partition of every selected term and its reference
+//      weight by selection position,
+//   5. sums the reference norms |R_p| (one CTA, k_ref_norms; each partition summed by one
+//      thread in rank order, in double).
+// A band of more than kBandMax terms is reported in the status word; the caller then selects
+// on the host.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <climits>
 
 #include "device.cuh"
@@ -25,20 +29,34 @@ namespace mrc {
 namespace {
 
 constexpr int kSelThreads = 1024;
-constexpr int kBandMax = 8192;  // band terms sorted in shared memory (64 KB of keys)
+constexpr int kBandMax = 8192;  // band terms (and selection positions) held on the device
+constexpr int kGroupThreads = 256;
 
 // Selection state (int64 words): [0] start, [1] L, [2] v_lo, [3] v_hi, [4] rank of the
 // band's first term, [5] band size, [6] status (0 ok, 1 band too large), [7] largest df.
 enum { kSsStart = 0, kSsL, kSsVlo, kSsVhi, kSsRank0, kSsBand, kSsStatus, kSsMaxdf, kSsWords = 8 };
 
-__global__ void k_df_hist(const int32_t* __restrict__ df, int32_t V, int32_t* __restrict__ hist,
-                          long long* __restrict__ state) {
-  const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  int32_t d = t < V ? df[t] : 0;
-  if (d > 0) atomicAdd(&hist[d], 1);
+__global__ void __launch_bounds__(1024) k_df_hist(const int32_t* __restrict__ df, int32_t V,
+                                                  int32_t* __restrict__ hist, long long* __restrict__ state) {
+  __shared__ int32_t s_max[32];
+  int32_t dmax = 0;
+  for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t - (int32_t)threadIdx.x < V; t += gridDim.x * blockDim.x) {
+    const int32_t d = t < V ? df[t] : 0;
+    // lanes of equal df add once (small df values are most of the vocabulary)
+    const unsigned same = __match_any_sync(kFull, d);
+    if (d > 0 && (threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&hist[d], __popc(same));
+    dmax = max(dmax, d);
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) d = max(d, __shfl_xor_sync(kFull, d, o));
-  if ((threadIdx.x & 31) == 0 && d > 0) atomicMax(&state[kSsMaxdf], (long long)d);
+  for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(kFull, dmax, o));
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = dmax;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    dmax = threadIdx.x < (blockDim.x >> 5) ? s_max[threadIdx.x] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(kFull, dmax, o));
+    if (threadIdx.x == 0 && dmax > 0) atomicMax(&state[kSsMaxdf], (long long)dmax);
+  }
 }
 
 // One CTA. above[v] = #{terms with df > v} for v in [0, maxdf]; then the selection and the
@@ -54,6 +72,7 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_sel_band(const int32_t* __re
   const int64_t per = (nv + kSelThreads - 1) / kSelThreads;
   const int64_t v_top = maxdf - (int64_t)threadIdx.x * per;  // this thread's largest value
   long long sum = 0;
+#pragma unroll 8
   for (int64_t q = 0; q < per; ++q) {
     const int64_t v = v_top - q;
     if (v >= 1) sum += hist[v];
@@ -98,10 +117,11 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_sel_band(const int32_t* __re
   }
   start = min(start, ranked);
   const int64_t end = min(start + L, ranked);
+#pragma unroll 4
   for (int64_t q = 0; q < per; ++q) {
     const int64_t v = v_top - q;
     if (v >= 1) {
-      const int64_t lo_rank = above[v], cnt = (int64_t)(v > 1 ? above[v - 1] : ranked) - above[v];
+      const int64_t lo_rank = above[v], cnt = (int64_t)above[v - 1] - above[v];
       if (cnt > 0 && lo_rank < end && lo_rank + cnt > start) {
         atomicMin(&s_lo, (long long)v);
         atomicMax(&s_hi, (long long)v);
@@ -110,72 +130,96 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_sel_band(const int32_t* __re
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    const long long v_lo = s_hi >= 0 ? s_lo : 1, v_hi = s_hi;  // v_hi = -1: empty selection
+    const long long rank0 = s_hi >= 0 ? above[s_hi] : 0;
+    const long long nb = s_hi >= 0 ? (long long)above[v_lo - 1] - rank0 : 0;
     state[kSsStart] = start;
     state[kSsL] = end - start;
-    state[kSsVlo] = s_hi >= 0 ? s_lo : 1;
-    state[kSsVhi] = s_hi;  // -1: empty selection
-    state[kSsRank0] = s_hi >= 0 ? above[s_hi] : 0;
-    state[kSsBand] = 0;
-    state[kSsStatus] = 0;
+    state[kSsVlo] = v_lo;
+    state[kSsVhi] = v_hi;
+    state[kSsRank0] = rank0;
+    state[kSsBand] = nb;
+    state[kSsStatus] = nb > kBandMax ? 1 : 0;
   }
 }
 
-__global__ void k_band_collect(const int32_t* __restrict__ df, int32_t V, long long* __restrict__ state,
-                               unsigned long long* __restrict__ keys) {
+// Each band term goes to a free slot of its df group's band range [above[d], above[d - 1]) -
+// rank0 (the group's histogram count is used up as the slot counter).
+__global__ void k_band_group(const int32_t* __restrict__ df, int32_t V, const int32_t* __restrict__ above,
+                             int32_t* __restrict__ hist, const long long* __restrict__ state,
+                             uint32_t* __restrict__ ids) {
   const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= V) return;
+  if (t >= V || state[kSsStatus] != 0) return;
   const int32_t d = df[t];
   if (d < state[kSsVlo] || d > state[kSsVhi]) return;
-  const long long at = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&state[kSsBand]), 1ull);
-  // ascending keys = df descending, then id ascending
-  if (at < kBandMax) keys[at] = ((unsigned long long)(0xFFFFFFFFu - (uint32_t)d) << 32) | (uint32_t)t;
+  const int32_t slot = atomicSub(&hist[d], 1) - 1;
+  ids[above[d] - state[kSsRank0] + slot] = (uint32_t)t;
 }
 
-// One CTA: sorts the band, writes the partition of each selected term (part holds -1 for
-// every term on entry) and the reference norms. idf NULL: count weighting (r = 1).
-__global__ void __launch_bounds__(kSelThreads) k_band_place(const unsigned long long* __restrict__ keys,
-                                                           long long* __restrict__ state, const float* __restrict__ idf,
-                                                           int32_t bf16, int32_t k, int32_t* __restrict__ part,
-                                                           double* __restrict__ rnorm, float* __restrict__ rinv) {
-  extern __shared__ unsigned long long sk[];  // [kBandMax]
-  const long long nb = state[kSsBand];
-  if (nb > kBandMax) {
-    if (threadIdx.x == 0) state[kSsStatus] = 1;
-    return;
-  }
-  int n2 = 1;
-  while (n2 < nb) n2 <<= 1;
-  for (int x = threadIdx.x; x < n2; x += kSelThreads) sk[x] = x < nb ? keys[x] : ~0ull;
-  __syncthreads();
-  for (int kk = 2; kk <= n2; kk <<= 1) {
-    for (int j = kk >> 1; j > 0; j >>= 1) {
-      for (int x = threadIdx.x; x < n2; x += kSelThreads) {
-        const int y = x ^ j;
-        if (y > x) {
-          const unsigned long long a = sk[x], b = sk[y];
-          if ((a > b) == ((x & kk) == 0)) {
-            sk[x] = b;
-            sk[y] = a;
+// One CTA per df group of the band (grid-stride): sorts the group's ids ascending in shared
+// memory (bitonic), which completes the ranking; writes the partition of each selected term
+// (part holds -1 for every term on entry) and its reference weight at its selection
+// position. idf NULL: count weighting (r = 1).
+__global__ void __launch_bounds__(kGroupThreads) k_group_sort(const int32_t* __restrict__ above, long long* __restrict__ state,
+                                                            const uint32_t* __restrict__ ids, const float* __restrict__ idf,
+                                                            int32_t bf16, int32_t k, int32_t* __restrict__ part,
+                                                            float* __restrict__ rsel) {
+  extern __shared__ uint32_t sid[];  // [next power of two >= group size]
+  if (state[kSsStatus] != 0 || state[kSsVhi] < 0) return;
+  const long long v_lo = state[kSsVlo], v_hi = state[kSsVhi], rank0 = state[kSsRank0];
+  const long long start = state[kSsStart], L = state[kSsL];
+  for (long long v = v_lo + blockIdx.x; v <= v_hi; v += gridDim.x) {
+    const int32_t g0 = above[v], m = above[v - 1] - g0;  // ranks [g0, g0 + m)
+    if (m <= 0 || g0 + m <= start || g0 >= start + L) continue;  // block-uniform
+    int n2 = 1;
+    while (n2 < m) n2 <<= 1;
+    const uint32_t* gi = ids + (g0 - rank0);
+    __syncthreads();  // the previous group's reads of sid are done
+    for (int x = threadIdx.x; x < n2; x += kGroupThreads) sid[x] = x < m ? gi[x] : 0xFFFFFFFFu;
+    __syncthreads();
+    for (int kk = 2; kk <= n2; kk <<= 1) {
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int x = threadIdx.x; x < n2; x += kGroupThreads) {
+          const int y = x ^ j;
+          if (y > x) {
+            const uint32_t a = sid[x], b = sid[y];
+            if ((a > b) == ((x & kk) == 0)) {
+              sid[x] = b;
+              sid[y] = a;
+            }
           }
         }
+        __syncthreads();
       }
-      __syncthreads();
+    }
+    for (int x = threadIdx.x; x < m; x += kGroupThreads) {
+      const long long pos = (long long)g0 + x - start;  // selection position
+      if (pos >= 0 && pos < L) {
+        const uint32_t t = sid[x];
+        part[t] = (int32_t)(((pos + 1) * k - 1) / L);
+        float r = 1.f;
+        if (idf) r = bf16 ? __bfloat162float(__float2bfloat16_rn(idf[t])) : idf[t];
+        rsel[pos] = r;
+      }
     }
   }
-  const long long start = state[kSsStart], L = state[kSsL], rank0 = state[kSsRank0];
-  // band position x holds rank rank0 + x; selection position = rank - start
-  for (int x = threadIdx.x; x < nb; x += kSelThreads) {
-    const long long pos = rank0 + x - start;
-    if (pos >= 0 && pos < L) part[(uint32_t)sk[x]] = (int32_t)(((pos + 1) * k - 1) / L);
-  }
-  // partition q: selection positions [floor(qL/k), floor((q+1)L/k)), summed in rank order
+}
+
+// One CTA: partition q holds selection positions [floor(qL/k), floor((q+1)L/k)); |R_q|^2 is
+// summed by one thread in rank order, in double.
+__global__ void __launch_bounds__(kSelThreads) k_ref_norms(const long long* __restrict__ state,
+                                                         const float* __restrict__ rsel, int32_t k,
+                                                         double* __restrict__ rnorm, float* __restrict__ rinv) {
+  __shared__ float sr[kBandMax];
+  if (state[kSsStatus] != 0) return;
+  const long long L = state[kSsVhi] < 0 ? 0 : state[kSsL];
+  for (long long x = threadIdx.x; x < L; x += kSelThreads) sr[x] = rsel[x];
+  __syncthreads();
   for (int q = threadIdx.x; q < k; q += kSelThreads) {
     double s = 0.0;
     const long long p0 = q * L / k, p1 = (q + 1) * L / k;
     for (long long pos = p0; pos < p1; ++pos) {
-      const uint32_t t = (uint32_t)sk[pos + start - rank0];
-      double r = 1.0;
-      if (idf) r = bf16 ? (double)__bfloat162float(__float2bfloat16_rn(idf[t])) : (double)idf[t];
+      const double r = (double)sr[pos];
       s += r * r;
     }
     const double nr = sqrt(s);
@@ -193,6 +237,9 @@ cudaError_t launch_select_region(mrc_ctx* ctx, const int32_t* df, int32_t V, int
                                  int32_t* above, long long* state, unsigned long long* keys, int32_t* part,
                                  double* rnorm, float* rinv) {
   if (V <= 0 || k <= 0) return cudaErrorInvalidValue;
+  // keys: 64 KB of scratch = band ids [kBandMax] + reference weights by position [kBandMax]
+  uint32_t* ids = reinterpret_cast<uint32_t*>(keys);
+  float* rsel = reinterpret_cast<float*>(ids + kBandMax);
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * ((size_t)n_docs + 2), ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(state, 0, sizeof(long long) * kSsWords, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(part, 0xFF, sizeof(int32_t) * (size_t)V, ctx->stream);
@@ -200,20 +247,26 @@ cudaError_t launch_select_region(mrc_ctx* ctx, const int32_t* df, int32_t V, int
   const unsigned blocks = (unsigned)(((int64_t)V + 255) / 256);
   {
     KernelTimer kt(ctx, "select_hist", 4.0 * V);
-    k_df_hist<<<blocks, 256, 0, ctx->stream>>>(df, V, hist, state);
+    const int64_t hb = std::min<int64_t>(((int64_t)V + 1023) / 1024, 2 * (int64_t)ctx->num_sms);
+    k_df_hist<<<(unsigned)hb, 1024, 0, ctx->stream>>>(df, V, hist, state);
   }
   {
     KernelTimer kt(ctx, "select_band", 8.0 * (double)n_docs);
     k_sel_band<<<1, kSelThreads, 0, ctx->stream>>>(hist, above, n_docs, L, region_start, state);
   }
   {
-    KernelTimer kt(ctx, "select_collect", 4.0 * V);
-    k_band_collect<<<blocks, 256, 0, ctx->stream>>>(df, V, state, keys);
+    KernelTimer kt(ctx, "select_group", 4.0 * V);
+    k_band_group<<<blocks, 256, 0, ctx->stream>>>(df, V, above, hist, state, ids);
   }
-  const size_t smem = sizeof(unsigned long long) * kBandMax;
-  if (resident_ctas(k_band_place, kSelThreads, smem) <= 0) return cudaErrorInvalidConfiguration;
-  KernelTimer kt(ctx, "select_place");
-  k_band_place<<<1, kSelThreads, smem, ctx->stream>>>(keys, state, idf, bf16, k, part, rnorm, rinv);
+  const size_t smem = sizeof(uint32_t) * kBandMax;
+  if (resident_ctas(k_group_sort, kGroupThreads, smem) <= 0) return cudaErrorInvalidConfiguration;
+  {
+    KernelTimer kt(ctx, "select_sort");
+    k_group_sort<<<(unsigned)(2 * ctx->num_sms), kGroupThreads, smem, ctx->stream>>>(above, state, ids, idf, bf16,
+                                                                                       k, part, rsel);
+  }
+  KernelTimer kt(ctx, "select_norms");
+  k_ref_norms<<<1, kSelThreads, 0, ctx->stream>>>(state, rsel, k, rnorm, rinv);
   return cudaGetLastError();
 }
 

@@ -361,11 +361,10 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_cosine_tail(
     const __half* __restrict__ hlo, int32_t kd, float tau, float delta, mrc_pair* pairs,
     unsigned long long* count, int64_t capacity, int32_t window, int32_t acc_len, int32_t n_windows, int64_t n_items,
     int32_t paired, unsigned long long* next_item) {
-  extern __shared__ int32_t acc[];    // [acc_len] accumulators, then the term tables
-  int32_t* t_st = acc + acc_len;      // [kTermBatch] posting index - flattened start, per term
-  int32_t* t_ex = t_st + kTermBatch;  // [kTermBatch + 1] flattened start of each term
-  float* t_w = reinterpret_cast<float*>(t_ex + kTermBatch + 1);  // [kTermBatch] 2^30 x the row's weight
-  int32_t* t_sh = reinterpret_cast<int32_t*>(t_w + kTermBatch);   // [kTermBatch] accumulator shift
+  extern __shared__ int32_t acc[];  // [acc_len] accumulators, then the term table
+  // per term of the batch, one 16-byte entry: x = end of its flattened range, y = posting
+  // index - flattened position, z = 2^30 x the row's weight (float bits), w = accumulator shift
+  int4* t_ent = reinterpret_cast<int4*>(acc + acc_len);  // [kTermBatch]
   __shared__ int32_t t_scan[33];
   __shared__ long long s_item[2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -416,27 +415,26 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_cosine_tail(
       int32_t total;
       const int32_t ex = cta_excl_scan(cnt, t_scan, &total);  // synchronises the CTA
       const int32_t nterm = min(kTermBatch, nt - b0);
-      t_st[threadIdx.x] = st - ex;  // posting index = t_st[term] + flattened position
-      t_ex[threadIdx.x] = ex;
-      t_w[threadIdx.x] = wi * kTailFix;
-      t_sh[threadIdx.x] = sh;
-      if (threadIdx.x == 0) t_ex[nterm] = total;
+      // posting index = y + flattened position
+      t_ent[threadIdx.x] = make_int4(ex + cnt, st - ex, __float_as_int(wi * kTailFix), sh);
       __syncthreads();
-      // the batch's postings flattened into [0, total); each warp takes an equal slice. A
-      // lane finds the term of its first position by binary search (the last term whose
-      // start <= position is the non-empty one) and then only moves forward.
+      // the batch's postings flattened into [0, total); each warp takes an equal slice. The
+      // term of position f is the first whose range ends after f (empty terms end where they
+      // start, so they are passed over): a lane finds it by binary search for its first
+      // position and then only moves forward.
       const int32_t s0 = (int32_t)((int64_t)total * warp / kTailWarps);
       const int32_t s1 = (int32_t)((int64_t)total * (warp + 1) / kTailWarps);
       int32_t own = 0;
       {
         const int32_t f = s0 + lane;
-        int32_t a = 0, c = nterm;  // t_ex[a] <= f < t_ex[c]
-        while (c - a > 1) {
+        int32_t a = 0, c = nterm - 1;  // end[c] > f for f < total; find the first such term
+        while (a < c) {
           const int32_t m = (a + c) >> 1;
-          if (t_ex[m] <= f) a = m; else c = m;
+          if (t_ent[m].x <= f) a = m + 1; else c = m;
         }
         own = a;
       }
+      int32_t end = t_ent[own].x;  // end of the current term's range
       for (int32_t f0 = s0; f0 < s1; f0 += 32 * kWalkChunks) {
         int2 pv[kWalkChunks];
         float wv[kWalkChunks];
@@ -448,10 +446,11 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_cosine_tail(
           wv[u] = 0.f;
           shv[u] = 0;
           if (f < s1) {
-            while (t_ex[own + 1] <= f) ++own;
-            pv[u] = spost[t_st[own] + f];  // (document, weight) of the posting
-            wv[u] = t_w[own];
-            shv[u] = t_sh[own];
+            while (end <= f) end = t_ent[++own].x;
+            const int4 te = t_ent[own];
+            pv[u] = spost[te.y + f];  // (document, weight) of the posting
+            wv[u] = __int_as_float(te.z);
+            shv[u] = te.w;
           }
         }
         // with one window per row every posting after a segment's row lies in its columns
@@ -624,7 +623,7 @@ cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t
   const int32_t paired = n_windows == 1 ? 1 : 0;
   const int64_t n_items = paired ? (n + 1) / 2 : n * n_windows;
   const int32_t acc_len = paired ? window + 32 : window;
-  const size_t smem = sizeof(int32_t) * ((size_t)acc_len + 4 * kTermBatch + 1);
+  const size_t smem = sizeof(int32_t) * (size_t)acc_len + sizeof(int4) * kTermBatch;
   const int per_sm = resident_ctas(k_cosine_tail, kTailThreads, smem);
   if (per_sm <= 0) return cudaErrorInvalidConfiguration;
   int64_t grid = (int64_t)ctx->num_sms * per_sm;
