@@ -73,6 +73,7 @@ struct GemmParams {
   __half* store16;
   int64_t ld;
   int32_t* err;
+  int32_t row_rr;  // resident kernel, triangle: whole row blocks dealt round-robin (see TileSeq)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -123,6 +124,25 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
       : "memory");
 }
 
+// The same copy written to the same shared-memory offset of every CTA in cta_mask (of this
+// cluster); each destination's barrier at bar's offset receives the bytes it gets.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar,
+                                               uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(cta_mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
 // groups 1024 bytes apart (SBO), descriptor version 1.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -153,6 +173,13 @@ __device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
         "l"(a), "l"(b), "r"(id), "r"(acc));
   }
+}
+// Arrives on the barrier at bar's offset in every CTA of cta_mask once this CTA's MMAs so far
+// are done.
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t cta_mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
+                   "r"(smem_u32(bar)), "h"(cta_mask)
+               : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -290,7 +317,13 @@ __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)
   __syncwarp();
 }
 
-template <int FMT>
+// MC = 1: launched as clusters of two CTAs that take the two 128-row halves of the same
+// 256-column super tile (consecutive tile indices), so they need the same B tile: each CTA
+// loads one 128-row half of it and multicasts it to both, halving B's L2-to-SM traffic. A
+// stage of either CTA may be refilled only when both CTAs' MMAs are done with it (each MMA
+// commit arrives on both CTAs' empty barrier), and both CTAs walk every tile of their pair
+// (a half beyond the last row is computed on zero rows and masked).
+template <int FMT, int MC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_compare(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
                    const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1, GemmParams p) {
@@ -319,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], MC ? 2 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -338,6 +371,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const uint32_t rank = MC ? cluster_rank() : 0u;
+  if (MC) cluster_sync();  // the peer's barriers are initialised before any multicast reaches them
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -348,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
         int64_t bi, bj;
-        if (!decode_tile<BN>(p, t, bi, bj)) continue;
+        if (!decode_tile<BN>(p, t, bi, bj) && !MC) continue;
         for (int kb = 0; kb < p.kblocks; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.err)) {
             ok = false;
@@ -359,7 +394,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           armed[stage] = (int32_t)phase;
           const int x = kb * (FMT == OP_E4M3 ? kRowBytes : kRowBytes / 2);
           tma_load_2d(sbase, &tA0, x, (int)(bi * kBM), &full[stage]);
-          tma_load_2d(sbase + A_BYTES, &tB0, x, (int)(bj * BN), &full[stage]);
+          if (MC)
+            tma_load_2d_mc(sbase + A_BYTES + rank * (B_BYTES / 2), &tB0, x, (int)(bj * BN + rank * (BN / 2)),
+                           &full[stage], (uint16_t)0x3);
+          else
+            tma_load_2d(sbase + A_BYTES, &tB0, x, (int)(bj * BN), &full[stage]);
           if (C::NOPS == 2) {
             tma_load_2d(sbase + A_BYTES + B_BYTES, &tA1, x, (int)(bi * kBM), &full[stage]);
             tma_load_2d(sbase + 2 * A_BYTES + B_BYTES, &tB1, x, (int)(bj * BN), &full[stage]);
@@ -387,7 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t id = idesc(BN);
       for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
         int64_t bi, bj;
-        if (!decode_tile<BN>(p, t, bi, bj)) continue;
+        if (!decode_tile<BN>(p, t, bi, bj) && !MC) continue;
         const uint32_t ab = (uint32_t)(it & 1);
         if (!mbar_wait(&acc_empty[ab], (uint32_t)((it >> 1) & 1) ^ 1u, abort_flag, p.err)) break;
         tc_fence_after();
@@ -412,7 +451,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               umma<FMT>(d1, sdesc(sa1 + kk * 32), bd, id, 1u);
             }
           }
-          umma_commit(&empty[stage]);
+          if (MC)
+            umma_commit_mc(&empty[stage], (uint16_t)0x3);
+          else
+            umma_commit(&empty[stage]);
           if (++stage == C::STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -434,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int64_t it = 0;
     for (int64_t t = blockIdx.x; t < p.n_tiles; t += gridDim.x) {
       int64_t bi, bj;
-      if (!decode_tile<BN>(p, t, bi, bj)) continue;
+      if (!decode_tile<BN>(p, t, bi, bj) && !MC) continue;
       const uint32_t ab = (uint32_t)(it & 1);
       int ok = 1;
       if (lane == 0) ok = mbar_wait(&acc_full[ab], (uint32_t)((it >> 1) & 1), abort_flag, p.err) ? 1 : 0;
@@ -520,6 +562,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
+  if (MC) cluster_sync();  // no CTA leaves while its peer may still multicast into it
 }
 
 // ---------------------------------------------------------------------------------------
@@ -570,6 +613,40 @@ __device__ __forceinline__ bool decode_rowmajor(const GemmParams& p, int64_t t64
   bi = (int64_t)I * H + h;
   return bi * kBM < p.na;
 }
+
+// The tiles of one CTA of the resident kernel, in the order all its roles walk them.
+// Contiguous mode: tiles [t_begin, t_end) of the row-major order (even shares; used when the
+// streamed operand fits in L2). Round-robin mode (triangle with a streamed operand larger
+// than L2 can hold): CTA c of G takes whole row blocks, kG + c in even rounds k and
+// kG + G - 1 - c in odd rounds (two rounds give every CTA the same work), each swept from its
+// diagonal column block up. The CTAs then sweep the column blocks together, a few dozen
+// blocks apart, so a streamed tile is read from HBM once and served to the other CTAs by L2
+// instead of every CTA streaming the whole operand at its own position.
+template <int BN>
+struct TileSeq {
+  int64_t t, t_end, k, bi, bj;
+  __device__ TileSeq(int64_t tb, int64_t te) : t(tb), t_end(te), k(-1), bi(0), bj(0) {}
+  __device__ __forceinline__ bool next(const GemmParams& p, int64_t& obi, int64_t& obj) {
+    if (!p.row_rr) {
+      while (t < t_end) {
+        const int64_t tt = t++;
+        if (decode_rowmajor<BN>(p, tt, obi, obj)) return true;
+      }
+      return false;
+    }
+    constexpr int H = BN / kBM;
+    while (k < 0 || bj >= p.super_rows) {
+      ++k;
+      const int64_t G = gridDim.x, c = blockIdx.x;
+      bi = k * G + ((k & 1) ? G - 1 - c : c);
+      if (bi >= p.tiles_m) return false;
+      bj = bi / H;
+    }
+    obi = bi;
+    obj = bj++;
+    return true;
+  }
+};
 
 template <int FMT, int RB, int BN>
 __global__ void __launch_bounds__(kResThreads, 1)
@@ -636,9 +713,9 @@ __global__ void __launch_bounds__(kResThreads, 1)
       for (int s = 0; s < kResStagesB; ++s) b_armed[s] = -1;
       uint32_t stage = 0, phase = 0, a_use = 0;
       int64_t last_bi = -1;
-      for (int64_t t = t_begin; t < t_end; ++t) {
-        int64_t bi, bj;
-        if (!decode_rowmajor<BN>(p, t, bi, bj)) continue;
+      TileSeq<BN> seq(t_begin, t_end);
+      int64_t bi, bj;
+      while (seq.next(p, bi, bj)) {
         if (bi != last_bi) {
           const uint32_t ab = a_use & 1u;
           if (!mbar_wait(&a_empty[ab], ((a_use >> 1) & 1u) ^ 1u, abort_flag, p.err)) break;
@@ -681,9 +758,9 @@ __global__ void __launch_bounds__(kResThreads, 1)
       const uint32_t id = idesc(BN);
       uint32_t stage = 0, phase = 0, a_use = 0, ab_a = 0;
       int64_t last_bi = -1, it = 0;
-      for (int64_t t = t_begin; t < t_end; ++t) {
-        int64_t bi, bj;
-        if (!decode_rowmajor<BN>(p, t, bi, bj)) continue;
+      TileSeq<BN> seq(t_begin, t_end);
+      int64_t bi, bj;
+      while (seq.next(p, bi, bj)) {
         if (bi != last_bi) {
           if (last_bi >= 0) umma_commit(&a_empty[ab_a]);  // previous row's MMAs release its A buffer
           ab_a = a_use & 1u;
@@ -727,9 +804,9 @@ __global__ void __launch_bounds__(kResThreads, 1)
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
     int64_t it = 0;
-    for (int64_t t = t_begin; t < t_end; ++t) {
-      int64_t bi, bj;
-      if (!decode_rowmajor<BN>(p, t, bi, bj)) continue;
+    TileSeq<BN> seq(t_begin, t_end);
+    int64_t bi, bj;
+    while (seq.next(p, bi, bj)) {
       const uint32_t ab = (uint32_t)(it & 1);
       int ok = 1;
       if (lane == 0) ok = mbar_wait(&acc_full[ab], (uint32_t)((it >> 1) & 1), abort_flag, p.err) ? 1 : 0;
@@ -858,6 +935,10 @@ cudaError_t run_gemm_resident(mrc_ctx* ctx, const GemmArgs& g) {
   p.count = g.count;
   p.capacity = g.capacity;
   p.err = g.err;
+  // round-robin rows when the streamed operand would not stay in L2 (over a quarter of it)
+  // and there are at least two rounds of row blocks to balance
+  p.row_rr = g.triangle && (double)C::NOPS * (double)g.nb * g.kbytes > 32.0 * 1024 * 1024 &&
+             p.tiles_m >= 2 * (int64_t)ctx->num_sms;
   // at least 120 KB, so that one CTA (which owns all 512 TMEM columns) runs per SM
   const size_t smem =
       std::max<size_t>(1024 + 2 * (size_t)C::NOPS * kBM * RB + (size_t)kResStagesB * C::NOPS * BN * RB + 256 +
@@ -884,8 +965,11 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   using C = Cfg<FMT>;
   constexpr int BN = C::BN;
   const bool fp8 = FMT == OP_E4M3;
+  // clusters of two with B multicast for the 256-column formats (see k_gemm_compare)
+  const bool mc = C::NOPS == 1 && BN == 2 * kBM && ctx->num_sms >= 2;
   CUtensorMap tA0, tA1, tB0, tB1;
-  if (!make_map(&tA0, g.a_hi, g.na, g.kbytes, kBM, fp8) || !make_map(&tB0, g.b_hi, g.nb, g.kbytes, BN, fp8))
+  if (!make_map(&tA0, g.a_hi, g.na, g.kbytes, kBM, fp8) ||
+      !make_map(&tB0, g.b_hi, g.nb, g.kbytes, mc ? BN / 2 : BN, fp8))
     return cudaErrorInvalidValue;
   if (C::NOPS == 2) {
     if (!make_map(&tA1, g.a_lo, g.na, g.kbytes, kBM, fp8) || !make_map(&tB1, g.b_lo, g.nb, g.kbytes, BN, fp8))
@@ -900,6 +984,7 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   p.kblocks = g.kbytes / kRowBytes;
   p.triangle = g.triangle;
   p.tiles_m = (g.na + kBM - 1) / kBM;
+  if (mc) p.tiles_m += p.tiles_m & 1;  // row blocks in pairs (a pair's second half may be all padding)
   p.tiles_n = (g.nb + BN - 1) / BN;
   p.super_rows = (g.na + BN - 1) / BN;
   p.n_tiles = g.triangle ? p.super_rows * (p.super_rows + 1) / 2 * (BN / kBM) : p.tiles_m * p.tiles_n;
@@ -918,9 +1003,33 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   p.err = g.err;
   const size_t smem = 1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256 + 4 * (32 * 33 + 32) * 4 +
                       4 * kPairBuf * sizeof(mrc_pair);
-  if (resident_ctas(k_gemm_compare<FMT>, kThreads, smem) <= 0) return cudaErrorInvalidConfiguration;
+  if (resident_ctas(k_gemm_compare<FMT, 0>, kThreads, smem) <= 0 ||
+      (mc && resident_ctas(k_gemm_compare<FMT, 1>, kThreads, smem) <= 0))
+    return cudaErrorInvalidConfiguration;
   int64_t grid = ctx->num_sms;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  if (mc) {
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // as many pairs as can be resident at once (a GPC with an odd SM count leaves one SM out)
+    cfg.gridDim = dim3((unsigned)(ctx->num_sms & ~1));
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_gemm_compare<FMT, 1>, &cfg) != cudaSuccess || clusters <= 0) {
+      cudaGetLastError();
+      return cudaErrorInvalidConfiguration;
+    }
+    grid = std::min<int64_t>(grid, 2 * (int64_t)clusters);
+  }
   if (p.n_tiles < grid) grid = p.n_tiles;
+  if (mc) grid &= ~int64_t(1);  // whole clusters; n_tiles is even, so both CTAs of a pair see the same tiles
   if (grid <= 0) return cudaSuccess;
   // algorithmic work: 2 K flops per evaluated pair (the triangle counts i < j only)
   const double k_elems = (double)g.kbytes / (fp8 ? 1.0 : 2.0);
@@ -933,8 +1042,15 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   const double bytes = (double)C::NOPS * (double)(g.na + (g.triangle ? 0 : g.nb)) * g.kbytes;
   cudaEvent_t ev = nullptr;
   timing_begin(ctx, name, bytes, flops, &ev);
-  k_gemm_compare<FMT><<<(unsigned)grid, kThreads, smem, ctx->stream>>>(tA0, tA1, tB0, tB1, p);
+  cudaError_t e = cudaSuccess;
+  if (mc) {
+    cfg.gridDim = dim3((unsigned)grid);
+    e = cudaLaunchKernelEx(&cfg, k_gemm_compare<FMT, 1>, tA0, tA1, tB0, tB1, p);
+  } else {
+    k_gemm_compare<FMT, 0><<<(unsigned)grid, kThreads, smem, ctx->stream>>>(tA0, tA1, tB0, tB1, p);
+  }
   timing_end(ctx, ev);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

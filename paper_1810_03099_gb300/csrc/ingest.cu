@@ -161,8 +161,9 @@ struct Acc {
 };
 
 // Per-term table values a mode needs besides the term's count: SIG (reference weight, reference
-// partition), DENSE (idf or 1, head column / -2 tail / -1), DFN (idf or 1). Loading them is the
-// only global-memory read per term, so the warp path gathers them for a whole document at once.
+// partition), DENSE (idf or 1, head column / -1 / for a tail term -3 - its posting slot), DFN
+// (idf or 1). Loading them is the only global-memory access per term, so the warp path gathers
+// them for a whole document at once and the CTA path one chunk ahead.
 struct TermAux {
   float w;
   int32_t code;
@@ -178,6 +179,10 @@ __device__ __forceinline__ TermAux load_aux(const IngestParams& p, uint32_t key)
   } else if (MODE == kDENSE) {
     if (p.dense.idf) x.w = __ldg(p.dense.idf + key);
     x.code = __ldg(p.dense.colmap + key);
+    if (x.code == -2) {  // a tail term: claim its posting slot now (slots < 2^31 - 64)
+      const int64_t pos = p.dense.tail_start[key] + atomicAdd(&p.dense.tail_fill[key], 1);
+      x.code = -3 - (int32_t)pos;
+    }
   } else if (MODE == kDFN) {
     if (p.norm_idf) x.w = __ldg(p.norm_idf + key);
   }
@@ -233,8 +238,8 @@ __device__ __forceinline__ void chunk(const IngestParams& p, uint32_t key, uint3
     const int64_t at = doc * (int64_t)p.dense.kd + code;
     reinterpret_cast<__half*>(p.dense.head_hi)[at] = hi;
     reinterpret_cast<__half*>(p.dense.head_lo)[at] = lo;
-  } else if (code == -2) {
-    const int64_t pos = p.dense.tail_start[key] + atomicAdd(&p.dense.tail_fill[key], 1);
+  } else if (code <= -3) {
+    const int64_t pos = -3 - (int64_t)code;
     const int32_t r = atomicAdd(row_cnt_s, 1);
     p.dense.post_doc[pos] = (int32_t)doc;
     p.dense.post_w[pos] = u;

@@ -233,7 +233,8 @@ def cached_corpus(name: str, cache_dir: str | None = None, **kw) -> Corpus:
         spec = spec.with_(**kw)
     cache_dir = cache_dir or os.environ.get("MRC_CORPUS_CACHE",
                                             os.path.join(os.path.dirname(__file__), "..", "_build", "corpora"))
-    key = f"{spec.name}_{spec.n_docs}_{spec.seed}_{spec.vocab}_{spec.length_law}_{spec.dup_frac}.npz"
+    key = (f"{spec.name}_{spec.n_docs}_{spec.seed}_{spec.vocab}_{spec.length_law}_{spec.length_median}_"
+           f"{spec.length_sigma}_{spec.dup_frac}.npz")
     path = os.path.join(cache_dir, key)
     if os.path.exists(path):
         z = np.load(path)

@@ -94,3 +94,43 @@ def test_fullsize_exact_cosine(setup):
         assert abs(s - orc.cosine_pair(ref.row_ptr, ref.terms, ref.w, i, j)) <= 1e-5
     _row_check(got, setup["rows"], ref.S.shape[0],
                lambda i, j: orc.cosine_pair(ref.row_ptr, ref.terms, ref.w, i, j), TAU)
+
+
+def test_large_allpairs_signature_match():
+    """300,000 documents (FP32 form, k = 64): the fp16 compare operand (38 MB) is larger than the
+    compare kernel keeps to one L2-resident sweep, so row blocks are dealt to the CTAs round
+    robin. Sampled rows (spread over the whole triangle, including the last row blocks) are
+    scored by the oracle against every later document; every emitted pair of a sample is
+    checked against the oracle's cosine."""
+    torch = cuda_or_skip()
+    from paper_1810_03099_gb300 import mrc
+    c = synth.cached_corpus("precision", n_docs=300_000, length_median=150.0)
+    orc = Oracle()
+    ref = build_index(c.offsets, c.tokens, c.vocab, Params(k=K, tau=TAU), orc)
+    n = ref.S.shape[0]
+    with mrc.Context() as ctx:
+        idx = mrc.mrc_build_index(ctx, torch.from_numpy(c.offsets).cuda(), torch.from_numpy(c.tokens).cuda(), c.vocab,
+                                  mrc.params_default(k=K, tau=TAU))
+        buf, total = mrc.mrc_match(ctx, idx, None, TAU, capacity=1 << 24)
+        got = mrc.pairs_to_numpy(buf)
+        idx.free()
+    assert total == got.shape[0] > 0
+    rng = np.random.Generator(np.random.PCG64(78))
+    rows = np.unique(np.concatenate([rng.choice(n - 1, 24, replace=False), [0, 1, n - 2, n - 3, n - 129, n - 300]]))
+    by_row, rowset = {}, set(rows.tolist())
+    for i, j, s in zip(got["i"].tolist(), got["j"].tolist(), got["score"].tolist()):
+        if i in rowset:
+            by_row.setdefault(i, {})[j] = s
+    for i in rows.tolist():
+        _, _, pj, ps = orc.sig_match(ref.S[i:i + 1], ref.S[i + 1:], TAU - 1e-5)
+        want = {i + 1 + int(j): float(s) for j, s in zip(pj, ps)}
+        have = by_row.get(i, {})
+        for j, s in want.items():
+            if j not in have:
+                assert abs(s - TAU) <= 1e-5, (i, j, s)
+        for j, s in have.items():
+            assert j in want, (i, j, s)
+            assert abs(s - want[j]) <= 1e-5, (i, j, s, want[j])
+    for x in rng.choice(got.shape[0], min(2000, got.shape[0]), replace=False).tolist():
+        i, j, s = int(got["i"][x]), int(got["j"][x]), float(got["score"][x])
+        assert i < j and abs(s - orc.cos_dense(ref.S[i], ref.S[j])) <= 1e-5
