@@ -37,13 +37,11 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the news20 step, valid only while the kernel's source file is unchanged since the capture.
-NCU_TRAFFIC = {
-    "cosine_tail": ("paper_1810_03099_gb300/csrc/tail.cu",
-                    "574ac818feffa43489d8a900a42dacf90426125ad2ba9489d30a6eb4cf653093", 415944960),
-    "gemm_f16_store": ("paper_1810_03099_gb300/csrc/compare_tc.cu",
-                       "86febfa900da6472714ddbacea36b2f5c93d9f7fff104bd1e6083945317581f7", 351744768),
-}
+NCU_TRAFFIC = {}
 KERNEL_NOTES = {
+    "gemm_f16_bound": "exact-cosine head GEMM with the bound epilogue: 2 kd flops per pair of the triangle "
+                      "(kd = 1024 head columns); candidates where head + tn_i tn_j >= tau - delta'",
+    "cosine_verify": "exact scores of the bound-pruned candidates (a few tens of thousands on news20)",
     "cosine_tail": "algorithmic bytes = the fp16 head scores of the upper triangle; the postings it also walks "
                    "are L2-resident. ncu: issue-active 66%, l1tex 53%: instruction/latency-bound, not HBM-bound",
     "gemm_f16_store": "2 kd flops per pair of the triangle (kd = 1024 head columns); tensor pipe 60% active "

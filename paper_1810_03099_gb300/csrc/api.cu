@@ -498,14 +498,24 @@ SigOut index_sig_out(mrc_index* x) {
 // Copies device pairs to a host destination (when `pairs` is host memory).
 // Ends a pair-producing call with one synchronisation: reads the pair count (and the call's
 // error word, when given; an error takes precedence), then copies host-side results.
+// With d_cand (an internal candidate count of capacity cand_cap), that count is read in the
+// same synchronisation; when it overflowed, *overflow is set and nothing is copied (the caller
+// takes its exhaustive path).
 mrc_status finish_pairs(mrc_ctx* ctx, mrc_pair* user, mrc_pair* dev, unsigned long long* d_count, int64_t capacity,
-                        int64_t* n_pairs, int32_t* d_err = nullptr) {
+                        int64_t* n_pairs, int32_t* d_err = nullptr, const unsigned long long* d_cand = nullptr,
+                        int64_t cand_cap = 0, bool* overflow = nullptr) {
   unsigned long long* hc = (unsigned long long*)ctx->pinned;
   int32_t* he = (int32_t*)((char*)ctx->pinned + 256);
   cudaError_t e = cudaMemcpyAsync(hc, d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess && d_cand)
+    e = cudaMemcpyAsync(hc + 1, d_cand, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess && d_err) e = cudaMemcpyAsync(he, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "reading pair count");
+  if (d_cand && hc[1] > (unsigned long long)cand_cap) {
+    *overflow = true;
+    return MRC_OK;
+  }
   if (d_err) {
     const mrc_status st = err_status(ctx, *he);
     if (st != MRC_OK) return st;
@@ -918,27 +928,15 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   if (n_post >= (1ll << 31) - 64)
     return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more than 2^31 tail postings");
   const int64_t ldh = (N + 7) / 8 * 8;
-  if ((double)N * (double)ldh * 2.0 > 64e9)
-    return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more documents than the 64 GB score buffer allows");
-
-  int32_t* d_pdoc = (int32_t*)ws_get(ctx, "cos.pdoc", sizeof(int32_t) * (size_t)std::max<int64_t>(n_post, 1), &st);
-  float* d_pw = (float*)ws_get(ctx, "cos.pw", sizeof(float) * (size_t)std::max<int64_t>(n_post, 1), &st);
-  int32_t* d_pr = (int32_t*)ws_get(ctx, "cos.pr", sizeof(int32_t) * (size_t)std::max<int64_t>(n_post, 1), &st);
-  void* d_spost = ws_get(ctx, "cos.spost", 8 * (size_t)std::max<int64_t>(n_post, 1), &st);
-  void* d_rwalk = ws_get(ctx, "cos.rwalk", 8 * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
   int32_t* d_rcnt = (int32_t*)ws_get(ctx, "cos.rcnt", sizeof(int32_t) * (size_t)N, &st);
   float* d_rw = (float*)ws_get(ctx, "cos.rw", sizeof(float) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
   void* d_hhi = ws_get(ctx, "cos.hhi", 2 * (size_t)N * kd, &st);
   void* d_hlo = ws_get(ctx, "cos.hlo", 2 * (size_t)N * kd, &st);
-  void* d_H = ws_get(ctx, "cos.H16", 2 * (size_t)N * ldh, &st);
-  unsigned long long* d_next = (unsigned long long*)ws_get(ctx, "cos.next", sizeof(unsigned long long), &st);
   if (st != MRC_OK) return st;
-  e = cudaMemsetAsync(d_tfill, 0, sizeof(int32_t) * V, ctx->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_hhi, 0, 2 * (size_t)N * kd, ctx->stream);
+  e = cudaMemsetAsync(d_hhi, 0, 2 * (size_t)N * kd, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_hlo, 0, 2 * (size_t)N * kd, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cosine set-up");
-
-  // unit weights: dense head operands and tail postings
+  // unit weights: dense head operands, and per document its tail terms (and postings or norms)
   DenseOut o{};
   o.idf = wid;
   o.colmap = d_colmap;
@@ -947,22 +945,14 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   o.head_lo = d_hlo;
   o.tail_start = d_tstart;
   o.tail_fill = d_tfill;
-  o.post_doc = d_pdoc;
-  o.post_w = d_pw;
-  o.post_r = d_pr;
   o.row_cnt = d_rcnt;
   o.norm = d_norm;
   o.row_w = d_rw;
-  e = launch_densify(ctx, d, V, index->tinfo, o);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "densify");
-  e = launch_rank_postings(ctx, d_cstart, d_rank_terms, n_small, d_rank_terms + n_small, n_tail - n_small, max_m, d_pdoc,
-                           d_pw, d_pr, d.offsets, d_spost, d_rwalk);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "sorting postings");
-
-  // head: single-fp16 tensor-core GEMM of the unit head columns, stored as fp16. Its error
-  // against the exact head sum is at most: fp16 rounding of both operands, 2^-10 sum|w_i w_j|
-  // <= 2^-10 (unit vectors); FP32 accumulation over kd terms, kd 2^-23; the fp16 store of a
-  // value <= 1, 2^-12; plus 1e-4 for subnormal operands and the FP32 addition of the tail.
+  // The head GEMM's error against the exact head sum is at most: fp16 rounding of both
+  // operands, 2^-10 sum|w_i w_j| <= 2^-10 (unit vectors); FP32 accumulation over kd terms,
+  // kd 2^-23; 2^-12 (the fp16 store of the tail-walk path); plus 1e-4 for subnormal operands
+  // and the FP32 addition of the tail.
+  const float delta = (float)(std::ldexp(1.0, -10) + std::ldexp(1.0, -12) + (double)kd * std::ldexp(1.0, -23) + 1e-4);
   GemmArgs g{};
   g.fmt = OP_F16;
   g.a_hi = g.b_hi = d_hhi;
@@ -970,18 +960,83 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   g.kbytes = kd * 2;
   g.triangle = 1;
   g.out_scale = 1.0f;
+  g.err = async ? ctx->async_err : d_err;
+
+  // Bound-pruned path. A pair's tail dot product is at most tn_i tn_j (Cauchy-Schwarz on the
+  // tail sub-vectors), so a pair whose head score plus tn_i tn_j stays below tau - delta' is
+  // below tau: the head GEMM emits only the other pairs as candidates, and each candidate gets
+  // its exact score (k_cosine_verify). delta' adds to delta the rounding of the tail sum
+  // (at most 2^-31 per shared term, under 3.1e-5 for 65,536 terms) and of the bound itself.
+  {
+    const int64_t cand_cap = std::max<int64_t>(4 * capacity, 1 << 22);
+    int32_t* d_rterm = (int32_t*)ws_get(ctx, "cos.rterm", sizeof(int32_t) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
+    float* d_tn = (float*)ws_get(ctx, "cos.tn", sizeof(float) * (size_t)N, &st);
+    mrc_pair* d_cand = (mrc_pair*)ws_get(ctx, "cos.cand", sizeof(mrc_pair) * (size_t)cand_cap, &st);
+    unsigned long long* d_ccount = (unsigned long long*)ws_get(ctx, "cos.ccount", sizeof(unsigned long long), &st);
+    if (st != MRC_OK) return st;
+    e = cudaMemsetAsync(d_ccount, 0, sizeof(unsigned long long), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cosine set-up");
+    o.postings = 0;
+    o.row_term = d_rterm;
+    o.tail_norm = d_tn;
+    e = launch_densify(ctx, d, V, index->tinfo, o);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "densify");
+    g.tn = d_tn;
+    g.thresh = tau - (delta + 4e-5f);
+    g.pairs = d_cand;
+    g.count = d_ccount;
+    g.capacity = cand_cap;
+    e = launch_gemm_compare(ctx, g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "head GEMM");
+    e = launch_cosine_verify(ctx, d_cand, d_ccount, cand_cap, d_hhi, d_hlo, kd, d.offsets, d_rcnt, d_rterm, d_rw, tau,
+                             dst, d_count, capacity, async ? ctx->async_err : d_err);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "candidate verification");
+    if (async) return MRC_OK;  // a candidate overflow is reported by mrc_ctx_sync
+    bool overflow = false;
+    st = finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs, d_err, d_ccount, cand_cap, &overflow);
+    if (!overflow) return st;
+    // too many candidates for the buffer: the exhaustive tail walk below
+    e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int32_t), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cosine set-up");
+    g.tn = nullptr;
+  }
+
+  // Tail-walk path: the head stored as fp16 scores, the tail postings of each term ordered by
+  // document, each row's tail products summed over the postings after it, candidates against
+  // tau - delta, exact head for each candidate.
+  if (n_post >= (1ll << 31) - 64)
+    return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more than 2^31 tail postings");
+  if ((double)N * (double)ldh * 2.0 > 64e9)
+    return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more documents than the 64 GB score buffer allows");
+  int4* d_post = (int4*)ws_get(ctx, "cos.post", sizeof(int4) * (size_t)std::max<int64_t>(n_post, 1), &st);
+  void* d_spost = ws_get(ctx, "cos.spost", 8 * (size_t)std::max<int64_t>(n_post, 1), &st);
+  void* d_rwalk = ws_get(ctx, "cos.rwalk", 8 * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
+  void* d_H = ws_get(ctx, "cos.H16", 2 * (size_t)N * ldh, &st);
+  unsigned long long* d_next = (unsigned long long*)ws_get(ctx, "cos.next", sizeof(unsigned long long), &st);
+  if (st != MRC_OK) return st;
+  e = cudaMemsetAsync(d_tfill, 0, sizeof(int32_t) * V, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cosine set-up");
+  o.postings = 1;
+  o.post = d_post;
+  o.row_term = nullptr;
+  o.tail_norm = nullptr;
+  e = launch_densify(ctx, d, V, index->tinfo, o);  // rewrites the same head rows
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "densify");
+  e = launch_rank_postings(ctx, d_cstart, d_rank_terms, n_small, d_rank_terms + n_small, n_tail - n_small, max_m, d_post,
+                           d.offsets, d_spost, d_rwalk);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sorting postings");
   g.store16 = d_H;
   g.ld = ldh;
-  g.err = async ? ctx->async_err : d_err;
+  g.thresh = 0.f;
+  g.pairs = nullptr;
+  g.count = nullptr;
+  g.capacity = 0;
   e = launch_gemm_compare(ctx, g);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "head GEMM");
-  const float delta = (float)(std::ldexp(1.0, -10) + std::ldexp(1.0, -12) + (double)kd * std::ldexp(1.0, -23) + 1e-4);
-
-  // tail: postings products, candidates against tau - delta, exact head for each candidate
   e = launch_cosine_tail(ctx, N, d_H, ldh, d.offsets, d_rcnt, d_rwalk, d_rw, d_spost, n_post, d_hhi, d_hlo, kd,
                          tau, delta, dst, d_count, capacity, tail_work, d_next);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tail pass");
-  if (async) return MRC_OK;
   return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs, d_err);
 }
 

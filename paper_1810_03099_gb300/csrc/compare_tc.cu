@@ -74,6 +74,7 @@ struct GemmParams {
   int64_t ld;
   int32_t* err;
   int32_t row_rr;  // resident kernel, triangle: whole row blocks dealt round-robin (see TileSeq)
+  const float* tn;  // streaming kernel: candidates by acc + tn[i] * tn[j] >= thresh (see GemmArgs)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -245,8 +246,11 @@ __device__ __forceinline__ void flush_pairs(const GemmParams& p, const mrc_pair*
 // Threshold one 32-column chunk held in registers (v[e] = score of column j0 + e for this
 // lane's row i) and append its pairs. Fast path: the chunk's maximum misses fast_thresh in
 // every lane. Otherwise each lane builds a 32-bit mask of candidate columns (bounds and the
-// triangle's j > i applied with bit arithmetic), tests the candidates exactly (E4M3: against
-// the column norms staged once per warp), and the warp appends its hits to its pair buffer.
+// triangle's j > i applied with bit arithmetic), tests the candidates exactly, and the warp
+// appends its hits to its pair buffer. E4M3 operands are only ever candidates for FP32
+// rescoring: a column is a hit when acc * out_scale >= thresh * |q_i| * |q_j| (column norms
+// staged once per warp; zero norms never hit), tested by multiplication, and the pair carries
+// the raw accumulator (the rescoring pass computes the reported score).
 template <int FMT>
 __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)[32], int64_t i, int64_t j0, int lane,
                                            float fast_thresh, float row_norm, float* stage, float* nstage,
@@ -271,14 +275,19 @@ __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)
   }
   if (i >= p.na) mask = 0u;
   uint32_t hits = 0;
+  // E4M3: the hit test acc >= hit_lim * |q_j| with hit_lim = thresh * |q_i| / out_scale
+  const float hit_lim = FMT == OP_E4M3 ? p.thresh * row_norm / p.out_scale : p.thresh;
   for (uint32_t mm = mask; mm; mm &= mm - 1u) {
     const int e = __ffs(mm) - 1;
-    float sc = stage[lane * 33 + e];
+    const float sc = stage[lane * 33 + e];
+    bool hit;
     if (FMT == OP_E4M3) {
-      const float nn = row_norm * nstage[e];
-      sc = nn > 0.f ? sc * p.out_scale / nn : 0.f;
+      const float nj = nstage[e];
+      hit = row_norm > 0.f && nj > 0.f && sc >= hit_lim * nj;
+    } else {
+      hit = sc >= hit_lim;
     }
-    if (sc >= p.thresh) hits |= 1u << e;
+    if (hit) hits |= 1u << e;
   }
   const int cnt = __popc(hits);
   int incl = cnt;
@@ -301,8 +310,7 @@ __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)
     int at = incl - cnt;
     for (uint32_t hh = hits; hh; hh &= hh - 1u, ++at) {
       const int e = __ffs(hh) - 1;
-      float sc = stage[lane * 33 + e];
-      if (FMT == OP_E4M3) sc = sc * p.out_scale / (row_norm * nstage[e]);
+      const float sc = stage[lane * 33 + e];
       mrc_pair pr;
       pr.i = (int32_t)i;
       pr.j = (int32_t)(j0 + e);
@@ -343,6 +351,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
   float* stage_all = reinterpret_cast<float*>(drain + 4);  // [4 epilogue warps][32 x 33 + 32]
   mrc_pair* pbuf_all = reinterpret_cast<mrc_pair*>(stage_all + 4 * (32 * 33 + 32));  // [4][kPairBuf]
+  float* tn_all = reinterpret_cast<float*>(pbuf_all + 4 * kPairBuf);  // [4][BN] column tail norms
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* stage = stage_all + (warp >= 2 ? warp - 2 : 0) * (32 * 33 + 32);
@@ -489,6 +498,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       // Every non-zero quantized unit row has norm >= 1 - 2^-4 > kNormLo, so raw accumulators
       // below thresh * |q_i| * kNormLo / out_scale cannot reach the threshold (fast path).
       float row_norm = 1.f, fast_thresh = p.thresh;
+      // bound-pruned exact cosine: the score tested is acc + tn_i * tn_j (Cauchy-Schwarz bound
+      // of head + tail); the column norms of this tile are staged once per warp
+      float tn_i = 0.f;
+      float* tn_s = tn_all + (warp >= 2 ? warp - 2 : 0) * BN;
+      if (p.tn) {
+        tn_i = i < p.na ? p.tn[i] : 0.f;
+        for (int x = lane; x < BN; x += 32) {
+          const int64_t j = bj * BN + x;
+          tn_s[x] = j < p.nb ? p.tn[j] : 0.f;
+        }
+        __syncwarp();
+      }
       if (FMT == OP_E4M3) {
         row_norm = i < p.na ? p.a_norm[i] : 0.f;
         if (p.thresh > 0.f)
@@ -545,6 +566,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         } else {
+          if (p.tn) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = fmaf(tn_i, tn_s[c * 32 + e], v[e]);
+          }
           emit_chunk<FMT>(p, v, i, j0, lane, fast_thresh, row_norm, stage, nstage, pbuf, nbuf);
         }
       }
@@ -1001,8 +1026,10 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   p.store16 = reinterpret_cast<__half*>(g.store16);
   p.ld = g.ld;
   p.err = g.err;
+  p.tn = g.tn;
+  if (g.tn && (!g.triangle || g.store || g.store16 || FMT != OP_F16)) return cudaErrorInvalidValue;
   const size_t smem = 1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256 + 4 * (32 * 33 + 32) * 4 +
-                      4 * kPairBuf * sizeof(mrc_pair);
+                      4 * kPairBuf * sizeof(mrc_pair) + 4 * (size_t)BN * sizeof(float);
   if (resident_ctas(k_gemm_compare<FMT, 0>, kThreads, smem) <= 0 ||
       (mc && resident_ctas(k_gemm_compare<FMT, 1>, kThreads, smem) <= 0))
     return cudaErrorInvalidConfiguration;
@@ -1037,7 +1064,7 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   const double flops = 2.0 * k_elems * pairs * (C::NOPS == 2 ? 3.0 : 1.0);
   const bool st = g.store || g.store16;
   const char* name = FMT == OP_SPLIT16 ? (st ? "gemm_split16_store" : "gemm_split16_thresh")
-                                        : (FMT == OP_F16 ? (st ? "gemm_f16_store" : "gemm_f16_thresh")
+                                        : (FMT == OP_F16 ? (st ? "gemm_f16_store" : (g.tn ? "gemm_f16_bound" : "gemm_f16_thresh"))
                                                          : "gemm_e4m3_thresh");
   const double bytes = (double)C::NOPS * (double)(g.na + (g.triangle ? 0 : g.nb)) * g.kbytes;
   cudaEvent_t ev = nullptr;
@@ -1059,7 +1086,7 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
 cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g) {
   if (g.na <= 0 || g.nb <= 0) return cudaErrorInvalidValue;
   if (g.na >= (1ll << 31) || g.nb >= (1ll << 31)) return cudaErrorInvalidValue;
-  if (!g.store && !g.store16 && (g.kbytes == 64 || g.kbytes == 128)) {
+  if (!g.store && !g.store16 && !g.tn && (g.kbytes == 64 || g.kbytes == 128)) {
     // one K block: resident-A kernel
     // tile width: 256 columns by default for single-accumulator formats, 128 on request
     const int wide = (g.fmt != OP_SPLIT16 && g.tile_n != 128) ? 1 : 0;

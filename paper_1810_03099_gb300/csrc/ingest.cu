@@ -80,6 +80,15 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 __device__ __forceinline__ unsigned long long to_fix(float x) { return __float2ull_rn(x * kFix); }
 
 // 1 / |w| from the fixed-point squared norm (0 for an empty document).
+// u^2 in 2^-40 fixed point, rounded up (u <= 1: at most 2^40 per term); the product of two
+// floats is exact in double.
+__device__ __forceinline__ unsigned long long to_fix40_up(float u) {
+  return __double2ull_ru((double)u * (double)u * 1099511627776.0);
+}
+// sqrt of a 2^-40 fixed-point sum, rounded up to float.
+__device__ __forceinline__ float tail_norm_of(unsigned long long n2) {
+  return __double2float_ru(sqrt((double)n2 * (1.0 / 1099511627776.0)) * (1.0 + 1e-12));
+}
 __device__ __forceinline__ float inv_norm_of(unsigned long long norm_q) {
   const float n2 = (float)norm_q * kInvFix;
   return n2 > 0.f ? 1.0f / sqrtf(n2) : 0.f;
@@ -179,7 +188,7 @@ __device__ __forceinline__ TermAux load_aux(const IngestParams& p, uint32_t key)
   } else if (MODE == kDENSE) {
     if (p.dense.idf) x.w = __ldg(p.dense.idf + key);
     x.code = __ldg(p.dense.colmap + key);
-    if (x.code == -2) {  // a tail term: claim its posting slot now (slots < 2^31 - 64)
+    if (x.code == -2 && p.dense.postings) {  // a tail term: claim its posting slot now (slots < 2^31 - 64)
       const int64_t pos = p.dense.tail_start[key] + atomicAdd(&p.dense.tail_fill[key], 1);
       x.code = -3 - (int32_t)pos;
     }
@@ -238,13 +247,16 @@ __device__ __forceinline__ void chunk(const IngestParams& p, uint32_t key, uint3
     const int64_t at = doc * (int64_t)p.dense.kd + code;
     reinterpret_cast<__half*>(p.dense.head_hi)[at] = hi;
     reinterpret_cast<__half*>(p.dense.head_lo)[at] = lo;
-  } else if (code <= -3) {
-    const int64_t pos = -3 - (int64_t)code;
+  } else if (code <= -2) {  // a tail term (-2: no posting slot, bound-pruned mode)
     const int32_t r = atomicAdd(row_cnt_s, 1);
-    p.dense.post_doc[pos] = (int32_t)doc;
-    p.dense.post_w[pos] = u;
-    p.dense.post_r[pos] = r;
     p.dense.row_w[row_base + r] = u;
+    if (code <= -3) {
+      const int64_t pos = -3 - (int64_t)code;
+      p.dense.post[pos] = make_int4((int32_t)doc, __float_as_int(u), r, 0);
+    } else {
+      p.dense.row_term[row_base + r] = (int32_t)key;
+      a.norm += to_fix40_up(u);  // the document's tail |t|^2, 2^-40 fixed point, rounded up
+    }
   }
 }
 
@@ -449,7 +461,13 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
       const unsigned long long nq = warp_sum(a.norm);
       if (lane == 0) p.norm_out[d] = nq;
     }
-    if (MODE == kDENSE && lane == 0) p.dense.row_cnt[d] = *row_cnt_s;
+    if (MODE == kDENSE) {
+      if (!p.dense.postings) {
+        const unsigned long long t2 = warp_sum(a.norm);
+        if (lane == 0) p.dense.tail_norm[d] = tail_norm_of(t2);
+      }
+      if (lane == 0) p.dense.row_cnt[d] = *row_cnt_s;
+    }
     __syncwarp();
     it = __shfl_sync(kFull, next, 0);
   }
@@ -594,7 +612,7 @@ __global__ void __launch_bounds__(kLongThreads, 2) k_ingest_long(IngestParams p)
                        p.bag_write ? &misc[2] : nullptr);
       }
     }
-    if (MODE == kDFN) {
+    if (MODE == kDFN || (MODE == kDENSE && !p.dense.postings)) {
       const unsigned long long nq = warp_sum(a.norm);
       if (lane == 0) atomicAdd(norm_s, nq);
     }
@@ -606,7 +624,10 @@ __global__ void __launch_bounds__(kLongThreads, 2) k_ingest_long(IngestParams p)
     }
     __syncthreads();
     if (MODE == kSIG && warp == 0) finalize_sig(p, d, len, *norm_s, num_q, P[lane], P[lane + 32], lane);
-    if (MODE == kDENSE && threadIdx.x == 0) p.dense.row_cnt[d] = misc[1];
+    if (MODE == kDENSE && threadIdx.x == 0) {
+      p.dense.row_cnt[d] = misc[1];
+      if (!p.dense.postings) p.dense.tail_norm[d] = tail_norm_of(*norm_s);
+    }
     if (MODE == kDFN && threadIdx.x == 0) p.norm_out[d] = *norm_s;
     if (p.bag_write && threadIdx.x == 0) p.bag_n[d] = misc[2];
     __syncthreads();

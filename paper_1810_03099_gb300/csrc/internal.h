@@ -196,12 +196,17 @@ struct DenseOut {
   void* head_lo;          // [n*kd] fp16
   const int64_t* tail_start;  // [vocab] start of the term's postings
   int32_t* tail_fill;         // [vocab] fill cursors (zeroed)
-  int32_t* post_doc;          // [n_post]
-  float* post_w;              // [n_post]
-  int32_t* post_r;            // [n_post] index of the posting's term in its document's tail list
+  int4* post;                 // [n_post] (document, weight bits, index of the posting's term in its
+                              // document's tail list, 0): one 16-byte store per posting
   int32_t* row_cnt;           // [n] tail terms of each doc
   float* row_w;               // [n_tokens] at the doc's token offsets: unit weight of its r-th tail term
   const unsigned long long* norm;  // [n] squared norms, 2^-22 fixed point (from launch_df_norm)
+  // postings == 1: tail postings (tail_start, tail_fill, post) for the tail walk. postings == 0
+  // (bound-pruned exact cosine): instead each document's tail term ids (row_term, beside row_w)
+  // and its tail norm |t_d| (tail_norm, rounded up).
+  int32_t postings;
+  int32_t* row_term;          // [n_tokens] at the doc's token offsets: id of its r-th tail term
+  float* tail_norm;           // [n] sqrt(sum of the document's tail u^2), rounded up
 };
 cudaError_t launch_densify(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo, const DenseOut& out);
 
@@ -229,6 +234,9 @@ struct GemmArgs {
   int64_t ld;
   int32_t tile_n;       // compare tile width for small K: 128, 256 or 0 (default)
   int32_t* err;         // device error word
+  // bound-pruned exact cosine (streaming kernel, triangle): a pair is a candidate when
+  // acc + tn[i] * tn[j] >= thresh (tn: the documents' tail norms); NULL otherwise
+  const float* tn;
 };
 cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g);
 
@@ -253,11 +261,18 @@ cudaError_t launch_cosine_terms(mrc_ctx* ctx, const int32_t* df, int32_t V, int3
 // follow that document. small_terms: tail terms (indices into cstart) with at most 32
 // postings; big_terms: the others, each with at most max_m postings.
 cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int32_t* small_terms, int32_t n_small,
-                                 const int32_t* big_terms, int32_t n_big, int32_t max_m, const int32_t* post_doc,
-                                 const float* post_w, const int32_t* post_r, const int64_t* doc_off, void* spost,
+                                 const int32_t* big_terms, int32_t n_big, int32_t max_m, const int4* post,
+                                 const int64_t* doc_off, void* spost,
                                  void* row_walk);
 // Exact cosine completion: approximate fp16 head scores H plus exact tail products, candidates
 // >= tau - delta rescored exactly (head from the hi/lo split rows [n x kd], tail exact).
+// Exact scores of the bound-pruned candidates (see k_cosine_verify); pairs with score >= tau
+// go to pairs/count; a candidate count above cand_cap sets kErrOverflow in err.
+cudaError_t launch_cosine_verify(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand,
+                                 int64_t cand_cap, const void* head_hi, const void* head_lo, int32_t kd,
+                                 const int64_t* row_off, const int32_t* row_cnt, const int32_t* row_term,
+                                 const float* row_w, float tau, mrc_pair* pairs, unsigned long long* count,
+                                 int64_t capacity, int32_t* err);
 cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t ldh, const int64_t* row_off,
                                const int32_t* row_cnt, const void* row_walk, const float* row_w, const void* spost,
                                int64_t n_postings, const void* head_hi, const void* head_lo,

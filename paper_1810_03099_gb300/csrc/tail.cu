@@ -44,9 +44,7 @@ __device__ __forceinline__ void put_ranked(int32_t at, int32_t end, int32_t d, f
 // posting (document, weight, slot, the document's offset) is issued before the ranking.
 __global__ void __launch_bounds__(256) k_rank_small(const int64_t* __restrict__ cstart,
                                                     const int32_t* __restrict__ terms, int32_t n_terms,
-                                                    const int32_t* __restrict__ post_doc,
-                                                    const float* __restrict__ post_w,
-                                                    const int32_t* __restrict__ post_r,
+                                                    const int4* __restrict__ post,
                                                     const int64_t* __restrict__ doc_off, int2* __restrict__ spost,
                                                     int2* __restrict__ row_walk) {
   const int lane = threadIdx.x & 31;
@@ -59,9 +57,10 @@ __global__ void __launch_bounds__(256) k_rank_small(const int64_t* __restrict__ 
     float w = 0.f;
     int64_t off = 0;
     if (lane < m) {
-      d = post_doc[p0 + lane];
-      w = post_w[p0 + lane];
-      r = post_r[p0 + lane];
+      const int4 pe = post[p0 + lane];
+      d = pe.x;
+      w = __int_as_float(pe.y);
+      r = pe.z;
       off = doc_off[d];
     }
     int32_t rank = 0;
@@ -74,8 +73,8 @@ __global__ void __launch_bounds__(256) k_rank_small(const int64_t* __restrict__ 
 // posting counts the smaller ids there, four per 16-byte broadcast read.
 __global__ void __launch_bounds__(kRankWarps * 32) k_rank_big(
     const int64_t* __restrict__ cstart, const int32_t* __restrict__ terms, int32_t n_terms, int32_t buf,
-    const int32_t* __restrict__ post_doc, const float* __restrict__ post_w, const int32_t* __restrict__ post_r,
-    const int64_t* __restrict__ doc_off, int2* __restrict__ spost, int2* __restrict__ row_walk) {
+    const int4* __restrict__ post, const int64_t* __restrict__ doc_off, int2* __restrict__ spost,
+    int2* __restrict__ row_walk) {
   extern __shared__ __align__(16) int32_t rbuf[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* sd = rbuf + warp * buf;
@@ -86,12 +85,13 @@ __global__ void __launch_bounds__(kRankWarps * 32) k_rank_big(
     const int32_t m = (int32_t)cstart[c + 1] - p0;
     const int32_t m4 = (m + 3) & ~3;
     if (m4 > buf) continue;  // excluded by the host
-    for (int32_t y = lane; y < m4; y += 32) sd[y] = y < m ? post_doc[p0 + y] : 0x7fffffff;
+    for (int32_t y = lane; y < m4; y += 32) sd[y] = y < m ? post[p0 + y].x : 0x7fffffff;
     __syncwarp();
     for (int32_t e = lane; e < m; e += 32) {
       const int32_t d = sd[e];
-      const float w = post_w[p0 + e];
-      const int32_t r = post_r[p0 + e];
+      const int4 pe = post[p0 + e];
+      const float w = __int_as_float(pe.y);
+      const int32_t r = pe.z;
       const int64_t off = doc_off[d];
       int32_t rank = 0;
       for (int32_t y = 0; y < m4; y += 4) {
@@ -253,9 +253,10 @@ __global__ void __launch_bounds__(kTermBlock) k_term_place(const int32_t* __rest
   }
 }
 
-// Exclusive scan of v over the CTA (kTailThreads threads); *total receives the sum. scratch:
-// 33 ints of shared memory. Synchronises the CTA.
-__device__ __forceinline__ int32_t cta_excl_scan(int32_t v, int32_t* scratch, int32_t* total) {
+// Exclusive scan of v over the CTA with one barrier: each warp publishes its total, then every
+// warp adds up the totals before it itself. scratch: kTailWarps words, not rewritten before
+// the CTA's next barrier.
+__device__ __forceinline__ int32_t cta_excl_scan1(int32_t v, int32_t* scratch, int32_t* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int32_t incl = v;
 #pragma unroll
@@ -265,20 +266,15 @@ __device__ __forceinline__ int32_t cta_excl_scan(int32_t v, int32_t* scratch, in
   }
   if (lane == 31) scratch[warp] = incl;
   __syncthreads();
-  if (warp == 0) {
-    const int32_t w = lane < kTailWarps ? scratch[lane] : 0;
-    int32_t wi = w;
+  const int32_t w = lane < kTailWarps ? scratch[lane] : 0;
+  int32_t before = lane < warp ? w : 0, all = w;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t y = __shfl_up_sync(kFull, wi, o);
-      if (lane >= o) wi += y;
-    }
-    if (lane < kTailWarps) scratch[lane] = wi - w;
-    if (lane == 31) scratch[32] = wi;
+  for (int o = 16; o > 0; o >>= 1) {
+    before += __shfl_xor_sync(kFull, before, o);
+    all += __shfl_xor_sync(kFull, all, o);
   }
-  __syncthreads();
-  *total = scratch[32];
-  return scratch[warp] + incl - v;
+  *total = all;
+  return before + incl - v;
 }
 
 // Exact score of one candidate pair (i, j): the head part recomputed from the split head rows
@@ -413,7 +409,7 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_cosine_tail(
         sh = q ? sb.off - sb.cb : sa.off - sa.cb;
       }
       int32_t total;
-      const int32_t ex = cta_excl_scan(cnt, t_scan, &total);  // synchronises the CTA
+      const int32_t ex = cta_excl_scan1(cnt, t_scan, &total);  // synchronises the CTA
       const int32_t nterm = min(kTermBatch, nt - b0);
       // posting index = y + flattened position
       t_ent[threadIdx.x] = make_int4(ex + cnt, st - ex, __float_as_int(wi * kTailFix), sh);
@@ -461,9 +457,8 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_cosine_tail(
             atomicAdd(&acc[j + shv[u]], __float2int_rn(wv[u] * __int_as_float(pv[u].y)));
         }
       }
-      __syncthreads();  // the next batch rewrites the term tables
+      __syncthreads();  // the next batch rewrites the term tables; the scan below reads acc
     }
-    __syncthreads();
     // scan: each lane takes eight consecutive columns of one segment (one 16-byte load of H16,
     // in the row's ldh >= round8(n) padding at the end, so never past the row)
     const int32_t g_a = (sa.c_hi - sa.cb + 7) >> 3;  // 8-column groups of the first segment
@@ -527,6 +522,160 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_cosine_tail(
   }
 }
 
+// ---- bound-pruned exact cosine: verification of the candidates ---------------------------
+// A pair (i, j) is a candidate when the tensor-core head score plus tn_i * tn_j reaches
+// tau - delta' (Cauchy-Schwarz bounds the tail dot product by the tail norms). Each candidate
+// gets the same score as the tail walk would give it: the head recomputed exactly from the
+// split rows plus the tail sum of round((u_i 2^30) u_j) over the tail terms the two documents
+// share, found by a hash join in the warp's shared-memory table (the shorter list inserted;
+// lists beyond a quarter of the table are joined in hash-partitioned passes).
+constexpr int kVerWarps = 8;
+constexpr int kVerSlots = 1024;  // per-warp table: term ids and weights (load <= 1/4 per pass)
+constexpr int kVerBatch = 8;     // list entries per lane loaded at once
+
+// Exact head from the split rows with all of a lane's loads for two 256-column steps in flight;
+// the same sum, in the same order, as exact_head.
+__device__ __forceinline__ float exact_head_batched(const __half* __restrict__ hhi, const __half* __restrict__ hlo,
+                                                    int32_t kd, int64_t i, int64_t j, int lane) {
+  const __half* ai = hhi + i * kd;
+  const __half* bi = hlo + i * kd;
+  const __half* aj = hhi + j * kd;
+  const __half* bj = hlo + j * kd;
+  float s = 0.f;
+  for (int32_t c0 = 8 * lane; c0 < kd; c0 += 512) {
+    uint4 xa[2], xb[2], ya[2], yb[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int32_t c = c0 + 256 * h;
+      if (c < kd) {
+        xa[h] = __ldg(reinterpret_cast<const uint4*>(ai + c));
+        xb[h] = __ldg(reinterpret_cast<const uint4*>(bi + c));
+        ya[h] = __ldg(reinterpret_cast<const uint4*>(aj + c));
+        yb[h] = __ldg(reinterpret_cast<const uint4*>(bj + c));
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (c0 + 256 * h >= kd) break;
+      const __half2* pa = reinterpret_cast<const __half2*>(&xa[h]);
+      const __half2* pb = reinterpret_cast<const __half2*>(&xb[h]);
+      const __half2* qa = reinterpret_cast<const __half2*>(&ya[h]);
+      const __half2* qb = reinterpret_cast<const __half2*>(&yb[h]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2 h1 = __half22float2(pa[u]), l1 = __half22float2(pb[u]);
+        const float2 h2 = __half22float2(qa[u]), l2 = __half22float2(qb[u]);
+        const float x0 = fmaf(l1.x, 1.0f / kSplitLoScale, h1.x), x1 = fmaf(l1.y, 1.0f / kSplitLoScale, h1.y);
+        const float y0 = fmaf(l2.x, 1.0f / kSplitLoScale, h2.x), y1 = fmaf(l2.y, 1.0f / kSplitLoScale, h2.y);
+        s = fmaf(x0, y0, s);
+        s = fmaf(x1, y1, s);
+      }
+    }
+  }
+  return warp_sum(s);
+}
+
+__global__ void __launch_bounds__(kVerWarps * 32) k_cosine_verify(
+    const mrc_pair* __restrict__ cand, const unsigned long long* __restrict__ n_cand, int64_t cand_cap,
+    const __half* __restrict__ hhi, const __half* __restrict__ hlo, int32_t kd, const int64_t* __restrict__ row_off,
+    const int32_t* __restrict__ row_cnt, const int32_t* __restrict__ row_term, const float* __restrict__ row_w,
+    float tau, mrc_pair* pairs, unsigned long long* count, int64_t capacity, int32_t* err) {
+  extern __shared__ __align__(16) int32_t vsm[];  // [kVerWarps][kVerSlots keys + kVerSlots weights]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t* keys = vsm + warp * 2 * kVerSlots;
+  float* vals = reinterpret_cast<float*>(keys + kVerSlots);
+  const unsigned long long nc0 = *n_cand;
+  const int64_t nc = nc0 < (unsigned long long)cand_cap ? (int64_t)nc0 : cand_cap;
+  if (err && nc0 > (unsigned long long)cand_cap && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, kErrOverflow);
+  const int64_t nwarps = (int64_t)gridDim.x * kVerWarps;
+  for (int64_t c = (int64_t)blockIdx.x * kVerWarps + warp; c < nc; c += nwarps) {
+    const mrc_pair pc = cand[c];
+    const int32_t i = pc.i, j = pc.j;
+    const int32_t ni = row_cnt[i], nj = row_cnt[j];
+    const bool i_small = ni <= nj;
+    const int64_t os = row_off[i_small ? i : j], ol = row_off[i_small ? j : i];
+    const int32_t ns = i_small ? ni : nj, nl = i_small ? nj : ni;
+    // passes: a power of two with at most about a quarter table per pass
+    int lp = 0;
+    while ((ns >> lp) > kVerSlots / 4) ++lp;
+    const int32_t passes = ns > 0 ? 1 << lp : 0;
+    long long acc = 0;
+    for (int32_t ps = 0; ps < passes; ++ps) {
+      for (int x = 4 * lane; x < kVerSlots; x += 128) *reinterpret_cast<int4*>(keys + x) = make_int4(-1, -1, -1, -1);
+      __syncwarp();
+      for (int32_t x0 = 0; x0 < ns; x0 += 32 * kVerBatch) {
+        int32_t tv[kVerBatch];
+        float wv[kVerBatch];
+#pragma unroll
+        for (int u = 0; u < kVerBatch; ++u) {
+          const int32_t x = x0 + 32 * u + lane;
+          tv[u] = x < ns ? __ldg(row_term + os + x) : -1;
+          wv[u] = x < ns ? __ldg(row_w + os + x) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kVerBatch; ++u) {
+          const int32_t t = tv[u];
+          if (t < 0 || (lp > 0 && (int32_t)(((uint32_t)t * 0x9E3779B1u) >> (32 - lp)) != ps)) continue;
+          uint32_t slot = ((uint32_t)t * 0x85EBCA6Bu) >> (32 - 10);
+          for (int probes = 0;; ++probes) {
+            if (atomicCAS(&keys[slot], -1, t) == -1) {
+              vals[slot] = wv[u];
+              break;
+            }
+            slot = (slot + 1) & (kVerSlots - 1);
+            if (probes + 1 == kVerSlots) {  // table full (cannot happen below a quarter load): give up
+              set_err(err, kErrTable);
+              break;
+            }
+          }
+        }
+      }
+      __syncwarp();
+      for (int32_t y0 = 0; y0 < nl; y0 += 32 * kVerBatch) {
+        int32_t tv[kVerBatch];
+        float wv[kVerBatch];
+#pragma unroll
+        for (int u = 0; u < kVerBatch; ++u) {
+          const int32_t y = y0 + 32 * u + lane;
+          tv[u] = y < nl ? __ldg(row_term + ol + y) : -1;
+          wv[u] = y < nl ? __ldg(row_w + ol + y) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kVerBatch; ++u) {
+          const int32_t t = tv[u];
+          if (t < 0 || (lp > 0 && (int32_t)(((uint32_t)t * 0x9E3779B1u) >> (32 - lp)) != ps)) continue;
+          uint32_t slot = ((uint32_t)t * 0x85EBCA6Bu) >> (32 - 10);
+          for (int probes = 0; probes < kVerSlots; ++probes) {
+            const int32_t k = keys[slot];
+            if (k == t) {
+              const float ws = vals[slot];
+              const float wi = i_small ? ws : wv[u], wj = i_small ? wv[u] : ws;
+              acc += __float2int_rn((wi * kTailFix) * wj);
+              break;
+            }
+            if (k == -1) break;
+            slot = (slot + 1) & (kVerSlots - 1);
+          }
+        }
+      }
+      __syncwarp();
+    }
+    const float head = exact_head_batched(hhi, hlo, kd, i, j, lane);
+    const long long tail = warp_sum(acc);
+    const float s = head + (float)tail * kTailInv;
+    if (lane == 0 && s >= tau) {
+      const unsigned long long at = atomicAdd(count, 1ull);
+      if (at < (unsigned long long)capacity) {
+        mrc_pair pr;
+        pr.i = i;
+        pr.j = j;
+        pr.score = s;
+        pairs[at] = pr;
+      }
+    }
+  }
+}
+
 __global__ void k_rescore(const mrc_pair* __restrict__ cand, const unsigned long long* n_cand, int64_t cand_cap,
                           const float* __restrict__ qunit, const float* __restrict__ xunit, int32_t k, float tau,
                           mrc_pair* pairs, unsigned long long* count, int64_t capacity, int32_t* err) {
@@ -576,15 +725,15 @@ cudaError_t launch_cosine_terms(mrc_ctx* ctx, const int32_t* df, int32_t V, int3
 }
 
 cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int32_t* small_terms, int32_t n_small,
-                                 const int32_t* big_terms, int32_t n_big, int32_t max_m, const int32_t* post_doc,
-                                 const float* post_w, const int32_t* post_r, const int64_t* doc_off, void* spost,
+                                 const int32_t* big_terms, int32_t n_big, int32_t max_m, const int4* post,
+                                 const int64_t* doc_off, void* spost,
                                  void* row_walk) {
   if (n_small > 0) {
     int64_t grid = (int64_t)ctx->num_sms * resident_ctas(k_rank_small, 256, 0);
     const int64_t need = ((int64_t)n_small + 7) / 8;
     if (need < grid) grid = need;
     KernelTimer kt(ctx, "rank_small");
-    k_rank_small<<<(unsigned)grid, 256, 0, ctx->stream>>>(cstart, small_terms, n_small, post_doc, post_w, post_r,
+    k_rank_small<<<(unsigned)grid, 256, 0, ctx->stream>>>(cstart, small_terms, n_small, post,
                                                            doc_off, reinterpret_cast<int2*>(spost),
                                                            reinterpret_cast<int2*>(row_walk));
   }
@@ -597,11 +746,27 @@ cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int3
     const int64_t need = ((int64_t)n_big + kRankWarps - 1) / kRankWarps;
     if (need < grid) grid = need;
     KernelTimer kt(ctx, "rank_big");
-    k_rank_big<<<(unsigned)grid, kRankWarps * 32, smem, ctx->stream>>>(cstart, big_terms, n_big, buf, post_doc,
-                                                                       post_w, post_r, doc_off,
+    k_rank_big<<<(unsigned)grid, kRankWarps * 32, smem, ctx->stream>>>(cstart, big_terms, n_big, buf, post,
+                                                                       doc_off,
                                                                        reinterpret_cast<int2*>(spost),
                                                                        reinterpret_cast<int2*>(row_walk));
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cosine_verify(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand,
+                                 int64_t cand_cap, const void* head_hi, const void* head_lo, int32_t kd,
+                                 const int64_t* row_off, const int32_t* row_cnt, const int32_t* row_term,
+                                 const float* row_w, float tau, mrc_pair* pairs, unsigned long long* count,
+                                 int64_t capacity, int32_t* err) {
+  if ((kd & 63) || kd <= 0) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(int32_t) * 2 * kVerSlots * kVerWarps;
+  const int per_sm = resident_ctas(k_cosine_verify, kVerWarps * 32, smem);
+  if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+  KernelTimer kt(ctx, "cosine_verify");
+  k_cosine_verify<<<(unsigned)(ctx->num_sms * per_sm), kVerWarps * 32, smem, ctx->stream>>>(
+      cand, n_cand, cand_cap, reinterpret_cast<const __half*>(head_hi), reinterpret_cast<const __half*>(head_lo), kd,
+      row_off, row_cnt, row_term, row_w, tau, pairs, count, capacity, err);
   return cudaGetLastError();
 }
 

@@ -216,6 +216,34 @@ def test_cosine_allpairs(torch, M, ctx, orc, tau, weighting):
     idx.free()
 
 
+def test_cosine_allpairs_candidate_overflow_takes_tail_walk(torch, M, ctx, orc):
+    """tau = 0: every one of the 4.5 M pairs of 3,000 documents is a candidate of the bound-pruned
+    path, more than its 2^22-entry buffer, so the call falls back to the exhaustive tail walk.
+    The total must be the oracle's (every pair) and the pairs written must carry the oracle's
+    cosine."""
+    c = synth.make_corpus("tiny", n_docs=3000)
+    V = c.vocab
+    p = Params(k=8)
+    ref = build_index(c.offsets, c.tokens, V, p, orc)
+    idx = M.mrc_build_index(ctx, dev(torch, c.offsets), dev(torch, c.tokens), V, mrc_params(M, p))
+    n = c.n_docs
+    buf, total = M.cosine_allpairs(ctx, idx, dev(torch, c.offsets), dev(torch, c.tokens), 0.0, capacity=1 << 20,
+                                   grow=False)
+    assert total == n * (n - 1) // 2
+    got = M.pairs_to_numpy(buf)
+    assert got.shape[0] == 1 << 20
+    rng = np.random.Generator(np.random.PCG64(5))
+    for x in rng.choice(got.shape[0], 500, replace=False).tolist():
+        i, j, s = int(got["i"][x]), int(got["j"][x]), float(got["score"][x])
+        assert i < j and abs(s - orc.cosine_pair(ref.row_ptr, ref.terms, ref.w, i, j)) <= COS_TOL
+    # tau = 0.6 on the same documents (bound-pruned path) against the oracle
+    a = M.pairs_to_numpy(M.cosine_allpairs(ctx, idx, dev(torch, c.offsets), dev(torch, c.tokens), 0.6)[0])
+    tot, pi, pj, ps = orc.cosine_pairs(ref.row_ptr, ref.terms, ref.w, 0.6)
+    compare_pairs(pair_dict(a["i"], a["j"], a["score"]), pair_dict(pi, pj, ps), 0.6, BAND, COS_TOL,
+                  lambda i, j: orc.cosine_pair(ref.row_ptr, ref.terms, ref.w, i, j))
+    idx.free()
+
+
 def test_simhash_match_bit_exact(torch, M, ctx, orc):
     c = synth.make_corpus("tiny")
     ref_F = orc.simhash(c.offsets, c.tokens, 0x1810030990)
