@@ -924,7 +924,9 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   const int64_t n_head = h_tsum[0], n_post = h_tsum[2];
   const int32_t n_tail = (int32_t)h_tsum[1], n_small = (int32_t)h_tsum[3], max_m = (int32_t)h_tsum[4];
   const double tail_work = (double)h_tsum[5];
-  const int32_t kd = std::max<int32_t>(64, round_up((int32_t)n_head, 64));
+  // head columns, then the kTailBuckets tail-bucket norm columns of the bound-pruned path
+  const int32_t kd_h = std::max<int32_t>(64, round_up((int32_t)n_head, 64));
+  const int32_t kd = kd_h + kTailBuckets;
   if (n_post >= (1ll << 31) - 64)
     return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more than 2^31 tail postings");
   const int64_t ldh = (N + 7) / 8 * 8;
@@ -948,10 +950,12 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   o.row_cnt = d_rcnt;
   o.norm = d_norm;
   o.row_w = d_rw;
-  // The head GEMM's error against the exact head sum is at most: fp16 rounding of both
-  // operands, 2^-10 sum|w_i w_j| <= 2^-10 (unit vectors); FP32 accumulation over kd terms,
-  // kd 2^-23; 2^-12 (the fp16 store of the tail-walk path); plus 1e-4 for subnormal operands
-  // and the FP32 addition of the tail.
+  o.kd_h = kd_h;
+  // The head GEMM's error against the exact sum of its columns is at most: fp16 rounding of
+  // both operands, 2^-10 sum|a_c b_c| <= 2^-10 (each row's columns have norm <= 1: unit head
+  // weights, and bucket norms whose squares add up to the tail's); FP32 accumulation over kd
+  // terms, kd 2^-23; 2^-12 (the fp16 store of the tail-walk path); plus 1e-4 for subnormal
+  // operands and the FP32 addition of the tail.
   const float delta = (float)(std::ldexp(1.0, -10) + std::ldexp(1.0, -12) + (double)kd * std::ldexp(1.0, -23) + 1e-4);
   GemmArgs g{};
   g.fmt = OP_F16;
@@ -962,44 +966,48 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   g.out_scale = 1.0f;
   g.err = async ? ctx->async_err : d_err;
 
-  // Bound-pruned path. A pair's tail dot product is at most tn_i tn_j (Cauchy-Schwarz on the
-  // tail sub-vectors), so a pair whose head score plus tn_i tn_j stays below tau - delta' is
-  // below tau: the head GEMM emits only the other pairs as candidates, and each candidate gets
-  // its exact score (k_cosine_verify). delta' adds to delta the rounding of the tail sum
-  // (at most 2^-31 per shared term, under 3.1e-5 for 65,536 terms) and of the bound itself.
+  // Bound-pruned path. Hash the tail terms into kTailBuckets buckets; by Cauchy-Schwarz in each
+  // bucket a pair's tail dot product is at most sum_s |t_i^s| |t_j^s|, the dot product of the
+  // two documents' bucket-norm vectors. Those norms ride in the head operand's last columns,
+  // so the head GEMM computes head score + bound; a pair below tau - delta' there is below tau,
+  // and the GEMM emits only the other pairs as candidates, each then scored exactly
+  // (k_cosine_verify). delta' adds to delta the rounding of the tail sum (at most 2^-31 per
+  // shared term, under 3.1e-5 for 65,536 terms).
   {
     const int64_t cand_cap = std::max<int64_t>(4 * capacity, 1 << 22);
     int32_t* d_rterm = (int32_t*)ws_get(ctx, "cos.rterm", sizeof(int32_t) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
-    float* d_tn = (float*)ws_get(ctx, "cos.tn", sizeof(float) * (size_t)N, &st);
     mrc_pair* d_cand = (mrc_pair*)ws_get(ctx, "cos.cand", sizeof(mrc_pair) * (size_t)cand_cap, &st);
+    int32_t* d_clong = (int32_t*)ws_get(ctx, "cos.clong", sizeof(int32_t) * (size_t)cand_cap, &st);
+    unsigned long long* d_nlong = (unsigned long long*)ws_get(ctx, "cos.nlong", sizeof(unsigned long long), &st);
     unsigned long long* d_ccount = (unsigned long long*)ws_get(ctx, "cos.ccount", sizeof(unsigned long long), &st);
     if (st != MRC_OK) return st;
     e = cudaMemsetAsync(d_ccount, 0, sizeof(unsigned long long), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cosine set-up");
     o.postings = 0;
     o.row_term = d_rterm;
-    o.tail_norm = d_tn;
     e = launch_densify(ctx, d, V, index->tinfo, o);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "densify");
-    g.tn = d_tn;
     g.thresh = tau - (delta + 4e-5f);
     g.pairs = d_cand;
     g.count = d_ccount;
     g.capacity = cand_cap;
+    g.name = "gemm_f16_bound";
     e = launch_gemm_compare(ctx, g);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "head GEMM");
-    e = launch_cosine_verify(ctx, d_cand, d_ccount, cand_cap, d_hhi, d_hlo, kd, d.offsets, d_rcnt, d_rterm, d_rw, tau,
-                             dst, d_count, capacity, async ? ctx->async_err : d_err);
+    e = launch_cosine_verify(ctx, d_cand, d_ccount, cand_cap, d_hhi, d_hlo, kd, kd_h, d.offsets, d_rcnt, d_rterm, d_rw,
+                             tau, dst, d_count, capacity, d_clong, d_nlong, async ? ctx->async_err : d_err);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "candidate verification");
     if (async) return MRC_OK;  // a candidate overflow is reported by mrc_ctx_sync
     bool overflow = false;
     st = finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs, d_err, d_ccount, cand_cap, &overflow);
     if (!overflow) return st;
-    // too many candidates for the buffer: the exhaustive tail walk below
+    // too many candidates for the buffer: the exhaustive tail walk below (head operands
+    // rebuilt without the bucket columns)
     e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int32_t), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_hhi, 0, 2 * (size_t)N * kd, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cosine set-up");
-    g.tn = nullptr;
+    g.name = nullptr;
   }
 
   // Tail-walk path: the head stored as fp16 scores, the tail postings of each term ordered by
@@ -1020,7 +1028,6 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   o.postings = 1;
   o.post = d_post;
   o.row_term = nullptr;
-  o.tail_norm = nullptr;
   e = launch_densify(ctx, d, V, index->tinfo, o);  // rewrites the same head rows
   if (e != cudaSuccess) return cuda_fail(ctx, e, "densify");
   e = launch_rank_postings(ctx, d_cstart, d_rank_terms, n_small, d_rank_terms + n_small, n_tail - n_small, max_m, d_post,

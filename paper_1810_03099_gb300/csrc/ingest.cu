@@ -85,10 +85,6 @@ __device__ __forceinline__ unsigned long long to_fix(float x) { return __float2u
 __device__ __forceinline__ unsigned long long to_fix40_up(float u) {
   return __double2ull_ru((double)u * (double)u * 1099511627776.0);
 }
-// sqrt of a 2^-40 fixed-point sum, rounded up to float.
-__device__ __forceinline__ float tail_norm_of(unsigned long long n2) {
-  return __double2float_ru(sqrt((double)n2 * (1.0 / 1099511627776.0)) * (1.0 + 1e-12));
-}
 __device__ __forceinline__ float inv_norm_of(unsigned long long norm_q) {
   const float n2 = (float)norm_q * kInvFix;
   return n2 > 0.f ? 1.0f / sqrtf(n2) : 0.f;
@@ -162,6 +158,13 @@ struct IngestParams {
   int32_t* bag_n;
   int32_t bag_write, bag_read;
 };
+
+// Shared-memory 64-bit accumulators per document: SIG, one per reference partition; DENSE in
+// the bound-pruned mode, one per tail bucket.
+template <int MODE>
+__host__ __device__ __forceinline__ int ingest_kq(const IngestParams& p) {
+  return MODE == kSIG ? p.k : (MODE == kDENSE && !p.dense.postings ? kTailBuckets : 0);
+}
 
 // Per-group accumulators of the SIG and DENSE modes.
 struct Acc {
@@ -255,9 +258,19 @@ __device__ __forceinline__ void chunk(const IngestParams& p, uint32_t key, uint3
       p.dense.post[pos] = make_int4((int32_t)doc, __float_as_int(u), r, 0);
     } else {
       p.dense.row_term[row_base + r] = (int32_t)key;
-      a.norm += to_fix40_up(u);  // the document's tail |t|^2, 2^-40 fixed point, rounded up
+      atomicAdd(&num_q[tail_bucket((int32_t)key)], to_fix40_up(u));  // bucket |t|^2, 2^-40 fixed point
     }
   }
+}
+
+// Bound-pruned exact cosine: the document's tail-bucket norms (sqrt of the 2^-40 fixed-point
+// sums) as fp16 head columns kd_h .. kd_h + kTailBuckets - 1 (the split low part stays 0).
+// Threads tid, tid + stride, ... of the document's group write.
+__device__ __forceinline__ void write_bucket_norms(const IngestParams& p, int64_t d, const unsigned long long* num_q,
+                                                   int tid, int stride) {
+  __half* row = reinterpret_cast<__half*>(p.dense.head_hi) + d * (int64_t)p.dense.kd + p.dense.kd_h;
+  for (int q = tid; q < kTailBuckets; q += stride)
+    row[q] = __float2half_rn((float)sqrt((double)num_q[q] * (1.0 / 1099511627776.0)));
 }
 
 // Writes the SIG outputs of one document; called by one full warp.
@@ -366,7 +379,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kq = MODE == kSIG ? p.k : 0;
+  const int kq = ingest_kq<MODE>(p);
   const size_t per_warp = (size_t)kShortSlots * 8 + (size_t)kq * 8 + 16;
   uint8_t* base = smem + per_warp * warp;
   unsigned long long* num_q = reinterpret_cast<unsigned long long*>(base);
@@ -462,10 +475,7 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
       if (lane == 0) p.norm_out[d] = nq;
     }
     if (MODE == kDENSE) {
-      if (!p.dense.postings) {
-        const unsigned long long t2 = warp_sum(a.norm);
-        if (lane == 0) p.dense.tail_norm[d] = tail_norm_of(t2);
-      }
+      if (!p.dense.postings) write_bucket_norms(p, d, num_q, lane, 32);
       if (lane == 0) p.dense.row_cnt[d] = *row_cnt_s;
     }
     __syncwarp();
@@ -521,7 +531,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kLongThreads, 2) k_ingest_long(IngestParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kq = MODE == kSIG ? p.k : 0;
+  const int kq = ingest_kq<MODE>(p);
   unsigned long long* num_q = reinterpret_cast<unsigned long long*>(smem);
   unsigned long long* norm_s = num_q + kq;
   uint32_t* P = reinterpret_cast<uint32_t*>(norm_s + 1);  // [64]
@@ -612,7 +622,7 @@ __global__ void __launch_bounds__(kLongThreads, 2) k_ingest_long(IngestParams p)
                        p.bag_write ? &misc[2] : nullptr);
       }
     }
-    if (MODE == kDFN || (MODE == kDENSE && !p.dense.postings)) {
+    if (MODE == kDFN) {
       const unsigned long long nq = warp_sum(a.norm);
       if (lane == 0) atomicAdd(norm_s, nq);
     }
@@ -624,9 +634,9 @@ __global__ void __launch_bounds__(kLongThreads, 2) k_ingest_long(IngestParams p)
     }
     __syncthreads();
     if (MODE == kSIG && warp == 0) finalize_sig(p, d, len, *norm_s, num_q, P[lane], P[lane + 32], lane);
-    if (MODE == kDENSE && threadIdx.x == 0) {
-      p.dense.row_cnt[d] = misc[1];
-      if (!p.dense.postings) p.dense.tail_norm[d] = tail_norm_of(*norm_s);
+    if (MODE == kDENSE) {
+      if (threadIdx.x == 0) p.dense.row_cnt[d] = misc[1];
+      if (!p.dense.postings) write_bucket_norms(p, d, num_q, threadIdx.x, kLongThreads);
     }
     if (MODE == kDFN && threadIdx.x == 0) p.norm_out[d] = *norm_s;
     if (p.bag_write && threadIdx.x == 0) p.bag_n[d] = misc[2];
@@ -784,7 +794,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   p.long_cursor = counts + kCntLongCursor;
   p.short_cursor = counts + kCntShortCursor;
   p.err = d.err;
-  const int kq = MODE == kSIG ? p.k : 0;
+  const int kq = ingest_kq<MODE>(p);
   const size_t s_smem = short_smem(kq), l_smem = long_smem(kq);
   const double tokens = (double)d.n_tokens;
   cudaEvent_t ev = nullptr;

@@ -203,11 +203,15 @@ struct DenseOut {
   const unsigned long long* norm;  // [n] squared norms, 2^-22 fixed point (from launch_df_norm)
   // postings == 1: tail postings (tail_start, tail_fill, post) for the tail walk. postings == 0
   // (bound-pruned exact cosine): instead each document's tail term ids (row_term, beside row_w)
-  // and its tail norm |t_d| (tail_norm, rounded up).
+  // and, in head columns kd_h .. kd_h + kTailBuckets - 1, the norms of its tail weights in each
+  // of kTailBuckets hash buckets of the term ids (so the head GEMM also sums the bound).
   int32_t postings;
   int32_t* row_term;          // [n_tokens] at the doc's token offsets: id of its r-th tail term
-  float* tail_norm;           // [n] sqrt(sum of the document's tail u^2), rounded up
+  int32_t kd_h;               // head columns proper (a multiple of 64; kd_h + kTailBuckets <= kd)
 };
+constexpr int kTailBuckets = 64;
+// Bucket of a tail term id (the top 6 bits of a multiplicative hash).
+__host__ __device__ inline int32_t tail_bucket(int32_t t) { return (int32_t)(((uint32_t)t * 0x9E3779B1u) >> 26); }
 cudaError_t launch_densify(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo, const DenseOut& out);
 
 // compare_tc.cu
@@ -234,9 +238,7 @@ struct GemmArgs {
   int64_t ld;
   int32_t tile_n;       // compare tile width for small K: 128, 256 or 0 (default)
   int32_t* err;         // device error word
-  // bound-pruned exact cosine (streaming kernel, triangle): a pair is a candidate when
-  // acc + tn[i] * tn[j] >= thresh (tn: the documents' tail norms); NULL otherwise
-  const float* tn;
+  const char* name;     // timing name (NULL: by format and epilogue)
 };
 cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g);
 
@@ -269,10 +271,10 @@ cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int3
 // Exact scores of the bound-pruned candidates (see k_cosine_verify); pairs with score >= tau
 // go to pairs/count; a candidate count above cand_cap sets kErrOverflow in err.
 cudaError_t launch_cosine_verify(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand,
-                                 int64_t cand_cap, const void* head_hi, const void* head_lo, int32_t kd,
+                                 int64_t cand_cap, const void* head_hi, const void* head_lo, int32_t ld, int32_t kd,
                                  const int64_t* row_off, const int32_t* row_cnt, const int32_t* row_term,
                                  const float* row_w, float tau, mrc_pair* pairs, unsigned long long* count,
-                                 int64_t capacity, int32_t* err);
+                                 int64_t capacity, int32_t* long_idx, unsigned long long* n_long, int32_t* err);
 cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t ldh, const int64_t* row_off,
                                const int32_t* row_cnt, const void* row_walk, const float* row_w, const void* spost,
                                int64_t n_postings, const void* head_hi, const void* head_lo,

@@ -535,12 +535,13 @@ constexpr int kVerBatch = 8;     // list entries per lane loaded at once
 
 // Exact head from the split rows with all of a lane's loads for two 256-column steps in flight;
 // the same sum, in the same order, as exact_head.
+// Columns [0, kd) of rows of stride ld.
 __device__ __forceinline__ float exact_head_batched(const __half* __restrict__ hhi, const __half* __restrict__ hlo,
-                                                    int32_t kd, int64_t i, int64_t j, int lane) {
-  const __half* ai = hhi + i * kd;
-  const __half* bi = hlo + i * kd;
-  const __half* aj = hhi + j * kd;
-  const __half* bj = hlo + j * kd;
+                                                    int32_t ld, int32_t kd, int64_t i, int64_t j, int lane) {
+  const __half* ai = hhi + i * ld;
+  const __half* bi = hlo + i * ld;
+  const __half* aj = hhi + j * ld;
+  const __half* bj = hlo + j * ld;
   float s = 0.f;
   for (int32_t c0 = 8 * lane; c0 < kd; c0 += 512) {
     uint4 xa[2], xb[2], ya[2], yb[2];
@@ -575,11 +576,89 @@ __device__ __forceinline__ float exact_head_batched(const __half* __restrict__ h
   return warp_sum(s);
 }
 
-__global__ void __launch_bounds__(kVerWarps * 32) k_cosine_verify(
+// One (term, weight) batch of a tail list: kVerBatch entries per thread, loads all in flight.
+struct ListBatch {
+  int32_t t[kVerBatch];
+  float w[kVerBatch];
+};
+__device__ __forceinline__ void load_batch(ListBatch& b, const int32_t* __restrict__ row_term,
+                                           const float* __restrict__ row_w, int64_t off, int32_t n, int32_t x0,
+                                           int stride, int tid) {
+#pragma unroll
+  for (int u = 0; u < kVerBatch; ++u) {
+    const int32_t x = x0 + stride * u + tid;
+    b.t[u] = x < n ? __ldg(row_term + off + x) : -1;
+    b.w[u] = x < n ? __ldg(row_w + off + x) : 0.f;
+  }
+}
+// Inserts a batch's terms (of partition ps of 2^lp) into a table of `slots` entries (linear
+// probing; a full table gives up and records kErrTable).
+__device__ __forceinline__ void insert_batch(const ListBatch& b, int32_t* keys, float* vals, int slots, int lslots,
+                                             int lp, int32_t ps, int32_t* err) {
+#pragma unroll
+  for (int u = 0; u < kVerBatch; ++u) {
+    const int32_t t = b.t[u];
+    if (t < 0 || (lp > 0 && (int32_t)(((uint32_t)t * 0x9E3779B1u) >> (32 - lp)) != ps)) continue;
+    uint32_t slot = ((uint32_t)t * 0x85EBCA6Bu) >> (32 - lslots);
+    for (int probes = 0;; ++probes) {
+      if (atomicCAS(&keys[slot], -1, t) == -1) {
+        vals[slot] = b.w[u];
+        break;
+      }
+      slot = (slot + 1) & (slots - 1);
+      if (probes + 1 == slots) {
+        set_err(err, kErrTable);
+        break;
+      }
+    }
+  }
+}
+// Adds round((w_i 2^30) w_j) for the batch's terms found in the table (the table holds the
+// weights of document i when i_small, else of document j).
+__device__ __forceinline__ long long probe_batch(const ListBatch& b, const int32_t* keys, const float* vals, int slots,
+                                                 int lslots, int lp, int32_t ps, bool i_small) {
+  long long acc = 0;
+#pragma unroll
+  for (int u = 0; u < kVerBatch; ++u) {
+    const int32_t t = b.t[u];
+    if (t < 0 || (lp > 0 && (int32_t)(((uint32_t)t * 0x9E3779B1u) >> (32 - lp)) != ps)) continue;
+    uint32_t slot = ((uint32_t)t * 0x85EBCA6Bu) >> (32 - lslots);
+    for (int probes = 0; probes < slots; ++probes) {
+      const int32_t k = keys[slot];
+      if (k == t) {
+        const float ws = vals[slot];
+        const float wi = i_small ? ws : b.w[u], wj = i_small ? b.w[u] : ws;
+        acc += __float2int_rn((wi * kTailFix) * wj);
+        break;
+      }
+      if (k == -1) break;
+      slot = (slot + 1) & (slots - 1);
+    }
+  }
+  return acc;
+}
+__device__ __forceinline__ void emit_verified(float s, float tau, int32_t i, int32_t j, mrc_pair* pairs,
+                                              unsigned long long* count, int64_t capacity) {
+  if (s >= tau) {
+    const unsigned long long at = atomicAdd(count, 1ull);
+    if (at < (unsigned long long)capacity) {
+      mrc_pair pr;
+      pr.i = i;
+      pr.j = j;
+      pr.score = s;
+      pairs[at] = pr;
+    }
+  }
+}
+
+// Warp per candidate whose shorter tail list fits a quarter of the warp's table (one pass);
+// the others are appended to long_idx for k_cosine_verify_long.
+__global__ void __launch_bounds__(kVerWarps * 32, 3) k_cosine_verify(
     const mrc_pair* __restrict__ cand, const unsigned long long* __restrict__ n_cand, int64_t cand_cap,
-    const __half* __restrict__ hhi, const __half* __restrict__ hlo, int32_t kd, const int64_t* __restrict__ row_off,
-    const int32_t* __restrict__ row_cnt, const int32_t* __restrict__ row_term, const float* __restrict__ row_w,
-    float tau, mrc_pair* pairs, unsigned long long* count, int64_t capacity, int32_t* err) {
+    const __half* __restrict__ hhi, const __half* __restrict__ hlo, int32_t ld, int32_t kd,
+    const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_cnt, const int32_t* __restrict__ row_term,
+    const float* __restrict__ row_w, float tau, mrc_pair* pairs, unsigned long long* count, int64_t capacity,
+    int32_t* long_idx, unsigned long long* n_long, int32_t* err) {
   extern __shared__ __align__(16) int32_t vsm[];  // [kVerWarps][kVerSlots keys + kVerSlots weights]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* keys = vsm + warp * 2 * kVerSlots;
@@ -593,86 +672,88 @@ __global__ void __launch_bounds__(kVerWarps * 32) k_cosine_verify(
     const int32_t i = pc.i, j = pc.j;
     const int32_t ni = row_cnt[i], nj = row_cnt[j];
     const bool i_small = ni <= nj;
-    const int64_t os = row_off[i_small ? i : j], ol = row_off[i_small ? j : i];
     const int32_t ns = i_small ? ni : nj, nl = i_small ? nj : ni;
-    // passes: a power of two with at most about a quarter table per pass
-    int lp = 0;
-    while ((ns >> lp) > kVerSlots / 4) ++lp;
-    const int32_t passes = ns > 0 ? 1 << lp : 0;
+    if (ns > kVerSlots / 4) {
+      if (lane == 0) long_idx[atomicAdd(n_long, 1ull)] = (int32_t)c;
+      continue;
+    }
+    const int64_t os = row_off[i_small ? i : j], ol = row_off[i_small ? j : i];
     long long acc = 0;
-    for (int32_t ps = 0; ps < passes; ++ps) {
+    if (ns > 0) {
+      ListBatch b;
+      load_batch(b, row_term, row_w, os, ns, 0, 32, lane);  // ns <= 32 * kVerBatch
       for (int x = 4 * lane; x < kVerSlots; x += 128) *reinterpret_cast<int4*>(keys + x) = make_int4(-1, -1, -1, -1);
       __syncwarp();
-      for (int32_t x0 = 0; x0 < ns; x0 += 32 * kVerBatch) {
-        int32_t tv[kVerBatch];
-        float wv[kVerBatch];
-#pragma unroll
-        for (int u = 0; u < kVerBatch; ++u) {
-          const int32_t x = x0 + 32 * u + lane;
-          tv[u] = x < ns ? __ldg(row_term + os + x) : -1;
-          wv[u] = x < ns ? __ldg(row_w + os + x) : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < kVerBatch; ++u) {
-          const int32_t t = tv[u];
-          if (t < 0 || (lp > 0 && (int32_t)(((uint32_t)t * 0x9E3779B1u) >> (32 - lp)) != ps)) continue;
-          uint32_t slot = ((uint32_t)t * 0x85EBCA6Bu) >> (32 - 10);
-          for (int probes = 0;; ++probes) {
-            if (atomicCAS(&keys[slot], -1, t) == -1) {
-              vals[slot] = wv[u];
-              break;
-            }
-            slot = (slot + 1) & (kVerSlots - 1);
-            if (probes + 1 == kVerSlots) {  // table full (cannot happen below a quarter load): give up
-              set_err(err, kErrTable);
-              break;
-            }
-          }
-        }
-      }
+      insert_batch(b, keys, vals, kVerSlots, 10, 0, 0, err);
       __syncwarp();
       for (int32_t y0 = 0; y0 < nl; y0 += 32 * kVerBatch) {
-        int32_t tv[kVerBatch];
-        float wv[kVerBatch];
-#pragma unroll
-        for (int u = 0; u < kVerBatch; ++u) {
-          const int32_t y = y0 + 32 * u + lane;
-          tv[u] = y < nl ? __ldg(row_term + ol + y) : -1;
-          wv[u] = y < nl ? __ldg(row_w + ol + y) : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < kVerBatch; ++u) {
-          const int32_t t = tv[u];
-          if (t < 0 || (lp > 0 && (int32_t)(((uint32_t)t * 0x9E3779B1u) >> (32 - lp)) != ps)) continue;
-          uint32_t slot = ((uint32_t)t * 0x85EBCA6Bu) >> (32 - 10);
-          for (int probes = 0; probes < kVerSlots; ++probes) {
-            const int32_t k = keys[slot];
-            if (k == t) {
-              const float ws = vals[slot];
-              const float wi = i_small ? ws : wv[u], wj = i_small ? wv[u] : ws;
-              acc += __float2int_rn((wi * kTailFix) * wj);
-              break;
-            }
-            if (k == -1) break;
-            slot = (slot + 1) & (kVerSlots - 1);
-          }
-        }
+        load_batch(b, row_term, row_w, ol, nl, y0, 32, lane);
+        acc += probe_batch(b, keys, vals, kVerSlots, 10, 0, 0, i_small);
       }
       __syncwarp();
     }
-    const float head = exact_head_batched(hhi, hlo, kd, i, j, lane);
+    const float head = exact_head_batched(hhi, hlo, ld, kd, i, j, lane);
     const long long tail = warp_sum(acc);
-    const float s = head + (float)tail * kTailInv;
-    if (lane == 0 && s >= tau) {
-      const unsigned long long at = atomicAdd(count, 1ull);
-      if (at < (unsigned long long)capacity) {
-        mrc_pair pr;
-        pr.i = i;
-        pr.j = j;
-        pr.score = s;
-        pairs[at] = pr;
+    if (lane == 0) emit_verified(head + (float)tail * kTailInv, tau, i, j, pairs, count, capacity);
+  }
+}
+
+// CTA per candidate with a long shorter list: the CTA's whole table (kVerWarps * kVerSlots
+// slots), a quarter of it per hash-partitioned pass. The head comes from warp 0 (the same sum
+// as every other path).
+__global__ void __launch_bounds__(kVerWarps * 32, 3) k_cosine_verify_long(
+    const mrc_pair* __restrict__ cand, const int32_t* __restrict__ long_idx, const unsigned long long* __restrict__ n_long,
+    const __half* __restrict__ hhi, const __half* __restrict__ hlo, int32_t ld, int32_t kd,
+    const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_cnt, const int32_t* __restrict__ row_term,
+    const float* __restrict__ row_w, float tau, mrc_pair* pairs, unsigned long long* count, int64_t capacity,
+    int32_t* err) {
+  constexpr int kSlots = kVerWarps * kVerSlots, kLog = 13;  // 8192 slots
+  static_assert((1 << kLog) == kSlots, "table size");
+  extern __shared__ __align__(16) int32_t vsm[];
+  int32_t* keys = vsm;
+  float* vals = reinterpret_cast<float*>(keys + kSlots);
+  __shared__ unsigned long long s_tail;
+  __shared__ float s_head;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nl_total = (int64_t)*n_long;
+  for (int64_t q = blockIdx.x; q < nl_total; q += gridDim.x) {
+    const mrc_pair pc = cand[long_idx[q]];
+    const int32_t i = pc.i, j = pc.j;
+    const int32_t ni = row_cnt[i], nj = row_cnt[j];
+    const bool i_small = ni <= nj;
+    const int64_t os = row_off[i_small ? i : j], ol = row_off[i_small ? j : i];
+    const int32_t ns = i_small ? ni : nj, nl = i_small ? nj : ni;
+    int lp = 0;
+    while ((ns >> lp) > kSlots / 4) ++lp;
+    const int32_t passes = 1 << lp;
+    if (threadIdx.x == 0) s_tail = 0ull;
+    long long acc = 0;
+    for (int32_t ps = 0; ps < passes; ++ps) {
+      __syncthreads();  // the previous pass's probes (and s_tail's reset) are done
+      for (int x = 4 * (int)threadIdx.x; x < kSlots; x += 4 * kVerWarps * 32)
+        *reinterpret_cast<int4*>(keys + x) = make_int4(-1, -1, -1, -1);
+      __syncthreads();
+      ListBatch b;
+      for (int32_t x0 = 0; x0 < ns; x0 += kVerWarps * 32 * kVerBatch) {
+        load_batch(b, row_term, row_w, os, ns, x0, kVerWarps * 32, threadIdx.x);
+        insert_batch(b, keys, vals, kSlots, kLog, lp, ps, err);
+      }
+      __syncthreads();
+      for (int32_t y0 = 0; y0 < nl; y0 += kVerWarps * 32 * kVerBatch) {
+        load_batch(b, row_term, row_w, ol, nl, y0, kVerWarps * 32, threadIdx.x);
+        acc += probe_batch(b, keys, vals, kSlots, kLog, lp, ps, i_small);
       }
     }
+    const long long wsum = warp_sum(acc);
+    if (lane == 0) atomicAdd(&s_tail, (unsigned long long)wsum);
+    if (warp == 0) {
+      const float h = exact_head_batched(hhi, hlo, ld, kd, i, j, lane);
+      if (lane == 0) s_head = h;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      emit_verified(s_head + (float)(long long)s_tail * kTailInv, tau, i, j, pairs, count, capacity);
+    __syncthreads();  // s_tail, s_head and the table are reused by the next candidate
   }
 }
 
@@ -755,18 +836,28 @@ cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int3
 }
 
 cudaError_t launch_cosine_verify(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand,
-                                 int64_t cand_cap, const void* head_hi, const void* head_lo, int32_t kd,
+                                 int64_t cand_cap, const void* head_hi, const void* head_lo, int32_t ld, int32_t kd,
                                  const int64_t* row_off, const int32_t* row_cnt, const int32_t* row_term,
                                  const float* row_w, float tau, mrc_pair* pairs, unsigned long long* count,
-                                 int64_t capacity, int32_t* err) {
-  if ((kd & 63) || kd <= 0) return cudaErrorInvalidValue;
+                                 int64_t capacity, int32_t* long_idx, unsigned long long* n_long, int32_t* err) {
+  if ((kd & 63) || kd <= 0 || (ld & 7) || ld < kd) return cudaErrorInvalidValue;
   const size_t smem = sizeof(int32_t) * 2 * kVerSlots * kVerWarps;
   const int per_sm = resident_ctas(k_cosine_verify, kVerWarps * 32, smem);
-  if (per_sm <= 0) return cudaErrorInvalidConfiguration;
-  KernelTimer kt(ctx, "cosine_verify");
-  k_cosine_verify<<<(unsigned)(ctx->num_sms * per_sm), kVerWarps * 32, smem, ctx->stream>>>(
-      cand, n_cand, cand_cap, reinterpret_cast<const __half*>(head_hi), reinterpret_cast<const __half*>(head_lo), kd,
-      row_off, row_cnt, row_term, row_w, tau, pairs, count, capacity, err);
+  const int per_sm_long = resident_ctas(k_cosine_verify_long, kVerWarps * 32, smem);
+  if (per_sm <= 0 || per_sm_long <= 0) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaMemsetAsync(n_long, 0, sizeof(unsigned long long), ctx->stream);
+  if (e != cudaSuccess) return e;
+  const __half* hi = reinterpret_cast<const __half*>(head_hi);
+  const __half* lo = reinterpret_cast<const __half*>(head_lo);
+  {
+    KernelTimer kt(ctx, "cosine_verify");
+    k_cosine_verify<<<(unsigned)(ctx->num_sms * per_sm), kVerWarps * 32, smem, ctx->stream>>>(
+        cand, n_cand, cand_cap, hi, lo, ld, kd, row_off, row_cnt, row_term, row_w, tau, pairs, count, capacity,
+        long_idx, n_long, err);
+  }
+  KernelTimer kt(ctx, "cosine_verify_long");
+  k_cosine_verify_long<<<(unsigned)(ctx->num_sms * per_sm_long), kVerWarps * 32, smem, ctx->stream>>>(
+      cand, long_idx, n_long, hi, lo, ld, kd, row_off, row_cnt, row_term, row_w, tau, pairs, count, capacity, err);
   return cudaGetLastError();
 }
 
