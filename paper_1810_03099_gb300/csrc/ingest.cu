@@ -80,10 +80,10 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 __device__ __forceinline__ unsigned long long to_fix(float x) { return __float2ull_rn(x * kFix); }
 
 // 1 / |w| from the fixed-point squared norm (0 for an empty document).
-// u^2 in 2^-40 fixed point, rounded up (u <= 1: at most 2^40 per term); the product of two
-// floats is exact in double.
+// u^2 in 2^-40 fixed point, rounded up (u <= 1: at most 2^40 per term); FP32 with directed
+// rounding (the power-of-two scaling is exact), so the bucket norms bound from above.
 __device__ __forceinline__ unsigned long long to_fix40_up(float u) {
-  return __double2ull_ru((double)u * (double)u * 1099511627776.0);
+  return __float2ull_ru(__fmul_ru(u, u) * 1099511627776.0f);
 }
 __device__ __forceinline__ float inv_norm_of(unsigned long long norm_q) {
   const float n2 = (float)norm_q * kInvFix;
@@ -270,7 +270,7 @@ __device__ __forceinline__ void write_bucket_norms(const IngestParams& p, int64_
                                                    int tid, int stride) {
   __half* row = reinterpret_cast<__half*>(p.dense.head_hi) + d * (int64_t)p.dense.kd + p.dense.kd_h;
   for (int q = tid; q < kTailBuckets; q += stride)
-    row[q] = __float2half_rn((float)sqrt((double)num_q[q] * (1.0 / 1099511627776.0)));
+    row[q] = __float2half_rn(__fsqrt_ru(__ull2float_ru(num_q[q]) * (1.0f / 1099511627776.0f)));
 }
 
 // Writes the SIG outputs of one document; called by one full warp.

@@ -651,8 +651,9 @@ __device__ __forceinline__ void emit_verified(float s, float tau, int32_t i, int
   }
 }
 
-// Warp per candidate whose shorter tail list fits a quarter of the warp's table (one pass);
-// the others are appended to long_idx for k_cosine_verify_long.
+// Warp per candidate whose shorter tail list fits a quarter of the warp's table (one pass) and
+// whose longer list takes at most two probe batches; the others are appended to long_idx for
+// k_cosine_verify_long.
 __global__ void __launch_bounds__(kVerWarps * 32, 3) k_cosine_verify(
     const mrc_pair* __restrict__ cand, const unsigned long long* __restrict__ n_cand, int64_t cand_cap,
     const __half* __restrict__ hhi, const __half* __restrict__ hlo, int32_t ld, int32_t kd,
@@ -673,7 +674,7 @@ __global__ void __launch_bounds__(kVerWarps * 32, 3) k_cosine_verify(
     const int32_t ni = row_cnt[i], nj = row_cnt[j];
     const bool i_small = ni <= nj;
     const int32_t ns = i_small ? ni : nj, nl = i_small ? nj : ni;
-    if (ns > kVerSlots / 4) {
+    if (ns > kVerSlots / 4 || nl > kVerSlots / 2) {  // more than one table pass or two probe batches
       if (lane == 0) long_idx[atomicAdd(n_long, 1ull)] = (int32_t)c;
       continue;
     }
