@@ -660,21 +660,25 @@ constexpr int kCntClass = 8, kCntClassFill = 16, kCntWords = 32;
 // length class); validates offsets.
 __global__ void k_classify(const int64_t* off, int64_t n, int32_t* short_list, int32_t* counts, int32_t* err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
   if (i == 0 && off[0] != 0) set_err(err, kErrBadOffsets);
-  if (i >= n) return;
-  const int64_t len = off[i + 1] - off[i];
-  if (len < 0) {
-    set_err(err, kErrBadOffsets);
-    return;
-  }
-  if (len > MRC_MAX_DOC_TOKENS) {
-    set_err(err, kErrTooLong);
-    return;
-  }
-  atomicMax(&counts[kCntMaxLen], (int32_t)len);
-  if (len <= kShortMax) {
-    short_list[atomicAdd(&counts[kCntShort], 1)] = (int32_t)i;
-  } else {
+  int64_t len = i < n ? off[i + 1] - off[i] : 0;
+  if (i < n && len < 0) set_err(err, kErrBadOffsets);
+  if (i < n && len > MRC_MAX_DOC_TOKENS) set_err(err, kErrTooLong);
+  const bool ok = i < n && len >= 0 && len <= MRC_MAX_DOC_TOKENS;
+  if (!ok) len = 0;
+  // one atomic per warp for the longest length and for the short-list appends
+  int32_t mx = (int32_t)len;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+  if (lane == 0 && mx > 0) atomicMax(&counts[kCntMaxLen], mx);
+  const bool is_short = ok && len <= kShortMax;
+  const unsigned sm = __ballot_sync(kFull, is_short);
+  int32_t base = 0;
+  if (lane == 0 && sm) base = atomicAdd(&counts[kCntShort], __popc(sm));
+  base = __shfl_sync(kFull, base, 0);
+  if (is_short) short_list[base + __popc(sm & ((1u << lane) - 1u))] = (int32_t)i;
+  if (ok && !is_short) {
     atomicAdd(&counts[kCntLong], 1);
     atomicAdd(&counts[kCntClass + len_class(len)], 1);
   }
