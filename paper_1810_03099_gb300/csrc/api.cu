@@ -889,11 +889,9 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), ctx->stream);
   if (N < 2) return async ? MRC_OK : finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
 
-  // document frequencies within these documents decide the head/tail split: head = terms
-  // whose postings are dense enough that a tensor-core column beats sparse products,
-  // df >= max(32, N / 48) (capped so that tail lists stay <= 4096 postings); tail = the
-  // other terms with df >= 2. The split is computed on the device; only its totals come back.
-  const int32_t cut = (int32_t)std::min<int64_t>(std::max<int64_t>(32, N / 48), 4097);
+  // Document frequencies within these documents decide the head/tail split: head = terms of
+  // df >= cut (dense tensor-core columns), tail = the other terms with df >= 2 (a term in one
+  // document joins no pair). The split is computed on the device; only its totals come back.
   const int64_t n_tblocks = ((int64_t)V + 1023) / 1024;
   int32_t* df = (int32_t*)ws_get(ctx, "cos.df", sizeof(int32_t) * V, &st);
   unsigned long long* d_norm = (unsigned long long*)ws_get(ctx, "cos.norm", sizeof(unsigned long long) * N, &st);
@@ -904,9 +902,10 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   int32_t* d_rank_terms = (int32_t*)ws_get(ctx, "cos.rterms", sizeof(int32_t) * (size_t)V, &st);
   long long* d_tpart = (long long*)ws_get(ctx, "cos.tpart", sizeof(long long) * 8 * (size_t)n_tblocks, &st);
   long long* d_tsum = (long long*)ws_get(ctx, "cos.tsum", sizeof(long long) * 8, &st);
+  int32_t* d_rcnt = (int32_t*)ws_get(ctx, "cos.rcnt", sizeof(int32_t) * (size_t)N, &st);
+  float* d_rw = (float*)ws_get(ctx, "cos.rw", sizeof(float) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
   if (st != MRC_OK) return st;
   cudaMemsetAsync(df, 0, sizeof(int32_t) * V, ctx->stream);
-  cudaMemsetAsync(d_cstart, 0, sizeof(int64_t), ctx->stream);
   const float* wid = index->params.weighting == MRC_WEIGHT_TFIDF ? index->idf : nullptr;
   attach_bag(ctx, &d);
   d.bag_write = 1;
@@ -915,56 +914,38 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   d.bag_read = 1;
   d.lists_ready = 1;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "df pass");
-  e = launch_cosine_terms(ctx, df, V, cut, d_tpart, d_tsum, d_colmap, d_tstart, d_cstart, d_rank_terms);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "head/tail split");
   long long* h_tsum = (long long*)((char*)ctx->pinned + 1024);
-  e = cudaMemcpyAsync(h_tsum, d_tsum, sizeof(long long) * 6, cudaMemcpyDeviceToHost, ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the head/tail split");
-  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;  // synchronises the stream
-  const int64_t n_head = h_tsum[0], n_post = h_tsum[2];
-  const int32_t n_tail = (int32_t)h_tsum[1], n_small = (int32_t)h_tsum[3], max_m = (int32_t)h_tsum[4];
-  const double tail_work = (double)h_tsum[5];
-  // head columns, then the kTailBuckets tail-bucket norm columns of the bound-pruned path
-  const int32_t kd_h = std::max<int32_t>(64, round_up((int32_t)n_head, 64));
-  const int32_t kd = kd_h + kTailBuckets;
-  if (n_post >= (1ll << 31) - 64)
-    return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more than 2^31 tail postings");
-  const int64_t ldh = (N + 7) / 8 * 8;
-  int32_t* d_rcnt = (int32_t*)ws_get(ctx, "cos.rcnt", sizeof(int32_t) * (size_t)N, &st);
-  float* d_rw = (float*)ws_get(ctx, "cos.rw", sizeof(float) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
-  void* d_hhi = ws_get(ctx, "cos.hhi", 2 * (size_t)N * kd, &st);
-  void* d_hlo = ws_get(ctx, "cos.hlo", 2 * (size_t)N * kd, &st);
-  if (st != MRC_OK) return st;
-  e = cudaMemsetAsync(d_hhi, 0, 2 * (size_t)N * kd, ctx->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_hlo, 0, 2 * (size_t)N * kd, ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "cosine set-up");
-  // unit weights: dense head operands, and per document its tail terms (and postings or norms)
+  // runs the split for `cut` and reads its totals (one synchronisation, with the error word)
+  auto split = [&](int32_t cut) -> mrc_status {
+    cudaError_t se = cudaMemsetAsync(d_cstart, 0, sizeof(int64_t), ctx->stream);
+    if (se == cudaSuccess)
+      se = launch_cosine_terms(ctx, df, V, cut, d_tpart, d_tsum, d_colmap, d_tstart, d_cstart, d_rank_terms);
+    if (se == cudaSuccess) se = cudaMemcpyAsync(h_tsum, d_tsum, sizeof(long long) * 6, cudaMemcpyDeviceToHost, ctx->stream);
+    if (se != cudaSuccess) return cuda_fail(ctx, se, "head/tail split");
+    return check_err_word(ctx, d_err);  // synchronises the stream
+  };
   DenseOut o{};
   o.idf = wid;
   o.colmap = d_colmap;
-  o.kd = kd;
-  o.head_hi = d_hhi;
-  o.head_lo = d_hlo;
   o.tail_start = d_tstart;
   o.tail_fill = d_tfill;
   o.row_cnt = d_rcnt;
   o.norm = d_norm;
   o.row_w = d_rw;
-  o.kd_h = kd_h;
+  GemmArgs g{};
+  g.fmt = OP_F16;
+  g.na = g.nb = N;
+  g.triangle = 1;
+  g.out_scale = 1.0f;
+  g.err = async ? ctx->async_err : d_err;
   // The head GEMM's error against the exact sum of its columns is at most: fp16 rounding of
   // both operands, 2^-10 sum|a_c b_c| <= 2^-10 (each row's columns have norm <= 1: unit head
   // weights, and bucket norms whose squares add up to the tail's); FP32 accumulation over kd
   // terms, kd 2^-23; 2^-12 (the fp16 store of the tail-walk path); plus 1e-4 for subnormal
   // operands and the FP32 addition of the tail.
-  const float delta = (float)(std::ldexp(1.0, -10) + std::ldexp(1.0, -12) + (double)kd * std::ldexp(1.0, -23) + 1e-4);
-  GemmArgs g{};
-  g.fmt = OP_F16;
-  g.a_hi = g.b_hi = d_hhi;
-  g.na = g.nb = N;
-  g.kbytes = kd * 2;
-  g.triangle = 1;
-  g.out_scale = 1.0f;
-  g.err = async ? ctx->async_err : d_err;
+  auto delta_of = [](int32_t kd) {
+    return (float)(std::ldexp(1.0, -10) + std::ldexp(1.0, -12) + (double)kd * std::ldexp(1.0, -23) + 1e-4);
+  };
 
   // Bound-pruned path. Hash the tail terms into kTailBuckets buckets; by Cauchy-Schwarz in each
   // bucket a pair's tail dot product is at most sum_s |t_i^s| |t_j^s|, the dot product of the
@@ -972,22 +953,36 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   // so the head GEMM computes head score + bound; a pair below tau - delta' there is below tau,
   // and the GEMM emits only the other pairs as candidates, each then scored exactly
   // (k_cosine_verify). delta' adds to delta the rounding of the tail sum (at most 2^-31 per
-  // shared term, under 3.1e-5 for 65,536 terms).
+  // shared term, under 3.1e-5 for 65,536 terms). The bucket columns make a looser head cheap:
+  // head = df >= max(32, N / 8).
   {
+    if ((st = split((int32_t)std::min<int64_t>(std::max<int64_t>(32, N / 8), INT32_MAX))) != MRC_OK) return st;
+    const int32_t kd_h = round_up((int32_t)h_tsum[0], 64);  // may be 0
+    const int32_t kd = kd_h + kTailBuckets;
     const int64_t cand_cap = std::max<int64_t>(4 * capacity, 1 << 22);
+    void* d_hhi = ws_get(ctx, "cos.hhi", 2 * (size_t)N * kd, &st);
+    void* d_hlo = ws_get(ctx, "cos.hlo", 2 * (size_t)N * kd, &st);
     int32_t* d_rterm = (int32_t*)ws_get(ctx, "cos.rterm", sizeof(int32_t) * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
     mrc_pair* d_cand = (mrc_pair*)ws_get(ctx, "cos.cand", sizeof(mrc_pair) * (size_t)cand_cap, &st);
     int32_t* d_clong = (int32_t*)ws_get(ctx, "cos.clong", sizeof(int32_t) * (size_t)cand_cap, &st);
     unsigned long long* d_nlong = (unsigned long long*)ws_get(ctx, "cos.nlong", sizeof(unsigned long long), &st);
     unsigned long long* d_ccount = (unsigned long long*)ws_get(ctx, "cos.ccount", sizeof(unsigned long long), &st);
     if (st != MRC_OK) return st;
-    e = cudaMemsetAsync(d_ccount, 0, sizeof(unsigned long long), ctx->stream);
+    e = cudaMemsetAsync(d_hhi, 0, 2 * (size_t)N * kd, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_hlo, 0, 2 * (size_t)N * kd, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_ccount, 0, sizeof(unsigned long long), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cosine set-up");
+    o.kd = kd;
+    o.kd_h = kd_h;
+    o.head_hi = d_hhi;
+    o.head_lo = d_hlo;
     o.postings = 0;
     o.row_term = d_rterm;
     e = launch_densify(ctx, d, V, index->tinfo, o);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "densify");
-    g.thresh = tau - (delta + 4e-5f);
+    g.a_hi = g.b_hi = d_hhi;
+    g.kbytes = kd * 2;
+    g.thresh = tau - (delta_of(kd) + 4e-5f);
     g.pairs = d_cand;
     g.count = d_ccount;
     g.capacity = cand_cap;
@@ -1001,22 +996,29 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
     bool overflow = false;
     st = finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs, d_err, d_ccount, cand_cap, &overflow);
     if (!overflow) return st;
-    // too many candidates for the buffer: the exhaustive tail walk below (head operands
-    // rebuilt without the bucket columns)
+    // too many candidates for the buffer: the exhaustive tail walk below
     e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int32_t), ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_hhi, 0, 2 * (size_t)N * kd, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cosine set-up");
-    g.name = nullptr;
   }
 
-  // Tail-walk path: the head stored as fp16 scores, the tail postings of each term ordered by
-  // document, each row's tail products summed over the postings after it, candidates against
-  // tau - delta, exact head for each candidate.
+  // Tail-walk path: head = df >= max(32, N / 48), the break-even of a tensor-core column
+  // against sparse products (capped so that tail lists stay <= 4096 postings); the head stored
+  // as fp16 scores, the tail postings of each term ordered by document, each row's tail
+  // products summed over the postings after it, candidates against tau - delta, exact head
+  // for each candidate.
+  if ((st = split((int32_t)std::min<int64_t>(std::max<int64_t>(32, N / 48), 4097))) != MRC_OK) return st;
+  const int64_t n_head = h_tsum[0], n_post = h_tsum[2];
+  const int32_t n_tail = (int32_t)h_tsum[1], n_small = (int32_t)h_tsum[3], max_m = (int32_t)h_tsum[4];
+  const double tail_work = (double)h_tsum[5];
+  const int32_t kd = std::max<int32_t>(64, round_up((int32_t)n_head, 64));
+  const int64_t ldh = (N + 7) / 8 * 8;
   if (n_post >= (1ll << 31) - 64)
     return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more than 2^31 tail postings");
   if ((double)N * (double)ldh * 2.0 > 64e9)
     return fail(ctx, MRC_ERR_UNSUPPORTED, "cosine_allpairs: more documents than the 64 GB score buffer allows");
+  void* d_hhi = ws_get(ctx, "cos.hhi", 2 * (size_t)N * kd, &st);
+  void* d_hlo = ws_get(ctx, "cos.hlo", 2 * (size_t)N * kd, &st);
   int4* d_post = (int4*)ws_get(ctx, "cos.post", sizeof(int4) * (size_t)std::max<int64_t>(n_post, 1), &st);
   void* d_spost = ws_get(ctx, "cos.spost", 8 * (size_t)std::max<int64_t>(n_post, 1), &st);
   void* d_rwalk = ws_get(ctx, "cos.rwalk", 8 * (size_t)std::max<int64_t>(d.n_tokens, 1), &st);
@@ -1024,25 +1026,34 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   unsigned long long* d_next = (unsigned long long*)ws_get(ctx, "cos.next", sizeof(unsigned long long), &st);
   if (st != MRC_OK) return st;
   e = cudaMemsetAsync(d_tfill, 0, sizeof(int32_t) * V, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_hhi, 0, 2 * (size_t)N * kd, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_hlo, 0, 2 * (size_t)N * kd, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cosine set-up");
+  o.kd = kd;
+  o.kd_h = kd;
+  o.head_hi = d_hhi;
+  o.head_lo = d_hlo;
   o.postings = 1;
   o.post = d_post;
   o.row_term = nullptr;
-  e = launch_densify(ctx, d, V, index->tinfo, o);  // rewrites the same head rows
+  e = launch_densify(ctx, d, V, index->tinfo, o);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "densify");
   e = launch_rank_postings(ctx, d_cstart, d_rank_terms, n_small, d_rank_terms + n_small, n_tail - n_small, max_m, d_post,
                            d.offsets, d_spost, d_rwalk);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sorting postings");
+  g.a_hi = g.b_hi = d_hhi;
+  g.kbytes = kd * 2;
   g.store16 = d_H;
   g.ld = ldh;
   g.thresh = 0.f;
   g.pairs = nullptr;
   g.count = nullptr;
   g.capacity = 0;
+  g.name = nullptr;
   e = launch_gemm_compare(ctx, g);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "head GEMM");
   e = launch_cosine_tail(ctx, N, d_H, ldh, d.offsets, d_rcnt, d_rwalk, d_rw, d_spost, n_post, d_hhi, d_hlo, kd,
-                         tau, delta, dst, d_count, capacity, tail_work, d_next);
+                         tau, delta_of(kd), dst, d_count, capacity, tail_work, d_next);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tail pass");
   return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs, d_err);
 }

@@ -252,8 +252,8 @@ __device__ __forceinline__ void flush_pairs(const GemmParams& p, const mrc_pair*
 // the raw accumulator (the rescoring pass computes the reported score).
 template <int FMT>
 __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)[32], int64_t i, int64_t j0, int lane,
-                                           float fast_thresh, float row_norm, float* stage, float* nstage,
-                                           mrc_pair* buf, int& nbuf) {
+                                           float fast_thresh, float row_norm, float hit_lim, float* stage,
+                                           float* nstage, mrc_pair* buf, int& nbuf) {
   float m = v[0];
 #pragma unroll
   for (int e = 1; e < 32; ++e) m = fmaxf(m, v[e]);
@@ -274,8 +274,8 @@ __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)
   }
   if (i >= p.na) mask = 0u;
   uint32_t hits = 0;
-  // E4M3: the hit test acc >= hit_lim * |q_j| with hit_lim = thresh * |q_i| / out_scale
-  const float hit_lim = FMT == OP_E4M3 ? p.thresh * row_norm / p.out_scale : p.thresh;
+  // E4M3: the hit test acc >= hit_lim * |q_j| with hit_lim = thresh * |q_i| / out_scale (per row,
+  // from the caller); otherwise acc >= hit_lim = thresh
   for (uint32_t mm = mask; mm; mm &= mm - 1u) {
     const int e = __ffs(mm) - 1;
     const float sc = stage[lane * 33 + e];
@@ -495,9 +495,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       // E4M3: the score is the cosine of the quantized vectors, acc * out_scale / (|q_i| |q_j|).
       // Every non-zero quantized unit row has norm >= 1 - 2^-4 > kNormLo, so raw accumulators
       // below thresh * |q_i| * kNormLo / out_scale cannot reach the threshold (fast path).
-      float row_norm = 1.f, fast_thresh = p.thresh;
+      float row_norm = 1.f, fast_thresh = p.thresh, hit_lim = p.thresh;
       if (FMT == OP_E4M3) {
         row_norm = i < p.na ? p.a_norm[i] : 0.f;
+        hit_lim = p.thresh * row_norm / p.out_scale;
         if (p.thresh > 0.f)
           fast_thresh = row_norm > 0.f ? p.thresh * row_norm * kNormLo / p.out_scale : __int_as_float(0x7f800000);
         else
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         } else {
-          emit_chunk<FMT>(p, v, i, j0, lane, fast_thresh, row_norm, stage, nstage, pbuf, nbuf);
+          emit_chunk<FMT>(p, v, i, j0, lane, fast_thresh, row_norm, hit_lim, stage, nstage, pbuf, nbuf);
         }
       }
       tc_fence_before();
@@ -825,14 +826,15 @@ __global__ void __launch_bounds__(kResThreads, 1)
       // E4M3: the score is the cosine of the quantized vectors, acc * out_scale / (|q_i| |q_j|);
       // raw accumulators below thresh * |q_i| * min_j |q_j| / out_scale (minimum over the
       // chunk's 128-column block) cannot reach the threshold (fast path)
-      float row_norm = 1.f, row_bound = p.thresh, nmin0 = 1.f, nmin1 = 1.f;
+      float row_norm = 1.f, row_bound = p.thresh, nmin0 = 1.f, nmin1 = 1.f, hit_lim = p.thresh;
       if (FMT == OP_E4M3) {  // issued before the TMEM loads so that their latencies overlap
         row_norm = i < p.na ? __ldg(p.a_norm + i) : 0.f;
         const int64_t b0 = (bj * BN) >> 7, nbk = (p.nb + 127) >> 7;
         nmin0 = b0 < nbk ? __ldg(p.b_norm_min + b0) : 1.f;
         if (BN > 128) nmin1 = b0 + 1 < nbk ? __ldg(p.b_norm_min + b0 + 1) : 1.f;
+        hit_lim = p.thresh * row_norm / p.out_scale;
         if (p.thresh > 0.f)
-          row_bound = row_norm > 0.f ? p.thresh * row_norm / p.out_scale : __int_as_float(0x7f800000);
+          row_bound = row_norm > 0.f ? hit_lim : __int_as_float(0x7f800000);
         else
           row_bound = -__int_as_float(0x7f800000);
       }
@@ -862,7 +864,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
         const int64_t j0 = bj * BN + (half * CH + c) * 32;
         float fast_thresh = row_bound;
         if (FMT == OP_E4M3 && p.thresh > 0.f) fast_thresh = row_bound * ((((half * CH + c) * 32) >> 7) ? nmin1 : nmin0);
-        emit_chunk<FMT>(p, v[c], i, j0, lane, fast_thresh, row_norm, stage, nstage, pbuf, nbuf);
+        emit_chunk<FMT>(p, v[c], i, j0, lane, fast_thresh, row_norm, hit_lim, stage, nstage, pbuf, nbuf);
       }
       ++it;
     }

@@ -80,11 +80,10 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 __device__ __forceinline__ unsigned long long to_fix(float x) { return __float2ull_rn(x * kFix); }
 
 // 1 / |w| from the fixed-point squared norm (0 for an empty document).
-// u^2 in 2^-40 fixed point, rounded up (u <= 1: at most 2^40 per term); FP32 with directed
-// rounding (the power-of-two scaling is exact), so the bucket norms bound from above.
-__device__ __forceinline__ unsigned long long to_fix40_up(float u) {
-  return __float2ull_ru(__fmul_ru(u, u) * 1099511627776.0f);
-}
+// u^2 in 2^-31 fixed point, rounded up: FP32 with directed rounding (the power-of-two scaling
+// is exact), so the bucket norms bound from above. A document's tail has sum u^2 <= 1, so a
+// bucket's sum stays below 2^31 + 65,536 < 2^32.
+__device__ __forceinline__ uint32_t to_fix31_up(float u) { return __float2uint_ru(__fmul_ru(u, u) * 2147483648.0f); }
 __device__ __forceinline__ float inv_norm_of(unsigned long long norm_q) {
   const float n2 = (float)norm_q * kInvFix;
   return n2 > 0.f ? 1.0f / sqrtf(n2) : 0.f;
@@ -159,11 +158,11 @@ struct IngestParams {
   int32_t bag_write, bag_read;
 };
 
-// Shared-memory 64-bit accumulators per document: SIG, one per reference partition; DENSE in
-// the bound-pruned mode, one per tail bucket.
+// Shared-memory 64-bit accumulator words per document: SIG, one per reference partition; DENSE
+// in the bound-pruned mode, one 32-bit sum per tail bucket (two per word).
 template <int MODE>
 __host__ __device__ __forceinline__ int ingest_kq(const IngestParams& p) {
-  return MODE == kSIG ? p.k : (MODE == kDENSE && !p.dense.postings ? kTailBuckets : 0);
+  return MODE == kSIG ? p.k : (MODE == kDENSE && !p.dense.postings ? kTailBuckets / 2 : 0);
 }
 
 // Per-group accumulators of the SIG and DENSE modes.
@@ -258,19 +257,21 @@ __device__ __forceinline__ void chunk(const IngestParams& p, uint32_t key, uint3
       p.dense.post[pos] = make_int4((int32_t)doc, __float_as_int(u), r, 0);
     } else {
       p.dense.row_term[row_base + r] = (int32_t)key;
-      atomicAdd(&num_q[tail_bucket((int32_t)key)], to_fix40_up(u));  // bucket |t|^2, 2^-40 fixed point
+      // bucket |t|^2 in 32-bit 2^-31 fixed point (the accumulator area holds two per 8 bytes)
+      atomicAdd(reinterpret_cast<uint32_t*>(num_q) + tail_bucket((int32_t)key), to_fix31_up(u));
     }
   }
 }
 
-// Bound-pruned exact cosine: the document's tail-bucket norms (sqrt of the 2^-40 fixed-point
+// Bound-pruned exact cosine: the document's tail-bucket norms (sqrt of the 2^-31 fixed-point
 // sums) as fp16 head columns kd_h .. kd_h + kTailBuckets - 1 (the split low part stays 0).
 // Threads tid, tid + stride, ... of the document's group write.
 __device__ __forceinline__ void write_bucket_norms(const IngestParams& p, int64_t d, const unsigned long long* num_q,
                                                    int tid, int stride) {
+  const uint32_t* sums = reinterpret_cast<const uint32_t*>(num_q);
   __half* row = reinterpret_cast<__half*>(p.dense.head_hi) + d * (int64_t)p.dense.kd + p.dense.kd_h;
   for (int q = tid; q < kTailBuckets; q += stride)
-    row[q] = __float2half_rn(__fsqrt_ru(__ull2float_ru(num_q[q]) * (1.0f / 1099511627776.0f)));
+    row[q] = __float2half_rn(__fsqrt_ru(__uint2float_ru(sums[q]) * (1.0f / 2147483648.0f)));
 }
 
 // Writes the SIG outputs of one document; called by one full warp.

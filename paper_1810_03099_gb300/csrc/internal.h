@@ -207,11 +207,11 @@ struct DenseOut {
   // of kTailBuckets hash buckets of the term ids (so the head GEMM also sums the bound).
   int32_t postings;
   int32_t* row_term;          // [n_tokens] at the doc's token offsets: id of its r-th tail term
-  int32_t kd_h;               // head columns proper (a multiple of 64; kd_h + kTailBuckets <= kd)
+  int32_t kd_h;               // head columns proper (a multiple of 64, may be 0; kd_h + kTailBuckets <= kd)
 };
-constexpr int kTailBuckets = 128;
-// Bucket of a tail term id (the top 7 bits of a multiplicative hash).
-__host__ __device__ inline int32_t tail_bucket(int32_t t) { return (int32_t)(((uint32_t)t * 0x9E3779B1u) >> 25); }
+constexpr int kTailBuckets = 256;
+// Bucket of a tail term id (the top 8 bits of a multiplicative hash).
+__host__ __device__ inline int32_t tail_bucket(int32_t t) { return (int32_t)(((uint32_t)t * 0x9E3779B1u) >> 24); }
 cudaError_t launch_densify(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo, const DenseOut& out);
 
 // compare_tc.cu

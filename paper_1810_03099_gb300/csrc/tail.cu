@@ -841,7 +841,7 @@ cudaError_t launch_cosine_verify(mrc_ctx* ctx, const mrc_pair* cand, const unsig
                                  const int64_t* row_off, const int32_t* row_cnt, const int32_t* row_term,
                                  const float* row_w, float tau, mrc_pair* pairs, unsigned long long* count,
                                  int64_t capacity, int32_t* long_idx, unsigned long long* n_long, int32_t* err) {
-  if ((kd & 63) || kd <= 0 || (ld & 7) || ld < kd) return cudaErrorInvalidValue;
+  if ((kd & 63) || kd < 0 || (ld & 7) || ld < kd) return cudaErrorInvalidValue;
   const size_t smem = sizeof(int32_t) * 2 * kVerSlots * kVerWarps;
   const int per_sm = resident_ctas(k_cosine_verify, kVerWarps * 32, smem);
   const int per_sm_long = resident_ctas(k_cosine_verify_long, kVerWarps * 32, smem);
