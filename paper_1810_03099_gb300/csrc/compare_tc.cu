@@ -243,28 +243,34 @@ __device__ __forceinline__ void flush_pairs(const GemmParams& p, const mrc_pair*
 }
 
 // Threshold one 32-column chunk held in registers (v[e] = score of column j0 + e for this
-// lane's row i) and append its pairs. Fast path: the chunk's maximum misses fast_thresh in
-// every lane. Otherwise each lane builds a 32-bit mask of candidate columns (bounds and the
-// triangle's j > i applied with bit arithmetic), tests the candidates exactly, and the warp
-// appends its hits to its pair buffer. E4M3 operands are only ever candidates for FP32
-// rescoring: a column is a hit when acc * out_scale >= thresh * |q_i| * |q_j| (column norms
-// staged once per warp; zero norms never hit), tested by multiplication, and the pair carries
-// the raw accumulator (the rescoring pass computes the reported score).
+// lane's row i) and append its candidate pairs. Fast path: the chunk's maximum misses
+// fast_thresh in every lane. Otherwise each lane builds the 32-bit mask of its hits straight
+// from its registers (a hit: v[e] >= hit_lim; E4M3: v[e] >= hit_lim * |q_j|, the column norms
+// staged once per warp, zero norms never hitting), applies the bounds and the triangle's j > i
+// with bit arithmetic, and the warp appends its hits to its pair buffer. Every caller rescores
+// its candidates (FP32 rescoring, exact-cosine verification), so a pair carries only the lane's
+// chunk maximum, an upper bound of its raw score.
 template <int FMT>
 __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)[32], int64_t i, int64_t j0, int lane,
-                                           float fast_thresh, float row_norm, float hit_lim, float* stage,
-                                           float* nstage, mrc_pair* buf, int& nbuf) {
+                                           float fast_thresh, float row_norm, float hit_lim, float* nstage,
+                                           mrc_pair* buf, int& nbuf) {
   float m = v[0];
 #pragma unroll
   for (int e = 1; e < 32; ++e) m = fmaxf(m, v[e]);
   if (!__any_sync(kFull, m >= fast_thresh)) return;
-#pragma unroll
-  for (int e = 0; e < 32; ++e) stage[lane * 33 + e] = v[e];
-  if (FMT == OP_E4M3) nstage[lane] = j0 + lane < p.nb ? __ldg(p.b_norm + j0 + lane) : 0.f;
-  __syncwarp();
   uint32_t mask = 0;
+  if (FMT == OP_E4M3) {
+    const float nj = j0 + lane < p.nb ? __ldg(p.b_norm + j0 + lane) : 0.f;
+    nstage[lane] = nj > 0.f ? nj : __int_as_float(0x7f800000);
+    __syncwarp();
+    if (row_norm > 0.f) {
 #pragma unroll
-  for (int e = 0; e < 32; ++e) mask |= (v[e] >= fast_thresh ? 1u : 0u) << e;
+      for (int e = 0; e < 32; ++e) mask |= (v[e] >= hit_lim * nstage[e] ? 1u : 0u) << e;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 32; ++e) mask |= (v[e] >= hit_lim ? 1u : 0u) << e;
+  }
   const int64_t lim = p.nb - j0;  // columns j0 + e < nb
   if (lim < 32) mask &= lim <= 0 ? 0u : ((1u << lim) - 1u);
   if (p.triangle) {  // j0 + e > i
@@ -273,21 +279,7 @@ __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)
     else if (dlt >= 0) mask &= ~((2u << dlt) - 1u);
   }
   if (i >= p.na) mask = 0u;
-  uint32_t hits = 0;
-  // E4M3: the hit test acc >= hit_lim * |q_j| with hit_lim = thresh * |q_i| / out_scale (per row,
-  // from the caller); otherwise acc >= hit_lim = thresh
-  for (uint32_t mm = mask; mm; mm &= mm - 1u) {
-    const int e = __ffs(mm) - 1;
-    const float sc = stage[lane * 33 + e];
-    bool hit;
-    if (FMT == OP_E4M3) {
-      const float nj = nstage[e];
-      hit = row_norm > 0.f && nj > 0.f && sc >= hit_lim * nj;
-    } else {
-      hit = sc >= hit_lim;
-    }
-    if (hit) hits |= 1u << e;
-  }
+  const uint32_t hits = mask;
   const int cnt = __popc(hits);
   int incl = cnt;
 #pragma unroll
@@ -309,11 +301,10 @@ __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)
     int at = incl - cnt;
     for (uint32_t hh = hits; hh; hh &= hh - 1u, ++at) {
       const int e = __ffs(hh) - 1;
-      const float sc = stage[lane * 33 + e];
       mrc_pair pr;
       pr.i = (int32_t)i;
       pr.j = (int32_t)(j0 + e);
-      pr.score = sc;
+      pr.score = m;
       if (!direct)
         buf[nbuf + at] = pr;
       else if (base + at < (unsigned long long)p.capacity)
@@ -553,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         } else {
-          emit_chunk<FMT>(p, v, i, j0, lane, fast_thresh, row_norm, hit_lim, stage, nstage, pbuf, nbuf);
+          emit_chunk<FMT>(p, v, i, j0, lane, fast_thresh, row_norm, hit_lim, nstage, pbuf, nbuf);
         }
       }
       tc_fence_before();
@@ -864,7 +855,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
         const int64_t j0 = bj * BN + (half * CH + c) * 32;
         float fast_thresh = row_bound;
         if (FMT == OP_E4M3 && p.thresh > 0.f) fast_thresh = row_bound * ((((half * CH + c) * 32) >> 7) ? nmin1 : nmin0);
-        emit_chunk<FMT>(p, v[c], i, j0, lane, fast_thresh, row_norm, hit_lim, stage, nstage, pbuf, nbuf);
+        emit_chunk<FMT>(p, v[c], i, j0, lane, fast_thresh, row_norm, hit_lim, nstage, pbuf, nbuf);
       }
       ++it;
     }
