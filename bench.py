@@ -39,12 +39,16 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # the news20 step, valid only while the kernel's source file is unchanged since the capture.
 NCU_TRAFFIC = {
     "gemm_f16_bound": ("paper_1810_03099_gb300/csrc/compare_tc.cu",
-                       "bdb7cbfc430d7725589870b43e2e71d4cf4b643bff64a00da128961d12698f1f", 50881280),
+                       "daccb9226e67077e6a8f000d47efaaadd566c95fcaa1980f22aa099bbcbf3b8f", 14508544),
+    "gemm_f16_thresh": ("paper_1810_03099_gb300/csrc/compare_tc.cu",
+                        "daccb9226e67077e6a8f000d47efaaadd566c95fcaa1980f22aa099bbcbf3b8f", 2470912),
 }
 KERNEL_NOTES = {
     "gemm_f16_bound": "exact-cosine head GEMM carrying the tail-bucket bound: 2 kd flops per pair of the "
-                      "triangle (kd = 1024 head + 128 bucket columns); ncu: tensor pipe 87.5% active; candidates "
+                      "triangle (kd = 128 head + 256 bucket columns); ncu: tensor pipe 75% active; candidates "
                       "where head + bound >= tau - delta'",
+    "gemm_f16_thresh": "signature compare at k = 64: one K block per tile, epilogue-bound (ncu: tensor pipe 23% "
+                       "active)",
     "cosine_verify": "exact scores of the bound-pruned candidates (a few tens of thousands on news20)",
     "cosine_tail": "algorithmic bytes = the fp16 head scores of the upper triangle; the postings it also walks "
                    "are L2-resident. ncu: issue-active 66%, l1tex 53%: instruction/latency-bound, not HBM-bound",
