@@ -210,8 +210,8 @@ mrc_status simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint
  * overflowed -- the reduced-precision forms first collect candidates in a
  * buffer of max(4 * capacity, 2^20) entries, which the synchronous form grows
  * and repeats on overflow) are recorded in the context and returned by the
- * next mrc_ctx_sync. cosine_allpairs_async still waits once, after its first
- * pass, for the sizes of its head/tail split.
+ * next mrc_ctx_sync. cosine_allpairs_async waits for nothing unless per-kernel
+ * timing is on (it then reads its head/tail split's sizes once).
  * Host-side argument errors return at once, as in the synchronous forms.
  *
  * mrc_ctx_sync waits for the context's stream and returns the first recorded

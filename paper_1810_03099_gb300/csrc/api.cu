@@ -864,8 +864,10 @@ static mrc_status match_impl(mrc_ctx* ctx, const mrc_index* index, const float* 
   return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
 }
 
-// cosine_allpairs, or with d_total its stream-ordered form (see match_impl); the head/tail split
-// still waits once for its totals.
+// cosine_allpairs, or with d_total its stream-ordered form (see match_impl). The bound-pruned
+// path reads the head/tail split's sizes on the device, so nothing waits (unless per-kernel
+// timing is on or the head's upper bound is too wide); errors of the stream-ordered form go to
+// the context's error word.
 static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float tau, mrc_pair* pairs,
                        int64_t capacity, int64_t* n_pairs, unsigned long long* d_total) {
   if (!ctx || !index) return MRC_ERR_INVALID;
@@ -876,7 +878,7 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   const bool async = d_total != nullptr;
   if (async && ((capacity > 0 && (!pairs || !is_device_ptr(pairs))) || !is_device_ptr(d_total)))
     return fail(ctx, MRC_ERR_INVALID, "stream-ordered calls take device pairs and a device pair count");
-  int32_t* d_err = call_err(ctx, &st);  // checked at the split's synchronisation
+  int32_t* d_err = async ? ctx->async_err : call_err(ctx, &st);
   if (!d_err) return st;
   DocsDev d;
   if ((st = stage_docs(ctx, docs, "cos", &d, d_err)) != MRC_OK) return st;
@@ -956,9 +958,30 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   // shared term, under 3.1e-5 for 65,536 terms). The bucket columns make a looser head cheap:
   // head = df >= max(32, N / 8).
   {
-    if ((st = split((int32_t)std::min<int64_t>(std::max<int64_t>(32, N / 8), INT32_MAX))) != MRC_OK) return st;
-    const int32_t kd_h = round_up((int32_t)h_tsum[0], 64);  // may be 0
-    const int32_t kd = kd_h + kTailBuckets;
+    const int32_t cut_b = (int32_t)std::min<int64_t>(std::max<int64_t>(32, N / 8), INT32_MAX);
+    // The head has at most n_tokens / cut terms (each adds >= cut to sum df <= n_tokens). With
+    // room for that many columns the split's totals never need to reach the host: the head
+    // width is read on the device (row stride kd_max, K blocks from k_cosine_dims). Per-kernel
+    // timing takes the synchronous split, so that the flop counts are exact.
+    const int32_t kd_h_max =
+        round_up((int32_t)std::min<int64_t>((int64_t)V, std::max<int64_t>(d.n_tokens, 0) / cut_b), 64);
+    const bool dims_dev = !ctx->timing && 4.0 * (double)N * (double)(kd_h_max + kTailBuckets) <= 8e9;
+    int32_t kd_h = 0, kd = 0;
+    int32_t* d_dims = (int32_t*)ws_get(ctx, "cos.dims", sizeof(int32_t) * 2, &st);
+    if (st != MRC_OK) return st;
+    if (dims_dev) {
+      e = cudaMemsetAsync(d_cstart, 0, sizeof(int64_t), ctx->stream);
+      if (e == cudaSuccess)
+        e = launch_cosine_terms(ctx, df, V, cut_b, d_tpart, d_tsum, d_colmap, d_tstart, d_cstart, d_rank_terms);
+      if (e == cudaSuccess) e = launch_cosine_dims(ctx, d_tsum, kd_h_max, d_dims);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "head/tail split");
+      kd_h = kd_h_max;  // an upper bound on the host
+      kd = kd_h_max + kTailBuckets;
+    } else {
+      if ((st = split(cut_b)) != MRC_OK) return st;
+      kd_h = round_up((int32_t)h_tsum[0], 64);  // may be 0
+      kd = kd_h + kTailBuckets;
+    }
     const int64_t cand_cap = std::max<int64_t>(4 * capacity, 1 << 22);
     void* d_hhi = ws_get(ctx, "cos.hhi", 2 * (size_t)N * kd, &st);
     void* d_hlo = ws_get(ctx, "cos.hlo", 2 * (size_t)N * kd, &st);
@@ -968,12 +991,19 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
     unsigned long long* d_nlong = (unsigned long long*)ws_get(ctx, "cos.nlong", sizeof(unsigned long long), &st);
     unsigned long long* d_ccount = (unsigned long long*)ws_get(ctx, "cos.ccount", sizeof(unsigned long long), &st);
     if (st != MRC_OK) return st;
-    e = cudaMemsetAsync(d_hhi, 0, 2 * (size_t)N * kd, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_hlo, 0, 2 * (size_t)N * kd, ctx->stream);
+    if (dims_dev) {
+      e = launch_zero_head(ctx, d_hhi, d_hlo, N, kd, d_dims);
+      // documents the ingest passes rejected (bad offsets or lengths) keep no tail terms
+      if (e == cudaSuccess) e = cudaMemsetAsync(d_rcnt, 0, sizeof(int32_t) * (size_t)N, ctx->stream);
+    } else {
+      e = cudaMemsetAsync(d_hhi, 0, 2 * (size_t)N * kd, ctx->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(d_hlo, 0, 2 * (size_t)N * kd, ctx->stream);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(d_ccount, 0, sizeof(unsigned long long), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cosine set-up");
     o.kd = kd;
     o.kd_h = kd_h;
+    o.kd_h_dev = dims_dev ? d_dims : nullptr;
     o.head_hi = d_hhi;
     o.head_lo = d_hlo;
     o.postings = 0;
@@ -982,15 +1012,17 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
     if (e != cudaSuccess) return cuda_fail(ctx, e, "densify");
     g.a_hi = g.b_hi = d_hhi;
     g.kbytes = kd * 2;
-    g.thresh = tau - (delta_of(kd) + 4e-5f);
+    g.kblocks_dev = dims_dev ? d_dims + 1 : nullptr;
+    g.thresh = tau - (delta_of(kd) + 4e-5f);  // kd: the actual width, or its upper bound
     g.pairs = d_cand;
     g.count = d_ccount;
     g.capacity = cand_cap;
     g.name = "gemm_f16_bound";
     e = launch_gemm_compare(ctx, g);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "head GEMM");
-    e = launch_cosine_verify(ctx, d_cand, d_ccount, cand_cap, d_hhi, d_hlo, kd, kd_h, d.offsets, d_rcnt, d_rterm, d_rw,
-                             tau, dst, d_count, capacity, d_clong, d_nlong, async ? ctx->async_err : d_err);
+    e = launch_cosine_verify(ctx, d_cand, d_ccount, cand_cap, d_hhi, d_hlo, kd, kd_h, dims_dev ? d_dims : nullptr,
+                             d.offsets, d_rcnt, d_rterm, d_rw, tau, dst, d_count, capacity, d_clong, d_nlong,
+                             async ? ctx->async_err : d_err);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "candidate verification");
     if (async) return MRC_OK;  // a candidate overflow is reported by mrc_ctx_sync
     bool overflow = false;
@@ -1031,6 +1063,7 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cosine set-up");
   o.kd = kd;
   o.kd_h = kd;
+  o.kd_h_dev = nullptr;
   o.head_hi = d_hhi;
   o.head_lo = d_hlo;
   o.postings = 1;
@@ -1043,6 +1076,7 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sorting postings");
   g.a_hi = g.b_hi = d_hhi;
   g.kbytes = kd * 2;
+  g.kblocks_dev = nullptr;
   g.store16 = d_H;
   g.ld = ldh;
   g.thresh = 0.f;

@@ -74,6 +74,7 @@ struct GemmParams {
   int64_t ld;
   int32_t* err;
   int32_t row_rr;  // resident kernel, triangle: whole row blocks dealt round-robin (see TileSeq)
+  const int32_t* kblocks_dev;  // streaming kernel: K blocks read from the device (see GemmArgs)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -371,6 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_slot;
   const uint32_t rank = MC ? cluster_rank() : 0u;
   if (MC) cluster_sync();  // the peer's barriers are initialised before any multicast reaches them
+  const int32_t kblocks = p.kblocks_dev ? *p.kblocks_dev : p.kblocks;
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -382,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
         int64_t bi, bj;
         if (!decode_tile<BN>(p, t, bi, bj) && !MC) continue;
-        for (int kb = 0; kb < p.kblocks; ++kb) {
+        for (int kb = 0; kb < kblocks; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.err)) {
             ok = false;
             break;
@@ -430,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint32_t d0 = tmem + ab * 256u;
         const uint32_t d1 = d0 + 128u;
-        for (int kb = 0; kb < p.kblocks; ++kb) {
+        for (int kb = 0; kb < kblocks; ++kb) {
           if (!mbar_wait(&full[stage], phase, abort_flag, p.err)) {
             ok = false;
             break;
@@ -1001,6 +1003,7 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   p.store16 = reinterpret_cast<__half*>(g.store16);
   p.ld = g.ld;
   p.err = g.err;
+  p.kblocks_dev = g.kblocks_dev;
   const size_t smem = 1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256 + 4 * (32 * 33 + 32) * 4 +
                       4 * kPairBuf * sizeof(mrc_pair);
   if (resident_ctas(k_gemm_compare<FMT, 0>, kThreads, smem) <= 0 ||

@@ -269,7 +269,8 @@ __device__ __forceinline__ void chunk(const IngestParams& p, uint32_t key, uint3
 __device__ __forceinline__ void write_bucket_norms(const IngestParams& p, int64_t d, const unsigned long long* num_q,
                                                    int tid, int stride) {
   const uint32_t* sums = reinterpret_cast<const uint32_t*>(num_q);
-  __half* row = reinterpret_cast<__half*>(p.dense.head_hi) + d * (int64_t)p.dense.kd + p.dense.kd_h;
+  const int32_t kd_h = p.dense.kd_h_dev ? *p.dense.kd_h_dev : p.dense.kd_h;
+  __half* row = reinterpret_cast<__half*>(p.dense.head_hi) + d * (int64_t)p.dense.kd + kd_h;
   for (int q = tid; q < kTailBuckets; q += stride)
     row[q] = __float2half_rn(__fsqrt_ru(__uint2float_ru(sums[q]) * (1.0f / 2147483648.0f)));
 }

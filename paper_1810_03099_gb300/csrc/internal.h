@@ -208,6 +208,7 @@ struct DenseOut {
   int32_t postings;
   int32_t* row_term;          // [n_tokens] at the doc's token offsets: id of its r-th tail term
   int32_t kd_h;               // head columns proper (a multiple of 64, may be 0; kd_h + kTailBuckets <= kd)
+  const int32_t* kd_h_dev;    // non-null: kd_h read from the device (kd is then only the row stride)
 };
 constexpr int kTailBuckets = 256;
 // Bucket of a tail term id (the top 8 bits of a multiplicative hash).
@@ -239,6 +240,8 @@ struct GemmArgs {
   int32_t tile_n;       // compare tile width for small K: 128, 256 or 0 (default)
   int32_t* err;         // device error word
   const char* name;     // timing name (NULL: by format and epilogue)
+  const int32_t* kblocks_dev;  // non-null: the number of 64-element K blocks, read from the device
+                               // (kbytes is then the row stride and the K extent of the maps)
 };
 cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g);
 
@@ -270,8 +273,14 @@ cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int3
 // >= tau - delta rescored exactly (head from the hi/lo split rows [n x kd], tail exact).
 // Exact scores of the bound-pruned candidates (see k_cosine_verify); pairs with score >= tau
 // go to pairs/count; a candidate count above cand_cap sets kErrOverflow in err.
+// dims[0] = kd_h = head columns rounded up to 64 (from the split's totals, at most kd_h_max),
+// dims[1] = (kd_h + kTailBuckets) / 64 K blocks of the bound-pruned head GEMM.
+cudaError_t launch_cosine_dims(mrc_ctx* ctx, const long long* split_totals, int32_t kd_h_max, int32_t* dims);
+// Zeroes columns [0, kd_h + kTailBuckets) of each hi row and [0, kd_h) of each lo row (stride ld).
+cudaError_t launch_zero_head(mrc_ctx* ctx, void* head_hi, void* head_lo, int64_t n, int32_t ld, const int32_t* dims);
 cudaError_t launch_cosine_verify(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand,
                                  int64_t cand_cap, const void* head_hi, const void* head_lo, int32_t ld, int32_t kd,
+                                 const int32_t* kd_dev,
                                  const int64_t* row_off, const int32_t* row_cnt, const int32_t* row_term,
                                  const float* row_w, float tau, mrc_pair* pairs, unsigned long long* count,
                                  int64_t capacity, int32_t* long_idx, unsigned long long* n_long, int32_t* err);

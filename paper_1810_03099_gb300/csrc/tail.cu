@@ -656,10 +656,11 @@ __device__ __forceinline__ void emit_verified(float s, float tau, int32_t i, int
 // k_cosine_verify_long.
 __global__ void __launch_bounds__(kVerWarps * 32, 3) k_cosine_verify(
     const mrc_pair* __restrict__ cand, const unsigned long long* __restrict__ n_cand, int64_t cand_cap,
-    const __half* __restrict__ hhi, const __half* __restrict__ hlo, int32_t ld, int32_t kd,
-    const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_cnt, const int32_t* __restrict__ row_term,
-    const float* __restrict__ row_w, float tau, mrc_pair* pairs, unsigned long long* count, int64_t capacity,
-    int32_t* long_idx, unsigned long long* n_long, int32_t* err) {
+    const __half* __restrict__ hhi, const __half* __restrict__ hlo, int32_t ld, int32_t kd_arg,
+    const int32_t* __restrict__ kd_dev, const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_cnt,
+    const int32_t* __restrict__ row_term, const float* __restrict__ row_w, float tau, mrc_pair* pairs,
+    unsigned long long* count, int64_t capacity, int32_t* long_idx, unsigned long long* n_long, int32_t* err) {
+  const int32_t kd = kd_dev ? *kd_dev : kd_arg;
   extern __shared__ __align__(16) int32_t vsm[];  // [kVerWarps][kVerSlots keys + kVerSlots weights]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* keys = vsm + warp * 2 * kVerSlots;
@@ -704,10 +705,11 @@ __global__ void __launch_bounds__(kVerWarps * 32, 3) k_cosine_verify(
 // as every other path).
 __global__ void __launch_bounds__(kVerWarps * 32, 3) k_cosine_verify_long(
     const mrc_pair* __restrict__ cand, const int32_t* __restrict__ long_idx, const unsigned long long* __restrict__ n_long,
-    const __half* __restrict__ hhi, const __half* __restrict__ hlo, int32_t ld, int32_t kd,
-    const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_cnt, const int32_t* __restrict__ row_term,
-    const float* __restrict__ row_w, float tau, mrc_pair* pairs, unsigned long long* count, int64_t capacity,
-    int32_t* err) {
+    const __half* __restrict__ hhi, const __half* __restrict__ hlo, int32_t ld, int32_t kd_arg,
+    const int32_t* __restrict__ kd_dev, const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_cnt,
+    const int32_t* __restrict__ row_term, const float* __restrict__ row_w, float tau, mrc_pair* pairs,
+    unsigned long long* count, int64_t capacity, int32_t* err) {
+  const int32_t kd = kd_dev ? *kd_dev : kd_arg;
   constexpr int kSlots = kVerWarps * kVerSlots, kLog = 13;  // 8192 slots
   static_assert((1 << kLog) == kSlots, "table size");
   extern __shared__ __align__(16) int32_t vsm[];
@@ -836,9 +838,46 @@ cudaError_t launch_rank_postings(mrc_ctx* ctx, const int64_t* cstart, const int3
   return cudaGetLastError();
 }
 
+__global__ void k_cosine_dims(const long long* __restrict__ tsum, int32_t kd_h_max, int32_t* __restrict__ dims) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const long long h = tsum[kTcHead];
+  int32_t kd_h = (int32_t)(((h < 0 ? 0 : h) + 63) / 64 * 64);
+  if (kd_h > kd_h_max) kd_h = kd_h_max;  // cannot happen: the head has at most n_tokens / cut terms
+  dims[0] = kd_h;
+  dims[1] = (kd_h + kTailBuckets) / 64;
+}
+
+cudaError_t launch_cosine_dims(mrc_ctx* ctx, const long long* split_totals, int32_t kd_h_max, int32_t* dims) {
+  KernelTimer kt(ctx, "cosine_dims");
+  k_cosine_dims<<<1, 32, 0, ctx->stream>>>(split_totals, kd_h_max, dims);
+  return cudaGetLastError();
+}
+
+// Rows of 16-byte chunks; hi: columns [0, kd_h + kTailBuckets), lo: [0, kd_h) (all multiples of 8).
+__global__ void k_zero_head(uint4* __restrict__ hi, uint4* __restrict__ lo, int64_t n, int32_t ld,
+                            const int32_t* __restrict__ dims) {
+  const int32_t kd_h = dims[0];
+  const int32_t chi = (kd_h + kTailBuckets) / 8, clo = kd_h / 8, cld = ld / 8;
+  const int64_t total = n * (int64_t)chi;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = x / chi;
+    const int32_t c = (int32_t)(x - r * chi);
+    hi[r * cld + c] = make_uint4(0u, 0u, 0u, 0u);
+    if (c < clo) lo[r * cld + c] = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+cudaError_t launch_zero_head(mrc_ctx* ctx, void* head_hi, void* head_lo, int64_t n, int32_t ld, const int32_t* dims) {
+  if (ld % 8 != 0 || n <= 0) return cudaErrorInvalidValue;
+  KernelTimer kt(ctx, "zero_head");
+  k_zero_head<<<(unsigned)(4 * ctx->num_sms), 256, 0, ctx->stream>>>(reinterpret_cast<uint4*>(head_hi),
+                                                                     reinterpret_cast<uint4*>(head_lo), n, ld, dims);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cosine_verify(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand,
                                  int64_t cand_cap, const void* head_hi, const void* head_lo, int32_t ld, int32_t kd,
-                                 const int64_t* row_off, const int32_t* row_cnt, const int32_t* row_term,
+                                 const int32_t* kd_dev, const int64_t* row_off, const int32_t* row_cnt, const int32_t* row_term,
                                  const float* row_w, float tau, mrc_pair* pairs, unsigned long long* count,
                                  int64_t capacity, int32_t* long_idx, unsigned long long* n_long, int32_t* err) {
   if ((kd & 63) || kd < 0 || (ld & 7) || ld < kd) return cudaErrorInvalidValue;
@@ -853,12 +892,13 @@ cudaError_t launch_cosine_verify(mrc_ctx* ctx, const mrc_pair* cand, const unsig
   {
     KernelTimer kt(ctx, "cosine_verify");
     k_cosine_verify<<<(unsigned)(ctx->num_sms * per_sm), kVerWarps * 32, smem, ctx->stream>>>(
-        cand, n_cand, cand_cap, hi, lo, ld, kd, row_off, row_cnt, row_term, row_w, tau, pairs, count, capacity,
-        long_idx, n_long, err);
+        cand, n_cand, cand_cap, hi, lo, ld, kd, kd_dev, row_off, row_cnt, row_term, row_w, tau, pairs, count,
+        capacity, long_idx, n_long, err);
   }
   KernelTimer kt(ctx, "cosine_verify_long");
   k_cosine_verify_long<<<(unsigned)(ctx->num_sms * per_sm_long), kVerWarps * 32, smem, ctx->stream>>>(
-      cand, long_idx, n_long, hi, lo, ld, kd, row_off, row_cnt, row_term, row_w, tau, pairs, count, capacity, err);
+      cand, long_idx, n_long, hi, lo, ld, kd, kd_dev, row_off, row_cnt, row_term, row_w, tau, pairs, count, capacity,
+      err);
   return cudaGetLastError();
 }
 
