@@ -36,21 +36,31 @@ constexpr int kGroupThreads = 256;
 // band's first term, [5] band size, [6] status (0 ok, 1 band too large), [7] largest df.
 enum { kSsStart = 0, kSsL, kSsVlo, kSsVhi, kSsRank0, kSsBand, kSsStatus, kSsMaxdf, kSsWords = 8 };
 
+// df histogram. The small df values hold most of the vocabulary (Zipf), so their counts are
+// first summed per CTA in shared memory (one global atomic per CTA and value); larger values go
+// straight to global memory, once per group of equal values in a warp.
+constexpr int kHistSmall = 1024;
 __global__ void __launch_bounds__(1024) k_df_hist(const int32_t* __restrict__ df, int32_t V,
                                                   int32_t* __restrict__ hist, long long* __restrict__ state) {
+  __shared__ int32_t s_hist[kHistSmall];
   __shared__ int32_t s_max[32];
+  for (int x = threadIdx.x; x < kHistSmall; x += blockDim.x) s_hist[x] = 0;
+  __syncthreads();
   int32_t dmax = 0;
   for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t - (int32_t)threadIdx.x < V; t += gridDim.x * blockDim.x) {
     const int32_t d = t < V ? df[t] : 0;
-    // lanes of equal df add once (small df values are most of the vocabulary)
-    const unsigned same = __match_any_sync(kFull, d);
-    if (d > 0 && (threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&hist[d], __popc(same));
+    if (d > 0 && d < kHistSmall) atomicAdd(&s_hist[d], 1);
+    const int32_t big = d >= kHistSmall ? d : -1;  // the loop is warp-uniform: every lane matches
+    const unsigned same = __match_any_sync(kFull, big);
+    if (big >= 0 && (threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&hist[big], __popc(same));
     dmax = max(dmax, d);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(kFull, dmax, o));
   if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = dmax;
   __syncthreads();
+  for (int x = threadIdx.x; x < kHistSmall; x += blockDim.x)
+    if (s_hist[x]) atomicAdd(&hist[x], s_hist[x]);
   if (threadIdx.x < 32) {
     dmax = threadIdx.x < (blockDim.x >> 5) ? s_max[threadIdx.x] : 0;
 #pragma unroll

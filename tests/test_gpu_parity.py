@@ -244,6 +244,28 @@ def test_cosine_allpairs_candidate_overflow_takes_tail_walk(torch, M, ctx, orc):
     idx.free()
 
 
+@pytest.mark.parametrize("n_docs,tau", [(20, 0.0), (60, 0.1)])
+def test_cosine_allpairs_long_documents_and_no_head(torch, M, ctx, orc, n_docs, tau):
+    """Few documents, most of them long (log-uniform 20..20,000 tokens). With N = 20 the head cut
+    max(32, N/8) exceeds every df, so the bound-pruned GEMM has no head columns at all; with a
+    low tau nearly every pair is a candidate, and the long documents' tail lists (thousands of
+    terms) take the CTA-level verification in several hash-partitioned passes."""
+    b = synth.make_corpus(synth.SPECS["batch_queries"].with_(n_docs=n_docs, vocab=5000, seed=41))
+    e = csr(edge_docs(5000))
+    offs, toks = concat((b.offsets, b.tokens), e)
+    V = 5000
+    p = Params(k=8)
+    ref = build_index(offs, toks, V, p, orc)
+    idx = M.mrc_build_index(ctx, dev(torch, offs), dev(torch, toks), V, mrc_params(M, p))
+    buf, total = M.cosine_allpairs(ctx, idx, dev(torch, offs), dev(torch, toks), tau)
+    got = M.pairs_to_numpy(buf)
+    tot, pi, pj, ps = orc.cosine_pairs(ref.row_ptr, ref.terms, ref.w, tau)
+    rep = compare_pairs(pair_dict(got["i"], got["j"], got["score"]), pair_dict(pi, pj, ps), tau, BAND, COS_TOL,
+                        lambda i, j: orc.cosine_pair(ref.row_ptr, ref.terms, ref.w, i, j))
+    assert rep["n"] == tot and tot > 0
+    idx.free()
+
+
 def test_simhash_match_bit_exact(torch, M, ctx, orc):
     c = synth.make_corpus("tiny")
     ref_F = orc.simhash(c.offsets, c.tokens, 0x1810030990)
