@@ -5,6 +5,7 @@ that the two can be checked against each other. Test infrastructure only.
 """
 from __future__ import annotations
 
+import hashlib
 import math
 from collections import Counter
 
@@ -80,10 +81,21 @@ def splitmix64(state):
     return z ^ (z >> 31)
 
 
-def simhash(doc_tokens, seed):
+def feature_hash(t, seed, mode=0):
+    """Mode 0: SplitMix64 of (t xor seed); modes 1 and 2: the first 8 bytes (little-endian) of
+    the MD5 / SHA-1 digest of t (4 bytes, little-endian) followed by the seed (8 bytes,
+    little-endian), taken from Python's hashlib."""
+    if mode == 0:
+        return splitmix64((t & 0xFFFFFFFF) ^ seed)
+    msg = (t & 0xFFFFFFFF).to_bytes(4, "little") + (seed & MASK64).to_bytes(8, "little")
+    dg = (hashlib.md5 if mode == 1 else hashlib.sha1)(msg).digest()
+    return int.from_bytes(dg[:8], "little")
+
+
+def simhash(doc_tokens, seed, mode=0):
     cols = [0] * 64
     for t in doc_tokens:
-        h = splitmix64((t & 0xFFFFFFFF) ^ seed)
+        h = feature_hash(t, seed, mode)
         for b in range(64):
             cols[b] += 1 if (h >> b) & 1 else -1
     return sum(1 << b for b in range(64) if cols[b] > 0)
@@ -93,7 +105,7 @@ def hamming(a, b):
     return bin(a ^ b).count("1")
 
 
-def pipeline(offsets, tokens, vocab, k, L, mode, start, tfidf, seed):
+def pipeline(offsets, tokens, vocab, k, L, mode, start, tfidf, seed, hash_mode=0):
     docs = docs_from_csr(offsets, tokens)
     bl = bags(docs)
     n = len(docs)
@@ -102,5 +114,5 @@ def pipeline(offsets, tokens, vocab, k, L, mode, start, tfidf, seed):
     parts = select(df, vocab, n, mode, L, start, k)
     wv = [weight_vec(b, idf) for b in bl]
     sig = [signature(w, parts, idf) for w in wv]
-    fp = [simhash(d, seed) for d in docs]
+    fp = [simhash(d, seed, hash_mode) for d in docs]
     return {"df": df, "idf": idf, "parts": parts, "w": wv, "sig": sig, "simhash": fp}

@@ -287,8 +287,9 @@ int64_t orc_cosine_pairs(int64_t n, const int64_t* row_ptr, const int32_t* terms
 }
 
 /*
- * 64-bit feature hash. The paper hashes words with MD5 or SHA1 (Section III).
- * Reading taken: the SplitMix64 generator of Steele, Lea and Flood (2014),
+ * 64-bit feature hash. The paper hashes words with MD5 or SHA1 (Section III);
+ * those two are hash modes 1 and 2 below. Default reading (mode 0): the
+ * SplitMix64 generator of Steele, Lea and Flood (2014),
  * one step from state (t XOR seed): add the golden-ratio increment
  * 0x9E3779B97F4A7C15, then the two xor-shift-multiply rounds with the
  * published multipliers and a final xor-shift.
@@ -303,17 +304,153 @@ uint64_t orc_splitmix64(uint64_t state) {
 uint64_t orc_term_hash(int32_t t, uint64_t seed) { return orc_splitmix64((uint64_t)(uint32_t)t ^ seed); }
 
 /*
- * Simhash (Section III): every token occurrence is hashed to 64 bits; bit
- * column b adds +1 where the bit is 1 and -1 where it is 0; result bit b is 1
- * iff the column sum is strictly greater than 0 (a tie gives 0). Bit b of the
- * result is (F >> b) & 1.
+ * MD5 (RFC 1321) of a byte message; digest[16] receives the four state words
+ * as little-endian bytes. The message is padded with one 0x80 byte, zeros up
+ * to 56 mod 64 bytes, then its length in bits as a little-endian 64-bit word,
+ * and processed in 64-byte blocks of sixteen little-endian words. The additive
+ * constant of step i (1..64) is floor(2^32 * |sin(i)|), computed here from
+ * that definition.
  */
-void orc_simhash(int64_t n, const int64_t* offsets, const int32_t* tokens, uint64_t seed, uint64_t* F) {
+static uint32_t orc_rotl32(uint32_t x, int s) { return (x << s) | (x >> (32 - s)); }
+
+static uint8_t orc_pad_byte_le(const uint8_t* msg, int64_t len, int64_t padded, int64_t pos) {
+    if (pos < len) return msg[pos];
+    if (pos == len) return 0x80;
+    if (pos >= padded - 8) return (uint8_t)(((uint64_t)len * 8u) >> (8 * (pos - (padded - 8))));
+    return 0;
+}
+
+void orc_md5(const uint8_t* msg, int64_t len, uint8_t* digest) {
+    static const int shift[4][4] = {{7, 12, 17, 22}, {5, 9, 14, 20}, {4, 11, 16, 23}, {6, 10, 15, 21}};
+    uint32_t T[64];
+    for (int i = 0; i < 64; ++i) T[i] = (uint32_t)floor(4294967296.0 * fabs(sin((double)(i + 1))));
+    uint32_t state[4] = {0x67452301u, 0xEFCDAB89u, 0x98BADCFEu, 0x10325476u};
+    const int64_t padded = (len + 9 + 63) / 64 * 64;
+    for (int64_t blk = 0; blk < padded; blk += 64) {
+        uint32_t X[16];
+        for (int w = 0; w < 16; ++w) {
+            uint32_t v = 0;
+            for (int b = 3; b >= 0; --b) v = (v << 8) | orc_pad_byte_le(msg, len, padded, blk + 4 * w + b);
+            X[w] = v;
+        }
+        uint32_t a = state[0], b = state[1], c = state[2], d = state[3];
+        for (int i = 0; i < 64; ++i) {
+            const int round = i / 16;
+            uint32_t f;
+            int k;
+            if (round == 0) {        /* F(X,Y,Z) = XY v not(X) Z */
+                f = (b & c) | (~b & d);
+                k = i;
+            } else if (round == 1) { /* G(X,Y,Z) = XZ v Y not(Z) */
+                f = (b & d) | (c & ~d);
+                k = (1 + 5 * i) % 16;
+            } else if (round == 2) { /* H(X,Y,Z) = X xor Y xor Z */
+                f = b ^ c ^ d;
+                k = (5 + 3 * i) % 16;
+            } else {                 /* I(X,Y,Z) = Y xor (X v not(Z)) */
+                f = c ^ (b | ~d);
+                k = (7 * i) % 16;
+            }
+            /* a = b + ((a + f(b,c,d) + X[k] + T[i]) <<< s), then the roles of a, b, c, d rotate */
+            const uint32_t nb = b + orc_rotl32(a + f + X[k] + T[i], shift[round][i % 4]);
+            a = d;
+            d = c;
+            c = b;
+            b = nb;
+        }
+        state[0] += a;
+        state[1] += b;
+        state[2] += c;
+        state[3] += d;
+    }
+    for (int w = 0; w < 4; ++w)
+        for (int b = 0; b < 4; ++b) digest[4 * w + b] = (uint8_t)(state[w] >> (8 * b));
+}
+
+/*
+ * SHA-1 (FIPS 180-4, Section 6.1) of a byte message; digest[20] receives the
+ * five state words as big-endian bytes. Padding as MD5's but with the bit
+ * length and the message words big-endian. The round constants are
+ * floor(2^30 * sqrt(n)) for n = 2, 3, 5, 10, computed here from that
+ * definition.
+ */
+static uint8_t orc_pad_byte_be(const uint8_t* msg, int64_t len, int64_t padded, int64_t pos) {
+    if (pos < len) return msg[pos];
+    if (pos == len) return 0x80;
+    if (pos >= padded - 8) return (uint8_t)(((uint64_t)len * 8u) >> (8 * (7 - (pos - (padded - 8)))));
+    return 0;
+}
+
+void orc_sha1(const uint8_t* msg, int64_t len, uint8_t* digest) {
+    static const double radicand[4] = {2.0, 3.0, 5.0, 10.0};
+    uint32_t K[4];
+    for (int q = 0; q < 4; ++q) K[q] = (uint32_t)floor(1073741824.0 * sqrt(radicand[q]));
+    uint32_t H[5] = {0x67452301u, 0xEFCDAB89u, 0x98BADCFEu, 0x10325476u, 0xC3D2E1F0u};
+    const int64_t padded = (len + 9 + 63) / 64 * 64;
+    for (int64_t blk = 0; blk < padded; blk += 64) {
+        uint32_t W[80];
+        for (int t = 0; t < 16; ++t) {
+            uint32_t v = 0;
+            for (int b = 0; b < 4; ++b) v = (v << 8) | orc_pad_byte_be(msg, len, padded, blk + 4 * t + b);
+            W[t] = v;
+        }
+        for (int t = 16; t < 80; ++t) W[t] = orc_rotl32(W[t - 3] ^ W[t - 8] ^ W[t - 14] ^ W[t - 16], 1);
+        uint32_t a = H[0], b = H[1], c = H[2], d = H[3], e = H[4];
+        for (int t = 0; t < 80; ++t) {
+            uint32_t f;
+            if (t < 20) f = (b & c) ^ (~b & d);             /* Ch */
+            else if (t < 40) f = b ^ c ^ d;                 /* Parity */
+            else if (t < 60) f = (b & c) ^ (b & d) ^ (c & d); /* Maj */
+            else f = b ^ c ^ d;                             /* Parity */
+            const uint32_t T = orc_rotl32(a, 5) + f + e + K[t / 20] + W[t];
+            e = d;
+            d = c;
+            c = orc_rotl32(b, 30);
+            b = a;
+            a = T;
+        }
+        H[0] += a;
+        H[1] += b;
+        H[2] += c;
+        H[3] += d;
+        H[4] += e;
+    }
+    for (int w = 0; w < 5; ++w)
+        for (int b = 0; b < 4; ++b) digest[4 * w + b] = (uint8_t)(H[w] >> (24 - 8 * b));
+}
+
+/*
+ * The 64-bit feature hash of term t under each hash mode. Mode 0 is the
+ * SplitMix64 step above. Modes 1 (MD5) and 2 (SHA-1) are the paper's hashes
+ * (Section III), applied to a 12-byte message: t as a 32-bit little-endian
+ * word, then the seed as a 64-bit little-endian word; the feature is the
+ * first 8 digest bytes read as a little-endian word (bit b of the feature is
+ * bit b % 8 of digest byte b / 8).
+ */
+uint64_t orc_feature_hash(int32_t t, uint64_t seed, int32_t mode) {
+    if (mode == 0) return orc_term_hash(t, seed);
+    uint8_t msg[12], dg[20];
+    for (int b = 0; b < 4; ++b) msg[b] = (uint8_t)((uint32_t)t >> (8 * b));
+    for (int b = 0; b < 8; ++b) msg[4 + b] = (uint8_t)(seed >> (8 * b));
+    if (mode == 1) orc_md5(msg, 12, dg);
+    else orc_sha1(msg, 12, dg);
+    uint64_t h = 0;
+    for (int b = 0; b < 8; ++b) h |= (uint64_t)dg[b] << (8 * b);
+    return h;
+}
+
+/*
+ * Simhash (Section III): every token occurrence is hashed to 64 bits (feature
+ * hash mode `mode`); bit column b adds +1 where the bit is 1 and -1 where it
+ * is 0; result bit b is 1 iff the column sum is strictly greater than 0 (a tie
+ * gives 0). Bit b of the result is (F >> b) & 1.
+ */
+void orc_simhash(int64_t n, const int64_t* offsets, const int32_t* tokens, uint64_t seed, int32_t mode, uint64_t* F) {
     for (int64_t d = 0; d < n; ++d) {
         int64_t col[64];
         for (int b = 0; b < 64; ++b) col[b] = 0;
         for (int64_t x = offsets[d]; x < offsets[d + 1]; ++x) {
-            uint64_t h = orc_term_hash(tokens[x], seed);
+            uint64_t h = orc_feature_hash(tokens[x], seed, mode);
             for (int b = 0; b < 64; ++b) col[b] += ((h >> b) & 1ULL) ? 1 : -1;
         }
         uint64_t f = 0;

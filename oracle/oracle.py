@@ -21,12 +21,14 @@ import numpy as np
 from . import build as _build
 
 MODE_ALL, MODE_REGION, MODE_DF1 = 0, 1, 2
+HASH_SPLITMIX64, HASH_MD5, HASH_SHA1 = 0, 1, 2
 WEIGHT_COUNT, WEIGHT_TFIDF = 0, 1
 
 _i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
 _i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
 _u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
 _vp = C.c_void_p
 
 
@@ -47,7 +49,10 @@ def _sig(lib):
         "orc_cosine_pairs": (i64, [i64, _i64p, _i32p, _f64p, f64, _i32p, _i32p, _f64p, i64]),
         "orc_splitmix64": (u64, [u64]),
         "orc_term_hash": (u64, [i32, u64]),
-        "orc_simhash": (None, [i64, _i64p, _i32p, u64, _u64p]),
+        "orc_md5": (None, [_vp, i64, _u8p]),
+        "orc_sha1": (None, [_vp, i64, _u8p]),
+        "orc_feature_hash": (u64, [i32, u64, i32]),
+        "orc_simhash": (None, [i64, _i64p, _i32p, u64, i32, _u64p]),
         "orc_hamming": (i32, [u64, u64]),
         "orc_hamming_pairs": (i64, [_u64p, i64, _vp, i64, i32, _i32p, _i32p, _i32p, i64]),
         "orc_error_stats": (None, [_f64p, _f64p, i64, _f64p]),
@@ -195,12 +200,25 @@ class Oracle:
     def term_hash(self, t, seed):
         return int(self.lib.orc_term_hash(int(t), C.c_uint64(int(seed) & (2**64 - 1))))
 
-    def simhash(self, offsets, tokens, seed):
+    def md5(self, msg: bytes) -> bytes:
+        out = np.zeros(16, np.uint8)
+        self.lib.orc_md5(C.c_char_p(bytes(msg)), len(msg), out)
+        return out.tobytes()
+
+    def sha1(self, msg: bytes) -> bytes:
+        out = np.zeros(20, np.uint8)
+        self.lib.orc_sha1(C.c_char_p(bytes(msg)), len(msg), out)
+        return out.tobytes()
+
+    def feature_hash(self, t, seed, mode):
+        return int(self.lib.orc_feature_hash(int(t), C.c_uint64(int(seed) & (2**64 - 1)), int(mode)))
+
+    def simhash(self, offsets, tokens, seed, mode=HASH_SPLITMIX64):
         offsets = np.ascontiguousarray(offsets, np.int64)
         n = offsets.shape[0] - 1
         out = np.zeros(n, np.uint64)
         self.lib.orc_simhash(n, offsets, np.ascontiguousarray(tokens, np.int32),
-                             C.c_uint64(int(seed) & (2**64 - 1)), out)
+                             C.c_uint64(int(seed) & (2**64 - 1)), int(mode), out)
         return out
 
     def hamming(self, a, b):
@@ -238,6 +256,7 @@ class Params:
     hamming_max: int = 3
     seed: int = 0x1810030990
     bf16: bool = False  # precision form: per-term weights stored as bfloat16
+    feature_hash: int = HASH_SPLITMIX64  # Simhash feature hash: HASH_SPLITMIX64, HASH_MD5 or HASH_SHA1
 
     @property
     def L_eff(self) -> int:
@@ -279,7 +298,7 @@ def build_index(offsets, tokens, vocab, params: Params | None = None, orc: Oracl
     part, used = o.select_refs(df, n, p.mode, p.L_eff, p.region_start, p.k)
     rnorm = o.ref_norms(part, p.k, idf)
     S = o.signatures(row_ptr, terms, w, part, idf, rnorm, p.k)
-    F = o.simhash(offsets, tokens, p.seed)
+    F = o.simhash(offsets, tokens, p.seed, p.feature_hash)
     return OracleIndex(p, n, vocab, df, idf, idf_values, part, used, rnorm, row_ptr, terms, counts, w, S, F)
 
 
@@ -290,5 +309,5 @@ def signature(index: OracleIndex, offsets, tokens, orc: Oracle | None = None):
     row_ptr, terms, counts = o.term_counts(offsets, tokens)
     w = o.weights(terms, counts, index.idf)
     S = o.signatures(row_ptr, terms, w, index.part, index.idf, index.rnorm, p.k)
-    F = o.simhash(offsets, tokens, p.seed)
+    F = o.simhash(offsets, tokens, p.seed, p.feature_hash)
     return S, F, (row_ptr, terms, w)

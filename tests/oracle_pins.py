@@ -5,7 +5,9 @@ The same suite runs on the real oracle (all must pass) and on deliberately
 broken copies of it (``test_oracle_mutants.py``: at least one must fail for
 each planted mistake). What each pin rests on:
 
-* published values (SplitMix64 outputs from state 0);
+* published values (SplitMix64 outputs from state 0; the MD5 test suite of
+  RFC 1321 and SHA-1 examples of FIPS 180) and Python's hashlib on messages
+  of every length around the padding boundaries;
 * closed forms worked by hand (idf values, a count-weighted signature,
   partition cuts of a hand-ranked df list, error statistics);
 * invariants the paper's definitions imply (symmetry, cos(x,x)=1, a
@@ -17,8 +19,10 @@ each planted mistake). What each pin rests on:
 """
 from __future__ import annotations
 
+import hashlib
 import math
 import os
+import shlex
 
 import numpy as np
 
@@ -59,6 +63,37 @@ def pin_splitmix64_published(o: Oracle):
         assert got == int(out, 16), (state, hex(got), out)
     # the term hash is one generator step from (t xor seed)
     assert o.term_hash(0, 0) == int(rows[0][1], 16)
+
+
+def pin_digests_published(o: Oracle):
+    with open(os.path.join(GOLDEN, "digests.txt")) as f:
+        rows = [shlex.split(ln) for ln in f if ln.strip() and not ln.startswith("#")]
+    assert len(rows) >= 8
+    for algo, msg, hexd in rows:
+        got = (o.md5 if algo == "md5" else o.sha1)(msg.encode())
+        assert got.hex() == hexd, (algo, msg, got.hex())
+
+
+def pin_digests_match_hashlib(o: Oracle):
+    """Every message length from 0 to 130 bytes (one, two and three padded blocks, both sides
+    of the 56-byte length-field boundary) and a few long ones, against Python's hashlib."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    for n in list(range(131)) + [191, 192, 1000]:
+        m = rng.integers(0, 256, size=n, dtype=np.uint8).tobytes()
+        assert o.md5(m) == hashlib.md5(m).digest(), n
+        assert o.sha1(m) == hashlib.sha1(m).digest(), n
+
+
+def pin_feature_hash_modes(o: Oracle):
+    """The 12-byte message (term, then seed, little-endian) and the first 8 digest bytes taken
+    little-endian, against hashlib; mode 0 is the SplitMix64 step."""
+    rng = np.random.Generator(np.random.PCG64(12))
+    for t, seed in [(0, 0), (1, 0), (0x7FFFFFFF, 2**64 - 1), (12345, 0x1810030990)] + \
+            [(int(rng.integers(0, 2**31)), int(rng.integers(0, 2**63))) for _ in range(20)]:
+        msg = t.to_bytes(4, "little") + seed.to_bytes(8, "little")
+        assert o.feature_hash(t, seed, 1) == int.from_bytes(hashlib.md5(msg).digest()[:8], "little")
+        assert o.feature_hash(t, seed, 2) == int.from_bytes(hashlib.sha1(msg).digest()[:8], "little")
+        assert o.feature_hash(t, seed, 0) == o.term_hash(t, seed)
 
 
 def pin_idf_closed_form(o: Oracle):
@@ -200,11 +235,16 @@ def pin_scaled_and_disjoint_docs(o: Oracle):
 
 
 def pin_simhash_small_cases(o: Oracle):
+    for mode in (0, 1, 2):
+        _simhash_small_cases(o, mode)
+
+
+def _simhash_small_cases(o: Oracle, mode):
     seed = 0x1234
-    h = [o.term_hash(t, seed) for t in range(4)]
+    h = [brute.feature_hash(t, seed, mode) for t in range(4)]
     # one term, any multiplicity: the term's own hash
     offs, toks = _csr([[2], [2, 2, 2], [0, 1], [0, 1, 1], [0, 1, 3], [0, 1, 3], []])
-    F = o.simhash(offs, toks, seed)
+    F = o.simhash(offs, toks, seed, mode)
     assert int(F[0]) == h[2] and int(F[1]) == h[2]
     # two terms once each: a column is positive only where both bits are 1 (a tie gives 0)
     assert int(F[2]) == h[0] & h[1]
@@ -251,9 +291,10 @@ def pin_brute_force_agreement(o: Oracle):
         docs = _tiny_corpus(100 + seed, n_docs=30)
         offs, toks = _csr(docs)
         vocab = 60
-        p = Params(k=k, L=L, mode=mode, region_start=start, weighting=1 if tfidf else 0, seed=0xABCDEF + seed)
+        p = Params(k=k, L=L, mode=mode, region_start=start, weighting=1 if tfidf else 0, seed=0xABCDEF + seed,
+                   feature_hash=seed % 3)
         idx = build_index(offs, toks, vocab, p, o)
-        ref = brute.pipeline(offs, toks, vocab, k, p.L_eff, mode, start, tfidf, p.seed)
+        ref = brute.pipeline(offs, toks, vocab, k, p.L_eff, mode, start, tfidf, p.seed, p.feature_hash)
         for t in range(vocab):
             assert idx.df[t] == ref["df"].get(t, 0)
         if tfidf:

@@ -39,6 +39,19 @@ MUTANTS = {
     "simhash_no_minus_one": ("col[b] += ((h >> b) & 1ULL) ? 1 : -1;", "col[b] += ((h >> b) & 1ULL) ? 1 : 0;"),
     "splitmix_shift": ("z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;", "z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ULL;"),
     "term_hash_no_seed": ("orc_splitmix64((uint64_t)(uint32_t)t ^ seed)", "orc_splitmix64((uint64_t)(uint32_t)t)"),
+    "md5_round2_index": ("k = (1 + 5 * i) % 16;", "k = (5 * i) % 16;"),
+    "md5_round3_shift": ("{4, 11, 16, 23}", "{4, 11, 16, 22}"),
+    "md5_I_no_not": ("f = c ^ (b | ~d);", "f = c ^ (b | d);"),
+    "md5_length_in_bytes": ("(uint8_t)(((uint64_t)len * 8u) >> (8 * (pos - (padded - 8))))",
+                            "(uint8_t)(((uint64_t)len) >> (8 * (pos - (padded - 8))))"),
+    "md5_no_feed_forward": ("state[2] += c;", "state[2] = c;"),
+    "sha1_rotate_31": ("c = orc_rotl32(b, 30);", "c = orc_rotl32(b, 31);"),
+    "sha1_schedule_index": ("W[t - 3] ^ W[t - 8] ^ W[t - 14] ^ W[t - 16]", "W[t - 3] ^ W[t - 8] ^ W[t - 14] ^ W[t - 15]"),
+    "sha1_maj_dropped_term": ("f = (b & c) ^ (b & d) ^ (c & d);", "f = (b & c) ^ (b & d);"),
+    "sha1_constant_sqrt3": ("{2.0, 3.0, 5.0, 10.0}", "{2.0, 2.0, 5.0, 10.0}"),
+    "feature_digest_big_endian": ("h |= (uint64_t)dg[b] << (8 * b);", "h |= (uint64_t)dg[b] << (8 * (7 - b));"),
+    "feature_seed_dropped": ("msg[4 + b] = (uint8_t)(seed >> (8 * b));", "msg[4 + b] = 0;"),
+    "feature_md5_sha1_swapped": ("if (mode == 1) orc_md5(msg, 12, dg);", "if (mode == 2) orc_md5(msg, 12, dg);"),
     "hamming_counts_equal_bits": ("c += (int32_t)((x >> bit) & 1ULL);", "c += (int32_t)(((x >> bit) & 1ULL) ^ 1ULL);"),
     "pairs_include_self": ("for (int64_t j = i + 1; j < n; ++j) {\n            double c = orc_cos_dense",
                            "for (int64_t j = i; j < n; ++j) {\n            double c = orc_cos_dense"),

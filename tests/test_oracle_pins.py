@@ -2,13 +2,15 @@
 
 Parity status of the oracle's functions (every function is pinned):
   orc_splitmix64 / orc_term_hash  published SplitMix64 outputs
+  orc_md5 / orc_sha1               RFC 1321 test suite, FIPS 180 examples; hashlib, lengths 0-130
+  orc_feature_hash                 hashlib on the 12-byte term/seed message, all three modes
   orc_idf                          hand-evaluated closed forms
   orc_term_counts, orc_df          hand example; brute force
   orc_select_refs                  hand-ranked example for all three modes; brute force
   orc_ref_norms, orc_signatures    hand closed form; one-hot reference documents;
                                    singleton-partition limit equals exact cosine; brute force
   orc_cos_dense, orc_cosine_pair   symmetry, cos(x,x)=1, scaled/disjoint docs; brute force
-  orc_simhash, orc_hamming         one/two/three-term closed forms; textbook popcount
+  orc_simhash, orc_hamming         one/two/three-term closed forms (each hash mode); textbook popcount
   orc_*_pairs                      emission rules by hand; brute-force pair sets
   orc_error_stats                  hand example
 """
