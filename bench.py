@@ -249,6 +249,50 @@ def form_precision(args):
     ctx.close()
 
 
+def form_features(args):
+    """Simhash feature hashes on the one-million-document corpus: the signature pass (rows a1-a4,
+    Simhash fused) over every document under SplitMix64, MD5 and SHA-1 features, and the
+    per-vocabulary feature table the MD5 / SHA-1 modes compute with the index."""
+    import torch
+    from paper_1810_03099_gb300 import mrc, synth
+    c = synth.make_corpus_device("precision")
+    ctx = mrc.Context()
+    n = c.n_docs
+    sig = torch.empty((n, 64), dtype=torch.float32, device="cuda")
+    sh = torch.empty(n, dtype=torch.int64, device="cuda")
+    res = {}
+    for name, mode in (("splitmix64", mrc.HASH_SPLITMIX64), ("md5", mrc.HASH_MD5), ("sha1", mrc.HASH_SHA1)):
+        p = mrc.params_default(k=64, feature_hash=mode)
+        idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, p)
+        idx.free()
+        ctx.reset_stats()
+        ctx.set_timing(True)
+        idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, p)
+        ctx.set_timing(False)
+        table_ms = sum(s["ms"] for s in ctx.kernel_stats() if s["name"] == "feature_table")
+        for _ in range(3):
+            mrc.mrc_signature(ctx, idx, c.offsets, c.tokens, sig, sh)
+        torch.cuda.synchronize()
+        reps = 10
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(reps):
+            mrc.mrc_signature(ctx, idx, c.offsets, c.tokens, sig, sh)
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / reps
+        res[name] = {"signature_ms": ms, "docs_per_s": n / (ms * 1e-3), "feature_table_ms": table_ms,
+                     "simhash_crc": int(sh[: min(n, 4096)].sum().item())}
+        idx.free()
+    line = {"metric": "docs/s", "form": "features", "value": res["md5"]["docs_per_s"], "unit": "docs/s",
+            "vs_splitmix64": res["md5"]["docs_per_s"] / res["splitmix64"]["docs_per_s"],
+            "config": {"workload": f"signature pass: {n} docs, {c.n_tokens} tokens, V={c.vocab}, k=64, "
+                                   "Simhash with MD5 features (SplitMix64 and SHA-1 beside it)"},
+            "detail": res}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def form_batching(args):
     """Batching form: 4,096 batches of 1-512 documents (log-uniform 20-20,000 tokens) against the
     one-million-document precision index, one graph launch per batch, autotuned tile width."""
@@ -343,7 +387,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mrc", choices=["mrc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="news20", choices=["news20", "precision", "batching", "serving", "forms"],
+    ap.add_argument("--form", default="news20", choices=["news20", "precision", "batching", "serving", "features", "forms"],
                     help="news20 (default): the headline step; the others measure the three forms")
     ap.add_argument("--batches", type=int, default=4096)
     ap.add_argument("--serving-docs", type=int, default=10_000_000)
@@ -352,7 +396,8 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         for f in (["precision", "batching", "serving"] if args.form == "forms" else [args.form]):
-            {"precision": form_precision, "batching": form_batching, "serving": form_serving}[f](args)
+            {"precision": form_precision, "batching": form_batching, "serving": form_serving,
+             "features": form_features}[f](args)
         return
 
     rank = int(os.environ.get("RANK", "0"))

@@ -66,6 +66,13 @@ typedef int32_t mrc_status;
 #define MRC_PREC_BF16_FP8 1 /* BF16 weights, FP8 E4M3 compare, FP32 rescoring near tau  */
 #define MRC_PREC_FP16 2     /* FP16 signatures, FP16 compare, FP32 rescoring near tau   */
 
+/* The 64-bit Simhash feature hash of a term t (Section III hashes words with MD5 or SHA1). */
+#define MRC_HASH_SPLITMIX64 0 /* one SplitMix64 step (Steele, Lea, Flood 2014) from t XOR seed */
+#define MRC_HASH_MD5 1        /* MD5 (RFC 1321) of the 12 bytes t (int32, little-endian), seed
+                                 (uint64, little-endian); the first 8 digest bytes, read as a
+                                 little-endian word, are the feature                         */
+#define MRC_HASH_SHA1 2       /* SHA-1 (FIPS 180-4) of the same message, same 8 bytes       */
+
 #define MRC_MAX_K 256               /* longest signature                                */
 #define MRC_MAX_DOC_TOKENS 65536    /* longest document (exact per-document sums)       */
 
@@ -94,7 +101,8 @@ typedef struct {
   float tau;            /* similarity threshold (inclusive), e.g. 0.9                       */
   float margin;         /* reduced precision: candidates >= tau - margin are rescored       */
   int32_t hamming_max;  /* Simhash: pairs with Hamming distance <= hamming_max              */
-  int32_t reserved;     /* must be 0                                                        */
+  int32_t feature_hash; /* MRC_HASH_*: Simhash feature hash (MD5 / SHA-1: a per-term table
+                           of 8 * vocab bytes is computed with the index)                  */
   uint64_t seed;        /* seed of the 64-bit Simhash feature hash                          */
 } mrc_params;
 
@@ -110,7 +118,8 @@ typedef struct {
 } mrc_index_info;
 
 /* Fill *p with the library defaults: k = 8, L = 32k, REGION from the default
- * start, TF-IDF, FP32, tau = 0.9, margin = 0.02, hamming_max = 3, seed 0x1810030990. */
+ * start, TF-IDF, FP32, tau = 0.9, margin = 0.02, hamming_max = 3, SplitMix64
+ * features, seed 0x1810030990. */
 void mrc_params_default(mrc_params* p);
 
 /* Create a context bound to the current CUDA device and to `cuda_stream`

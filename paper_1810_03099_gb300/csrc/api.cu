@@ -267,6 +267,7 @@ bool valid_params(const mrc_params* p, std::string* why) {
   if (p->weighting != MRC_WEIGHT_COUNT && p->weighting != MRC_WEIGHT_TFIDF) return *why = "bad weighting", false;
   if (p->precision < MRC_PREC_FP32 || p->precision > MRC_PREC_FP16) return *why = "bad precision", false;
   if (!(p->margin >= 0.f)) return *why = "margin must be >= 0", false;
+  if (p->feature_hash < MRC_HASH_SPLITMIX64 || p->feature_hash > MRC_HASH_SHA1) return *why = "bad feature_hash", false;
   return true;
 }
 
@@ -396,11 +397,12 @@ mrc_status alloc_index_arrays(mrc_ctx* ctx, mrc_index* x) {
   const size_t n = (size_t)std::max<int64_t>(x->n_docs, 1), V = (size_t)x->vocab, k = (size_t)x->k;
   const bool f16 = x->params.precision == MRC_PREC_FP32 || x->params.precision == MRC_PREC_FP16;
   const bool e4m3 = x->params.precision == MRC_PREC_BF16_FP8;
+  const bool fh = x->params.feature_hash != MRC_HASH_SPLITMIX64;
   const size_t sizes[] = {4 * V, 4 * V, 8 * V, 4 * k, 4 * n * k, 4 * n * k, 8 * n,
                           f16 ? 2 * n * (size_t)x->kp : 0, e4m3 ? n * (size_t)x->kp8 : 0, e4m3 ? 4 * n : 0,
-                          e4m3 ? 4 * ((n + 127) / 128) : 0, 8 * k};
-  size_t off[12], total = 0;
-  for (int q = 0; q < 12; ++q) {
+                          e4m3 ? 4 * ((n + 127) / 128) : 0, 8 * k, fh ? 8 * V : 0};
+  size_t off[13], total = 0;
+  for (int q = 0; q < 13; ++q) {
     off[q] = total;
     total += (sizes[q] + 255) / 256 * 256;
   }
@@ -423,6 +425,11 @@ mrc_status alloc_index_arrays(mrc_ctx* ctx, mrc_index* x) {
   x->qnorm = e4m3 ? (float*)(b + off[9]) : nullptr;
   x->qnorm_min = e4m3 ? (float*)(b + off[10]) : nullptr;
   x->rnorm = (double*)(b + off[11]);
+  x->fhash = fh ? (uint64_t*)(b + off[12]) : nullptr;
+  if (fh) {  // the Simhash feature of every vocabulary term, computed once per index
+    const cudaError_t e = launch_feature_table(ctx, x->vocab, x->params.seed, x->params.feature_hash, x->fhash);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "feature hash table");
+  }
   return MRC_OK;
 }
 
@@ -629,7 +636,8 @@ mrc_status launch_index_signatures(mrc_ctx* ctx, mrc_index* x, const DocsDev& d)
   if (x->op_lo) cudaMemsetAsync(x->op_lo, 0, sizeof(uint16_t) * (size_t)x->n_docs * x->kp, ctx->stream);
   if (x->op_e4m3) cudaMemsetAsync(x->op_e4m3, 0, (size_t)x->n_docs * x->kp8, ctx->stream);
   cudaError_t e = launch_signature(ctx, d, x->vocab, x->tinfo, x->rinv, x->k,
-                                   x->params.precision == MRC_PREC_BF16_FP8, x->params.seed, index_sig_out(x));
+                                   x->params.precision == MRC_PREC_BF16_FP8, x->params.seed,
+                                   x->fhash, index_sig_out(x));
   if (e == cudaSuccess && x->qnorm_min) e = launch_block_min(ctx, x->qnorm, x->n_docs, x->qnorm_min);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "signature pass");
   return MRC_OK;
@@ -753,7 +761,8 @@ mrc_status mrc_signature(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* d
   o.simhash = sh_host ? (uint64_t*)ws_get(ctx, "sig.simhash", sizeof(uint64_t) * (size_t)n, &st) : simhash;
   if (st != MRC_OK) return st;
   cudaError_t e = launch_signature(ctx, d, index->vocab, index->tinfo, index->rinv, index->k,
-                                   index->params.precision == MRC_PREC_BF16_FP8, index->params.seed, o);
+                                   index->params.precision == MRC_PREC_BF16_FP8, index->params.seed,
+                                   index->fhash, o);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "signature pass");
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;
   if (sig_host) e = cudaMemcpyAsync(sig, o.sig, sizeof(float) * (size_t)n * index->k, cudaMemcpyDeviceToHost, ctx->stream);

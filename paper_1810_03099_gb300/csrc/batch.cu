@@ -129,7 +129,7 @@ cudaError_t record(mrc_batch* b) {
     o.op_hi = b->d_op;
     o.kp = x->kp;
   }
-  e = launch_signature(ctx, d, x->vocab, x->tinfo, x->rinv, x->k, 0, x->params.seed, o);
+  e = launch_signature(ctx, d, x->vocab, x->tinfo, x->rinv, x->k, 0, x->params.seed, x->fhash, o);
   if (e != cudaSuccess) return e;
   GemmArgs g{};
   g.na = b->max_docs;

@@ -63,6 +63,97 @@ __device__ __forceinline__ uint64_t feature_hash(uint32_t t, uint64_t seed) {
   return z ^ (z >> 31);
 }
 
+// The paper's feature hashes (Section III hashes words with MD5 or SHA1): MD5 (RFC 1321) or
+// SHA-1 (FIPS 180-4) of a 12-byte message, term t as a 32-bit little-endian word followed by
+// the seed as a 64-bit little-endian word; the feature is the first 8 digest bytes read as a
+// little-endian word. A 12-byte message is one padded block: the 0x80 byte follows it, then
+// zeros, then the bit length 96 in the last 8 bytes (little-endian for MD5, big-endian for
+// SHA-1). Computed once per vocabulary term (k_feature_table) and gathered per term.
+__constant__ uint32_t kMd5Add[64] = {  // floor(2^32 |sin(i)|), i = 1..64
+    0xD76AA478u, 0xE8C7B756u, 0x242070DBu, 0xC1BDCEEEu, 0xF57C0FAFu, 0x4787C62Au, 0xA8304613u, 0xFD469501u,
+    0x698098D8u, 0x8B44F7AFu, 0xFFFF5BB1u, 0x895CD7BEu, 0x6B901122u, 0xFD987193u, 0xA679438Eu, 0x49B40821u,
+    0xF61E2562u, 0xC040B340u, 0x265E5A51u, 0xE9B6C7AAu, 0xD62F105Du, 0x02441453u, 0xD8A1E681u, 0xE7D3FBC8u,
+    0x21E1CDE6u, 0xC33707D6u, 0xF4D50D87u, 0x455A14EDu, 0xA9E3E905u, 0xFCEFA3F8u, 0x676F02D9u, 0x8D2A4C8Au,
+    0xFFFA3942u, 0x8771F681u, 0x6D9D6122u, 0xFDE5380Cu, 0xA4BEEA44u, 0x4BDECFA9u, 0xF6BB4B60u, 0xBEBFBC70u,
+    0x289B7EC6u, 0xEAA127FAu, 0xD4EF3085u, 0x04881D05u, 0xD9D4D039u, 0xE6DB99E5u, 0x1FA27CF8u, 0xC4AC5665u,
+    0xF4292244u, 0x432AFF97u, 0xAB9423A7u, 0xFC93A039u, 0x655B59C3u, 0x8F0CCC92u, 0xFFEFF47Du, 0x85845DD1u,
+    0x6FA87E4Fu, 0xFE2CE6E0u, 0xA3014314u, 0x4E0811A1u, 0xF7537E82u, 0xBD3AF235u, 0x2AD7D2BBu, 0xEB86D391u,
+};
+
+__device__ __forceinline__ uint32_t rotl32(uint32_t x, int s) { return __funnelshift_l(x, x, s); }
+__device__ __forceinline__ uint32_t bswap32(uint32_t x) { return __byte_perm(x, 0u, 0x0123); }
+
+__device__ uint64_t md5_feature(uint32_t t, uint64_t seed) {
+  uint32_t X[16] = {t, (uint32_t)seed, (uint32_t)(seed >> 32), 0x80u, 0u, 0u, 0u, 0u,
+                    0u, 0u, 0u, 0u, 0u, 0u, 96u, 0u};
+  const int shift[16] = {7, 12, 17, 22, 5, 9, 14, 20, 4, 11, 16, 23, 6, 10, 15, 21};
+  uint32_t a = 0x67452301u, b = 0xEFCDAB89u, c = 0x98BADCFEu, d = 0x10325476u;
+#pragma unroll
+  for (int i = 0; i < 64; ++i) {
+    const int r = i >> 4;
+    uint32_t f;
+    int g;
+    if (r == 0) {
+      f = (b & c) | (~b & d);
+      g = i;
+    } else if (r == 1) {
+      f = (b & d) | (c & ~d);
+      g = (1 + 5 * i) & 15;
+    } else if (r == 2) {
+      f = b ^ c ^ d;
+      g = (5 + 3 * i) & 15;
+    } else {
+      f = c ^ (b | ~d);
+      g = (7 * i) & 15;
+    }
+    const uint32_t nb = b + rotl32(a + f + X[g] + kMd5Add[i], shift[4 * r + (i & 3)]);
+    a = d;
+    d = c;
+    c = b;
+    b = nb;
+  }
+  // digest bytes 0..7 are the first two state words, little-endian
+  return (uint64_t)(0x67452301u + a) | ((uint64_t)(0xEFCDAB89u + b) << 32);
+}
+
+__device__ uint64_t sha1_feature(uint32_t t, uint64_t seed) {
+  uint32_t W[16] = {bswap32(t), bswap32((uint32_t)seed), bswap32((uint32_t)(seed >> 32)), 0x80000000u,
+                    0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 96u};
+  uint32_t a = 0x67452301u, b = 0xEFCDAB89u, c = 0x98BADCFEu, d = 0x10325476u, e = 0xC3D2E1F0u;
+#pragma unroll
+  for (int i = 0; i < 80; ++i) {
+    uint32_t w;
+    if (i < 16) {
+      w = W[i];
+    } else {  // message schedule in a 16-word ring
+      w = rotl32(W[(i - 3) & 15] ^ W[(i - 8) & 15] ^ W[(i - 14) & 15] ^ W[i & 15], 1);
+      W[i & 15] = w;
+    }
+    uint32_t f, kc;
+    if (i < 20) {
+      f = (b & c) ^ (~b & d);
+      kc = 0x5A827999u;
+    } else if (i < 40) {
+      f = b ^ c ^ d;
+      kc = 0x6ED9EBA1u;
+    } else if (i < 60) {
+      f = (b & c) ^ (b & d) ^ (c & d);
+      kc = 0x8F1BBCDCu;
+    } else {
+      f = b ^ c ^ d;
+      kc = 0xCA62C1D6u;
+    }
+    const uint32_t tmp = rotl32(a, 5) + f + e + kc + w;
+    e = d;
+    d = c;
+    c = rotl32(b, 30);
+    b = a;
+    a = tmp;
+  }
+  // digest bytes 0..7 are the first two state words, big-endian
+  return (uint64_t)bswap32(0x67452301u + a) | ((uint64_t)bswap32(0xEFCDAB89u + b) << 32);
+}
+
 // 32x32 bit-matrix transpose across a warp: on entry lane r holds row r
 // (bit c = element (r, c)); on exit lane r holds column r of the input.
 __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
@@ -146,6 +237,7 @@ struct IngestParams {
   int32_t k;
   int32_t bf16w;
   uint64_t seed;
+  const uint64_t* fhash;  // [vocab] feature hashes (MD5 / SHA-1 modes); NULL: SplitMix64 of (t ^ seed)
   SigOut sig;
   // DENSE
   DenseOut dense;
@@ -178,11 +270,19 @@ struct Acc {
 struct TermAux {
   float w;
   int32_t code;
+  uint64_t h;  // feature hash from the table (signature pass with a hash table only)
 };
+
+// The Simhash feature of `key` from the hash table (signature pass with MD5 / SHA-1 features).
+template <int MODE>
+__device__ __forceinline__ uint64_t load_hash(const IngestParams& p, uint32_t key) {
+  return (MODE == kSIG && p.fhash && key != kEmpty) ? __ldg(reinterpret_cast<const unsigned long long*>(p.fhash) + key)
+                                                    : 0ull;
+}
 
 template <int MODE>
 __device__ __forceinline__ TermAux load_aux(const IngestParams& p, uint32_t key) {
-  TermAux x{1.0f, 0};
+  TermAux x{1.0f, 0, 0ull};
   if (MODE == kSIG) {
     const int2 ti = __ldg(reinterpret_cast<const int2*>(p.tinfo) + key);
     x.w = __int_as_float(ti.x);
@@ -218,7 +318,7 @@ __device__ __forceinline__ void chunk(const IngestParams& p, uint32_t key, uint3
   }
   if (MODE == kSIG) {
     if (p.sig.simhash) {
-      const uint64_t h = valid ? feature_hash(key, p.seed) : 0ull;
+      const uint64_t h = !valid ? 0ull : p.fhash ? aux.h : feature_hash(key, p.seed);
       const uint32_t hl = transpose32((uint32_t)h, lane);
       const uint32_t hh = transpose32((uint32_t)(h >> 32), lane);
       const uint32_t cmax = __reduce_max_sync(kFull, c);
@@ -462,12 +562,17 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
     Acc a{0ull, 0u, 0u};
     float inv_norm = 0.f;
     if (MODE == kDENSE) inv_norm = inv_norm_of(p.dense.norm[d]);
+    uint64_t h_next = load_hash<MODE>(p, lane < nnz ? keys[lane] : kEmpty);
     for (int s0 = 0; s0 < nnz; s0 += 32) {
       const int sl = s0 + lane;
       const uint32_t key = sl < nnz ? keys[sl] : kEmpty;
       const uint32_t c = sl < nnz ? cnts[sl] : 0u;
-      TermAux ax{1.0f, 0};
-      if (MODE != kDF && sl < nnz) ax = TermAux{aux_w[sl], aux_c[sl]};
+      TermAux ax{1.0f, 0, h_next};
+      h_next = load_hash<MODE>(p, sl + 32 < nnz ? keys[sl + 32] : kEmpty);  // next chunk's, in flight
+      if (MODE != kDF && sl < nnz) {
+        ax.w = aux_w[sl];
+        ax.code = aux_c[sl];
+      }
       chunk<MODE>(p, key, c, ax, lane, num_q, a, d, inv_norm, row_cnt_s, o0);
     }
     __syncwarp();
@@ -500,14 +605,16 @@ __device__ __forceinline__ void cta_walk(const IngestParams& p, const uint32_t* 
   int s0 = warp * 32;
   uint32_t key = s0 + lane < lim ? keys[s0 + lane] : kEmpty;
   uint32_t c = key != kEmpty ? cnts[s0 + lane] : 0u;
-  TermAux ax{1.0f, 0};
+  TermAux ax{1.0f, 0, 0ull};
   if (MODE != kDF && key != kEmpty) ax = load_aux<MODE>(p, key);
+  ax.h = load_hash<MODE>(p, key);
   while (s0 < lim) {
     const int s1 = s0 + nwarps * 32;
     const uint32_t key1 = s1 + lane < lim ? keys[s1 + lane] : kEmpty;
     const uint32_t c1 = key1 != kEmpty ? cnts[s1 + lane] : 0u;
-    TermAux ax1{1.0f, 0};
+    TermAux ax1{1.0f, 0, 0ull};
     if (MODE != kDF && key1 != kEmpty) ax1 = load_aux<MODE>(p, key1);
+    ax1.h = load_hash<MODE>(p, key1);
     const unsigned occ = __ballot_sync(kFull, key != kEmpty);
     if (occ != 0u) {
       chunk<MODE>(p, key, c, ax, lane, num_q, a, d, inv_norm, row_cnt_s, o0);
@@ -896,6 +1003,19 @@ cudaError_t launch_term_info(mrc_ctx* ctx, const float* idf, const int32_t* part
   return cudaGetLastError();
 }
 
+__global__ void k_feature_table(int32_t vocab, uint64_t seed, int32_t mode, uint64_t* out) {
+  const int32_t t = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (t >= vocab) return;
+  out[t] = mode == MRC_HASH_SHA1 ? sha1_feature((uint32_t)t, seed) : md5_feature((uint32_t)t, seed);
+}
+
+cudaError_t launch_feature_table(mrc_ctx* ctx, int32_t vocab, uint64_t seed, int32_t mode, uint64_t* out) {
+  if (vocab <= 0) return cudaSuccess;
+  KernelTimer kt(ctx, "feature_table", 8.0 * vocab);
+  k_feature_table<<<(vocab + 255) / 256, 256, 0, ctx->stream>>>(vocab, seed, mode, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_idf(mrc_ctx* ctx, int64_t n_docs, const int32_t* df, int32_t vocab, int32_t weighting, float* idf,
                        TermInfo* tinfo) {
   KernelTimer kt(ctx, "idf", 8.0 * vocab);
@@ -905,6 +1025,7 @@ cudaError_t launch_idf(mrc_ctx* ctx, int64_t n_docs, const int32_t* df, int32_t 
 
 cudaError_t launch_signature(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo,
                                      const float* rinv, int32_t k, int32_t bf16_weights, uint64_t seed,
+                                     const uint64_t* fhash,
                                      const SigOut& out) {
   IngestParams p = base_params(d);
   p.vocab = vocab;
@@ -913,6 +1034,7 @@ cudaError_t launch_signature(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, cons
   p.k = k;
   p.bf16w = bf16_weights;
   p.seed = seed;
+  p.fhash = fhash;
   p.sig = out;
   return run_ingest<kSIG>(ctx, d, p, "signature", 4.0, 8.0 + 4.0 * k + 8.0);
 }
@@ -967,6 +1089,7 @@ namespace mrc {
 // err: [1] int32; all device memory, n_docs <= cap. *host_err receives the error word.
 cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo,
                                      const float* rinv, int32_t k, int32_t bf16_weights, uint64_t seed,
+                                     const uint64_t* fhash,
                                      const SigOut& out, int32_t* lists, int64_t cap, int32_t* counts, int32_t* err,
                                      int32_t* host_err) {
   *host_err = 0;
@@ -978,6 +1101,7 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
   p.k = k;
   p.bf16w = bf16_weights;
   p.seed = seed;
+  p.fhash = fhash;
   p.sig = out;
   int32_t* short_list = lists;
   int32_t* long_list = lists + cap;

@@ -85,6 +85,7 @@ struct mrc_index {
   float* sig = nullptr;           // [n * k] raw signatures
   float* sig_unit = nullptr;      // [n * k] unit signatures (FP32 rescoring)
   uint64_t* simhash = nullptr;    // [n]
+  uint64_t* fhash = nullptr;      // [vocab] Simhash features (MD5 / SHA-1 modes; NULL under SplitMix64)
   void* op_hi = nullptr;          // [n * kp] fp16 (hi or the single fp16 operand)
   void* op_lo = nullptr;          // [n * kp] fp16 (lo of the split)
   void* op_e4m3 = nullptr;        // [n * kp8] e4m3
@@ -182,7 +183,10 @@ struct SigOut {
   int32_t kp, kp8;
 };
 cudaError_t launch_signature(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo, const float* rinv,
-                             int32_t k, int32_t bf16_weights, uint64_t seed, const SigOut& out);
+                             int32_t k, int32_t bf16_weights, uint64_t seed, const uint64_t* fhash,
+                             const SigOut& out);
+// out[t] = the MD5 (mode MRC_HASH_MD5) or SHA-1 (MRC_HASH_SHA1) Simhash feature of term t < vocab.
+cudaError_t launch_feature_table(mrc_ctx* ctx, int32_t vocab, uint64_t seed, int32_t mode, uint64_t* out);
 // Packs rows of `sig` (normalised to unit length first when `normalize`) into compare operands.
 cudaError_t launch_pack(mrc_ctx* ctx, const float* sig, int64_t n, int32_t k, int32_t normalize, void* hi, void* lo,
                         void* e4m3, float* qnorm, float* unit, int32_t kp, int32_t kp8);

@@ -20,6 +20,7 @@ MRC_OK, MRC_ERR_INVALID, MRC_ERR_OOM, MRC_ERR_CAPACITY = 0, 1, 2, 3
 MRC_ERR_CUDA, MRC_ERR_TIMEOUT, MRC_ERR_UNSUPPORTED = 4, 5, 6
 SELECT_ALL, SELECT_REGION, SELECT_DF1 = 0, 1, 2
 WEIGHT_COUNT, WEIGHT_TFIDF = 0, 1
+HASH_SPLITMIX64, HASH_MD5, HASH_SHA1 = 0, 1, 2
 PREC_FP32, PREC_BF16_FP8, PREC_FP16 = 0, 1, 2
 MAX_K = 256
 
@@ -34,7 +35,7 @@ class MrcError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("k", C.c_int32), ("L", C.c_int32), ("select_mode", C.c_int32), ("region_start", C.c_int32),
                 ("weighting", C.c_int32), ("precision", C.c_int32), ("tau", C.c_float), ("margin", C.c_float),
-                ("hamming_max", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64)]
+                ("hamming_max", C.c_int32), ("feature_hash", C.c_int32), ("seed", C.c_uint64)]
 
 
 class Pair(C.Structure):

@@ -53,6 +53,7 @@ def test_struct_layouts_match_header(lib_path):
     assert ctypes.sizeof(mrc.Docs) == 24
     assert ctypes.sizeof(mrc.Params) == 48
     assert ctypes.sizeof(mrc.IndexInfo) == 40
+    assert mrc.Params.feature_hash.offset == 36 and mrc.Params.seed.offset == 40
 
 
 def test_params_default_is_pure_host(lib_path):
@@ -60,6 +61,7 @@ def test_params_default_is_pure_host(lib_path):
     p = mrc.params_default()
     assert p.k == 8 and p.L == -1 and p.select_mode == mrc.SELECT_REGION and p.weighting == mrc.WEIGHT_TFIDF
     assert abs(p.tau - 0.9) < 1e-7 and p.hamming_max == 3 and p.precision == mrc.PREC_FP32
+    assert p.feature_hash == mrc.HASH_SPLITMIX64 and p.seed == 0x1810030990
 
 
 def test_product_package_never_imports_the_oracle():

@@ -12,7 +12,8 @@ from __future__ import annotations
 import numpy as np
 import pytest
 
-from oracle.oracle import MODE_ALL, MODE_DF1, MODE_REGION, Oracle, Params, build_index, signature
+from oracle.oracle import (HASH_MD5, HASH_SHA1, MODE_ALL, MODE_DF1, MODE_REGION, Oracle, Params, build_index,
+                           signature)
 from paper_1810_03099_gb300 import synth
 from tests.gpu_common import compare_pairs, concat, csr, cuda_or_skip, edge_docs, mixed_corpus, pair_dict
 
@@ -52,7 +53,8 @@ def dev(torch, a):
 
 def mrc_params(M, p: Params, precision=0):
     return M.params_default(k=p.k, L=p.L, select_mode=p.mode, region_start=p.region_start, weighting=p.weighting,
-                            precision=precision, tau=p.tau, hamming_max=p.hamming_max, seed=p.seed)
+                            precision=precision, tau=p.tau, hamming_max=p.hamming_max, seed=p.seed,
+                            feature_hash=p.feature_hash)
 
 
 PARAM_CASES = [
@@ -61,6 +63,8 @@ PARAM_CASES = [
     Params(k=64, mode=MODE_DF1, L=200),
     Params(k=200, mode=MODE_ALL),
     Params(k=33, mode=MODE_REGION, L=500, region_start=40, seed=7),
+    Params(k=8, feature_hash=HASH_MD5),
+    Params(k=16, mode=MODE_ALL, weighting=0, feature_hash=HASH_SHA1, seed=2**64 - 1),
 ]
 
 
@@ -263,6 +267,43 @@ def test_cosine_allpairs_long_documents_and_no_head(torch, M, ctx, orc, n_docs, 
     rep = compare_pairs(pair_dict(got["i"], got["j"], got["score"]), pair_dict(pi, pj, ps), tau, BAND, COS_TOL,
                         lambda i, j: orc.cosine_pair(ref.row_ptr, ref.terms, ref.w, i, j))
     assert rep["n"] == tot and tot > 0
+    idx.free()
+
+
+@pytest.mark.parametrize("mode", [HASH_MD5, HASH_SHA1])
+def test_paper_feature_hashes_queries_reload(torch, M, ctx, orc, corpus, mode, tmp_path):
+    """MD5 / SHA-1 Simhash features (Section III): fingerprints of new documents (allocating and
+    no-allocation calls, also after a save / load round trip, which recomputes the feature
+    table) equal the oracle's bit for bit, and so do the Hamming pair sets."""
+    offs, toks = corpus
+    V = 5000
+    p = Params(k=8, feature_hash=mode, seed=0x0123456789ABCDEF)
+    ref = build_index(offs, toks, V, p, orc)
+    idx = M.mrc_build_index(ctx, dev(torch, offs), dev(torch, toks), V, mrc_params(M, p))
+    assert np.array_equal(M.mrc_index_export(ctx, idx)["simhash"], ref.F)
+    q = synth.make_corpus(synth.SPECS["tiny"].with_(n_docs=300, vocab=V, seed=98))
+    qo, qt = concat((q.offsets, q.tokens), csr(edge_docs(V, seed=6)))
+    _, F_ref, _ = signature(ref, qo, qt, orc)
+    path = str(tmp_path / "md5.mrcidx")
+    M.mrc_index_save(ctx, idx, path)
+    idx2 = M.mrc_index_load(ctx, path)
+    for x in (idx, idx2):
+        _, sh = M.mrc_signature(ctx, x, dev(torch, qo), dev(torch, qt))
+        assert np.array_equal(sh.cpu().numpy().view(np.uint64), F_ref)
+        n = qo.shape[0] - 1
+        sig = torch.empty((n, p.k), dtype=torch.float32, device="cuda")
+        sh2 = torch.empty(n, dtype=torch.int64, device="cuda")
+        M.mrc_signature_noalloc(ctx, x, dev(torch, qo), dev(torch, qt), sig, sh2)
+        assert np.array_equal(sh2.cpu().numpy().view(np.uint64), F_ref)
+    # a different mode gives different fingerprints (the table is the one asked for)
+    assert not np.array_equal(ref.F, build_index(offs, toks, V, Params(k=8, seed=p.seed), orc).F)
+    buf, total = M.simhash_match(ctx, dev(torch, F_ref.view(np.int64)), dev(torch, ref.F.view(np.int64)), 3)
+    got = M.pairs_to_numpy(buf)
+    tot, pi, pj, ph = orc.hamming_pairs(F_ref, ref.F, 3)
+    assert total == tot
+    assert sorted(zip(got["i"].tolist(), got["j"].tolist(), got["score"].astype(int).tolist())) == sorted(
+        zip(pi.tolist(), pj.tolist(), ph.tolist()))
+    idx2.free()
     idx.free()
 
 
