@@ -7,9 +7,22 @@ from __future__ import annotations
 
 import hashlib
 import math
+import re
 from collections import Counter
 
 MASK64 = (1 << 64) - 1
+
+
+def char3grams(doc: bytes):
+    """3-gram ids of one document: letter runs found by a regular expression, lower-cased,
+    every window of three letters numbered in base 26."""
+    out = []
+    for run in re.findall(rb"[A-Za-z]+", doc):
+        run = run.lower()
+        for i in range(len(run) - 2):
+            a, b, c = (x - ord("a") for x in run[i:i + 3])
+            out.append((a * 26 + b) * 26 + c)
+    return out
 
 
 def docs_from_csr(offsets, tokens):

@@ -29,6 +29,37 @@ static int cmp_i32(const void* a, const void* b) {
 }
 
 /*
+ * Character 3-grams of raw text (Section III: a document is the vector of its
+ * N-gram counts, N = 3; an N-gram is a sequence of N letters of the alphabet).
+ * Reading taken: the alphabet is the 26 ASCII letters with case folded
+ * (A-Z equal a-z), so there are 26^3 = 17,576 possible 3-grams; every other
+ * byte separates, and a 3-gram is any 3 consecutive letters of a document
+ * (a letter run of length m gives m - 2 of them). The 3-gram (x, y, z), each
+ * letter numbered 0..25, has id 676 x + 26 y + z. Document d is the bytes
+ * [text_offsets[d], text_offsets[d+1]); its 3-gram ids are written in text
+ * order. grams needs room for text_offsets[n] entries. Returns the total.
+ */
+static int orc_letter(uint8_t c) {
+    if (c >= 'a' && c <= 'z') return c - 'a';
+    if (c >= 'A' && c <= 'Z') return c - 'A';
+    return -1;
+}
+
+int64_t orc_char3grams(int64_t n, const int64_t* text_offsets, const uint8_t* text, int64_t* gram_offsets,
+                       int32_t* grams) {
+    int64_t out = 0;
+    gram_offsets[0] = 0;
+    for (int64_t d = 0; d < n; ++d) {
+        for (int64_t p = text_offsets[d]; p + 2 < text_offsets[d + 1]; ++p) {
+            int x = orc_letter(text[p]), y = orc_letter(text[p + 1]), z = orc_letter(text[p + 2]);
+            if (x >= 0 && y >= 0 && z >= 0) grams[out++] = 676 * x + 26 * y + z;
+        }
+        gram_offsets[d + 1] = out;
+    }
+    return out;
+}
+
+/*
  * Term counts of each document (Section III: a document becomes the vector of
  * its N-gram counts). Output rows are sorted by term id. Capacity of
  * terms/counts must be >= offsets[n]. Returns the number of entries written.

@@ -22,6 +22,7 @@ from . import build as _build
 
 MODE_ALL, MODE_REGION, MODE_DF1 = 0, 1, 2
 HASH_SPLITMIX64, HASH_MD5, HASH_SHA1 = 0, 1, 2
+GRAM_VOCAB = 26 ** 3  # character 3-grams over the case-folded 26-letter alphabet
 WEIGHT_COUNT, WEIGHT_TFIDF = 0, 1
 
 _i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
@@ -35,6 +36,7 @@ _vp = C.c_void_p
 def _sig(lib):
     i64, i32, f64, u64 = C.c_int64, C.c_int32, C.c_double, C.c_uint64
     spec = {
+        "orc_char3grams": (i64, [i64, _i64p, _u8p, _i64p, _i32p]),
         "orc_term_counts": (i64, [i64, _i64p, _i32p, _i64p, _i32p, _i32p]),
         "orc_df": (None, [i64, _i64p, _i32p, i32, _i64p]),
         "orc_idf": (None, [i64, i32, _i64p, _f64p]),
@@ -192,6 +194,19 @@ class Oracle:
         tot = self.lib.orc_cosine_pairs(n, row_ptr, terms, w, tau, pi, pj, ps, cap)
         m = min(tot, cap)
         return tot, pi[:m], pj[:m], ps[:m]
+
+    # ---- Section III: character 3-grams ------------------------------------------------
+    def char3grams(self, text_offsets, text):
+        """(gram_offsets [n+1] int64, grams [G] int32) of a text CSR (bytes as uint8)."""
+        text_offsets = np.ascontiguousarray(text_offsets, np.int64)
+        text = np.frombuffer(text, np.uint8) if isinstance(text, (bytes, bytearray)) else np.asarray(text, np.uint8)
+        padded = np.zeros(text.shape[0] + 2, np.uint8)  # two zero bytes after the text
+        padded[:text.shape[0]] = text
+        n = text_offsets.shape[0] - 1
+        go = np.zeros(n + 1, np.int64)
+        grams = np.zeros(max(int(text_offsets[-1]), 1), np.int32)
+        g = self.lib.orc_char3grams(n, text_offsets, padded, go, grams)
+        return go, grams[:g]
 
     # ---- Section III: Simhash ------------------------------------------------------------
     def splitmix64(self, state):

@@ -226,6 +226,85 @@ def make_corpus(spec: CorpusSpec | str, n_docs: int | None = None, seed: int | N
     return Corpus(spec, offsets, tokens, dup_src, edits)
 
 
+# ---------------------------------------------------------------------------------------------
+# Raw text (input of the character 3-gram front end)
+
+# Approximate relative letter frequencies of English text (a..z), so that the drawn words give
+# a skewed 3-gram law: a few 3-grams common, most rare, as in the paper's corpus statistics.
+_LETTER_FREQ = np.array([8.2, 1.5, 2.8, 4.3, 12.7, 2.2, 2.0, 6.1, 7.0, 0.15, 0.8, 4.0, 2.4, 6.7, 7.5, 1.9,
+                         0.1, 6.0, 6.3, 9.1, 2.8, 1.0, 2.4, 0.15, 2.0, 0.07])
+# Single-byte separators between words and their probabilities: space, newline, comma, full
+# stop, apostrophe, hyphen, a digit, tab.
+_SEPARATORS = np.frombuffer(b" \n,.'-7\t", np.uint8)
+_SEP_P = np.array([0.80, 0.05, 0.04, 0.04, 0.02, 0.02, 0.02, 0.01])
+
+
+@dataclass
+class TextCorpus:
+    words: Corpus  # the word-id documents the text renders (dup links included)
+    offsets: np.ndarray  # int64[N+1] byte offsets
+    text: np.ndarray  # uint8[B]
+
+    @property
+    def n_docs(self) -> int:
+        return int(self.offsets.shape[0] - 1)
+
+    @property
+    def n_bytes(self) -> int:
+        return int(self.text.shape[0])
+
+    def doc(self, i: int) -> bytes:
+        return self.text[self.offsets[i]:self.offsets[i + 1]].tobytes()
+
+
+def _lexicon(n_words: int, rng: np.random.Generator):
+    """Seeded word list: lengths 1 + Poisson(4) (at most 15 letters), letters drawn by English
+    letter frequency; 1 % of the words carry a two-byte UTF-8 letter (0xC3 0xA9) inside."""
+    lens = np.minimum(1 + rng.poisson(4.0, size=n_words), 15).astype(np.int64)
+    accent = rng.random(n_words) < 0.01
+    lens_b = lens + 2 * (accent & (lens >= 2))
+    offs = np.zeros(n_words + 1, np.int64)
+    np.cumsum(lens_b, out=offs[1:])
+    letters = (rng.choice(26, size=int(offs[-1]), p=_LETTER_FREQ / _LETTER_FREQ.sum()) + ord("a")).astype(np.uint8)
+    for w in np.nonzero(accent & (lens >= 2))[0].tolist():
+        at = int(offs[w]) + 1
+        letters[at:at + 2] = (0xC3, 0xA9)
+    return offs, letters
+
+
+def make_text_corpus(spec: CorpusSpec | str = "news20", n_docs: int | None = None, seed: int | None = None,
+                     words_median: float = 300.0) -> TextCorpus:
+    """Raw text shaped like NEWS20 posts: documents of words drawn as ``make_corpus`` draws
+    terms (topic mixtures over Zipf laws, lognormal lengths with median ``words_median`` words,
+    near-duplicates with 1-10 % of the words replaced), each word rendered from a seeded
+    lexicon, 10 % capitalised, followed by one separator byte."""
+    if isinstance(spec, str):
+        spec = SPECS[spec]
+    spec = spec.with_(length_median=float(words_median))
+    c = make_corpus(spec, n_docs=n_docs, seed=seed)
+    rng = np.random.Generator(np.random.PCG64(c.spec.seed + 7919))
+    lex_offs, lex = _lexicon(c.vocab, rng)
+    w = c.tokens.astype(np.int64)
+    wl = lex_offs[w + 1] - lex_offs[w]
+    out_len = wl + 1
+    starts = np.zeros(w.shape[0] + 1, np.int64)
+    np.cumsum(out_len, out=starts[1:])
+    B = int(starts[-1])
+    text = np.empty(B, np.uint8)
+    # every output byte: the word occurrence it belongs to and its position inside the word
+    occ = np.repeat(np.arange(w.shape[0], dtype=np.int64), out_len)
+    pos = np.arange(B, dtype=np.int64) - starts[occ]
+    is_sep = pos == wl[occ]
+    body = ~is_sep
+    text[body] = lex[lex_offs[w[occ[body]]] + pos[body]]
+    text[is_sep] = _SEPARATORS[rng.choice(_SEPARATORS.shape[0], size=w.shape[0], p=_SEP_P)]
+    cap = np.nonzero(rng.random(w.shape[0]) < 0.10)[0]
+    first = starts[cap]
+    text[first] = np.where((text[first] >= ord("a")) & (text[first] <= ord("z")), text[first] - 32, text[first])
+    offsets = starts[c.offsets]
+    return TextCorpus(c, offsets, text)
+
+
 def cached_corpus(name: str, cache_dir: str | None = None, **kw) -> Corpus:
     """``make_corpus`` with an on-disk .npz cache (large workloads take a while to draw)."""
     spec = SPECS[name]

@@ -22,6 +22,7 @@ from __future__ import annotations
 import hashlib
 import math
 import os
+import re
 import shlex
 
 import numpy as np
@@ -94,6 +95,36 @@ def pin_feature_hash_modes(o: Oracle):
         assert o.feature_hash(t, seed, 1) == int.from_bytes(hashlib.md5(msg).digest()[:8], "little")
         assert o.feature_hash(t, seed, 2) == int.from_bytes(hashlib.sha1(msg).digest()[:8], "little")
         assert o.feature_hash(t, seed, 0) == o.term_hash(t, seed)
+
+
+def _text_csr(docs):
+    offs = np.zeros(len(docs) + 1, np.int64)
+    offs[1:] = np.cumsum([len(d) for d in docs])
+    return offs, np.frombuffer(b"".join(docs), np.uint8).copy()
+
+
+def pin_char3grams_by_hand(o: Oracle):
+    # the = (19, 7, 4) -> 19*676 + 7*26 + 4 = 13030; cat = 1371; and = 341; hat = 4751;
+    # abc = 28, bcd = 731, aaa = 0, zzz = 17575 (the largest id)
+    docs = [b"The cat, AND the hat.", b"", b"ab", b"c", b"abcd", b"a1bc", b"aaa zzz", b"x y z", b"ZzZ\xc3\xa9ab"]
+    go, g = o.char3grams(*_text_csr(docs))
+    assert go.tolist() == [0, 5, 5, 5, 5, 7, 7, 9, 9, 10]
+    assert g.tolist() == [13030, 1371, 341, 13030, 4751, 28, 731, 0, 17575, 17575]
+
+
+def pin_char3grams_brute_force(o: Oracle):
+    """Random byte documents (letters of both cases, separators, UTF-8 bytes) against the
+    regular-expression version in brute.py; the count of each document is the sum of
+    max(0, m - 2) over its letter runs of length m."""
+    rng = np.random.Generator(np.random.PCG64(14))
+    alphabet = np.frombuffer(b"abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ  .,\n09@[`{\xc3\xa9\xff", np.uint8)
+    docs = [rng.choice(alphabet, size=int(rng.integers(0, 200))).tobytes() for _ in range(60)]
+    go, g = o.char3grams(*_text_csr(docs))
+    for d, doc in enumerate(docs):
+        assert g[go[d]:go[d + 1]].tolist() == brute.char3grams(doc), d
+        runs = re.findall(rb"[A-Za-z]+", doc)
+        assert go[d + 1] - go[d] == sum(max(0, len(r) - 2) for r in runs)
+    assert go[-1] == g.shape[0] and int(g.max()) < 26 ** 3
 
 
 def pin_idf_closed_form(o: Oracle):

@@ -39,6 +39,11 @@ MUTANTS = {
     "simhash_no_minus_one": ("col[b] += ((h >> b) & 1ULL) ? 1 : -1;", "col[b] += ((h >> b) & 1ULL) ? 1 : 0;"),
     "splitmix_shift": ("z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;", "z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ULL;"),
     "term_hash_no_seed": ("orc_splitmix64((uint64_t)(uint32_t)t ^ seed)", "orc_splitmix64((uint64_t)(uint32_t)t)"),
+    "grams_no_case_fold": ("if (c >= 'A' && c <= 'Z') return c - 'A';", "if (c >= 'A' && c <= 'Z') return -1;"),
+    "grams_base_27": ("grams[out++] = 676 * x + 26 * y + z;", "grams[out++] = 729 * x + 27 * y + z;"),
+    "grams_reversed_letters": ("grams[out++] = 676 * x + 26 * y + z;", "grams[out++] = 676 * z + 26 * y + x;"),
+    "grams_cross_documents": ("p + 2 < text_offsets[d + 1]; ++p)", "p < text_offsets[d + 1]; ++p)"),
+    "grams_last_window_dropped": ("p + 2 < text_offsets[d + 1]; ++p)", "p + 3 < text_offsets[d + 1]; ++p)"),
     "md5_round2_index": ("k = (1 + 5 * i) % 16;", "k = (5 * i) % 16;"),
     "md5_round3_shift": ("{4, 11, 16, 23}", "{4, 11, 16, 22}"),
     "md5_I_no_not": ("f = c ^ (b | ~d);", "f = c ^ (b | d);"),

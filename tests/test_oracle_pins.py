@@ -4,6 +4,7 @@ Parity status of the oracle's functions (every function is pinned):
   orc_splitmix64 / orc_term_hash  published SplitMix64 outputs
   orc_md5 / orc_sha1               RFC 1321 test suite, FIPS 180 examples; hashlib, lengths 0-130
   orc_feature_hash                 hashlib on the 12-byte term/seed message, all three modes
+  orc_char3grams                   hand-numbered 3-grams; regular-expression brute force, run-length counts
   orc_idf                          hand-evaluated closed forms
   orc_term_counts, orc_df          hand example; brute force
   orc_select_refs                  hand-ranked example for all three modes; brute force

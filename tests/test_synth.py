@@ -51,3 +51,18 @@ def test_fingerprints_and_signatures_helpers():
     assert f.dtype == np.uint64 and f.shape == (100,)
     s = synth.random_signatures(10, 8, 4)
     assert s.dtype == np.float32 and (s >= 0).all() and (s == 0).any()
+
+
+def test_text_corpus_is_seeded_and_well_formed():
+    a = synth.make_text_corpus("tiny", n_docs=300)
+    b = synth.make_text_corpus("tiny", n_docs=300)
+    assert np.array_equal(a.offsets, b.offsets) and np.array_equal(a.text, b.text)
+    assert a.offsets[0] == 0 and np.all(np.diff(a.offsets) > 0) and a.offsets[-1] == a.n_bytes
+    # every document ends with a separator byte; letters of both cases and UTF-8 bytes occur
+    seps = set(b" \n,.'-7\t")
+    assert all(a.text[e - 1] in seps for e in a.offsets[1:].tolist())
+    assert (a.text >= ord("A")).any() and ((a.text >= ord("A")) & (a.text <= ord("Z"))).any()
+    assert (a.text == 0xC3).any()
+    # a near-duplicate's text is its source's word sequence with a few words replaced
+    i = int(np.nonzero(a.words.dup_src >= 0)[0][0])
+    assert a.words.edits[i] >= 1
