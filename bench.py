@@ -293,6 +293,56 @@ def form_features(args):
     ctx.close()
 
 
+def form_text(args):
+    """Character 3-gram front end: raw text -> 3-gram token CSR (mrc_text_grams) on eight
+    copies of the NEWS20-shaped text (about 440 MB, larger than L2), device buffers; the call's
+    wall time per pass (including its one synchronisation) and the per-kernel CUDA-event times
+    of the count and write passes against the measured HBM copy bandwidth."""
+    import torch
+    from paper_1810_03099_gb300 import mrc, synth
+    tc = synth.make_text_corpus("news20")
+    reps_text = 8
+    n1, b1 = tc.n_docs, tc.n_bytes
+    offs = np.concatenate([tc.offsets[:-1] + r * b1 for r in range(reps_text)] + [[reps_text * b1]]).astype(np.int64)
+    d_off = torch.from_numpy(offs).cuda()
+    d_text = torch.from_numpy(tc.text).cuda().repeat(reps_text)
+    n, B = n1 * reps_text, b1 * reps_text
+    ctx = mrc.Context()
+    go = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    g = torch.empty(B, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        _, gr = mrc.mrc_text_grams(ctx, d_off, d_text, go, g)
+    G = int(gr.shape[0])
+    steps = max(args.steps // 10, 10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        mrc.mrc_text_grams(ctx, d_off, d_text, go, g)
+    wall = (time.perf_counter() - t0) / steps
+    ctx.reset_stats()
+    ctx.set_timing(True)
+    for _ in range(steps):
+        mrc.mrc_text_grams(ctx, d_off, d_text, go, g)
+    ctx.set_timing(False)
+    ks = {s["name"]: s for s in ctx.kernel_stats()}
+    hbm = _peaks()["hbm_gbs"]
+    # algorithmic bytes: count pass reads the text; write pass reads the text and the document
+    # offsets, writes 4 bytes per 3-gram and the 3-gram offsets
+    alg = {"text_grams_count": B, "text_grams_write": B + 4 * G + 16 * (n + 1)}
+    kern = {}
+    for name, by in alg.items():
+        ms = ks[name]["ms"] / ks[name]["launches"]
+        kern[name] = {"ms": ms, "gbs": by / (ms * 1e-3) / 1e9, "frac_of_measured_hbm": by / (ms * 1e-3) / 1e9 / hbm}
+    line = {"metric": "docs/s", "form": "text", "value": n / wall, "unit": "docs/s",
+            "text_gbs": B / wall / 1e9, "grams": G,
+            "config": {"workload": f"character 3-grams: {n} docs, {B} bytes of text (8 copies of the NEWS20-shaped "
+                                   f"text), {G} 3-grams"},
+            "kernels": kern, "hbm_peak_gbs": hbm,
+            "tile_scan_ms": ks["tile_scan"]["ms"] / ks["tile_scan"]["launches"]}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def form_batching(args):
     """Batching form: 4,096 batches of 1-512 documents (log-uniform 20-20,000 tokens) against the
     one-million-document precision index, one graph launch per batch, autotuned tile width."""
@@ -387,7 +437,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mrc", choices=["mrc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="news20", choices=["news20", "precision", "batching", "serving", "features", "forms"],
+    ap.add_argument("--form", default="news20", choices=["news20", "precision", "batching", "serving", "features", "text", "forms"],
                     help="news20 (default): the headline step; the others measure the three forms")
     ap.add_argument("--batches", type=int, default=4096)
     ap.add_argument("--serving-docs", type=int, default=10_000_000)
@@ -397,7 +447,7 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         for f in (["precision", "batching", "serving"] if args.form == "forms" else [args.form]):
             {"precision": form_precision, "batching": form_batching, "serving": form_serving,
-             "features": form_features}[f](args)
+             "features": form_features, "text": form_text}[f](args)
         return
 
     rank = int(os.environ.get("RANK", "0"))

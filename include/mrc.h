@@ -130,6 +130,30 @@ void mrc_ctx_destroy(mrc_ctx* ctx);
 const char* mrc_last_error(const mrc_ctx* ctx);
 
 /*
+ * Character 3-grams of raw text (Section III: a document is the vector of its
+ * 3-gram counts; a 3-gram is a sequence of three letters of the alphabet).
+ * The alphabet is the 26 ASCII letters with case folded; every other byte
+ * (digits, punctuation, white space, bytes >= 0x80) separates. A 3-gram is
+ * any three consecutive letters of one document, numbered 676 x + 26 y + z
+ * (letters 0..25), so ids lie in [0, MRC_GRAM_VOCAB).
+ * Input: n_docs documents; text_offsets [n_docs + 1] int64 byte offsets
+ * (text_offsets[0] = 0, non-decreasing), text [text_offsets[n_docs]] bytes.
+ * Output, a token CSR for mrc_build_index / mrc_signature / cosine_allpairs
+ * with vocab = MRC_GRAM_VOCAB: gram_offsets [n_docs + 1] int64 and grams
+ * [capacity] int32, each document's 3-grams in text order. A document has at
+ * most max(0, bytes - 2) 3-grams, so capacity >= text_offsets[n_docs]
+ * always suffices. Every pointer may be device or host memory (host inputs
+ * are copied in, host outputs copied back before the call returns; the call
+ * synchronises the stream once). *n_grams (host) receives the total.
+ * Errors: MRC_ERR_INVALID for NULL pointers or invalid offsets;
+ * MRC_ERR_CAPACITY when the total exceeds capacity (gram_offsets complete,
+ * the first `capacity` ids written).
+ */
+#define MRC_GRAM_VOCAB 17576 /* 26^3 */
+mrc_status mrc_text_grams(mrc_ctx* ctx, int64_t n_docs, const int64_t* text_offsets, const uint8_t* text,
+                          int64_t* gram_offsets, int32_t* grams, int64_t capacity, int64_t* n_grams);
+
+/*
  * Build a device-resident signature index over `corpus` (Sections III-IV):
  * term counts per document, document frequencies, idf (frozen for later
  * queries), reference selection and partitioning (a host-side sort of the

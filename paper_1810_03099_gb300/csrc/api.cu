@@ -743,6 +743,62 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   return MRC_OK;
 }
 
+mrc_status mrc_text_grams(mrc_ctx* ctx, int64_t n_docs, const int64_t* text_offsets, const uint8_t* text,
+                          int64_t* gram_offsets, int32_t* grams, int64_t capacity, int64_t* n_grams) {
+  if (!ctx) return MRC_ERR_INVALID;
+  Scope scope(ctx);
+  if (n_docs < 0 || !text_offsets || !gram_offsets || !n_grams || capacity < 0 || (capacity > 0 && !grams))
+    return fail(ctx, MRC_ERR_INVALID, "mrc_text_grams: NULL pointer or negative size");
+  if (n_docs >= (1ll << 40)) return fail(ctx, MRC_ERR_UNSUPPORTED, "too many documents");
+  *n_grams = 0;
+  mrc_status st = MRC_OK;
+  int32_t* d_err = call_err(ctx, &st);
+  if (!d_err) return st;
+  int64_t B = 0;
+  if (is_device_ptr(text_offsets)) {
+    if (cudaMemcpy(&B, text_offsets + n_docs, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return cuda_fail(ctx, cudaGetLastError(), "reading text_offsets[n_docs]");
+  } else {
+    B = text_offsets[n_docs];
+  }
+  if (B < 0) return fail(ctx, MRC_ERR_INVALID, "text_offsets[n_docs] < 0");
+  if (B > 0 && !text) return fail(ctx, MRC_ERR_INVALID, "text is NULL");
+  const int64_t* d_off =
+      (const int64_t*)stage_in(ctx, "text.offsets", text_offsets, sizeof(int64_t) * (size_t)(n_docs + 1), &st);
+  if (st != MRC_OK) return st;
+  const uint8_t* d_text = B > 0 ? (const uint8_t*)stage_in(ctx, "text.bytes", text, (size_t)B, &st) : nullptr;
+  if (st != MRC_OK) return st;
+  const bool go_host = !is_device_ptr(gram_offsets), g_host = capacity > 0 && !is_device_ptr(grams);
+  int64_t* d_go =
+      go_host ? (int64_t*)ws_get(ctx, "text.gram_offsets", sizeof(int64_t) * (size_t)(n_docs + 1), &st) : gram_offsets;
+  int32_t* d_g = g_host ? (int32_t*)ws_get(ctx, "text.grams", sizeof(int32_t) * (size_t)capacity, &st) : grams;
+  const int64_t tiles = text_gram_tiles(B);
+  int64_t* tile_doc = (int64_t*)ws_get(ctx, "text.tile_doc", sizeof(int64_t) * (size_t)std::max<int64_t>(tiles, 1), &st);
+  int32_t* tile_cnt = (int32_t*)ws_get(ctx, "text.tile_cnt", sizeof(int32_t) * (size_t)std::max<int64_t>(tiles, 1), &st);
+  int64_t* tile_base = (int64_t*)ws_get(ctx, "text.tile_base", sizeof(int64_t) * (size_t)(tiles + 1), &st);
+  int64_t* group_sum =
+      (int64_t*)ws_get(ctx, "text.group_sum", sizeof(int64_t) * (size_t)std::max<int64_t>((tiles + 1023) / 1024, 1), &st);
+  if (st != MRC_OK) return st;
+  cudaError_t e = launch_text_grams(ctx, n_docs, d_off, d_text, B, d_go, d_g, capacity, tile_doc, tile_cnt, group_sum,
+                                    tile_base, d_err);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "text 3-grams");
+  int64_t* h_total = (int64_t*)((char*)ctx->pinned + 512);
+  e = cudaMemcpyAsync(h_total, tile_base + tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the 3-gram total");
+  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;  // synchronises the stream
+  const int64_t total = *h_total;
+  *n_grams = total;
+  if (go_host)
+    e = cudaMemcpyAsync(gram_offsets, d_go, sizeof(int64_t) * (size_t)(n_docs + 1), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess && g_host && total > 0)
+    e = cudaMemcpyAsync(grams, d_g, sizeof(int32_t) * (size_t)std::min(total, capacity), cudaMemcpyDeviceToHost,
+                        ctx->stream);
+  if (e == cudaSuccess && (go_host || g_host)) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "copying the 3-grams out");
+  if (total > capacity) return fail(ctx, MRC_ERR_CAPACITY, "more 3-grams than capacity");
+  return MRC_OK;
+}
+
 mrc_status mrc_signature(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float* sig, uint64_t* simhash) {
   if (!ctx || !index) return MRC_ERR_INVALID;
   Scope scope(ctx);

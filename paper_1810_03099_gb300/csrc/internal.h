@@ -185,6 +185,15 @@ struct SigOut {
 cudaError_t launch_signature(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo, const float* rinv,
                              int32_t k, int32_t bf16_weights, uint64_t seed, const uint64_t* fhash,
                              const SigOut& out);
+// Character 3-grams of a text CSR (text.cu): gram_offsets [n_docs + 1], grams [capacity] (ids past
+// capacity dropped); tile_doc, tile_cnt [text_gram_tiles(n_bytes)], group_sum [ceil(tiles / 1024)],
+// tile_base [tiles + 1] scratch, the total
+// lands in tile_base[tiles]; invalid offsets set kErrBadOffsets in err.
+int64_t text_gram_tiles(int64_t n_bytes);
+cudaError_t launch_text_grams(mrc_ctx* ctx, int64_t n_docs, const int64_t* text_offsets, const uint8_t* text,
+                              int64_t n_bytes, int64_t* gram_offsets, int32_t* grams, int64_t capacity,
+                              int64_t* tile_doc, int32_t* tile_cnt, int64_t* group_sum, int64_t* tile_base,
+                              int32_t* err);
 // out[t] = the MD5 (mode MRC_HASH_MD5) or SHA-1 (MRC_HASH_SHA1) Simhash feature of term t < vocab.
 cudaError_t launch_feature_table(mrc_ctx* ctx, int32_t vocab, uint64_t seed, int32_t mode, uint64_t* out);
 // Packs rows of `sig` (normalised to unit length first when `normalize`) into compare operands.

@@ -21,6 +21,7 @@ MRC_ERR_CUDA, MRC_ERR_TIMEOUT, MRC_ERR_UNSUPPORTED = 4, 5, 6
 SELECT_ALL, SELECT_REGION, SELECT_DF1 = 0, 1, 2
 WEIGHT_COUNT, WEIGHT_TFIDF = 0, 1
 HASH_SPLITMIX64, HASH_MD5, HASH_SHA1 = 0, 1, 2
+GRAM_VOCAB = 17576  # MRC_GRAM_VOCAB: character 3-grams over the 26-letter alphabet
 PREC_FP32, PREC_BF16_FP8, PREC_FP16 = 0, 1, 2
 MAX_K = 256
 
@@ -59,6 +60,8 @@ _SIGNATURES = {
     "mrc_ctx_create": (C.c_int32, [C.c_void_p, C.POINTER(C.c_void_p)]),
     "mrc_ctx_destroy": (None, [C.c_void_p]),
     "mrc_last_error": (C.c_char_p, [C.c_void_p]),
+    "mrc_text_grams": (C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                   C.POINTER(C.c_int64)]),
     "mrc_build_index": (C.c_int32, [C.c_void_p, C.POINTER(Docs), C.c_int32, C.POINTER(Params), C.POINTER(C.c_void_p)]),
     "mrc_signature": (C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(Docs), C.c_void_p, C.c_void_p]),
     "mrc_signature_noalloc": (C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(Docs), C.c_void_p, C.c_void_p]),
@@ -306,6 +309,30 @@ def params_default(**kw) -> Params:
     for k, v in kw.items():
         setattr(p, k, v)
     return p
+
+
+def mrc_text_grams(ctx: Context, text_offsets, text, gram_offsets=None, grams=None):
+    """Character 3-grams of raw text: (gram_offsets int64 [n+1], grams int32 [total]) on the
+    inputs' side (torch CUDA tensors, or numpy arrays). text: uint8 bytes (numpy/torch) or a
+    bytes object; caller buffers, when given, must hold n+1 offsets and n_bytes ids."""
+    if isinstance(text, (bytes, bytearray)):
+        text = np.frombuffer(text, np.uint8)
+    _check_dtype(text_offsets, np.int64, "int64")
+    _check_dtype(text, np.uint8, "uint8")
+    n = int(text_offsets.shape[0]) - 1
+    n_bytes = int(text.shape[0])
+    if gram_offsets is None:
+        if _on_device(text_offsets):
+            import torch
+            gram_offsets = torch.empty(n + 1, dtype=torch.int64, device=text_offsets.device)
+            grams = torch.empty(max(n_bytes, 1), dtype=torch.int32, device=text_offsets.device)
+        else:
+            gram_offsets = np.empty(n + 1, np.int64)
+            grams = np.empty(max(n_bytes, 1), np.int32)
+    total = C.c_int64()
+    ctx.check(ctx.lib.mrc_text_grams(ctx.handle, n, _ptr(text_offsets), _ptr(text), _ptr(gram_offsets), _ptr(grams),
+                                     int(grams.shape[0]), C.byref(total)))
+    return gram_offsets, grams[:total.value]
 
 
 def mrc_build_index(ctx: Context, offsets, tokens, vocab: int, params: Params | None = None) -> Index:
