@@ -41,28 +41,27 @@ struct GramArgs {
   int vec16;  // text is 16-byte aligned: 16-byte loads
 };
 
-// letter number 0..25 of a byte, or >= 26 for any other byte
-__device__ __forceinline__ uint32_t letter_of(uint32_t c) { return (c | 0x20u) - (uint32_t)'a'; }
-
 constexpr int64_t kNoDoc = 0x7FFFFFFFFFFFFFFFll;  // offset of a document past the last
 
-// Bit k (k = 0..3): byte k of w is an ASCII letter of either case. Four bytes at a time: bytes
-// >= 0x80 are excluded by their top bit; for the others (low 7 bits z, case folded) the adds
-// z + 0x1F and z + 0x05 reach the top bit exactly when z >= 'a' and z > 'z', and never carry
-// into the next byte.
-__device__ __forceinline__ uint32_t letter_bits4(uint32_t w) {
+// Byte k of letter_bytes4(w) is 1 iff byte k of w is an ASCII letter of either case (bit k of
+// letter_bits4, packed). Four bytes at a time: bytes >= 0x80 are excluded by their top bit; for
+// the others (low 7 bits z, case folded) the adds z + 0x1F and z + 0x05 reach the top bit
+// exactly when z >= 'a' and z > 'z', and never carry into the next byte.
+__device__ __forceinline__ uint32_t letter_bytes4(uint32_t w) {  // 0x01 in each letter byte
   const uint32_t y = w | 0x20202020u;
   const uint32_t z = y & 0x7F7F7F7Fu;
   const uint32_t ge = (z + 0x1F1F1F1Fu) & 0x80808080u;
   const uint32_t gt = (z + 0x05050505u) & 0x80808080u;
-  const uint32_t m = (ge & ~gt & ~(y & 0x80808080u)) >> 7;  // bits 0, 8, 16, 24
+  return (ge & ~gt & ~(y & 0x80808080u)) >> 7;
+}
+__device__ __forceinline__ uint32_t letter_bits4(uint32_t m) {  // m = letter_bytes4(w)
   return (m | (m >> 7) | (m >> 14) | (m >> 21)) & 0xFu;
 }
 
-// Byte k of the result: the letter number 0..25 of byte k of w when that byte is a letter
+// Byte k of the result: the letter number 0..25 of byte k of w if that byte is a letter, else 0
 // ((b | 0xA0) - 0x61 has its top bit set and never borrows; the low 7 bits are the number).
-__device__ __forceinline__ uint32_t letter_nums4(uint32_t w) {
-  return ((w | 0xA0A0A0A0u) - 0x61616161u) & 0x7F7F7F7Fu;
+__device__ __forceinline__ uint32_t letter_nums4(uint32_t w, uint32_t m) {
+  return ((w | 0xA0A0A0A0u) - 0x61616161u) & (m * 0x7Fu);
 }
 
 // The 36 text bytes [p, p + 36) as nine little-endian words (zeros past the end of the text).
@@ -110,6 +109,7 @@ __global__ void __launch_bounds__(kGramThreads) k_text_grams(GramArgs a) {
   for (int x = tid; x <= kGramWords; x += kGramThreads) starts[x] = 0u;
   const int64_t first_doc = __ldg(a.tile_doc + t);
   const int64_t first_start = doc_start(a, first_doc + tid);
+  const int64_t base = WRITE ? __ldg(a.tile_base + t) : 0;
   __syncthreads();
   const int64_t bound = lo + kGramTile + 2;
   for (int64_t d = first_doc + tid, s = first_start; s < bound;) {
@@ -122,9 +122,13 @@ __global__ void __launch_bounds__(kGramThreads) k_text_grams(GramArgs a) {
 
   // 2. position j starts a 3-gram iff bytes j, j+1, j+2 are letters and no document starts at
   //    j+1 or j+2
+  uint32_t mb[9];
   uint64_t lm = 0ull;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) lm |= (uint64_t)letter_bits4(w[k]) << (4 * k);
+  for (int k = 0; k < 9; ++k) {
+    mb[k] = letter_bytes4(w[k]);
+    lm |= (uint64_t)letter_bits4(mb[k]) << (4 * k);
+  }
   const uint64_t sm = (uint64_t)starts[tid] | ((uint64_t)starts[tid + 1] << 32);
   const uint32_t valid = (uint32_t)(lm & (lm >> 1) & (lm >> 2) & ~(sm >> 1) & ~(sm >> 2));
 
@@ -159,19 +163,25 @@ __global__ void __launch_bounds__(kGramThreads) k_text_grams(GramArgs a) {
   // 4. ids into shared memory in text order, then one coalesced copy to the output
   uint32_t L[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) L[k] = letter_nums4(w[k]);
+  for (int k = 0; k < 9; ++k) L[k] = letter_nums4(w[k], mb[k]);  // 0 for other bytes: lanes stay < 2^15
+  // ids two at a time in 16-bit lanes (ids < 2^15, so the lanes never carry into each other):
+  // for positions 4g + r, r = 0..3, with letter numbers n_0..n_5 of bytes 4g..4g+5,
+  // even = 676 (n0, n2) + 26 (n1, n3) + (n2, n4) and odd = 676 (n1, n3) + 26 (n2, n4) + (n3, n5)
   int at = pre;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    if ((valid >> j) & 1u) {
-      const uint32_t x = (L[j >> 2] >> (8 * (j & 3))) & 0xFFu;
-      const uint32_t y = (L[(j + 1) >> 2] >> (8 * ((j + 1) & 3))) & 0xFFu;
-      const uint32_t z = (L[(j + 2) >> 2] >> (8 * ((j + 2) & 3))) & 0xFFu;
-      stage[at++] = (int32_t)(676u * x + 26u * y + z);
-    }
+  for (int g = 0; g < 8; ++g) {
+    const uint32_t a0 = __byte_perm(L[g], 0u, 0x4240);                   // (n0, n2)
+    const uint32_t a1 = __byte_perm(L[g], 0u, 0x4341);                   // (n1, n3)
+    const uint32_t a2 = __byte_perm(L[g], L[g + 1], 0x4442) & 0x00FF00FFu;  // (n2, n4)
+    const uint32_t a3 = __byte_perm(L[g], L[g + 1], 0x4543) & 0x00FF00FFu;  // (n3, n5)
+    const uint32_t ev = 676u * a0 + 26u * a1 + a2;
+    const uint32_t od = 676u * a1 + 26u * a2 + a3;
+    const uint32_t ids[4] = {ev & 0xFFFFu, od & 0xFFFFu, ev >> 16, od >> 16};
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if ((valid >> (4 * g + r)) & 1u) stage[at++] = (int32_t)ids[r];
   }
   __syncthreads();
-  const int64_t base = __ldg(a.tile_base + t);
   const int64_t lim = a.capacity - base;  // ids past the caller's capacity are dropped
   for (int x = tid; x < total && x < lim; x += kGramThreads) a.grams[base + x] = stage[x];
 
