@@ -343,6 +343,88 @@ def form_text(args):
     ctx.close()
 
 
+def _pair_values(M, buf, n):
+    """(i, j, score) pairs -> score per pair i < j, as a dense vector indexed by the pair's rank."""
+    p = M.pairs_to_numpy(buf)
+    i, j = p["i"].astype(np.int64), p["j"].astype(np.int64)
+    rank = i * n - i * (i + 1) // 2 + (j - i - 1)  # row-major rank of (i, j) among i < j
+    out = np.zeros(n * (n - 1) // 2, np.float64)
+    out[rank] = p["score"].astype(np.float64)
+    return out
+
+
+def _error_stats(approx, exact):
+    e = approx - exact
+    return {"mae": float(np.abs(e).mean()), "mean": float(e.mean()), "var": float(e.var())}
+
+
+def form_study(args):
+    """Reference-selection study (Section IV, Eq. 2 and Eq. 3): MAE and variance of the
+    signature cosine against the exact TF-IDF cosine over all pairs of 3,000 documents of the
+    NEWS20-shaped text (3-grams from mrc_text_grams), for the reference families of the paper:
+    every 3-gram (ALL) split into k partitions, four frequency regions of 2,000 3-grams, and the
+    3-grams that occur in one document only (DF1) with L = 1,000 / 1,500 / 2,000; k from 15 to
+    240. The FP64 oracle repeats one configuration on a 400-document subset."""
+    import torch
+    from paper_1810_03099_gb300 import mrc, synth
+    n = 3000
+    tc = synth.make_text_corpus("news20", n_docs=n)
+    ctx = mrc.Context()
+    go, g = mrc.mrc_text_grams(ctx, torch.from_numpy(tc.offsets).cuda(), torch.from_numpy(tc.text).cuda())
+    V = mrc.GRAM_VOCAB
+    npairs = n * (n - 1) // 2
+    idx = mrc.mrc_build_index(ctx, go, g, V, mrc.params_default(k=8, select_mode=mrc.SELECT_ALL))
+    exact = _pair_values(mrc, mrc.cosine_allpairs(ctx, idx, go, g, 0.0, capacity=npairs + 1)[0], n)
+    idx.free()
+    configs = [("ALL", mrc.SELECT_ALL, -1, 0, k) for k in (15, 30, 60, 120, 240)]
+    configs += [(f"REGION {r}-{r + 2000}", mrc.SELECT_REGION, 2000, r, k) for r in (0, 2000, 4000, 6000)
+                for k in (30, 60, 120, 240)]
+    configs += [(f"DF1 L={L}", mrc.SELECT_DF1, L, 0, k) for L in (1000, 1500, 2000) for k in (30, 60, 120)]
+    rows = []
+    for name, mode, L, start, k in configs:
+        p = mrc.params_default(k=k, select_mode=mode, L=L, region_start=start)
+        idx = mrc.mrc_build_index(ctx, go, g, V, p)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        buf, total = mrc.mrc_match(ctx, idx, None, -1.0, capacity=npairs + 1)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        approx = _pair_values(mrc, buf, n)
+        st = _error_stats(approx, exact)
+        rows.append({"reference": name, "k": k, "L_used": int(idx.L_used), "mae": st["mae"], "var": st["var"],
+                     "all_pairs_match_ms": ms, "pairs": int(total)})
+        idx.free()
+    # FP64 oracle on a 400-document subset, one configuration (every 3-gram, k = 60)
+    from oracle.oracle import MODE_ALL, Oracle, Params, build_index
+    orc = Oracle()
+    m = 400
+    so, st_ = tc.offsets[:m + 1].copy(), tc.text[:int(tc.offsets[m])].copy()
+    ogo, og = orc.char3grams(so, st_)
+    ref = build_index(ogo, og, V, Params(k=60, mode=MODE_ALL), orc)
+    _, pi, pj, ps = orc.sig_pairs(ref.S, -1.0)
+    _, ci, cj, cs = orc.cosine_pairs(ref.row_ptr, ref.terms, ref.w, 0.0)
+    o_sig, o_ex = np.zeros(m * (m - 1) // 2), np.zeros(m * (m - 1) // 2)
+    o_sig[pi * m - pi * (pi + 1) // 2 + (pj - pi - 1)] = ps
+    o_ex[ci.astype(np.int64) * m - ci * (ci + 1) // 2 + (cj - ci - 1)] = cs
+    ost = orc.error_stats(o_sig, o_ex)
+    sgo, sg = mrc.mrc_text_grams(ctx, torch.from_numpy(so).cuda(), torch.from_numpy(st_).cuda())
+    idx = mrc.mrc_build_index(ctx, sgo, sg, V, mrc.params_default(k=60, select_mode=mrc.SELECT_ALL))
+    gsig = _pair_values(mrc, mrc.mrc_match(ctx, idx, None, -1.0, capacity=m * m)[0], m)
+    gex = _pair_values(mrc, mrc.cosine_allpairs(ctx, idx, sgo, sg, 0.0, capacity=m * m)[0], m)
+    gst = _error_stats(gsig, gex)
+    idx.free()
+    best = min(rows, key=lambda r: r["mae"])
+    line = {"metric": "MAE", "form": "study", "value": best["mae"], "unit": "mean |signature cosine - cosine|",
+            "higher_is_better": False,
+            "config": {"workload": f"reference-selection study: all {npairs} pairs of {n} NEWS20-shaped text "
+                                   f"documents, 3-grams, {len(configs)} reference configurations"},
+            "best": best, "rows": rows,
+            "oracle_check": {"docs": m, "config": "ALL, k=60", "oracle_mae": ost["mae"], "oracle_var": ost["var"],
+                             "gpu_mae": gst["mae"], "gpu_var": gst["var"]}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def form_batching(args):
     """Batching form: 4,096 batches of 1-512 documents (log-uniform 20-20,000 tokens) against the
     one-million-document precision index, one graph launch per batch, autotuned tile width."""
@@ -437,7 +519,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mrc", choices=["mrc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="news20", choices=["news20", "precision", "batching", "serving", "features", "text", "forms"],
+    ap.add_argument("--form", default="news20", choices=["news20", "precision", "batching", "serving", "features", "text", "study", "forms"],
                     help="news20 (default): the headline step; the others measure the three forms")
     ap.add_argument("--batches", type=int, default=4096)
     ap.add_argument("--serving-docs", type=int, default=10_000_000)
@@ -447,7 +529,7 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         for f in (["precision", "batching", "serving"] if args.form == "forms" else [args.form]):
             {"precision": form_precision, "batching": form_batching, "serving": form_serving,
-             "features": form_features, "text": form_text}[f](args)
+             "features": form_features, "text": form_text, "study": form_study}[f](args)
         return
 
     rank = int(os.environ.get("RANK", "0"))

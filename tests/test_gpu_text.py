@@ -6,7 +6,7 @@ from __future__ import annotations
 import numpy as np
 import pytest
 
-from oracle.oracle import GRAM_VOCAB, MODE_ALL, Params, build_index
+from oracle.oracle import GRAM_VOCAB, MODE_ALL, MODE_DF1, Params, build_index
 from paper_1810_03099_gb300 import synth
 from tests.gpu_common import compare_pairs, cuda_or_skip, pair_dict
 
@@ -158,3 +158,30 @@ def test_text_grams_news20_sized_text(torch, M, ctx, orc):
     benchmark times, every id compared."""
     tc = synth.make_text_corpus("news20")
     check_grams(M, ctx, orc, torch, tc.offsets, tc.text)
+
+
+def test_study_error_statistics_match_oracle(torch, M, ctx, orc):
+    """The reference-selection study's statistic (Eq. 2, Eq. 3: MAE and variance of the signature
+    cosine against the exact cosine over all pairs), from the GPU's all-pair lists (tau = -1 for
+    signatures, 0 for the exact cosine), equals the oracle's on 300 text documents."""
+    m = 300
+    tc = synth.make_text_corpus("tiny", n_docs=m)
+    go_ref, g_ref = orc.char3grams(tc.offsets, tc.text)
+    for mode, k, L in ((MODE_ALL, 60, -1), (MODE_DF1, 30, 500)):
+        ref = build_index(go_ref, g_ref, GRAM_VOCAB, Params(k=k, mode=mode, L=L), orc)
+        _, pi, pj, ps = orc.sig_pairs(ref.S, -1.0)
+        _, ci, cj, cs = orc.cosine_pairs(ref.row_ptr, ref.terms, ref.w, 0.0)
+        assert pi.shape[0] == ci.shape[0] == m * (m - 1) // 2
+        ost = orc.error_stats(ps, cs)  # both lists in row-major (i, j) order
+        go, g = M.mrc_text_grams(ctx, dev(torch, tc.offsets), dev(torch, tc.text))
+        idx = M.mrc_build_index(ctx, go, g, GRAM_VOCAB, M.params_default(k=k, select_mode=mode, L=L))
+        sig = M.pairs_to_numpy(M.mrc_match(ctx, idx, None, -1.0, capacity=m * m)[0])
+        ex = M.pairs_to_numpy(M.cosine_allpairs(ctx, idx, go, g, 0.0, capacity=m * m)[0])
+        order_s = np.lexsort((sig["j"], sig["i"]))
+        order_e = np.lexsort((ex["j"], ex["i"]))
+        assert np.array_equal(sig["i"][order_s], pi) and np.array_equal(sig["j"][order_s], pj)
+        assert np.array_equal(ex["i"][order_e], ci) and np.array_equal(ex["j"][order_e], cj)
+        e = sig["score"][order_s].astype(np.float64) - ex["score"][order_e].astype(np.float64)
+        assert abs(np.abs(e).mean() - ost["mae"]) < 1e-5
+        assert abs(e.var() - ost["var"]) < 1e-5
+        idx.free()
