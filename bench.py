@@ -425,6 +425,66 @@ def form_study(args):
     ctx.close()
 
 
+def form_simhash_index(args):
+    """Block-table Hamming index (F4) against the all-pairs POPC sweep: a 10,000,000-fingerprint
+    index (10 % near copies with up to 4 flipped bits) searched by 100,000 queries (half of them
+    near copies of index entries), Hamming distance <= 3. Same pair count from both paths; wall
+    time per search call (including its one synchronisation) and the build time."""
+    import torch
+    from paper_1810_03099_gb300 import mrc, synth
+    n, nq, h = 10_000_000, 100_000, 3
+    X = synth.random_fingerprints(n, 41, n_near=n // 10, max_flip=4) if n <= 2_000_000 else None
+    if X is None:  # drawn on the device: random words, then near copies of earlier ones
+        g = torch.Generator(device="cuda").manual_seed(41)
+        X = torch.randint(-2**63, 2**63 - 1, (n,), dtype=torch.int64, device="cuda", generator=g)
+        src = torch.randint(0, n - n // 10, (n // 10,), device="cuda", generator=g)
+        flips = torch.zeros(n // 10, dtype=torch.int64, device="cuda")
+        for _ in range(4):
+            bit = torch.randint(0, 64, (n // 10,), device="cuda", generator=g)
+            keep = torch.rand(n // 10, device="cuda", generator=g) < 0.5
+            flips ^= torch.where(keep, torch.bitwise_left_shift(torch.ones_like(bit), bit), torch.zeros_like(bit))
+        X[n - n // 10:] = X[src] ^ flips
+    else:
+        X = torch.from_numpy(X.view(np.int64)).cuda()
+    g2 = torch.Generator(device="cuda").manual_seed(42)
+    pick = torch.randint(0, n, (nq // 2,), device="cuda", generator=g2)
+    Q = torch.cat([X[pick] ^ (1 << 7), torch.randint(-2**63, 2**63 - 1, (nq - nq // 2,), dtype=torch.int64,
+                                                    device="cuda", generator=g2)])
+    ctx = mrc.Context()
+    t0 = time.perf_counter()
+    sidx = mrc.simhash_index_build(ctx, X, h)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    sidx.free()
+    t0 = time.perf_counter()
+    sidx = mrc.simhash_index_build(ctx, X, h)
+    torch.cuda.synchronize()
+    build_s = min(build_s, time.perf_counter() - t0)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            out = fn()
+        torch.cuda.synchronize()
+        return out, (time.perf_counter() - t) / reps
+
+    (bi, tot_i), t_idx = timed(lambda: mrc.simhash_index_match(ctx, sidx, Q, h, capacity=1 << 22), 10)
+    (bb, tot_b), t_brute = timed(lambda: mrc.simhash_match(ctx, Q, X, h, capacity=1 << 22), 2)
+    pi, pb = mrc.pairs_to_numpy(bi), mrc.pairs_to_numpy(bb)
+    same = sorted(zip(pi["i"].tolist(), pi["j"].tolist())) == sorted(zip(pb["i"].tolist(), pb["j"].tolist()))
+    line = {"metric": "queries/s", "form": "simhash_index", "value": nq / t_idx, "unit": "queries/s",
+            "config": {"workload": f"Hamming <= {h}: {nq} queries x {n} fingerprints (block-table index, 4 tables "
+                                   f"of 16-bit blocks)"},
+            "index_search_ms": t_idx * 1e3, "brute_force_search_ms": t_brute * 1e3, "speedup": t_brute / t_idx,
+            "pairs": int(tot_i), "pairs_brute_force": int(tot_b), "same_pairs": bool(same), "build_ms": build_s * 1e3,
+            "index_bytes": int(n * 4 * 12 + n * 8)}
+    print(json.dumps(line), flush=True)
+    sidx.free()
+    ctx.close()
+
+
 def form_batching(args):
     """Batching form: 4,096 batches of 1-512 documents (log-uniform 20-20,000 tokens) against the
     one-million-document precision index, one graph launch per batch, autotuned tile width."""
@@ -519,7 +579,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mrc", choices=["mrc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="news20", choices=["news20", "precision", "batching", "serving", "features", "text", "study", "forms"],
+    ap.add_argument("--form", default="news20", choices=["news20", "precision", "batching", "serving", "features", "text", "study", "simhash_index",
+                             "forms"],
                     help="news20 (default): the headline step; the others measure the three forms")
     ap.add_argument("--batches", type=int, default=4096)
     ap.add_argument("--serving-docs", type=int, default=10_000_000)
@@ -529,7 +590,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         for f in (["precision", "batching", "serving"] if args.form == "forms" else [args.form]):
             {"precision": form_precision, "batching": form_batching, "serving": form_serving,
-             "features": form_features, "text": form_text, "study": form_study}[f](args)
+             "features": form_features, "text": form_text, "study": form_study,
+             "simhash_index": form_simhash_index}[f](args)
         return
 
     rank = int(os.environ.get("RANK", "0"))

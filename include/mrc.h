@@ -294,6 +294,30 @@ mrc_status mrc_batch_wait(mrc_batch* batch, mrc_pair* pairs, int64_t capacity, i
 const char* mrc_batch_last_error(const mrc_batch* batch);
 void mrc_batch_free(mrc_batch* batch);
 
+/*
+ * Block-table Hamming index over 64-bit Simhash fingerprints (Section I cites
+ * Simhash for web-scale near-duplicate detection; Section III defines the
+ * Hamming distance). The 64 bits are cut into b = max(hamming_max + 1, 4)
+ * blocks; two fingerprints within distance hamming_max agree on at least one
+ * block, so a search reads, in each of the b tables, only the bucket of the
+ * query's block value. Results equal simhash_match's: same pairs, each once,
+ * score = Hamming distance (pair order may differ).
+ * Build: fps [n] uint64 (device or host; copied into the index), n < 2^31,
+ * 0 <= hamming_max <= 15 (the largest distance later searches may ask for).
+ * The index holds 12 * b * n bytes plus the bucket offsets; free it with
+ * mrc_simhash_index_free (ordered on the building context's stream).
+ * Match: queries [nq] (device or host) x the index, pairs (q, x); queries ==
+ * NULL: all pairs i < j of the index itself. hamming_max <= the build's.
+ * Pairs, capacity and *n_pairs as simhash_match. Errors: MRC_ERR_INVALID for
+ * bad sizes or a distance above the build's, MRC_ERR_CAPACITY on overflow.
+ */
+typedef struct mrc_simhash_index mrc_simhash_index;
+mrc_status mrc_simhash_index_build(mrc_ctx* ctx, const uint64_t* fps, int64_t n, int32_t hamming_max,
+                                   mrc_simhash_index** out);
+mrc_status mrc_simhash_index_match(mrc_ctx* ctx, const mrc_simhash_index* index, const uint64_t* queries, int64_t nq,
+                                   int32_t hamming_max, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs);
+void mrc_simhash_index_free(mrc_simhash_index* index);
+
 /* Index introspection and export (for checks and persistence). Each output
  * pointer may be NULL to skip it; sizes follow mrc_index_info. Host outputs
  * are complete on return; device outputs are written in order on the

@@ -1220,6 +1220,93 @@ mrc_status simhash_match_async(mrc_ctx* ctx, const uint64_t* a, int64_t na, cons
   return simhash_impl(ctx, a, na, b, nb, hamming_max, pairs, capacity, nullptr, (unsigned long long*)d_n_pairs);
 }
 
+mrc_status mrc_simhash_index_build(mrc_ctx* ctx, const uint64_t* fps, int64_t n, int32_t hamming_max,
+                                   mrc_simhash_index** out) {
+  if (!ctx || !out) return MRC_ERR_INVALID;
+  *out = nullptr;
+  Scope scope(ctx);
+  if (n < 0 || (n > 0 && !fps)) return fail(ctx, MRC_ERR_INVALID, "mrc_simhash_index_build: bad size or NULL input");
+  if (n >= (1ll << 31) - 1) return fail(ctx, MRC_ERR_UNSUPPORTED, "more than 2^31 - 2 fingerprints");
+  if (hamming_max < 0 || hamming_max > 15) return fail(ctx, MRC_ERR_INVALID, "hamming_max must be in [0, 15]");
+  mrc_status st = MRC_OK;
+  const SimhashLayout L = simhash_layout(hamming_max);
+  const uint64_t* d_fps = (const uint64_t*)stage_in(ctx, "shx.in", fps, sizeof(uint64_t) * (size_t)n, &st);
+  int32_t* cnt = (int32_t*)ws_get(ctx, "shx.cnt", sizeof(int32_t) * (size_t)L.off_words, &st);
+  int32_t* cursor = (int32_t*)ws_get(ctx, "shx.cursor", sizeof(int32_t) * (size_t)L.off_words, &st);
+  if (st != MRC_OK) return st;
+  mrc_simhash_index* x = new mrc_simhash_index();
+  x->device = ctx->device;
+  x->stream = ctx->stream;
+  x->n = n;
+  x->hamming_max = hamming_max;
+  x->layout = L;
+  const size_t nn = (size_t)std::max<int64_t>(n, 1) * (size_t)L.blocks;
+  const size_t b_fp = (8 * nn + 255) / 256 * 256, b_id = (4 * nn + 255) / 256 * 256;
+  const size_t b_own = (8 * (size_t)std::max<int64_t>(n, 1) + 255) / 256 * 256;
+  char* b = nullptr;
+  if (cudaMallocAsync((void**)&b, b_fp + b_id + b_own + sizeof(int32_t) * (size_t)L.off_words, ctx->stream) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    delete x;
+    return fail(ctx, MRC_ERR_OOM, "device allocation failed: fingerprint index");
+  }
+  x->block = b;
+  x->fp = (uint64_t*)b;
+  x->id = (int32_t*)(b + b_fp);
+  x->own = (uint64_t*)(b + b_fp + b_id);
+  x->off = (int32_t*)(b + b_fp + b_id + b_own);
+  cudaError_t e = n > 0 ? cudaMemcpyAsync(x->own, d_fps, sizeof(uint64_t) * (size_t)n, cudaMemcpyDeviceToDevice,
+                                          ctx->stream)
+                        : cudaSuccess;
+  if (e == cudaSuccess) e = launch_simhash_index_build(ctx, d_fps, n, L, cnt, cursor, x->off, x->fp, x->id);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // the staging slots may be reused after this
+  if (e != cudaSuccess) {
+    cudaFreeAsync(x->block, ctx->stream);
+    delete x;
+    return cuda_fail(ctx, e, "fingerprint index build");
+  }
+  *out = x;
+  return MRC_OK;
+}
+
+mrc_status mrc_simhash_index_match(mrc_ctx* ctx, const mrc_simhash_index* index, const uint64_t* queries, int64_t nq,
+                                   int32_t hamming_max, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs) {
+  if (!ctx) return MRC_ERR_INVALID;
+  Scope scope(ctx);
+  if (!index || (queries && nq < 0) || capacity < 0 || (!queries && nq != 0))
+    return fail(ctx, MRC_ERR_INVALID, "mrc_simhash_index_match: bad sizes or NULL index");
+  if (nq >= (1ll << 31)) return fail(ctx, MRC_ERR_UNSUPPORTED, "more than 2^31 queries");
+  if (hamming_max < 0 || hamming_max > index->hamming_max)
+    return fail(ctx, MRC_ERR_INVALID, "hamming_max above the distance the index was built for");
+  if (n_pairs) *n_pairs = 0;
+  mrc_status st = MRC_OK;
+  unsigned long long* d_count = (unsigned long long*)ws_get(ctx, "shx.count", sizeof(unsigned long long), &st);
+  mrc_pair* dst = pair_dest(ctx, pairs, capacity, &st);
+  if (st != MRC_OK) return st;
+  cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), ctx->stream);
+  const bool all = queries == nullptr;  // all pairs: the index's own fingerprints are the queries
+  const uint64_t* dq = index->own;
+  const int64_t m = all ? index->n : nq;
+  if (!all) {
+    dq = (const uint64_t*)stage_in(ctx, "shx.q", queries, sizeof(uint64_t) * (size_t)nq, &st);
+    if (st != MRC_OK) return st;
+  }
+  cudaError_t e = launch_simhash_index_probe(ctx, dq, m, all, hamming_max, index->layout, index->n, index->fp,
+                                             index->id, index->off, dst, d_count, capacity);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fingerprint index probe");
+  return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
+}
+
+void mrc_simhash_index_free(mrc_simhash_index* x) {
+  if (!x) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != x->device) cudaSetDevice(x->device);
+  if (x->block) cudaFreeAsync(x->block, x->stream);
+  if (cur >= 0 && cur != x->device) cudaSetDevice(cur);
+  delete x;
+}
+
 mrc_status mrc_ctx_sync(mrc_ctx* ctx) {
   if (!ctx) return MRC_ERR_INVALID;
   Scope scope(ctx);

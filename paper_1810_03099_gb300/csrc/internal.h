@@ -46,7 +46,30 @@ struct Buffer {
   size_t bytes = 0;
 };
 
+// Blocks of the fingerprint index: block t covers bits [shift[t], shift[t] + width[t]); its
+// bucket offsets start at off_base[t] in the offsets array (2^width[t] + 1 entries each).
+struct SimhashLayout {
+  int32_t blocks;
+  int32_t shift[16];
+  int32_t width[16];
+  int64_t off_base[16];
+  int64_t off_words;
+};
+
 }  // namespace mrc
+
+struct mrc_simhash_index {
+  int device = 0;
+  cudaStream_t stream = nullptr;  // stream of the building context (the free is ordered on it)
+  int64_t n = 0;
+  int32_t hamming_max = 0;
+  mrc::SimhashLayout layout{};
+  uint64_t* fp = nullptr;  // [blocks * n] table t: fingerprints grouped by the value of block t
+  int32_t* id = nullptr;   // [blocks * n] their positions in the input
+  uint64_t* own = nullptr; // [n] the fingerprints in input order
+  int32_t* off = nullptr;  // [layout.off_words] bucket offsets of every table
+  void* block = nullptr;   // one stream-ordered allocation holding the arrays above
+};
 
 struct mrc_ctx {
   cudaStream_t stream = nullptr;
@@ -194,6 +217,15 @@ cudaError_t launch_text_grams(mrc_ctx* ctx, int64_t n_docs, const int64_t* text_
                               int64_t n_bytes, int64_t* gram_offsets, int32_t* grams, int64_t capacity,
                               int64_t* tile_doc, int32_t* tile_cnt, int64_t* group_sum, int64_t* tile_base,
                               int32_t* err);
+// Block-table Hamming index (simhash_index.cu). cnt, cursor: [L.off_words] scratch.
+SimhashLayout simhash_layout(int32_t hamming_max);
+cudaError_t launch_simhash_index_build(mrc_ctx* ctx, const uint64_t* fps, int64_t n, const SimhashLayout& L,
+                                       int32_t* cnt, int32_t* cursor, int32_t* off, uint64_t* fp_out,
+                                       int32_t* id_out);
+cudaError_t launch_simhash_index_probe(mrc_ctx* ctx, const uint64_t* q, int64_t nq, bool all_pairs, int32_t hmax,
+                                       const SimhashLayout& L, int64_t n, const uint64_t* fp, const int32_t* id,
+                                       const int32_t* off, mrc_pair* pairs, unsigned long long* count,
+                                       int64_t capacity);
 // out[t] = the MD5 (mode MRC_HASH_MD5) or SHA-1 (MRC_HASH_SHA1) Simhash feature of term t < vocab.
 cudaError_t launch_feature_table(mrc_ctx* ctx, int32_t vocab, uint64_t seed, int32_t mode, uint64_t* out);
 // Packs rows of `sig` (normalised to unit length first when `normalize`) into compare operands.

@@ -62,6 +62,10 @@ _SIGNATURES = {
     "mrc_last_error": (C.c_char_p, [C.c_void_p]),
     "mrc_text_grams": (C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                    C.POINTER(C.c_int64)]),
+    "mrc_simhash_index_build": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_void_p)]),
+    "mrc_simhash_index_match": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
+                                            C.c_int64, C.POINTER(C.c_int64)]),
+    "mrc_simhash_index_free": (None, [C.c_void_p]),
     "mrc_build_index": (C.c_int32, [C.c_void_p, C.POINTER(Docs), C.c_int32, C.POINTER(Params), C.POINTER(C.c_void_p)]),
     "mrc_signature": (C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(Docs), C.c_void_p, C.c_void_p]),
     "mrc_signature_noalloc": (C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(Docs), C.c_void_p, C.c_void_p]),
@@ -435,6 +439,38 @@ def simhash_match(ctx: Context, a, b=None, hamming_max: int = 3, capacity: int =
     def fn(buf, cap, total):
         return ctx.lib.simhash_match(ctx.handle, _ptr(a), na, _ptr(b), nb, int(hamming_max), _ptr(buf), cap,
                                      C.byref(total))
+    return _pair_call(ctx, fn, capacity, device, grow)
+
+
+class SimhashIndex:
+    """Block-table Hamming index over 64-bit fingerprints (mrc_simhash_index_*)."""
+
+    def __init__(self, ctx: Context, handle, n: int, hamming_max: int):
+        self.ctx, self.handle, self.n, self.hamming_max = ctx, handle, n, hamming_max
+
+    def free(self):
+        if self.handle:
+            self.ctx.lib.mrc_simhash_index_free(self.handle)
+            self.handle = None
+
+
+def simhash_index_build(ctx: Context, fps, hamming_max: int = 3) -> SimhashIndex:
+    n = int(fps.shape[0])
+    h = C.c_void_p()
+    ctx.check(ctx.lib.mrc_simhash_index_build(ctx.handle, _ptr(fps), n, int(hamming_max), C.byref(h)))
+    return SimhashIndex(ctx, h, n, hamming_max)
+
+
+def simhash_index_match(ctx: Context, index: SimhashIndex, queries=None, hamming_max: int | None = None,
+                        capacity: int = 1 << 20, device="cuda", grow=True):
+    """Pairs (query, index position) within hamming_max (default: the build's), or all pairs i < j
+    of the index when queries is None; the same pairs as simhash_match."""
+    nq = 0 if queries is None else int(queries.shape[0])
+    hm = index.hamming_max if hamming_max is None else int(hamming_max)
+
+    def fn(buf, cap, total):
+        return ctx.lib.mrc_simhash_index_match(ctx.handle, index.handle, _ptr(queries), nq, hm, _ptr(buf), cap,
+                                               C.byref(total))
     return _pair_call(ctx, fn, capacity, device, grow)
 
 
