@@ -39,15 +39,15 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # the news20 step, valid only while the kernel's source file is unchanged since the capture.
 NCU_TRAFFIC = {
     "gemm_f16_bound": ("paper_1810_03099_gb300/csrc/compare_tc.cu",
-                       "daccb9226e67077e6a8f000d47efaaadd566c95fcaa1980f22aa099bbcbf3b8f", 14508544),
+                       "ec6e6280a592556d6992a1efb45990cbf3a846dbb540dae47bdf989727c5936b", 15766784),
     "gemm_f16_thresh": ("paper_1810_03099_gb300/csrc/compare_tc.cu",
-                        "daccb9226e67077e6a8f000d47efaaadd566c95fcaa1980f22aa099bbcbf3b8f", 2470912),
+                        "ec6e6280a592556d6992a1efb45990cbf3a846dbb540dae47bdf989727c5936b", 2470400),
 }
 KERNEL_NOTES = {
     "gemm_f16_bound": "exact-cosine head GEMM carrying the tail-bucket bound: 2 kd flops per pair of the "
                       "triangle (kd = 128 head + 256 bucket columns); ncu: tensor pipe 75% active; candidates "
                       "where head + bound >= tau - delta'",
-    "gemm_f16_thresh": "signature compare at k = 64: one K block per tile, epilogue-bound (ncu: tensor pipe 23% "
+    "gemm_f16_thresh": "signature compare at k = 64: one K block per tile, epilogue-bound (ncu: tensor pipe 29% "
                        "active)",
     "cosine_verify": "exact scores of the bound-pruned candidates (a few tens of thousands on news20)",
     "cosine_tail": "algorithmic bytes = the fp16 head scores of the upper triangle; the postings it also walks "
