@@ -22,6 +22,7 @@ import subprocess
 import sys
 import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -631,13 +632,23 @@ def main():
     ctx2 = mrc.Context(stream2.cuda_stream)
     built = torch.cuda.Event()
 
+    # host step: the same split, as a user of the synchronous calls would write it: a second host
+    # thread (with the second context) runs the signature and Simhash matches while this thread
+    # runs the exact cosine; every call takes and returns host buffers
+    pool = ThreadPoolExecutor(max_workers=1)
+
+    def host_matches(idx):
+        ex_sh = mrc.index_simhash(ctx2, idx, np.empty(N, np.uint64))
+        p1, n1 = mrc.mrc_match(ctx2, idx, None, TAU, capacity=caps["sig"], device=None)
+        p2, n2 = mrc.simhash_match(ctx2, ex_sh, None, HMAX, capacity=caps["sh"], device=None)
+        return p1, n1, p2, n2
+
     def step(host: bool):
         if host:
             idx = mrc.mrc_build_index(ctx, offs_h, toks_h, V, params)
-            ex_sh = mrc.index_simhash(ctx, idx, np.empty(N, np.uint64))
-            p1, n1 = mrc.mrc_match(ctx, idx, None, TAU, capacity=caps["sig"], device=None)
-            p2, n2 = mrc.simhash_match(ctx, ex_sh, None, HMAX, capacity=caps["sh"], device=None)
+            fut = pool.submit(host_matches, idx)
             p3, n3 = mrc.cosine_allpairs(ctx, idx, offs_h, toks_h, TAU, capacity=caps["cos"], device=None)
+            p1, n1, p2, n2 = fut.result()
         else:
             idx = mrc.mrc_build_index(ctx, offs_d, toks_d, V, params)
             sh = mrc.index_simhash(ctx, idx, sh_dev)

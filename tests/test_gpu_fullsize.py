@@ -134,3 +134,34 @@ def test_large_allpairs_signature_match():
     for x in rng.choice(got.shape[0], min(2000, got.shape[0]), replace=False).tolist():
         i, j, s = int(got["i"][x]), int(got["j"][x]), float(got["score"][x])
         assert i < j and abs(s - orc.cos_dense(ref.S[i], ref.S[j])) <= 1e-5
+
+
+def test_fullsize_simhash_index():
+    """The block-table Hamming index at the fingerprint-index benchmark's size (10,000,000
+    fingerprints, Hamming <= 3): sampled queries and sampled rows of the all-pairs search, each
+    against the oracle's brute-force pairs of that query or row."""
+    torch = cuda_or_skip()
+    from paper_1810_03099_gb300 import mrc
+    orc = Oracle()
+    n = 10_000_000
+    X = synth.random_fingerprints(n, 51, n_near=100_000, max_flip=4)
+    rng = np.random.Generator(np.random.PCG64(52))
+    near = rng.choice(np.arange(n - 100_000, n), 8, replace=False)
+    Q = np.concatenate([X[near] ^ np.uint64(1 << 9), synth.random_fingerprints(8, 53)])
+    ctx = mrc.Context()
+    sidx = mrc.simhash_index_build(ctx, torch.from_numpy(X.view(np.int64)).cuda(), HMAX)
+    got = mrc.pairs_to_numpy(mrc.simhash_index_match(ctx, sidx, torch.from_numpy(Q.view(np.int64)).cuda())[0])
+    _, pi, pj, ph = orc.hamming_pairs(Q, X, HMAX)
+    assert sorted(zip(got["i"].tolist(), got["j"].tolist(), got["score"].astype(int).tolist())) == \
+        sorted(zip(pi.tolist(), pj.tolist(), ph.tolist()))
+    assert len(pi) >= 8
+    # all pairs of the index: the pairs of sampled rows i (with j > i)
+    allp = mrc.pairs_to_numpy(mrc.simhash_index_match(ctx, sidx, capacity=1 << 22)[0])
+    rows = np.concatenate([X.shape[0] - 100_000 - 1 - np.arange(4), near[:4]])
+    for i in rows.tolist():
+        i = int(i)
+        mine = sorted((int(j), int(s)) for a, j, s in zip(allp["i"], allp["j"], allp["score"]) if a == i)
+        _, _, rj, rh = orc.hamming_pairs(X[i:i + 1], X[i + 1:], HMAX)
+        assert mine == sorted(zip((rj + i + 1).tolist(), rh.tolist())), i
+    sidx.free()
+    ctx.close()
