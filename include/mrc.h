@@ -162,7 +162,11 @@ mrc_status mrc_text_grams(mrc_ctx* ctx, int64_t n_docs, const int64_t* text_offs
  * packed form for comparison, and its 64-bit Simhash (Section III).
  * vocab: number of term ids. The returned index must be freed with
  * mrc_index_free. Errors: MRC_ERR_INVALID for bad sizes/params/term ids,
- * MRC_ERR_UNSUPPORTED for documents longer than MRC_MAX_DOC_TOKENS.
+ * MRC_ERR_UNSUPPORTED for documents longer than MRC_MAX_DOC_TOKENS (the call
+ * waits for the passes that validate the documents). The signature pass may
+ * still be running when the call returns: the index is complete in order on
+ * ctx's stream. Every call that takes the index on another context's stream
+ * first makes that stream wait for the index (an event, no host wait).
  */
 mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, const mrc_params* params,
                            mrc_index** out);

@@ -56,6 +56,21 @@ void* ws_get(mrc_ctx* ctx, const char* slot, size_t bytes, mrc_status* st) {
   return p;
 }
 
+void mark_index_ready(mrc_ctx* ctx, mrc_index* x) {
+  if (!x->ready && cudaEventCreateWithFlags(&x->ready, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    x->ready = nullptr;
+    return;
+  }
+  cudaEventRecord(x->ready, ctx->stream);
+}
+
+void wait_for_index(mrc_ctx* ctx, const mrc_index* x) {
+  if (ctx->stream == x->stream) return;
+  if (x->ready) cudaStreamWaitEvent(ctx->stream, x->ready, 0);
+  else cudaStreamSynchronize(x->stream);
+}
+
 int resident_ctas(const void* func, int threads, size_t smem) {
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, size_t> smem_set;  // (kernel, device) -> limit set
@@ -706,8 +721,9 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
                              x->k, hist, above, sstate, keys, d_part, x->rnorm, x->rinv);
     if (e == cudaSuccess) e = launch_term_info(ctx, x->idf, d_part, vocab, tfidf, bf16, x->tinfo);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "reference selection"));
-    if ((st = launch_index_signatures(ctx, x, d)) != MRC_OK) return bail(st);
-    // one synchronisation: the error word, the selection state and |R_p|
+    // one synchronisation, before the signature pass: the error word of the df pass, the
+    // selection state and |R_p|; the call then returns while the signature pass runs (it meets
+    // only documents the df pass validated)
     char* hs = (char*)ctx->pinned + 1024;
     e = cudaMemcpyAsync(hs, sstate, sizeof(long long) * device_selection_words(), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess)
@@ -718,6 +734,8 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
     if (hss[6] == 0) {
       x->L_used = hss[1];
       x->h_rnorm.assign((const double*)(hs + 128), (const double*)(hs + 128) + x->k);
+      if ((st = launch_index_signatures(ctx, x, d)) != MRC_OK) return bail(st);
+      mark_index_ready(ctx, x);
       *out = x;
       return MRC_OK;
     }
@@ -739,6 +757,7 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   // The df pass already validated these documents (offsets, lengths, token ids) and the
   // signature pass meets the same ones, so the call returns without waiting for it: the index
   // is ready in stream order, like any device result.
+  mark_index_ready(ctx, x);
   *out = x;
   return MRC_OK;
 }
@@ -802,6 +821,7 @@ mrc_status mrc_text_grams(mrc_ctx* ctx, int64_t n_docs, const int64_t* text_offs
 mrc_status mrc_signature(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float* sig, uint64_t* simhash) {
   if (!ctx || !index) return MRC_ERR_INVALID;
   Scope scope(ctx);
+  wait_for_index(ctx, index);
   if (!docs) return fail(ctx, MRC_ERR_INVALID, "docs is NULL");
   if (docs->n_docs == 0) return MRC_OK;
   if (!sig && !simhash) return fail(ctx, MRC_ERR_INVALID, "no output requested");
@@ -835,6 +855,7 @@ static mrc_status match_impl(mrc_ctx* ctx, const mrc_index* index, const float* 
                       mrc_pair* pairs, int64_t capacity, int64_t* n_pairs, unsigned long long* d_total) {
   if (!ctx || !index) return MRC_ERR_INVALID;
   Scope scope(ctx);
+  wait_for_index(ctx, index);
   if (capacity < 0) return fail(ctx, MRC_ERR_INVALID, "capacity < 0");
   if (query_sig && nq < 0) return fail(ctx, MRC_ERR_INVALID, "nq < 0");
   if (n_pairs) *n_pairs = 0;
@@ -937,6 +958,7 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
                        int64_t capacity, int64_t* n_pairs, unsigned long long* d_total) {
   if (!ctx || !index) return MRC_ERR_INVALID;
   Scope scope(ctx);
+  wait_for_index(ctx, index);
   if (capacity < 0) return fail(ctx, MRC_ERR_INVALID, "capacity < 0");
   if (n_pairs) *n_pairs = 0;
   mrc_status st = MRC_OK;
@@ -1335,6 +1357,7 @@ mrc_status mrc_index_export(mrc_ctx* ctx, const mrc_index* x, float* sig, uint64
                             int32_t* part, double* rnorm) {
   if (!ctx || !x) return MRC_ERR_INVALID;
   Scope scope(ctx);
+  wait_for_index(ctx, x);
   const size_t n = (size_t)x->n_docs;
   auto cp = [&](void* dst, const void* src, size_t bytes) {
     return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream);
@@ -1365,6 +1388,7 @@ void mrc_index_free(mrc_index* x) {
   cudaGetDevice(&cur);
   if (cur != x->device) cudaSetDevice(x->device);
   free_index_arrays(x);
+  if (x->ready) cudaEventDestroy(x->ready);
   if (cur >= 0 && cur != x->device) cudaSetDevice(cur);
   delete x;
 }
@@ -1375,6 +1399,9 @@ static const char kMagic[8] = {'M', 'R', 'C', 'I', 'D', 'X', '0', '1'};
 mrc_status mrc_index_save(mrc_ctx* ctx, const mrc_index* x, const char* path) {
   if (!ctx || !x || !path) return MRC_ERR_INVALID;
   Scope scope(ctx);
+  // the copies below are plain ones: the index must be complete first
+  wait_for_index(ctx, x);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "waiting for the index");
   FILE* f = std::fopen(path, "wb");
   if (!f) return fail(ctx, MRC_ERR_INVALID, std::string("cannot open ") + path);
   const size_t n = (size_t)x->n_docs;
@@ -1500,6 +1527,7 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
   if (e == cudaSuccess && x->qnorm_min) e = launch_block_min(ctx, x->qnorm, x->n_docs, x->qnorm_min);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "index load packing"));
+  mark_index_ready(ctx, x);
   *out = x;
   return MRC_OK;
 }

@@ -199,6 +199,9 @@ mrc_status mrc_batch_create(mrc_ctx* ctx, const mrc_index* index, int64_t max_do
   if (tile_n != 0 && tile_n != 128 && tile_n != 256)
     return fail(ctx, MRC_ERR_INVALID, "mrc_batch_create: tile_n must be 0, 128 or 256");
   cudaSetDevice(ctx->device);
+  // the batch runs on a stream of its own: the index must be complete first
+  wait_for_index(ctx, index);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "waiting for the index");
   mrc_batch* b = new mrc_batch();
   b->index = index;
   b->max_docs = max_docs;

@@ -116,12 +116,17 @@ struct mrc_index {
   float* qnorm_min = nullptr;     // [ceil(n / 128)] smallest non-zero qnorm of each 128-row block
   double* rnorm = nullptr;        // [k] |R_p| (written by the device reference selection)
   void* block = nullptr;          // one stream-ordered allocation holding every array above
+  cudaEvent_t ready = nullptr;    // recorded on the building stream after the index's last pass
 };
 
 namespace mrc {
 
 // ---- error / workspace helpers (api.cu) ----
 mrc_status fail(mrc_ctx* ctx, mrc_status st, const std::string& msg);
+// Index completion across streams: the build records x->ready after its last pass; a call on
+// another stream makes that stream wait for it (no host wait).
+void mark_index_ready(mrc_ctx* ctx, mrc_index* x);
+void wait_for_index(mrc_ctx* ctx, const mrc_index* x);
 mrc_status cuda_fail(mrc_ctx* ctx, cudaError_t e, const char* what);
 void* ws_get(mrc_ctx* ctx, const char* slot, size_t bytes, mrc_status* st);
 

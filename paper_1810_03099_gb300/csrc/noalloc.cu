@@ -82,6 +82,7 @@ extern "C" mrc_status mrc_signature_noalloc(mrc_ctx* ctx, const mrc_index* index
       if (prev >= 0 && prev != dev) cudaSetDevice(prev);
     }
   } restore{prev, ctx->device};
+  mrc::wait_for_index(ctx, index);
 
   if (!docs || docs->n_docs < 0) return mrc::fail(ctx, MRC_ERR_INVALID, "docs is NULL or n_docs < 0");
   if (docs->n_docs > kMaxDocs)
