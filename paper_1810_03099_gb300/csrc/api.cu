@@ -56,20 +56,25 @@ void* ws_get(mrc_ctx* ctx, const char* slot, size_t bytes, mrc_status* st) {
   return p;
 }
 
-void mark_index_ready(mrc_ctx* ctx, mrc_index* x) {
-  if (!x->ready && cudaEventCreateWithFlags(&x->ready, cudaEventDisableTiming) != cudaSuccess) {
+static void record_index_event(mrc_ctx* ctx, cudaEvent_t* ev) {
+  if (!*ev && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
-    x->ready = nullptr;
+    *ev = nullptr;
     return;
   }
-  cudaEventRecord(x->ready, ctx->stream);
+  cudaEventRecord(*ev, ctx->stream);
 }
 
-void wait_for_index(mrc_ctx* ctx, const mrc_index* x) {
+static void wait_index_event(mrc_ctx* ctx, const mrc_index* x, cudaEvent_t ev) {
   if (ctx->stream == x->stream) return;
-  if (x->ready) cudaStreamWaitEvent(ctx->stream, x->ready, 0);
+  if (ev) cudaStreamWaitEvent(ctx->stream, ev, 0);
   else cudaStreamSynchronize(x->stream);
 }
+
+void mark_index_ready(mrc_ctx* ctx, mrc_index* x) { record_index_event(ctx, &x->ready); }
+void wait_for_index(mrc_ctx* ctx, const mrc_index* x) { wait_index_event(ctx, x, x->ready); }
+void mark_index_tables(mrc_ctx* ctx, mrc_index* x) { record_index_event(ctx, &x->tables); }
+void wait_for_index_tables(mrc_ctx* ctx, const mrc_index* x) { wait_index_event(ctx, x, x->tables); }
 
 int resident_ctas(const void* func, int threads, size_t smem) {
   static std::mutex mu;
@@ -721,6 +726,7 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
                              x->k, hist, above, sstate, keys, d_part, x->rnorm, x->rinv);
     if (e == cudaSuccess) e = launch_term_info(ctx, x->idf, d_part, vocab, tfidf, bf16, x->tinfo);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "reference selection"));
+    mark_index_tables(ctx, x);
     // one synchronisation, before the signature pass: the error word of the df pass, the
     // selection state and |R_p|; the call then returns while the signature pass runs (it meets
     // only documents the df pass validated)
@@ -753,6 +759,7 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   int32_t* part_stage = (int32_t*)(stage + 8 * (size_t)vocab);
   x->L_used = select_references(h_df, vocab, d.n_docs, *params, part_stage, h_idf, &x->h_rnorm);
   if ((st = upload_references(ctx, x, part_stage, (float*)(stage + 12 * (size_t)vocab))) != MRC_OK) return bail(st);
+  mark_index_tables(ctx, x);
   if ((st = launch_index_signatures(ctx, x, d)) != MRC_OK) return bail(st);
   // The df pass already validated these documents (offsets, lengths, token ids) and the
   // signature pass meets the same ones, so the call returns without waiting for it: the index
@@ -958,7 +965,7 @@ static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_do
                        int64_t capacity, int64_t* n_pairs, unsigned long long* d_total) {
   if (!ctx || !index) return MRC_ERR_INVALID;
   Scope scope(ctx);
-  wait_for_index(ctx, index);
+  wait_for_index_tables(ctx, index);  // idf and the term table only
   if (capacity < 0) return fail(ctx, MRC_ERR_INVALID, "capacity < 0");
   if (n_pairs) *n_pairs = 0;
   mrc_status st = MRC_OK;
@@ -1389,6 +1396,7 @@ void mrc_index_free(mrc_index* x) {
   if (cur != x->device) cudaSetDevice(x->device);
   free_index_arrays(x);
   if (x->ready) cudaEventDestroy(x->ready);
+  if (x->tables) cudaEventDestroy(x->tables);
   if (cur >= 0 && cur != x->device) cudaSetDevice(cur);
   delete x;
 }
@@ -1527,6 +1535,7 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
   if (e == cudaSuccess && x->qnorm_min) e = launch_block_min(ctx, x->qnorm, x->n_docs, x->qnorm_min);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "index load packing"));
+  mark_index_tables(ctx, x);
   mark_index_ready(ctx, x);
   *out = x;
   return MRC_OK;

@@ -117,6 +117,7 @@ struct mrc_index {
   double* rnorm = nullptr;        // [k] |R_p| (written by the device reference selection)
   void* block = nullptr;          // one stream-ordered allocation holding every array above
   cudaEvent_t ready = nullptr;    // recorded on the building stream after the index's last pass
+  cudaEvent_t tables = nullptr;   // recorded once the term tables (df, idf, tinfo) are complete
 };
 
 namespace mrc {
@@ -127,6 +128,10 @@ mrc_status fail(mrc_ctx* ctx, mrc_status st, const std::string& msg);
 // another stream makes that stream wait for it (no host wait).
 void mark_index_ready(mrc_ctx* ctx, mrc_index* x);
 void wait_for_index(mrc_ctx* ctx, const mrc_index* x);
+// The same for the term tables alone (the exact cosine reads idf and the term table only, so it
+// may run beside the index's signature pass).
+void mark_index_tables(mrc_ctx* ctx, mrc_index* x);
+void wait_for_index_tables(mrc_ctx* ctx, const mrc_index* x);
 mrc_status cuda_fail(mrc_ctx* ctx, cudaError_t e, const char* what);
 void* ws_get(mrc_ctx* ctx, const char* slot, size_t bytes, mrc_status* st);
 
