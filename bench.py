@@ -129,6 +129,14 @@ def load_workload():
     return synth.cached_corpus(WORKLOAD)
 
 
+def max_over_ranks(value: float, dist, device: str) -> float:
+    """The largest of every rank's value (the job's time is its slowest rank's)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, rank, world):
     """The FP64 oracle on the host cores, on a bounded sample of the same workload."""
     if rank != 0:
@@ -724,9 +732,7 @@ def main():
                     acc[key] += st[key]
         stats = list(stats.values())
         if dist:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+            total_ms = max_over_ranks(total_ms, dist, "cuda")
         return total_ms, stats
 
     # the headline region runs the library as a user does; a second region of the same steps
