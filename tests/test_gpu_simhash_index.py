@@ -123,3 +123,18 @@ def test_large_index_query_search(torch, M, ctx, orc):
     got = triples(M, M.simhash_index_match(ctx, sidx, dev(torch, Q), 3)[0])
     assert got == oracle_triples(orc, Q, X, 3) and len(got) >= 250
     sidx.free()
+
+
+def test_capacity_overflow_keeps_a_subset_and_reports_the_total(torch, M, ctx, orc):
+    X = skewed_fingerprints(8000, 5)
+    want = oracle_triples(orc, X, None, 3)
+    sidx = M.simhash_index_build(ctx, dev(torch, X), 3)
+    for cap in (0, 1, 1000):
+        buf, total = M.simhash_index_match(ctx, sidx, capacity=cap, grow=False)
+        assert total == len(want)
+        got = triples(M, buf) if cap > 0 else []
+        assert len(got) == min(cap, len(want)) and set(got) <= set(want)
+    # host pairs grown to the total
+    got = M.simhash_index_match(ctx, sidx, capacity=16, device=None)[0]
+    assert sorted(zip(got["i"].tolist(), got["j"].tolist(), got["score"].astype(int).tolist())) == want
+    sidx.free()
