@@ -92,12 +92,16 @@ __global__ void __launch_bounds__(256) k_sh_probe(const uint64_t* __restrict__ q
   const int32_t s = __ldg(o + key), e = __ldg(o + key + 1);
   const uint64_t* tf = fp + (int64_t)t * n;
   const int32_t* ti = id + (int64_t)t * n;
+  // two candidate loads in flight per lane: the second step's load is issued with the first
+  uint64_t nxt = s + lane < e ? __ldg(tf + s + lane) : 0ull;
   for (int32_t x0 = s; x0 < e; x0 += 32) {
     const int32_t x = x0 + lane;
+    const uint64_t cur = nxt;
+    if (x0 + 32 < e) nxt = x + 32 < e ? __ldg(tf + x + 32) : 0ull;  // warp-uniform branch
     bool ok = false;
     int32_t j = 0, d = 0;
     if (x < e) {
-      const uint64_t m = __ldg(tf + x) ^ fq;
+      const uint64_t m = cur ^ fq;
       d = __popcll(m);
       ok = d <= hmax;
       if (ok) {
