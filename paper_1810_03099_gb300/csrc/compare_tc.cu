@@ -125,25 +125,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
       : "memory");
 }
 
-// The same copy written to the same shared-memory offset of every CTA in cta_mask (of this
-// cluster); each destination's barrier at bar's offset receives the bytes it gets.
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar,
-                                               uint16_t cta_mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(cta_mask)
-      : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
 // groups 1024 bytes apart (SBO), descriptor version 1.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -174,13 +155,6 @@ __device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
         "l"(a), "l"(b), "r"(id), "r"(acc));
   }
-}
-// Arrives on the barrier at bar's offset in every CTA of cta_mask once this CTA's MMAs so far
-// are done.
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t cta_mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
-                   "r"(smem_u32(bar)), "h"(cta_mask)
-               : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -316,13 +290,8 @@ __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)
   __syncwarp();
 }
 
-// MC = 1: launched as clusters of two CTAs that take the two 128-row halves of the same
-// 256-column super tile (consecutive tile indices), so they need the same B tile: each CTA
-// loads one 128-row half of it and multicasts it to both, halving B's L2-to-SM traffic. A
-// stage of either CTA may be refilled only when both CTAs' MMAs are done with it (each MMA
-// commit arrives on both CTAs' empty barrier), and both CTAs walk every tile of their pair
-// (a half beyond the last row is computed on zero rows and masked).
-template <int FMT, int MC>
+// Streaming kernel (any K): every CTA loads its own A and B tiles into a STAGES-deep ring.
+template <int FMT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_compare(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
                    const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1, GemmParams p) {
@@ -351,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], MC ? 2 : 1);
+      mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -370,8 +339,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t rank = MC ? cluster_rank() : 0u;
-  if (MC) cluster_sync();  // the peer's barriers are initialised before any multicast reaches them
   const int32_t kblocks = p.kblocks_dev ? *p.kblocks_dev : p.kblocks;
 
   if (warp == 0) {
@@ -383,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
         int64_t bi, bj;
-        if (!decode_tile<BN>(p, t, bi, bj) && !MC) continue;
+        if (!decode_tile<BN>(p, t, bi, bj)) continue;
         for (int kb = 0; kb < kblocks; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.err)) {
             ok = false;
@@ -394,11 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           armed[stage] = (int32_t)phase;
           const int x = kb * (FMT == OP_E4M3 ? kRowBytes : kRowBytes / 2);
           tma_load_2d(sbase, &tA0, x, (int)(bi * kBM), &full[stage]);
-          if (MC)
-            tma_load_2d_mc(sbase + A_BYTES + rank * (B_BYTES / 2), &tB0, x, (int)(bj * BN + rank * (BN / 2)),
-                           &full[stage], (uint16_t)0x3);
-          else
-            tma_load_2d(sbase + A_BYTES, &tB0, x, (int)(bj * BN), &full[stage]);
+          tma_load_2d(sbase + A_BYTES, &tB0, x, (int)(bj * BN), &full[stage]);
           if (C::NOPS == 2) {
             tma_load_2d(sbase + A_BYTES + B_BYTES, &tA1, x, (int)(bi * kBM), &full[stage]);
             tma_load_2d(sbase + 2 * A_BYTES + B_BYTES, &tB1, x, (int)(bj * BN), &full[stage]);
@@ -426,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t id = idesc(BN);
       for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
         int64_t bi, bj;
-        if (!decode_tile<BN>(p, t, bi, bj) && !MC) continue;
+        if (!decode_tile<BN>(p, t, bi, bj)) continue;
         const uint32_t ab = (uint32_t)(it & 1);
         if (!mbar_wait(&acc_empty[ab], (uint32_t)((it >> 1) & 1) ^ 1u, abort_flag, p.err)) break;
         tc_fence_after();
@@ -451,10 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               umma<FMT>(d1, sdesc(sa1 + kk * 32), bd, id, 1u);
             }
           }
-          if (MC)
-            umma_commit_mc(&empty[stage], (uint16_t)0x3);
-          else
-            umma_commit(&empty[stage]);
+          umma_commit(&empty[stage]);
           if (++stage == C::STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -476,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int64_t it = 0;
     for (int64_t t = blockIdx.x; t < p.n_tiles; t += gridDim.x) {
       int64_t bi, bj;
-      if (!decode_tile<BN>(p, t, bi, bj) && !MC) continue;
+      if (!decode_tile<BN>(p, t, bi, bj)) continue;
       const uint32_t ab = (uint32_t)(it & 1);
       int ok = 1;
       if (lane == 0) ok = mbar_wait(&acc_full[ab], (uint32_t)((it >> 1) & 1), abort_flag, p.err) ? 1 : 0;
@@ -563,7 +523,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
-  if (MC) cluster_sync();  // no CTA leaves while its peer may still multicast into it
 }
 
 // ---------------------------------------------------------------------------------------
@@ -982,11 +941,9 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   using C = Cfg<FMT>;
   constexpr int BN = C::BN;
   const bool fp8 = FMT == OP_E4M3;
-  // clusters of two with B multicast for the 256-column formats (see k_gemm_compare)
-  const bool mc = C::NOPS == 1 && BN == 2 * kBM && ctx->num_sms >= 2;
   CUtensorMap tA0, tA1, tB0, tB1;
   if (!make_map(&tA0, g.a_hi, g.na, g.kbytes, kBM, fp8) ||
-      !make_map(&tB0, g.b_hi, g.nb, g.kbytes, mc ? BN / 2 : BN, fp8))
+      !make_map(&tB0, g.b_hi, g.nb, g.kbytes, BN, fp8))
     return cudaErrorInvalidValue;
   if (C::NOPS == 2) {
     if (!make_map(&tA1, g.a_lo, g.na, g.kbytes, kBM, fp8) || !make_map(&tB1, g.b_lo, g.nb, g.kbytes, BN, fp8))
@@ -1001,7 +958,6 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   p.kblocks = g.kbytes / kRowBytes;
   p.triangle = g.triangle;
   p.tiles_m = (g.na + kBM - 1) / kBM;
-  if (mc) p.tiles_m += p.tiles_m & 1;  // row blocks in pairs (a pair's second half may be all padding)
   p.tiles_n = (g.nb + BN - 1) / BN;
   p.super_rows = (g.na + BN - 1) / BN;
   p.n_tiles = g.triangle ? p.super_rows * (p.super_rows + 1) / 2 * (BN / kBM) : p.tiles_m * p.tiles_n;
@@ -1021,33 +977,9 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   p.kblocks_dev = g.kblocks_dev;
   const size_t smem = 1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256 + 4 * (32 * 33 + 32) * 4 +
                       4 * kPairBuf * sizeof(mrc_pair);
-  if (resident_ctas(k_gemm_compare<FMT, 0>, kThreads, smem) <= 0 ||
-      (mc && resident_ctas(k_gemm_compare<FMT, 1>, kThreads, smem) <= 0))
-    return cudaErrorInvalidConfiguration;
+  if (resident_ctas(k_gemm_compare<FMT>, kThreads, smem) <= 0) return cudaErrorInvalidConfiguration;
   int64_t grid = ctx->num_sms;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  if (mc) {
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = ctx->stream;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    // as many pairs as can be resident at once (a GPC with an odd SM count leaves one SM out)
-    cfg.gridDim = dim3((unsigned)(ctx->num_sms & ~1));
-    int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, k_gemm_compare<FMT, 1>, &cfg) != cudaSuccess || clusters <= 0) {
-      cudaGetLastError();
-      return cudaErrorInvalidConfiguration;
-    }
-    grid = std::min<int64_t>(grid, 2 * (int64_t)clusters);
-  }
   if (p.n_tiles < grid) grid = p.n_tiles;
-  if (mc) grid &= ~int64_t(1);  // whole clusters; n_tiles is even, so both CTAs of a pair see the same tiles
   if (grid <= 0) return cudaSuccess;
   // algorithmic work: 2 K flops per evaluated pair (the triangle counts i < j only)
   const double k_elems = (double)g.kbytes / (fp8 ? 1.0 : 2.0);
@@ -1060,15 +992,8 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   const double bytes = (double)C::NOPS * (double)(g.na + (g.triangle ? 0 : g.nb)) * g.kbytes;
   cudaEvent_t ev = nullptr;
   timing_begin(ctx, g.name ? g.name : name, bytes, flops, &ev);
-  cudaError_t e = cudaSuccess;
-  if (mc) {
-    cfg.gridDim = dim3((unsigned)grid);
-    e = cudaLaunchKernelEx(&cfg, k_gemm_compare<FMT, 1>, tA0, tA1, tB0, tB1, p);
-  } else {
-    k_gemm_compare<FMT, 0><<<(unsigned)grid, kThreads, smem, ctx->stream>>>(tA0, tA1, tB0, tB1, p);
-  }
+  k_gemm_compare<FMT><<<(unsigned)grid, kThreads, smem, ctx->stream>>>(tA0, tA1, tB0, tB1, p);
   timing_end(ctx, ev);
-  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
