@@ -1,16 +1,24 @@
 """Benchmark of the Multi-reference Cosine hot path on one GB300 (replicas on N GPUs).
 
-One step = the whole path over the NEWS20-shaped synthetic corpus (18,846
-documents, 60,000 terms, k = 64): index build (term counts, TF-IDF, reference
-selection, signatures, Simhash, packed operands), all-pairs signature match
-(FP32 form, tau = 0.9), all-pairs Simhash match (Hamming <= 3), and all-pairs
-exact TF-IDF cosine (tau = 0.9).
+Headline step (the million-document precision workload: 1,000,000 synthetic documents, 2^18
+hashed terms, Zipf(1.05) topic mixtures, lognormal lengths with median 300, 5 % near-duplicates;
+k = 64 references, tau = 0.9, Hamming <= 3): one pass of the whole hot path over the corpus,
+  index build (term counts, TF-IDF with bfloat16 weights, reference selection, signatures,
+  fused Simhash, unit-length E4M3 operands) -> all-pairs signature compare on the tensor cores
+  in FP8 E4M3 with FP32 accumulation at tau - 0.02 -> FP32 rescoring of every candidate ->
+  block-table Hamming index over the Simhashes -> all Simhash pairs within distance 3.
+The same step in the plain FP32 form (fp32 weights, fp16 compare at the proven bound
+tau - 2e-3, FP32 rescoring) runs on the same corpus for the forms' ratio.
 
-value = documents/s of the whole step with inputs resident in HBM; e2e = the
-same through the C ABI with host buffers (host->device copies of the corpus
-and device->host copies of every pair list inside the timed region).
+value = documents/s of the precision-form step with inputs resident in HBM; e2e = the same step
+through the C ABI with host buffers (the corpus copied in, every pair list copied out). The line
+also carries: the FP32 form's docs/s and the ratio, signature pairs/s, recall / precision and
+per-stage errors of both forms against the FP64 oracle on a seeded 20,000-document subset, the
+serving form's p50 / p99 latency at arrival rates from 10k to 500k docs/s against a
+10-million-document index, the NEWS20-shaped step with the exact cosine, per-kernel rooflines,
+and the oracle's own speed on one and on all host cores.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mrc|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mrc|reference] [--form ...]
 """
 from __future__ import annotations
 
@@ -29,11 +37,16 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "news20"
+HEADLINE = "precision"  # workload recipe of the headline step (1,000,000 documents)
 K = 64
 TAU = 0.9
+MARGIN = 0.02
 HMAX = 3
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+SUBSET_DOCS = 20000  # accuracy subset: the FP64 oracle's all pairs
+ORACLE_SAMPLE = 12000  # documents of the reference arm's step
+CPU_BASELINE_SAMPLE = 4000  # documents of the main line's oracle timing
+
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
@@ -124,11 +137,6 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def load_workload():
-    from paper_1810_03099_gb300 import synth
-    return synth.cached_corpus(WORKLOAD)
-
-
 def max_over_ranks(value: float, dist, device: str) -> float:
     """The largest of every rank's value (the job's time is its slowest rank's)."""
     import torch
@@ -137,63 +145,78 @@ def max_over_ranks(value: float, dist, device: str) -> float:
     return float(t.item())
 
 
+
+def _oracle_step(to, sub, vocab, tau, hmax):
+    """One oracle step on a host corpus: index build, all signature pairs, all Simhash pairs."""
+    from oracle.oracle import Params
+    t0 = time.perf_counter()
+    ref = to.build_index(sub.offsets, sub.tokens, vocab, Params(k=K, tau=tau, hamming_max=hmax, bf16=True))
+    t1 = time.perf_counter()
+    n_sig = to.sig_pairs(ref.S, tau)[0]
+    n_sh = to.hamming_pairs(ref.F, hmax)[0]
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1, n_sig, n_sh
+
+
+def _oracle_subset(n):
+    """The first n documents of the headline recipe, drawn on the host (no GPU needed)."""
+    from paper_1810_03099_gb300 import synth
+    return synth.make_corpus(HEADLINE, n_docs=n)
+
+
 def run_reference(args, rank, world):
-    """The FP64 oracle on the host cores, on a bounded sample of the same workload."""
+    """The FP64 oracle as it stands, on every host core: the headline step (index build, all
+    signature pairs, all Simhash pairs) over the first ORACLE_SAMPLE documents of the headline recipe
+    (a subset: all-pairs work grows with the square of the documents, so this is a stated
+    sample, not scaled up). Rank 0 only; other ranks exit without work."""
     if rank != 0:
         return
-    from oracle.oracle import Oracle, Params, build_index
-    c = load_workload()
-    N = c.n_docs
-    n = 3000  # sample: the first 3,000 documents
-    sub = c.subset(np.arange(n))
-    orc = Oracle()
-    p = Params(k=K, tau=TAU, hamming_max=HMAX)
+    from oracle.threaded import ThreadedOracle, cpu_model, host_cores
+    sub = _oracle_subset(ORACLE_SAMPLE)
+    to = ThreadedOracle(host_cores())
     times = []
     for it in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        ref = build_index(sub.offsets, sub.tokens, c.vocab, p, orc)
-        t1 = time.perf_counter()
-        orc.sig_pairs(ref.S, TAU)
-        orc.hamming_pairs(ref.F, None, HMAX)
-        orc.cosine_pairs(ref.row_ptr, ref.terms, ref.w, TAU)
-        t2 = time.perf_counter()
+        r = _oracle_step(to, sub, sub.vocab, TAU, HMAX)
         if it >= args.warmup:
-            times.append((t1 - t0, t2 - t1))
-    lin = float(np.mean([t[0] for t in times]))
-    quad = float(np.mean([t[1] for t in times]))
-    # per-document work scales with N, pair work with N^2: extrapolate the sample to the workload
-    full_s = lin * (N / n) + quad * (N / n) ** 2
-    value = N / full_s
+            times.append(r[0] + r[1])
+    to.close()
+    step_s = float(np.mean(times))
+    value = sub.n_docs / step_s
     line = {"metric": "docs/s", "value": value, "unit": "docs/s", "n_gpus": 0, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": full_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"{WORKLOAD}: 18,846 docs, 60,000 terms, k={K}, all-pairs signature match "
-                                   f"tau={TAU} + Simhash h<={HMAX} + exact cosine tau={TAU}"},
-            "cpu_baseline": {"kind": "oracle", "value": value, "unit": "docs/s", "cores": 1,
-                             "sample": f"first {n} of {N} documents per step; per-document time scaled by N/n and "
-                                       f"all-pairs time by (N/n)^2"},
+            "config": {"workload": f"{HEADLINE}: first {sub.n_docs} of 1,000,000 documents of the recipe (2^18 "
+                                   f"terms, Zipf 1.05, median 300 tokens), k={K}, bf16 weights, all signature pairs "
+                                   f"tau={TAU} + all Simhash pairs h<={HMAX}",
+                       "parallelism": f"{to.threads} host threads"},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": "docs/s", "cores": to.threads,
+                             "cpu": cpu_model(),
+                             "sample": f"first {sub.n_docs} documents of the headline recipe, whole step on them "
+                                       f"(not scaled to 1,000,000)"},
             "e2e": {"value": value, "unit": "docs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_leg(c):
-    """A short timing of the oracle (same as --impl reference, fewer steps)."""
-    from oracle.oracle import Oracle, Params, build_index
-    N = c.n_docs
-    n = 3000
-    sub = c.subset(np.arange(n))
-    orc = Oracle()
-    p = Params(k=K, tau=TAU, hamming_max=HMAX)
-    t0 = time.perf_counter()
-    ref = build_index(sub.offsets, sub.tokens, c.vocab, p, orc)
-    t1 = time.perf_counter()
-    orc.sig_pairs(ref.S, TAU)
-    orc.hamming_pairs(ref.F, None, HMAX)
-    orc.cosine_pairs(ref.row_ptr, ref.terms, ref.w, TAU)
-    t2 = time.perf_counter()
-    full_s = (t1 - t0) * (N / n) + (t2 - t1) * (N / n) ** 2
-    return {"value": N / full_s, "unit": "docs/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {n} of {N} documents, one pass; per-document time x N/n, all-pairs time x (N/n)^2"}
+def cpu_baseline_leg():
+    """The oracle on CPU_BASELINE_SAMPLE documents of the headline recipe, once on one core and
+    once on all cores: docs/s of the whole step on that sample, and its parts."""
+    from oracle.threaded import ThreadedOracle, cpu_model, host_cores
+    sub = _oracle_subset(CPU_BASELINE_SAMPLE)
+    out = {}
+    for label, threads in (("one_core", 1), ("all_cores", host_cores())):
+        to = ThreadedOracle(threads)
+        tb, tp, n_sig, n_sh = _oracle_step(to, sub, sub.vocab, TAU, HMAX)
+        to.close()
+        n = sub.n_docs
+        out[label] = {"docs_per_s": n / (tb + tp), "build_docs_per_s": n / tb,
+                      "pairs_per_s": n * (n - 1) / 2 / tp, "threads": threads, "sig_pairs": n_sig,
+                      "simhash_pairs": n_sh}
+    best = out["all_cores"]
+    return {"value": best["docs_per_s"], "unit": "docs/s", "cores": best["threads"], "kind": "oracle",
+            "cpu": cpu_model(), "one_core_docs_per_s": out["one_core"]["docs_per_s"], "detail": out,
+            "sample": f"first {sub.n_docs} documents of the headline recipe (FP64 oracle: index build, all "
+                      f"signature pairs tau={TAU}, all Simhash pairs h<={HMAX}), whole step on the sample, not "
+                      f"scaled to 1,000,000 documents"}
 
 
 def _timed(fn, reps=1):
@@ -581,236 +604,406 @@ def form_serving(args):
 BASE_QUERY_SEED = 1810031999
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="mrc", choices=["mrc", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="news20", choices=["news20", "precision", "batching", "serving", "features", "text", "study", "simhash_index",
-                             "forms"],
-                    help="news20 (default): the headline step; the others measure the three forms")
-    ap.add_argument("--batches", type=int, default=4096)
-    ap.add_argument("--serving-docs", type=int, default=10_000_000)
-    args = ap.parse_args()
-    if args.form != "news20" and args.impl == "mrc":
-        import torch
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        for f in (["precision", "batching", "serving"] if args.form == "forms" else [args.form]):
-            {"precision": form_precision, "batching": form_batching, "serving": form_serving,
-             "features": form_features, "text": form_text, "study": form_study,
-             "simhash_index": form_simhash_index}[f](args)
-        return
+def _stage_err(a, b):
+    d = np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64))
+    return {"max": float(d.max()) if d.size else 0.0, "mean": float(d.mean()) if d.size else 0.0, "n": int(d.size)}
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        return
 
+def accuracy_vs_fp64(c, ctx):
+    """Both forms against the plain FP64 oracle on a seeded SUBSET_DOCS-document subset of the
+    corpus (which is then the index corpus): recall and precision of the final pair sets, the
+    misses, and the error of each stage of the pipeline against FP64 -- the signature entries
+    (bfloat16 weight table in the precision form), the tensor-core compare's own cosine of every
+    candidate (FP8 E4M3 or fp16), and the FP32-rescored scores of the final pairs."""
+    from oracle.oracle import Params
+    from oracle.threaded import ThreadedOracle, host_cores
+    from paper_1810_03099_gb300 import mrc
+    sel = np.sort(np.random.Generator(np.random.PCG64(7)).choice(c.n_docs, SUBSET_DOCS, replace=False))
+    sub = c.host_subset(sel)
+    to = ThreadedOracle(host_cores())
+    ref = to.build_index(sub.offsets, sub.tokens, c.vocab, Params(k=K))
+    tot, pi, pj, _ = to.sig_pairs(ref.S, TAU)
+    to.close()
+    truth = set(zip(pi.tolist(), pj.tolist()))
+    nrm = np.linalg.norm(ref.S, axis=1)
+    U = np.divide(ref.S, nrm[:, None], out=np.zeros_like(ref.S), where=nrm[:, None] > 0)
+
+    def cos64(i, j):
+        return np.einsum("ij,ij->i", U[i], U[j])
+
+    out = {"docs": SUBSET_DOCS, "pairs_fp64": int(tot), "tau": TAU, "margin": MARGIN,
+           "reading": "precision form: idf / reference weights stored as bfloat16, signature arithmetic FP32"}
+    for name, prec in (("bf16_fp8", 1), ("fp32", 0)):
+        idx = mrc.mrc_build_index(ctx, sub.offsets, sub.tokens, c.vocab, mrc.params_default(k=K, precision=prec))
+        ex = mrc.mrc_index_export(ctx, idx)
+        final = mrc.mrc_match(ctx, idx, None, TAU, device=None)[0]
+        ctx.set_rescoring(False)
+        cand = mrc.mrc_match(ctx, idx, None, TAU, device=None)[0]
+        ctx.set_rescoring(True)
+        idx.free()
+        have = set(zip(final["i"].tolist(), final["j"].tolist()))
+        inter = len(have & truth)
+        cand_set = set(zip(cand["i"].tolist(), cand["j"].tolist()))
+        fi, fj = final["i"].astype(np.int64), final["j"].astype(np.int64)
+        ci, cj = cand["i"].astype(np.int64), cand["j"].astype(np.int64)
+        # signature stage: the raw signature entries against FP64; the unit signatures compared
+        su = ex["sig"].astype(np.float64)
+        out[name] = {
+            "pairs": len(have), "recall": inter / max(len(truth), 1), "precision": inter / max(len(have), 1),
+            "missed": len(truth - have), "extra": len(have - truth),
+            "candidates": len(cand_set), "missed_by_compare": len(truth - cand_set),
+            "stage_error_vs_fp64": {
+                "signature_entries": _stage_err(su, ref.S),
+                "compare_cosine_of_candidates": _stage_err(cand["score"], cos64(ci, cj)),
+                "rescored_scores_of_pairs": _stage_err(final["score"], cos64(fi, fj)),
+            },
+        }
+    return out
+
+
+def _kernel_stats(ctxs):
+    stats = {}
+    for cx in ctxs:
+        for st in cx.kernel_stats():
+            acc = stats.setdefault(st["name"], dict(st, launches=0, ms=0.0, bytes=0.0, flops=0.0))
+            for key in ("launches", "ms", "bytes", "flops"):
+                acc[key] += st[key]
+    return list(stats.values())
+
+
+def _roofline(s, peaks, n_docs=None, k=K, sustained=True):
+    """Roofline object of one kernel from its per-kernel event totals. Compares are held to the
+    peak of their own operand type (FP8 = 2 x the measured bf16 rate, fp16 = the bf16 rate),
+    with the method's work (2 k flops per compared pair, the triangle only for all pairs); the
+    other kernels to the measured HBM copy bandwidth with their algorithmic bytes."""
+    per_launch_s = s["ms"] / s["launches"] / 1e3
+    name = s["name"]
+    if s["flops"] > 0 and name.startswith("gemm"):
+        fp8 = "e4m3" in name
+        bf16 = peaks["bf16_tflops_sustained"] if sustained else peaks["bf16_tflops"]
+        peak = bf16 * (2.0 if fp8 else 1.0)
+        achieved = s["flops"] / s["launches"] / per_launch_s / 1e12
+        r = {"bound": "tensor", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+             "frac": achieved / peak, "traffic": ncu_traffic(name),
+             "peak_source": f"{peaks['source']} bf16 {'sustained' if sustained else 'burst'}"
+                            f"{' x 2 (FP8 nominal ratio 4.5 / 2.25)' if fp8 else ' (fp16: same nominal rate)'}",
+             "work": "2 k flops per compared pair (method work)"}
+    else:
+        achieved = s["bytes"] / s["launches"] / per_launch_s / 1e9
+        peak = peaks["hbm_gbs"]
+        r = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+             "frac": achieved / peak, "traffic": ncu_traffic(name), "peak_source": peaks["source"] + " copy"}
+    r["ms_per_launch"] = per_launch_s * 1e3
+    if name in KERNEL_NOTES:
+        r["note"] = KERNEL_NOTES[name]
+    return r
+
+
+def run_headline(args, rank, world, local):
     import torch
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    from paper_1810_03099_gb300 import mrc
+    from paper_1810_03099_gb300 import mrc, synth
 
-    c = load_workload()
-    N, V = c.n_docs, c.vocab
-    offs_d = torch.from_numpy(c.offsets).cuda()
-    toks_d = torch.from_numpy(c.tokens).cuda()
-    offs_h = torch.from_numpy(c.offsets).pin_memory()
-    toks_h = torch.from_numpy(c.tokens).pin_memory()
-    # the index build and the exact cosine (the critical path) run on a high-priority stream, so
-    # the matches on the second stream fill idle SMs instead of delaying its kernels
-    stream = torch.cuda.Stream(priority=-1)
+    c = synth.make_corpus_device(HEADLINE)
+    N, V, T = c.n_docs, c.vocab, c.n_tokens
+    stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = mrc.Context(stream.cuda_stream)
-    params = mrc.params_default(k=K, tau=TAU, hamming_max=HMAX)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    caps = {"sig": 1 << 22, "cos": 1 << 22, "sh": 1 << 22}
-    counts = {}
-    # device step: stream-ordered calls into preallocated device pair buffers, counts on the device;
-    # the signature and Simhash matches run on a second stream (their own context) beside the
-    # exact cosine, which needs the index only
-    pbuf = {key: torch.empty((cap, 3), dtype=torch.int32, device="cuda") for key, cap in caps.items()}
-    dcount = torch.zeros(3, dtype=torch.int64, device="cuda")
+    params = {1: mrc.params_default(k=K, tau=TAU, precision=1, margin=MARGIN, hamming_max=HMAX),
+              0: mrc.params_default(k=K, tau=TAU, precision=0, hamming_max=HMAX)}
+    cap, sh_cap = 1 << 25, 1 << 23
+    pbuf = torch.empty((cap, 3), dtype=torch.int32, device="cuda")
+    shbuf = torch.empty((sh_cap, 3), dtype=torch.int32, device="cuda")
+    dcount = torch.zeros(1, dtype=torch.int64, device="cuda")
     sh_dev = torch.empty(N, dtype=torch.int64, device="cuda")
-    stream2 = torch.cuda.Stream()
-    ctx2 = mrc.Context(stream2.cuda_stream)
-    stream3 = torch.cuda.Stream(priority=-1)
-    ctx3 = mrc.Context(stream3.cuda_stream)
-    built = torch.cuda.Event()
-    cos_done = torch.cuda.Event()
-    torch.cuda.synchronize()  # buffers above were filled on the default stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    offs_h = c.offsets.cpu().pin_memory()
+    toks_h = c.tokens.cpu().pin_memory()
+    sh_h = np.empty(N, np.uint64)
+    torch.cuda.synchronize()
+    counts = {}
 
-    # host step: the same split, as a user of the synchronous calls would write it: a second host
-    # thread (with the second context) runs the signature and Simhash matches while this thread
-    # runs the exact cosine; every call takes and returns host buffers
-    pool = ThreadPoolExecutor(max_workers=1)
-
-    def host_matches(idx):
-        stream2.wait_event(built)  # the index is complete in order on the building stream
-        ex_sh = mrc.index_simhash(ctx2, idx, np.empty(N, np.uint64))
-        p1, n1 = mrc.mrc_match(ctx2, idx, None, TAU, capacity=caps["sig"], device=None)
-        p2, n2 = mrc.simhash_match(ctx2, ex_sh, None, HMAX, capacity=caps["sh"], device=None)
-        return p1, n1, p2, n2
-
-    def step(host: bool, serial: bool = False):
-        if host:
-            idx = mrc.mrc_build_index(ctx, offs_h, toks_h, V, params)
-            built.record(stream)
-            fut = pool.submit(host_matches, idx)
-            p3, n3 = mrc.cosine_allpairs(ctx3, idx, offs_h, toks_h, TAU, capacity=caps["cos"], device=None)
-            p1, n1, p2, n2 = fut.result()
-        else:
-            idx = mrc.mrc_build_index(ctx, offs_d, toks_d, V, params)
-            # the exact cosine needs only the index's term tables: on a third (high-priority)
-            # stream it starts beside the index's signature pass (the library orders it after
-            # the tables); it is the longest chain, so it is enqueued first
-            if serial:  # per-kernel attribution: every stream after the previous one, no overlap
-                stream3.wait_stream(stream)
-            mrc.cosine_allpairs_async(ctx3, idx, offs_d, toks_d, pbuf["cos"], dcount[2:3], TAU)
-            cos_done.record(stream3)
-            sh = mrc.index_simhash(ctx, idx, sh_dev)
-            built.record(stream)
-            if serial:
-                stream2.wait_event(cos_done)
-            stream2.wait_event(built)
-            mrc.mrc_match_async(ctx2, idx, pbuf["sig"], dcount[0:1], None, TAU)
-            mrc.simhash_match_async(ctx2, sh, pbuf["sh"], dcount[1:2], None, HMAX)
-            stream.wait_stream(stream2)
-            stream.wait_stream(stream3)
-            idx.free()  # in order on the index's stream, after both streams' uses
-            return None
-        idx.free()
-        counts.update(sig_pairs=n1, simhash_pairs=n2, cosine_pairs=n3)
-        return (p1, p2, p3)
-
-    def device_counts():
-        ctx3.sync()
-        ctx2.sync()
-        ctx.sync()  # raises a device-side error of the stream-ordered calls
-        n1, n2, n3 = (int(x) for x in dcount.tolist())
-        assert n1 <= caps["sig"] and n2 <= caps["sh"] and n3 <= caps["cos"], "pair buffers too small"
-        counts.update(sig_pairs=n1, simhash_pairs=n2, cosine_pairs=n3)
-
-    def timed(host: bool, steps: int, warmup: int, with_timing: bool):
-        # with per-kernel timing the two streams are serialised, so each kernel's CUDA-event time
-        # is its own duration, not shared with the other stream's kernels
-        for _ in range(warmup):
-            step(host, serial=with_timing)
-        torch.cuda.synchronize()
+    def step(prec, host=False):
         if not host:
-            device_counts()
+            idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, V, params[prec])
+            mrc.mrc_match_async(ctx, idx, pbuf, dcount, None, TAU)  # compare + rescoring, count on the device
+            sh = mrc.index_simhash(ctx, idx, sh_dev)
+            shx = mrc.simhash_index_build(ctx, sh, HMAX)
+            _, n_sh = mrc.simhash_index_match(ctx, shx, None, HMAX, capacity=sh_cap, device="cuda")
+            shx.free()
+            idx.free()
+            counts[prec] = {"simhash_pairs": n_sh}
+            return None
+        idx = mrc.mrc_build_index(ctx, offs_h, toks_h, V, params[prec])
+        p1, n1 = mrc.mrc_match(ctx, idx, None, TAU, capacity=cap, device=None)
+        mrc.index_simhash(ctx, idx, sh_h)
+        shx = mrc.simhash_index_build(ctx, sh_h, HMAX)
+        p2, n2 = mrc.simhash_index_match(ctx, shx, None, HMAX, capacity=sh_cap, device=None)
+        shx.free()
+        idx.free()
+        counts[("host", prec)] = {"sig_pairs": n1, "simhash_pairs": n2}
+        return p1, p2
+
+    def timed(prec, steps, warmup, host=False, with_timing=False):
+        for _ in range(warmup):
+            step(prec, host)
+        torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        for cx in (ctx, ctx2, ctx3):
-            cx.reset_stats()
-            cx.set_timing(with_timing)
+        ctx.reset_stats()
+        ctx.set_timing(with_timing)
         total_ms = 0.0
         for _ in range(steps):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            step(host, serial=with_timing)
+            step(prec, host)
             e1.record(stream)
             torch.cuda.synchronize()
             total_ms += e0.elapsed_time(e1)
             if not host:
-                device_counts()
-        stats = {}
-        for cx in (ctx, ctx2, ctx3):
-            cx.set_timing(False)
-            for st in cx.kernel_stats():
-                acc = stats.setdefault(st["name"], dict(st, launches=0, ms=0.0, bytes=0.0, flops=0.0))
-                for key in ("launches", "ms", "bytes", "flops"):
-                    acc[key] += st[key]
-        stats = list(stats.values())
+                ctx.sync()
+                counts[prec]["sig_pairs"] = int(dcount.item())
+        ctx.set_timing(False)
+        stats = _kernel_stats([ctx])
         if dist:
             total_ms = max_over_ranks(total_ms, dist, "cuda")
-        return total_ms, stats
+        return total_ms / steps, stats
 
-    # the headline region runs the library as a user does; a second region of the same steps
-    # records every library kernel with CUDA events (host-side event records cost a few µs per
-    # launch, so they stay out of the headline) for the per-kernel rooflines
     clocks = ClockSampler(local)
     clocks.start()
-    dev_ms, _ = timed(False, args.steps, args.warmup, False)
+    ms8, _ = timed(1, args.steps, args.warmup)
     clk = clocks.stop()
-    inst_ms, stats = timed(False, args.steps, 1, True)
-    host_ms, _ = timed(True, max(2, args.steps // 2), 1, False)
-
-    ms_step = dev_ms / args.steps
-    value = world * N / (ms_step / 1e3)
-    e2e_ms = host_ms / max(2, args.steps // 2)
-    e2e = world * N / (e2e_ms / 1e3)
-    pair_bytes = 12 * (counts["sig_pairs"] + counts["simhash_pairs"] + counts["cosine_pairs"])
-
+    ms32, _ = timed(0, args.steps, 1)
+    _, st8 = timed(1, 2, 0, with_timing=True)
+    _, st32 = timed(0, 2, 0, with_timing=True)
+    e2e_steps = max(2, args.steps // 4)
+    ms_e2e, _ = timed(1, e2e_steps, 1, host=True)
+    # the signature pass over the whole corpus as new documents (rows a1-a4 + Simhash, from tokens)
+    sig_out = torch.empty((N, K), dtype=torch.float32, device="cuda")
+    idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, V, params[1])
+    for _ in range(2):
+        mrc.mrc_signature(ctx, idx, c.offsets, c.tokens, sig_out, sh_dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(5):
+        mrc.mrc_signature(ctx, idx, c.offsets, c.tokens, sig_out, sh_dev)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sig_ms = e0.elapsed_time(e1) / 5
+    idx.free()
+    del sig_out
     peaks = _peaks()
-    top = max(stats, key=lambda s: s["ms"]) if stats else None
-    roofline = None
-    kernels = []
-    for s in sorted(stats, key=lambda s: -s["ms"]):
-        per = s["ms"] / max(s["launches"], 1)
-        kernels.append({"name": s["name"], "launches": s["launches"], "ms_per_launch": per,
-                        "share": s["ms"] / max(sum(x["ms"] for x in stats), 1e-9)})
-    def kernel_roofline(s):
-        per_launch_s = s["ms"] / s["launches"] / 1e3
-        if s["flops"] > 0 and s["name"].startswith("gemm"):
-            achieved = s["flops"] / s["launches"] / per_launch_s / 1e12
-            peak = peaks["bf16_tflops"]
-            r = {"bound": "tensor", "kernel": s["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                 "frac": achieved / peak, "traffic": ncu_traffic(s["name"]),
-                 "peak_source": peaks["source"] + " bf16 burst (fp16 same rate)"}
-        else:
-            achieved = s["bytes"] / s["launches"] / per_launch_s / 1e9
-            peak = peaks["hbm_gbs"]
-            r = {"bound": "hbm", "kernel": s["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                 "frac": achieved / peak, "traffic": ncu_traffic(s["name"]), "peak_source": peaks["source"]}
-        if s["name"] in KERNEL_NOTES:
-            r["note"] = KERNEL_NOTES[s["name"]]
-        return r
-
-    ranked = sorted(stats, key=lambda s: -s["ms"])
-    if top:
-        roofline = kernel_roofline(top)
-    others = [kernel_roofline(s) for s in ranked[1:3] if s["bytes"] > 0 or s["flops"] > 0]
-    gpu_launches = int(sum(s["launches"] for s in stats))
-
+    sig_bytes = 4.0 * T + N * (8 + 4 * K + 8)  # tokens, offsets, raw signature out, Simhash out
+    value = world * N / (ms8 / 1e3)
+    npairs = N * (N - 1) / 2
+    stats8 = sorted(st8, key=lambda s: -s["ms"])
+    kernels = [{"name": s["name"], "launches": s["launches"] // 2, "ms_per_launch": s["ms"] / s["launches"],
+                "share": s["ms"] / max(sum(x["ms"] for x in st8), 1e-9)} for s in stats8]
+    top = stats8[0]
     line = {
         "metric": "docs/s", "value": value, "unit": "docs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: 18,846 docs, 60,000 terms, k={K}, all-pairs signature match "
-                               f"tau={TAU} (FP32 form) + Simhash h<={HMAX} + exact TF-IDF cosine tau={TAU}",
-                   "parallelism": f"replicas x{world}", "l2": "flushed (512 MB write) before every timed step"},
-        "e2e": {"value": e2e, "unit": "docs/s", "h2d_bytes_per_step": int(8 * (N + 1) + 4 * c.n_tokens) * 2,
-                "d2h_bytes_per_step": int(pair_bytes + 8 * N)},
-        "gpu_launches": gpu_launches,
-        "roofline": roofline,
+        "warmup": args.warmup, "ms_per_step": ms8, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "e4m3+f32", "data": "synthetic",
+        "config": {"workload": f"{HEADLINE}: {N} docs, {T} tokens, V=2^18, Zipf 1.05, median 300 tokens; k={K}; "
+                               f"precision form (bf16 weights, FP8 E4M3 compare, FP32 rescoring at tau={TAU} "
+                               f"+/- {MARGIN}) + all Simhash pairs h<={HMAX} via the block-table index",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "flushed (512 MB write) before every timed step; corpus 2 GB > L2"},
+        "signature_pairs_per_s": world * npairs / (ms8 / 1e3),
+        "fp32_form": {"docs_per_s": world * N / (ms32 / 1e3), "ms_per_step": ms32,
+                      "signature_pairs_per_s": world * npairs / (ms32 / 1e3), "pairs": counts.get(0, {})},
+        "vs_fp32_form": ms32 / ms8,
+        "pairs": counts.get(1, {}),
+        "e2e": {"value": world * N / (ms_e2e / 1e3), "unit": "docs/s",
+                "h2d_bytes_per_step": int(8 * (N + 1) + 4 * T + 8 * N),
+                "d2h_bytes_per_step": int(12 * (counts[("host", 1)]["sig_pairs"] + counts[("host", 1)]["simhash_pairs"])
+                                          + 8 * N)},
+        "gpu_launches": int(sum(s["launches"] for s in st8) // 2) * args.steps,
+        "roofline": _roofline(top, peaks),
+        "rooflines_next": [_roofline(s, peaks) for s in stats8[1:4] if s["bytes"] > 0 or s["flops"] > 0],
+        "signature_pass": {"ms": sig_ms, "docs_per_s": N / (sig_ms / 1e3), "bytes": sig_bytes,
+                           "achieved_gbs": sig_bytes / (sig_ms / 1e3) / 1e9,
+                           "frac": sig_bytes / (sig_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                           "work": "4 B per token + 8 B offsets + 4k B signature + 8 B Simhash per document"},
+        "fp32_form_kernels": [{"name": s["name"], "ms_per_launch": s["ms"] / s["launches"]}
+                              for s in sorted(st32, key=lambda s: -s["ms"])[:6]],
         "clocks": clk,
-        "pairs": counts,
-        "signature_pairs_per_s": None,
-        "rooflines_next": others,
-        "kernel_events_region_ms_per_step": inst_ms / args.steps,
         "kernels": kernels,
     }
-    sig_k = [s for s in stats if s["name"] == "gemm_f16_thresh"]
-    if sig_k:
-        per = sig_k[0]["ms"] / sig_k[0]["launches"] / 1e3
-        line["signature_pairs_per_s"] = N * (N - 1) / 2 / per
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_leg(c)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    ctx3.close()
-    ctx2.close()
+    return line, (c, ctx, stream, dist)
+
+
+def news20_leg(steps):
+    """The NEWS20-shaped step with both rivals (18,846 documents, 60,000 terms, k = 64): index
+    build, all-pairs FP32-form signature match, all-pairs Simhash match, all-pairs exact TF-IDF
+    cosine; the exact cosine on its own stream beside the build's signature pass and the matches."""
+    import torch
+    from paper_1810_03099_gb300 import mrc, synth
+    c = synth.cached_corpus("news20")
+    N, V = c.n_docs, c.vocab
+    offs_d = torch.from_numpy(c.offsets).cuda()
+    toks_d = torch.from_numpy(c.tokens).cuda()
+    s1, s2, s3 = torch.cuda.Stream(priority=-1), torch.cuda.Stream(), torch.cuda.Stream(priority=-1)
+    ctx, ctx2, ctx3 = mrc.Context(s1.cuda_stream), mrc.Context(s2.cuda_stream), mrc.Context(s3.cuda_stream)
+    params = mrc.params_default(k=K, tau=TAU, hamming_max=HMAX)
+    caps = 1 << 22
+    pbuf = [torch.empty((caps, 3), dtype=torch.int32, device="cuda") for _ in range(3)]
+    dcount = torch.zeros(3, dtype=torch.int64, device="cuda")
+    sh_dev = torch.empty(N, dtype=torch.int64, device="cuda")
+    built = torch.cuda.Event()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    def step(serial=False):
+        idx = mrc.mrc_build_index(ctx, offs_d, toks_d, V, params)
+        if serial:
+            s3.wait_stream(s1)
+        mrc.cosine_allpairs_async(ctx3, idx, offs_d, toks_d, pbuf[2], dcount[2:3], TAU)
+        sh = mrc.index_simhash(ctx, idx, sh_dev)
+        built.record(s1)
+        if serial:
+            s2.wait_stream(s3)
+        s2.wait_event(built)
+        mrc.mrc_match_async(ctx2, idx, pbuf[0], dcount[0:1], None, TAU)
+        mrc.simhash_match_async(ctx2, sh, pbuf[1], dcount[1:2], None, HMAX)
+        s1.wait_stream(s2)
+        s1.wait_stream(s3)
+        idx.free()
+
+    def run(n, timing):
+        for cx in (ctx, ctx2, ctx3):
+            cx.reset_stats()
+            cx.set_timing(timing)
+        tot = 0.0
+        for _ in range(n):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(s1)
+            step(serial=timing)
+            e1.record(s1)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        for cx in (ctx3, ctx2, ctx):
+            cx.sync()
+            cx.set_timing(False)
+        return tot / n, _kernel_stats([ctx, ctx2, ctx3])
+
+    for _ in range(3):
+        step()
+    ms, _ = run(steps, False)
+    _, stats = run(max(2, steps // 10), True)
+    n1, n2, n3 = (int(x) for x in dcount.tolist())
+    for cx in (ctx3, ctx2, ctx):
+        cx.close()
+    peaks = _peaks()
+    head = [s for s in stats if s["name"] == "gemm_f16_bound"]
+    out = {"docs_per_s": N / (ms / 1e3), "ms_per_step": ms,
+           "config": f"news20: {N} docs, {c.n_tokens} tokens, 60,000 terms, k={K}, FP32-form signature match "
+                     f"tau={TAU} + Simhash h<={HMAX} + exact TF-IDF cosine tau={TAU}",
+           "pairs": {"sig_pairs": n1, "simhash_pairs": n2, "cosine_pairs": n3},
+           "kernels": [{"name": s["name"], "ms_per_launch": s["ms"] / s["launches"]}
+                       for s in sorted(stats, key=lambda s: -s["ms"])[:8]]}
+    if head:
+        s = head[0]
+        t = s["ms"] / s["launches"] / 1e3
+        exec_tf = s["flops"] / s["launches"] / t / 1e12
+        method = 1.95e9  # sum over terms of df (df - 1): one multiply and one add per shared term
+        out["exact_cosine_head_gemm"] = {
+            "ms": t * 1e3, "executed_tflops": exec_tf, "executed_frac_of_bf16_burst": exec_tf / peaks["bf16_tflops"],
+            "method_tflops": method / t / 1e12, "method_frac": method / t / 1e12 / peaks["bf16_tflops"],
+            "note": "the GEMM executes 2 x 384 flops per pair of the triangle (128 head + 256 bucket-norm "
+                    "columns); the method's own work is sum_t df_t (df_t - 1) = 1.95e9 flops"}
+    return out
+
+
+def serving_leg(n_index, rates=(10000, 50000, 100000, 250000, 500000), requests=6000):
+    """The serving form: Poisson arrivals of new documents against a device-resident index of
+    n_index documents (FP16 signatures, k = 64) and their Simhashes; p50 / p99 per rate."""
+    import torch
+    from paper_1810_03099_gb300 import mrc, serving, synth
+    c = synth.make_corpus_device("serving", n_docs=n_index)
+    ctx = mrc.Context()
+    idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, mrc.params_default(k=K, precision=2))
+    n_tok = c.n_tokens
+    del c
+    torch.cuda.empty_cache()
+    pool = synth.make_corpus_device(synth.SPECS["precision"].with_(n_docs=requests, seed=BASE_QUERY_SEED))
+    pool = pool.host_subset(np.arange(requests))
+    docs = [pool.doc(i) for i in range(pool.n_docs)]
+    srv = serving.Server(ctx, idx, TAU, micro_batch=128, deadline_s=1e-3, slots=4, max_doc_tokens=10000,
+                         capacity=1 << 21)
+    srv.run(docs[:1000], np.zeros(1000))  # warm-up
+    rows = []
+    for rate in rates:
+        arr = synth.poisson_arrivals(float(rate), requests)
+        reqs = srv.run(docs, arr)
+        rep = serving.latency_report(reqs, srv.wall_s)
+        rep["rate"] = rate
+        rep["pairs_per_request"] = float(np.mean([len(r.pairs) for r in reqs]))
+        rows.append(rep)
+    srv.free()
+    idx.free()
     ctx.close()
+    return {"index_docs": n_index, "index_tokens": n_tok, "micro_batch": 128, "deadline_ms": 1.0,
+            "slots": srv.admitted_slots, "requests_per_rate": requests, "rates": rows}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mrc", choices=["mrc", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="leave the serving leg out of the headline line")
+    ap.add_argument("--form", default="headline",
+                    choices=["headline", "precision", "batching", "serving", "features", "text", "study",
+                             "simhash_index", "forms"],
+                    help="headline (default): the million-document step and its legs; the others measure one form")
+    ap.add_argument("--batches", type=int, default=4096)
+    ap.add_argument("--serving-docs", type=int, default=10_000_000)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if args.form != "headline":
+        import torch
+        torch.cuda.set_device(local)
+        for f in (["precision", "batching", "serving"] if args.form == "forms" else [args.form]):
+            {"precision": form_precision, "batching": form_batching, "serving": form_serving,
+             "features": form_features, "text": form_text, "study": form_study,
+             "simhash_index": form_simhash_index}[f](args)
+        return
+
+    line, (c, ctx, stream, dist) = run_headline(args, rank, world, local)
+    if rank == 0:
+        # legs outside the timed regions: accuracy against FP64, the NEWS20-shaped step with the
+        # exact cosine, the serving form, the oracle's own speed
+        line["accuracy_vs_fp64"] = accuracy_vs_fp64(c, ctx)
+        ctx.close()
+        del c
+        import torch
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        line["news20"] = news20_leg(max(50, 5 * args.steps))
+        if world == 1 and not args.no_serving:
+            line["serving"] = serving_leg(args.serving_docs)
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_leg()
+        print(json.dumps(line), flush=True)
+    else:
+        ctx.close()
     if dist:
         dist.destroy_process_group()
 

@@ -156,8 +156,9 @@ mrc_status mrc_text_grams(mrc_ctx* ctx, int64_t n_docs, const int64_t* text_offs
 /*
  * Build a device-resident signature index over `corpus` (Sections III-IV):
  * term counts per document, document frequencies, idf (frozen for later
- * queries), reference selection and partitioning (a host-side sort of the
- * vocabulary by df inside this call), then every document's signature
+ * queries), reference selection and partitioning (REGION ranks the df band
+ * it needs on the device; ALL and DF1 rank the vocabulary on the host after
+ * one device-to-host copy of df), then every document's signature
  * s_p(d) = cos(v(d), v(R_p)) (Eq. 1 against partition p), its unit-length
  * packed form for comparison, and its 64-bit Simhash (Section III).
  * vocab: number of term ids. The returned index must be freed with
@@ -194,9 +195,11 @@ mrc_status mrc_signature(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* d
  * - at most MRC_NOALLOC_MAX_DOCS documents per call (more: MRC_ERR_INVALID);
  * - offsets, tokens, sig and simhash must all be device memory (it copies
  *   nothing; host pointers: MRC_ERR_INVALID);
- * - the first call on a device looks up the array's device address (one
- *   runtime call, which also loads the library's device code if it is not
- *   loaded yet); make that first call before any stream capture;
+ * - every call looks up the array's device address on the current device
+ *   (one runtime call; the first call on a device also loads the library's
+ *   device code there), so a device reset between calls is harmless;
+ * - it waits for its stream (list sizes, error word), so it cannot run while
+ *   that stream is being captured into a graph (MRC_ERR_UNSUPPORTED);
  * - all calls on a device share the array: calls whose work overlaps on the
  *   GPU (other streams, other host threads) race and must be serialised.
  * The call synchronises the context's stream.
@@ -210,9 +213,13 @@ mrc_status mrc_signature_noalloc(mrc_ctx* ctx, const mrc_index* index, const mrc
  * (the "multi reference cosine" of Eq. 2) >= tau. query_sig == NULL compares
  * all index pairs i < j; otherwise query_sig holds nq raw float32 signatures
  * ([nq * k], e.g. from mrc_signature) compared against every index document.
- * The index's precision decides the arithmetic (see MRC_PREC_*): in the
- * reduced-precision forms every candidate >= tau - margin is rescored in FP32
- * and kept iff its FP32 cosine >= tau.
+ * The index's precision decides the arithmetic (see MRC_PREC_*): the
+ * tensor-core compare finds candidates at a lowered threshold (tau - 2e-3 in
+ * the FP32 form, a proven bound; tau - margin in the reduced forms); each
+ * candidate is then rescored as the FP32 dot product of the two unit
+ * signatures and written iff that score >= tau (score = that FP32 cosine).
+ * With rescoring turned off on the context (mrc_ctx_set_rescoring) the
+ * candidates themselves are written, scored with the compare's own cosine.
  */
 mrc_status mrc_match(mrc_ctx* ctx, const mrc_index* index, const float* query_sig, int64_t nq, float tau,
                      mrc_pair* pairs, int64_t capacity, int64_t* n_pairs);
@@ -220,9 +227,14 @@ mrc_status mrc_match(mrc_ctx* ctx, const mrc_index* index, const float* query_si
 /*
  * Exact cosine (Eq. 1) of the weighted term vectors of every pair i < j of
  * `docs` (the ground truth of Section V), emitting pairs with cosine >= tau.
- * Weights use the index's idf and weighting. FP32-accurate: frequent terms go
- * through a tensor-core GEMM in fp16 hi/lo split arithmetic, the remaining
- * terms through sparse postings, summed before the threshold.
+ * Weights use the index's idf and weighting. FP32-accurate: the most frequent
+ * terms form a dense fp16 head operand; every other term is hashed into one of
+ * 256 buckets whose per-document norms ride as extra columns, so one
+ * tensor-core GEMM gives head score + a Cauchy-Schwarz bound of the rest.
+ * Pairs whose bound reaches tau minus the proven rounding slack are rescored
+ * exactly (the head from its split rows, the rest by a hash join of the two
+ * documents' term lists) and kept iff >= tau. If the candidates overflow their
+ * buffer, the call falls back to an exhaustive sparse walk.
  */
 mrc_status cosine_allpairs(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float tau,
                            mrc_pair* pairs, int64_t capacity, int64_t* n_pairs);
@@ -244,10 +256,11 @@ mrc_status simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint
  * the caller reads *d_n_pairs and compares. Inputs may be host or device memory
  * as everywhere; a host input is copied before the call returns.
  * Device-side errors (a bounded wait that expired, a candidate buffer that
- * overflowed -- the reduced-precision forms first collect candidates in a
- * buffer of max(4 * capacity, 2^20) entries, which the synchronous form grows
- * and repeats on overflow) are recorded in the context and returned by the
- * next mrc_ctx_sync. cosine_allpairs_async waits for nothing unless per-kernel
+ * overflowed -- mrc_match collects its candidates in a buffer of
+ * max(4 * capacity, 2^20) entries, which the synchronous form grows and
+ * repeats on overflow; the exact cosine's buffer holds max(4 * capacity,
+ * 2^22), and its synchronous form falls back to an exhaustive path) are
+ * recorded in the context and returned by the next mrc_ctx_sync. cosine_allpairs_async waits for nothing unless per-kernel
  * timing is on (it then reads its head/tail split's sizes once).
  * Host-side argument errors return at once, as in the synchronous forms.
  *
@@ -270,7 +283,8 @@ mrc_status mrc_ctx_sync(mrc_ctx* ctx);
  * database (Section I, Section IV); a batch does that for up to max_docs new
  * documents at once against every document of `index`: signature pass,
  * tensor-core compare at a lowered threshold (tau - 2e-3 in the FP32 form, a
- * proven bound; tau - margin in the reduced forms), FP32 rescoring. Pairs are
+ * proven bound; tau - margin in the reduced forms), FP32 rescoring, grouping
+ * of the pairs by query. Pairs are
  * (query position i in the batch, index document j).
  *   mrc_batch_create : allocates the pipeline's device buffers (inputs, outputs,
  *     workspace) and its own non-blocking stream, runs the pipeline once and
@@ -309,7 +323,10 @@ void mrc_batch_free(mrc_batch* batch);
  * Build: fps [n] uint64 (device or host; copied into the index), n < 2^31,
  * 0 <= hamming_max <= 15 (the largest distance later searches may ask for).
  * The index holds 12 * b * n bytes plus the bucket offsets; free it with
- * mrc_simhash_index_free (ordered on the building context's stream).
+ * mrc_simhash_index_free (ordered on the building context's stream). Every
+ * match call returns only after its probe has finished (it synchronises its
+ * stream to read the pair count), so freeing the index after the match calls
+ * that use it have returned is safe, whichever contexts they ran on.
  * Match: queries [nq] (device or host) x the index, pairs (q, x); queries ==
  * NULL: all pairs i < j of the index itself. hamming_max <= the build's.
  * Pairs, capacity and *n_pairs as simhash_match. Errors: MRC_ERR_INVALID for
@@ -338,6 +355,48 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out);
 /* Release an index. Its memory is returned in order on the stream of the context that
  * built (or loaded) it, so that stream must still exist. */
 void mrc_index_free(mrc_index* index);
+
+/*
+ * Bound of every device-side wait of the context's kernels (the pipeline
+ * barriers of the tensor-core compares), in nanoseconds; default 4 s. Not in
+ * the paper: failure detection of this library. A wait that runs out stops
+ * its kernel early (after the kernel's own copies and tensor-core operations
+ * in flight have landed and its tensor memory is freed); the call then returns
+ * MRC_ERR_TIMEOUT (stream-ordered calls: at mrc_ctx_sync) and the context
+ * stays usable. 1 <= ns <= 600e9, else MRC_ERR_INVALID. Applies to calls made
+ * after it returns.
+ */
+mrc_status mrc_ctx_set_wait_limit(mrc_ctx* ctx, int64_t ns);
+
+/*
+ * Test of the bounded waits (failure detection; not in the paper). With
+ * on != 0, the tensor-core compare kernels this context launches issue no
+ * tensor-core operation, so the waits of their other roles for those results
+ * are never met and run out after the wait limit: the call returns
+ * MRC_ERR_TIMEOUT without hanging or faulting the GPU. Off by default; turn it
+ * off again before normal use.
+ */
+mrc_status mrc_ctx_set_test_stall(mrc_ctx* ctx, int32_t on);
+
+/*
+ * Diagnostics of the reduced-precision forms (not in the paper). With on == 0,
+ * mrc_match (and mrc_match_async) write the tensor-core compare's candidates
+ * -- every pair whose compare cosine is >= tau - 2e-3 (FP32 form) or
+ * tau - margin (reduced forms) -- scored with that cosine (fp16: the product
+ * of the fp16 unit signatures; E4M3: the cosine of the quantized vectors),
+ * without FP32 rescoring. Default on.
+ */
+mrc_status mrc_ctx_set_rescoring(mrc_ctx* ctx, int32_t on);
+
+/*
+ * Measurement helper (not in the paper): the rate at which ctx's device issues
+ * 32-bit population counts, in POPC per second, from a probe kernel that keeps
+ * eight independent XOR + POPC + add chains per thread in flight (best of three
+ * timed runs after one warm-up). simhash_match evaluates one XOR and one POPC
+ * per pair on the fingerprints' low halves, so this rate bounds its pairs/s.
+ * Synchronises ctx's stream.
+ */
+mrc_status mrc_measure_popc_rate(mrc_ctx* ctx, double* popc_per_s);
 
 /*
  * Per-kernel timing. With timing on, every kernel the context launches is

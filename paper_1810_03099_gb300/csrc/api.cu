@@ -928,6 +928,14 @@ static mrc_status match_impl(mrc_ctx* ctx, const mrc_index* index, const float* 
     g.b_norm_min = index->qnorm_min;
   }
   g.thresh = tau - (prec == MRC_PREC_FP32 ? kF16CompareBound : index->params.margin);
+  if (!ctx->rescore) {  // diagnostics: the compare's candidates are the result
+    g.pairs = dst;
+    g.count = pc;
+    g.capacity = capacity;
+    cudaError_t e = launch_gemm_compare(ctx, g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "signature compare");
+    return async ? MRC_OK : finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs, d_err);
+  }
   // candidates, then their rescoring (which reads the candidate count on the device), then one
   // synchronisation; only if the candidate buffer overflowed is the pass repeated, larger
   int64_t cand_cap = std::max<int64_t>(4 * capacity, 1 << 20);
@@ -1312,7 +1320,8 @@ mrc_status mrc_simhash_index_match(mrc_ctx* ctx, const mrc_simhash_index* index,
   unsigned long long* d_count = (unsigned long long*)ws_get(ctx, "shx.count", sizeof(unsigned long long), &st);
   mrc_pair* dst = pair_dest(ctx, pairs, capacity, &st);
   if (st != MRC_OK) return st;
-  cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), ctx->stream);
+  cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "clearing the pair count");
   const bool all = queries == nullptr;  // all pairs: the index's own fingerprints are the queries
   const uint64_t* dq = index->own;
   const int64_t m = all ? index->n : nq;
@@ -1320,7 +1329,7 @@ mrc_status mrc_simhash_index_match(mrc_ctx* ctx, const mrc_simhash_index* index,
     dq = (const uint64_t*)stage_in(ctx, "shx.q", queries, sizeof(uint64_t) * (size_t)nq, &st);
     if (st != MRC_OK) return st;
   }
-  cudaError_t e = launch_simhash_index_probe(ctx, dq, m, all, hamming_max, index->layout, index->n, index->fp,
+  e = launch_simhash_index_probe(ctx, dq, m, all, hamming_max, index->layout, index->n, index->fp,
                                              index->id, index->off, dst, d_count, capacity);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fingerprint index probe");
   return finish_pairs(ctx, pairs, dst, d_count, capacity, n_pairs);
@@ -1538,6 +1547,32 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
   mark_index_tables(ctx, x);
   mark_index_ready(ctx, x);
   *out = x;
+  return MRC_OK;
+}
+
+mrc_status mrc_ctx_set_wait_limit(mrc_ctx* ctx, int64_t ns) {
+  if (!ctx) return MRC_ERR_INVALID;
+  if (ns < 1 || ns > 600000000000ll) return fail(ctx, MRC_ERR_INVALID, "wait limit outside [1 ns, 600 s]");
+  ctx->wait_limit_ns = (uint64_t)ns;
+  return MRC_OK;
+}
+
+mrc_status mrc_measure_popc_rate(mrc_ctx* ctx, double* popc_per_s) {
+  if (!ctx || !popc_per_s) return MRC_ERR_INVALID;
+  Scope scope(ctx);
+  const cudaError_t e = measure_popc_rate(ctx, popc_per_s);
+  return e == cudaSuccess ? MRC_OK : cuda_fail(ctx, e, "POPC rate probe");
+}
+
+mrc_status mrc_ctx_set_rescoring(mrc_ctx* ctx, int32_t on) {
+  if (!ctx) return MRC_ERR_INVALID;
+  ctx->rescore = on != 0;
+  return MRC_OK;
+}
+
+mrc_status mrc_ctx_set_test_stall(mrc_ctx* ctx, int32_t on) {
+  if (!ctx) return MRC_ERR_INVALID;
+  ctx->test_stall = on != 0;
   return MRC_OK;
 }
 

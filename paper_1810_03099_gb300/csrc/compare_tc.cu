@@ -38,7 +38,10 @@ namespace {
 constexpr int kBM = 128;
 constexpr int kThreads = 192;
 constexpr int kRowBytes = 128;  // K bytes per stage per row (one 128B swizzle atom)
-constexpr uint64_t kTimeoutNs = 4000000000ull;
+// After a role gives up, the CTA still waits for its own TMA copies and MMAs in flight before it
+// frees TMEM and exits. They complete in microseconds; the bound only keeps a broken invariant
+// from spinning forever (it is then reported as a timeout too).
+constexpr uint64_t kDrainNs = 2000000000ull;
 constexpr int kPairBuf = 64;  // pairs buffered per epilogue warp before one global atomic
 constexpr float kNormLo = 0.93f;  // lower bound of |e4m3(x * 256)| / 256 for unit x (1 - 2^-4 = 0.9375)
 
@@ -75,6 +78,9 @@ struct GemmParams {
   int32_t* err;
   int32_t row_rr;  // resident kernel, triangle: whole row blocks dealt round-robin (see TileSeq)
   const int32_t* kblocks_dev;  // streaming kernel: K blocks read from the device (see GemmArgs)
+  uint64_t timeout_ns;         // bound of every pipeline wait (the context's wait limit)
+  int32_t stall;               // failure-detection test: the MMA issuer issues nothing, so the
+                               // other roles' waits for its results run out (mrc_ctx_set_test_stall)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -96,7 +102,8 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait: false on abort (another role gave up) or timeout (records it).
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort, int32_t* err) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort, int32_t* err,
+                                          uint64_t timeout_ns) {
   if (mbar_try(b, parity)) return true;
   const uint64_t t0 = gtime();
   while (true) {
@@ -104,10 +111,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
     for (int i = 0; i < 32; ++i)
       if (mbar_try(b, parity)) return true;
     if (*abort) return false;
-    if (gtime() - t0 > kTimeoutNs) {
+    if (gtime() - t0 > timeout_ns) {
       *abort = 1;
       set_err(err, kErrTimeout);
       return false;
+    }
+  }
+}
+// Drain wait of the abort path: the copy or MMA behind the barrier was issued and completes on
+// its own; the bound is a safeguard only.
+__device__ __forceinline__ void mbar_drain(uint64_t* b, uint32_t parity, int32_t* err) {
+  const uint64_t t0 = gtime();
+  while (!mbar_try(b, parity)) {
+    if (gtime() - t0 > kDrainNs) {
+      set_err(err, kErrTimeout);
+      return;
     }
   }
 }
@@ -205,6 +223,23 @@ __device__ __forceinline__ bool decode_tile(const GemmParams& p, int64_t t64, in
   return bi * kBM < p.na;
 }
 
+// Three-input maximum (one instruction on sm_100 and later).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+// Maximum of 32 registers as a tree of three-input maxima: 15 instructions, 4 levels deep, so
+// the chains of several chunks overlap instead of waiting on one 31-step dependency chain.
+__device__ __forceinline__ float max32(const float (&v)[32]) {
+  float a[11];
+#pragma unroll
+  for (int e = 0; e < 10; ++e) a[e] = fmax3(v[3 * e], v[3 * e + 1], v[3 * e + 2]);
+  a[10] = fmaxf(v[30], v[31]);
+  const float b0 = fmax3(a[0], a[1], a[2]), b1 = fmax3(a[3], a[4], a[5]), b2 = fmax3(a[6], a[7], a[8]);
+  return fmax3(fmax3(a[9], a[10], b0), b1, b2);
+}
+
 // Writes a warp's buffered pairs (nbuf of them, in buf) to the global list with one atomic.
 __device__ __forceinline__ void flush_pairs(const GemmParams& p, const mrc_pair* buf, int& nbuf, int lane) {
   if (nbuf == 0) return;
@@ -218,20 +253,19 @@ __device__ __forceinline__ void flush_pairs(const GemmParams& p, const mrc_pair*
 }
 
 // Threshold one 32-column chunk held in registers (v[e] = score of column j0 + e for this
-// lane's row i) and append its candidate pairs. Fast path: the chunk's maximum misses
-// fast_thresh in every lane. Otherwise each lane builds the 32-bit mask of its hits straight
-// from its registers (a hit: v[e] >= hit_lim; E4M3: v[e] >= hit_lim * |q_j|, the column norms
-// staged once per warp, zero norms never hitting), applies the bounds and the triangle's j > i
-// with bit arithmetic, and the warp appends its hits to its pair buffer. Every caller rescores
-// its candidates (FP32 rescoring, exact-cosine verification), so a pair carries only the lane's
-// chunk maximum, an upper bound of its raw score.
+// lane's row i) and append its pairs. Fast path: the chunk's maximum misses fast_thresh in
+// every lane. Otherwise each lane builds the 32-bit mask of its hits straight from its
+// registers (a hit: v[e] >= hit_lim; E4M3: v[e] >= hit_lim * |q_j|, the column norms staged
+// once per warp, zero norms never hitting), applies the bounds and the triangle's j > i with
+// bit arithmetic, and scores each hit with the compare's own cosine (fp16: the accumulator;
+// E4M3: the cosine of the quantized vectors), staged in this lane's row of the warp's 32 x 33
+// area. The warp then appends its hits to its pair buffer. Callers that need FP32 scores
+// rescore these candidates.
 template <int FMT>
 __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)[32], int64_t i, int64_t j0, int lane,
                                            float fast_thresh, float row_norm, float hit_lim, float* nstage,
-                                           mrc_pair* buf, int& nbuf) {
-  float m = v[0];
-#pragma unroll
-  for (int e = 1; e < 32; ++e) m = fmaxf(m, v[e]);
+                                           float* stage, mrc_pair* buf, int& nbuf) {
+  const float m = max32(v);
   if (!__any_sync(kFull, m >= fast_thresh)) return;
   uint32_t mask = 0;
   if (FMT == OP_E4M3) {
@@ -255,6 +289,11 @@ __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)
   }
   if (i >= p.na) mask = 0u;
   const uint32_t hits = mask;
+  float* sc = stage + lane * 33;  // the raw scores, for the emission loop's per-hit index
+  if (hits) {
+#pragma unroll
+    for (int e = 0; e < 32; ++e) sc[e] = v[e];
+  }
   const int cnt = __popc(hits);
   int incl = cnt;
 #pragma unroll
@@ -279,7 +318,7 @@ __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)
       mrc_pair pr;
       pr.i = (int32_t)i;
       pr.j = (int32_t)(j0 + e);
-      pr.score = m;
+      pr.score = FMT == OP_E4M3 ? sc[e] * p.out_scale / (row_norm * nstage[e]) : sc[e];
       if (!direct)
         buf[nbuf + at] = pr;
       else if (base + at < (unsigned long long)p.capacity)
@@ -352,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int64_t bi, bj;
         if (!decode_tile<BN>(p, t, bi, bj)) continue;
         for (int kb = 0; kb < kblocks; ++kb) {
-          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.err)) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.err, p.timeout_ns)) {
             ok = false;
             break;
           }
@@ -375,14 +414,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       // drain: the last copy armed on each stage lands before the CTA may exit
       for (int s = 0; s < C::STAGES; ++s) {
         if (armed[s] < 0) continue;
-        const uint64_t t0 = gtime();
-        while (!mbar_try(&full[s], (uint32_t)armed[s]) && gtime() - t0 < 100000000ull) {
-        }
+        mbar_drain(&full[s], (uint32_t)armed[s], p.err);
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    if (lane == 0 && !p.stall) {
       uint32_t stage = 0, phase = 0;
       int64_t it = 0;
       bool ok = true;
@@ -391,12 +428,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         int64_t bi, bj;
         if (!decode_tile<BN>(p, t, bi, bj)) continue;
         const uint32_t ab = (uint32_t)(it & 1);
-        if (!mbar_wait(&acc_empty[ab], (uint32_t)((it >> 1) & 1) ^ 1u, abort_flag, p.err)) break;
+        if (!mbar_wait(&acc_empty[ab], (uint32_t)((it >> 1) & 1) ^ 1u, abort_flag, p.err, p.timeout_ns)) break;
         tc_fence_after();
         const uint32_t d0 = tmem + ab * 256u;
         const uint32_t d1 = d0 + 128u;
         for (int kb = 0; kb < kblocks; ++kb) {
-          if (!mbar_wait(&full[stage], phase, abort_flag, p.err)) {
+          if (!mbar_wait(&full[stage], phase, abort_flag, p.err, p.timeout_ns)) {
             ok = false;
             break;
           }
@@ -426,9 +463,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // wait for every MMA issued so far before TMEM can be released
       umma_commit(drain);
-      const uint64_t t0 = gtime();
-      while (!mbar_try(drain, 0) && gtime() - t0 < 100000000ull) {
-      }
+      mbar_drain(drain, 0, p.err);
     }
   } else {
     // ------------------------------------------------------------ epilogue
@@ -439,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!decode_tile<BN>(p, t, bi, bj)) continue;
       const uint32_t ab = (uint32_t)(it & 1);
       int ok = 1;
-      if (lane == 0) ok = mbar_wait(&acc_full[ab], (uint32_t)((it >> 1) & 1), abort_flag, p.err) ? 1 : 0;
+      if (lane == 0) ok = mbar_wait(&acc_full[ab], (uint32_t)((it >> 1) & 1), abort_flag, p.err, p.timeout_ns) ? 1 : 0;
       ok = __shfl_sync(kFull, ok, 0);
       if (!ok) break;
       tc_fence_after();
@@ -506,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         } else {
-          emit_chunk<FMT>(p, v, i, j0, lane, fast_thresh, row_norm, hit_lim, nstage, pbuf, nbuf);
+          emit_chunk<FMT>(p, v, i, j0, lane, fast_thresh, row_norm, hit_lim, nstage, stage, pbuf, nbuf);
         }
       }
       tc_fence_before();
@@ -531,7 +566,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 // loaded once per row block into one of two resident buffers and only B streams through
 // a 4-stage ring. Eight epilogue warps (two per TMEM lane quarter) split the columns.
 constexpr int kResThreads = 320;  // warp 0 TMA, warp 1 MMA + TMEM, warps 2..9 epilogue
-constexpr int kResStagesB = 4;
+// Depth of the streamed-B ring: as many stages as shared memory holds next to the two A
+// buffers and the epilogue's staging. The B tiles come from L2 with a latency of about
+// a microsecond, so a CTA needs that many bytes in flight to stream at the rate its tensor core
+// consumes them (E4M3 tiles are half the size of fp16 ones and go by twice as fast). 3 to 12.
+constexpr size_t kResEpiBytes = 8 * (32 * 33 + 32) * sizeof(float) + 8 * kPairBuf * sizeof(mrc_pair);
+__host__ __device__ constexpr int res_stages_b(int nops, int rb, int bn) {
+  return (int)(((227u * 1024u - 1024u - kResEpiBytes - 512u) - 2u * nops * kBM * rb) / ((size_t)nops * bn * rb)) > 12
+             ? 12
+             : (int)(((227u * 1024u - 1024u - kResEpiBytes - 512u) - 2u * nops * kBM * rb) / ((size_t)nops * bn * rb));
+}
 
 // 64-byte-swizzle descriptor (8-row groups 512 bytes apart) or the 128-byte one.
 template <int RB>
@@ -629,6 +673,8 @@ __global__ void __launch_bounds__(kResThreads, 1)
   static_assert(NB >= 2 && NB <= 4, "two to four accumulator buffers");
   constexpr uint32_t A_BYTES = kBM * RB, B_BYTES = BN * RB;
   constexpr uint32_t A_STAGE = C::NOPS * A_BYTES, B_STAGE = C::NOPS * B_BYTES;
+  constexpr int kResStagesB = res_stages_b(C::NOPS, RB, BN);
+  static_assert(kResStagesB >= 3, "at least three B stages");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* abuf = smem;                    // [2][A_STAGE]
@@ -693,7 +739,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
       while (seq.next(p, bi, bj)) {
         if (bi != last_bi) {
           const uint32_t ab = a_use & 1u;
-          if (!mbar_wait(&a_empty[ab], ((a_use >> 1) & 1u) ^ 1u, abort_flag, p.err)) break;
+          if (!mbar_wait(&a_empty[ab], ((a_use >> 1) & 1u) ^ 1u, abort_flag, p.err, p.timeout_ns)) break;
           mbar_expect_tx(&a_full[ab], A_STAGE);
           a_armed[ab] = (int32_t)((a_use >> 1) & 1u);
           uint8_t* dst = abuf + ab * A_STAGE;
@@ -702,7 +748,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
           last_bi = bi;
           ++a_use;
         }
-        if (!mbar_wait(&b_empty[stage], phase ^ 1u, abort_flag, p.err)) break;
+        if (!mbar_wait(&b_empty[stage], phase ^ 1u, abort_flag, p.err, p.timeout_ns)) break;
         mbar_expect_tx(&b_full[stage], B_STAGE);
         b_armed[stage] = (int32_t)phase;
         uint8_t* dst = bbuf + stage * B_STAGE;
@@ -716,19 +762,15 @@ __global__ void __launch_bounds__(kResThreads, 1)
       // drain: every armed copy lands before the CTA may exit
       for (int b = 0; b < 2; ++b) {
         if (a_armed[b] < 0) continue;
-        const uint64_t t0 = gtime();
-        while (!mbar_try(&a_full[b], (uint32_t)a_armed[b]) && gtime() - t0 < 100000000ull) {
-        }
+        mbar_drain(&a_full[b], (uint32_t)a_armed[b], p.err);
       }
       for (int s = 0; s < kResStagesB; ++s) {
         if (b_armed[s] < 0) continue;
-        const uint64_t t0 = gtime();
-        while (!mbar_try(&b_full[s], (uint32_t)b_armed[s]) && gtime() - t0 < 100000000ull) {
-        }
+        mbar_drain(&b_full[s], (uint32_t)b_armed[s], p.err);
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && !p.stall) {
       // ------------------------------------------------------------ MMA issuer
       const uint32_t id = idesc(BN);
       uint32_t stage = 0, phase = 0, a_use = 0, ab_a = 0;
@@ -739,13 +781,13 @@ __global__ void __launch_bounds__(kResThreads, 1)
         if (bi != last_bi) {
           if (last_bi >= 0) umma_commit(&a_empty[ab_a]);  // previous row's MMAs release its A buffer
           ab_a = a_use & 1u;
-          if (!mbar_wait(&a_full[ab_a], (a_use >> 1) & 1u, abort_flag, p.err)) break;
+          if (!mbar_wait(&a_full[ab_a], (a_use >> 1) & 1u, abort_flag, p.err, p.timeout_ns)) break;
           last_bi = bi;
           ++a_use;
         }
         const uint32_t ab = (uint32_t)(it % NB);
-        if (!mbar_wait(&acc_empty[ab], (uint32_t)((it / NB) & 1) ^ 1u, abort_flag, p.err)) break;
-        if (!mbar_wait(&b_full[stage], phase, abort_flag, p.err)) break;
+        if (!mbar_wait(&acc_empty[ab], (uint32_t)((it / NB) & 1) ^ 1u, abort_flag, p.err, p.timeout_ns)) break;
+        if (!mbar_wait(&b_full[stage], phase, abort_flag, p.err, p.timeout_ns)) break;
         tc_fence_after();
         const uint32_t d0 = tmem + ab * (uint32_t)(C::ACCS * BN), d1 = d0 + (uint32_t)BN;
         const uint32_t sa = smem_u32(abuf + ab_a * A_STAGE), sb = smem_u32(bbuf + stage * B_STAGE);
@@ -770,9 +812,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
         ++it;
       }
       umma_commit(drain);
-      const uint64_t t0 = gtime();
-      while (!mbar_try(drain, 0) && gtime() - t0 < 100000000ull) {
-      }
+      mbar_drain(drain, 0, p.err);
     }
   } else {
     // ------------------------------------------------------------ epilogue (8 warps)
@@ -784,7 +824,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
     while (seq.next(p, bi, bj)) {
       const uint32_t ab = (uint32_t)(it % NB);
       int ok = 1;
-      if (lane == 0) ok = mbar_wait(&acc_full[ab], (uint32_t)((it / NB) & 1), abort_flag, p.err) ? 1 : 0;
+      if (lane == 0) ok = mbar_wait(&acc_full[ab], (uint32_t)((it / NB) & 1), abort_flag, p.err, p.timeout_ns) ? 1 : 0;
       ok = __shfl_sync(kFull, ok, 0);
       if (!ok) break;
       tc_fence_after();
@@ -826,12 +866,20 @@ __global__ void __launch_bounds__(kResThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[ab]);
+      // a warp's columns lie in one 128-column block (half 0: the first, half 1: the second), so one
+      // fast threshold covers all its chunks; the usual case, no lane near it in any chunk, costs
+      // the maxima (a tree of three-input maxima per chunk) and one vote
+      float fast_thresh = row_bound;
+      if (FMT == OP_E4M3 && p.thresh > 0.f) fast_thresh = row_bound * ((((half * CH) * 32) >> 7) ? nmin1 : nmin0);
+      float mall = max32(v[0]);
 #pragma unroll
-      for (int c = 0; c < CH; ++c) {
-        const int64_t j0 = bj * BN + (half * CH + c) * 32;
-        float fast_thresh = row_bound;
-        if (FMT == OP_E4M3 && p.thresh > 0.f) fast_thresh = row_bound * ((((half * CH + c) * 32) >> 7) ? nmin1 : nmin0);
-        emit_chunk<FMT>(p, v[c], i, j0, lane, fast_thresh, row_norm, hit_lim, nstage, pbuf, nbuf);
+      for (int c = 1; c < CH; ++c) mall = fmaxf(mall, max32(v[c]));
+      if (__any_sync(kFull, mall >= fast_thresh)) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          const int64_t j0 = bj * BN + (half * CH + c) * 32;
+          emit_chunk<FMT>(p, v[c], i, j0, lane, fast_thresh, row_norm, hit_lim, nstage, stage, pbuf, nbuf);
+        }
       }
       ++it;
     }
@@ -911,15 +959,18 @@ cudaError_t run_gemm_resident(mrc_ctx* ctx, const GemmArgs& g) {
   p.count = g.count;
   p.capacity = g.capacity;
   p.err = g.err;
+  p.timeout_ns = ctx->wait_limit_ns;
+  p.stall = ctx->test_stall ? 1 : 0;
   // round-robin rows whenever there are at least two rounds of row blocks to balance: the CTAs
   // then share each streamed tile through L2 even when the operand would fit there (300,000
   // documents, 19 MB of E4M3 rows: 15.2 -> 11.5 ms)
   p.row_rr = g.triangle && p.tiles_m >= 2 * (int64_t)ctx->num_sms;
   // at least 120 KB, so that one CTA (which owns all 512 TMEM columns) runs per SM
-  const size_t smem =
-      std::max<size_t>(1024 + 2 * (size_t)C::NOPS * kBM * RB + (size_t)kResStagesB * C::NOPS * BN * RB + 256 +
-                           8 * (32 * 33 + 32) * sizeof(float) + 8 * kPairBuf * sizeof(mrc_pair),
-                       120 * 1024);
+  constexpr int NBUF = 512 / (C::ACCS * BN);
+  constexpr int SB = res_stages_b(C::NOPS, RB, BN);
+  const size_t smem = std::max<size_t>(1024 + 2 * (size_t)C::NOPS * kBM * RB + (size_t)SB * C::NOPS * BN * RB +
+                                           (size_t)(8 + 2 * SB + 2 * NBUF) * 8 + kResEpiBytes,
+                                       120 * 1024);
   if (resident_ctas(k_gemm_resident<FMT, RB, BN>, kResThreads, smem) <= 0) return cudaErrorInvalidConfiguration;
   int64_t grid = ctx->num_sms;
   if (p.n_tiles < grid) grid = p.n_tiles;
@@ -975,6 +1026,8 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   p.ld = g.ld;
   p.err = g.err;
   p.kblocks_dev = g.kblocks_dev;
+  p.timeout_ns = ctx->wait_limit_ns;
+  p.stall = ctx->test_stall ? 1 : 0;
   const size_t smem = 1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256 + 4 * (32 * 33 + 32) * 4 +
                       4 * kPairBuf * sizeof(mrc_pair);
   if (resident_ctas(k_gemm_compare<FMT>, kThreads, smem) <= 0) return cudaErrorInvalidConfiguration;

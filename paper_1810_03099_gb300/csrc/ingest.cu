@@ -40,11 +40,14 @@ namespace {
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr int kShortMax = 512;      // documents up to this length take the warp path
 constexpr int kShortSlots = 1024;   // per-warp table (load <= 1/2)
-constexpr int kWarpsShort = 8;      // warps per CTA in the warp path
-constexpr int kShortRegs = kShortMax / 32;  // tokens per lane held in registers (warp path)
-constexpr int kLongThreads = 512;   // CTA size of the long-document path
-constexpr int kLongSlots = 8192;    // per-CTA table: documents with > 4096 tokens take several passes
-constexpr int kLongUnroll = 4;      // token loads per thread in flight (CTA path)
+constexpr int kWarpsShort = 7;      // warps per CTA in the warp path (three CTAs per SM)
+constexpr int kShortRegs = kShortMax / 32;  // tokens (then terms) per lane held in registers (warp path)
+constexpr int kGroupWarps = 4;      // warps per document group of the long-document path
+constexpr int kGroupThreads = kGroupWarps * 32;
+constexpr int kGroupsLong = 5;      // groups per CTA (one CTA per SM: five tables fill shared memory)
+constexpr int kLongThreads = kGroupsLong * kGroupThreads;
+constexpr int kLongSlots = 4096;    // per-group table: documents with > 2048 tokens take several passes
+constexpr int kLongUnroll = 4;      // token loads per thread in flight (long-document path)
 constexpr float kFix = 4194304.0f;  // 2^22
 constexpr float kInvFix = 1.0f / 4194304.0f;
 
@@ -154,19 +157,35 @@ __device__ uint64_t sha1_feature(uint32_t t, uint64_t seed) {
   return (uint64_t)bswap32(0x67452301u + a) | ((uint64_t)bswap32(0xEFCDAB89u + b) << 32);
 }
 
-// 32x32 bit-matrix transpose across a warp: on entry lane r holds row r
-// (bit c = element (r, c)); on exit lane r holds column r of the input.
-__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
-  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+// 32x32 bit-matrix transpose across a warp: on entry lane r holds row r (bit c = element
+// (r, c)); on exit lane r holds column r of the input. Five exchange steps of distance
+// s = 16, 8, 4, 2, 1: the lane whose bit s is clear keeps the bits of mask m_s and takes its
+// partner's other bits shifted up by s; the other lane keeps ~m_s and takes its partner's bits
+// shifted down. Both shifts are one rotation (by s or 32 - s; the bits that wrap around fall
+// outside the taken mask), so a step is a shuffle, a funnel rotation and one three-input
+// logic operation with per-lane constants computed once.
+struct Transposer {
+  uint32_t keep[5], rot[5];
+  __device__ __forceinline__ explicit Transposer(int lane) {
+    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const int s = 16 >> i;
-    const uint32_t m = masks[i];
-    const uint32_t y = __shfl_xor_sync(kFull, x, s);
-    x = (lane & s) ? ((x & ~m) | ((y & ~m) >> s)) : ((x & m) | ((y & m) << s));
+    for (int i = 0; i < 5; ++i) {
+      const uint32_t st = 16u >> i;
+      const bool up = (lane & st) != 0;
+      keep[i] = up ? ~masks[i] : masks[i];
+      rot[i] = up ? 32u - st : st;
+    }
   }
-  return x;
-}
+  __device__ __forceinline__ uint32_t operator()(uint32_t x) const {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const uint32_t y = __shfl_xor_sync(kFull, x, 16 >> i);
+      const uint32_t t = __funnelshift_l(y, y, rot[i]);
+      x = (x & keep[i]) | (t & ~keep[i]);
+    }
+    return x;
+  }
+};
 
 __device__ __forceinline__ unsigned long long to_fix(float x) { return __float2ull_rn(x * kFix); }
 
@@ -180,32 +199,50 @@ __device__ __forceinline__ float inv_norm_of(unsigned long long norm_q) {
   return n2 > 0.f ? 1.0f / sqrtf(n2) : 0.f;
 }
 
-// Inserts up to B terms (those whose bit is set in pend) with all of a round's
-// compare-and-swaps in flight: each round tries every pending term at its current probe
-// slot; a term is placed when its slot was empty or already holds it, otherwise it moves to
-// the next slot. Linear probing from the same start slot keeps the table consistent under
-// concurrent inserts (slots are never emptied). Returns false if a term found no slot.
+// Open-addressing table of a document's bag of terms: 64-bit slots, term id in the high word
+// and its count in the low word (kEmpty64: free). Inserts up to B tokens per lane (those whose
+// bit is set in pend) with all of a round's compare-and-swaps in flight: a token whose slot is
+// free claims it with count 1; a token that finds its own term adds 1 to the slot; otherwise
+// it moves to the next slot (linear probing from the same start slot keeps concurrent inserts
+// consistent, and slots are never freed). A token that claimed a slot is its term's first
+// occurrence in the document: the slot goes to the document's list of occupied slots (one
+// shared-memory counter, so later passes walk only occupied slots) and, with df, the term's
+// document frequency gets its 1. Returns false if a term found no slot.
+constexpr unsigned long long kEmpty64 = 0xFFFFFFFF00000000ull;
 template <int B>
-__device__ __forceinline__ bool table_insert_batch(uint32_t* keys, uint32_t* cnts, int log2ts, const int32_t (&tk)[B],
-                                                   uint32_t pend) {
+__device__ __forceinline__ bool insert_batch(unsigned long long* tab, uint16_t* list, int32_t* list_n, int log2ts,
+                                             const int32_t (&tk)[B], uint32_t pend, int32_t* df) {
   const uint32_t mask = (1u << log2ts) - 1u;
   uint32_t slot[B];
 #pragma unroll
   for (int u = 0; u < B; ++u) slot[u] = slot_of((uint32_t)tk[u], log2ts);
+  uint32_t fresh = 0u;
   for (uint32_t round = 0; pend != 0u && round <= mask; ++round) {
-    uint32_t prev[B];
+    unsigned long long prev[B];
 #pragma unroll
     for (int u = 0; u < B; ++u)
-      if ((pend >> u) & 1u) prev[u] = atomicCAS(&keys[slot[u]], kEmpty, (uint32_t)tk[u]);
+      if ((pend >> u) & 1u) prev[u] = atomicCAS(&tab[slot[u]], kEmpty64, ((unsigned long long)(uint32_t)tk[u] << 32) | 1ull);
 #pragma unroll
     for (int u = 0; u < B; ++u)
       if ((pend >> u) & 1u) {
-        if (prev[u] == kEmpty || prev[u] == (uint32_t)tk[u]) {
-          atomicAdd(&cnts[slot[u]], 1u);
+        if (prev[u] == kEmpty64) {
+          fresh |= 1u << u;
+          pend &= ~(1u << u);
+        } else if ((uint32_t)(prev[u] >> 32) == (uint32_t)tk[u]) {
+          atomicAdd(&tab[slot[u]], 1ull);
           pend &= ~(1u << u);
         } else {
           slot[u] = (slot[u] + 1u) & mask;
         }
+      }
+  }
+  if (fresh) {
+    int at = atomicAdd(list_n, __popc(fresh));
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if ((fresh >> u) & 1u) {
+        list[at++] = (uint16_t)slot[u];
+        if (df) atomicAdd(&df[tk[u]], 1);
       }
   }
   return pend == 0u;
@@ -302,13 +339,13 @@ __device__ __forceinline__ TermAux load_aux(const IngestParams& p, uint32_t key)
 
 // The work of one warp-chunk of 32 terms (key == kEmpty: no term in this lane).
 template <int MODE>
-__device__ __forceinline__ void chunk(const IngestParams& p, uint32_t key, uint32_t c, TermAux aux, int lane,
-                                      unsigned long long* num_q, Acc& a, int64_t doc, float inv_norm,
-                                      int32_t* row_cnt_s, int64_t row_base) {
+__device__ __forceinline__ void chunk(const IngestParams& p, uint32_t key, uint32_t c, TermAux aux,
+                                      const Transposer& tr, unsigned long long* num_q, Acc& a, int64_t doc,
+                                      float inv_norm, int32_t* row_cnt_s, int64_t row_base) {
   const bool valid = key != kEmpty;
   if (MODE == kDF || MODE == kDFN) {
     if (valid) {
-      atomicAdd(&p.df[key], 1);
+      if (p.bag_read) atomicAdd(&p.df[key], 1);  // hashing passes count df at insertion
       if (MODE == kDFN) {
         const float w = (float)c * aux.w;
         a.norm += to_fix(w * w);
@@ -319,8 +356,8 @@ __device__ __forceinline__ void chunk(const IngestParams& p, uint32_t key, uint3
   if (MODE == kSIG) {
     if (p.sig.simhash) {
       const uint64_t h = !valid ? 0ull : p.fhash ? aux.h : feature_hash(key, p.seed);
-      const uint32_t hl = transpose32((uint32_t)h, lane);
-      const uint32_t hh = transpose32((uint32_t)(h >> 32), lane);
+      const uint32_t hl = tr((uint32_t)h);
+      const uint32_t hh = tr((uint32_t)(h >> 32));
       const uint32_t cmax = __reduce_max_sync(kFull, c);
       for (uint32_t b = 0; (cmax >> b) != 0u; ++b) {
         const uint32_t plane = __ballot_sync(kFull, (c >> b) & 1u);
@@ -424,74 +461,32 @@ __device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsi
   }
 }
 
-// Builds the bag of terms of one document (<= kShortMax tokens) in a warp's table of 2^l2
-// slots: clears the table, inserts every token (all of the document's token loads in flight
-// at once, 16 per lane; inserts in batches of 8 with their compare-and-swaps in flight
-// together), then compacts the occupied slots to the front. Returns the number of distinct
-// terms (<= 2^l2 / 2).
-__device__ __forceinline__ int warp_hash_doc(const IngestParams& p, uint32_t* keys, uint32_t* cnts, int l2, int64_t o0,
-                                             int64_t len, int lane) {
-  const int ts = 1 << l2;
-  for (int s = lane; s < ts; s += 32) {
-    keys[s] = kEmpty;
-    cnts[s] = 0u;
-  }
-  int32_t tk[kShortRegs];
-#pragma unroll
-  for (int u = 0; u < kShortRegs; ++u) tk[u] = lane + 32 * u < len ? __ldcs(p.tokens + o0 + lane + 32 * u) : -1;
-  __syncwarp();
-#pragma unroll
-  for (int h = 0; h < kShortRegs; h += 8) {
-    if (32 * h >= len) break;  // warp-uniform
-    int32_t tb[8];
-    uint32_t pend = 0u;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      tb[u] = tk[h + u];
-      if (lane + 32 * (h + u) < len) {
-        if ((uint32_t)tb[u] >= (uint32_t)p.vocab)
-          set_err(p.err, kErrBadToken);
-        else
-          pend |= 1u << u;
-      }
-    }
-    if (!table_insert_batch<8>(keys, cnts, l2, tb, pend)) set_err(p.err, kErrTable);
-  }
-  __syncwarp();
-  // compact the occupied slots to the front, in place (a write never passes an unread slot)
-  int nnz = 0;
-  for (int s0 = 0; s0 < ts; s0 += 32) {
-    const uint32_t key = keys[s0 + lane], c = cnts[s0 + lane];
-    const bool valid = key != kEmpty;
-    const unsigned bal = __ballot_sync(kFull, valid);
-    __syncwarp();
-    if (valid) {
-      const int at = nnz + __popc(bal & ((1u << lane) - 1u));
-      keys[at] = key;
-      cnts[at] = c;
-    }
-    nnz += __popc(bal);
-    __syncwarp();
-  }
-  return nnz;
+// ---------------------------------------------------------------- warp path
+// Shared memory of one warp of the warp path: partition accumulators, the table, the list of
+// occupied slots and two counters.
+__host__ __device__ __forceinline__ size_t short_warp_bytes(int kq) {
+  return (size_t)kq * 8 + (size_t)kShortSlots * 8 + (size_t)kShortMax * 2 + 16;
 }
 
-// ---------------------------------------------------------------- warp path
+// One warp per document of <= kShortMax tokens, documents taken one at a time from a device
+// counter as warps free up (their lengths vary 100-fold). The document's terms are either
+// read from the stored bag into the table area (all loads in flight at once), or built by
+// hashing the tokens (all token loads in flight at once, inserts in batches of 8) and found
+// through the list of occupied slots. They are then walked 32 at a time, each chunk's table
+// values gathered while the previous chunk is worked on.
 template <int MODE>
 __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kq = ingest_kq<MODE>(p);
-  const size_t per_warp = (size_t)kShortSlots * 8 + (size_t)kq * 8 + 16;
-  uint8_t* base = smem + per_warp * warp;
+  uint8_t* base = smem + short_warp_bytes(kq) * warp;
   unsigned long long* num_q = reinterpret_cast<unsigned long long*>(base);
-  uint32_t* keys = reinterpret_cast<uint32_t*>(base + (size_t)kq * 8);
-  uint32_t* cnts = keys + kShortSlots;
-  int32_t* row_cnt_s = reinterpret_cast<int32_t*>(cnts + kShortSlots);
+  unsigned long long* tab = num_q + kq;
+  uint16_t* list = reinterpret_cast<uint16_t*>(tab + kShortSlots);
+  int32_t* misc = reinterpret_cast<int32_t*>(list + kShortMax);  // [0] list size, [1] row count
+  const Transposer tr(lane);
 
   const int32_t n_short = p.list_counts[0];
-  // documents are taken one at a time as warps free up (their lengths vary 100-fold); each
-  // warp asks for its next document while it works on the current one
   int32_t it = 0;
   if (lane == 0) it = atomicAdd(p.short_cursor, 1);
   it = __shfl_sync(kFull, it, 0);
@@ -500,80 +495,93 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
     if (lane == 0) next = atomicAdd(p.short_cursor, 1);
     const int64_t d = p.short_list[it];
     const int64_t o0 = p.offsets[d], len = p.offsets[d + 1] - o0;
-    const int l2 = log2_slots(len, 10);
-    const int ts = 1 << l2;
     for (int q = lane; q < kq; q += 32) num_q[q] = 0ull;
-    if (lane == 0) *row_cnt_s = 0;
+    if (lane == 0) {
+      misc[0] = 0;
+      misc[1] = 0;
+    }
     int nnz = 0;
     if (p.bag_read) {
-      // the document's bag, built by an earlier pass: (term, count) pairs, four loads in flight
+      // the document's bag, built by an earlier pass: every load in flight at once, then
+      // packed into the table area as (term, count) words 0 .. nnz - 1
       nnz = p.bag_n[d];
-      for (int s0 = 0; s0 < nnz; s0 += 4 * 32) {
-        int32_t bt[4], bc[4];
+      int32_t bt[kShortRegs], bc[kShortRegs];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int sl = s0 + 32 * u + lane;
-          bt[u] = sl < nnz ? __ldcs(p.bag_terms + o0 + sl) : 0;
-          bc[u] = sl < nnz ? __ldcs(p.bag_cnts + o0 + sl) : 0;
-        }
+      for (int u = 0; u < kShortRegs; ++u) {
+        const int x = lane + 32 * u;
+        bt[u] = x < nnz ? __ldcs(p.bag_terms + o0 + x) : 0;
+        bc[u] = x < nnz ? __ldcs(p.bag_cnts + o0 + x) : 0;
+      }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int sl = s0 + 32 * u + lane;
-          if (sl < nnz) {
-            keys[sl] = (uint32_t)bt[u];
-            cnts[sl] = (uint32_t)bc[u];
-          }
-        }
+      for (int u = 0; u < kShortRegs; ++u) {
+        const int x = lane + 32 * u;
+        if (x < nnz) tab[x] = ((unsigned long long)(uint32_t)bt[u] << 32) | (uint32_t)bc[u];
       }
       __syncwarp();
     } else {
-      nnz = warp_hash_doc(p, keys, cnts, l2, o0, len, lane);
+      const int l2 = log2_slots(len, 10);
+      const int ts = 1 << l2;
+      for (int s = lane; s < ts; s += 32) tab[s] = kEmpty64;
+      int32_t tk[kShortRegs];
+#pragma unroll
+      for (int u = 0; u < kShortRegs; ++u) tk[u] = lane + 32 * u < len ? __ldcs(p.tokens + o0 + lane + 32 * u) : -1;
+      __syncwarp();
+      int32_t* df = (MODE == kDF || MODE == kDFN) ? p.df : nullptr;
+#pragma unroll
+      for (int h = 0; h < kShortRegs; h += 8) {
+        if (32 * h >= len) break;  // warp-uniform
+        int32_t tb[8];
+        uint32_t pend = 0u;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          tb[u] = tk[h + u];
+          if (lane + 32 * (h + u) < len) {
+            if ((uint32_t)tb[u] >= (uint32_t)p.vocab)
+              set_err(p.err, kErrBadToken);
+            else
+              pend |= 1u << u;
+          }
+        }
+        if (!insert_batch<8>(tab, list, &misc[0], l2, tb, pend, df)) set_err(p.err, kErrTable);
+      }
+      __syncwarp();
+      nnz = misc[0];
       if (p.bag_write) {
-        for (int sl = lane; sl < nnz; sl += 32) {
-          p.bag_terms[o0 + sl] = (int32_t)keys[sl];
-          p.bag_cnts[o0 + sl] = (int32_t)cnts[sl];
+        for (int x = lane; x < nnz; x += 32) {
+          const unsigned long long v = tab[list[x]];
+          p.bag_terms[o0 + x] = (int32_t)(uint32_t)(v >> 32);
+          p.bag_cnts[o0 + x] = (int32_t)(uint32_t)v;
         }
         if (lane == 0) p.bag_n[d] = nnz;
       }
     }
-    // gather the terms' table values into the free upper half of the table (nnz <= ts / 2),
-    // eight loads per lane in flight
-    float* aux_w = reinterpret_cast<float*>(keys + ts / 2);
-    int32_t* aux_c = reinterpret_cast<int32_t*>(cnts + ts / 2);
-    if (MODE != kDF) {
-      for (int s0 = 0; s0 < nnz; s0 += 8 * 32) {
-        TermAux ax[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int sl = s0 + 32 * u + lane;
-          if (sl < nnz) ax[u] = load_aux<MODE>(p, keys[sl]);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int sl = s0 + 32 * u + lane;
-          if (sl < nnz) {
-            aux_w[sl] = ax[u].w;
-            aux_c[sl] = ax[u].code;
-          }
-        }
-      }
-      __syncwarp();
-    }
     Acc a{0ull, 0u, 0u};
     float inv_norm = 0.f;
     if (MODE == kDENSE) inv_norm = inv_norm_of(p.dense.norm[d]);
-    uint64_t h_next = load_hash<MODE>(p, lane < nnz ? keys[lane] : kEmpty);
-    for (int s0 = 0; s0 < nnz; s0 += 32) {
-      const int sl = s0 + lane;
-      const uint32_t key = sl < nnz ? keys[sl] : kEmpty;
-      const uint32_t c = sl < nnz ? cnts[sl] : 0u;
-      TermAux ax{1.0f, 0, h_next};
-      h_next = load_hash<MODE>(p, sl + 32 < nnz ? keys[sl + 32] : kEmpty);  // next chunk's, in flight
-      if (MODE != kDF && sl < nnz) {
-        ax.w = aux_w[sl];
-        ax.code = aux_c[sl];
+    if (MODE != kDF || p.bag_read) {
+      // term x: the bag's word x, or the table slot the list's entry x names
+      const bool bag = p.bag_read != 0;
+      auto term = [&](int x, uint32_t& key, uint32_t& c) {
+        const unsigned long long v = x < nnz ? tab[bag ? x : list[x]] : kEmpty64;
+        key = (uint32_t)(v >> 32);
+        c = (uint32_t)v;
+      };
+      uint32_t key, c;
+      term(lane, key, c);
+      TermAux ax{1.0f, 0, 0ull};
+      if (MODE != kDF && key != kEmpty) ax = load_aux<MODE>(p, key);
+      ax.h = load_hash<MODE>(p, key);
+      for (int x0 = 0; x0 < nnz; x0 += 32) {
+        uint32_t key1 = kEmpty, c1 = 0u;
+        if (x0 + 32 < nnz) term(x0 + 32 + lane, key1, c1);  // the next chunk's table values, in flight
+        TermAux ax1{1.0f, 0, 0ull};
+        if (MODE != kDF && key1 != kEmpty) ax1 = load_aux<MODE>(p, key1);
+        ax1.h = load_hash<MODE>(p, key1);
+        chunk<MODE>(p, key, c, ax, tr, num_q, a, d, inv_norm, &misc[1], o0);
+        key = key1;
+        c = c1;
+        ax = ax1;
       }
-      chunk<MODE>(p, key, c, ax, lane, num_q, a, d, inv_norm, row_cnt_s, o0);
     }
     __syncwarp();
     if (MODE == kSIG) finalize_sig(p, d, len, warp_sum(a.norm), num_q, a.plo, a.phi, lane);
@@ -583,139 +591,142 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
     }
     if (MODE == kDENSE) {
       if (!p.dense.postings) write_bucket_norms(p, d, num_q, lane, 32);
-      if (lane == 0) p.dense.row_cnt[d] = *row_cnt_s;
+      if (lane == 0) p.dense.row_cnt[d] = misc[1];
     }
     __syncwarp();
     it = __shfl_sync(kFull, next, 0);
   }
-  // This grid may start while the CTA path's grid (launched just before it) is still running;
-  // it completes only after that grid, so the next launch on the stream sees both.
+  // This grid may start while the long-document grid (launched just before it) is still
+  // running; it completes only after that grid, so the next launch on the stream sees both.
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-// The CTA's warps walk table slots [0, lim) in 32-slot chunks, each with the next chunk's
-// table values already in flight. With bag_cursor, the occupied slots of each chunk are also
-// appended to the document's bag (coalesced; the bag's order does not matter to any pass:
-// every sum over it is an integer sum).
-template <int MODE>
-__device__ __forceinline__ void cta_walk(const IngestParams& p, const uint32_t* keys, const uint32_t* cnts, int lim,
-                                         int warp, int lane, unsigned long long* num_q, Acc& a, int64_t d,
-                                         float inv_norm, int32_t* row_cnt_s, int64_t o0, int32_t* bag_cursor) {
-  constexpr int nwarps = kLongThreads / 32;
-  int s0 = warp * 32;
-  uint32_t key = s0 + lane < lim ? keys[s0 + lane] : kEmpty;
-  uint32_t c = key != kEmpty ? cnts[s0 + lane] : 0u;
+// ---------------------------------------------------------------- long-document path
+// Documents longer than kShortMax go to groups of kGroupWarps warps (kGroupsLong groups per
+// CTA, each with its own table and named barrier), one document per group at a time, longest
+// length class first. A document with more than kLongSlots / 2 tokens is hashed in several
+// passes, each keeping the terms of one hash partition (a second hash of the term id), so the
+// table runs about half full. The list of occupied slots has room for every slot.
+__host__ __device__ __forceinline__ size_t long_group_bytes(int kq) {
+  return (size_t)kq * 8 + 8 + 64 * 4 + 16 + (size_t)kLongSlots * 8 + (size_t)kLongSlots * 2;
+}
+
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGroupThreads) : "memory");
+}
+
+// The group's warps walk the terms [0, n) of one document, warp gw taking chunks gw, gw + W, ...
+// of 32 terms; term x is (key, count) = at(x) (kEmpty for x >= n). Each chunk's table values
+// are gathered while the previous chunk is worked on. With bag_cursor, the terms are also
+// appended to the document's bag (coalesced; no pass depends on the bag's order, every sum
+// over it being an integer sum).
+template <int MODE, typename At>
+__device__ __forceinline__ void group_walk(const IngestParams& p, int n, int gw, int lane, const At& at,
+                                           const Transposer& tr, unsigned long long* num_q, Acc& a, int64_t d,
+                                           float inv_norm, int32_t* row_cnt_s, int64_t o0, int32_t* bag_cursor) {
+  int x0 = gw * 32;
+  uint32_t key = kEmpty, c = 0u;
+  at(x0 + lane, key, c);
   TermAux ax{1.0f, 0, 0ull};
   if (MODE != kDF && key != kEmpty) ax = load_aux<MODE>(p, key);
   ax.h = load_hash<MODE>(p, key);
-  while (s0 < lim) {
-    const int s1 = s0 + nwarps * 32;
-    const uint32_t key1 = s1 + lane < lim ? keys[s1 + lane] : kEmpty;
-    const uint32_t c1 = key1 != kEmpty ? cnts[s1 + lane] : 0u;
+  while (x0 < n) {
+    const int x1 = x0 + kGroupWarps * 32;
+    uint32_t key1 = kEmpty, c1 = 0u;
+    if (x1 < n) at(x1 + lane, key1, c1);
     TermAux ax1{1.0f, 0, 0ull};
     if (MODE != kDF && key1 != kEmpty) ax1 = load_aux<MODE>(p, key1);
     ax1.h = load_hash<MODE>(p, key1);
-    const unsigned occ = __ballot_sync(kFull, key != kEmpty);
-    if (occ != 0u) {
-      chunk<MODE>(p, key, c, ax, lane, num_q, a, d, inv_norm, row_cnt_s, o0);
-      if (bag_cursor) {
-        int32_t at = 0;
-        if (lane == 0) at = atomicAdd(bag_cursor, __popc(occ));
-        at = __shfl_sync(kFull, at, 0) + __popc(occ & ((1u << lane) - 1u));
-        if (key != kEmpty) {
-          p.bag_terms[o0 + at] = (int32_t)key;
-          p.bag_cnts[o0 + at] = (int32_t)c;
-        }
+    if (bag_cursor) {
+      const unsigned occ = __ballot_sync(kFull, key != kEmpty);
+      int32_t b = 0;
+      if (lane == 0) b = atomicAdd(bag_cursor, __popc(occ));
+      b = __shfl_sync(kFull, b, 0) + __popc(occ & ((1u << lane) - 1u));
+      if (key != kEmpty) {
+        p.bag_terms[o0 + b] = (int32_t)key;
+        p.bag_cnts[o0 + b] = (int32_t)c;
       }
     }
-    s0 = s1;
+    if (MODE != kDF || p.bag_read) chunk<MODE>(p, key, c, ax, tr, num_q, a, d, inv_norm, row_cnt_s, o0);
+    x0 = x1;
     key = key1;
     c = c1;
     ax = ax1;
   }
 }
 
-// ---------------------------------------------------------------- CTA path
 template <int MODE>
-__global__ void __launch_bounds__(kLongThreads, 2) k_ingest_long(IngestParams p) {
+__global__ void __launch_bounds__(kLongThreads, 1) k_ingest_long(IngestParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = threadIdx.x / kGroupThreads, gt = threadIdx.x % kGroupThreads;
+  const int gw = gt >> 5, lane = threadIdx.x & 31;
   const int kq = ingest_kq<MODE>(p);
-  unsigned long long* num_q = reinterpret_cast<unsigned long long*>(smem);
+  uint8_t* base = smem + long_group_bytes(kq) * g;
+  unsigned long long* num_q = reinterpret_cast<unsigned long long*>(base);
   unsigned long long* norm_s = num_q + kq;
-  uint32_t* P = reinterpret_cast<uint32_t*>(norm_s + 1);  // [64]
-  int32_t* misc = reinterpret_cast<int32_t*>(P + 64);     // [0] doc slot, [1] row count
-  uint32_t* keys = reinterpret_cast<uint32_t*>(misc + 4);  // misc: [0] doc slot, [1] row count, [2] bag size
-  uint32_t* cnts = keys + kLongSlots;
+  uint32_t* P = reinterpret_cast<uint32_t*>(norm_s + 1);  // [64] Simhash column sums
+  int32_t* misc = reinterpret_cast<int32_t*>(P + 64);     // [0] document, [1] row count, [2] bag size, [3] list size
+  unsigned long long* tab = reinterpret_cast<unsigned long long*>(misc + 4);
+  uint16_t* list = reinterpret_cast<uint16_t*>(tab + kLongSlots);
+  const Transposer tr(lane);
 
   const int32_t n_long = p.list_counts[1];
   // the warp path's grid may start on SMs this grid leaves (the two touch disjoint documents)
   asm volatile("griddepcontrol.launch_dependents;");
   while (true) {
-    if (threadIdx.x == 0) misc[0] = atomicAdd(p.long_cursor, 1);
-    __syncthreads();
+    if (gt == 0) misc[0] = atomicAdd(p.long_cursor, 1);
+    group_sync(g);
     const int32_t it = misc[0];
     if (it >= n_long) break;
     const int64_t d = p.long_list[it];
     const int64_t o0 = p.offsets[d], len = p.offsets[d + 1] - o0;
-    const int l2 = log2_slots(len, 13);
-    const int ts = 1 << l2;
-    const uint32_t passes = (uint32_t)((len + (kLongSlots / 2) - 1) / (kLongSlots / 2));
-    for (int q = threadIdx.x; q < kq; q += kLongThreads) num_q[q] = 0ull;
-    if (threadIdx.x < 64) P[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) {
+    for (int q = gt; q < kq; q += kGroupThreads) num_q[q] = 0ull;
+    if (gt < 64) P[gt] = 0u;
+    if (gt == 0) {
       *norm_s = 0ull;
       misc[1] = 0;
+      misc[2] = 0;
     }
     Acc a{0ull, 0u, 0u};
     float inv_norm = 0.f;
     if (MODE == kDENSE) inv_norm = inv_norm_of(p.dense.norm[d]);
     if (p.bag_read) {
-      // the document's bag, built by an earlier pass, in table-sized slices
       const int32_t nb = p.bag_n[d];
-      for (int32_t b0 = 0; b0 < nb; b0 += kLongSlots) {
-        const int32_t m = min(kLongSlots, nb - b0);
-        __syncthreads();
-        for (int32_t x0 = threadIdx.x; x0 < m; x0 += 4 * kLongThreads) {
-          int32_t bt[4], bc[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int32_t x = x0 + u * kLongThreads;
-            bt[u] = x < m ? __ldcs(p.bag_terms + o0 + b0 + x) : 0;
-            bc[u] = x < m ? __ldcs(p.bag_cnts + o0 + b0 + x) : 0;
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int32_t x = x0 + u * kLongThreads;
-            if (x < m) {
-              keys[x] = (uint32_t)bt[u];
-              cnts[x] = (uint32_t)bc[u];
-            }
-          }
+      group_sync(g);
+      const int32_t* bt = p.bag_terms + o0;
+      const int32_t* bcn = p.bag_cnts + o0;
+      auto at = [&](int x, uint32_t& key, uint32_t& c) {
+        if (x < nb) {
+          key = (uint32_t)__ldcs(bt + x);
+          c = (uint32_t)__ldcs(bcn + x);
+        } else {
+          key = kEmpty;
+          c = 0u;
         }
-        __syncthreads();
-        cta_walk<MODE>(p, keys, cnts, m, warp, lane, num_q, a, d, inv_norm, &misc[1], o0, nullptr);
-      }
+      };
+      group_walk<MODE>(p, nb, gw, lane, at, tr, num_q, a, d, inv_norm, &misc[1], o0, nullptr);
     } else {
-      if (threadIdx.x == 0) misc[2] = 0;
+      const int l2 = log2_slots(len, 12);
+      const int ts = 1 << l2;
+      const uint32_t passes = (uint32_t)((len + (kLongSlots / 2) - 1) / (kLongSlots / 2));
+      int32_t* df = (MODE == kDF || MODE == kDFN) ? p.df : nullptr;
+      const bool walk = MODE != kDF || p.bag_write;
       for (uint32_t pass = 0; pass < passes; ++pass) {
-        __syncthreads();
-        for (int s = threadIdx.x; s < ts; s += kLongThreads) {
-          keys[s] = kEmpty;
-          cnts[s] = 0u;
-        }
-        __syncthreads();
-        for (int64_t x0 = threadIdx.x; x0 < len; x0 += kLongUnroll * kLongThreads) {
+        group_sync(g);
+        for (int s = gt; s < ts; s += kGroupThreads) tab[s] = kEmpty64;
+        if (gt == 0) misc[3] = 0;
+        group_sync(g);
+        for (int64_t x0 = gt; x0 < len; x0 += kLongUnroll * kGroupThreads) {
           int32_t tk[kLongUnroll];  // kLongUnroll token loads in flight per thread
 #pragma unroll
           for (int u = 0; u < kLongUnroll; ++u) {
-            const int64_t x = x0 + u * kLongThreads;
+            const int64_t x = x0 + u * kGroupThreads;
             tk[u] = x < len ? __ldcs(p.tokens + o0 + x) : -1;
           }
           uint32_t pend = 0u;
 #pragma unroll
           for (int u = 0; u < kLongUnroll; ++u) {
-            if (x0 + u * kLongThreads >= len) break;
+            if (x0 + u * kGroupThreads >= len) break;
             const int32_t t = tk[u];
             if ((uint32_t)t >= (uint32_t)p.vocab) {
               if (pass == 0) set_err(p.err, kErrBadToken);
@@ -724,32 +735,38 @@ __global__ void __launch_bounds__(kLongThreads, 2) k_ingest_long(IngestParams p)
             if (passes > 1 && pass_of((uint32_t)t, passes) != pass) continue;
             pend |= 1u << u;
           }
-          if (!table_insert_batch<kLongUnroll>(keys, cnts, l2, tk, pend)) set_err(p.err, kErrTable);
+          if (!insert_batch<kLongUnroll>(tab, list, &misc[3], l2, tk, pend, df)) set_err(p.err, kErrTable);
         }
-        __syncthreads();
-        cta_walk<MODE>(p, keys, cnts, ts, warp, lane, num_q, a, d, inv_norm, &misc[1], o0,
-                       p.bag_write ? &misc[2] : nullptr);
+        group_sync(g);
+        if (walk) {
+          const int n = misc[3];
+          auto at = [&](int x, uint32_t& key, uint32_t& c) {
+            const unsigned long long v = x < n ? tab[list[x]] : kEmpty64;
+            key = (uint32_t)(v >> 32);
+            c = (uint32_t)v;
+          };
+          group_walk<MODE>(p, n, gw, lane, at, tr, num_q, a, d, inv_norm, &misc[1], o0,
+                           p.bag_write ? &misc[2] : nullptr);
+        }
       }
     }
-    if (MODE == kDFN) {
+    if (MODE == kDFN || MODE == kSIG) {
       const unsigned long long nq = warp_sum(a.norm);
-      if (lane == 0) atomicAdd(norm_s, nq);
+      if (lane == 0 && nq) atomicAdd(norm_s, nq);
     }
     if (MODE == kSIG) {
-      const unsigned long long nq = warp_sum(a.norm);
-      if (lane == 0) atomicAdd(norm_s, nq);
       atomicAdd(&P[lane], a.plo);
       atomicAdd(&P[lane + 32], a.phi);
     }
-    __syncthreads();
-    if (MODE == kSIG && warp == 0) finalize_sig(p, d, len, *norm_s, num_q, P[lane], P[lane + 32], lane);
+    group_sync(g);
+    if (MODE == kSIG && gw == 0) finalize_sig(p, d, len, *norm_s, num_q, P[lane], P[lane + 32], lane);
     if (MODE == kDENSE) {
-      if (threadIdx.x == 0) p.dense.row_cnt[d] = misc[1];
-      if (!p.dense.postings) write_bucket_norms(p, d, num_q, threadIdx.x, kLongThreads);
+      if (gt == 0) p.dense.row_cnt[d] = misc[1];
+      if (!p.dense.postings) write_bucket_norms(p, d, num_q, gt, kGroupThreads);
     }
-    if (MODE == kDFN && threadIdx.x == 0) p.norm_out[d] = *norm_s;
-    if (p.bag_write && threadIdx.x == 0) p.bag_n[d] = misc[2];
-    __syncthreads();
+    if (MODE == kDFN && gt == 0) p.norm_out[d] = *norm_s;
+    if (p.bag_write && gt == 0) p.bag_n[d] = misc[2];
+    group_sync(g);
   }
 }
 
@@ -877,8 +894,8 @@ int long_grid(const mrc_ctx* ctx, size_t smem) {
   return ctx->num_sms * resident_ctas(k_ingest_long<MODE>, kLongThreads, smem);
 }
 
-size_t short_smem(int kq) { return (size_t)kWarpsShort * ((size_t)kShortSlots * 8 + (size_t)kq * 8 + 16); }
-size_t long_smem(int kq) { return (size_t)kq * 8 + 8 + 64 * 4 + 16 + (size_t)kLongSlots * 8; }
+size_t short_smem(int kq) { return (size_t)kWarpsShort * short_warp_bytes(kq); }
+size_t long_smem(int kq) { return (size_t)kGroupsLong * long_group_bytes(kq); }
 
 template <int MODE>
 cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const char* name, double bytes_per_token,

@@ -86,6 +86,9 @@ struct mrc_ctx {
   size_t host_ws_bytes = 0;
   cudaEvent_t host_ws_done = nullptr;  // recorded after the last copy that reads host_ws
   int32_t* async_err = nullptr;  // device error word of the stream-ordered calls (until mrc_ctx_sync)
+  uint64_t wait_limit_ns = 4000000000ull;  // bound of every device-side wait (mrc_ctx_set_wait_limit)
+  bool test_stall = false;                 // compare kernels issue no MMA (mrc_ctx_set_test_stall)
+  bool rescore = true;                     // mrc_match rescores its candidates (mrc_ctx_set_rescoring)
 };
 
 struct mrc_index {
@@ -299,8 +302,16 @@ struct GemmArgs {
                                // (kbytes is then the row stride and the K extent of the maps)
 };
 cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g);
+// FP32 rescoring of the first min(*n_cand, cand_cap) candidates (unit_dot of rows i of qunit
+// and j of xunit, k entries each); pairs scoring >= tau are appended to pairs / count (at most
+// capacity written). A candidate count above cand_cap sets kErrOverflow in err (if given).
+cudaError_t launch_rescore(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand, int64_t cand_cap,
+                           const float* qunit, const float* xunit, int32_t k, float tau, mrc_pair* pairs,
+                           unsigned long long* count, int64_t capacity, int32_t* err);
 
 // simhash_match.cu
+// Measured issue rate of 32-bit POPC on this device (population counts per second).
+cudaError_t measure_popc_rate(mrc_ctx* ctx, double* popc_per_s);
 cudaError_t launch_simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
                                  int32_t hmax, mrc_pair* pairs, unsigned long long* count, int64_t capacity);
 
@@ -344,8 +355,5 @@ cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t
                                int64_t n_postings, const void* head_hi, const void* head_lo,
                                int32_t kd, float tau, float delta, mrc_pair* pairs, unsigned long long* count,
                                int64_t capacity, double work_pairs, unsigned long long* next_item);
-cudaError_t launch_rescore(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand, int64_t cand_cap,
-                           const float* qunit, const float* xunit, int32_t k, float tau, mrc_pair* pairs,
-                           unsigned long long* count, int64_t capacity, int32_t* err);
 
 }  // namespace mrc

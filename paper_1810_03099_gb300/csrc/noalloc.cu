@@ -18,7 +18,6 @@
 // each call, and the lists are rewritten before they are read. Two calls
 // whose work overlaps on the same device (different streams or host
 // threads) race on the array and must be serialised by the caller.
-#include <mutex>
 #include <string>
 
 #include "device.cuh"
@@ -34,28 +33,21 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
 namespace {
 
 constexpr int64_t kMaxDocs = MRC_NOALLOC_MAX_DOCS;
-constexpr int kMaxDevices = 64;
 // [0, kMaxDocs): warp-path list; [kMaxDocs, 2 kMaxDocs): CTA-path list;
 // then 32 counter words and the error word.
 constexpr int64_t kWords = 2 * kMaxDocs + 64;
 
 static __device__ __align__(256) int32_t g_signature_scratch[kWords];
 
-std::mutex g_mutex;
-int32_t* g_scratch[kMaxDevices] = {};
-
-// Device address of the array on `device`, looked up once per device with that
-// device current (the host-side name of a __device__ array is not a device address).
-mrc_status scratch_on(mrc_ctx* ctx, int device, int32_t** out) {
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (device < 0 || device >= kMaxDevices) return mrc::fail(ctx, MRC_ERR_UNSUPPORTED, "device ordinal too large");
-  if (!g_scratch[device]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_signature_scratch);
-    if (e != cudaSuccess || !p) return mrc::cuda_fail(ctx, e, "cudaGetSymbolAddress of the signature scratch");
-    g_scratch[device] = static_cast<int32_t*>(p);
-  }
-  *out = g_scratch[device];
+// Device address of the array on the current device. The host-side name of a __device__ array
+// is not a device address; the runtime resolves it for the current device's context. It is
+// looked up on every call (a host-side table lookup once the module is loaded, which the
+// first call on a device does), so no address outlives a device reset or a module reload.
+mrc_status scratch_on(mrc_ctx* ctx, int32_t** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_signature_scratch);
+  if (e != cudaSuccess || !p) return mrc::cuda_fail(ctx, e, "cudaGetSymbolAddress of the signature scratch");
+  *out = static_cast<int32_t*>(p);
   return MRC_OK;
 }
 
@@ -96,8 +88,14 @@ extern "C" mrc_status mrc_signature_noalloc(mrc_ctx* ctx, const mrc_index* index
     return mrc::fail(ctx, MRC_ERR_INVALID,
                      "mrc_signature_noalloc: offsets, tokens and outputs must be device memory (it copies nothing)");
 
+  // the call waits for its own stream (list sizes, error word), which a stream capture forbids
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return mrc::fail(ctx, MRC_ERR_UNSUPPORTED, "mrc_signature_noalloc cannot run while its stream is being captured");
+  }
   int32_t* scratch = nullptr;
-  mrc_status st = scratch_on(ctx, ctx->device, &scratch);
+  mrc_status st = scratch_on(ctx, &scratch);
   if (st != MRC_OK) return st;
   int32_t* lists = scratch;
   int32_t* counts = scratch + 2 * kMaxDocs;

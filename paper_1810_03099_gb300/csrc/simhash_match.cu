@@ -76,7 +76,58 @@ __global__ void __launch_bounds__(kRows) k_simhash_match(const uint64_t* __restr
   }
 }
 
+// Throughput probe of the all-pairs match's bounding unit: every thread keeps eight independent
+// population counts of a rotating word in flight (XOR, POPC, add each), so the loop runs at the
+// rate the SMs issue 32-bit POPC. The result is kept live through a data-dependent store that
+// never happens for these inputs.
+__global__ void __launch_bounds__(256) k_popc_rate(uint32_t seed, int32_t iters, unsigned long long* sink) {
+  uint32_t x[8], acc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    x[u] = seed * (threadIdx.x + 1u) + (uint32_t)u * 0x9E3779B9u + blockIdx.x;
+    acc[u] = 0u;
+  }
+  uint32_t k = blockIdx.x * 0x85EBCA6Bu;
+  for (int32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] += (uint32_t)__popc(x[u] ^ k);
+    k += 0x9E3779B9u;
+  }
+  uint32_t t = 0u;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) t += acc[u];
+  if (t == 0xFFFFFFFFu) *sink = t;  // at most 8 * 32 * iters < 2^32 - 1
+}
+
 }  // namespace
+
+cudaError_t measure_popc_rate(mrc_ctx* ctx, double* popc_per_s) {
+  constexpr int32_t kIters = 4096;
+  const int64_t blocks = (int64_t)ctx->num_sms * 8;
+  unsigned long long* sink = nullptr;
+  cudaError_t e = cudaMallocAsync(&sink, sizeof(unsigned long long), ctx->stream);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best_ms = 0.f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first run warms up
+    e = cudaEventRecord(e0, ctx->stream);
+    k_popc_rate<<<(unsigned)blocks, 256, 0, ctx->stream>>>(0x1810u + (uint32_t)rep, kIters, sink);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && rep > 0 && (best_ms == 0.f || ms < best_ms)) best_ms = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(sink, ctx->stream);
+  if (e != cudaSuccess) return e;
+  *popc_per_s = (double)blocks * 256.0 * 8.0 * kIters / (best_ms * 1e-3);
+  return cudaStreamSynchronize(ctx->stream);
+}
 
 cudaError_t launch_simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
                                  int32_t hmax, mrc_pair* pairs, unsigned long long* count, int64_t capacity) {

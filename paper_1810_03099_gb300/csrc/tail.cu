@@ -760,28 +760,32 @@ __global__ void __launch_bounds__(kVerWarps * 32, 3) k_cosine_verify_long(
   }
 }
 
+// FP32 rescoring of candidates: one thread per candidate (unit_dot of its two unit signatures,
+// so the loads of both rows are in flight together), kept iff the score is >= tau; the warp's
+// kept pairs are appended with one atomic.
 __global__ void k_rescore(const mrc_pair* __restrict__ cand, const unsigned long long* n_cand, int64_t cand_cap,
                           const float* __restrict__ qunit, const float* __restrict__ xunit, int32_t k, float tau,
                           mrc_pair* pairs, unsigned long long* count, int64_t capacity, int32_t* err) {
   const int lane = threadIdx.x & 31;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t nc0 = (int64_t)*n_cand;
   const int64_t nc = nc0 < cand_cap ? nc0 : cand_cap;
   if (err && nc0 > cand_cap && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, kErrOverflow);
-  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nc; c += nwarps) {
-    const mrc_pair pc = cand[c];
-    const float* qa = qunit + (int64_t)pc.i * k;
-    const float* xb = xunit + (int64_t)pc.j * k;
-    float s = 0.f;
-    for (int q = lane; q < k; q += 32) s = fmaf(qa[q], xb[q], s);
-    s = warp_sum(s);
-    if (lane == 0 && s >= tau) {
-      const unsigned long long at = atomicAdd(count, 1ull);
-      if (at < (unsigned long long)capacity) {
-        mrc_pair pr = pc;
-        pr.score = s;
-        pairs[at] = pr;
-      }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < nc; w0 += stride) {
+    const int64_t c = w0 + lane;
+    mrc_pair pr{0, 0, 0.f};
+    bool keep = false;
+    if (c < nc) {
+      pr = cand[c];
+      pr.score = unit_dot(qunit + (int64_t)pr.i * k, xunit + (int64_t)pr.j * k, k);
+      keep = pr.score >= tau;
+    }
+    const unsigned m = __ballot_sync(kFull, keep);
+    if (m) {
+      unsigned long long b = 0;
+      if (lane == 0) b = atomicAdd(count, (unsigned long long)__popc(m));
+      b = __shfl_sync(kFull, b, 0) + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+      if (keep && b < (unsigned long long)capacity) pairs[b] = pr;
     }
   }
 }
@@ -942,7 +946,7 @@ cudaError_t launch_cosine_tail(mrc_ctx* ctx, int64_t n, const void* H16, int64_t
 cudaError_t launch_rescore(mrc_ctx* ctx, const mrc_pair* cand, const unsigned long long* n_cand, int64_t cand_cap,
                            const float* qunit, const float* xunit, int32_t k, float tau, mrc_pair* pairs,
                            unsigned long long* count, int64_t capacity, int32_t* err) {
-  int64_t grid = (int64_t)ctx->num_sms * 8;
+  const int64_t grid = (int64_t)ctx->num_sms * 8;
   cudaEvent_t ev = nullptr;
   timing_begin(ctx, "rescore", 0.0, 0.0, &ev);
   k_rescore<<<(unsigned)grid, 256, 0, ctx->stream>>>(cand, n_cand, cand_cap, qunit, xunit, k, tau, pairs, count,

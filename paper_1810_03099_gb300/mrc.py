@@ -89,6 +89,10 @@ _SIGNATURES = {
     "mrc_index_load": (C.c_int32, [C.c_void_p, C.c_char_p, C.POINTER(C.c_void_p)]),
     "mrc_index_free": (None, [C.c_void_p]),
     "mrc_ctx_set_timing": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "mrc_ctx_set_wait_limit": (C.c_int32, [C.c_void_p, C.c_int64]),
+    "mrc_ctx_set_test_stall": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "mrc_ctx_set_rescoring": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "mrc_measure_popc_rate": (C.c_int32, [C.c_void_p, C.c_void_p]),
     "mrc_ctx_kernel_stat": (C.c_int32, [C.c_void_p, C.c_int32, C.c_char_p, C.POINTER(C.c_int64),
                                         C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mrc_ctx_reset_stats": (None, [C.c_void_p]),
@@ -192,6 +196,24 @@ class Context:
 
     def set_timing(self, on: bool = True):
         self.check(self.lib.mrc_ctx_set_timing(self.handle, 1 if on else 0))
+
+    def set_wait_limit(self, ns: int):
+        """Bound of every device-side wait of this context's kernels (nanoseconds)."""
+        self.check(self.lib.mrc_ctx_set_wait_limit(self.handle, int(ns)))
+
+    def popc_rate(self) -> float:
+        """Measured 32-bit POPC issue rate of this context's device (per second)."""
+        out = C.c_double()
+        self.check(self.lib.mrc_measure_popc_rate(self.handle, C.byref(out)))
+        return out.value
+
+    def set_rescoring(self, on: bool):
+        """Off: mrc_match returns the compare's candidates with the compare's own cosine (diagnostics)."""
+        self.check(self.lib.mrc_ctx_set_rescoring(self.handle, 1 if on else 0))
+
+    def set_test_stall(self, on: bool):
+        """Failure-detection test: this context's compare kernels issue no MMA, so their waits run out."""
+        self.check(self.lib.mrc_ctx_set_test_stall(self.handle, 1 if on else 0))
 
     def kernel_stats(self):
         out = []
