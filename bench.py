@@ -901,8 +901,6 @@ def news20_leg(steps):
     ms, _ = run(steps, False)
     _, stats = run(max(2, steps // 10), True)
     n1, n2, n3 = (int(x) for x in dcount.tolist())
-    for cx in (ctx3, ctx2, ctx):
-        cx.close()
     peaks = _peaks()
     head = [s for s in stats if s["name"] == "gemm_f16_bound"]
     out = {"docs_per_s": N / (ms / 1e3), "ms_per_step": ms,
@@ -911,6 +909,17 @@ def news20_leg(steps):
            "pairs": {"sig_pairs": n1, "simhash_pairs": n2, "cosine_pairs": n3},
            "kernels": [{"name": s["name"], "ms_per_launch": s["ms"] / s["launches"]}
                        for s in sorted(stats, key=lambda s: -s["ms"])[:8]]}
+    sh = [s for s in stats if s["name"] == "simhash_match"]
+    if sh:
+        # a7 roofline: one XOR + POPC per pair on the low halves, against the measured POPC rate
+        s = sh[0]
+        t = s["ms"] / s["launches"] / 1e3
+        rate = ctx.popc_rate()
+        pps = N * (N - 1) / 2 / t
+        out["simhash_match_roofline"] = {"bound": "alu", "kernel": "simhash_match", "achieved": pps / 1e12,
+                                         "peak": rate / 1e12, "unit": "T pairs/s (T POPC/s)", "frac": pps / rate,
+                                         "ms": t * 1e3,
+                                         "peak_source": "measured: mrc_measure_popc_rate (32-bit POPC per second)"}
     if head:
         s = head[0]
         t = s["ms"] / s["launches"] / 1e3
@@ -921,6 +930,8 @@ def news20_leg(steps):
             "method_tflops": method / t / 1e12, "method_frac": method / t / 1e12 / peaks["bf16_tflops"],
             "note": "the GEMM executes 2 x 384 flops per pair of the triangle (128 head + 256 bucket-norm "
                     "columns); the method's own work is sum_t df_t (df_t - 1) = 1.95e9 flops"}
+    for cx in (ctx3, ctx2, ctx):
+        cx.close()
     return out
 
 

@@ -63,7 +63,9 @@ typedef int32_t mrc_status;
 /* Arithmetic of the signature comparison. */
 #define MRC_PREC_FP32 0     /* FP32-accurate: fp16 tensor-core candidates within a proven
                                bound of tau, every candidate rescored in FP32 */
-#define MRC_PREC_BF16_FP8 1 /* BF16 weights, FP8 E4M3 compare, FP32 rescoring near tau  */
+#define MRC_PREC_BF16_FP8 1 /* compare operands from BF16 weights, FP8 E4M3 compare,
+                               candidates within margin of tau rescored in FP32 from the
+                               FP32-weight signatures (the stored signatures)           */
 #define MRC_PREC_FP16 2     /* FP16 signatures, FP16 compare, FP32 rescoring near tau   */
 
 /* The 64-bit Simhash feature hash of a term t (Section III hashes words with MD5 or SHA1). */
@@ -303,6 +305,7 @@ mrc_status mrc_ctx_sync(mrc_ctx* ctx);
  *     MRC_ERR_CAPACITY when the pairs (or the internal candidate list) overflowed.
  */
 typedef struct mrc_batch mrc_batch;
+typedef struct mrc_simhash_index mrc_simhash_index; /* block-table fingerprint index (below) */
 mrc_status mrc_batch_create(mrc_ctx* ctx, const mrc_index* index, int64_t max_docs, int64_t max_tokens, float tau,
                             int64_t capacity, int32_t tile_n, mrc_batch** out);
 mrc_status mrc_batch_launch(mrc_batch* batch, const mrc_docs* docs);
@@ -311,6 +314,27 @@ mrc_status mrc_batch_wait(mrc_batch* batch, mrc_pair* pairs, int64_t capacity, i
                           int64_t* query_offsets);
 const char* mrc_batch_last_error(const mrc_batch* batch);
 void mrc_batch_free(mrc_batch* batch);
+
+/*
+ * Hamming leg of a batch pipeline (Section III: each new page's Simhash is
+ * compared with the stored fingerprints; the serving form matches it against
+ * the resident index's Simhashes). mrc_batch_attach_simhash adds, to the
+ * captured graph, a probe of `index` (a block-table fingerprint index, see
+ * mrc_simhash_index_build) with the batch's own Simhash fingerprints: every
+ * (query position i, index position j) within hamming_max (<= the index's),
+ * score = the Hamming distance, grouped by query like the signature pairs;
+ * capacity bounds the Hamming pairs of one batch. Call it with no launch in
+ * flight; the batch keeps `index` (not owned; it must outlive the batch).
+ * mrc_batch_hamming, after mrc_batch_wait: copies min(total, capacity) pairs
+ * of the last launch (host or device), *n_pairs = total, query_offsets (may be
+ * NULL, [n_docs + 1]) where each query's pairs start. MRC_ERR_CAPACITY on
+ * overflow. The results equal mrc_simhash_index_match with the batch's
+ * fingerprints as queries.
+ */
+mrc_status mrc_batch_attach_simhash(mrc_batch* batch, const mrc_simhash_index* index, int32_t hamming_max,
+                                    int64_t capacity);
+mrc_status mrc_batch_hamming(mrc_batch* batch, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs,
+                             int64_t* query_offsets);
 
 /*
  * Block-table Hamming index over 64-bit Simhash fingerprints (Section I cites
@@ -332,7 +356,6 @@ void mrc_batch_free(mrc_batch* batch);
  * Pairs, capacity and *n_pairs as simhash_match. Errors: MRC_ERR_INVALID for
  * bad sizes or a distance above the build's, MRC_ERR_CAPACITY on overflow.
  */
-typedef struct mrc_simhash_index mrc_simhash_index;
 mrc_status mrc_simhash_index_build(mrc_ctx* ctx, const uint64_t* fps, int64_t n, int32_t hamming_max,
                                    mrc_simhash_index** out);
 mrc_status mrc_simhash_index_match(mrc_ctx* ctx, const mrc_simhash_index* index, const uint64_t* queries, int64_t nq,
@@ -348,8 +371,10 @@ mrc_status mrc_index_export(mrc_ctx* ctx, const mrc_index* index, float* sig /*[
                             int32_t* df /*[vocab]*/, float* idf /*[vocab]*/, int32_t* part /*[vocab]*/,
                             double* rnorm /*[k]*/);
 
-/* Persist an index (params, idf, references, signatures, Simhashes) to a
- * versioned binary file, and load it back onto ctx's device. */
+/* Persist an index (params, idf, references, signatures, Simhashes and, in
+ * the precision form, its E4M3 compare rows and their norms) to a versioned
+ * binary file, and load it back onto ctx's device (version 1 files, which
+ * lack the E4M3 rows, are re-packed from the unit signatures). */
 mrc_status mrc_index_save(mrc_ctx* ctx, const mrc_index* index, const char* path);
 mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out);
 /* Release an index. Its memory is returned in order on the stream of the context that

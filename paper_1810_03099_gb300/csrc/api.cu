@@ -308,11 +308,10 @@ float bf16_round(float f) {
   return f;
 }
 
-// The reference weight of term t: idf under TF-IDF (bfloat16-rounded in the precision form,
-// as the kernels use it), 1 under counts.
+// The reference weight of term t: idf under TF-IDF, 1 under counts.
 double reference_weight(const mrc_params& p, const float* idf, int32_t t) {
   if (p.weighting != MRC_WEIGHT_TFIDF) return 1.0;
-  return p.precision == MRC_PREC_BF16_FP8 ? bf16_round(idf[t]) : idf[t];
+  return idf[t];
 }
 
 // Reference selection (Section IV): terms ranked by df descending, ids ascending within equal
@@ -420,9 +419,9 @@ mrc_status alloc_index_arrays(mrc_ctx* ctx, mrc_index* x) {
   const bool fh = x->params.feature_hash != MRC_HASH_SPLITMIX64;
   const size_t sizes[] = {4 * V, 4 * V, 8 * V, 4 * k, 4 * n * k, 4 * n * k, 8 * n,
                           f16 ? 2 * n * (size_t)x->kp : 0, e4m3 ? n * (size_t)x->kp8 : 0, e4m3 ? 4 * n : 0,
-                          e4m3 ? 4 * ((n + 127) / 128) : 0, 8 * k, fh ? 8 * V : 0};
-  size_t off[13], total = 0;
-  for (int q = 0; q < 13; ++q) {
+                          e4m3 ? 4 * ((n + 127) / 128) : 0, 8 * k, fh ? 8 * V : 0, e4m3 ? 4 * k : 0};
+  size_t off[14], total = 0;
+  for (int q = 0; q < 14; ++q) {
     off[q] = total;
     total += (sizes[q] + 255) / 256 * 256;
   }
@@ -446,6 +445,7 @@ mrc_status alloc_index_arrays(mrc_ctx* ctx, mrc_index* x) {
   x->qnorm_min = e4m3 ? (float*)(b + off[10]) : nullptr;
   x->rnorm = (double*)(b + off[11]);
   x->fhash = fh ? (uint64_t*)(b + off[12]) : nullptr;
+  x->rinv16 = e4m3 ? (float*)(b + off[13]) : nullptr;
   if (fh) {  // the Simhash feature of every vocabulary term, computed once per index
     const cudaError_t e = launch_feature_table(ctx, x->vocab, x->params.seed, x->params.feature_hash, x->fhash);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "feature hash table");
@@ -457,11 +457,22 @@ mrc_status alloc_index_arrays(mrc_ctx* ctx, mrc_index* x) {
 // become the norms), the term table built on the device from the partition of every term
 // (part_stage: pinned, [vocab]) and the device idf. The copies read pinned staging, so the
 // context's host_ws_done event marks when the staging may be reused.
-mrc_status upload_references(mrc_ctx* ctx, mrc_index* x, const int32_t* part_stage, float* rinv_stage) {
+mrc_status upload_references(mrc_ctx* ctx, mrc_index* x, const int32_t* part_stage, float* rinv_stage,
+                             const float* h_idf) {
   const int32_t V = x->vocab;
   for (int32_t q = 0; q < x->k; ++q) {
     x->h_rnorm[q] = std::sqrt(x->h_rnorm[q]);
     rinv_stage[q] = x->h_rnorm[q] > 0 ? (float)(1.0 / x->h_rnorm[q]) : 0.f;
+  }
+  if (x->rinv16) {  // 1 / |R_p| of the bfloat16-rounded reference weights, summed in term-id order
+    std::vector<double> n16(x->k, 0.0);
+    for (int32_t t = 0; t < V; ++t) {
+      const int32_t q = part_stage[t];
+      if (q < 0 || q >= x->k) continue;
+      const double r = x->params.weighting == MRC_WEIGHT_TFIDF ? (double)bf16_round(h_idf[t]) : 1.0;
+      n16[q] += r * r;
+    }
+    for (int32_t q = 0; q < x->k; ++q) rinv_stage[x->k + q] = n16[q] > 0 ? (float)(1.0 / std::sqrt(n16[q])) : 0.f;
   }
   mrc_status st = MRC_OK;
   int32_t* d_part = (int32_t*)ws_get(ctx, "build.part", sizeof(int32_t) * V, &st);
@@ -469,9 +480,10 @@ mrc_status upload_references(mrc_ctx* ctx, mrc_index* x, const int32_t* part_sta
   cudaError_t e = cudaMemcpyAsync(d_part, part_stage, sizeof(int32_t) * V, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(x->rinv, rinv_stage, sizeof(float) * x->k, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess && x->rinv16)
+    e = cudaMemcpyAsync(x->rinv16, rinv_stage + x->k, sizeof(float) * x->k, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
-    e = launch_term_info(ctx, x->idf, d_part, V, x->params.weighting == MRC_WEIGHT_TFIDF,
-                         x->params.precision == MRC_PREC_BF16_FP8, x->tinfo);
+    e = launch_term_info(ctx, x->idf, d_part, V, x->params.weighting == MRC_WEIGHT_TFIDF, 0, x->tinfo);
   if (e == cudaSuccess && !ctx->host_ws_done) e = cudaEventCreateWithFlags(&ctx->host_ws_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->host_ws_done, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "uploading references");
@@ -655,9 +667,8 @@ mrc_status launch_index_signatures(mrc_ctx* ctx, mrc_index* x, const DocsDev& d)
   if (x->op_hi) cudaMemsetAsync(x->op_hi, 0, sizeof(uint16_t) * (size_t)x->n_docs * x->kp, ctx->stream);
   if (x->op_lo) cudaMemsetAsync(x->op_lo, 0, sizeof(uint16_t) * (size_t)x->n_docs * x->kp, ctx->stream);
   if (x->op_e4m3) cudaMemsetAsync(x->op_e4m3, 0, (size_t)x->n_docs * x->kp8, ctx->stream);
-  cudaError_t e = launch_signature(ctx, d, x->vocab, x->tinfo, x->rinv, x->k,
-                                   x->params.precision == MRC_PREC_BF16_FP8, x->params.seed,
-                                   x->fhash, index_sig_out(x));
+  cudaError_t e = launch_signature(ctx, d, x->vocab, x->tinfo, x->rinv, x->rinv16, x->k, x->params.seed, x->fhash,
+                                   index_sig_out(x));
   if (e == cudaSuccess && x->qnorm_min) e = launch_block_min(ctx, x->qnorm, x->n_docs, x->qnorm_min);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "signature pass");
   return MRC_OK;
@@ -720,11 +731,11 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
     unsigned long long* keys = (unsigned long long*)ws_get(ctx, "sel.keys", 8 * 8192, &st);
     int32_t* d_part = (int32_t*)ws_get(ctx, "build.part", sizeof(int32_t) * vocab, &st);
     if (st != MRC_OK) return bail(st);
-    const bool tfidf = params->weighting == MRC_WEIGHT_TFIDF, bf16 = params->precision == MRC_PREC_BF16_FP8;
+    const bool tfidf = params->weighting == MRC_WEIGHT_TFIDF;
     const int64_t L = params->L < 0 ? 32ll * params->k : params->L;
-    e = launch_select_region(ctx, x->df, vocab, d.n_docs, L, params->region_start, tfidf ? x->idf : nullptr, bf16,
-                             x->k, hist, above, sstate, keys, d_part, x->rnorm, x->rinv);
-    if (e == cudaSuccess) e = launch_term_info(ctx, x->idf, d_part, vocab, tfidf, bf16, x->tinfo);
+    e = launch_select_region(ctx, x->df, vocab, d.n_docs, L, params->region_start, tfidf ? x->idf : nullptr, 0,
+                             x->k, hist, above, sstate, keys, d_part, x->rnorm, x->rinv, x->rinv16);
+    if (e == cudaSuccess) e = launch_term_info(ctx, x->idf, d_part, vocab, tfidf, 0, x->tinfo);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "reference selection"));
     mark_index_tables(ctx, x);
     // one synchronisation, before the signature pass: the error word of the df pass, the
@@ -748,7 +759,7 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   }
   // host selection: df and idf read back to pinned staging, then the partition [vocab] and
   // 1 / |R_p| [k] staged for the device tables
-  char* stage = (char*)host_ws(ctx, 12 * (size_t)vocab + 4 * (size_t)x->k + 64, &st);
+  char* stage = (char*)host_ws(ctx, 12 * (size_t)vocab + 8 * (size_t)x->k + 64, &st);
   if (!stage) return bail(st);
   int32_t* h_df = (int32_t*)stage;
   float* h_idf = (float*)(stage + 4 * (size_t)vocab);
@@ -758,7 +769,8 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);  // synchronises the stream
   int32_t* part_stage = (int32_t*)(stage + 8 * (size_t)vocab);
   x->L_used = select_references(h_df, vocab, d.n_docs, *params, part_stage, h_idf, &x->h_rnorm);
-  if ((st = upload_references(ctx, x, part_stage, (float*)(stage + 12 * (size_t)vocab))) != MRC_OK) return bail(st);
+  if ((st = upload_references(ctx, x, part_stage, (float*)(stage + 12 * (size_t)vocab), h_idf)) != MRC_OK)
+    return bail(st);
   mark_index_tables(ctx, x);
   if ((st = launch_index_signatures(ctx, x, d)) != MRC_OK) return bail(st);
   // The df pass already validated these documents (offsets, lengths, token ids) and the
@@ -843,9 +855,8 @@ mrc_status mrc_signature(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* d
   o.sig = sig_host ? (float*)ws_get(ctx, "sig.out", sizeof(float) * (size_t)n * index->k, &st) : sig;
   o.simhash = sh_host ? (uint64_t*)ws_get(ctx, "sig.simhash", sizeof(uint64_t) * (size_t)n, &st) : simhash;
   if (st != MRC_OK) return st;
-  cudaError_t e = launch_signature(ctx, d, index->vocab, index->tinfo, index->rinv, index->k,
-                                   index->params.precision == MRC_PREC_BF16_FP8, index->params.seed,
-                                   index->fhash, o);
+  cudaError_t e = launch_signature(ctx, d, index->vocab, index->tinfo, index->rinv, nullptr, index->k,
+                                   index->params.seed, index->fhash, o);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "signature pass");
   if ((st = check_err_word(ctx, d_err)) != MRC_OK) return st;
   if (sig_host) e = cudaMemcpyAsync(sig, o.sig, sizeof(float) * (size_t)n * index->k, cudaMemcpyDeviceToHost, ctx->stream);
@@ -929,6 +940,7 @@ static mrc_status match_impl(mrc_ctx* ctx, const mrc_index* index, const float* 
   }
   g.thresh = tau - (prec == MRC_PREC_FP32 ? kF16CompareBound : index->params.margin);
   if (!ctx->rescore) {  // diagnostics: the compare's candidates are the result
+    g.exact_scores = 1;
     g.pairs = dst;
     g.count = pc;
     g.capacity = capacity;
@@ -1442,7 +1454,16 @@ mrc_status mrc_index_save(mrc_ctx* ctx, const mrc_index* x, const char* path) {
     std::fclose(f);
     return cuda_fail(ctx, cudaGetLastError(), "index save");
   }
-  const int32_t version = 1;
+  // version 2 appends the precision form's E4M3 operand rows and their norms (they come from
+  // the bfloat16-weight signatures, which the file does not hold otherwise)
+  std::vector<uint8_t> op8(x->op_e4m3 ? n * (size_t)x->kp8 : 0);
+  std::vector<float> qn(x->op_e4m3 ? n : 0);
+  if (x->op_e4m3 && (cudaMemcpy(op8.data(), x->op_e4m3, op8.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                     cudaMemcpy(qn.data(), x->qnorm, sizeof(float) * n, cudaMemcpyDeviceToHost) != cudaSuccess)) {
+    std::fclose(f);
+    return cuda_fail(ctx, cudaGetLastError(), "index save");
+  }
+  const int32_t version = 2;
   bool ok = std::fwrite(kMagic, 1, 8, f) == 8;
   ok = ok && std::fwrite(&version, sizeof(version), 1, f) == 1;
   ok = ok && std::fwrite(&x->params, sizeof(mrc_params), 1, f) == 1;
@@ -1455,6 +1476,8 @@ mrc_status mrc_index_save(mrc_ctx* ctx, const mrc_index* x, const char* path) {
   ok = ok && std::fwrite(sig.data(), sizeof(float), sig.size(), f) == sig.size();
   ok = ok && std::fwrite(unit.data(), sizeof(float), unit.size(), f) == unit.size();
   ok = ok && std::fwrite(sh.data(), sizeof(uint64_t), n, f) == n;
+  ok = ok && std::fwrite(op8.data(), 1, op8.size(), f) == op8.size();
+  ok = ok && std::fwrite(qn.data(), sizeof(float), qn.size(), f) == qn.size();
   std::fclose(f);
   if (!ok) return fail(ctx, MRC_ERR_INVALID, std::string("write failed: ") + path);
   return MRC_OK;
@@ -1470,7 +1493,7 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
   int32_t version = 0;
   mrc_index* x = new mrc_index();
   bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0;
-  ok = ok && std::fread(&version, sizeof(version), 1, f) == 1 && version == 1;
+  ok = ok && std::fread(&version, sizeof(version), 1, f) == 1 && (version == 1 || version == 2);
   ok = ok && std::fread(&x->params, sizeof(mrc_params), 1, f) == 1;
   ok = ok && std::fread(&x->n_docs, sizeof(int64_t), 1, f) == 1;
   ok = ok && std::fread(&x->vocab, sizeof(int32_t), 1, f) == 1;
@@ -1480,6 +1503,8 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
   std::vector<float> sig, unit, hidf;
   std::vector<int32_t> hdf, hpart;
   std::vector<uint64_t> sh;
+  std::vector<uint8_t> op8;
+  std::vector<float> qn;
   if (ok) {
     x->k = x->params.k;
     x->kp = padded_kp(x->k);
@@ -1499,6 +1524,12 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
     ok = ok && std::fread(sig.data(), sizeof(float), sig.size(), f) == sig.size();
     ok = ok && std::fread(unit.data(), sizeof(float), unit.size(), f) == unit.size();
     ok = ok && std::fread(sh.data(), sizeof(uint64_t), n, f) == n;
+    if (ok && version >= 2 && x->params.precision == MRC_PREC_BF16_FP8) {
+      op8.resize(n * (size_t)x->kp8);
+      qn.resize(n);
+      ok = std::fread(op8.data(), 1, op8.size(), f) == op8.size();
+      ok = ok && std::fread(qn.data(), sizeof(float), n, f) == n;
+    }
   }
   std::fclose(f);
   if (!ok) {
@@ -1521,7 +1552,7 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
   if (e == cudaSuccess) e = cudaMemcpy(x->sig_unit, unit.data(), sizeof(float) * unit.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(x->simhash, sh.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "index load"));
-  char* stage = (char*)host_ws(ctx, 4 * (size_t)x->vocab + 4 * (size_t)x->k + 64, &st);
+  char* stage = (char*)host_ws(ctx, 4 * (size_t)x->vocab + 8 * (size_t)x->k + 64, &st);
   if (!stage) return bail(st);
   x->h_rnorm.assign(x->k, 0.0);
   for (int32_t t = 0; t < x->vocab; ++t) {
@@ -1533,14 +1564,22 @@ mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
     }
   }
   std::memcpy(stage, hpart.data(), sizeof(int32_t) * x->vocab);
-  if ((st = upload_references(ctx, x, (int32_t*)stage, (float*)(stage + 4 * (size_t)x->vocab))) != MRC_OK)
+  if ((st = upload_references(ctx, x, (int32_t*)stage, (float*)(stage + 4 * (size_t)x->vocab), hidf.data())) != MRC_OK)
     return bail(st);
   // compare operands are re-packed from the unit signatures
   if (x->op_hi) cudaMemsetAsync(x->op_hi, 0, 2 * n * x->kp, ctx->stream);
   if (x->op_lo) cudaMemsetAsync(x->op_lo, 0, 2 * n * x->kp, ctx->stream);
   if (x->op_e4m3) cudaMemsetAsync(x->op_e4m3, 0, n * x->kp8, ctx->stream);
-  e = launch_pack(ctx, x->sig_unit, x->n_docs, x->k, 0, x->op_hi, x->op_lo, x->op_e4m3, x->qnorm, nullptr,
-                  x->op_hi ? x->kp : 0, x->op_e4m3 ? x->kp8 : 0);
+  if (!op8.empty()) {  // the stored E4M3 rows (version 2), else re-packed from the unit signatures
+    e = cudaMemcpyAsync(x->op_e4m3, op8.data(), op8.size(), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(x->qnorm, qn.data(), sizeof(float) * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && x->op_hi)
+      e = launch_pack(ctx, x->sig_unit, x->n_docs, x->k, 0, x->op_hi, x->op_lo, nullptr, nullptr, nullptr, x->kp, 0);
+  } else {
+    e = launch_pack(ctx, x->sig_unit, x->n_docs, x->k, 0, x->op_hi, x->op_lo, x->op_e4m3, x->qnorm, nullptr,
+                    x->op_hi ? x->kp : 0, x->op_e4m3 ? x->kp8 : 0);
+  }
   if (e == cudaSuccess && x->qnorm_min) e = launch_block_min(ctx, x->qnorm, x->n_docs, x->qnorm_min);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "index load packing"));

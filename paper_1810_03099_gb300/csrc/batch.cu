@@ -5,7 +5,9 @@
 // the signature database, Section I / Section IV):
 //   signature pass (bag of terms, TF-IDF, cosine to each reference partition; unit
 //   signature and compare operands written directly) -> tensor-core compare of the
-//   batch against the whole index at a lowered threshold -> FP32 rescoring.
+//   batch against the whole index at a lowered threshold -> FP32 rescoring -> pairs grouped
+//   by query; with a fingerprint index attached, the batch's Simhashes then probe it
+//   (Hamming pairs, grouped by query as well).
 // The whole pipeline is captured once into a CUDA graph on the batch's own stream, for
 // exactly max_docs documents; a batch of fewer documents is padded with empty ones
 // (zero signatures, which match nothing). Each batch is then one graph launch, after
@@ -38,7 +40,18 @@ struct mrc_batch {
   int32_t* d_qfill = nullptr;              // [max_docs] scatter cursors
   unsigned long long* d_counts = nullptr;  // [0] pairs, [1] candidates
   int32_t* d_err = nullptr;
-  unsigned long long* h_counts = nullptr;  // pinned: [0] pairs [1] candidates [2] error word
+  unsigned long long* h_counts = nullptr;  // pinned: [0] pairs [1] candidates [2] error word [3] Hamming pairs
+  uint64_t* d_simhash = nullptr;           // [max_docs] the batch's Simhash fingerprints
+  // Hamming leg (mrc_batch_attach_simhash): the batch's fingerprints probe a block-table index
+  const mrc_simhash_index* shx = nullptr;
+  int32_t hmax = 0;
+  int64_t h_capacity = 0;
+  mrc_pair* d_hpairs = nullptr;
+  mrc_pair* d_hgrouped = nullptr;
+  int64_t* d_hqoff = nullptr;
+  int32_t* d_hqcnt = nullptr;
+  int32_t* d_hqfill = nullptr;
+  unsigned long long* d_hcount = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t done = nullptr;
   bool pending = false;
@@ -121,6 +134,7 @@ cudaError_t record(mrc_batch* b) {
   d.err = b->d_err;
   SigOut o{};
   o.sig_unit = b->d_unit;
+  o.simhash = b->d_simhash;
   if (prec == MRC_PREC_BF16_FP8) {
     o.op_e4m3 = b->d_op;
     o.qnorm = b->d_qnorm;
@@ -129,7 +143,8 @@ cudaError_t record(mrc_batch* b) {
     o.op_hi = b->d_op;
     o.kp = x->kp;
   }
-  e = launch_signature(ctx, d, x->vocab, x->tinfo, x->rinv, x->k, 0, x->params.seed, x->fhash, o);
+  // query operands from FP32 weights, as mrc_match packs the signatures of mrc_signature
+  e = launch_signature(ctx, d, x->vocab, x->tinfo, x->rinv, nullptr, x->k, x->params.seed, x->fhash, o);
   if (e != cudaSuccess) return e;
   GemmArgs g{};
   g.na = b->max_docs;
@@ -165,7 +180,44 @@ cudaError_t record(mrc_batch* b) {
   k_group_scan<<<1, 1024, 0, ctx->stream>>>(b->d_qcnt, b->max_docs, b->d_qoff, b->d_qfill);
   k_group_scatter<<<grid, 256, 0, ctx->stream>>>(b->d_pairs, b->d_counts, b->capacity, b->d_qoff, b->d_qfill,
                                                  b->d_grouped);
+  if (b->shx) {
+    // Hamming leg: the batch's fingerprints (padding documents included: they are empty, and
+    // their pairs fall after the real queries' once grouped) against the block-table index
+    const mrc_simhash_index* h = b->shx;
+    e = cudaMemsetAsync(b->d_hcount, 0, sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_hqcnt, 0, sizeof(int32_t) * (size_t)b->max_docs, ctx->stream);
+    if (e != cudaSuccess) return e;
+    e = launch_simhash_index_probe(ctx, b->d_simhash, b->max_docs, false, b->hmax, h->layout, h->n, h->fp, h->id,
+                                   h->off, b->d_hpairs, b->d_hcount, b->h_capacity);
+    if (e != cudaSuccess) return e;
+    k_group_count<<<grid, 256, 0, ctx->stream>>>(b->d_hpairs, b->d_hcount, b->h_capacity, b->d_hqcnt);
+    k_group_scan<<<1, 1024, 0, ctx->stream>>>(b->d_hqcnt, b->max_docs, b->d_hqoff, b->d_hqfill);
+    k_group_scatter<<<grid, 256, 0, ctx->stream>>>(b->d_hpairs, b->d_hcount, b->h_capacity, b->d_hqoff,
+                                                   b->d_hqfill, b->d_hgrouped);
+  }
   return cudaGetLastError();
+}
+
+// Runs the pipeline once uncaptured (sizing every workspace buffer), then captures it into
+// the batch's graph (replacing an earlier one).
+cudaError_t capture(mrc_batch* b) {
+  cudaStream_t s = b->ctx->stream;
+  cudaError_t e = record(b);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaGraph_t graph = nullptr;
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    const cudaError_t er = record(b);
+    e = cudaStreamEndCapture(s, &graph);
+    if (er != cudaSuccess) e = er;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return e;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = exec;
+  return cudaSuccess;
 }
 
 void release(mrc_batch* b) {
@@ -173,8 +225,10 @@ void release(mrc_batch* b) {
   if (b->ctx) cudaStreamSynchronize(b->ctx->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->done) cudaEventDestroy(b->done);
-  void* ptrs[] = {b->d_offsets, b->d_tokens, b->d_unit,  b->d_op,  b->d_qnorm, b->d_cand,   b->d_pairs,
-                  b->d_grouped, b->d_qoff,   b->d_qcnt, b->d_qfill, b->d_counts, b->d_err};
+  void* ptrs[] = {b->d_offsets, b->d_tokens, b->d_unit,    b->d_op,     b->d_qnorm,   b->d_cand,
+                  b->d_pairs,   b->d_grouped, b->d_qoff,   b->d_qcnt,   b->d_qfill,   b->d_counts,
+                  b->d_err,     b->d_simhash, b->d_hpairs, b->d_hgrouped, b->d_hqoff, b->d_hqcnt,
+                  b->d_hqfill,  b->d_hcount};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->h_counts) cudaFreeHost(b->h_counts);
@@ -237,6 +291,7 @@ mrc_status mrc_batch_create(mrc_ctx* ctx, const mrc_index* index, int64_t max_do
   if (e == cudaSuccess) e = cudaMalloc(&b->d_qfill, sizeof(int32_t) * (size_t)max_docs);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_simhash, sizeof(uint64_t) * (size_t)max_docs);
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_counts, 4 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_offsets, 0, sizeof(int64_t) * (size_t)(max_docs + 1), s);
@@ -247,17 +302,7 @@ mrc_status mrc_batch_create(mrc_ctx* ctx, const mrc_index* index, int64_t max_do
     return st;
   }
   // one uncaptured run sizes every workspace buffer; then the same work is captured
-  e = record(b);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaGraph_t graph = nullptr;
-  if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
-  if (e == cudaSuccess) {
-    const cudaError_t er = record(b);
-    e = cudaStreamEndCapture(s, &graph);
-    if (er != cudaSuccess) e = er;
-  }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
-  if (graph) cudaGraphDestroy(graph);
+  e = capture(b);
   if (e != cudaSuccess) {
     mrc_status st = cuda_fail(ctx, e, "capturing the batch pipeline");
     release(b);
@@ -302,6 +347,8 @@ mrc_status mrc_batch_launch(mrc_batch* b, const mrc_docs* docs) {
     e = cudaMemcpyAsync(b->h_counts, b->d_counts, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->h_counts + 2, b->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess && b->shx)
+    e = cudaMemcpyAsync(b->h_counts + 3, b->d_hqoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaEventRecord(b->done, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "mrc_batch_launch");
   b->pending = true;
@@ -349,6 +396,57 @@ mrc_status mrc_batch_wait(mrc_batch* b, mrc_pair* pairs, int64_t capacity, int64
   }
   if (total > std::min(capacity, b->capacity))
     return fail(ctx, MRC_ERR_CAPACITY, "more pairs than capacity; *n_pairs holds the total");
+  return MRC_OK;
+}
+
+mrc_status mrc_batch_attach_simhash(mrc_batch* b, const mrc_simhash_index* index, int32_t hamming_max,
+                                    int64_t capacity) {
+  if (!b) return MRC_ERR_INVALID;
+  mrc_ctx* ctx = b->ctx;
+  cudaSetDevice(ctx->device);
+  if (b->pending) return fail(ctx, MRC_ERR_INVALID, "mrc_batch_attach_simhash: a launch is in flight");
+  if (!index || capacity < 1 || hamming_max < 0 || hamming_max > index->hamming_max)
+    return fail(ctx, MRC_ERR_INVALID, "mrc_batch_attach_simhash: NULL index, capacity < 1 or a distance above the "
+                                      "index's");
+  if (index->device != ctx->device) return fail(ctx, MRC_ERR_INVALID, "the fingerprint index is on another device");
+  if (b->shx) return fail(ctx, MRC_ERR_INVALID, "mrc_batch_attach_simhash: a fingerprint index is attached already");
+  cudaError_t e = cudaMalloc(&b->d_hpairs, sizeof(mrc_pair) * (size_t)capacity);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_hgrouped, sizeof(mrc_pair) * (size_t)capacity);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_hqoff, sizeof(int64_t) * (size_t)(b->max_docs + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_hqcnt, sizeof(int32_t) * (size_t)b->max_docs);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_hqfill, sizeof(int32_t) * (size_t)b->max_docs);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_hcount, sizeof(unsigned long long));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "mrc_batch_attach_simhash allocations");
+  b->shx = index;
+  b->hmax = hamming_max;
+  b->h_capacity = capacity;
+  e = capture(b);
+  if (e != cudaSuccess) {
+    b->shx = nullptr;
+    return cuda_fail(ctx, e, "capturing the batch pipeline with its Hamming leg");
+  }
+  return MRC_OK;
+}
+
+mrc_status mrc_batch_hamming(mrc_batch* b, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs,
+                             int64_t* query_offsets) {
+  if (!b) return MRC_ERR_INVALID;
+  mrc_ctx* ctx = b->ctx;
+  if (n_pairs) *n_pairs = 0;
+  if (!b->shx) return fail(ctx, MRC_ERR_INVALID, "mrc_batch_hamming: no fingerprint index attached");
+  if (b->pending) return fail(ctx, MRC_ERR_INVALID, "mrc_batch_hamming: wait for the launch first");
+  cudaSetDevice(ctx->device);
+  int64_t total = 0;  // the real queries' pairs: grouped by query, they come first
+  std::memcpy(&total, b->h_counts + 3, sizeof(int64_t));
+  if (n_pairs) *n_pairs = total;
+  const int64_t m = std::min<int64_t>(std::min<int64_t>(total, b->h_capacity), capacity);
+  cudaError_t e = cudaSuccess;
+  if (m > 0 && pairs) e = cudaMemcpy(pairs, b->d_hgrouped, sizeof(mrc_pair) * (size_t)m, cudaMemcpyDefault);
+  if (e == cudaSuccess && query_offsets)
+    e = cudaMemcpy(query_offsets, b->d_hqoff, sizeof(int64_t) * (size_t)(b->last_n + 1), cudaMemcpyDefault);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "copying Hamming pairs");
+  if (total > std::min(capacity, b->h_capacity))
+    return fail(ctx, MRC_ERR_CAPACITY, "more Hamming pairs than capacity; *n_pairs holds the total");
   return MRC_OK;
 }
 

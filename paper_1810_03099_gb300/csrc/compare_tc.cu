@@ -79,6 +79,7 @@ struct GemmParams {
   int32_t row_rr;  // resident kernel, triangle: whole row blocks dealt round-robin (see TileSeq)
   const int32_t* kblocks_dev;  // streaming kernel: K blocks read from the device (see GemmArgs)
   uint64_t timeout_ns;         // bound of every pipeline wait (the context's wait limit)
+  int32_t exact;               // E4M3: exact candidate test and quantized-cosine scores (see emit_chunk)
   int32_t stall;               // failure-detection test: the MMA issuer issues nothing, so the
                                // other roles' waits for its results run out (mrc_ctx_set_test_stall)
 };
@@ -255,26 +256,26 @@ __device__ __forceinline__ void flush_pairs(const GemmParams& p, const mrc_pair*
 // Threshold one 32-column chunk held in registers (v[e] = score of column j0 + e for this
 // lane's row i) and append its pairs. Fast path: the chunk's maximum misses fast_thresh in
 // every lane. Otherwise each lane builds the 32-bit mask of its hits straight from its
-// registers (a hit: v[e] >= hit_lim; E4M3: v[e] >= hit_lim * |q_j|, the column norms staged
-// once per warp, zero norms never hitting), applies the bounds and the triangle's j > i with
-// bit arithmetic, and scores each hit with the compare's own cosine (fp16: the accumulator;
-// E4M3: the cosine of the quantized vectors), staged in this lane's row of the warp's 32 x 33
-// area. The warp then appends its hits to its pair buffer. Callers that need FP32 scores
-// rescore these candidates.
+// registers and applies the bounds and the triangle's j > i with bit arithmetic. fp16: a hit
+// is v[e] >= hit_lim, scored with v[e]. E4M3: a hit passes the row's block bound
+// (fast_thresh, which uses the smallest column norm of the 128-column block); the caller
+// rescores every hit in FP32, so the raw accumulator is its score. With p.exact (the
+// candidates themselves are the result) each such hit is tested exactly,
+// v[e] >= hit_lim * |q_j| with the column's norm (zero norms never hit), and scored with the
+// cosine of the quantized vectors. The warp then appends its hits to its pair buffer.
 template <int FMT>
 __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)[32], int64_t i, int64_t j0, int lane,
-                                           float fast_thresh, float row_norm, float hit_lim, float* nstage,
-                                           float* stage, mrc_pair* buf, int& nbuf) {
+                                           float fast_thresh, float row_norm, float hit_lim, float* stage,
+                                           mrc_pair* buf, int& nbuf) {
   const float m = max32(v);
   if (!__any_sync(kFull, m >= fast_thresh)) return;
   uint32_t mask = 0;
   if (FMT == OP_E4M3) {
-    const float nj = j0 + lane < p.nb ? __ldg(p.b_norm + j0 + lane) : 0.f;
-    nstage[lane] = nj > 0.f ? nj : __int_as_float(0x7f800000);
-    __syncwarp();
+    // the block bound first (no per-column data); the exact test v >= hit_lim |q_j| follows
+    // for the few columns that pass it; zero norms never hit
     if (row_norm > 0.f) {
 #pragma unroll
-      for (int e = 0; e < 32; ++e) mask |= (v[e] >= hit_lim * nstage[e] ? 1u : 0u) << e;
+      for (int e = 0; e < 32; ++e) mask |= (v[e] >= fast_thresh ? 1u : 0u) << e;
     }
   } else {
 #pragma unroll
@@ -288,12 +289,24 @@ __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)
     else if (dlt >= 0) mask &= ~((2u << dlt) - 1u);
   }
   if (i >= p.na) mask = 0u;
-  const uint32_t hits = mask;
-  float* sc = stage + lane * 33;  // the raw scores, for the emission loop's per-hit index
-  if (hits) {
+  // the lane's scores go to its row of the warp's 32 x 33 staging area, so that the loops
+  // below index them at run time (compact code: they run only for the rare chunks with hits)
+  float* sc = stage + lane * 33;
+  if (mask) {
 #pragma unroll
     for (int e = 0; e < 32; ++e) sc[e] = v[e];
+    if (FMT == OP_E4M3 && p.exact) {
+      for (uint32_t hh = mask; hh; hh &= hh - 1u) {
+        const int e = __ffs(hh) - 1;
+        const float nj = __ldg(p.b_norm + j0 + e);
+        if (nj > 0.f && sc[e] >= hit_lim * nj)
+          sc[e] = sc[e] * p.out_scale / (row_norm * nj);  // the cosine of the quantized vectors
+        else
+          mask &= ~(1u << e);
+      }
+    }
   }
+  const uint32_t hits = mask;
   const int cnt = __popc(hits);
   int incl = cnt;
 #pragma unroll
@@ -318,7 +331,7 @@ __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)
       mrc_pair pr;
       pr.i = (int32_t)i;
       pr.j = (int32_t)(j0 + e);
-      pr.score = FMT == OP_E4M3 ? sc[e] * p.out_scale / (row_norm * nstage[e]) : sc[e];
+      pr.score = sc[e];
       if (!direct)
         buf[nbuf + at] = pr;
       else if (base + at < (unsigned long long)p.capacity)
@@ -348,12 +361,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* drain = acc_empty + 2;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
-  float* stage_all = reinterpret_cast<float*>(drain + 4);  // [4 epilogue warps][32 x 33 + 32]
-  mrc_pair* pbuf_all = reinterpret_cast<mrc_pair*>(stage_all + 4 * (32 * 33 + 32));  // [4][kPairBuf]
+  float* stage_all = reinterpret_cast<float*>(drain + 4);  // [4 epilogue warps][32 x 33] scores
+  mrc_pair* pbuf_all = reinterpret_cast<mrc_pair*>(stage_all + 4 * 32 * 33);  // [4][kPairBuf]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* stage = stage_all + (warp >= 2 ? warp - 2 : 0) * (32 * 33 + 32);
-  float* nstage = stage + 32 * 33;
+  float* stage = stage_all + (warp >= 2 ? warp - 2 : 0) * 32 * 33;
   mrc_pair* pbuf = pbuf_all + (warp >= 2 ? warp - 2 : 0) * kPairBuf;
   int nbuf = 0;
   if (threadIdx.x == 0) {
@@ -541,7 +553,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         } else {
-          emit_chunk<FMT>(p, v, i, j0, lane, fast_thresh, row_norm, hit_lim, nstage, stage, pbuf, nbuf);
+          emit_chunk<FMT>(p, v, i, j0, lane, fast_thresh, row_norm, hit_lim, stage, pbuf, nbuf);
         }
       }
       tc_fence_before();
@@ -565,12 +577,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 // contiguous, row-major range of tiles, so consecutive tiles share their A rows: A is
 // loaded once per row block into one of two resident buffers and only B streams through
 // a 4-stage ring. Eight epilogue warps (two per TMEM lane quarter) split the columns.
-constexpr int kResThreads = 320;  // warp 0 TMA, warp 1 MMA + TMEM, warps 2..9 epilogue
+constexpr int kResEpiWarps = 8;  // two per TMEM lane quarter, each half of the tile's columns
+constexpr int kResThreads = 64 + 32 * kResEpiWarps;  // warp 0 TMA, warp 1 MMA + TMEM, then the epilogue
 // Depth of the streamed-B ring: as many stages as shared memory holds next to the two A
 // buffers and the epilogue's staging. The B tiles come from L2 with a latency of about
 // a microsecond, so a CTA needs that many bytes in flight to stream at the rate its tensor core
 // consumes them (E4M3 tiles are half the size of fp16 ones and go by twice as fast). 3 to 12.
-constexpr size_t kResEpiBytes = 8 * (32 * 33 + 32) * sizeof(float) + 8 * kPairBuf * sizeof(mrc_pair);
+constexpr size_t kResEpiBytes = kResEpiWarps * (32 * 33 * sizeof(float) + kPairBuf * sizeof(mrc_pair));
 __host__ __device__ constexpr int res_stages_b(int nops, int rb, int bn) {
   return (int)(((227u * 1024u - 1024u - kResEpiBytes - 512u) - 2u * nops * kBM * rb) / ((size_t)nops * bn * rb)) > 12
              ? 12
@@ -689,12 +702,11 @@ __global__ void __launch_bounds__(kResThreads, 1)
   uint64_t* drain = acc_empty + NB;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
-  float* stage_all = reinterpret_cast<float*>(drain + 4);  // [8 warps][32 x 33 + 32]
-  mrc_pair* pbuf_all = reinterpret_cast<mrc_pair*>(stage_all + 8 * (32 * 33 + 32));  // [8][kPairBuf]
+  float* stage_all = reinterpret_cast<float*>(drain + 4);  // [epilogue warps][32 x 33] scores
+  mrc_pair* pbuf_all = reinterpret_cast<mrc_pair*>(stage_all + kResEpiWarps * 32 * 33);  // [epilogue warps][kPairBuf]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* stage = stage_all + (warp >= 2 ? warp - 2 : 0) * (32 * 33 + 32);
-  float* nstage = stage + 32 * 33;
+  float* stage = stage_all + (warp >= 2 ? warp - 2 : 0) * 32 * 33;
   mrc_pair* pbuf = pbuf_all + (warp >= 2 ? warp - 2 : 0) * kPairBuf;
   int nbuf = 0;
   const int64_t t_begin = p.n_tiles * blockIdx.x / gridDim.x;
@@ -706,7 +718,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
     }
     for (int b = 0; b < NB; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 8);
+      mbar_init(&acc_empty[b], kResEpiWarps);
     }
     for (int s = 0; s < kResStagesB; ++s) {
       mbar_init(&b_full[s], 1);
@@ -817,36 +829,46 @@ __global__ void __launch_bounds__(kResThreads, 1)
   } else {
     // ------------------------------------------------------------ epilogue (8 warps)
     const int q = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int half = (warp - 2) >> 2;  // which half of the tile's columns
+    constexpr int CH = BN / 64;        // 32-column chunks per warp
     int64_t it = 0;
-    TileSeq<BN> seq(t_begin, t_end);
-    int64_t bi, bj;
-    while (seq.next(p, bi, bj)) {
+    TileSeq<BN> ahead(t_begin, t_end);
+    int64_t bi, bj, nbi = -1, nbj = -1;
+    bool have_next = ahead.next(p, nbi, nbj);
+    // E4M3: the score is the cosine of the quantized vectors, acc * out_scale / (|q_i| |q_j|);
+    // raw accumulators below thresh * |q_i| * min_j |q_j| / out_scale (minimum over the warp's
+    // 128-column block) cannot reach the threshold (fast path). The row's values change only
+    // with the row block; the block minimum of the next tile is loaded one tile ahead.
+    int64_t row_of = -1;
+    float row_norm = 1.f, hit_lim = p.thresh, row_bound = p.thresh;
+    const int64_t nbk = (p.nb + 127) >> 7;
+    auto block_min = [&](int64_t cj) {
+      const int64_t b = ((cj * BN) >> 7) + ((half * CH * 32) >> 7);
+      return b < nbk ? __ldg(p.b_norm_min + b) : 1.f;
+    };
+    float nmin_next = (FMT == OP_E4M3 && have_next) ? block_min(nbj) : 1.f;
+    while (have_next) {
+      bi = nbi;
+      bj = nbj;
+      const float nmin = nmin_next;
+      have_next = ahead.next(p, nbi, nbj);
+      if (FMT == OP_E4M3 && have_next) nmin_next = block_min(nbj);
       const uint32_t ab = (uint32_t)(it % NB);
+      const int64_t i = bi * kBM + q * 32 + lane;
+      if (FMT == OP_E4M3 && bi != row_of) {
+        row_of = bi;
+        row_norm = i < p.na ? __ldg(p.a_norm + i) : 0.f;
+        hit_lim = p.thresh * row_norm / p.out_scale;
+        row_bound = p.thresh > 0.f ? (row_norm > 0.f ? hit_lim : __int_as_float(0x7f800000))
+                                   : -__int_as_float(0x7f800000);
+      }
       int ok = 1;
       if (lane == 0) ok = mbar_wait(&acc_full[ab], (uint32_t)((it / NB) & 1), abort_flag, p.err, p.timeout_ns) ? 1 : 0;
       ok = __shfl_sync(kFull, ok, 0);
       if (!ok) break;
       tc_fence_after();
-      const int64_t i = bi * kBM + q * 32 + lane;
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + ab * (uint32_t)(C::ACCS * BN);
-      // E4M3: the score is the cosine of the quantized vectors, acc * out_scale / (|q_i| |q_j|);
-      // raw accumulators below thresh * |q_i| * min_j |q_j| / out_scale (minimum over the
-      // chunk's 128-column block) cannot reach the threshold (fast path)
-      float row_norm = 1.f, row_bound = p.thresh, nmin0 = 1.f, nmin1 = 1.f, hit_lim = p.thresh;
-      if (FMT == OP_E4M3) {  // issued before the TMEM loads so that their latencies overlap
-        row_norm = i < p.na ? __ldg(p.a_norm + i) : 0.f;
-        const int64_t b0 = (bj * BN) >> 7, nbk = (p.nb + 127) >> 7;
-        nmin0 = b0 < nbk ? __ldg(p.b_norm_min + b0) : 1.f;
-        if (BN > 128) nmin1 = b0 + 1 < nbk ? __ldg(p.b_norm_min + b0 + 1) : 1.f;
-        hit_lim = p.thresh * row_norm / p.out_scale;
-        if (p.thresh > 0.f)
-          row_bound = row_norm > 0.f ? hit_lim : __int_as_float(0x7f800000);
-        else
-          row_bound = -__int_as_float(0x7f800000);
-      }
       // all of this warp's TMEM loads are issued before one wait, so they overlap
-      constexpr int CH = BN / 64;  // 32-column chunks per warp (half of the tile)
       float v[CH][32];
 #pragma unroll
       for (int c = 0; c < CH; ++c) tmem_ld32(trow + (half * CH + c) * 32, v[c]);
@@ -866,11 +888,10 @@ __global__ void __launch_bounds__(kResThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[ab]);
-      // a warp's columns lie in one 128-column block (half 0: the first, half 1: the second), so one
-      // fast threshold covers all its chunks; the usual case, no lane near it in any chunk, costs
-      // the maxima (a tree of three-input maxima per chunk) and one vote
-      float fast_thresh = row_bound;
-      if (FMT == OP_E4M3 && p.thresh > 0.f) fast_thresh = row_bound * ((((half * CH) * 32) >> 7) ? nmin1 : nmin0);
+      // a warp's columns lie in one 128-column block, so one fast threshold covers all its
+      // chunks; the usual case, no lane near it in any chunk, costs the maxima (a tree of
+      // three-input maxima per chunk) and one vote
+      const float fast_thresh = (FMT == OP_E4M3 && p.thresh > 0.f) ? row_bound * nmin : row_bound;
       float mall = max32(v[0]);
 #pragma unroll
       for (int c = 1; c < CH; ++c) mall = fmaxf(mall, max32(v[c]));
@@ -878,7 +899,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
           const int64_t j0 = bj * BN + (half * CH + c) * 32;
-          emit_chunk<FMT>(p, v[c], i, j0, lane, fast_thresh, row_norm, hit_lim, nstage, stage, pbuf, nbuf);
+          emit_chunk<FMT>(p, v[c], i, j0, lane, fast_thresh, row_norm, hit_lim, stage, pbuf, nbuf);
         }
       }
       ++it;
@@ -960,6 +981,7 @@ cudaError_t run_gemm_resident(mrc_ctx* ctx, const GemmArgs& g) {
   p.capacity = g.capacity;
   p.err = g.err;
   p.timeout_ns = ctx->wait_limit_ns;
+  p.exact = g.exact_scores;
   p.stall = ctx->test_stall ? 1 : 0;
   // round-robin rows whenever there are at least two rounds of row blocks to balance: the CTAs
   // then share each streamed tile through L2 even when the operand would fit there (300,000
@@ -1027,8 +1049,9 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   p.err = g.err;
   p.kblocks_dev = g.kblocks_dev;
   p.timeout_ns = ctx->wait_limit_ns;
+  p.exact = g.exact_scores;
   p.stall = ctx->test_stall ? 1 : 0;
-  const size_t smem = 1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256 + 4 * (32 * 33 + 32) * 4 +
+  const size_t smem = 1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256 + 4 * 32 * 33 * 4 +
                       4 * kPairBuf * sizeof(mrc_pair);
   if (resident_ctas(k_gemm_compare<FMT>, kThreads, smem) <= 0) return cudaErrorInvalidConfiguration;
   int64_t grid = ctx->num_sms;

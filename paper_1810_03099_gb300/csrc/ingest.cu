@@ -272,7 +272,8 @@ struct IngestParams {
   const TermInfo* tinfo;
   const float* rinv;
   int32_t k;
-  int32_t bf16w;
+  int32_t bf16w;         // precision form: also the signature of bfloat16 weights, for the E4M3 operand
+  const float* rinv16;   // [k] 1 / |R_p| of the bfloat16 reference weights (with bf16w)
   uint64_t seed;
   const uint64_t* fhash;  // [vocab] feature hashes (MD5 / SHA-1 modes); NULL: SplitMix64 of (t ^ seed)
   SigOut sig;
@@ -291,12 +292,12 @@ struct IngestParams {
 // in the bound-pruned mode, one 32-bit sum per tail bucket (two per word).
 template <int MODE>
 __host__ __device__ __forceinline__ int ingest_kq(const IngestParams& p) {
-  return MODE == kSIG ? p.k : (MODE == kDENSE && !p.dense.postings ? kTailBuckets / 2 : 0);
+  return MODE == kSIG ? (p.bf16w ? 2 * p.k : p.k) : (MODE == kDENSE && !p.dense.postings ? kTailBuckets / 2 : 0);
 }
 
 // Per-group accumulators of the SIG and DENSE modes.
 struct Acc {
-  unsigned long long norm;
+  unsigned long long norm, norm16;  // norm16: squared norm of the bfloat16-weight vector (bf16w)
   uint32_t plo, phi;
 };
 
@@ -366,12 +367,17 @@ __device__ __forceinline__ void chunk(const IngestParams& p, uint32_t key, uint3
       }
     }
     if (valid) {
-      // the term table holds idf (or 1 under count weighting; bfloat16-rounded idf in the
-      // precision form); c * idf is exact in FP32 for bfloat16 idf (c < 2^16)
+      // the term table holds idf (or 1 under count weighting)
       const float r = aux.w;
       const float w = (float)c * r;
       a.norm += to_fix(w * w);
       if (aux.code >= 0) atomicAdd(&num_q[aux.code], to_fix(w * r));
+      if (p.bf16w) {  // the same with the weight rounded to bfloat16 (c * r16 is exact in FP32)
+        const float r16 = __bfloat162float(__float2bfloat16_rn(r));
+        const float w16 = (float)c * r16;
+        a.norm16 += to_fix(w16 * w16);
+        if (aux.code >= 0) atomicAdd(&num_q[p.k + aux.code], to_fix(w16 * r16));
+      }
     }
     return;
   }
@@ -412,20 +418,31 @@ __device__ __forceinline__ void write_bucket_norms(const IngestParams& p, int64_
     row[q] = __float2half_rn(__fsqrt_ru(__uint2float_ru(sums[q]) * (1.0f / 2147483648.0f)));
 }
 
-// Writes the SIG outputs of one document; called by one full warp.
+// Writes the SIG outputs of one document; called by one full warp. With bf16w, the E4M3
+// operand and its norm come from the unit signature of the bfloat16-weight vector (numerators
+// num_q[k + p], squared norm norm16_q, reference norms rinv16); everything else from FP32 weights.
 __device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsigned long long norm_q,
-                             const unsigned long long* num_q, uint32_t plo, uint32_t phi, int lane) {
+                             unsigned long long norm16_q, const unsigned long long* num_q, uint32_t plo, uint32_t phi,
+                             int lane) {
   const float nrm = sqrtf((float)norm_q * kInvFix);
+  const float nrm16 = p.bf16w ? sqrtf((float)norm16_q * kInvFix) : 0.f;
   // raw signature s_p = t_p / |d|, t_p = num_p / |R_p|; the unit signature is s / |s|,
   // computed exactly as the packing of stored raw signatures computes it
-  float ss = 0.f;
+  float ss = 0.f, ss16 = 0.f;
   for (int q = lane; q < p.k; q += 32) {
     const float t = (float)num_q[q] * kInvFix * p.rinv[q];
     const float sv = nrm > 0.f ? t / nrm : 0.f;
     ss += sv * sv;
+    if (p.bf16w) {
+      const float t16 = (float)num_q[p.k + q] * kInvFix * p.rinv16[q];
+      const float sv16 = nrm16 > 0.f ? t16 / nrm16 : 0.f;
+      ss16 += sv16 * sv16;
+    }
   }
   ss = warp_sum(ss);
   const float sn = sqrtf(ss);
+  float sn16 = 0.f;
+  if (p.bf16w) sn16 = sqrtf(warp_sum(ss16));
   const int width = max(p.k, max(p.sig.kp, p.sig.kp8));
   float q2 = 0.f;  // squared norm of the E4M3-quantized unit signature
   for (int q = lane; q < width; q += 32) {
@@ -444,7 +461,13 @@ __device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsi
             __float2half_rn((u - __half2float(hi)) * kSplitLoScale);
     }
     if (q < p.sig.kp8 && p.sig.op_e4m3) {
-      const __nv_fp8_storage_t e = __nv_cvt_float_to_fp8(u * kE4M3Scale, __NV_SATFINITE, __NV_E4M3);
+      float u8 = u;
+      if (p.bf16w) {
+        const float t16 = q < p.k ? (float)num_q[p.k + q] * kInvFix * p.rinv16[q] : 0.f;
+        const float sv16 = nrm16 > 0.f ? t16 / nrm16 : 0.f;
+        u8 = (q < p.k && sn16 > 0.f) ? sv16 / sn16 : 0.f;
+      }
+      const __nv_fp8_storage_t e = __nv_cvt_float_to_fp8(u8 * kE4M3Scale, __NV_SATFINITE, __NV_E4M3);
       reinterpret_cast<uint8_t*>(p.sig.op_e4m3)[d * p.sig.kp8 + q] = (uint8_t)e;
       const float v = __half2float(__half(__nv_cvt_fp8_to_halfraw(e, __NV_E4M3))) * (1.0f / kE4M3Scale);
       q2 += v * v;
@@ -555,7 +578,7 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
         if (lane == 0) p.bag_n[d] = nnz;
       }
     }
-    Acc a{0ull, 0u, 0u};
+    Acc a{0ull, 0ull, 0u, 0u};
     float inv_norm = 0.f;
     if (MODE == kDENSE) inv_norm = inv_norm_of(p.dense.norm[d]);
     if (MODE != kDF || p.bag_read) {
@@ -584,7 +607,7 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
       }
     }
     __syncwarp();
-    if (MODE == kSIG) finalize_sig(p, d, len, warp_sum(a.norm), num_q, a.plo, a.phi, lane);
+    if (MODE == kSIG) finalize_sig(p, d, len, warp_sum(a.norm), warp_sum(a.norm16), num_q, a.plo, a.phi, lane);
     if (MODE == kDFN) {
       const unsigned long long nq = warp_sum(a.norm);
       if (lane == 0) p.norm_out[d] = nq;
@@ -608,7 +631,7 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
 // passes, each keeping the terms of one hash partition (a second hash of the term id), so the
 // table runs about half full. The list of occupied slots has room for every slot.
 __host__ __device__ __forceinline__ size_t long_group_bytes(int kq) {
-  return (size_t)kq * 8 + 8 + 64 * 4 + 16 + (size_t)kLongSlots * 8 + (size_t)kLongSlots * 2;
+  return (size_t)kq * 8 + 16 + 64 * 4 + 16 + (size_t)kLongSlots * 8 + (size_t)kLongSlots * 2;
 }
 
 __device__ __forceinline__ void group_sync(int g) {
@@ -663,8 +686,8 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_ingest_long(IngestParams p)
   const int kq = ingest_kq<MODE>(p);
   uint8_t* base = smem + long_group_bytes(kq) * g;
   unsigned long long* num_q = reinterpret_cast<unsigned long long*>(base);
-  unsigned long long* norm_s = num_q + kq;
-  uint32_t* P = reinterpret_cast<uint32_t*>(norm_s + 1);  // [64] Simhash column sums
+  unsigned long long* norm_s = num_q + kq;  // [0] |d|^2, [1] of the bfloat16 weights
+  uint32_t* P = reinterpret_cast<uint32_t*>(norm_s + 2);  // [64] Simhash column sums
   int32_t* misc = reinterpret_cast<int32_t*>(P + 64);     // [0] document, [1] row count, [2] bag size, [3] list size
   unsigned long long* tab = reinterpret_cast<unsigned long long*>(misc + 4);
   uint16_t* list = reinterpret_cast<uint16_t*>(tab + kLongSlots);
@@ -683,11 +706,12 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_ingest_long(IngestParams p)
     for (int q = gt; q < kq; q += kGroupThreads) num_q[q] = 0ull;
     if (gt < 64) P[gt] = 0u;
     if (gt == 0) {
-      *norm_s = 0ull;
+      norm_s[0] = 0ull;
+      norm_s[1] = 0ull;
       misc[1] = 0;
       misc[2] = 0;
     }
-    Acc a{0ull, 0u, 0u};
+    Acc a{0ull, 0ull, 0u, 0u};
     float inv_norm = 0.f;
     if (MODE == kDENSE) inv_norm = inv_norm_of(p.dense.norm[d]);
     if (p.bag_read) {
@@ -754,17 +778,21 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_ingest_long(IngestParams p)
       const unsigned long long nq = warp_sum(a.norm);
       if (lane == 0 && nq) atomicAdd(norm_s, nq);
     }
+    if (MODE == kSIG && p.bf16w) {
+      const unsigned long long nq = warp_sum(a.norm16);
+      if (lane == 0 && nq) atomicAdd(norm_s + 1, nq);
+    }
     if (MODE == kSIG) {
       atomicAdd(&P[lane], a.plo);
       atomicAdd(&P[lane + 32], a.phi);
     }
     group_sync(g);
-    if (MODE == kSIG && gw == 0) finalize_sig(p, d, len, *norm_s, num_q, P[lane], P[lane + 32], lane);
+    if (MODE == kSIG && gw == 0) finalize_sig(p, d, len, norm_s[0], norm_s[1], num_q, P[lane], P[lane + 32], lane);
     if (MODE == kDENSE) {
       if (gt == 0) p.dense.row_cnt[d] = misc[1];
       if (!p.dense.postings) write_bucket_norms(p, d, num_q, gt, kGroupThreads);
     }
-    if (MODE == kDFN && gt == 0) p.norm_out[d] = *norm_s;
+    if (MODE == kDFN && gt == 0) p.norm_out[d] = norm_s[0];
     if (p.bag_write && gt == 0) p.bag_n[d] = misc[2];
     group_sync(g);
   }
@@ -1041,15 +1069,15 @@ cudaError_t launch_idf(mrc_ctx* ctx, int64_t n_docs, const int32_t* df, int32_t 
 }
 
 cudaError_t launch_signature(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo,
-                                     const float* rinv, int32_t k, int32_t bf16_weights, uint64_t seed,
-                                     const uint64_t* fhash,
-                                     const SigOut& out) {
+                             const float* rinv, const float* rinv16, int32_t k, uint64_t seed, const uint64_t* fhash,
+                             const SigOut& out) {
   IngestParams p = base_params(d);
   p.vocab = vocab;
   p.tinfo = tinfo;
   p.rinv = rinv;
   p.k = k;
-  p.bf16w = bf16_weights;
+  p.bf16w = rinv16 && out.op_e4m3 ? 1 : 0;
+  p.rinv16 = rinv16;
   p.seed = seed;
   p.fhash = fhash;
   p.sig = out;
@@ -1105,7 +1133,7 @@ namespace mrc {
 // caller instead of the context's workspace. lists: [2 * cap] int32; counts: [32] int32;
 // err: [1] int32; all device memory, n_docs <= cap. *host_err receives the error word.
 cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo,
-                                     const float* rinv, int32_t k, int32_t bf16_weights, uint64_t seed,
+                                     const float* rinv, int32_t k, uint64_t seed,
                                      const uint64_t* fhash,
                                      const SigOut& out, int32_t* lists, int64_t cap, int32_t* counts, int32_t* err,
                                      int32_t* host_err) {
@@ -1116,7 +1144,7 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
   p.tinfo = tinfo;
   p.rinv = rinv;
   p.k = k;
-  p.bf16w = bf16_weights;
+  p.bf16w = 0;
   p.seed = seed;
   p.fhash = fhash;
   p.sig = out;

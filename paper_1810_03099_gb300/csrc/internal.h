@@ -108,6 +108,7 @@ struct mrc_index {
   float* idf = nullptr;           // [vocab]
   mrc::TermInfo* tinfo = nullptr; // [vocab]
   float* rinv = nullptr;          // [k] 1 / |R_p| (0 for empty partitions)
+  float* rinv16 = nullptr;        // [k] the same of the bfloat16 weights (precision form only)
   float* sig = nullptr;           // [n * k] raw signatures
   float* sig_unit = nullptr;      // [n * k] unit signatures (FP32 rescoring)
   uint64_t* simhash = nullptr;    // [n]
@@ -186,7 +187,8 @@ struct DocsDev {
 // select.cu
 // REGION reference selection on the device from df [V]: partition of every term into part
 // [V] (-1 unselected), |R_p| into rnorm [k] (double) and 1 / |R_p| into rinv [k]; idf NULL
-// under count weighting, bf16: weights rounded to bfloat16 (precision form). Scratch: hist
+// under count weighting, bf16: weights rounded to bfloat16; rinv16 (may be NULL): 1 / |R_p| of
+// the bfloat16-rounded weights (the precision form's compare operands). Scratch: hist
 // and above [n_docs + 2] int32, state [device_selection_words()] int64, keys [8192] uint64.
 // state[5] = band size, state[6] = 1 if the band exceeded 8192 terms (part, rnorm and rinv
 // are then not written: select on the host), state[1] = L.
@@ -194,7 +196,7 @@ int64_t device_selection_words();
 cudaError_t launch_select_region(mrc_ctx* ctx, const int32_t* df, int32_t V, int64_t n_docs, int64_t L,
                                  int64_t region_start, const float* idf, int32_t bf16, int32_t k, int32_t* hist,
                                  int32_t* above, long long* state, unsigned long long* keys, int32_t* part,
-                                 double* rnorm, float* rinv);
+                                 double* rnorm, float* rinv, float* rinv16);
 
 // ingest.cu
 cudaError_t launch_df(mrc_ctx* ctx, const DocsDev& d, int32_t* df, int32_t vocab);
@@ -218,8 +220,11 @@ struct SigOut {
   float* qnorm;        // [n] norm of the quantized E4M3 unit signature (may be null)
   int32_t kp, kp8;
 };
+// Signature pass. The stored signatures (sig, sig_unit, fp16 operands) use the FP32 term table;
+// with rinv16 (the precision form), the E4M3 operand and its norm come from signatures of the
+// same documents whose weights and reference weights are rounded to bfloat16.
 cudaError_t launch_signature(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo, const float* rinv,
-                             int32_t k, int32_t bf16_weights, uint64_t seed, const uint64_t* fhash,
+                             const float* rinv16, int32_t k, uint64_t seed, const uint64_t* fhash,
                              const SigOut& out);
 // Character 3-grams of a text CSR (text.cu): gram_offsets [n_docs + 1], grams [capacity] (ids past
 // capacity dropped); tile_doc, tile_cnt [text_gram_tiles(n_bytes)], group_sum [ceil(tiles / 1024)],
@@ -300,6 +305,9 @@ struct GemmArgs {
   const char* name;     // timing name (NULL: by format and epilogue)
   const int32_t* kblocks_dev;  // non-null: the number of 64-element K blocks, read from the device
                                // (kbytes is then the row stride and the K extent of the maps)
+  int32_t exact_scores;  // E4M3 thresholding: 1 = exact per-column test and quantized-cosine
+                         // scores (the candidates are the result); 0 = the block bound alone,
+                         // raw accumulators (every candidate is rescored afterwards)
 };
 cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g);
 // FP32 rescoring of the first min(*n_cand, cand_cap) candidates (unit_dot of rows i of qunit

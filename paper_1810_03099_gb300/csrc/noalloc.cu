@@ -25,7 +25,7 @@
 
 namespace mrc {
 cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t vocab, const TermInfo* tinfo,
-                                     const float* rinv, int32_t k, int32_t bf16_weights, uint64_t seed,
+                                     const float* rinv, int32_t k, uint64_t seed,
                                      const uint64_t* fhash, const SigOut& out, int32_t* lists, int64_t cap, int32_t* counts, int32_t* err,
                                      int32_t* host_err);
 }  // namespace mrc
@@ -112,7 +112,6 @@ extern "C" mrc_status mrc_signature_noalloc(mrc_ctx* ctx, const mrc_index* index
   o.simhash = simhash;
   int32_t herr = 0;
   const cudaError_t e = mrc::launch_signature_scratch(ctx, d, index->vocab, index->tinfo, index->rinv, index->k,
-                                                      index->params.precision == MRC_PREC_BF16_FP8,
                                                       index->params.seed, index->fhash, o, lists, kMaxDocs,
                                                       counts, err, &herr);
   if (e != cudaSuccess) return mrc::cuda_fail(ctx, e, "mrc_signature_noalloc");

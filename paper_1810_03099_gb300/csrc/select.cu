@@ -216,10 +216,12 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_sort(const int32_t* __r
 }
 
 // One CTA: partition q holds selection positions [floor(qL/k), floor((q+1)L/k)); |R_q|^2 is
-// summed by one thread in rank order, in double.
+// summed by one thread in rank order, in double. With rinv16, the same norms of the
+// bfloat16-rounded weights (the precision form's compare operands) as well.
 __global__ void __launch_bounds__(kSelThreads) k_ref_norms(const long long* __restrict__ state,
                                                          const float* __restrict__ rsel, int32_t k,
-                                                         double* __restrict__ rnorm, float* __restrict__ rinv) {
+                                                         double* __restrict__ rnorm, float* __restrict__ rinv,
+                                                         float* __restrict__ rinv16) {
   __shared__ float sr[kBandMax];
   if (state[kSsStatus] != 0) return;
   const long long L = state[kSsVhi] < 0 ? 0 : state[kSsL];
@@ -235,6 +237,14 @@ __global__ void __launch_bounds__(kSelThreads) k_ref_norms(const long long* __re
     const double nr = sqrt(s);
     rnorm[q] = nr;
     rinv[q] = nr > 0.0 ? (float)(1.0 / nr) : 0.f;
+    if (rinv16) {
+      double s16 = 0.0;
+      for (long long pos = p0; pos < p1; ++pos) {
+        const double r = (double)__bfloat162float(__float2bfloat16_rn(sr[pos]));
+        s16 += r * r;
+      }
+      rinv16[q] = s16 > 0.0 ? (float)(1.0 / sqrt(s16)) : 0.f;
+    }
   }
 }
 
@@ -245,7 +255,7 @@ int64_t device_selection_words() { return kSsWords; }
 cudaError_t launch_select_region(mrc_ctx* ctx, const int32_t* df, int32_t V, int64_t n_docs, int64_t L,
                                  int64_t region_start, const float* idf, int32_t bf16, int32_t k, int32_t* hist,
                                  int32_t* above, long long* state, unsigned long long* keys, int32_t* part,
-                                 double* rnorm, float* rinv) {
+                                 double* rnorm, float* rinv, float* rinv16) {
   if (V <= 0 || k <= 0) return cudaErrorInvalidValue;
   // keys: 64 KB of scratch = band ids [kBandMax] + reference weights by position [kBandMax]
   uint32_t* ids = reinterpret_cast<uint32_t*>(keys);
@@ -276,7 +286,7 @@ cudaError_t launch_select_region(mrc_ctx* ctx, const int32_t* df, int32_t V, int
                                                                                        k, part, rsel);
   }
   KernelTimer kt(ctx, "select_norms");
-  k_ref_norms<<<1, kSelThreads, 0, ctx->stream>>>(state, rsel, k, rnorm, rinv);
+  k_ref_norms<<<1, kSelThreads, 0, ctx->stream>>>(state, rsel, k, rnorm, rinv, rinv16);
   return cudaGetLastError();
 }
 

@@ -102,6 +102,8 @@ _SIGNATURES = {
     "mrc_batch_poll": (C.c_int32, [C.c_void_p]),
     "mrc_batch_wait": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
     "mrc_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "mrc_batch_attach_simhash": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64]),
+    "mrc_batch_hamming": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
     "mrc_batch_free": (None, [C.c_void_p]),
 }
 
@@ -307,6 +309,7 @@ class Batch:
         else:
             buf = out
         n = 0 if self._keep is None else int(self._keep[0].shape[0]) - 1
+        self._last_n = n
         qoff = np.zeros(n + 1, np.int64)
         total = C.c_int64()
         st = self.ctx.lib.mrc_batch_wait(self.handle, _ptr(buf), int(buf.shape[0]), C.byref(total),
@@ -315,6 +318,26 @@ class Batch:
         self._check(st)
         m = min(int(total.value), buf.shape[0])
         pairs = buf[:m].copy() if own else buf[:m]
+        return (pairs, int(total.value), qoff) if offsets else (pairs, int(total.value))
+
+    def attach_simhash(self, shindex: "SimhashIndex", hamming_max: int | None = None, capacity: int = 1 << 16):
+        """Add the Hamming leg: each launch also probes `shindex` with the batch's Simhashes."""
+        hm = shindex.hamming_max if hamming_max is None else int(hamming_max)
+        self._check(self.ctx.lib.mrc_batch_attach_simhash(self.handle, shindex.handle, hm, int(capacity)))
+        self.h_capacity = int(capacity)
+        self._shindex = shindex  # the batch keeps the fingerprint index in use
+
+    def hamming(self, offsets=False):
+        """After wait(): the last launch's Hamming pairs (query position, index position, distance),
+        grouped by query; with offsets=True also where each query's pairs start."""
+        n = getattr(self, "_last_n", 0)
+        if getattr(self, "_hout", None) is None:
+            self._hout = np.empty(self.h_capacity, PAIR_DTYPE)
+        qoff = np.zeros(n + 1, np.int64)
+        total = C.c_int64()
+        self._check(self.ctx.lib.mrc_batch_hamming(self.handle, _ptr(self._hout), int(self._hout.shape[0]),
+                                                   C.byref(total), qoff.ctypes.data if offsets else None))
+        pairs = self._hout[:min(int(total.value), self._hout.shape[0])].copy()
         return (pairs, int(total.value), qoff) if offsets else (pairs, int(total.value))
 
     def free(self):

@@ -9,6 +9,9 @@ host loop
     others are still on the GPU overlap on the device;
   * completes slots as their GPU work finishes (non-blocking polls) and stamps
     every request's latency (completion minus arrival).
+With a block-table fingerprint index of the resident documents' Simhashes, every slot also
+matches its requests' Simhashes against it (Hamming pairs per request, beside the
+signature pairs).
 The number of slots is admitted against free HBM at start-up: a slot is only
 created while its device footprint fits in ``hbm_fraction`` of the free memory.
 Each document's result does not depend on the other documents of its batch
@@ -32,6 +35,7 @@ class Request:
     arrival: float
     done: float = -1.0
     pairs: np.ndarray = field(default_factory=lambda: np.empty(0, mrc.PAIR_DTYPE))  # (i, j, score) rows
+    hamming: np.ndarray = field(default_factory=lambda: np.empty(0, mrc.PAIR_DTYPE))  # (i, j, distance) rows
 
 
 def slot_footprint(index, max_docs: int, max_tokens: int, capacity: int) -> int:
@@ -47,7 +51,8 @@ def slot_footprint(index, max_docs: int, max_tokens: int, capacity: int) -> int:
 class Server:
     def __init__(self, ctx, index, tau: float = 0.9, micro_batch: int = 128, deadline_s: float = 1e-3,
                  slots: int = 4, max_doc_tokens: int = 10000, capacity: int = 1 << 16, hbm_fraction: float = 0.5,
-                 tile_n: int = 0, free_bytes: int | None = None):
+                 tile_n: int = 0, free_bytes: int | None = None, simhash_index=None, hamming_max: int | None = None,
+                 hamming_capacity: int = 1 << 16):
         import torch
         self.ctx, self.index, self.tau = ctx, index, tau
         self.micro_batch, self.deadline_s = micro_batch, deadline_s
@@ -60,6 +65,10 @@ class Server:
             raise MemoryError("not enough free device memory for one pipeline slot")
         self.slots = [mrc.Batch(ctx, index, micro_batch, self.max_tokens, tau, capacity, tile_n)
                       for _ in range(self.admitted_slots)]
+        self.hamming = simhash_index is not None
+        if self.hamming:  # each slot also matches its requests' Simhashes against the resident ones
+            for b in self.slots:
+                b.attach_simhash(simhash_index, hamming_max, hamming_capacity)
         self.busy: list[list[Request] | None] = [None] * len(self.slots)
         # pinned staging per slot (stream-ordered copies read them until the batch finishes)
         self.h_off = [torch.empty(micro_batch + 1, dtype=torch.int64).pin_memory() for _ in self.slots]
@@ -80,9 +89,13 @@ class Server:
         # the pipeline returns the batch's pairs grouped by request, with each request's start
         pairs, _, qoff = self.slots[s].wait(offsets=True)
         reqs = self.busy[s]
+        if self.hamming:
+            hp, _, hoff = self.slots[s].hamming(offsets=True)
         for q, r in enumerate(reqs):
             r.done = now
             r.pairs = pairs[qoff[q]:qoff[q + 1]]
+            if self.hamming:
+                r.hamming = hp[hoff[q]:hoff[q + 1]]
         self.busy[s] = None
 
     def run(self, docs: list[np.ndarray], arrivals: np.ndarray) -> list[Request]:

@@ -45,7 +45,7 @@ def _queries(c, n, seed):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_batch_matches_oracle_and_eager(env, precision):
     mrc, ctx, c, orc, torch = env["mrc"], env["ctx"], env["c"], env["orc"], env["torch"]
-    p = Params(k=32, bf16=precision == 1)
+    p = Params(k=32)  # stored signatures and rescoring use FP32 weights in every form
     ref = build_index(c.offsets, c.tokens, c.vocab, p, orc)
     idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, mrc.params_default(k=32, precision=precision))
     qo, qt = _queries(c, 100, 5)
@@ -72,6 +72,9 @@ def test_batch_matches_oracle_and_eager(env, precision):
         assert o >= tau - 1e-5 and abs(sc - o) <= 1e-5
     missed = [pr for pr, o in od.items() if pr not in gd and o > tau + 1e-5]
     assert len(missed) <= (0 if precision == 0 else 0.01 * len(od))
+    # against the FP64 pair set: recall and precision >= 0.99
+    g, o = set(gd), set(od)
+    assert len(g & o) >= 0.99 * len(o) and len(g & o) >= 0.99 * len(g)
     idx.free()
 
 
@@ -127,4 +130,41 @@ def test_serving_admission_by_free_memory(env):
     s.free()
     with pytest.raises(MemoryError):
         serving.Server(ctx, idx, micro_batch=32, slots=8, max_doc_tokens=5000, hbm_fraction=1.0, free_bytes=foot - 1)
+    idx.free()
+
+
+def test_serving_signature_and_hamming_pairs_match_oracle(env):
+    """The serving form with its Hamming leg: against a resident index (FP16 signatures) and a
+    block-table index of its Simhashes, every served request gets its signature pairs (the
+    oracle's query x index pair set, equal except within 1e-5 of tau; scores within 1e-5) and
+    its Hamming pairs (bit-exact: the oracle's fingerprints of the request against the index's,
+    distance <= 3)."""
+    mrc, ctx, c, orc, torch = env["mrc"], env["ctx"], env["c"], env["orc"], env["torch"]
+    from paper_1810_03099_gb300 import serving
+    p = Params(k=32)
+    ref = build_index(c.offsets, c.tokens, c.vocab, p, orc)
+    idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, mrc.params_default(k=32, precision=2))
+    fps = mrc.index_simhash(ctx, idx, torch.empty(c.n_docs, dtype=torch.int64, device="cuda"))
+    shx = mrc.simhash_index_build(ctx, fps, 3)
+    n = 240
+    qo, qt = _queries(c, n, 17)
+    docs = [qt[qo[i]:qo[i + 1]] for i in range(n)]
+    srv = serving.Server(ctx, idx, 0.9, micro_batch=32, deadline_s=2e-4, slots=3, max_doc_tokens=5000,
+                         simhash_index=shx, hamming_max=3)
+    reqs = srv.run(docs, synth.poisson_arrivals(100000.0, n, seed=5))
+    Sq, Fq, _ = signature(ref, qo, qt, orc)
+    tot, pi, pj, ps = orc.sig_match(Sq, ref.S, 0.9)
+    od = pair_dict(pi, pj, ps)
+    gd = {(r.rid, int(j)): float(s) for r in reqs for j, s in zip(r.pairs["j"], r.pairs["score"])}
+    for pr, sc in gd.items():
+        o = od.get(pr, orc.cos_dense(Sq[pr[0]], ref.S[pr[1]]))
+        assert o >= 0.9 - 1e-5 and abs(sc - o) <= 1e-5, (pr, sc, o)
+    assert all(pr in gd for pr, o in od.items() if o > 0.9 + 1e-5)
+    htot, hi, hj, hh = orc.hamming_pairs(Fq, ref.F, 3)
+    want = sorted(zip(hi.tolist(), hj.tolist(), hh.tolist()))
+    got = sorted((r.rid, int(j), int(s)) for r in reqs for j, s in zip(r.hamming["j"], r.hamming["score"]))
+    assert got == want and htot > 20
+    assert tot > 20
+    srv.free()
+    shx.free()
     idx.free()
