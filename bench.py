@@ -150,7 +150,7 @@ def _oracle_step(to, sub, vocab, tau, hmax):
     """One oracle step on a host corpus: index build, all signature pairs, all Simhash pairs."""
     from oracle.oracle import Params
     t0 = time.perf_counter()
-    ref = to.build_index(sub.offsets, sub.tokens, vocab, Params(k=K, tau=tau, hamming_max=hmax, bf16=True))
+    ref = to.build_index(sub.offsets, sub.tokens, vocab, Params(k=K, tau=tau, hamming_max=hmax))
     t1 = time.perf_counter()
     n_sig = to.sig_pairs(ref.S, tau)[0]
     n_sh = to.hamming_pairs(ref.F, hmax)[0]
@@ -186,7 +186,7 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": f"{HEADLINE}: first {sub.n_docs} of 1,000,000 documents of the recipe (2^18 "
-                                   f"terms, Zipf 1.05, median 300 tokens), k={K}, bf16 weights, all signature pairs "
+                                   f"terms, Zipf 1.05, median 300 tokens), k={K}, FP64, all signature pairs "
                                    f"tau={TAU} + all Simhash pairs h<={HMAX}",
                        "parallelism": f"{to.threads} host threads"},
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": "docs/s", "cores": to.threads,
@@ -632,7 +632,8 @@ def accuracy_vs_fp64(c, ctx):
         return np.einsum("ij,ij->i", U[i], U[j])
 
     out = {"docs": SUBSET_DOCS, "pairs_fp64": int(tot), "tau": TAU, "margin": MARGIN,
-           "reading": "precision form: idf / reference weights stored as bfloat16, signature arithmetic FP32"}
+           "reading": "precision form: E4M3 compare operands from bfloat16 idf / reference weights; stored "
+                      "signatures and the FP32 rescoring from FP32 weights"}
     for name, prec in (("bf16_fp8", 1), ("fp32", 0)):
         idx = mrc.mrc_build_index(ctx, sub.offsets, sub.tokens, c.vocab, mrc.params_default(k=K, precision=prec))
         ex = mrc.mrc_index_export(ctx, idx)
@@ -715,7 +716,7 @@ def run_headline(args, rank, world, local):
     ctx = mrc.Context(stream.cuda_stream)
     params = {1: mrc.params_default(k=K, tau=TAU, precision=1, margin=MARGIN, hamming_max=HMAX),
               0: mrc.params_default(k=K, tau=TAU, precision=0, hamming_max=HMAX)}
-    cap, sh_cap = 1 << 25, 1 << 23
+    cap, sh_cap = 1 << 25, 1 << 24
     pbuf = torch.empty((cap, 3), dtype=torch.int32, device="cuda")
     shbuf = torch.empty((sh_cap, 3), dtype=torch.int32, device="cuda")
     dcount = torch.zeros(1, dtype=torch.int64, device="cuda")

@@ -29,7 +29,16 @@ def host_cores() -> int:
 
 
 def cpu_model() -> str:
-    """The host CPU's model name (or its architecture when /proc/cpuinfo names none)."""
+    """The host CPU's model name (lscpu's, else /proc/cpuinfo's, else the architecture)."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip().lower() == "model name":
+                return f"{line.split(':', 1)[1].strip()} ({platform.machine()})"
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
@@ -38,7 +47,6 @@ def cpu_model() -> str:
                     return line.split(":", 1)[1].strip()
     except OSError:
         pass
-    import platform
     return platform.machine()
 
 

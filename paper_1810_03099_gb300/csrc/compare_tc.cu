@@ -264,11 +264,10 @@ __device__ __forceinline__ void flush_pairs(const GemmParams& p, const mrc_pair*
 // v[e] >= hit_lim * |q_j| with the column's norm (zero norms never hit), and scored with the
 // cosine of the quantized vectors. The warp then appends its hits to its pair buffer.
 template <int FMT>
-__device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)[32], int64_t i, int64_t j0, int lane,
-                                           float fast_thresh, float row_norm, float hit_lim, float* stage,
+__device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)[32], float m, int64_t i, int64_t j0,
+                                           int lane, float fast_thresh, float row_norm, float hit_lim, float* stage,
                                            mrc_pair* buf, int& nbuf) {
-  const float m = max32(v);
-  if (!__any_sync(kFull, m >= fast_thresh)) return;
+  if (!__any_sync(kFull, m >= fast_thresh)) return;  // m: this lane's maximum over the chunk
   uint32_t mask = 0;
   if (FMT == OP_E4M3) {
     // the block bound first (no per-column data); the exact test v >= hit_lim |q_j| follows
@@ -553,7 +552,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         } else {
-          emit_chunk<FMT>(p, v, i, j0, lane, fast_thresh, row_norm, hit_lim, stage, pbuf, nbuf);
+          emit_chunk<FMT>(p, v, max32(v), i, j0, lane, fast_thresh, row_norm, hit_lim, stage, pbuf, nbuf);
         }
       }
       tc_fence_before();
@@ -577,7 +576,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // contiguous, row-major range of tiles, so consecutive tiles share their A rows: A is
 // loaded once per row block into one of two resident buffers and only B streams through
 // a 4-stage ring. Eight epilogue warps (two per TMEM lane quarter) split the columns.
-constexpr int kResEpiWarps = 8;  // two per TMEM lane quarter, each half of the tile's columns
+constexpr int kResEpiWarps = 8;  // epilogue warps: two per TMEM lane quarter, each half of the tile's columns
 constexpr int kResThreads = 64 + 32 * kResEpiWarps;  // warp 0 TMA, warp 1 MMA + TMEM, then the epilogue
 // Depth of the streamed-B ring: as many stages as shared memory holds next to the two A
 // buffers and the epilogue's staging. The B tiles come from L2 with a latency of about
@@ -827,10 +826,13 @@ __global__ void __launch_bounds__(kResThreads, 1)
       mbar_drain(drain, 0, p.err);
     }
   } else {
-    // ------------------------------------------------------------ epilogue (8 warps)
+    // ------------------------------------------------------------ epilogue
+    // kResEpiWarps / 4 warps per TMEM lane quarter, each a contiguous share of the columns
+    constexpr int PARTS = kResEpiWarps / 4;
+    constexpr int CH = BN / 32 / PARTS;  // 32-column chunks per warp
+    static_assert(CH >= 1 && CH * 32 * PARTS == BN, "columns split evenly over the epilogue warps");
     const int q = warp & 3;
-    const int half = (warp - 2) >> 2;  // which half of the tile's columns
-    constexpr int CH = BN / 64;        // 32-column chunks per warp
+    const int half = (warp - 2) >> 2;  // which share of the tile's columns
     int64_t it = 0;
     TileSeq<BN> ahead(t_begin, t_end);
     int64_t bi, bj, nbi = -1, nbj = -1;
@@ -892,14 +894,17 @@ __global__ void __launch_bounds__(kResThreads, 1)
       // chunks; the usual case, no lane near it in any chunk, costs the maxima (a tree of
       // three-input maxima per chunk) and one vote
       const float fast_thresh = (FMT == OP_E4M3 && p.thresh > 0.f) ? row_bound * nmin : row_bound;
-      float mall = max32(v[0]);
+      float mc[CH];
 #pragma unroll
-      for (int c = 1; c < CH; ++c) mall = fmaxf(mall, max32(v[c]));
+      for (int c = 0; c < CH; ++c) mc[c] = max32(v[c]);
+      float mall = mc[0];
+#pragma unroll
+      for (int c = 1; c < CH; ++c) mall = fmaxf(mall, mc[c]);
       if (__any_sync(kFull, mall >= fast_thresh)) {
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
           const int64_t j0 = bj * BN + (half * CH + c) * 32;
-          emit_chunk<FMT>(p, v[c], i, j0, lane, fast_thresh, row_norm, hit_lim, stage, pbuf, nbuf);
+          emit_chunk<FMT>(p, v[c], mc[c], i, j0, lane, fast_thresh, row_norm, hit_lim, stage, pbuf, nbuf);
         }
       }
       ++it;

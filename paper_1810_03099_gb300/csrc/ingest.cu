@@ -261,7 +261,8 @@ struct IngestParams {
   const int32_t* short_list;
   const int32_t* long_list;
   const int32_t* list_counts;  // [0] short, [1] long
-  int32_t* long_cursor;        // dynamic grab of long documents
+  int32_t* long_cursor;        // dynamic grab of long documents (group path)
+  int32_t* huge_cursor;        // dynamic grab of the longest documents (CTA-wide)
   int32_t* short_cursor;       // dynamic grab of short documents (one warp each)
   int32_t* err;
   // DF (and DFN: df plus squared norms)
@@ -509,14 +510,18 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
   int32_t* misc = reinterpret_cast<int32_t*>(list + kShortMax);  // [0] list size, [1] row count
   const Transposer tr(lane);
 
+  // A pass that reads stored bags needs no table, so it takes every document here, the
+  // long-document list (longest first) before the short one; a hashing pass takes the short
+  // documents only (the long ones go to the group path).
   const int32_t n_short = p.list_counts[0];
+  const int32_t n_long = p.bag_read ? p.list_counts[1] : 0;
   int32_t it = 0;
   if (lane == 0) it = atomicAdd(p.short_cursor, 1);
   it = __shfl_sync(kFull, it, 0);
-  while (it < n_short) {
+  while (it < n_short + n_long) {
     int32_t next = 0;
     if (lane == 0) next = atomicAdd(p.short_cursor, 1);
-    const int64_t d = p.short_list[it];
+    const int64_t d = it < n_long ? p.long_list[it] : p.short_list[it - n_long];
     const int64_t o0 = p.offsets[d], len = p.offsets[d + 1] - o0;
     for (int q = lane; q < kq; q += 32) num_q[q] = 0ull;
     if (lane == 0) {
@@ -525,22 +530,7 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
     }
     int nnz = 0;
     if (p.bag_read) {
-      // the document's bag, built by an earlier pass: every load in flight at once, then
-      // packed into the table area as (term, count) words 0 .. nnz - 1
-      nnz = p.bag_n[d];
-      int32_t bt[kShortRegs], bc[kShortRegs];
-#pragma unroll
-      for (int u = 0; u < kShortRegs; ++u) {
-        const int x = lane + 32 * u;
-        bt[u] = x < nnz ? __ldcs(p.bag_terms + o0 + x) : 0;
-        bc[u] = x < nnz ? __ldcs(p.bag_cnts + o0 + x) : 0;
-      }
-#pragma unroll
-      for (int u = 0; u < kShortRegs; ++u) {
-        const int x = lane + 32 * u;
-        if (x < nnz) tab[x] = ((unsigned long long)(uint32_t)bt[u] << 32) | (uint32_t)bc[u];
-      }
-      __syncwarp();
+      nnz = p.bag_n[d];  // the document's bag, built by an earlier pass, read as it is walked
     } else {
       const int l2 = log2_slots(len, 10);
       const int ts = 1 << l2;
@@ -582,12 +572,20 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
     float inv_norm = 0.f;
     if (MODE == kDENSE) inv_norm = inv_norm_of(p.dense.norm[d]);
     if (MODE != kDF || p.bag_read) {
-      // term x: the bag's word x, or the table slot the list's entry x names
+      // term x: the bag's entry x, or the table slot the list's entry x names
       const bool bag = p.bag_read != 0;
       auto term = [&](int x, uint32_t& key, uint32_t& c) {
-        const unsigned long long v = x < nnz ? tab[bag ? x : list[x]] : kEmpty64;
-        key = (uint32_t)(v >> 32);
-        c = (uint32_t)v;
+        if (x >= nnz) {
+          key = kEmpty;
+          c = 0u;
+        } else if (bag) {
+          key = (uint32_t)__ldcs(p.bag_terms + o0 + x);
+          c = (uint32_t)__ldcs(p.bag_cnts + o0 + x);
+        } else {
+          const unsigned long long v = tab[list[x]];
+          key = (uint32_t)(v >> 32);
+          c = (uint32_t)v;
+        }
       };
       uint32_t key, c;
       term(lane, key, c);
@@ -624,37 +622,54 @@ __global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestPara
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Length classes of the long-document path: class c holds lengths in [2^(9+c), 2^(10+c)),
+// c = 0..7.
+constexpr int kLenClasses = 8;
+// Counter words of one ingest call (int32).
+constexpr int kCntShort = 0, kCntLong = 1, kCntMaxLen = 2, kCntLongCursor = 3, kCntShortCursor = 4,
+              kCntHugeCursor = 5;
+constexpr int kCntClass = 8, kCntClassFill = 16, kCntWords = 32;
+
 // ---------------------------------------------------------------- long-document path
 // Documents longer than kShortMax go to groups of kGroupWarps warps (kGroupsLong groups per
 // CTA, each with its own table and named barrier), one document per group at a time, longest
-// length class first. A document with more than kLongSlots / 2 tokens is hashed in several
-// passes, each keeping the terms of one hash partition (a second hash of the term id), so the
-// table runs about half full. The list of occupied slots has room for every slot.
+// length class first. Documents of kHugeMin tokens or more are taken first, each by a whole
+// CTA with one table in all of its shared memory (kHugeSlots slots). A document with more
+// tokens than half its table is hashed in several passes, each keeping the terms of one hash
+// partition (a second hash of the term id), so the table runs about half full. The list of
+// occupied slots has room for every slot.
+constexpr int kHugeMin = 2048;       // documents this long take a whole CTA
+constexpr int kHugeSlots = 16384;    // the CTA-wide table
+static_assert(kHugeMin == (2 << (9 + 1)), "length classes 2 and up are the documents of kHugeMin tokens or more");
 __host__ __device__ __forceinline__ size_t long_group_bytes(int kq) {
   return (size_t)kq * 8 + 16 + 64 * 4 + 16 + (size_t)kLongSlots * 8 + (size_t)kLongSlots * 2;
 }
-
-__device__ __forceinline__ void group_sync(int g) {
-  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGroupThreads) : "memory");
+__host__ __device__ __forceinline__ size_t long_huge_bytes(int kq) {
+  return (size_t)kq * 8 + 16 + 64 * 4 + 16 + (size_t)kHugeSlots * 8 + (size_t)kHugeSlots * 2;
 }
 
-// The group's warps walk the terms [0, n) of one document, warp gw taking chunks gw, gw + W, ...
+// Barrier `id` over `n` threads (id 0 with the whole CTA).
+__device__ __forceinline__ void team_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// The team's warps walk the terms [0, n) of one document, warp tw taking chunks tw, tw + W, ...
 // of 32 terms; term x is (key, count) = at(x) (kEmpty for x >= n). Each chunk's table values
 // are gathered while the previous chunk is worked on. With bag_cursor, the terms are also
 // appended to the document's bag (coalesced; no pass depends on the bag's order, every sum
 // over it being an integer sum).
 template <int MODE, typename At>
-__device__ __forceinline__ void group_walk(const IngestParams& p, int n, int gw, int lane, const At& at,
-                                           const Transposer& tr, unsigned long long* num_q, Acc& a, int64_t d,
-                                           float inv_norm, int32_t* row_cnt_s, int64_t o0, int32_t* bag_cursor) {
-  int x0 = gw * 32;
+__device__ __forceinline__ void team_walk(const IngestParams& p, int n, int tw, int nwarps, int lane, const At& at,
+                                          const Transposer& tr, unsigned long long* num_q, Acc& a, int64_t d,
+                                          float inv_norm, int32_t* row_cnt_s, int64_t o0, int32_t* bag_cursor) {
+  int x0 = tw * 32;
   uint32_t key = kEmpty, c = 0u;
   at(x0 + lane, key, c);
   TermAux ax{1.0f, 0, 0ull};
   if (MODE != kDF && key != kEmpty) ax = load_aux<MODE>(p, key);
   ax.h = load_hash<MODE>(p, key);
   while (x0 < n) {
-    const int x1 = x0 + kGroupWarps * 32;
+    const int x1 = x0 + nwarps * 32;
     uint32_t key1 = kEmpty, c1 = 0u;
     if (x1 < n) at(x1 + lane, key1, c1);
     TermAux ax1{1.0f, 0, 0ull};
@@ -678,137 +693,163 @@ __device__ __forceinline__ void group_walk(const IngestParams& p, int n, int gw,
   }
 }
 
+// One long document by a team of `nthreads` threads (barrier `bar`) with a table of `slots`
+// 64-bit entries in `base`: accumulators, then hashing passes (or the stored bag) and the
+// walks, then the document's outputs. Called by every thread of the team.
 template <int MODE>
-__global__ void __launch_bounds__(kLongThreads, 1) k_ingest_long(IngestParams p) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  const int g = threadIdx.x / kGroupThreads, gt = threadIdx.x % kGroupThreads;
-  const int gw = gt >> 5, lane = threadIdx.x & 31;
-  const int kq = ingest_kq<MODE>(p);
-  uint8_t* base = smem + long_group_bytes(kq) * g;
+__device__ void team_doc(const IngestParams& p, int64_t d, uint8_t* base, int kq, int slots, int nthreads, int bar,
+                         int tt, const Transposer& tr) {
+  const int tw = tt >> 5, lane = tt & 31, nwarps = nthreads >> 5;
   unsigned long long* num_q = reinterpret_cast<unsigned long long*>(base);
   unsigned long long* norm_s = num_q + kq;  // [0] |d|^2, [1] of the bfloat16 weights
   uint32_t* P = reinterpret_cast<uint32_t*>(norm_s + 2);  // [64] Simhash column sums
-  int32_t* misc = reinterpret_cast<int32_t*>(P + 64);     // [0] document, [1] row count, [2] bag size, [3] list size
+  int32_t* misc = reinterpret_cast<int32_t*>(P + 64);     // [1] row count, [2] bag size, [3] list size
   unsigned long long* tab = reinterpret_cast<unsigned long long*>(misc + 4);
-  uint16_t* list = reinterpret_cast<uint16_t*>(tab + kLongSlots);
-  const Transposer tr(lane);
-
-  const int32_t n_long = p.list_counts[1];
-  // the warp path's grid may start on SMs this grid leaves (the two touch disjoint documents)
-  asm volatile("griddepcontrol.launch_dependents;");
-  while (true) {
-    if (gt == 0) misc[0] = atomicAdd(p.long_cursor, 1);
-    group_sync(g);
-    const int32_t it = misc[0];
-    if (it >= n_long) break;
-    const int64_t d = p.long_list[it];
-    const int64_t o0 = p.offsets[d], len = p.offsets[d + 1] - o0;
-    for (int q = gt; q < kq; q += kGroupThreads) num_q[q] = 0ull;
-    if (gt < 64) P[gt] = 0u;
-    if (gt == 0) {
-      norm_s[0] = 0ull;
-      norm_s[1] = 0ull;
-      misc[1] = 0;
-      misc[2] = 0;
-    }
-    Acc a{0ull, 0ull, 0u, 0u};
-    float inv_norm = 0.f;
-    if (MODE == kDENSE) inv_norm = inv_norm_of(p.dense.norm[d]);
-    if (p.bag_read) {
-      const int32_t nb = p.bag_n[d];
-      group_sync(g);
-      const int32_t* bt = p.bag_terms + o0;
-      const int32_t* bcn = p.bag_cnts + o0;
-      auto at = [&](int x, uint32_t& key, uint32_t& c) {
-        if (x < nb) {
-          key = (uint32_t)__ldcs(bt + x);
-          c = (uint32_t)__ldcs(bcn + x);
-        } else {
-          key = kEmpty;
-          c = 0u;
-        }
-      };
-      group_walk<MODE>(p, nb, gw, lane, at, tr, num_q, a, d, inv_norm, &misc[1], o0, nullptr);
-    } else {
-      const int l2 = log2_slots(len, 12);
-      const int ts = 1 << l2;
-      const uint32_t passes = (uint32_t)((len + (kLongSlots / 2) - 1) / (kLongSlots / 2));
-      int32_t* df = (MODE == kDF || MODE == kDFN) ? p.df : nullptr;
-      const bool walk = MODE != kDF || p.bag_write;
-      for (uint32_t pass = 0; pass < passes; ++pass) {
-        group_sync(g);
-        for (int s = gt; s < ts; s += kGroupThreads) tab[s] = kEmpty64;
-        if (gt == 0) misc[3] = 0;
-        group_sync(g);
-        for (int64_t x0 = gt; x0 < len; x0 += kLongUnroll * kGroupThreads) {
-          int32_t tk[kLongUnroll];  // kLongUnroll token loads in flight per thread
+  uint16_t* list = reinterpret_cast<uint16_t*>(tab + slots);
+  const int64_t o0 = p.offsets[d], len = p.offsets[d + 1] - o0;
+  for (int q = tt; q < kq; q += nthreads) num_q[q] = 0ull;
+  if (tt < 64) P[tt] = 0u;
+  if (tt == 0) {
+    norm_s[0] = 0ull;
+    norm_s[1] = 0ull;
+    misc[1] = 0;
+    misc[2] = 0;
+  }
+  Acc a{0ull, 0ull, 0u, 0u};
+  float inv_norm = 0.f;
+  if (MODE == kDENSE) inv_norm = inv_norm_of(p.dense.norm[d]);
+  if (p.bag_read) {
+    const int32_t nb = p.bag_n[d];
+    team_sync(bar, nthreads);
+    const int32_t* bt = p.bag_terms + o0;
+    const int32_t* bcn = p.bag_cnts + o0;
+    auto at = [&](int x, uint32_t& key, uint32_t& c) {
+      if (x < nb) {
+        key = (uint32_t)__ldcs(bt + x);
+        c = (uint32_t)__ldcs(bcn + x);
+      } else {
+        key = kEmpty;
+        c = 0u;
+      }
+    };
+    team_walk<MODE>(p, nb, tw, nwarps, lane, at, tr, num_q, a, d, inv_norm, &misc[1], o0, nullptr);
+  } else {
+    int max_l2 = 6;
+    while ((1 << (max_l2 + 1)) <= slots) ++max_l2;
+    const int l2 = log2_slots(len, max_l2);
+    const int ts = 1 << l2;
+    const uint32_t passes = (uint32_t)((len + (slots / 2) - 1) / (slots / 2));
+    int32_t* df = (MODE == kDF || MODE == kDFN) ? p.df : nullptr;
+    const bool walk = MODE != kDF || p.bag_write;
+    for (uint32_t pass = 0; pass < passes; ++pass) {
+      team_sync(bar, nthreads);
+      for (int sl = tt; sl < ts; sl += nthreads) tab[sl] = kEmpty64;
+      if (tt == 0) misc[3] = 0;
+      team_sync(bar, nthreads);
+      for (int64_t x0 = tt; x0 < len; x0 += kLongUnroll * nthreads) {
+        int32_t tk[kLongUnroll];  // kLongUnroll token loads in flight per thread
 #pragma unroll
-          for (int u = 0; u < kLongUnroll; ++u) {
-            const int64_t x = x0 + u * kGroupThreads;
-            tk[u] = x < len ? __ldcs(p.tokens + o0 + x) : -1;
-          }
-          uint32_t pend = 0u;
+        for (int u = 0; u < kLongUnroll; ++u) {
+          const int64_t x = x0 + u * nthreads;
+          tk[u] = x < len ? __ldcs(p.tokens + o0 + x) : -1;
+        }
+        uint32_t pend = 0u;
 #pragma unroll
-          for (int u = 0; u < kLongUnroll; ++u) {
-            if (x0 + u * kGroupThreads >= len) break;
-            const int32_t t = tk[u];
-            if ((uint32_t)t >= (uint32_t)p.vocab) {
-              if (pass == 0) set_err(p.err, kErrBadToken);
-              continue;
-            }
-            if (passes > 1 && pass_of((uint32_t)t, passes) != pass) continue;
-            pend |= 1u << u;
+        for (int u = 0; u < kLongUnroll; ++u) {
+          if (x0 + u * nthreads >= len) break;
+          const int32_t t = tk[u];
+          if ((uint32_t)t >= (uint32_t)p.vocab) {
+            if (pass == 0) set_err(p.err, kErrBadToken);
+            continue;
           }
-          if (!insert_batch<kLongUnroll>(tab, list, &misc[3], l2, tk, pend, df)) set_err(p.err, kErrTable);
+          if (passes > 1 && pass_of((uint32_t)t, passes) != pass) continue;
+          pend |= 1u << u;
         }
-        group_sync(g);
-        if (walk) {
-          const int n = misc[3];
-          auto at = [&](int x, uint32_t& key, uint32_t& c) {
-            const unsigned long long v = x < n ? tab[list[x]] : kEmpty64;
-            key = (uint32_t)(v >> 32);
-            c = (uint32_t)v;
-          };
-          group_walk<MODE>(p, n, gw, lane, at, tr, num_q, a, d, inv_norm, &misc[1], o0,
-                           p.bag_write ? &misc[2] : nullptr);
-        }
+        if (!insert_batch<kLongUnroll>(tab, list, &misc[3], l2, tk, pend, df)) set_err(p.err, kErrTable);
+      }
+      team_sync(bar, nthreads);
+      if (walk) {
+        const int n = misc[3];
+        auto at = [&](int x, uint32_t& key, uint32_t& c) {
+          const unsigned long long v = x < n ? tab[list[x]] : kEmpty64;
+          key = (uint32_t)(v >> 32);
+          c = (uint32_t)v;
+        };
+        team_walk<MODE>(p, n, tw, nwarps, lane, at, tr, num_q, a, d, inv_norm, &misc[1], o0,
+                        p.bag_write ? &misc[2] : nullptr);
       }
     }
-    if (MODE == kDFN || MODE == kSIG) {
-      const unsigned long long nq = warp_sum(a.norm);
-      if (lane == 0 && nq) atomicAdd(norm_s, nq);
-    }
-    if (MODE == kSIG && p.bf16w) {
-      const unsigned long long nq = warp_sum(a.norm16);
-      if (lane == 0 && nq) atomicAdd(norm_s + 1, nq);
-    }
-    if (MODE == kSIG) {
-      atomicAdd(&P[lane], a.plo);
-      atomicAdd(&P[lane + 32], a.phi);
-    }
-    group_sync(g);
-    if (MODE == kSIG && gw == 0) finalize_sig(p, d, len, norm_s[0], norm_s[1], num_q, P[lane], P[lane + 32], lane);
-    if (MODE == kDENSE) {
-      if (gt == 0) p.dense.row_cnt[d] = misc[1];
-      if (!p.dense.postings) write_bucket_norms(p, d, num_q, gt, kGroupThreads);
-    }
-    if (MODE == kDFN && gt == 0) p.norm_out[d] = norm_s[0];
-    if (p.bag_write && gt == 0) p.bag_n[d] = misc[2];
-    group_sync(g);
+  }
+  if (MODE == kDFN || MODE == kSIG) {
+    const unsigned long long nq = warp_sum(a.norm);
+    if (lane == 0 && nq) atomicAdd(norm_s, nq);
+  }
+  if (MODE == kSIG && p.bf16w) {
+    const unsigned long long nq = warp_sum(a.norm16);
+    if (lane == 0 && nq) atomicAdd(norm_s + 1, nq);
+  }
+  if (MODE == kSIG) {
+    atomicAdd(&P[lane], a.plo);
+    atomicAdd(&P[lane + 32], a.phi);
+  }
+  team_sync(bar, nthreads);
+  if (MODE == kSIG && tw == 0) finalize_sig(p, d, len, norm_s[0], norm_s[1], num_q, P[lane], P[lane + 32], lane);
+  if (MODE == kDENSE) {
+    if (tt == 0) p.dense.row_cnt[d] = misc[1];
+    if (!p.dense.postings) write_bucket_norms(p, d, num_q, tt, nthreads);
+  }
+  if (MODE == kDFN && tt == 0) p.norm_out[d] = norm_s[0];
+  if (p.bag_write && tt == 0) p.bag_n[d] = misc[2];
+  team_sync(bar, nthreads);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kLongThreads, 1) k_ingest_long(IngestParams p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ int32_t s_next, s_huge;
+  const int g = threadIdx.x / kGroupThreads, gt = threadIdx.x % kGroupThreads;
+  const int lane = threadIdx.x & 31;
+  const int kq = ingest_kq<MODE>(p);
+  const Transposer tr(lane);
+  const int32_t n_long = p.list_counts[1];
+  if (threadIdx.x == 0) {  // documents of kHugeMin tokens or more: length classes 2 and up, listed first
+    int32_t h = 0;
+    for (int c = 2; c < kLenClasses; ++c) h += p.list_counts[kCntClass + c];
+    s_huge = h;
+  }
+  __syncthreads();
+  const int32_t n_huge = s_huge;
+  // the warp path's grid may start on SMs this grid leaves (the two touch disjoint documents)
+  asm volatile("griddepcontrol.launch_dependents;");
+  // phase 1: the huge documents, one per CTA at a time
+  while (true) {
+    if (threadIdx.x == 0) s_next = atomicAdd(p.huge_cursor, 1);
+    __syncthreads();
+    const int32_t it = s_next;
+    __syncthreads();
+    if (it >= n_huge) break;
+    team_doc<MODE>(p, p.long_list[it], smem, kq, kHugeSlots, kLongThreads, 0, threadIdx.x, tr);
+  }
+  // phase 2: the other long documents, one per group at a time
+  uint8_t* base = smem + long_group_bytes(kq) * g;
+  int32_t* slot = reinterpret_cast<int32_t*>(base + (size_t)kq * 8 + 16 + 64 * 4);  // misc[0] of the group
+  while (true) {
+    if (gt == 0) *slot = n_huge + atomicAdd(p.long_cursor, 1);
+    team_sync(1 + g, kGroupThreads);
+    const int32_t it = *slot;
+    if (it >= n_long) break;
+    team_doc<MODE>(p, p.long_list[it], base, kq, kLongSlots, kGroupThreads, 1 + g, gt, tr);
   }
 }
 
-// Length classes of the CTA path: class c holds lengths in [2^(9+c), 2^(10+c)), c = 0..7.
-constexpr int kLenClasses = 8;
+// (length classes: see the long-document path)
 __device__ __forceinline__ int len_class(int64_t len) {
   int c = 0;
   while (c < kLenClasses - 1 && len >= (2ll << (9 + c))) ++c;
   return c;
 }
 
-// Counter words of one ingest call (int32).
-constexpr int kCntShort = 0, kCntLong = 1, kCntMaxLen = 2, kCntLongCursor = 3, kCntShortCursor = 4;
-constexpr int kCntClass = 8, kCntClassFill = 16, kCntWords = 32;
+
 
 // Splits documents into the warp path (appended to short_list) and the CTA path (counted per
 // length class); validates offsets.
@@ -923,7 +964,7 @@ int long_grid(const mrc_ctx* ctx, size_t smem) {
 }
 
 size_t short_smem(int kq) { return (size_t)kWarpsShort * short_warp_bytes(kq); }
-size_t long_smem(int kq) { return (size_t)kGroupsLong * long_group_bytes(kq); }
+size_t long_smem(int kq) { return std::max((size_t)kGroupsLong * long_group_bytes(kq), long_huge_bytes(kq)); }
 
 template <int MODE>
 cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const char* name, double bytes_per_token,
@@ -939,7 +980,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   if (d.n_docs <= 0) return cudaSuccess;
   cudaError_t e;
   if (d.lists_ready) {  // the lists of the previous pass over these documents: reset the cursors
-    e = cudaMemsetAsync(counts + kCntLongCursor, 0, sizeof(int32_t) * 2, ctx->stream);
+    e = cudaMemsetAsync(counts + kCntLongCursor, 0, sizeof(int32_t) * 3, ctx->stream);
     if (e != cudaSuccess) return e;
   } else {
     e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * kCntWords, ctx->stream);
@@ -951,6 +992,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   p.list_counts = counts;
   p.long_cursor = counts + kCntLongCursor;
   p.short_cursor = counts + kCntShortCursor;
+  p.huge_cursor = counts + kCntHugeCursor;
   p.err = d.err;
   const int kq = ingest_kq<MODE>(p);
   const size_t s_smem = short_smem(kq), l_smem = long_smem(kq);
@@ -962,7 +1004,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(ctx->stream, &cap);
   const bool overlap = cap == cudaStreamCaptureStatusNone && !ctx->timing;
-  {
+  if (!p.bag_read) {  // a pass over stored bags takes every document in the warp path
     int grid = long_grid<MODE>(ctx, l_smem);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     if (d.n_docs < grid) grid = (int)d.n_docs;
@@ -989,7 +1031,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = overlap ? 1 : 0;
+    cfg.numAttrs = overlap && !p.bag_read ? 1 : 0;
     e = cudaLaunchKernelEx(&cfg, k_ingest_short<MODE>, p);
     timing_end(ctx, ev);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -1169,6 +1211,7 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
   p.list_counts = counts;
   p.long_cursor = counts + kCntLongCursor;
   p.short_cursor = counts + kCntShortCursor;
+  p.huge_cursor = counts + kCntHugeCursor;
   p.err = err;
   const size_t s_smem = short_smem(k), l_smem = long_smem(k);
   if (h[0] > 0) {

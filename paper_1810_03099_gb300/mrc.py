@@ -270,6 +270,17 @@ class Index:
             pass
 
 
+def _pinned_pairs(n: int) -> np.ndarray:
+    """A host pair array in page-locked memory (device-to-host copies into it run at full speed).
+    The array is a view of a pinned torch tensor, which numpy keeps alive as the view's base."""
+    import torch
+    try:
+        t = torch.empty(max(n, 1) * PAIR_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    except RuntimeError:  # no device to pin for: plain host memory
+        return np.empty(max(n, 1), PAIR_DTYPE)
+    return t.numpy().view(PAIR_DTYPE)
+
+
 class Batch:
     """A graph-captured query pipeline (mrc_batch_*): up to max_docs new documents per launch,
     compared against every document of `index`."""
@@ -304,7 +315,7 @@ class Batch:
         own = out is None
         if own:
             if getattr(self, "_out", None) is None:
-                self._out = np.empty(self.capacity, PAIR_DTYPE)
+                self._out = _pinned_pairs(self.capacity)
             buf = self._out
         else:
             buf = out
@@ -332,7 +343,7 @@ class Batch:
         grouped by query; with offsets=True also where each query's pairs start."""
         n = getattr(self, "_last_n", 0)
         if getattr(self, "_hout", None) is None:
-            self._hout = np.empty(self.h_capacity, PAIR_DTYPE)
+            self._hout = _pinned_pairs(self.h_capacity)
         qoff = np.zeros(n + 1, np.int64)
         total = C.c_int64()
         self._check(self.ctx.lib.mrc_batch_hamming(self.handle, _ptr(self._hout), int(self._hout.shape[0]),
