@@ -66,7 +66,9 @@ typedef int32_t mrc_status;
 #define MRC_PREC_BF16_FP8 1 /* compare operands from BF16 weights, FP8 E4M3 compare,
                                candidates within margin of tau rescored in FP32 from the
                                FP32-weight signatures (the stored signatures)           */
-#define MRC_PREC_FP16 2     /* FP16 signatures, FP16 compare, FP32 rescoring near tau   */
+#define MRC_PREC_FP16 2     /* FP16 compare operands at the proven bound tau - 2e-3,
+                               FP32 rescoring: the arithmetic of MRC_PREC_FP32 (the
+                               serving configuration's name for it)                     */
 
 /* The 64-bit Simhash feature hash of a term t (Section III hashes words with MD5 or SHA1). */
 #define MRC_HASH_SPLITMIX64 0 /* one SplitMix64 step (Steele, Lea, Flood 2014) from t XOR seed */
@@ -101,7 +103,7 @@ typedef struct {
   int32_t weighting;    /* MRC_WEIGHT_*                                                     */
   int32_t precision;    /* MRC_PREC_*                                                       */
   float tau;            /* similarity threshold (inclusive), e.g. 0.9                       */
-  float margin;         /* reduced precision: candidates >= tau - margin are rescored       */
+  float margin;         /* precision form (E4M3): candidates >= tau - margin are rescored   */
   int32_t hamming_max;  /* Simhash: pairs with Hamming distance <= hamming_max              */
   int32_t feature_hash; /* MRC_HASH_*: Simhash feature hash (MD5 / SHA-1: a per-term table
                            of 8 * vocab bytes is computed with the index)                  */
@@ -217,7 +219,7 @@ mrc_status mrc_signature_noalloc(mrc_ctx* ctx, const mrc_index* index, const mrc
  * ([nq * k], e.g. from mrc_signature) compared against every index document.
  * The index's precision decides the arithmetic (see MRC_PREC_*): the
  * tensor-core compare finds candidates at a lowered threshold (tau - 2e-3 in
- * the FP32 form, a proven bound; tau - margin in the reduced forms); each
+ * the fp16 forms, a proven bound; tau - margin in the E4M3 form); each
  * candidate is then rescored as the FP32 dot product of the two unit
  * signatures and written iff that score >= tau (score = that FP32 cosine).
  * With rescoring turned off on the context (mrc_ctx_set_rescoring) the
@@ -285,7 +287,7 @@ mrc_status mrc_ctx_sync(mrc_ctx* ctx);
  * database (Section I, Section IV); a batch does that for up to max_docs new
  * documents at once against every document of `index`: signature pass,
  * tensor-core compare at a lowered threshold (tau - 2e-3 in the FP32 form, a
- * proven bound; tau - margin in the reduced forms), FP32 rescoring, grouping
+ * proven bound; tau - margin in the E4M3 form), FP32 rescoring, grouping
  * of the pairs by query. Pairs are
  * (query position i in the batch, index document j).
  *   mrc_batch_create : allocates the pipeline's device buffers (inputs, outputs,
@@ -406,8 +408,8 @@ mrc_status mrc_ctx_set_test_stall(mrc_ctx* ctx, int32_t on);
 /*
  * Diagnostics of the reduced-precision forms (not in the paper). With on == 0,
  * mrc_match (and mrc_match_async) write the tensor-core compare's candidates
- * -- every pair whose compare cosine is >= tau - 2e-3 (FP32 form) or
- * tau - margin (reduced forms) -- scored with that cosine (fp16: the product
+ * -- every pair whose compare cosine is >= tau - 2e-3 (fp16 forms) or
+ * tau - margin (E4M3 form) -- scored with that cosine (fp16: the product
  * of the fp16 unit signatures; E4M3: the cosine of the quantized vectors),
  * without FP32 rescoring. Default on.
  */

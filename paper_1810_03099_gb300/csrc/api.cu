@@ -938,7 +938,8 @@ static mrc_status match_impl(mrc_ctx* ctx, const mrc_index* index, const float* 
     g.b_norm = index->qnorm;
     g.b_norm_min = index->qnorm_min;
   }
-  g.thresh = tau - (prec == MRC_PREC_FP32 ? kF16CompareBound : index->params.margin);
+  // fp16 operands (FP32 and FP16 forms): the proven bound; E4M3: the margin
+  g.thresh = tau - (prec == MRC_PREC_BF16_FP8 ? index->params.margin : kF16CompareBound);
   if (!ctx->rescore) {  // diagnostics: the compare's candidates are the result
     g.exact_scores = 1;
     g.pairs = dst;

@@ -163,7 +163,7 @@ cudaError_t record(mrc_batch* b) {
     g.b_norm = x->qnorm;
     g.b_norm_min = x->qnorm_min;
   }
-  g.thresh = b->tau - (prec == MRC_PREC_FP32 ? kF16Bound : x->params.margin);
+  g.thresh = b->tau - (prec == MRC_PREC_BF16_FP8 ? x->params.margin : kF16Bound);
   g.pairs = b->d_cand;
   g.count = b->d_counts + 1;
   g.capacity = b->cand_cap;
