@@ -556,7 +556,7 @@ def form_batching(args):
             "config": {"workload": f"{len(sizes)} batches of 1-512 docs ({docs} docs, {q.n_tokens} tokens), "
                                    f"log-uniform 20-20,000 tokens, vs 1M-doc bf16/FP8 index, k=64, tau={TAU}"},
             "batch_latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3)},
-            "pairs": total_pairs, "tiles": {str(k): v for k, v in runner.tiles.items()}}
+            "pairs": total_pairs, "tuning": {str(k): v for k, v in runner.tuning.items()}}
     print(json.dumps(line), flush=True)
     runner.free()
     idx.free()

@@ -286,19 +286,32 @@ mrc_status mrc_ctx_sync(mrc_ctx* ctx);
  * The paper signatures each new page and compares it with the signature
  * database (Section I, Section IV); a batch does that for up to max_docs new
  * documents at once against every document of `index`: signature pass,
- * tensor-core compare at a lowered threshold (tau - 2e-3 in the FP32 form, a
- * proven bound; tau - margin in the E4M3 form), FP32 rescoring, grouping
- * of the pairs by query. Pairs are
+ * tensor-core compare at a lowered threshold (tau - 2e-3 in the FP32 and FP16
+ * forms, a proven bound; tau - margin in the E4M3 form), FP32 rescoring,
+ * grouping of the pairs by query. Pairs are
  * (query position i in the batch, index document j).
+ * With compare rows of one K block (k <= 64; k <= 128 in the E4M3 form) the graph holds one
+ * persistent cooperative kernel (after a memset of its control words) that runs
+ * every step, the Hamming leg included; wider rows run the steps as separate
+ * kernels of the graph. mrc_batch_kernels returns the number of kernel nodes
+ * in the captured graph (-1 for NULL).
  *   mrc_batch_create : allocates the pipeline's device buffers (inputs, outputs,
  *     workspace) and its own non-blocking stream, runs the pipeline once and
  *     captures it. max_tokens bounds the tokens of one batch; capacity bounds
  *     the pairs of one batch; tile_n is the compare tile width (0 = default,
  *     128 or 256; see the autotuner). The batch keeps `index` (not owned).
  *   mrc_batch_launch : asynchronous. Copies the batch's offsets/tokens (host or
- *     device memory) into the pipeline, pads it to max_docs with empty documents
- *     and launches the graph. At most one launch in flight per batch object; use
- *     several objects to overlap batches on the device.
+ *     device memory) and its document count into the pipeline (the separate-
+ *     kernel form pads the batch to max_docs with empty documents) and launches
+ *     the graph. At most one launch in flight per batch object; use several
+ *     objects to overlap batches on the device.
+ *   mrc_batch_tune   : the compare's tuning knobs (the autotuner's search space):
+ *     tile_n (0, 128 or 256), ring = depth of the compare's streamed-operand ring
+ *     (0 = as deep as shared memory allows, else 2..64, capped at what fits),
+ *     prefetch = L2 prefetch distance in index tiles (-1 = by the index size:
+ *     8 tiles when the index rows exceed 64 MB, else none; 0 = none; up to 64).
+ *     Re-captures the graph; no launch may be in flight. Results do not depend
+ *     on the knobs.
  *   mrc_batch_poll   : 1 when the last launch has finished (or none is pending), else 0.
  *   mrc_batch_wait   : waits for the last launch and copies min(total, capacity)
  *     pairs to `pairs` (host or device), grouped by query position i (order
@@ -314,6 +327,8 @@ mrc_status mrc_batch_launch(mrc_batch* batch, const mrc_docs* docs);
 int32_t mrc_batch_poll(mrc_batch* batch);
 mrc_status mrc_batch_wait(mrc_batch* batch, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs,
                           int64_t* query_offsets);
+mrc_status mrc_batch_tune(mrc_batch* batch, int32_t tile_n, int32_t ring, int32_t prefetch);
+int32_t mrc_batch_kernels(const mrc_batch* batch);
 const char* mrc_batch_last_error(const mrc_batch* batch);
 void mrc_batch_free(mrc_batch* batch);
 

@@ -2,9 +2,11 @@
 
 Batches of new documents (here 1-512 documents of 20-20,000 tokens) are each
 compared with every index document through one graph-captured pipeline launch
-(``mrc_batch_*`` in the C ABI). Batch sizes vary, so pipelines are captured per
-size bucket (powers of two up to ``max_docs``) and a batch is padded to its
-bucket. The compare tile width of each bucket comes from the autotuner.
+(``mrc_batch_*`` in the C ABI; for k <= 64 one persistent kernel per batch). Batch
+sizes vary, so pipelines are captured per size bucket (powers of two up to
+``max_docs``); a batch runs in its bucket's pipeline, whose compare covers the
+bucket's rows. The compare's tile width, streamed-operand ring depth and L2 prefetch
+distance of each bucket come from the autotuner.
 """
 from __future__ import annotations
 
@@ -27,10 +29,18 @@ def bucket_of(n: int, max_docs: int) -> int:
     return min(b, max_docs)
 
 
-def autotune_tile(ctx, index, bucket: int, max_tokens: int, sample, reps: int = 5, cache: str | None = TUNE_CACHE,
-                  candidates=(128, 256)) -> int:
-    """Time each compare tile width on a sample batch (offsets, tokens) and return the fastest.
-    Results are cached by (GPU, index size, k, precision, bucket)."""
+# The autotuner's search space: compare tile width, depth of the compare's streamed-operand
+# ring (0 = as deep as shared memory allows) and L2 prefetch distance in index tiles.
+TILES = (128, 256)
+RINGS = (0, 3, 6)
+PREFETCHES = (0, 8, 24)
+
+
+def autotune(ctx, index, bucket: int, max_tokens: int, sample, reps: int = 5, cache: str | None = TUNE_CACHE,
+             tiles=TILES, rings=RINGS, prefetches=PREFETCHES) -> dict:
+    """Time every (tile width, ring depth, prefetch distance) on a sample batch (offsets, tokens)
+    and return the fastest as {"tile_n", "ring", "prefetch"}. Results are cached by (GPU, index
+    size, k, precision, bucket)."""
     import torch
     key = f"{torch.cuda.get_device_name()}|N{index.n_docs}|k{index.k}|p{index.precision}|b{bucket}"
     table = {}
@@ -40,29 +50,33 @@ def autotune_tile(ctx, index, bucket: int, max_tokens: int, sample, reps: int = 
                 table = json.load(f)
         except (OSError, ValueError):
             table = {}
-    if key in table:
-        return int(table[key]["tile_n"])
+    if key in table and "ring" in table[key]:
+        return {k: int(table[key][k]) for k in ("tile_n", "ring", "prefetch")}
     offs, toks = sample
     timings = {}
-    for tn in candidates:
+    for tn in tiles:
         b = mrc.Batch(ctx, index, bucket, max_tokens, capacity=1 << 16, tile_n=tn)
-        b.launch(offs, toks)
-        b.wait()
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            b.launch(offs, toks)
-            b.wait()
-        timings[tn] = (time.perf_counter() - t0) / reps
+        for ring in rings:
+            for pf in prefetches:
+                b.tune(tn, ring, pf)
+                b.launch(offs, toks)
+                b.wait()
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    b.launch(offs, toks)
+                    b.wait()
+                timings[(tn, ring, pf)] = (time.perf_counter() - t0) / reps
         b.free()
     best = min(timings, key=timings.get)
-    table[key] = {"tile_n": best, "seconds": {str(k): v for k, v in timings.items()}}
+    table[key] = {"tile_n": best[0], "ring": best[1], "prefetch": best[2],
+                  "seconds": {f"{t}/{r}/{p}": v for (t, r, p), v in timings.items()}}
     if cache:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         tmp = f"{cache}.tmp{os.getpid()}"
         with open(tmp, "w") as f:
             json.dump(table, f, indent=1)
         os.replace(tmp, cache)
-    return best
+    return {"tile_n": best[0], "ring": best[1], "prefetch": best[2]}
 
 
 class BatchRunner:
@@ -74,16 +88,19 @@ class BatchRunner:
         self.max_docs, self.max_doc_tokens, self.capacity = max_docs, max_doc_tokens, capacity
         self.autotune = autotune
         self.pipes: dict[int, mrc.Batch] = {}
-        self.tiles: dict[int, int] = {}
+        self.tuning: dict[int, dict] = {}
 
     def pipe(self, bucket: int, sample=None) -> mrc.Batch:
         if bucket not in self.pipes:
             max_tokens = bucket * self.max_doc_tokens
-            tn = 0
+            knobs = {"tile_n": 0, "ring": 0, "prefetch": -1}
             if self.autotune and sample is not None:
-                tn = autotune_tile(self.ctx, self.index, bucket, max_tokens, sample)
-            self.tiles[bucket] = tn
-            self.pipes[bucket] = mrc.Batch(self.ctx, self.index, bucket, max_tokens, self.tau, self.capacity, tn)
+                knobs = autotune(self.ctx, self.index, bucket, max_tokens, sample)
+            self.tuning[bucket] = knobs
+            b = mrc.Batch(self.ctx, self.index, bucket, max_tokens, self.tau, self.capacity, knobs["tile_n"])
+            if knobs["ring"] != 0 or knobs["prefetch"] != -1:
+                b.tune(knobs["tile_n"], knobs["ring"], knobs["prefetch"])
+            self.pipes[bucket] = b
         return self.pipes[bucket]
 
     def prepare(self, batches):

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmrc.so")
-SOURCES = ["api.cu", "ingest.cu", "compare_tc.cu", "simhash_match.cu", "tail.cu", "noalloc.cu", "batch.cu", "select.cu",
+SOURCES = ["api.cu", "ingest.cu", "compare_tc.cu", "batch_kernel.cu", "simhash_match.cu", "tail.cu", "noalloc.cu", "batch.cu", "select.cu",
            "text.cu", "simhash_index.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")

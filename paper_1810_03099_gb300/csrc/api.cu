@@ -921,11 +921,13 @@ static mrc_status match_impl(mrc_ctx* ctx, const mrc_index* index, const float* 
   // Candidates from the tensor cores at a lowered threshold, then FP32 rescoring of every
   // candidate. FP32 form: fp16 unit vectors; |fp16 cosine - cosine| <= 2^-10 sum|x_p y_p| +
   // subnormal and FP32-accumulation terms <= ~1e-3 (Cauchy-Schwarz), so tau - 2e-3 loses no
-  // pair and the rescored scores are FP32-accurate. FP16 / E4M3 forms: tau - margin.
+  // pair and the rescored scores are FP32-accurate; the FP16 form computes the same. E4M3
+  // form: tau - margin.
   GemmArgs g{};
   g.na = na;
   g.nb = N;
   g.triangle = query_sig ? 0 : 1;
+  g.prefetch = -1;
   g.err = d_err;
   g.out_scale = 1.0f;
   g.fmt = prec == MRC_PREC_BF16_FP8 ? OP_E4M3 : OP_F16;

@@ -8,13 +8,17 @@
 //   batch against the whole index at a lowered threshold -> FP32 rescoring -> pairs grouped
 //   by query; with a fingerprint index attached, the batch's Simhashes then probe it
 //   (Hamming pairs, grouped by query as well).
-// The whole pipeline is captured once into a CUDA graph on the batch's own stream, for
-// exactly max_docs documents; a batch of fewer documents is padded with empty ones
-// (zero signatures, which match nothing). Each batch is then one graph launch, after
-// the copies of its offsets and tokens.
+// For compare rows of 64 or 128 bytes (k <= 64) the whole pipeline is one persistent
+// cooperative kernel (batch_kernel.cu), captured with the memset of its control block into a
+// CUDA graph on the batch's own stream; the kernel reads the number of documents of each
+// launch from the device, so documents past it cost nothing but an empty signature row.
+// Wider rows take the same steps as separate kernels in the graph, the batch then padded with
+// empty documents (zero signatures, which match nothing). Each batch is one graph launch,
+// after the copies of its offsets, tokens and document count.
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "device.cuh"
 #include "internal.h"
@@ -38,9 +42,21 @@ struct mrc_batch {
   int64_t* d_qoff = nullptr;               // [max_docs + 1] start of each query's pairs
   int32_t* d_qcnt = nullptr;               // [max_docs] pairs per query
   int32_t* d_qfill = nullptr;              // [max_docs] scatter cursors
+  // control block (one allocation, zeroed before each launch): pair and candidate counts,
+  // the Hamming pair count, the error word and the batch kernel's control words; then the
+  // launch's document count (not zeroed)
+  void* d_block = nullptr;
   unsigned long long* d_counts = nullptr;  // [0] pairs, [1] candidates
+  unsigned long long* d_hcount = nullptr;
   int32_t* d_err = nullptr;
+  int32_t* d_ctl = nullptr;
+  int64_t* d_nlive = nullptr;
+  int32_t* d_long = nullptr;               // [max_docs] the batch kernel's long-document list
+  bool fused = false;                      // one persistent kernel (else separate kernels)
+  int32_t qstride = 1;                     // per-query counter stride (words)
+  int32_t ring = 0, prefetch = -1;         // compare tuning (B ring depth, L2 prefetch distance)
   unsigned long long* h_counts = nullptr;  // pinned: [0] pairs [1] candidates [2] error word [3] Hamming pairs
+                                           // [4] the launch's document count (staging)
   uint64_t* d_simhash = nullptr;           // [max_docs] the batch's Simhash fingerprints
   // Hamming leg (mrc_batch_attach_simhash): the batch's fingerprints probe a block-table index
   const mrc_simhash_index* shx = nullptr;
@@ -51,8 +67,8 @@ struct mrc_batch {
   int64_t* d_hqoff = nullptr;
   int32_t* d_hqcnt = nullptr;
   int32_t* d_hqfill = nullptr;
-  unsigned long long* d_hcount = nullptr;
   cudaGraphExec_t exec = nullptr;
+  int32_t kernel_nodes = 0;  // kernel nodes of the captured graph
   cudaEvent_t done = nullptr;
   bool pending = false;
   int64_t last_n = 0;  // documents of the last launch
@@ -61,6 +77,8 @@ struct mrc_batch {
 namespace {
 
 constexpr float kF16Bound = 2e-3f;  // > max |fp16 cosine - cosine| of unit vectors
+constexpr size_t kBlockZeroBytes = 64;  // counts (16), Hamming count (8), error word (8), control words (32)
+static_assert(kBlockZeroBytes == 32 + 8 * sizeof(int32_t) && kBatchCtlWords == 8, "control block layout");
 
 // Groups the batch's pairs by query: per-query counts, exclusive scan (one CTA), scatter.
 __global__ void k_group_count(const mrc_pair* pairs, const unsigned long long* n_pairs, int64_t cap, int32_t* cnt) {
@@ -118,8 +136,59 @@ bool on_device(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// The stream-ordered work of one batch (captured into the graph).
+// The persistent kernel's launch (captured into the graph).
+cudaError_t record_fused(mrc_batch* b) {
+  mrc_ctx* ctx = b->ctx;
+  const mrc_index* x = b->index;
+  const int32_t prec = x->params.precision;
+  cudaError_t e = cudaMemsetAsync(b->d_block, 0, kBlockZeroBytes, ctx->stream);
+  if (e != cudaSuccess) return e;
+  BatchKernelArgs a{};
+  a.index = x;
+  a.max_docs = b->max_docs;
+  a.max_tokens = b->max_tokens;
+  a.offsets = b->d_offsets;
+  a.tokens = b->d_tokens;
+  a.n_live = b->d_nlive;
+  a.unit = b->d_unit;
+  a.op = b->d_op;
+  a.qnorm = b->d_qnorm;
+  a.simhash = b->d_simhash;
+  a.tau = b->tau;
+  a.thresh = b->tau - (prec == MRC_PREC_BF16_FP8 ? x->params.margin : kF16Bound);
+  a.tile_n = b->tile_n;
+  a.ring = b->ring;
+  a.prefetch = b->prefetch;
+  a.cand = b->d_cand;
+  a.cand_cap = b->cand_cap;
+  a.pairs = b->d_pairs;
+  a.capacity = b->capacity;
+  a.counts = b->d_counts;
+  a.err = b->d_err;
+  a.ctl = b->d_ctl;
+  a.long_list = b->d_long;
+  a.qstride = b->qstride;
+  a.qcnt = b->d_qcnt;
+  a.qfill = b->d_qfill;
+  a.qoff = b->d_qoff;
+  a.grouped = b->d_grouped;
+  if (b->shx) {
+    a.shx = b->shx;
+    a.hmax = b->hmax;
+    a.hpairs = b->d_hpairs;
+    a.hcount = b->d_hcount;
+    a.hcapacity = b->h_capacity;
+    a.hqcnt = b->d_hqcnt;
+    a.hqfill = b->d_hqfill;
+    a.hqoff = b->d_hqoff;
+    a.hgrouped = b->d_hgrouped;
+  }
+  return launch_batch_kernel(ctx, a);
+}
+
+// The stream-ordered work of one batch as separate kernels (captured into the graph).
 cudaError_t record(mrc_batch* b) {
+  if (b->fused) return record_fused(b);
   mrc_ctx* ctx = b->ctx;
   const mrc_index* x = b->index;
   const int32_t prec = x->params.precision;
@@ -167,6 +236,8 @@ cudaError_t record(mrc_batch* b) {
   g.pairs = b->d_cand;
   g.count = b->d_counts + 1;
   g.capacity = b->cand_cap;
+  g.ring = b->ring;
+  g.prefetch = b->prefetch;
   e = launch_gemm_compare(ctx, g);
   if (e != cudaSuccess) return e;
   e = launch_rescore(ctx, b->d_cand, b->d_counts + 1, b->cand_cap, b->d_unit, x->sig_unit, x->k, b->tau,
@@ -212,11 +283,24 @@ cudaError_t capture(mrc_batch* b) {
     if (er != cudaSuccess) e = er;
   }
   cudaGraphExec_t exec = nullptr;
+  int32_t kernels = 0;
+  if (e == cudaSuccess) {
+    size_t nn = 0;
+    e = cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e == cudaSuccess && nn) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+    for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+      cudaGraphNodeType t;
+      e = cudaGraphNodeGetType(nodes[i], &t);
+      if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+    }
+  }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
   if (graph) cudaGraphDestroy(graph);
   if (e != cudaSuccess) return e;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   b->exec = exec;
+  b->kernel_nodes = kernels;
   return cudaSuccess;
 }
 
@@ -225,10 +309,10 @@ void release(mrc_batch* b) {
   if (b->ctx) cudaStreamSynchronize(b->ctx->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->done) cudaEventDestroy(b->done);
-  void* ptrs[] = {b->d_offsets, b->d_tokens, b->d_unit,    b->d_op,     b->d_qnorm,   b->d_cand,
-                  b->d_pairs,   b->d_grouped, b->d_qoff,   b->d_qcnt,   b->d_qfill,   b->d_counts,
-                  b->d_err,     b->d_simhash, b->d_hpairs, b->d_hgrouped, b->d_hqoff, b->d_hqcnt,
-                  b->d_hqfill,  b->d_hcount};
+  void* ptrs[] = {b->d_offsets, b->d_tokens,    b->d_unit,  b->d_op,    b->d_qnorm,  b->d_cand,
+                  b->d_pairs,   b->d_grouped,   b->d_qoff,  b->d_qcnt,  b->d_qfill,  b->d_block,
+                  b->d_long,    b->d_simhash,   b->d_hpairs, b->d_hgrouped, b->d_hqoff, b->d_hqcnt,
+                  b->d_hqfill};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->h_counts) cudaFreeHost(b->h_counts);
@@ -264,6 +348,10 @@ mrc_status mrc_batch_create(mrc_ctx* ctx, const mrc_index* index, int64_t max_do
   b->cand_cap = std::max<int64_t>(4 * capacity, 1 << 16);
   b->tau = tau;
   b->tile_n = tile_n;
+  b->fused = batch_kernel_supported(index);
+  // per-query counters in separate 128-byte lines (atomics on different L2 lines) while that
+  // costs at most 8 MB
+  b->qstride = b->fused && max_docs <= 65536 ? 32 : 1;
   cudaStream_t s = nullptr;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
     delete b;
@@ -287,14 +375,22 @@ mrc_status mrc_batch_create(mrc_ctx* ctx, const mrc_index* index, int64_t max_do
   if (e == cudaSuccess) e = cudaMalloc(&b->d_pairs, sizeof(mrc_pair) * (size_t)capacity);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_grouped, sizeof(mrc_pair) * (size_t)capacity);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_qoff, sizeof(int64_t) * (size_t)(max_docs + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_qcnt, sizeof(int32_t) * (size_t)max_docs);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_qfill, sizeof(int32_t) * (size_t)max_docs);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, 2 * sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_qcnt, sizeof(int32_t) * (size_t)max_docs * b->qstride);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_qfill, sizeof(int32_t) * (size_t)max_docs * b->qstride);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_block, kBlockZeroBytes + sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_long, sizeof(int32_t) * (size_t)max_docs);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_simhash, sizeof(uint64_t) * (size_t)max_docs);
-  if (e == cudaSuccess) e = cudaMallocHost(&b->h_counts, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_counts, 5 * sizeof(unsigned long long));
+  if (e == cudaSuccess) {
+    b->d_counts = reinterpret_cast<unsigned long long*>(b->d_block);
+    b->d_hcount = b->d_counts + 2;
+    b->d_err = reinterpret_cast<int32_t*>(b->d_counts + 3);
+    b->d_ctl = b->d_err + 2;
+    b->d_nlive = reinterpret_cast<int64_t*>(reinterpret_cast<uint8_t*>(b->d_block) + kBlockZeroBytes);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_offsets, 0, sizeof(int64_t) * (size_t)(max_docs + 1), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_block, 0, kBlockZeroBytes + sizeof(int64_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_op, 0, op_bytes, s);
   if (e != cudaSuccess) {
     mrc_status st = cuda_fail(ctx, e, "mrc_batch_create allocations");
@@ -337,7 +433,11 @@ mrc_status mrc_batch_launch(mrc_batch* b, const mrc_docs* docs) {
   } else {
     e = cudaMemsetAsync(b->d_offsets, 0, sizeof(int64_t), ctx->stream);
   }
-  if (e == cudaSuccess && n < b->max_docs) {
+  if (e == cudaSuccess && b->fused) {
+    // the kernel reads the document count; offsets past it are not read
+    b->h_counts[4] = (unsigned long long)n;
+    e = cudaMemcpyAsync(b->d_nlive, b->h_counts + 4, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream);
+  } else if (e == cudaSuccess && n < b->max_docs) {
     const int64_t m = b->max_docs - n;
     k_pad_offsets<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(b->d_offsets, n, b->max_docs);
     e = cudaGetLastError();
@@ -413,9 +513,8 @@ mrc_status mrc_batch_attach_simhash(mrc_batch* b, const mrc_simhash_index* index
   cudaError_t e = cudaMalloc(&b->d_hpairs, sizeof(mrc_pair) * (size_t)capacity);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_hgrouped, sizeof(mrc_pair) * (size_t)capacity);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_hqoff, sizeof(int64_t) * (size_t)(b->max_docs + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_hqcnt, sizeof(int32_t) * (size_t)b->max_docs);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_hqfill, sizeof(int32_t) * (size_t)b->max_docs);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_hcount, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_hqcnt, sizeof(int32_t) * (size_t)b->max_docs * b->qstride);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_hqfill, sizeof(int32_t) * (size_t)b->max_docs * b->qstride);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "mrc_batch_attach_simhash allocations");
   b->shx = index;
   b->hmax = hamming_max;
@@ -449,6 +548,30 @@ mrc_status mrc_batch_hamming(mrc_batch* b, mrc_pair* pairs, int64_t capacity, in
     return fail(ctx, MRC_ERR_CAPACITY, "more Hamming pairs than capacity; *n_pairs holds the total");
   return MRC_OK;
 }
+
+mrc_status mrc_batch_tune(mrc_batch* b, int32_t tile_n, int32_t ring, int32_t prefetch) {
+  if (!b) return MRC_ERR_INVALID;
+  mrc_ctx* ctx = b->ctx;
+  cudaSetDevice(ctx->device);
+  if (b->pending) return fail(ctx, MRC_ERR_INVALID, "mrc_batch_tune: a launch is in flight");
+  if ((tile_n != 0 && tile_n != 128 && tile_n != 256) || ring < 0 || ring == 1 || ring > 64 || prefetch < -1 ||
+      prefetch > 64)
+    return fail(ctx, MRC_ERR_INVALID, "mrc_batch_tune: tile_n in {0, 128, 256}, ring 0 or in [2, 64], prefetch in [-1, 64]");
+  const int32_t old_tile = b->tile_n, old_ring = b->ring, old_pf = b->prefetch;
+  b->tile_n = tile_n;
+  b->ring = ring;
+  b->prefetch = prefetch;
+  const cudaError_t e = capture(b);
+  if (e != cudaSuccess) {
+    b->tile_n = old_tile;
+    b->ring = old_ring;
+    b->prefetch = old_pf;
+    return cuda_fail(ctx, e, "re-capturing the batch pipeline");
+  }
+  return MRC_OK;
+}
+
+int32_t mrc_batch_kernels(const mrc_batch* b) { return b ? b->kernel_nodes : -1; }
 
 const char* mrc_batch_last_error(const mrc_batch* b) { return b ? b->ctx->last_error.c_str() : "no batch"; }
 

@@ -32,6 +32,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 // (s0 + s1) + (s2 + s3). Every rescoring path uses this one order, so a pair gets the same
 // score wherever it is rescored. Rows are read as float4 when k is a multiple of 4 (row
 // starts are then 16-byte aligned); the order of the arithmetic is the same either way.
+// X_L2: x is read through L2 only (rows written earlier in the same kernel).
+template <bool X_L2 = false>
 __device__ __forceinline__ float unit_dot(const float* __restrict__ x, const float* __restrict__ y, int k) {
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
   if ((k & 3) == 0) {
@@ -39,7 +41,7 @@ __device__ __forceinline__ float unit_dot(const float* __restrict__ x, const flo
     const float4* y4 = reinterpret_cast<const float4*>(y);
 #pragma unroll 4
     for (int q = 0; q < (k >> 2); ++q) {
-      const float4 a = __ldg(x4 + q), b = __ldg(y4 + q);
+      const float4 a = X_L2 ? __ldcg(x4 + q) : __ldg(x4 + q), b = __ldg(y4 + q);
       s0 = fmaf(a.x, b.x, s0);
       s1 = fmaf(a.y, b.y, s1);
       s2 = fmaf(a.z, b.z, s2);
@@ -47,7 +49,7 @@ __device__ __forceinline__ float unit_dot(const float* __restrict__ x, const flo
     }
   } else {
     for (int q = 0; q < k; ++q) {
-      const float a = __ldg(x + q), b = __ldg(y + q);
+      const float a = X_L2 ? __ldcg(x + q) : __ldg(x + q), b = __ldg(y + q);
       switch (q & 3) {
         case 0: s0 = fmaf(a, b, s0); break;
         case 1: s1 = fmaf(a, b, s1); break;

@@ -172,7 +172,29 @@ struct IngestParams {
   int32_t* bag_cnts;
   int32_t* bag_n;
   int32_t bag_write, bag_read;
+  // Persistent batch kernel: the number of real documents, read on the device; documents from
+  // *n_live on are empty (their offsets are not read), and so is a document whose tokens do
+  // not lie in [0, n_tokens). NULL elsewhere.
+  const int64_t* n_live;
+  int64_t n_tokens;
 };
+
+// Token range of document d. A document past *n_live, or with a length outside
+// [0, MRC_MAX_DOC_TOKENS] (reported by the pass that lists the documents), is empty.
+__device__ __forceinline__ void doc_span(const IngestParams& p, int64_t d, int64_t& o0, int64_t& len) {
+  if (p.n_live && d >= *p.n_live) {
+    o0 = 0;
+    len = 0;
+    return;
+  }
+  o0 = p.offsets[d];
+  len = p.offsets[d + 1] - o0;
+  if (len < 0 || len > MRC_MAX_DOC_TOKENS) len = 0;
+  if (p.n_live && (o0 < 0 || o0 + len > p.n_tokens)) {
+    o0 = 0;
+    len = 0;
+  }
+}
 
 // Shared-memory 64-bit accumulator words per document: SIG, one per reference partition; DENSE
 // in the bound-pruned mode, one 32-bit sum per tail bucket (two per word).
@@ -388,7 +410,8 @@ __device__ void warp_doc(const IngestParams& p, int64_t d, uint8_t* base, int kq
   unsigned long long* tab = num_q + kq;
   uint16_t* list = reinterpret_cast<uint16_t*>(tab + kShortSlots);
   int32_t* misc = reinterpret_cast<int32_t*>(list + kShortMax);  // [0] list size, [1] row count
-  const int64_t o0 = p.offsets[d], len = p.offsets[d + 1] - o0;
+  int64_t o0, len;
+  doc_span(p, d, o0, len);
   for (int q = lane; q < kq; q += 32) num_q[q] = 0ull;
   if (lane == 0) {
     misc[0] = 0;
@@ -567,7 +590,8 @@ __device__ void team_doc(const IngestParams& p, int64_t d, uint8_t* base, int kq
   int32_t* misc = reinterpret_cast<int32_t*>(P + 64);     // [1] row count, [2] bag size, [3] list size
   unsigned long long* tab = reinterpret_cast<unsigned long long*>(misc + 4);
   uint16_t* list = reinterpret_cast<uint16_t*>(tab + slots);
-  const int64_t o0 = p.offsets[d], len = p.offsets[d + 1] - o0;
+  int64_t o0, len;
+  doc_span(p, d, o0, len);
   for (int q = tt; q < kq; q += nthreads) num_q[q] = 0ull;
   if (tt < 64) P[tt] = 0u;
   if (tt == 0) {

@@ -244,6 +244,49 @@ cudaError_t launch_simhash_index_probe(mrc_ctx* ctx, const uint64_t* q, int64_t 
                                        const SimhashLayout& L, int64_t n, const uint64_t* fp, const int32_t* id,
                                        const int32_t* off, mrc_pair* pairs, unsigned long long* count,
                                        int64_t capacity);
+// batch_kernel.cu: a query batch's whole pipeline (signature pass, tensor-core compare with the
+// index, FP32 rescoring, Hamming probe of a fingerprint index, grouping by query) as one
+// persistent cooperative kernel. All pointers are device memory owned by the batch.
+struct BatchKernelArgs {
+  const mrc_index* index;
+  int64_t max_docs, max_tokens;
+  const int64_t* offsets;  // [max_docs + 1]; entries past n_live are not read
+  const int32_t* tokens;   // [max_tokens]
+  const int64_t* n_live;   // [1] documents of this launch (<= max_docs)
+  float* unit;             // [max_docs * k] unit signatures
+  void* op;                // [max_docs * kp] fp16 or [max_docs * kp8] E4M3 compare operands
+  float* qnorm;            // [max_docs] E4M3 operand norms
+  uint64_t* simhash;       // [max_docs]
+  float tau, thresh;       // result threshold; compare threshold (tau less the form's bound or margin)
+  int32_t tile_n, ring, prefetch;  // compare tile width (128 / 256), B ring depth, L2 prefetch distance
+  mrc_pair* cand;
+  int64_t cand_cap;
+  mrc_pair* pairs;
+  int64_t capacity;
+  unsigned long long* counts;  // [0] pairs, [1] candidates
+  int32_t* err;
+  int32_t* ctl;            // [kBatchCtlWords], zero before each launch
+  int32_t* long_list;      // [max_docs]
+  int32_t qstride;         // per-query counter stride (words)
+  int32_t* qcnt;           // [max_docs * qstride]
+  int32_t* qfill;          // [max_docs * qstride]
+  int64_t* qoff;           // [max_docs + 1]
+  mrc_pair* grouped;       // [capacity]
+  // Hamming leg (shx == NULL: none)
+  const mrc_simhash_index* shx;
+  int32_t hmax;
+  mrc_pair* hpairs;
+  unsigned long long* hcount;
+  int64_t hcapacity;
+  int32_t* hqcnt;
+  int32_t* hqfill;
+  int64_t* hqoff;
+  mrc_pair* hgrouped;
+};
+constexpr int kBatchCtlWords = 8;
+// True if the persistent batch kernel handles this index (compare rows of 64 or 128 bytes).
+bool batch_kernel_supported(const mrc_index* index);
+cudaError_t launch_batch_kernel(mrc_ctx* ctx, const BatchKernelArgs& a);
 // out[t] = the MD5 (mode MRC_HASH_MD5) or SHA-1 (MRC_HASH_SHA1) Simhash feature of term t < vocab.
 cudaError_t launch_feature_table(mrc_ctx* ctx, int32_t vocab, uint64_t seed, int32_t mode, uint64_t* out);
 // Packs rows of `sig` (normalised to unit length first when `normalize`) into compare operands.
@@ -308,7 +351,14 @@ struct GemmArgs {
   int32_t exact_scores;  // E4M3 thresholding: 1 = exact per-column test and quantized-cosine
                          // scores (the candidates are the result); 0 = the block bound alone,
                          // raw accumulators (every candidate is rescored afterwards)
+  int32_t prefetch;      // resident kernel: L2 prefetch distance in B tiles (0: none, < 0: by size)
+  int32_t ring;          // resident kernel: B ring depth (0: as deep as shared memory allows)
 };
+// L2 prefetch distance the resident compare uses when GemmArgs.prefetch < 0: B tiles streamed
+// from DRAM (a query x index compare whose index rows exceed kPrefetchMinBytes) are prefetched
+// this many tiles ahead.
+constexpr int32_t kPrefetchTiles = 8;
+constexpr int64_t kPrefetchMinBytes = 64ll << 20;
 cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g);
 // FP32 rescoring of the first min(*n_cand, cand_cap) candidates (unit_dot of rows i of qunit
 // and j of xunit, k entries each); pairs scoring >= tau are appended to pairs / count (at most

@@ -105,6 +105,8 @@ _SIGNATURES = {
     "mrc_batch_attach_simhash": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64]),
     "mrc_batch_hamming": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
     "mrc_batch_free": (None, [C.c_void_p]),
+    "mrc_batch_tune": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
+    "mrc_batch_kernels": (C.c_int32, [C.c_void_p]),
 }
 
 _LIB = None
@@ -307,6 +309,17 @@ class Batch:
 
     def poll(self) -> bool:
         return bool(self.ctx.lib.mrc_batch_poll(self.handle))
+
+    def tune(self, tile_n: int = 0, ring: int = 0, prefetch: int = -1):
+        """Set the compare's tile width, streamed-operand ring depth and L2 prefetch distance
+        (mrc_batch_tune; re-captures the graph)."""
+        self._check(self.ctx.lib.mrc_batch_tune(self.handle, int(tile_n), int(ring), int(prefetch)))
+        self.tile_n = int(tile_n)
+
+    @property
+    def kernel_nodes(self) -> int:
+        """Kernel nodes of the captured graph (mrc_batch_kernels): 1 with the persistent kernel."""
+        return int(self.ctx.lib.mrc_batch_kernels(self.handle))
 
     def wait(self, out=None, offsets=False):
         """Wait for the last launch; returns (pairs grouped by query position, total) and, with

@@ -60,6 +60,7 @@ def test_batch_matches_oracle_and_eager(env, precision):
     assert tot > 20
     for max_docs, tile in ((100, 0), (128, 128), (256, 256)):
         b = mrc.Batch(ctx, idx, max_docs, 200000, tau, capacity=1 << 16, tile_n=tile)
+        assert b.kernel_nodes == 1  # the whole pipeline is one persistent kernel
         for _ in range(2):  # replays are repeatable
             b.launch(qo, qt)
             got, total = b.wait()
@@ -78,15 +79,81 @@ def test_batch_matches_oracle_and_eager(env, precision):
     idx.free()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_persistent_batch_every_document_path_hamming_and_errors(env, precision):
+    """The one-kernel batch on documents of every signature-pass path (empty; short, one warp;
+    long, a whole CTA; 9,000 and 20,000 tokens, several hashing passes) gives the eager calls'
+    signature pairs (same scores), the fingerprint index's Hamming pairs, and per-query offsets
+    that delimit each query's pairs. Offsets that decrease are reported (MRC_ERR_INVALID) and the
+    next launch is correct again; so is a launch of fewer documents than the one before."""
+    mrc, ctx, c, torch = env["mrc"], env["ctx"], env["c"], env["torch"]
+    idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, mrc.params_default(k=64, precision=precision))
+    fps = mrc.index_simhash(ctx, idx, torch.empty(c.n_docs, dtype=torch.int64, device="cuda"))
+    shx = mrc.simhash_index_build(ctx, fps, 3)
+    n = 90
+    qo, qt = _queries(c, n, 23)
+    docs = [qt[qo[i]:qo[i + 1]].copy() for i in range(n)]
+    rng = np.random.Generator(np.random.PCG64(41))
+    docs[1] = np.zeros(0, np.int32)
+    docs[3] = rng.integers(0, c.vocab, 3000).astype(np.int32)
+    d7 = c.doc(7)
+    docs[5] = np.tile(d7, 20000 // max(d7.size, 1) + 1)[:20000].astype(np.int32)  # index document 7, repeated
+    docs[8] = rng.integers(0, c.vocab, 9000).astype(np.int32)
+    docs[11] = c.doc(11).copy()  # an exact copy: Hamming distance 0
+    offs = np.zeros(n + 1, np.int64)
+    offs[1:] = np.cumsum([d.size for d in docs])
+    toks = np.concatenate(docs).astype(np.int32)
+
+    def eager(o, t):
+        sig, sh = mrc.mrc_signature(ctx, idx, o, t)
+        sp = mrc.pairs_to_numpy(mrc.mrc_match(ctx, idx, sig, 0.9, device=None)[0])
+        hp = mrc.pairs_to_numpy(mrc.simhash_index_match(ctx, shx, torch.from_numpy(sh.view(np.int64)).cuda(),
+                                                        3, device=None)[0])
+        return sorted(sp.tolist()), sorted(hp.tolist())
+
+    want_s, want_h = eager(offs, toks)
+    assert len(want_s) > 20 and len(want_h) > 0
+    b = mrc.Batch(ctx, idx, 128, 80000, 0.9, capacity=1 << 16)
+    b.attach_simhash(shx, 3, 1 << 16)
+    assert b.kernel_nodes == 1
+
+    def check(o, t, ws, wh):
+        b.launch(o, t)
+        got, total, qoff = b.wait(offsets=True)
+        hp, htot, hqoff = b.hamming(offsets=True)
+        assert sorted(got.tolist()) == ws and total == len(ws)
+        assert sorted(hp.tolist()) == wh and htot == len(wh)
+        for pairs, off in ((got, qoff), (hp, hqoff)):
+            assert off[0] == 0 and off[-1] == len(pairs) and np.all(np.diff(off) >= 0)
+            for q in range(len(off) - 1):
+                assert np.all(pairs["i"][off[q]:off[q + 1]] == q)
+
+    check(offs, toks, want_s, want_h)
+    bad = offs.copy()
+    bad[4] = bad[2] - 1  # document 3 ends before it starts
+    b.launch(bad, toks)
+    with pytest.raises(mrc.MrcError) as ei:
+        b.wait()
+    assert ei.value.status == mrc.MRC_ERR_INVALID
+    check(offs, toks, want_s, want_h)
+    m = 17  # fewer documents than the launch before
+    ws, wh = eager(offs[:m + 1], toks[:offs[m]])
+    check(offs[:m + 1], toks[:offs[m]], ws, wh)
+    b.free()
+    shx.free()
+    idx.free()
+
+
 def test_batch_runner_buckets_and_autotune(env, tmp_path):
     mrc, ctx, c = env["mrc"], env["ctx"], env["c"]
     from paper_1810_03099_gb300 import batching
     idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, mrc.params_default(k=32))
     qo, qt = _queries(c, 300, 9)
     batches = batching.make_batches(qo, qt, [1, 7, 64, 200, 33], seed=3)
-    tn = batching.autotune_tile(ctx, idx, 64, 64 * 5000, batches[2][:2], reps=2, cache=str(tmp_path / "t.json"))
-    assert tn in (128, 256)
-    assert batching.autotune_tile(ctx, idx, 64, 64 * 5000, batches[2][:2], cache=str(tmp_path / "t.json")) == tn
+    knobs = batching.autotune(ctx, idx, 64, 64 * 5000, batches[2][:2], reps=1, cache=str(tmp_path / "t.json"),
+                              rings=(0, 3), prefetches=(0, 8))
+    assert knobs["tile_n"] in (128, 256) and knobs["ring"] in (0, 3) and knobs["prefetch"] in (0, 8)
+    assert batching.autotune(ctx, idx, 64, 64 * 5000, batches[2][:2], cache=str(tmp_path / "t.json")) == knobs
     runner = batching.BatchRunner(ctx, idx, 0.9, max_docs=256, max_doc_tokens=5000, autotune=False)
     for offs, toks, pick in batches:
         got, total = runner.run(offs, toks)
