@@ -220,14 +220,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
       for (int c = 0; c < BN / 32; ++c) {
         float v[32];
-        tmem_ld32(trow + c * 32, v);
+        float m;  // the chunk's row maximum (thresholding)
         if (C::ACCS == 2) {
+          tmem_ld32(trow + c * 32, v);
           float x[32];
           tmem_ld32(trow + 128 + c * 32, x);
           tmem_wait_ld();
 #pragma unroll
           for (int e = 0; e < 32; ++e) v[e] = fmaf(x[e], 1.0f / kSplitLoScale, v[e]);
+          m = max32(v);
         } else {
+          tmem_ld32_max(trow + c * 32, v, m);
           tmem_wait_ld();
         }
         const int64_t j0 = bj * BN + c * 32;
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         } else {
-          emit_chunk<FMT>(p, v, max32(v), i, j0, lane, fast_thresh, row_norm, hit_lim, stage, pbuf, nbuf);
+          emit_chunk<FMT>(p, v, m, i, j0, lane, fast_thresh, row_norm, hit_lim, stage, pbuf, nbuf);
         }
       }
       tc_fence_before();

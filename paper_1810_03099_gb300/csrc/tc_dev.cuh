@@ -180,6 +180,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+// The same load, which also returns the largest of the 32 values each thread loads (the
+// reduction of tcgen05.ld.red, sm_103a): a chunk's row maximum at no ALU cost.
+__device__ __forceinline__ void tmem_ld32_max(uint32_t taddr, float (&v)[32], float& m) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+      "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, %32, [%33];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=f"(m)
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 // L2 prefetch of one tensor-map tile (no shared memory, no completion to wait for).
 __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* tm, int x, int y) {
@@ -627,20 +642,26 @@ __device__ __forceinline__ void resident_body(const CUtensorMap* tA0, const CUte
       if (!ok) break;
       tc_fence_after();
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + ab * (uint32_t)(C::ACCS * BN);
-      // all of this warp's TMEM loads are issued before one wait, so they overlap
+      // all of this warp's TMEM loads are issued before one wait, so they overlap; with one
+      // accumulator the load also reduces each chunk to its row maximum
       float v[CH][32];
-#pragma unroll
-      for (int c = 0; c < CH; ++c) tmem_ld32(trow + (half * CH + c) * 32, v[c]);
+      float mc[CH];
       if (C::ACCS == 2) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) tmem_ld32(trow + (half * CH + c) * 32, v[c]);
         float x[CH][32];
 #pragma unroll
         for (int c = 0; c < CH; ++c) tmem_ld32(trow + BN + (half * CH + c) * 32, x[c]);
         tmem_wait_ld();
 #pragma unroll
-        for (int c = 0; c < CH; ++c)
+        for (int c = 0; c < CH; ++c) {
 #pragma unroll
           for (int e = 0; e < 32; ++e) v[c][e] = fmaf(x[c][e], 1.0f / kSplitLoScale, v[c][e]);
+          mc[c] = max32(v[c]);
+        }
       } else {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) tmem_ld32_max(trow + (half * CH + c) * 32, v[c], mc[c]);
         tmem_wait_ld();
       }
       // the accumulators are in registers: hand the TMEM buffer back before thresholding
@@ -648,12 +669,8 @@ __device__ __forceinline__ void resident_body(const CUtensorMap* tA0, const CUte
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[ab]);
       // a warp's columns lie in one 128-column block, so one fast threshold covers all its
-      // chunks; the usual case, no lane near it in any chunk, costs the maxima (a tree of
-      // three-input maxima per chunk) and one vote
+      // chunks; the usual case, no lane near it in any chunk, costs one vote on the maxima
       const float fast_thresh = (FMT == OP_E4M3 && p.thresh > 0.f) ? row_bound * nmin : row_bound;
-      float mc[CH];
-#pragma unroll
-      for (int c = 0; c < CH; ++c) mc[c] = max32(v[c]);
       float mall = mc[0];
 #pragma unroll
       for (int c = 1; c < CH; ++c) mall = fmaxf(mall, mc[c]);
