@@ -75,12 +75,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
   float* stage_all = reinterpret_cast<float*>(drain + 4);  // [4 epilogue warps][32 x 33] scores
-  mrc_pair* pbuf_all = reinterpret_cast<mrc_pair*>(stage_all + 4 * 32 * 33);  // [4][kPairBuf]
+  uint8_t* pbuf_all = reinterpret_cast<uint8_t*>(stage_all + 4 * 32 * 33);  // [4 epilogue warps] pairs, fill
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* stage = stage_all + (warp >= 2 ? warp - 2 : 0) * 32 * 33;
-  mrc_pair* pbuf = pbuf_all + (warp >= 2 ? warp - 2 : 0) * kPairBuf;
-  int nbuf = 0;
+  mrc_pair* pbuf = reinterpret_cast<mrc_pair*>(pbuf_all + (warp >= 2 ? warp - 2 : 0) * kWarpPairBytes);
+  int32_t* pfill = reinterpret_cast<int32_t*>(pbuf + kPairBuf);
+  if (warp >= 2 && (threadIdx.x & 31) == 0) *pfill = 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         } else {
-          emit_chunk<FMT>(p, v, m, i, j0, lane, fast_thresh, row_norm, hit_lim, stage, pbuf, nbuf);
+          emit_chunk<FMT>(p, v, m, i, j0, lane, fast_thresh, row_norm, hit_lim, stage, pbuf, pfill);
         }
       }
       tc_fence_before();
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) mbar_arrive(&acc_empty[ab]);
       ++it;
     }
-    flush_pairs(p, pbuf, nbuf, lane);
+    flush_pairs(p, pbuf, pfill, lane);
   }
   tc_fence_before();
   __syncthreads();
@@ -422,8 +423,8 @@ cudaError_t run_gemm(mrc_ctx* ctx, const GemmArgs& g) {
   p.timeout_ns = ctx->wait_limit_ns;
   p.exact = g.exact_scores;
   p.stall = ctx->test_stall ? 1 : 0;
-  const size_t smem = 1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256 + 4 * 32 * 33 * 4 +
-                      4 * kPairBuf * sizeof(mrc_pair);
+  const size_t smem =
+      1024 + (size_t)C::STAGES * C::NOPS * (kBM + BN) * kRowBytes + 256 + 4 * (32 * 33 * 4 + kWarpPairBytes);
   if (resident_ctas(k_gemm_compare<FMT>, kThreads, smem) <= 0) return cudaErrorInvalidConfiguration;
   int64_t grid = ctx->num_sms;
   if (p.n_tiles < grid) grid = p.n_tiles;

@@ -23,7 +23,9 @@ constexpr int kRowBytes = 128;  // K bytes per stage per row (one 128B swizzle a
 // frees TMEM and exits. They complete in microseconds; the bound only keeps a broken invariant
 // from spinning forever (it is then reported as a timeout too).
 constexpr uint64_t kDrainNs = 2000000000ull;
-constexpr int kPairBuf = 64;  // pairs buffered per epilogue warp before one global atomic
+constexpr int kPairBuf = 256;  // pairs buffered per epilogue warp (then its fill count)
+constexpr int kFlushAt = 192;  // a warp flushes its buffer to the global list at this many pairs
+constexpr size_t kWarpPairBytes = kPairBuf * sizeof(mrc_pair) + 16;  // one warp's buffer and count
 constexpr float kNormLo = 0.93f;  // lower bound of |e4m3(x * 256)| / 256 for unit x (1 - 2^-4 = 0.9375)
 
 template <int FMT>
@@ -219,44 +221,55 @@ __device__ __forceinline__ float max32(const float (&v)[32]) {
   return fmax3(fmax3(a[9], a[10], b0), b1, b2);
 }
 
-// Writes a warp's buffered pairs (nbuf of them, in buf) to the global list with one atomic.
-__device__ __forceinline__ void flush_pairs(const GemmParams& p, const mrc_pair* buf, int& nbuf, int lane) {
-  if (nbuf == 0) return;
-  unsigned long long base = 0;
-  if (lane == 0) base = atomicAdd(p.count, (unsigned long long)nbuf);
-  base = __shfl_sync(kFull, base, 0);
-  for (int x = lane; x < nbuf; x += 32)
-    if (base + x < (unsigned long long)p.capacity) p.pairs[base + x] = buf[x];
-  nbuf = 0;
+// Writes a warp's buffered pairs (min(*fill, kPairBuf) slots of buf) to the global list with
+// one atomic and empties the buffer. Slots with i < 0 are holes (a lane whose hits did not fit
+// sent them out directly) and are skipped. Called by the whole warp.
+__device__ __forceinline__ void flush_pairs(const GemmParams& p, mrc_pair* buf, int32_t* fill, int lane) {
+  __syncwarp();
+  const int n = min(*fill, kPairBuf);
+  int valid = 0;
+  for (int x = lane; x < n; x += 32) valid += buf[x].i >= 0 ? 1 : 0;
+  valid = warp_sum(valid);
+  if (valid) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(p.count, (unsigned long long)valid);
+    base = __shfl_sync(kFull, base, 0);
+    for (int b0 = 0; b0 < n; b0 += 32) {
+      const int x = b0 + lane;
+      const bool ok = x < n && buf[x].i >= 0;
+      const unsigned bal = __ballot_sync(kFull, ok);
+      const unsigned long long at = base + __popc(bal & ((1u << lane) - 1u));
+      if (ok && at < (unsigned long long)p.capacity) p.pairs[at] = buf[x];
+      base += __popc(bal);
+    }
+  }
+  __syncwarp();
+  if (lane == 0) *fill = 0;
   __syncwarp();
 }
 
 // Threshold one 32-column chunk held in registers (v[e] = score of column j0 + e for this
-// lane's row i) and append its pairs. Fast path: the chunk's maximum misses fast_thresh in
-// every lane. Otherwise each lane builds the 32-bit mask of its hits straight from its
-// registers and applies the bounds and the triangle's j > i with bit arithmetic. fp16: a hit
-// is v[e] >= hit_lim, scored with v[e]. E4M3: a hit passes the row's block bound
-// (fast_thresh, which uses the smallest column norm of the 128-column block); the caller
-// rescores every hit in FP32, so the raw accumulator is its score. With p.exact (the
-// candidates themselves are the result) each such hit is tested exactly,
-// v[e] >= hit_lim * |q_j| with the column's norm (zero norms never hit), and scored with the
-// cosine of the quantized vectors. The warp then appends its hits to its pair buffer.
+// lane's row i; m = this lane's maximum over the chunk) and append its pairs to the warp's
+// buffer. The usual case, no lane at fast_thresh, costs one vote. Otherwise each lane builds
+// the 32-bit mask of its hits straight from its registers and applies the bounds and the
+// triangle's j > i with bit arithmetic; fp16: a hit is v[e] >= hit_lim (= fast_thresh),
+// scored with v[e]. E4M3: a hit passes the row's block bound (fast_thresh, which uses the
+// smallest column norm of the 128-column block); the caller rescores every hit in FP32, so
+// the raw accumulator is its score. With p.exact (the candidates themselves are the result)
+// each such hit is tested exactly, v[e] >= hit_lim * |q_j| with the column's norm (zero norms
+// never hit), and scored with the cosine of the quantized vectors. A lane with hits stages its
+// scores in its row of the warp's 32 x 33 area (so that the loops below index them at run time
+// and stay compact: they run only for the rare chunks with hits), reserves its buffer slots
+// with one shared-memory atomic and writes its hits; the warp flushes at kFlushAt pairs.
 template <int FMT>
 __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)[32], float m, int64_t i, int64_t j0,
                                            int lane, float fast_thresh, float row_norm, float hit_lim, float* stage,
-                                           mrc_pair* buf, int& nbuf) {
-  if (!__any_sync(kFull, m >= fast_thresh)) return;  // m: this lane's maximum over the chunk
+                                           mrc_pair* buf, int32_t* fill) {
+  if (!__any_sync(kFull, m >= fast_thresh)) return;
   uint32_t mask = 0;
-  if (FMT == OP_E4M3) {
-    // the block bound first (no per-column data); the exact test v >= hit_lim |q_j| follows
-    // for the few columns that pass it; zero norms never hit
-    if (row_norm > 0.f) {
+  if (FMT != OP_E4M3 || row_norm > 0.f) {
 #pragma unroll
-      for (int e = 0; e < 32; ++e) mask |= (v[e] >= fast_thresh ? 1u : 0u) << e;
-    }
-  } else {
-#pragma unroll
-    for (int e = 0; e < 32; ++e) mask |= (v[e] >= hit_lim ? 1u : 0u) << e;
+    for (int e = 0; e < 32; ++e) mask |= (v[e] >= fast_thresh ? 1u : 0u) << e;
   }
   const int64_t lim = p.nb - j0;  // columns j0 + e < nb
   if (lim < 32) mask &= lim <= 0 ? 0u : ((1u << lim) - 1u);
@@ -266,10 +279,8 @@ __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)
     else if (dlt >= 0) mask &= ~((2u << dlt) - 1u);
   }
   if (i >= p.na || (p.na_live && i >= *p.na_live)) mask = 0u;
-  // the lane's scores go to its row of the warp's 32 x 33 staging area, so that the loops
-  // below index them at run time (compact code: they run only for the rare chunks with hits)
-  float* sc = stage + lane * 33;
   if (mask) {
+    float* sc = stage + lane * 33;
 #pragma unroll
     for (int e = 0; e < 32; ++e) sc[e] = v[e];
     if (FMT == OP_E4M3 && p.exact) {
@@ -282,41 +293,32 @@ __device__ __forceinline__ void emit_chunk(const GemmParams& p, const float (&v)
           mask &= ~(1u << e);
       }
     }
-  }
-  const uint32_t hits = mask;
-  const int cnt = __popc(hits);
-  int incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(kFull, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const int total = __shfl_sync(kFull, incl, 31);
-  if (total) {
-    // pairs go to the warp's buffer (one global atomic per flush instead of per chunk); a
-    // chunk with more pairs than the buffer holds goes out directly
-    if (nbuf + total > kPairBuf) flush_pairs(p, buf, nbuf, lane);
-    const bool direct = total > kPairBuf;
-    unsigned long long base = 0;
-    if (direct) {
-      if (lane == 31) base = atomicAdd(p.count, (unsigned long long)total);
-      base = __shfl_sync(kFull, base, 31);
+    const int cnt = __popc(mask);
+    if (cnt) {
+      int pos = atomicAdd(fill, cnt);
+      const bool direct = pos + cnt > kPairBuf;
+      unsigned long long g = 0;
+      if (direct) {  // no room: holes in the slots reserved inside the buffer, the hits go out directly
+        for (int x = pos; x < kPairBuf && x < pos + cnt; ++x) buf[x].i = -1;
+        g = atomicAdd(p.count, (unsigned long long)cnt);
+      }
+      for (uint32_t hh = mask; hh; hh &= hh - 1u) {
+        const int e = __ffs(hh) - 1;
+        mrc_pair pr;
+        pr.i = (int32_t)i;
+        pr.j = (int32_t)(j0 + e);
+        pr.score = sc[e];
+        if (!direct) {
+          buf[pos++] = pr;
+        } else {
+          if (g < (unsigned long long)p.capacity) p.pairs[g] = pr;
+          ++g;
+        }
+      }
     }
-    int at = incl - cnt;
-    for (uint32_t hh = hits; hh; hh &= hh - 1u, ++at) {
-      const int e = __ffs(hh) - 1;
-      mrc_pair pr;
-      pr.i = (int32_t)i;
-      pr.j = (int32_t)(j0 + e);
-      pr.score = sc[e];
-      if (!direct)
-        buf[nbuf + at] = pr;
-      else if (base + at < (unsigned long long)p.capacity)
-        p.pairs[base + at] = pr;
-    }
-    if (!direct) nbuf += total;
   }
   __syncwarp();
+  if (*fill >= kFlushAt) flush_pairs(p, buf, fill, lane);
 }
 
 
@@ -331,7 +333,7 @@ constexpr int kResThreads = 64 + 32 * kResEpiWarps;  // warp 0 TMA, warp 1 MMA +
 // buffers and the epilogue's staging. The B tiles come from L2 with a latency of about
 // a microsecond, so a CTA needs that many bytes in flight to stream at the rate its tensor core
 // consumes them (E4M3 tiles are half the size of fp16 ones and go by twice as fast). 3 to 12.
-constexpr size_t kResEpiBytes = kResEpiWarps * (32 * 33 * sizeof(float) + kPairBuf * sizeof(mrc_pair));
+constexpr size_t kResEpiBytes = kResEpiWarps * (kWarpPairBytes + 32 * 33 * sizeof(float));
 __host__ __device__ constexpr int res_stages_b(int nops, int rb, int bn) {
   return (int)(((227u * 1024u - 1024u - kResEpiBytes - 512u) - 2u * nops * kBM * rb) / ((size_t)nops * bn * rb)) > 12
              ? 12
@@ -466,12 +468,13 @@ __device__ __forceinline__ void resident_body(const CUtensorMap* tA0, const CUte
   uint64_t* drain = acc_empty + NB;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 1);
   float* stage_all = reinterpret_cast<float*>(drain + 4);  // [epilogue warps][32 x 33] scores
-  mrc_pair* pbuf_all = reinterpret_cast<mrc_pair*>(stage_all + kResEpiWarps * 32 * 33);  // [epilogue warps][kPairBuf]
+  uint8_t* pbuf_all = reinterpret_cast<uint8_t*>(stage_all + kResEpiWarps * 32 * 33);  // [epilogue warps] pairs, fill
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* stage = stage_all + (warp >= 2 ? warp - 2 : 0) * 32 * 33;
-  mrc_pair* pbuf = pbuf_all + (warp >= 2 ? warp - 2 : 0) * kPairBuf;
-  int nbuf = 0;
+  mrc_pair* pbuf = reinterpret_cast<mrc_pair*>(pbuf_all + (warp >= 2 ? warp - 2 : 0) * kWarpPairBytes);
+  int32_t* pfill = reinterpret_cast<int32_t*>(pbuf + kPairBuf);
+  if (warp >= 2 && (threadIdx.x & 31) == 0) *pfill = 0;
   if (threadIdx.x == 0) {
     for (int b = 0; b < 2; ++b) {
       mbar_init(&a_full[b], 1);
@@ -678,12 +681,12 @@ __device__ __forceinline__ void resident_body(const CUtensorMap* tA0, const CUte
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
           const int64_t j0 = bj * BN + (half * CH + c) * 32;
-          emit_chunk<FMT>(p, v[c], mc[c], i, j0, lane, fast_thresh, row_norm, hit_lim, stage, pbuf, nbuf);
+          emit_chunk<FMT>(p, v[c], mc[c], i, j0, lane, fast_thresh, row_norm, hit_lim, stage, pbuf, pfill);
         }
       }
       ++it;
     }
-    flush_pairs(p, pbuf, nbuf, lane);
+    flush_pairs(p, pbuf, pfill, lane);
   }
 }
 
