@@ -947,11 +947,16 @@ def serving_leg(n_index, rates=(10000, 50000, 100000, 250000, 500000), requests=
     n_tok = c.n_tokens
     del c
     torch.cuda.empty_cache()
+    # the index's Simhashes in a block-table index: every request is also matched by Hamming
+    # distance <= HMAX inside its slot's launch
+    fps = mrc.index_simhash(ctx, idx, torch.empty(n_index, dtype=torch.int64, device="cuda"))
+    shx = mrc.simhash_index_build(ctx, fps, HMAX)
+    del fps
     pool = synth.make_corpus_device(synth.SPECS["precision"].with_(n_docs=requests, seed=BASE_QUERY_SEED))
     pool = pool.host_subset(np.arange(requests))
     docs = [pool.doc(i) for i in range(pool.n_docs)]
     srv = serving.Server(ctx, idx, TAU, micro_batch=128, deadline_s=1e-3, slots=4, max_doc_tokens=10000,
-                         capacity=1 << 21)
+                         capacity=1 << 21, simhash_index=shx, hamming_max=HMAX, hamming_capacity=1 << 18)
     srv.run(docs[:1000], np.zeros(1000))  # warm-up
     rows = []
     for rate in rates:
@@ -960,11 +965,13 @@ def serving_leg(n_index, rates=(10000, 50000, 100000, 250000, 500000), requests=
         rep = serving.latency_report(reqs, srv.wall_s)
         rep["rate"] = rate
         rep["pairs_per_request"] = float(np.mean([len(r.pairs) for r in reqs]))
+        rep["hamming_pairs_per_request"] = float(np.mean([len(r.hamming) for r in reqs]))
         rows.append(rep)
     srv.free()
+    shx.free()
     idx.free()
     ctx.close()
-    return {"index_docs": n_index, "index_tokens": n_tok, "micro_batch": 128, "deadline_ms": 1.0,
+    return {"index_docs": n_index, "index_tokens": n_tok, "hamming_max": HMAX, "micro_batch": 128, "deadline_ms": 1.0,
             "slots": srv.admitted_slots, "requests_per_rate": requests, "rates": rows}
 
 

@@ -317,7 +317,9 @@ mrc_status mrc_ctx_sync(mrc_ctx* ctx);
  *     pairs to `pairs` (host or device), grouped by query position i (order
  *     within a query unspecified); *n_pairs = total; query_offsets (may be NULL,
  *     [n_docs + 1] of the last launch) receives where each query's pairs start.
- *     MRC_ERR_CAPACITY when the pairs (or the internal candidate list) overflowed.
+ *     pairs may be NULL (the total only). The results stay available until the
+ *     next launch: calling it again copies them again. MRC_ERR_CAPACITY when the
+ *     pairs (or the internal candidate list) overflowed.
  */
 typedef struct mrc_batch mrc_batch;
 typedef struct mrc_simhash_index mrc_simhash_index; /* block-table fingerprint index (below) */
@@ -342,10 +344,10 @@ void mrc_batch_free(mrc_batch* batch);
  * score = the Hamming distance, grouped by query like the signature pairs;
  * capacity bounds the Hamming pairs of one batch. Call it with no launch in
  * flight; the batch keeps `index` (not owned; it must outlive the batch).
- * mrc_batch_hamming, after mrc_batch_wait: copies min(total, capacity) pairs
- * of the last launch (host or device), *n_pairs = total, query_offsets (may be
- * NULL, [n_docs + 1]) where each query's pairs start. MRC_ERR_CAPACITY on
- * overflow. The results equal mrc_simhash_index_match with the batch's
+ * mrc_batch_hamming (waits for the launch like mrc_batch_wait): copies
+ * min(total, capacity) pairs of the last launch (host or device; pairs may be
+ * NULL), *n_pairs = total, query_offsets (may be NULL, [n_docs + 1]) where each
+ * query's pairs start. MRC_ERR_CAPACITY on overflow. The results equal mrc_simhash_index_match with the batch's
  * fingerprints as queries.
  */
 mrc_status mrc_batch_attach_simhash(mrc_batch* batch, const mrc_simhash_index* index, int32_t hamming_max,

@@ -71,6 +71,7 @@ struct mrc_batch {
   int32_t kernel_nodes = 0;  // kernel nodes of the captured graph
   cudaEvent_t done = nullptr;
   bool pending = false;
+  bool has_result = false;  // the last launch finished; its results can be copied out (again)
   int64_t last_n = 0;  // documents of the last launch
 };
 
@@ -324,6 +325,46 @@ void release(mrc_batch* b) {
   delete b;
 }
 
+// Waits for the last launch (once) and checks its error word; the results stay available until
+// the next launch.
+mrc_status finish_launch(mrc_batch* b) {
+  mrc_ctx* ctx = b->ctx;
+  if (b->pending) {
+    const cudaError_t e = cudaEventSynchronize(b->done);
+    b->pending = false;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "mrc_batch_wait");
+    b->has_result = true;
+  }
+  if (!b->has_result) return fail(ctx, MRC_ERR_INVALID, "mrc_batch_wait: nothing launched");
+  int32_t err = 0;
+  std::memcpy(&err, b->h_counts + 2, sizeof(int32_t));
+  if (err & kErrTimeout) return fail(ctx, MRC_ERR_TIMEOUT, "a bounded device wait expired");
+  if (err & kErrBadToken) return fail(ctx, MRC_ERR_INVALID, "a token id is outside [0, vocab)");
+  if (err & kErrBadOffsets) return fail(ctx, MRC_ERR_INVALID, "offsets must start at 0 and be non-decreasing");
+  if (err & kErrTooLong) return fail(ctx, MRC_ERR_UNSUPPORTED, "a document is longer than MRC_MAX_DOC_TOKENS tokens");
+  return MRC_OK;
+}
+
+// Copies a finished launch's grouped pairs (min(total, own capacity, capacity) of them) and
+// its query offsets out, on the batch's stream.
+mrc_status copy_out(mrc_batch* b, const mrc_pair* d_pairs, int64_t total, int64_t own_cap, const int64_t* d_off,
+                    mrc_pair* pairs, int64_t capacity, int64_t* query_offsets, const char* what) {
+  mrc_ctx* ctx = b->ctx;
+  const int64_t m = std::min<int64_t>(std::min<int64_t>(total, own_cap), capacity);
+  cudaError_t e = cudaSuccess;
+  if (m > 0 && pairs)
+    e = cudaMemcpyAsync(pairs, d_pairs, sizeof(mrc_pair) * (size_t)m, cudaMemcpyDefault, ctx->stream);
+  if (e == cudaSuccess && query_offsets)
+    e = cudaMemcpyAsync(query_offsets, d_off, sizeof(int64_t) * (size_t)(b->last_n + 1), cudaMemcpyDefault,
+                        ctx->stream);
+  if (e == cudaSuccess && ((m > 0 && pairs) || query_offsets)) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+  if (pairs && total > std::min(capacity, own_cap))
+    return fail(ctx, MRC_ERR_CAPACITY, "more pairs than capacity; *n_pairs holds the total");
+  if (!pairs && total > own_cap) return fail(ctx, MRC_ERR_CAPACITY, "more pairs than the batch's capacity");
+  return MRC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -452,6 +493,7 @@ mrc_status mrc_batch_launch(mrc_batch* b, const mrc_docs* docs) {
   if (e == cudaSuccess) e = cudaEventRecord(b->done, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "mrc_batch_launch");
   b->pending = true;
+  b->has_result = false;
   b->last_n = n;
   return MRC_OK;
 }
@@ -469,34 +511,16 @@ int32_t mrc_batch_poll(mrc_batch* b) {
 mrc_status mrc_batch_wait(mrc_batch* b, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs, int64_t* query_offsets) {
   if (!b) return MRC_ERR_INVALID;
   mrc_ctx* ctx = b->ctx;
+  cudaSetDevice(ctx->device);
   if (n_pairs) *n_pairs = 0;
-  if (!b->pending) return fail(ctx, MRC_ERR_INVALID, "mrc_batch_wait: nothing launched");
-  cudaError_t e = cudaEventSynchronize(b->done);
-  b->pending = false;
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "mrc_batch_wait");
+  const mrc_status st = finish_launch(b);
+  if (st != MRC_OK) return st;
   const int64_t total = (int64_t)b->h_counts[0];
   const int64_t cand = (int64_t)b->h_counts[1];
-  int32_t err = 0;
-  std::memcpy(&err, b->h_counts + 2, sizeof(int32_t));
-  if (err & kErrTimeout) return fail(ctx, MRC_ERR_TIMEOUT, "a bounded device wait expired");
-  if (err & kErrBadToken) return fail(ctx, MRC_ERR_INVALID, "a token id is outside [0, vocab)");
-  if (err & kErrBadOffsets) return fail(ctx, MRC_ERR_INVALID, "offsets must start at 0 and be non-decreasing");
-  if (err & kErrTooLong) return fail(ctx, MRC_ERR_UNSUPPORTED, "a document is longer than MRC_MAX_DOC_TOKENS tokens");
   if (n_pairs) *n_pairs = total;
   if (cand > b->cand_cap)
     return fail(ctx, MRC_ERR_CAPACITY, "candidate list overflowed: create the batch with a larger capacity");
-  const int64_t m = std::min<int64_t>(std::min<int64_t>(total, b->capacity), capacity);
-  if (m > 0 && pairs) {
-    e = cudaMemcpy(pairs, b->d_grouped, sizeof(mrc_pair) * (size_t)m, cudaMemcpyDefault);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "copying batch pairs");
-  }
-  if (query_offsets) {
-    e = cudaMemcpy(query_offsets, b->d_qoff, sizeof(int64_t) * (size_t)(b->last_n + 1), cudaMemcpyDefault);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "copying query offsets");
-  }
-  if (total > std::min(capacity, b->capacity))
-    return fail(ctx, MRC_ERR_CAPACITY, "more pairs than capacity; *n_pairs holds the total");
-  return MRC_OK;
+  return copy_out(b, b->d_grouped, total, b->capacity, b->d_qoff, pairs, capacity, query_offsets, "copying batch pairs");
 }
 
 mrc_status mrc_batch_attach_simhash(mrc_batch* b, const mrc_simhash_index* index, int32_t hamming_max,
@@ -533,20 +557,14 @@ mrc_status mrc_batch_hamming(mrc_batch* b, mrc_pair* pairs, int64_t capacity, in
   mrc_ctx* ctx = b->ctx;
   if (n_pairs) *n_pairs = 0;
   if (!b->shx) return fail(ctx, MRC_ERR_INVALID, "mrc_batch_hamming: no fingerprint index attached");
-  if (b->pending) return fail(ctx, MRC_ERR_INVALID, "mrc_batch_hamming: wait for the launch first");
   cudaSetDevice(ctx->device);
+  const mrc_status st = finish_launch(b);
+  if (st != MRC_OK) return st;
   int64_t total = 0;  // the real queries' pairs: grouped by query, they come first
   std::memcpy(&total, b->h_counts + 3, sizeof(int64_t));
   if (n_pairs) *n_pairs = total;
-  const int64_t m = std::min<int64_t>(std::min<int64_t>(total, b->h_capacity), capacity);
-  cudaError_t e = cudaSuccess;
-  if (m > 0 && pairs) e = cudaMemcpy(pairs, b->d_hgrouped, sizeof(mrc_pair) * (size_t)m, cudaMemcpyDefault);
-  if (e == cudaSuccess && query_offsets)
-    e = cudaMemcpy(query_offsets, b->d_hqoff, sizeof(int64_t) * (size_t)(b->last_n + 1), cudaMemcpyDefault);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "copying Hamming pairs");
-  if (total > std::min(capacity, b->h_capacity))
-    return fail(ctx, MRC_ERR_CAPACITY, "more Hamming pairs than capacity; *n_pairs holds the total");
-  return MRC_OK;
+  return copy_out(b, b->d_hgrouped, total, b->h_capacity, b->d_hqoff, pairs, capacity, query_offsets,
+                  "copying Hamming pairs");
 }
 
 mrc_status mrc_batch_tune(mrc_batch* b, int32_t tile_n, int32_t ring, int32_t prefetch) {

@@ -277,7 +277,7 @@ def _pinned_pairs(n: int) -> np.ndarray:
     The array is a view of a pinned torch tensor, which numpy keeps alive as the view's base."""
     import torch
     try:
-        t = torch.empty(max(n, 1) * PAIR_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+        t = torch.empty(max(n, 1) * PAIR_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
     except RuntimeError:  # no device to pin for: plain host memory
         return np.empty(max(n, 1), PAIR_DTYPE)
     return t.numpy().view(PAIR_DTYPE)
@@ -344,6 +344,17 @@ class Batch:
         pairs = buf[:m].copy() if own else buf[:m]
         return (pairs, int(total.value), qoff) if offsets else (pairs, int(total.value))
 
+    def totals(self):
+        """Wait for the last launch and return its (signature pair, Hamming pair) totals without
+        copying pairs (errors are raised as by wait); the pairs can then be copied with wait() /
+        hamming() until the next launch."""
+        t = C.c_int64()
+        self._check(self.ctx.lib.mrc_batch_wait(self.handle, None, 0, C.byref(t), None))
+        h = C.c_int64(0)
+        if getattr(self, "h_capacity", None):
+            self._check(self.ctx.lib.mrc_batch_hamming(self.handle, None, 0, C.byref(h), None))
+        return int(t.value), int(h.value)
+
     def attach_simhash(self, shindex: "SimhashIndex", hamming_max: int | None = None, capacity: int = 1 << 16):
         """Add the Hamming leg: each launch also probes `shindex` with the batch's Simhashes."""
         hm = shindex.hamming_max if hamming_max is None else int(hamming_max)
@@ -351,17 +362,24 @@ class Batch:
         self.h_capacity = int(capacity)
         self._shindex = shindex  # the batch keeps the fingerprint index in use
 
-    def hamming(self, offsets=False):
+    def hamming(self, out=None, offsets=False):
         """After wait(): the last launch's Hamming pairs (query position, index position, distance),
-        grouped by query; with offsets=True also where each query's pairs start."""
+        grouped by query; with offsets=True also where each query's pairs start. Without `out`
+        the pairs land in a buffer owned by this object and a copy of them is returned."""
         n = getattr(self, "_last_n", 0)
-        if getattr(self, "_hout", None) is None:
-            self._hout = _pinned_pairs(self.h_capacity)
+        own = out is None
+        if own:
+            if getattr(self, "_hout", None) is None:
+                self._hout = _pinned_pairs(self.h_capacity)
+            buf = self._hout
+        else:
+            buf = out
         qoff = np.zeros(n + 1, np.int64)
         total = C.c_int64()
-        self._check(self.ctx.lib.mrc_batch_hamming(self.handle, _ptr(self._hout), int(self._hout.shape[0]),
+        self._check(self.ctx.lib.mrc_batch_hamming(self.handle, _ptr(buf), int(buf.shape[0]),
                                                    C.byref(total), qoff.ctypes.data if offsets else None))
-        pairs = self._hout[:min(int(total.value), self._hout.shape[0])].copy()
+        m = min(int(total.value), buf.shape[0])
+        pairs = buf[:m].copy() if own else buf[:m]
         return (pairs, int(total.value), qoff) if offsets else (pairs, int(total.value))
 
     def free(self):

@@ -8,7 +8,9 @@ host loop
     graph-captured ``mrc_batch`` with its own stream, so batches launched while
     others are still on the GPU overlap on the device;
   * completes slots as their GPU work finishes (non-blocking polls) and stamps
-    every request's latency (completion minus arrival).
+    every request's latency (completion minus arrival). A finished batch's pairs go by
+    one DMA straight into a ring of pinned host memory, and each request's pairs are a view
+    of its slice; before a ring region is reused, the requests still viewing it get copies.
 With a block-table fingerprint index of the resident documents' Simhashes, every slot also
 matches its requests' Simhashes against it (Hamming pairs per request, beside the
 signature pairs).
@@ -20,7 +22,9 @@ pairs are the same alone and in the mix.
 """
 from __future__ import annotations
 
+import collections
 import time
+import weakref
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -48,11 +52,42 @@ def slot_footprint(index, max_docs: int, max_tokens: int, capacity: int) -> int:
     return 8 * (max_docs + 1) + 4 * max_tokens + 4 * max_docs * k + op + 4 * max_docs + cand + 12 * capacity + ws + grouped
 
 
+class _Ring:
+    """Pinned host arena for batch results, handed out in order and wrapping around. Live
+    regions are kept oldest first; a region about to be overwritten first gives the requests
+    still viewing it (held elsewhere) their own copies."""
+
+    def __init__(self, n_pairs: int, attr: str):
+        self.buf = mrc._pinned_pairs(n_pairs)
+        self.n, self.head, self.attr = self.buf.shape[0], 0, attr
+        self.live: collections.deque = collections.deque()  # (start, end, requests)
+        self.evicted = 0  # requests given their own copies
+
+    def take(self, m: int):
+        """A view of m free slots (None if m exceeds the arena)."""
+        if m > self.n:
+            return None
+        start = self.head if self.head + m <= self.n else 0
+        end = start + m
+        while self.live and self.live[0][0] < end and start < self.live[0][1]:
+            for w in self.live.popleft()[2]:
+                r = w()
+                if r is not None:  # still held by the caller
+                    setattr(r, self.attr, getattr(r, self.attr).copy())
+                    self.evicted += 1
+        self.head = end
+        return start
+
+    def keep(self, start: int, m: int, reqs):
+        if m:
+            self.live.append((start, start + m, [weakref.ref(r) for r in reqs]))
+
+
 class Server:
     def __init__(self, ctx, index, tau: float = 0.9, micro_batch: int = 128, deadline_s: float = 1e-3,
                  slots: int = 4, max_doc_tokens: int = 10000, capacity: int = 1 << 16, hbm_fraction: float = 0.5,
                  tile_n: int = 0, free_bytes: int | None = None, simhash_index=None, hamming_max: int | None = None,
-                 hamming_capacity: int = 1 << 16):
+                 hamming_capacity: int = 1 << 16, result_pairs: int = 1 << 24):
         import torch
         self.ctx, self.index, self.tau = ctx, index, tau
         self.micro_batch, self.deadline_s = micro_batch, deadline_s
@@ -70,6 +105,9 @@ class Server:
             for b in self.slots:
                 b.attach_simhash(simhash_index, hamming_max, hamming_capacity)
         self.busy: list[list[Request] | None] = [None] * len(self.slots)
+        # pinned rings for the results (result_pairs pairs; the Hamming ring a quarter of that)
+        self.ring = _Ring(result_pairs, "pairs")
+        self.hring = _Ring(max(result_pairs // 4, 1), "hamming") if self.hamming else None
         # pinned staging per slot (stream-ordered copies read them until the batch finishes)
         self.h_off = [torch.empty(micro_batch + 1, dtype=torch.int64).pin_memory() for _ in self.slots]
         self.h_tok = [torch.empty(self.max_tokens, dtype=torch.int32).pin_memory() for _ in self.slots]
@@ -85,17 +123,31 @@ class Server:
         self.slots[s].launch(self.h_off[s][:len(reqs) + 1], self.h_tok[s][:int(off[-1])])
         self.busy[s] = reqs
 
+    def _fetch(self, ring, total, copy):
+        """One result kind of a finished batch into its ring: (pairs view, query offsets)."""
+        start = ring.take(total)
+        if start is None:  # larger than the whole arena: a copy of its own
+            pairs, _, qoff = copy(None, True)
+            return pairs, qoff, None
+        pairs, _, qoff = copy(ring.buf[start:start + total], True)
+        return pairs, qoff, start
+
     def _complete(self, s: int, now: float):
         # the pipeline returns the batch's pairs grouped by request, with each request's start
-        pairs, _, qoff = self.slots[s].wait(offsets=True)
-        reqs = self.busy[s]
+        b, reqs = self.slots[s], self.busy[s]
+        tot, htot = b.totals()
+        pairs, qoff, at = self._fetch(self.ring, min(tot, self.capacity), lambda o, f: b.wait(out=o, offsets=f))
         if self.hamming:
-            hp, _, hoff = self.slots[s].hamming(offsets=True)
+            hp, hoff, hat = self._fetch(self.hring, min(htot, b.h_capacity), lambda o, f: b.hamming(out=o, offsets=f))
         for q, r in enumerate(reqs):
             r.done = now
             r.pairs = pairs[qoff[q]:qoff[q + 1]]
             if self.hamming:
                 r.hamming = hp[hoff[q]:hoff[q + 1]]
+        if at is not None:
+            self.ring.keep(at, len(pairs), reqs)
+        if self.hamming and hat is not None:
+            self.hring.keep(hat, len(hp), reqs)
         self.busy[s] = None
 
     def run(self, docs: list[np.ndarray], arrivals: np.ndarray) -> list[Request]:

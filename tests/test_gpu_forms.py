@@ -181,6 +181,17 @@ def test_serving_alone_equals_mix(env):
         assert sorted(zip(a.pairs["j"].tolist(), a.pairs["score"].tolist())) == \
             sorted(zip(b.pairs["j"].tolist(), b.pairs["score"].tolist()))
     assert sum(len(r.pairs) for r in mixed) > 50
+    # results in a small ring of pinned memory: regions are reused and the requests that still
+    # view them get copies first; every request keeps its pairs
+    ring = max(32, sum(len(r.pairs) for r in mixed) // 4)
+    small = serving.Server(ctx, idx, 0.9, micro_batch=32, deadline_s=2e-4, slots=3, max_doc_tokens=5000,
+                           result_pairs=ring)
+    again = small.run(docs, arrivals)
+    assert small.ring.evicted > 0
+    for a, b in zip(mixed, again):
+        assert sorted(zip(a.pairs["j"].tolist(), a.pairs["score"].tolist())) == \
+            sorted(zip(b.pairs["j"].tolist(), b.pairs["score"].tolist()))
+    small.free()
     srv.free()
     alone.free()
     idx.free()
