@@ -298,8 +298,9 @@ mrc_status mrc_ctx_sync(mrc_ctx* ctx);
  *   mrc_batch_create : allocates the pipeline's device buffers (inputs, outputs,
  *     workspace) and its own non-blocking stream, runs the pipeline once and
  *     captures it. max_tokens bounds the tokens of one batch; capacity bounds
- *     the pairs of one batch; tile_n is the compare tile width (0 = default,
- *     128 or 256; see the autotuner). The batch keeps `index` (not owned).
+ *     the pairs of one batch; tile_n is the compare tile width (0 = default:
+ *     128 columns for the one-kernel batch; 128 or 256; see the autotuner). The
+ *     batch keeps `index` (not owned).
  *   mrc_batch_launch : asynchronous. Copies the batch's offsets/tokens (host or
  *     device memory) and its document count into the pipeline (the separate-
  *     kernel form pads the batch to max_docs with empty documents) and launches
@@ -331,6 +332,11 @@ mrc_status mrc_batch_wait(mrc_batch* batch, mrc_pair* pairs, int64_t capacity, i
                           int64_t* query_offsets);
 mrc_status mrc_batch_tune(mrc_batch* batch, int32_t tile_n, int32_t ring, int32_t prefetch);
 int32_t mrc_batch_kernels(const mrc_batch* batch);
+/* Phase durations (ns, global timer of CTA 0) of the persistent kernel's last launch (waits for
+ * it): [0] list documents, [1] signature pass, [2] compare, [3] rescoring and Hamming probe,
+ * [4] offset scans, [5] scatter into query order (phase_ns: int64[6]). MRC_ERR_UNSUPPORTED
+ * for a batch that runs separate kernels. */
+mrc_status mrc_batch_phase_ns(mrc_batch* batch, int64_t* phase_ns);
 const char* mrc_batch_last_error(const mrc_batch* batch);
 void mrc_batch_free(mrc_batch* batch);
 

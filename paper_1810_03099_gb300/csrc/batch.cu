@@ -52,6 +52,7 @@ struct mrc_batch {
   int32_t* d_ctl = nullptr;
   int64_t* d_nlive = nullptr;
   int32_t* d_long = nullptr;               // [max_docs] the batch kernel's long-document list
+  unsigned long long* d_stamps = nullptr;  // [kBatchStamps] phase timestamps of the batch kernel
   bool fused = false;                      // one persistent kernel (else separate kernels)
   int32_t qstride = 1;                     // per-query counter stride (words)
   int32_t ring = 0, prefetch = -1;         // compare tuning (B ring depth, L2 prefetch distance)
@@ -173,6 +174,7 @@ cudaError_t record_fused(mrc_batch* b) {
   a.qfill = b->d_qfill;
   a.qoff = b->d_qoff;
   a.grouped = b->d_grouped;
+  a.stamps = b->d_stamps;
   if (b->shx) {
     a.shx = b->shx;
     a.hmax = b->hmax;
@@ -313,7 +315,7 @@ void release(mrc_batch* b) {
   void* ptrs[] = {b->d_offsets, b->d_tokens,    b->d_unit,  b->d_op,    b->d_qnorm,  b->d_cand,
                   b->d_pairs,   b->d_grouped,   b->d_qoff,  b->d_qcnt,  b->d_qfill,  b->d_block,
                   b->d_long,    b->d_simhash,   b->d_hpairs, b->d_hgrouped, b->d_hqoff, b->d_hqcnt,
-                  b->d_hqfill};
+                  b->d_hqfill,  b->d_stamps};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->h_counts) cudaFreeHost(b->h_counts);
@@ -420,6 +422,8 @@ mrc_status mrc_batch_create(mrc_ctx* ctx, const mrc_index* index, int64_t max_do
   if (e == cudaSuccess) e = cudaMalloc(&b->d_qfill, sizeof(int32_t) * (size_t)max_docs * b->qstride);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_block, kBlockZeroBytes + sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_long, sizeof(int32_t) * (size_t)max_docs);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_stamps, sizeof(unsigned long long) * kBatchStamps);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_stamps, 0, sizeof(unsigned long long) * kBatchStamps, s);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_simhash, sizeof(uint64_t) * (size_t)max_docs);
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_counts, 5 * sizeof(unsigned long long));
   if (e == cudaSuccess) {
@@ -590,6 +594,21 @@ mrc_status mrc_batch_tune(mrc_batch* b, int32_t tile_n, int32_t ring, int32_t pr
 }
 
 int32_t mrc_batch_kernels(const mrc_batch* b) { return b ? b->kernel_nodes : -1; }
+
+mrc_status mrc_batch_phase_ns(mrc_batch* b, int64_t* phase_ns) {
+  if (!b || !phase_ns) return MRC_ERR_INVALID;
+  mrc_ctx* ctx = b->ctx;
+  cudaSetDevice(ctx->device);
+  if (!b->fused) return fail(ctx, MRC_ERR_UNSUPPORTED, "mrc_batch_phase_ns: the batch runs separate kernels");
+  const mrc_status st = finish_launch(b);
+  if (st != MRC_OK) return st;
+  unsigned long long t[kBatchStamps];
+  cudaError_t e = cudaMemcpyAsync(t, b->d_stamps, sizeof(t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the phase timestamps");
+  for (int i = 0; i + 1 < kBatchStamps; ++i) phase_ns[i] = t[i + 1] >= t[i] ? (int64_t)(t[i + 1] - t[i]) : -1;
+  return MRC_OK;
+}
 
 const char* mrc_batch_last_error(const mrc_batch* b) { return b ? b->ctx->last_error.c_str() : "no batch"; }
 

@@ -71,6 +71,7 @@ struct BatchParams {
   mrc_pair* hgrouped;
   int32_t* err;
   uint64_t timeout_ns;
+  unsigned long long* stamps;  // [kBatchStamps] CTA 0's global timer at the start and after each phase
 };
 
 __device__ __forceinline__ uint32_t ld_acquire(const unsigned* p) {
@@ -121,7 +122,12 @@ __device__ __forceinline__ int32_t cta_grab(int32_t* cursor, int32_t* slot) {
   return x;
 }
 
-// Phase 0: documents longer than kShortMax go to the long list; offset errors are recorded
+// A batch of at most one document per CTA hashes every document with a whole CTA (a shorter
+// latency than one warp per document); a larger one uses warps for documents of up to kShortMax
+// tokens.
+__device__ __forceinline__ bool team_all(int64_t n) { return n <= (int64_t)gridDim.x; }
+
+// Phase 0: documents for the CTA-wide path go to the long list; offset errors are recorded
 // (the documents concerned are then empty); per-query counters are cleared.
 __device__ void phase_list(const BatchParams& bp, int64_t n) {
   const IngestParams& ing = bp.ing;
@@ -139,13 +145,13 @@ __device__ void phase_list(const BatchParams& bp, int64_t n) {
     else if (raw > MRC_MAX_DOC_TOKENS) set_err(bp.err, kErrTooLong);
     int64_t s, len;
     doc_span(ing, d, s, len);
-    if (len > kShortMax) bp.long_list[atomicAdd(&bp.ctl[kCtlLongN], 1)] = (int32_t)d;
+    if (len > kShortMax || (team_all(n) && len > 0)) bp.long_list[atomicAdd(&bp.ctl[kCtlLongN], 1)] = (int32_t)d;
   }
 }
 
 // Phase 1: the signature pass of the batch's documents (documents past n are written as empty
 // ones: zero signature and operand, Simhash 0).
-__device__ void phase_signature(const BatchParams& bp, uint8_t* smem, int32_t* slot) {
+__device__ void phase_signature(const BatchParams& bp, int64_t n, uint8_t* smem, int32_t* slot) {
   const IngestParams& ing = bp.ing;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const Transposer tr(lane);
@@ -164,7 +170,7 @@ __device__ void phase_signature(const BatchParams& bp, uint8_t* smem, int32_t* s
     if (d >= bp.max_docs) break;
     int64_t o0, len;
     doc_span(ing, d, o0, len);
-    if (len > kShortMax) continue;  // a CTA took it
+    if (len > kShortMax || (team_all(n) && len > 0)) continue;  // a CTA took it
     warp_doc<kSIG>(ing, d, wbase, kq, lane, tr);
   }
   // the compare operands are read by TMA (the async proxy) after the next barrier
@@ -266,19 +272,29 @@ __device__ void cta_exclusive_scan(const int32_t* cnt, int32_t stride, int64_t m
   const int64_t a = min(m, (int64_t)threadIdx.x * per), b = min(m, a + per);
   int64_t s = 0;
   for (int64_t q = a; q < b; ++q) s += __ldcg(cnt + q * stride);
-  part[threadIdx.x] = s;
+  // inclusive scan of the threads' sums: by shuffles within each warp, then over the warp totals
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+  int64_t incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) part[warp] = incl;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int64_t run = 0;
-    for (int t = 0; t < T; ++t) {
-      const int64_t v = part[t];
-      part[t] = run;
-      run += v;
+  if (warp == 0) {
+    const int64_t v = lane < nw ? part[lane] : 0;
+    int64_t w = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(kFull, w, o);
+      if (lane >= o) w += y;
     }
-    off[m] = run;
+    if (lane < nw) part[lane] = w - v;  // exclusive warp offsets
+    if (lane == nw - 1) off[m] = w;
   }
   __syncthreads();
-  int64_t run = part[threadIdx.x];
+  int64_t run = part[warp] + incl - s;
   for (int64_t q = a; q < b; ++q) {
     off[q] = run;
     run += __ldcg(cnt + q * stride);
@@ -348,12 +364,20 @@ __global__ void __launch_bounds__(kResThreads, 1)
   n = n < 0 ? 0 : (n > bp.max_docs ? bp.max_docs : n);
   unsigned target = 0;
   bool ok = true;
+  int stamp = 0;
+  auto mark = [&]() {
+    if (blockIdx.x == 0 && threadIdx.x == 0) bp.stamps[stamp] = gtime();
+    ++stamp;
+  };
+  mark();
 
   phase_list(bp, n);
   ok = grid_sync(bp, target, &ok_s);
+  mark();
   if (ok) {
-    phase_signature(bp, smem, &slot_s);
+    phase_signature(bp, n, smem, &slot_s);
     ok = grid_sync(bp, target, &ok_s);
+    mark();
   }
   if (ok) {
     // shared memory held tables (generic stores); TMA now writes it, and reads the operands
@@ -364,11 +388,13 @@ __global__ void __launch_bounds__(kResThreads, 1)
     resident_body<FMT, RB, BN>(&tA, &tA, &tB, &tB, bp.g, smem, tmem, t_begin, t_end);
     free_tmem();
     ok = grid_sync(bp, target, &ok_s);
+    mark();
   }
   if (ok) {
     phase_rescore(bp);
     phase_probe(bp, n, &slot_s);
     ok = grid_sync(bp, target, &ok_s);
+    mark();
   }
   if (ok) {
     if (blockIdx.x == 0) {
@@ -376,10 +402,12 @@ __global__ void __launch_bounds__(kResThreads, 1)
       if (bp.hmax >= 0) cta_exclusive_scan(bp.hqcnt, bp.qstride, bp.max_docs, bp.hqoff, part_s);
     }
     ok = grid_sync(bp, target, &ok_s);
+    mark();
   }
   if (ok) {
     scatter_pairs(bp.pairs, bp.n_pairs, bp.capacity, bp.qoff, bp.qfill, bp.qstride, bp.grouped);
     if (bp.hmax >= 0) scatter_pairs(bp.hpairs, bp.n_hpairs, bp.hcapacity, bp.hqoff, bp.hqfill, bp.qstride, bp.hgrouped);
+    mark();
   }
   if (tmem_held) free_tmem();
 }
@@ -501,6 +529,7 @@ cudaError_t run_batch(mrc_ctx* ctx, const BatchKernelArgs& a) {
   }
   bp.err = a.err;
   bp.timeout_ns = ctx->wait_limit_ns;
+  bp.stamps = a.stamps;
   auto kern = k_batch<FMT, RB, BN>;
   if (resident_ctas(kern, kResThreads, smem) < 1) return cudaErrorInvalidConfiguration;
   // every CTA must be resident at once (grid barriers): one per SM, cooperative launch
@@ -531,7 +560,9 @@ cudaError_t launch_batch_kernel(mrc_ctx* ctx, const BatchKernelArgs& a) {
   if (!batch_kernel_supported(x) || a.max_docs < 1 || x->n_docs < 1) return cudaErrorInvalidValue;
   const bool fp8 = x->params.precision == MRC_PREC_BF16_FP8;
   const int64_t kbytes = fp8 ? x->kp8 : 2ll * x->kp;
-  const bool wide = a.tile_n != 128;
+  // 128-column tiles unless asked otherwise: a batch has few row blocks, and with four TMEM
+  // accumulators in flight the index streams faster than with two 256-column ones
+  const bool wide = a.tile_n == 256;
   if (fp8) {
     if (kbytes == 64) return wide ? run_batch<OP_E4M3, 64, 256>(ctx, a) : run_batch<OP_E4M3, 64, 128>(ctx, a);
     return wide ? run_batch<OP_E4M3, 128, 256>(ctx, a) : run_batch<OP_E4M3, 128, 128>(ctx, a);

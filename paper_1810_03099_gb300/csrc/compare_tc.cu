@@ -452,8 +452,11 @@ cudaError_t launch_gemm_compare(mrc_ctx* ctx, const GemmArgs& g) {
   if (g.na >= (1ll << 31) || g.nb >= (1ll << 31)) return cudaErrorInvalidValue;
   if (!g.store && !g.store16 && (g.kbytes == 64 || g.kbytes == 128)) {
     // one K block: resident-A kernel
-    // tile width: 256 columns by default for single-accumulator formats, 128 on request
-    const int wide = (g.fmt != OP_SPLIT16 && g.tile_n != 128) ? 1 : 0;
+    // tile width: by default 256 columns for single-accumulator formats, except for a query x
+    // index compare of at most two row blocks (four TMEM accumulators in flight stream the index
+    // faster); 128 or 256 on request
+    const bool few_rows = !g.triangle && g.na <= 2 * kBM;
+    const int wide = (g.fmt != OP_SPLIT16 && (g.tile_n == 256 || (g.tile_n == 0 && !few_rows))) ? 1 : 0;
     switch ((g.fmt * 2 + (g.kbytes == 128 ? 1 : 0)) * 2 + wide) {
       case (OP_SPLIT16 * 2) * 2: return run_gemm_resident<OP_SPLIT16, 64, 128>(ctx, g);
       case (OP_SPLIT16 * 2 + 1) * 2: return run_gemm_resident<OP_SPLIT16, 128, 128>(ctx, g);

@@ -36,7 +36,23 @@ __device__ __forceinline__ T warp_sum(T v) {
 template <bool X_L2 = false>
 __device__ __forceinline__ float unit_dot(const float* __restrict__ x, const float* __restrict__ y, int k) {
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  if ((k & 3) == 0) {
+  if (k == 64) {  // the usual signature length: all 16 row loads of each side in flight at once
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    const float4* y4 = reinterpret_cast<const float4*>(y);
+    float4 a[16], b[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      a[q] = X_L2 ? __ldcg(x4 + q) : __ldg(x4 + q);
+      b[q] = __ldg(y4 + q);
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      s0 = fmaf(a[q].x, b[q].x, s0);
+      s1 = fmaf(a[q].y, b[q].y, s1);
+      s2 = fmaf(a[q].z, b[q].z, s2);
+      s3 = fmaf(a[q].w, b[q].w, s3);
+    }
+  } else if ((k & 3) == 0) {
     const float4* x4 = reinterpret_cast<const float4*>(x);
     const float4* y4 = reinterpret_cast<const float4*>(y);
 #pragma unroll 4

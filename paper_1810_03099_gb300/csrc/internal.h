@@ -282,8 +282,10 @@ struct BatchKernelArgs {
   int32_t* hqfill;
   int64_t* hqoff;
   mrc_pair* hgrouped;
+  unsigned long long* stamps;  // [kBatchStamps] phase timestamps of the last launch (global timer, ns)
 };
 constexpr int kBatchCtlWords = 8;
+constexpr int kBatchStamps = 7;  // start, then the end of phases 0..5
 // True if the persistent batch kernel handles this index (compare rows of 64 or 128 bytes).
 bool batch_kernel_supported(const mrc_index* index);
 cudaError_t launch_batch_kernel(mrc_ctx* ctx, const BatchKernelArgs& a);

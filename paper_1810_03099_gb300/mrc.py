@@ -107,6 +107,7 @@ _SIGNATURES = {
     "mrc_batch_free": (None, [C.c_void_p]),
     "mrc_batch_tune": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
     "mrc_batch_kernels": (C.c_int32, [C.c_void_p]),
+    "mrc_batch_phase_ns": (C.c_int32, [C.c_void_p, C.c_void_p]),
 }
 
 _LIB = None
@@ -315,6 +316,12 @@ class Batch:
         (mrc_batch_tune; re-captures the graph)."""
         self._check(self.ctx.lib.mrc_batch_tune(self.handle, int(tile_n), int(ring), int(prefetch)))
         self.tile_n = int(tile_n)
+
+    def phase_ns(self) -> dict:
+        """Phase durations (ns) of the persistent kernel's last launch (mrc_batch_phase_ns)."""
+        out = np.zeros(6, np.int64)
+        self._check(self.ctx.lib.mrc_batch_phase_ns(self.handle, out.ctypes.data))
+        return dict(zip(("list", "signature", "compare", "rescore_probe", "scan", "scatter"), out.tolist()))
 
     @property
     def kernel_nodes(self) -> int:

@@ -53,9 +53,9 @@ def slot_footprint(index, max_docs: int, max_tokens: int, capacity: int) -> int:
 
 
 class _Ring:
-    """Pinned host arena for batch results, handed out in order and wrapping around. Live
-    regions are kept oldest first; a region about to be overwritten first gives the requests
-    still viewing it (held elsewhere) their own copies."""
+    """Pinned host arena for batch results, handed out in order and wrapping around. A region
+    about to be overwritten first gives the requests still viewing it (held elsewhere) their
+    own copies."""
 
     def __init__(self, n_pairs: int, attr: str):
         self.buf = mrc._pinned_pairs(n_pairs)
@@ -69,12 +69,17 @@ class _Ring:
             return None
         start = self.head if self.head + m <= self.n else 0
         end = start + m
-        while self.live and self.live[0][0] < end and start < self.live[0][1]:
-            for w in self.live.popleft()[2]:
-                r = w()
-                if r is not None:  # still held by the caller
-                    setattr(r, self.attr, getattr(r, self.attr).copy())
-                    self.evicted += 1
+        keep = collections.deque()
+        for a, b, refs in self.live:  # every region the new one overlaps (the tail left at a wrap too)
+            if a < end and start < b:
+                for w in refs:
+                    r = w()
+                    if r is not None:  # still held by the caller
+                        setattr(r, self.attr, getattr(r, self.attr).copy())
+                        self.evicted += 1
+            else:
+                keep.append((a, b, refs))
+        self.live = keep
         self.head = end
         return start
 

@@ -129,6 +129,8 @@ def test_persistent_batch_every_document_path_hamming_and_errors(env, precision)
                 assert np.all(pairs["i"][off[q]:off[q + 1]] == q)
 
     check(offs, toks, want_s, want_h)
+    ph = b.phase_ns()  # the persistent kernel's phases, timed on the device
+    assert len(ph) == 6 and all(v >= 0 for v in ph.values()) and ph["compare"] > 0
     bad = offs.copy()
     bad[4] = bad[2] - 1  # document 3 ends before it starts
     b.launch(bad, toks)
