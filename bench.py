@@ -49,20 +49,26 @@ CPU_BASELINE_SAMPLE = 4000  # documents of the main line's oracle timing
 
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
-# the news20 step, valid only while the kernel's source file is unchanged since the capture.
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one single-pass ncu
+# capture of the launch at the bench's size (1,000,000 documents; `--form profile --case
+# compare-e4m3 / compare-fp16 --docs 1000000`), valid only while the compare's device code is
+# unchanged since the capture.
+_TC = "paper_1810_03099_gb300/csrc/tc_dev.cuh"
+_TC_DIGEST = "b1b3073cc4fa17c12cd39068c95250d2fea1f46e65d9d76f9cd781c81efda0e3"
 NCU_TRAFFIC = {
-    "gemm_f16_bound": ("paper_1810_03099_gb300/csrc/compare_tc.cu",
-                       "ec6e6280a592556d6992a1efb45990cbf3a846dbb540dae47bdf989727c5936b", 15766784),
-    "gemm_f16_thresh": ("paper_1810_03099_gb300/csrc/compare_tc.cu",
-                        "ec6e6280a592556d6992a1efb45990cbf3a846dbb540dae47bdf989727c5936b", 2470400),
+    "gemm_e4m3_thresh": (_TC, _TC_DIGEST, 114_680_000 + 141_090_000),
+    "gemm_f16_thresh": (_TC, _TC_DIGEST, 47_140_000_000 + 139_190_000),
 }
 KERNEL_NOTES = {
     "gemm_f16_bound": "exact-cosine head GEMM carrying the tail-bucket bound: 2 kd flops per pair of the "
                       "triangle (kd = 128 head + 256 bucket columns); ncu: tensor pipe 75% active; candidates "
                       "where head + bound >= tau - delta'",
-    "gemm_f16_thresh": "signature compare at k = 64: one K block per tile, epilogue-bound (ncu: tensor pipe 29% "
-                       "active)",
+    "gemm_e4m3_thresh": "signature compare at k = 64, E4M3: epilogue-bound (ncu at 100,000 documents: tensor pipe "
+                        "20% active, L2 hit rate 99%); traffic = operand reads (the 64 MB operand stays in L2) "
+                        "plus the candidate list written",
+    "gemm_f16_thresh": "signature compare at k = 64, fp16: epilogue-bound (ncu at 100,000 documents: tensor pipe "
+                       "42% active); at 1 M documents the 128 MB operand does not stay in L2 and is re-read "
+                       "from DRAM (~47 GB per launch, 0.74 TB/s), which the epilogue-bound rate hides",
     "cosine_verify": "exact scores of the bound-pruned candidates (a few tens of thousands on news20)",
     "cosine_tail": "algorithmic bytes = the fp16 head scores of the upper triangle; the postings it also walks "
                    "are L2-resident. ncu: issue-active 66%, l1tex 53%: instruction/latency-bound, not HBM-bound",
@@ -967,12 +973,64 @@ def serving_leg(n_index, rates=(10000, 50000, 100000, 250000, 500000), requests=
         rep["pairs_per_request"] = float(np.mean([len(r.pairs) for r in reqs]))
         rep["hamming_pairs_per_request"] = float(np.mean([len(r.hamming) for r in reqs]))
         rows.append(rep)
+    # the last launch of one slot, phase by phase (the slot's one persistent kernel)
+    phases = {k: round(v / 1e3, 1) for k, v in srv.slots[0].phase_ns().items()}
+    nodes = srv.slots[0].kernel_nodes
     srv.free()
     shx.free()
     idx.free()
     ctx.close()
     return {"index_docs": n_index, "index_tokens": n_tok, "hamming_max": HMAX, "micro_batch": 128, "deadline_ms": 1.0,
+            "batch_kernel_nodes": nodes, "batch_phases_us": phases,
             "slots": srv.admitted_slots, "requests_per_rate": requests, "rates": rows}
+
+
+def form_profile(args):
+    """Small cases of single kernels for ncu captures (the profiling commands in profiles/):
+    compare-e4m3 / compare-fp16: all-pairs signature compare of the first --docs documents of the
+    headline recipe (k = 64, tau = 0.9), warm-up launches first; batch: one 128-document query
+    batch against an index of --docs serving-recipe documents (one persistent kernel per launch,
+    Hamming leg attached), four launches; signature: the signature pass over --docs documents."""
+    import torch
+    from paper_1810_03099_gb300 import mrc, synth
+    n = args.docs
+    ctx = mrc.Context()
+    out = {"case": args.case, "docs": n}
+    if args.case in ("compare-e4m3", "compare-fp16", "signature"):
+        c = synth.make_corpus_device("precision", n_docs=n)
+        prec = mrc.PREC_BF16_FP8 if args.case == "compare-e4m3" else mrc.PREC_FP32
+        idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, mrc.params_default(k=K, precision=prec))
+        if args.case == "signature":
+            sig = torch.empty((n, K), dtype=torch.float32, device="cuda")
+            sh = torch.empty(n, dtype=torch.int64, device="cuda")
+            for _ in range(3):
+                mrc.mrc_signature(ctx, idx, c.offsets, c.tokens, sig, sh)
+        else:
+            for _ in range(3):
+                _, out["pairs"] = mrc.mrc_match(ctx, idx, None, TAU, capacity=1 << 24)
+        idx.free()
+    elif args.case == "batch":
+        c = synth.make_corpus_device("serving", n_docs=n)
+        idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, mrc.params_default(k=K, precision=mrc.PREC_FP16))
+        del c
+        torch.cuda.empty_cache()
+        fps = mrc.index_simhash(ctx, idx, torch.empty(n, dtype=torch.int64, device="cuda"))
+        shx = mrc.simhash_index_build(ctx, fps, HMAX)
+        pool = synth.make_corpus_device(synth.SPECS["precision"].with_(n_docs=128, seed=BASE_QUERY_SEED))
+        pool = pool.host_subset(np.arange(128))
+        b = mrc.Batch(ctx, idx, 128, 128 * 10000, TAU, 1 << 21)
+        b.attach_simhash(shx, HMAX, 1 << 18)
+        for _ in range(4):
+            b.launch(pool.offsets, pool.tokens)
+            _, out["pairs"] = b.wait()
+        out["phases_ns"] = b.phase_ns()
+        out["kernel_nodes"] = b.kernel_nodes
+        b.free()
+        shx.free()
+        idx.free()
+    torch.cuda.synchronize()
+    ctx.close()
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -983,12 +1041,17 @@ def main():
     ap.add_argument("--impl", default="mrc", choices=["mrc", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="leave the serving leg out of the headline line")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="the million-document step alone (no accuracy, news20, serving or CPU legs; for launch lists)")
     ap.add_argument("--form", default="headline",
                     choices=["headline", "precision", "batching", "serving", "features", "text", "study",
-                             "simhash_index", "forms"],
+                             "simhash_index", "forms", "profile"],
                     help="headline (default): the million-document step and its legs; the others measure one form")
     ap.add_argument("--batches", type=int, default=4096)
     ap.add_argument("--serving-docs", type=int, default=10_000_000)
+    ap.add_argument("--case", default="compare-e4m3", choices=["compare-e4m3", "compare-fp16", "batch", "signature"],
+                    help="--form profile: the kernel case to run")
+    ap.add_argument("--docs", type=int, default=100_000, help="--form profile: documents of the case")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -1002,11 +1065,14 @@ def main():
         for f in (["precision", "batching", "serving"] if args.form == "forms" else [args.form]):
             {"precision": form_precision, "batching": form_batching, "serving": form_serving,
              "features": form_features, "text": form_text, "study": form_study,
-             "simhash_index": form_simhash_index}[f](args)
+             "simhash_index": form_simhash_index, "profile": form_profile}[f](args)
         return
 
     line, (c, ctx, stream, dist) = run_headline(args, rank, world, local)
-    if rank == 0:
+    if rank == 0 and args.headline_only:
+        ctx.close()
+        print(json.dumps(line), flush=True)
+    elif rank == 0:
         # legs outside the timed regions: accuracy against FP64, the NEWS20-shaped step with the
         # exact cosine, the serving form, the oracle's own speed
         line["accuracy_vs_fp64"] = accuracy_vs_fp64(c, ctx)

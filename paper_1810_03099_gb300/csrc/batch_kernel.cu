@@ -213,65 +213,16 @@ __device__ __forceinline__ uint32_t block_key(uint64_t f, int shift, int width) 
   return (uint32_t)((f >> shift) & ((1ull << width) - 1ull));
 }
 
-// Phase 3b: Hamming probe of the block-table index. Item x = (query x / blocks, table
-// x % blocks) is taken by a whole CTA; its warps take the bucket's entries 32 at a time. A
-// pair is emitted by the first table whose block agrees (so once), as in the probe kernel.
-__device__ void phase_probe(const BatchParams& bp, int64_t n, int32_t* slot) {
-  if (bp.hmax < 0 || bp.hn <= 0) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const SimhashLayout& L = bp.L;
-  const int64_t items = n * L.blocks;
-  while (true) {
-    const int32_t x = cta_grab(bp.ctl + kCtlProbeCur, slot);
-    if (x >= items) break;
-    const int64_t qi = x / L.blocks;
-    const int t = (int)(x - qi * L.blocks);
-    const uint64_t fq = __ldcg(reinterpret_cast<const unsigned long long*>(bp.qfp) + qi);
-    const int32_t* o = bp.hoff + L.off_base[t];
-    const uint32_t key = block_key(fq, L.shift[t], L.width[t]);
-    const int32_t s = __ldg(o + key), e = __ldg(o + key + 1);
-    const uint64_t* tf = bp.hfp + (int64_t)t * bp.hn;
-    const int32_t* ti = bp.hid + (int64_t)t * bp.hn;
-    for (int32_t x0 = s + warp * 32; x0 < e; x0 += nwarps * 32) {
-      const int32_t xx = x0 + lane;
-      bool ok = false;
-      int32_t j = 0, dist = 0;
-      if (xx < e) {
-        const uint64_t m = __ldg(reinterpret_cast<const unsigned long long*>(tf) + xx) ^ fq;
-        dist = __popcll(m);
-        ok = dist <= bp.hmax;
-        if (ok) {
-          j = __ldg(ti + xx);
-          for (int u = 0; u < t && ok; ++u) ok = block_key(m, L.shift[u], L.width[u]) != 0u;
-        }
-      }
-      const unsigned hit = __ballot_sync(kFull, ok);
-      if (hit == 0u) continue;
-      unsigned long long base = 0ull;
-      if (lane == 0) base = atomicAdd(bp.n_hpairs, (unsigned long long)__popc(hit));
-      base = __shfl_sync(kFull, base, 0);
-      const unsigned long long at = base + __popc(hit & ((1u << lane) - 1u));
-      const bool stored = ok && at < (unsigned long long)bp.hcapacity;
-      if (stored) {
-        mrc_pair pr;
-        pr.i = (int32_t)qi;
-        pr.j = j;
-        pr.score = (float)dist;
-        bp.hpairs[at] = pr;
-      }
-      const unsigned st = __ballot_sync(kFull, stored);
-      if (st && lane == 0) atomicAdd(bp.hqcnt + qi * bp.qstride, __popc(st));
-    }
-  }
-}
-
-// Phase 4: off[q] = sum of cnt[q'] for q' < q (q < m), off[m] = the total; one CTA.
+// Exclusive scan by one CTA (phase 4, and the probe's chunk list): off[q] = sum of cnt[q' * stride]
+// for q' < q (q < m), off[m] = the total. cnt is global memory written in this launch (read
+// through L2) or, with GLOBAL_IN false, shared memory.
+template <bool GLOBAL_IN = true>
 __device__ void cta_exclusive_scan(const int32_t* cnt, int32_t stride, int64_t m, int64_t* off, int64_t* part) {
   const int T = blockDim.x;
   const int64_t per = (m + T - 1) / T;
   const int64_t a = min(m, (int64_t)threadIdx.x * per), b = min(m, a + per);
   int64_t s = 0;
-  for (int64_t q = a; q < b; ++q) s += __ldcg(cnt + q * stride);
+  for (int64_t q = a; q < b; ++q) s += GLOBAL_IN ? __ldcg(cnt + q * stride) : cnt[q * stride];
   // inclusive scan of the threads' sums: by shuffles within each warp, then over the warp totals
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
   int64_t incl = s;
@@ -297,9 +248,119 @@ __device__ void cta_exclusive_scan(const int32_t* cnt, int32_t stride, int64_t m
   int64_t run = part[warp] + incl - s;
   for (int64_t q = a; q < b; ++q) {
     off[q] = run;
-    run += __ldcg(cnt + q * stride);
+    run += GLOBAL_IN ? __ldcg(cnt + q * stride) : cnt[q * stride];
   }
   __syncthreads();
+}
+
+// Entries [a, b) of bucket (query qi, table t) against the query's fingerprint fq, 32 per warp
+// step, the CTA's warps interleaved. A pair is emitted by the first table whose block agrees (so
+// once), as in the probe kernel; stored pairs are counted per query.
+__device__ void probe_range(const BatchParams& bp, int64_t qi, int t, uint64_t fq, int32_t a, int32_t b) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const SimhashLayout& L = bp.L;
+  const uint64_t* tf = bp.hfp + (int64_t)t * bp.hn;
+  const int32_t* ti = bp.hid + (int64_t)t * bp.hn;
+  for (int32_t x0 = a + warp * 32; x0 < b; x0 += nwarps * 32) {
+    const int32_t xx = x0 + lane;
+    bool ok = false;
+    int32_t j = 0, dist = 0;
+    if (xx < b) {
+      const uint64_t m = __ldg(reinterpret_cast<const unsigned long long*>(tf) + xx) ^ fq;
+      dist = __popcll(m);
+      ok = dist <= bp.hmax;
+      if (ok) {
+        j = __ldg(ti + xx);
+        for (int u = 0; u < t && ok; ++u) ok = block_key(m, L.shift[u], L.width[u]) != 0u;
+      }
+    }
+    const unsigned hit = __ballot_sync(kFull, ok);
+    if (hit == 0u) continue;
+    unsigned long long base = 0ull;
+    if (lane == 0) base = atomicAdd(bp.n_hpairs, (unsigned long long)__popc(hit));
+    base = __shfl_sync(kFull, base, 0);
+    const unsigned long long at = base + __popc(hit & ((1u << lane) - 1u));
+    const bool stored = ok && at < (unsigned long long)bp.hcapacity;
+    if (stored) {
+      mrc_pair pr;
+      pr.i = (int32_t)qi;
+      pr.j = j;
+      pr.score = (float)dist;
+      bp.hpairs[at] = pr;
+    }
+    const unsigned st = __ballot_sync(kFull, stored);
+    if (st && lane == 0) atomicAdd(bp.hqcnt + qi * bp.qstride, __popc(st));
+  }
+}
+
+// The bucket of item x = (query x / blocks, table x % blocks): its query's fingerprint and
+// entry range.
+__device__ __forceinline__ void probe_item(const BatchParams& bp, int64_t x, int64_t& qi, int& t, uint64_t& fq,
+                                           int32_t& a, int32_t& b) {
+  const SimhashLayout& L = bp.L;
+  qi = x / L.blocks;
+  t = (int)(x - qi * L.blocks);
+  fq = __ldcg(reinterpret_cast<const unsigned long long*>(bp.qfp) + qi);
+  const int32_t* o = bp.hoff + L.off_base[t];
+  const uint32_t key = block_key(fq, L.shift[t], L.width[t]);
+  a = __ldg(o + key);
+  b = __ldg(o + key + 1);
+}
+
+constexpr int kProbeChunk = 2048;     // bucket entries per work unit of the chunked probe
+constexpr int kProbeItemsMax = 4096;  // (query, table) items the chunked probe lists in shared memory
+
+// Phase 3b: Hamming probe of the block-table index. Buckets differ in size by orders of
+// magnitude (fingerprints of documents dominated by the same frequent terms share blocks), so
+// work units are chunks of kProbeChunk entries of a bucket: every CTA lists the chunk counts of
+// all items in shared memory (the same list in each CTA), and CTAs take chunks from one cursor.
+// A batch with more items than kProbeItemsMax takes whole items instead.
+__device__ void phase_probe(const BatchParams& bp, int64_t n, uint8_t* smem, int32_t* slot, int64_t* part) {
+  if (bp.hmax < 0 || bp.hn <= 0) return;
+  const int64_t items = n * bp.L.blocks;
+  int64_t qi;
+  int t;
+  uint64_t fq;
+  int32_t a, b;
+  if (items > kProbeItemsMax) {
+    while (true) {
+      const int32_t x = cta_grab(bp.ctl + kCtlProbeCur, slot);
+      if (x >= items) break;
+      probe_item(bp, x, qi, t, fq, a, b);
+      probe_range(bp, qi, t, fq, a, b);
+    }
+    return;
+  }
+  int32_t* cnt = reinterpret_cast<int32_t*>(smem);                        // [items] chunks per item
+  int64_t* first = reinterpret_cast<int64_t*>(smem + 4 * kProbeItemsMax);  // [items + 1] first chunk
+  for (int64_t x = threadIdx.x; x < items; x += blockDim.x) {
+    probe_item(bp, x, qi, t, fq, a, b);
+    cnt[x] = (b - a + kProbeChunk - 1) / kProbeChunk;
+  }
+  __syncthreads();
+  cta_exclusive_scan<false>(cnt, 1, items, first, part);
+  const int64_t chunks = first[items];
+  __shared__ int64_t unit_s[2];
+  while (true) {
+    const int32_t c = cta_grab(bp.ctl + kCtlProbeCur, slot);
+    if (c >= chunks) break;
+    if (threadIdx.x == 0) {  // the item holding chunk c: the last x with first[x] <= c
+      int64_t lo = 0, hi = items - 1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= c) lo = mid;
+        else hi = mid - 1;
+      }
+      unit_s[0] = lo;
+      unit_s[1] = c - first[lo];
+    }
+    __syncthreads();
+    const int64_t x = unit_s[0], k = unit_s[1];
+    __syncthreads();
+    probe_item(bp, x, qi, t, fq, a, b);
+    const int32_t ca = a + (int32_t)k * kProbeChunk;
+    probe_range(bp, qi, t, fq, ca, min(b, ca + kProbeChunk));
+  }
 }
 
 // Phase 5: the first min(total, cap) pairs go to their query's slice of out, in the order the
@@ -392,7 +453,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
   }
   if (ok) {
     phase_rescore(bp);
-    phase_probe(bp, n, &slot_s);
+    phase_probe(bp, n, smem, &slot_s, part_s);
     ok = grid_sync(bp, target, &ok_s);
     mark();
   }
