@@ -72,7 +72,32 @@ struct Transposer {
   }
 };
 
-__device__ __forceinline__ unsigned long long to_fix(float x) { return __float2ull_rn(x * kFix); }
+// Conversions between FP32 and 64-bit integers with integer operations only: the hardware
+// conversions of 64-bit integers run on the FP64 units, which are few on this part. Both round to
+// nearest, ties to even, exactly as the 64-bit conversion instructions do.
+// x >= 0 finite -> the nearest integer.
+__device__ __forceinline__ unsigned long long f32_to_u64_rn(float x) {
+  if (x < 4294967296.0f) return (unsigned long long)__float2uint_rn(x);
+  const uint32_t b = __float_as_uint(x);  // >= 2^32: an integer, mantissa << (exponent - 23)
+  const int e = (int)((b >> 23) & 0xFFu) - 127;
+  return (unsigned long long)((b & 0x7FFFFFu) | 0x800000u) << (e - 23);
+}
+// v -> the nearest float.
+__device__ __forceinline__ float u64_to_f32_rn(unsigned long long v) {
+  if ((v >> 32) == 0ull) return __uint2float_rn((uint32_t)v);
+  const int sh = 40 - __clzll((long long)v);  // bits below the 24 kept (v >= 2^32: sh >= 8)
+  unsigned long long m = v >> sh;
+  const unsigned long long rem = v & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  if (rem > half || (rem == half && (m & 1ull))) ++m;
+  int ex = sh + 23;
+  if (m == (1ull << 24)) {
+    m >>= 1;
+    ++ex;
+  }
+  return __uint_as_float(((uint32_t)(ex + 127) << 23) | ((uint32_t)m & 0x7FFFFFu));
+}
+
+__device__ __forceinline__ unsigned long long to_fix(float x) { return f32_to_u64_rn(x * kFix); }
 
 // 1 / |w| from the fixed-point squared norm (0 for an empty document).
 // u^2 in 2^-31 fixed point, rounded up: FP32 with directed rounding (the power-of-two scaling
@@ -80,7 +105,7 @@ __device__ __forceinline__ unsigned long long to_fix(float x) { return __float2u
 // bucket's sum stays below 2^31 + 65,536 < 2^32.
 __device__ __forceinline__ uint32_t to_fix31_up(float u) { return __float2uint_ru(__fmul_ru(u, u) * 2147483648.0f); }
 __device__ __forceinline__ float inv_norm_of(unsigned long long norm_q) {
-  const float n2 = (float)norm_q * kInvFix;
+  const float n2 = u64_to_f32_rn(norm_q) * kInvFix;
   return n2 > 0.f ? 1.0f / sqrtf(n2) : 0.f;
 }
 
@@ -332,17 +357,17 @@ __device__ __forceinline__ void write_bucket_norms(const IngestParams& p, int64_
 __device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsigned long long norm_q,
                              unsigned long long norm16_q, const unsigned long long* num_q, uint32_t plo, uint32_t phi,
                              int lane) {
-  const float nrm = sqrtf((float)norm_q * kInvFix);
-  const float nrm16 = p.bf16w ? sqrtf((float)norm16_q * kInvFix) : 0.f;
+  const float nrm = sqrtf(u64_to_f32_rn(norm_q) * kInvFix);
+  const float nrm16 = p.bf16w ? sqrtf(u64_to_f32_rn(norm16_q) * kInvFix) : 0.f;
   // raw signature s_p = t_p / |d|, t_p = num_p / |R_p|; the unit signature is s / |s|,
   // computed exactly as the packing of stored raw signatures computes it
   float ss = 0.f, ss16 = 0.f;
   for (int q = lane; q < p.k; q += 32) {
-    const float t = (float)num_q[q] * kInvFix * p.rinv[q];
+    const float t = u64_to_f32_rn(num_q[q]) * kInvFix * p.rinv[q];
     const float sv = nrm > 0.f ? t / nrm : 0.f;
     ss += sv * sv;
     if (p.bf16w) {
-      const float t16 = (float)num_q[p.k + q] * kInvFix * p.rinv16[q];
+      const float t16 = u64_to_f32_rn(num_q[p.k + q]) * kInvFix * p.rinv16[q];
       const float sv16 = nrm16 > 0.f ? t16 / nrm16 : 0.f;
       ss16 += sv16 * sv16;
     }
@@ -354,7 +379,7 @@ __device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsi
   const int width = max(p.k, max(p.sig.kp, p.sig.kp8));
   float q2 = 0.f;  // squared norm of the E4M3-quantized unit signature
   for (int q = lane; q < width; q += 32) {
-    const float t = q < p.k ? (float)num_q[q] * kInvFix * p.rinv[q] : 0.f;
+    const float t = q < p.k ? u64_to_f32_rn(num_q[q]) * kInvFix * p.rinv[q] : 0.f;
     const float sv = nrm > 0.f ? t / nrm : 0.f;
     const float u = (q < p.k && sn > 0.f) ? sv / sn : 0.f;
     if (q < p.k) {
@@ -371,7 +396,7 @@ __device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsi
     if (q < p.sig.kp8 && p.sig.op_e4m3) {
       float u8 = u;
       if (p.bf16w) {
-        const float t16 = q < p.k ? (float)num_q[p.k + q] * kInvFix * p.rinv16[q] : 0.f;
+        const float t16 = q < p.k ? u64_to_f32_rn(num_q[p.k + q]) * kInvFix * p.rinv16[q] : 0.f;
         const float sv16 = nrm16 > 0.f ? t16 / nrm16 : 0.f;
         u8 = (q < p.k && sn16 > 0.f) ? sv16 / sn16 : 0.f;
       }
