@@ -523,9 +523,10 @@ def form_simhash_index(args):
     ctx.close()
 
 
-def form_batching(args):
-    """Batching form: 4,096 batches of 1-512 documents (log-uniform 20-20,000 tokens) against the
-    one-million-document precision index, one graph launch per batch, autotuned tile width."""
+def batching_leg(n_batches):
+    """Batching form: n_batches batches of 1-512 documents (log-uniform 20-20,000 tokens) against
+    the one-million-document precision index; each batch is one launch of the persistent batch
+    kernel, the pipeline of each size bucket autotuned (tile width, ring depth, L2 prefetch)."""
     import torch
     from paper_1810_03099_gb300 import batching, mrc, synth
     c = synth.make_corpus_device("precision")
@@ -533,10 +534,11 @@ def form_batching(args):
     idx = mrc.mrc_build_index(ctx, c.offsets, c.tokens, c.vocab, mrc.params_default(k=64, precision=1))
     del c
     torch.cuda.empty_cache()
-    sizes = synth.query_batch_sizes(args.batches)
+    sizes = synth.query_batch_sizes(n_batches)
     q = synth.make_corpus_device(synth.SPECS["batch_queries"].with_(n_docs=int(sizes.sum())))
     starts = np.concatenate([[0], np.cumsum(sizes)])
     runner = batching.BatchRunner(ctx, idx, TAU, max_docs=512, max_doc_tokens=20000, capacity=1 << 18)
+
     def batch(b):
         s0, s1 = int(starts[b]), int(starts[b + 1])
         o = q.offsets[s0:s1 + 1] - q.offsets[s0]
@@ -558,15 +560,24 @@ def form_batching(args):
         total_pairs += tot
     wall = time.perf_counter() - t0
     docs = int(sizes.sum())
-    line = {"metric": "docs/s", "form": "batching", "value": docs / wall, "unit": "docs/s",
-            "config": {"workload": f"{len(sizes)} batches of 1-512 docs ({docs} docs, {q.n_tokens} tokens), "
-                                   f"log-uniform 20-20,000 tokens, vs 1M-doc bf16/FP8 index, k=64, tau={TAU}"},
-            "batch_latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3)},
-            "pairs": total_pairs, "tuning": {str(k): v for k, v in runner.tuning.items()}}
-    print(json.dumps(line), flush=True)
+    kernels = sorted({p.kernel_nodes for p in runner.pipes.values()})
+    out = {"docs_per_s": docs / wall, "batches": len(sizes), "docs": docs, "tokens": int(q.n_tokens),
+           "batch_latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3)},
+           "kernel_nodes_per_batch": kernels, "pairs": total_pairs,
+           "tuning": {str(k): v for k, v in runner.tuning.items()},
+           "config": f"{len(sizes)} batches of 1-512 docs, log-uniform 20-20,000 tokens, vs the 1M-doc bf16/FP8 "
+                     f"index, k=64, tau={TAU}; host-timed per batch (launch to pairs on the host)"}
     runner.free()
     idx.free()
     ctx.close()
+    return out
+
+
+def form_batching(args):
+    """Batching form on its own (bench.py --form batching --batches N)."""
+    leg = batching_leg(args.batches)
+    line = {"metric": "docs/s", "form": "batching", "value": leg["docs_per_s"], "unit": "docs/s", **leg}
+    print(json.dumps(line), flush=True)
 
 
 def form_serving(args):
@@ -1092,6 +1103,7 @@ def main():
         torch.cuda.empty_cache()
         line["news20"] = news20_leg(max(50, 5 * args.steps))
         if world == 1 and not args.no_serving:
+            line["batching"] = batching_leg(1024)
             line["serving"] = serving_leg(args.serving_docs)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_leg()
