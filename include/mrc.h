@@ -89,6 +89,11 @@ typedef struct {
   float score; /* signature or exact cosine; Hamming distance for Simhash */
 } mrc_pair;
 
+/* A document batch (token CSR). offsets and tokens may be device or host memory. Host
+ * offsets are copied in; page-locked host tokens (cudaHostAlloc / cudaHostRegister) are read in
+ * place by the kernels over the CPU-GPU link, other host tokens are copied in. Either way the
+ * caller keeps them unchanged until the call's stream has passed the call's kernels (a call
+ * with host outputs has, on return). */
 typedef struct {
   int64_t n_docs;
   const int64_t* offsets; /* [n_docs + 1] */

@@ -177,9 +177,25 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Device copy of a caller buffer (the buffer itself when it already lives on the device).
-const void* stage_in(mrc_ctx* ctx, const char* slot, const void* p, size_t bytes, mrc_status* st) {
+// The device address of page-locked host memory (read by kernels over the CPU-GPU link), or
+// NULL for any other pointer.
+const void* pinned_device_ptr(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Device copy of a caller buffer (the buffer itself when it already lives on the device; with
+// zero_copy, page-locked host memory is read in place by the kernels instead of being copied).
+const void* stage_in(mrc_ctx* ctx, const char* slot, const void* p, size_t bytes, mrc_status* st,
+                     bool zero_copy = false) {
   if (!p || is_device_ptr(p)) return p;
+  if (zero_copy)
+    if (const void* dp = pinned_device_ptr(p)) return dp;
   void* d = ws_get(ctx, slot, bytes, st);
   if (!d) return nullptr;
   if (bytes && cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
@@ -269,7 +285,8 @@ mrc_status stage_docs(mrc_ctx* ctx, const mrc_docs* docs, const char* tag, DocsD
   out->n_docs = n;
   out->offsets = (const int64_t*)stage_in(ctx, s1.c_str(), docs->offsets, sizeof(int64_t) * (size_t)(n + 1), &st);
   if (st != MRC_OK) return st;
-  out->tokens = (const int32_t*)stage_in(ctx, s2.c_str(), docs->tokens, sizeof(int32_t) * (size_t)T, &st);
+  // tokens are read once per pass: page-locked host tokens are read in place (no staging copy)
+  out->tokens = (const int32_t*)stage_in(ctx, s2.c_str(), docs->tokens, sizeof(int32_t) * (size_t)T, &st, true);
   if (st != MRC_OK) return st;
   if (T == 0) {
     out->tokens = (const int32_t*)ws_get(ctx, "empty.tokens", 16, &st);

@@ -128,6 +128,16 @@ def test_signature_of_new_documents(torch, M, ctx, orc, corpus):
     # host buffers give the same bits
     sig_h, sh_h = M.mrc_signature(ctx, idx, qo, qt)
     assert np.array_equal(sig_h, sig.cpu().numpy()) and np.array_equal(sh_h, sh.cpu().numpy().view(np.uint64))
+    # page-locked host tokens are read in place by the kernels: the same bits again, and an
+    # index built from page-locked buffers equals one built from device buffers
+    po, pt = torch.from_numpy(qo).pin_memory(), torch.from_numpy(qt).pin_memory()
+    sig_p, sh_p = M.mrc_signature(ctx, idx, po, pt)  # host outputs (numpy), ready on return
+    assert np.array_equal(sig_p, sig.cpu().numpy()) and np.array_equal(sh_p, sh.cpu().numpy().view(np.uint64))
+    idx_p = M.mrc_build_index(ctx, torch.from_numpy(offs).pin_memory(), torch.from_numpy(toks).pin_memory(), V,
+                              mrc_params(M, p))
+    a, b = M.mrc_index_export(ctx, idx), M.mrc_index_export(ctx, idx_p)
+    assert all(np.array_equal(a[key], b[key]) for key in ("df", "sig", "simhash"))
+    idx_p.free()
     idx.free()
 
 
