@@ -823,6 +823,7 @@ def run_headline(args, rank, world, local):
     e1.record(stream)
     torch.cuda.synchronize()
     sig_ms = e0.elapsed_time(e1) / 5
+    atom_rate = ctx.smem_atomic_rate()
     idx.free()
     del sig_out
     peaks = _peaks()
@@ -857,7 +858,14 @@ def run_headline(args, rank, world, local):
         "signature_pass": {"ms": sig_ms, "docs_per_s": N / (sig_ms / 1e3), "bytes": sig_bytes,
                            "achieved_gbs": sig_bytes / (sig_ms / 1e3) / 1e9,
                            "frac": sig_bytes / (sig_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
-                           "work": "4 B per token + 8 B offsets + 4k B signature + 8 B Simhash per document"},
+                           "work": "4 B per token + 8 B offsets + 4k B signature + 8 B Simhash per document",
+                           "smem_atomic_roofline": {
+                               "bound": "alu", "unit": "G tokens/s (G shared-memory 64-bit atomics/s)",
+                               "achieved": T / (sig_ms / 1e3) / 1e9, "peak": atom_rate / 1e9,
+                               "frac": T / (sig_ms / 1e3) / atom_rate,
+                               "peak_source": "measured: mrc_measure_smem_atomic_rate",
+                               "note": "building a document's bag of terms takes at least one shared-memory atomic "
+                                       "per token (claim or increment), so this rate bounds tokens/s"}},
         "fp32_form_kernels": [{"name": s["name"], "ms_per_launch": s["ms"] / s["launches"]}
                               for s in sorted(st32, key=lambda s: -s["ms"])[:6]],
         "clocks": clk,

@@ -454,6 +454,16 @@ mrc_status mrc_ctx_set_rescoring(mrc_ctx* ctx, int32_t on);
 mrc_status mrc_measure_popc_rate(mrc_ctx* ctx, double* popc_per_s);
 
 /*
+ * Measurement helper (not in the paper): the rate at which ctx's device completes 64-bit
+ * shared-memory atomic adds, per second, from a probe kernel in which every thread keeps eight
+ * adds to distinct slots of a 4,096-slot shared table in flight (best of three timed runs after
+ * one warm-up). Building a document's bag of terms takes at least one such atomic per token (a
+ * claim or an increment of the term's slot), so this rate bounds the signature pass's tokens/s.
+ * Synchronises ctx's stream.
+ */
+mrc_status mrc_measure_smem_atomic_rate(mrc_ctx* ctx, double* atomics_per_s);
+
+/*
  * Per-kernel timing. With timing on, every kernel the context launches is
  * bracketed by CUDA events on the context's stream; mrc_ctx_kernel_stat
  * returns, for kernel slot `slot` (0..count-1), its name, launches, summed

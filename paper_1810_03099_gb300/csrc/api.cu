@@ -1623,6 +1623,13 @@ mrc_status mrc_measure_popc_rate(mrc_ctx* ctx, double* popc_per_s) {
   return e == cudaSuccess ? MRC_OK : cuda_fail(ctx, e, "POPC rate probe");
 }
 
+mrc_status mrc_measure_smem_atomic_rate(mrc_ctx* ctx, double* atomics_per_s) {
+  if (!ctx || !atomics_per_s) return MRC_ERR_INVALID;
+  Scope scope(ctx);
+  const cudaError_t e = measure_smem_atomic_rate(ctx, atomics_per_s);
+  return e == cudaSuccess ? MRC_OK : cuda_fail(ctx, e, "shared-memory atomic rate probe");
+}
+
 mrc_status mrc_ctx_set_rescoring(mrc_ctx* ctx, int32_t on) {
   if (!ctx) return MRC_ERR_INVALID;
   ctx->rescore = on != 0;

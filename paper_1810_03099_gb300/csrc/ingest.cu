@@ -591,3 +591,56 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
 }
 
 }  // namespace mrc
+
+namespace mrc {
+namespace {
+
+// Throughput probe of the bag-of-terms tables' bounding operation: every thread keeps eight
+// 64-bit shared-memory atomic adds to distinct slots of a 4,096-slot table in flight, so the
+// loop runs at the rate the SMs complete shared-memory 64-bit atomics. Hashing a token takes at
+// least one such atomic (a claim or an increment). The table's sum is kept live through a
+// store that never happens for these inputs.
+constexpr int kAtomSlots = 4096;
+__global__ void __launch_bounds__(256) k_smem_atomic_rate(int32_t iters, unsigned long long* sink) {
+  __shared__ unsigned long long tab[kAtomSlots];
+  for (int s = threadIdx.x; s < kAtomSlots; s += blockDim.x) tab[s] = 0ull;
+  __syncthreads();
+  for (int32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) atomicAdd(&tab[(threadIdx.x + 256 * u + 2048 * (it & 1)) & (kAtomSlots - 1)], 1ull);
+  }
+  __syncthreads();
+  if (tab[threadIdx.x] == 0xFFFFFFFFFFFFFFFFull) *sink = tab[threadIdx.x];  // each slot ends at iters
+}
+
+}  // namespace
+
+cudaError_t measure_smem_atomic_rate(mrc_ctx* ctx, double* atomics_per_s) {
+  constexpr int32_t kIters = 2048;
+  const int64_t blocks = (int64_t)ctx->num_sms * 8;
+  unsigned long long* sink = nullptr;
+  cudaError_t e = cudaMallocAsync(&sink, sizeof(unsigned long long), ctx->stream);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best_ms = 0.f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first run warms up
+    e = cudaEventRecord(e0, ctx->stream);
+    k_smem_atomic_rate<<<(unsigned)blocks, 256, 0, ctx->stream>>>(kIters, sink);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && rep > 0 && (best_ms == 0.f || ms < best_ms)) best_ms = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(sink, ctx->stream);
+  if (e != cudaSuccess) return e;
+  *atomics_per_s = (double)blocks * 256.0 * 8.0 * kIters / (best_ms * 1e-3);
+  return cudaStreamSynchronize(ctx->stream);
+}
+
+}  // namespace mrc

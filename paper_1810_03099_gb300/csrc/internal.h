@@ -372,6 +372,8 @@ cudaError_t launch_rescore(mrc_ctx* ctx, const mrc_pair* cand, const unsigned lo
 // simhash_match.cu
 // Measured issue rate of 32-bit POPC on this device (population counts per second).
 cudaError_t measure_popc_rate(mrc_ctx* ctx, double* popc_per_s);
+// ingest.cu: measured rate of 64-bit shared-memory atomic adds on this device (per second).
+cudaError_t measure_smem_atomic_rate(mrc_ctx* ctx, double* atomics_per_s);
 cudaError_t launch_simhash_match(mrc_ctx* ctx, const uint64_t* a, int64_t na, const uint64_t* b, int64_t nb,
                                  int32_t hmax, mrc_pair* pairs, unsigned long long* count, int64_t capacity);
 

@@ -93,6 +93,7 @@ _SIGNATURES = {
     "mrc_ctx_set_test_stall": (C.c_int32, [C.c_void_p, C.c_int32]),
     "mrc_ctx_set_rescoring": (C.c_int32, [C.c_void_p, C.c_int32]),
     "mrc_measure_popc_rate": (C.c_int32, [C.c_void_p, C.c_void_p]),
+    "mrc_measure_smem_atomic_rate": (C.c_int32, [C.c_void_p, C.c_void_p]),
     "mrc_ctx_kernel_stat": (C.c_int32, [C.c_void_p, C.c_int32, C.c_char_p, C.POINTER(C.c_int64),
                                         C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mrc_ctx_reset_stats": (None, [C.c_void_p]),
@@ -210,6 +211,12 @@ class Context:
         """Measured 32-bit POPC issue rate of this context's device (per second)."""
         out = C.c_double()
         self.check(self.lib.mrc_measure_popc_rate(self.handle, C.byref(out)))
+        return out.value
+
+    def smem_atomic_rate(self) -> float:
+        """Measured rate of 64-bit shared-memory atomic adds of this context's device (per second)."""
+        out = C.c_double()
+        self.check(self.lib.mrc_measure_smem_atomic_rate(self.handle, C.byref(out)))
         return out.value
 
     def set_rescoring(self, on: bool):
