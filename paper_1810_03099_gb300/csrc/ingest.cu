@@ -133,12 +133,14 @@ __device__ uint64_t sha1_feature(uint32_t t, uint64_t seed) {
 // (their lengths vary 100-fold). A pass that reads stored bags needs no table, so it takes
 // every document here, the long-document list (longest first) before the short one; a hashing
 // pass takes the short documents only (the long ones go to the group path).
-template <int MODE>
-__global__ void __launch_bounds__(kWarpsShort * 32, 3) k_ingest_short(IngestParams p) {
+// MINB: CTAs per SM the register budget is cut for (3 with tables; 4 for passes over stored
+// bags, whose warps need little shared memory, so that more documents are in flight).
+template <int MODE, int MINB>
+__global__ void __launch_bounds__(kWarpsShort * 32, MINB) k_ingest_short(IngestParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kq = ingest_kq<MODE>(p);
-  uint8_t* base = smem + short_warp_bytes(kq) * warp;
+  uint8_t* base = smem + (p.bag_read ? bag_warp_bytes(kq) : short_warp_bytes(kq)) * warp;
   const Transposer tr(lane);
   const int32_t n_short = p.list_counts[0];
   const int32_t n_long = p.bag_read ? p.list_counts[1] : 0;
@@ -308,16 +310,16 @@ __global__ void k_pack(const float* sig, int64_t n, int32_t k, int32_t normalize
 
 // Persistent grids: as many CTAs as fit on every SM at once (0: the shared memory limit could
 // not be raised).
-template <int MODE>
+template <int MODE, int MINB>
 int short_grid(const mrc_ctx* ctx, size_t smem) {
-  return ctx->num_sms * resident_ctas(k_ingest_short<MODE>, kWarpsShort * 32, smem);
+  return ctx->num_sms * resident_ctas(k_ingest_short<MODE, MINB>, kWarpsShort * 32, smem);
 }
 template <int MODE>
 int long_grid(const mrc_ctx* ctx, size_t smem) {
   return ctx->num_sms * resident_ctas(k_ingest_long<MODE>, kLongThreads, smem);
 }
 
-size_t short_smem(int kq) { return (size_t)kWarpsShort * short_warp_bytes(kq); }
+size_t short_smem(int kq, bool bag) { return (size_t)kWarpsShort * (bag ? bag_warp_bytes(kq) : short_warp_bytes(kq)); }
 size_t long_smem(int kq) { return std::max((size_t)kGroupsLong * long_group_bytes(kq), long_huge_bytes(kq)); }
 
 template <int MODE>
@@ -349,7 +351,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   p.huge_cursor = counts + kCntHugeCursor;
   p.err = d.err;
   const int kq = ingest_kq<MODE>(p);
-  const size_t s_smem = short_smem(kq), l_smem = long_smem(kq);
+  const size_t s_smem = short_smem(kq, p.bag_read != 0), l_smem = long_smem(kq);
   const double tokens = (double)d.n_tokens;
   cudaEvent_t ev = nullptr;
   // The CTA path (longest documents first) is launched first; the warp path follows as a
@@ -370,7 +372,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
     if (e != cudaSuccess) return e;
   }
   {
-    int grid = short_grid<MODE>(ctx, s_smem);
+    int grid = p.bag_read ? short_grid<MODE, 4>(ctx, s_smem) : short_grid<MODE, 3>(ctx, s_smem);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     const int64_t need = (d.n_docs + kWarpsShort - 1) / kWarpsShort;
     if (need < grid) grid = (int)need;
@@ -386,7 +388,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = overlap && !p.bag_read ? 1 : 0;
-    e = cudaLaunchKernelEx(&cfg, k_ingest_short<MODE>, p);
+    e = p.bag_read ? cudaLaunchKernelEx(&cfg, k_ingest_short<MODE, 4>, p) : cudaLaunchKernelEx(&cfg, k_ingest_short<MODE, 3>, p);
     timing_end(ctx, ev);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -567,13 +569,13 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
   p.short_cursor = counts + kCntShortCursor;
   p.huge_cursor = counts + kCntHugeCursor;
   p.err = err;
-  const size_t s_smem = short_smem(k), l_smem = long_smem(k);
+  const size_t s_smem = short_smem(k, false), l_smem = long_smem(k);
   if (h[0] > 0) {
-    int grid = short_grid<kSIG>(ctx, s_smem);
+    int grid = short_grid<kSIG, 3>(ctx, s_smem);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     const int need = (h[0] + kWarpsShort - 1) / kWarpsShort;
     if (need < grid) grid = need;
-    k_ingest_short<kSIG><<<grid, kWarpsShort * 32, s_smem, ctx->stream>>>(p);
+    k_ingest_short<kSIG, 3><<<grid, kWarpsShort * 32, s_smem, ctx->stream>>>(p);
   }
   if (h[1] > 0) {
     int grid = long_grid<kSIG>(ctx, l_smem);

@@ -420,6 +420,8 @@ __device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsi
 // ---------------------------------------------------------------- warp path
 // Shared memory of one warp of the warp path: partition accumulators, the table, the list of
 // occupied slots and two counters.
+// A pass over stored bags uses no table: its warps need only the accumulators and counters.
+__host__ __device__ __forceinline__ size_t bag_warp_bytes(int kq) { return (size_t)kq * 8 + 16; }
 __host__ __device__ __forceinline__ size_t short_warp_bytes(int kq) {
   return (size_t)kq * 8 + (size_t)kShortSlots * 8 + (size_t)kShortMax * 2 + 16;
 }
@@ -434,7 +436,8 @@ __device__ void warp_doc(const IngestParams& p, int64_t d, uint8_t* base, int kq
   unsigned long long* num_q = reinterpret_cast<unsigned long long*>(base);
   unsigned long long* tab = num_q + kq;
   uint16_t* list = reinterpret_cast<uint16_t*>(tab + kShortSlots);
-  int32_t* misc = reinterpret_cast<int32_t*>(list + kShortMax);  // [0] list size, [1] row count
+  // [0] list size, [1] row count (right after the accumulators in a pass over stored bags)
+  int32_t* misc = p.bag_read ? reinterpret_cast<int32_t*>(tab) : reinterpret_cast<int32_t*>(list + kShortMax);
   int64_t o0, len;
   doc_span(p, d, o0, len);
   for (int q = lane; q < kq; q += 32) num_q[q] = 0ull;
