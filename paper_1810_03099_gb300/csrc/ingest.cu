@@ -133,7 +133,7 @@ __device__ uint64_t sha1_feature(uint32_t t, uint64_t seed) {
 // (their lengths vary 100-fold). A pass that reads stored bags needs no table, so it takes
 // every document here, the long-document list (longest first) before the short one; a hashing
 // pass takes the short documents only (the long ones go to the group path).
-// MINB: CTAs per SM the register budget is cut for (3 with tables; 4 for passes over stored
+// MINB: CTAs per SM the register budget is cut for (3 with tables; 5 for passes over stored
 // bags, whose warps need little shared memory, so that more documents are in flight).
 template <int MODE, int MINB>
 __global__ void __launch_bounds__(kWarpsShort * 32, MINB) k_ingest_short(IngestParams p) {
@@ -372,7 +372,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
     if (e != cudaSuccess) return e;
   }
   {
-    int grid = p.bag_read ? short_grid<MODE, 4>(ctx, s_smem) : short_grid<MODE, 3>(ctx, s_smem);
+    int grid = p.bag_read ? short_grid<MODE, 5>(ctx, s_smem) : short_grid<MODE, 3>(ctx, s_smem);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     const int64_t need = (d.n_docs + kWarpsShort - 1) / kWarpsShort;
     if (need < grid) grid = (int)need;
@@ -388,7 +388,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = overlap && !p.bag_read ? 1 : 0;
-    e = p.bag_read ? cudaLaunchKernelEx(&cfg, k_ingest_short<MODE, 4>, p) : cudaLaunchKernelEx(&cfg, k_ingest_short<MODE, 3>, p);
+    e = p.bag_read ? cudaLaunchKernelEx(&cfg, k_ingest_short<MODE, 5>, p) : cudaLaunchKernelEx(&cfg, k_ingest_short<MODE, 3>, p);
     timing_end(ctx, ev);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
