@@ -162,7 +162,7 @@ __device__ void phase_signature(const BatchParams& bp, int64_t n, uint8_t* smem,
     if (x >= n_long) break;
     team_doc<kSIG>(ing, __ldcg(bp.long_list + x), smem, kq, bp.team_slots, blockDim.x, 1, threadIdx.x, tr);
   }
-  uint8_t* wbase = smem + (size_t)warp * short_warp_bytes(kq);
+  uint8_t* wbase = smem + (size_t)warp * short_warp_bytes(kq, ing.narrow != 0);
   while (true) {
     int32_t d = 0;
     if (lane == 0) d = atomicAdd(bp.ctl + kCtlShortCur, 1);
@@ -514,9 +514,10 @@ cudaError_t run_batch(mrc_ctx* ctx, const BatchKernelArgs& a) {
   }
   p.n_live = a.n_live;
   p.n_tokens = a.max_tokens;
+  p.narrow = narrow_slots(p.vocab) ? 1 : 0;
   const int kq = ingest_kq<kSIG>(p);
   constexpr size_t smem = batch_smem_bytes<FMT, RB, BN>();
-  if ((size_t)(kResThreads / 32) * short_warp_bytes(kq) > smem - 1024) return cudaErrorInvalidValue;
+  if ((size_t)(kResThreads / 32) * short_warp_bytes(kq, p.narrow != 0) > smem - 1024) return cudaErrorInvalidValue;
   int slots = kHugeSlots;
   while (slots > 1024 && long_huge_bytes(kq) - (size_t)(kHugeSlots - slots) * 10 > smem - 1024) slots >>= 1;
   if ((size_t)kq * 8 + 304 + (size_t)slots * 10 > smem - 1024) return cudaErrorInvalidValue;

@@ -133,14 +133,15 @@ __device__ uint64_t sha1_feature(uint32_t t, uint64_t seed) {
 // (their lengths vary 100-fold). A pass that reads stored bags needs no table, so it takes
 // every document here, the long-document list (longest first) before the short one; a hashing
 // pass takes the short documents only (the long ones go to the group path).
-// MINB: CTAs per SM the register budget is cut for (3 with tables; 5 for passes over stored
-// bags, whose warps need little shared memory, so that more documents are in flight).
+// MINB: CTAs per SM the register budget is cut for (3 with 64-bit tables, 4 with 32-bit ones; 5
+// for passes over stored bags, whose warps need little shared memory), so that as many
+// documents as the shared memory holds are in flight.
 template <int MODE, int MINB>
 __global__ void __launch_bounds__(kWarpsShort * 32, MINB) k_ingest_short(IngestParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kq = ingest_kq<MODE>(p);
-  uint8_t* base = smem + (p.bag_read ? bag_warp_bytes(kq) : short_warp_bytes(kq)) * warp;
+  uint8_t* base = smem + (p.bag_read ? bag_warp_bytes(kq) : short_warp_bytes(kq, p.narrow != 0)) * warp;
   const Transposer tr(lane);
   const int32_t n_short = p.list_counts[0];
   const int32_t n_long = p.bag_read ? p.list_counts[1] : 0;
@@ -319,7 +320,9 @@ int long_grid(const mrc_ctx* ctx, size_t smem) {
   return ctx->num_sms * resident_ctas(k_ingest_long<MODE>, kLongThreads, smem);
 }
 
-size_t short_smem(int kq, bool bag) { return (size_t)kWarpsShort * (bag ? bag_warp_bytes(kq) : short_warp_bytes(kq)); }
+size_t short_smem(int kq, bool bag, bool narrow) {
+  return (size_t)kWarpsShort * (bag ? bag_warp_bytes(kq) : short_warp_bytes(kq, narrow));
+}
 size_t long_smem(int kq) { return std::max((size_t)kGroupsLong * long_group_bytes(kq), long_huge_bytes(kq)); }
 
 template <int MODE>
@@ -350,8 +353,9 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   p.short_cursor = counts + kCntShortCursor;
   p.huge_cursor = counts + kCntHugeCursor;
   p.err = d.err;
+  p.narrow = narrow_slots(p.vocab) ? 1 : 0;
   const int kq = ingest_kq<MODE>(p);
-  const size_t s_smem = short_smem(kq, p.bag_read != 0), l_smem = long_smem(kq);
+  const size_t s_smem = short_smem(kq, p.bag_read != 0, p.narrow != 0), l_smem = long_smem(kq);
   const double tokens = (double)d.n_tokens;
   cudaEvent_t ev = nullptr;
   // The CTA path (longest documents first) is launched first; the warp path follows as a
@@ -372,7 +376,9 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
     if (e != cudaSuccess) return e;
   }
   {
-    int grid = p.bag_read ? short_grid<MODE, 5>(ctx, s_smem) : short_grid<MODE, 3>(ctx, s_smem);
+    // CTAs per SM: five over stored bags, four with 32-bit tables, three with 64-bit ones
+    int grid = p.bag_read ? short_grid<MODE, 5>(ctx, s_smem)
+                          : (p.narrow ? short_grid<MODE, 4>(ctx, s_smem) : short_grid<MODE, 3>(ctx, s_smem));
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     const int64_t need = (d.n_docs + kWarpsShort - 1) / kWarpsShort;
     if (need < grid) grid = (int)need;
@@ -388,7 +394,9 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = overlap && !p.bag_read ? 1 : 0;
-    e = p.bag_read ? cudaLaunchKernelEx(&cfg, k_ingest_short<MODE, 5>, p) : cudaLaunchKernelEx(&cfg, k_ingest_short<MODE, 3>, p);
+    e = p.bag_read ? cudaLaunchKernelEx(&cfg, k_ingest_short<MODE, 5>, p)
+                   : (p.narrow ? cudaLaunchKernelEx(&cfg, k_ingest_short<MODE, 4>, p)
+                               : cudaLaunchKernelEx(&cfg, k_ingest_short<MODE, 3>, p));
     timing_end(ctx, ev);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -569,7 +577,8 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
   p.short_cursor = counts + kCntShortCursor;
   p.huge_cursor = counts + kCntHugeCursor;
   p.err = err;
-  const size_t s_smem = short_smem(k, false), l_smem = long_smem(k);
+  p.narrow = narrow_slots(p.vocab) ? 1 : 0;
+  const size_t s_smem = short_smem(k, false, p.narrow != 0), l_smem = long_smem(k);
   if (h[0] > 0) {
     int grid = short_grid<kSIG, 3>(ctx, s_smem);
     if (grid <= 0) return cudaErrorInvalidConfiguration;

@@ -119,27 +119,52 @@ __device__ __forceinline__ float inv_norm_of(unsigned long long norm_q) {
 // shared-memory counter, so later passes walk only occupied slots) and, with df, the term's
 // document frequency gets its 1. Returns false if a term found no slot.
 constexpr unsigned long long kEmpty64 = 0xFFFFFFFF00000000ull;
-template <int B>
-__device__ __forceinline__ bool insert_batch(unsigned long long* tab, uint16_t* list, int32_t* list_n, int log2ts,
+// Warp-path tables of a vocabulary of fewer than kNarrowVocab term ids use 32-bit slots: the term
+// id above kSlotCountBits bits of count (a document of at most kShortMax tokens counts a term at
+// most 512 times), and all ones for a free slot (no term id reaches it). Half the shared memory
+// per warp, so more documents are in flight per SM.
+constexpr int kSlotCountBits = 10;
+constexpr uint32_t kEmpty32 = 0xFFFFFFFFu;
+constexpr int32_t kNarrowVocab = (1 << (32 - kSlotCountBits)) - 1;
+static_assert(kShortMax < (1 << kSlotCountBits), "a warp-path document's counts fit a 32-bit slot");
+template <typename S>
+struct Slot;
+template <>
+struct Slot<unsigned long long> {
+  static constexpr unsigned long long kFree = kEmpty64, kOne = 1ull;
+  __device__ static unsigned long long make(uint32_t t) { return ((unsigned long long)t << 32) | 1ull; }
+  __device__ static uint32_t term(unsigned long long v) { return (uint32_t)(v >> 32); }
+  __device__ static uint32_t count(unsigned long long v) { return (uint32_t)v; }
+};
+template <>
+struct Slot<uint32_t> {
+  static constexpr uint32_t kFree = kEmpty32, kOne = 1u;
+  __device__ static uint32_t make(uint32_t t) { return (t << kSlotCountBits) | 1u; }
+  __device__ static uint32_t term(uint32_t v) { return v >> kSlotCountBits; }
+  __device__ static uint32_t count(uint32_t v) { return v & ((1u << kSlotCountBits) - 1u); }
+};
+template <int B, typename S>
+__device__ __forceinline__ bool insert_batch(S* tab, uint16_t* list, int32_t* list_n, int log2ts,
                                              const int32_t (&tk)[B], uint32_t pend, int32_t* df) {
+  using T = Slot<S>;
   const uint32_t mask = (1u << log2ts) - 1u;
   uint32_t slot[B];
 #pragma unroll
   for (int u = 0; u < B; ++u) slot[u] = slot_of((uint32_t)tk[u], log2ts);
   uint32_t fresh = 0u;
   for (uint32_t round = 0; pend != 0u && round <= mask; ++round) {
-    unsigned long long prev[B];
+    S prev[B];
 #pragma unroll
     for (int u = 0; u < B; ++u)
-      if ((pend >> u) & 1u) prev[u] = atomicCAS(&tab[slot[u]], kEmpty64, ((unsigned long long)(uint32_t)tk[u] << 32) | 1ull);
+      if ((pend >> u) & 1u) prev[u] = atomicCAS(&tab[slot[u]], T::kFree, T::make((uint32_t)tk[u]));
 #pragma unroll
     for (int u = 0; u < B; ++u)
       if ((pend >> u) & 1u) {
-        if (prev[u] == kEmpty64) {
+        if (prev[u] == T::kFree) {
           fresh |= 1u << u;
           pend &= ~(1u << u);
-        } else if ((uint32_t)(prev[u] >> 32) == (uint32_t)tk[u]) {
-          atomicAdd(&tab[slot[u]], 1ull);
+        } else if (T::term(prev[u]) == (uint32_t)tk[u]) {
+          atomicAdd(&tab[slot[u]], T::kOne);
           pend &= ~(1u << u);
         } else {
           slot[u] = (slot[u] + 1u) & mask;
@@ -202,6 +227,7 @@ struct IngestParams {
   // not lie in [0, n_tokens). NULL elsewhere.
   const int64_t* n_live;
   int64_t n_tokens;
+  int32_t narrow;  // warp-path tables with 32-bit slots (vocab < kNarrowVocab)
 };
 
 // Token range of document d. A document past *n_live, or with a length outside
@@ -422,20 +448,67 @@ __device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsi
 // occupied slots and two counters.
 // A pass over stored bags uses no table: its warps need only the accumulators and counters.
 __host__ __device__ __forceinline__ size_t bag_warp_bytes(int kq) { return (size_t)kq * 8 + 16; }
-__host__ __device__ __forceinline__ size_t short_warp_bytes(int kq) {
-  return (size_t)kq * 8 + (size_t)kShortSlots * 8 + (size_t)kShortMax * 2 + 16;
+__host__ __device__ __forceinline__ size_t short_warp_bytes(int kq, bool narrow) {
+  return (size_t)kq * 8 + (size_t)kShortSlots * (narrow ? 4 : 8) + (size_t)kShortMax * 2 + 16;
+}
+__host__ __device__ __forceinline__ bool narrow_slots(int32_t vocab) { return vocab > 0 && vocab <= kNarrowVocab; }
+
+// The hashing part of warp_doc: the document's tokens into the warp's table of S slots, the
+// occupied slots listed; with bag_write the bag is stored. Returns the number of distinct terms.
+template <int MODE, typename S>
+__device__ __forceinline__ int hash_doc(const IngestParams& p, int64_t d, S* tab, uint16_t* list, int32_t* misc,
+                                        int64_t o0, int64_t len, int lane) {
+  using T = Slot<S>;
+  const int l2 = log2_slots(len, 10);
+  const int ts = 1 << l2;
+  for (int s = lane; s < ts; s += 32) tab[s] = T::kFree;
+  int32_t tk[kShortRegs];
+#pragma unroll
+  for (int u = 0; u < kShortRegs; ++u) tk[u] = lane + 32 * u < len ? __ldcs(p.tokens + o0 + lane + 32 * u) : -1;
+  __syncwarp();
+  int32_t* df = (MODE == kDF || MODE == kDFN) ? p.df : nullptr;
+#pragma unroll
+  for (int h = 0; h < kShortRegs; h += 8) {
+    if (32 * h >= len) break;  // warp-uniform
+    int32_t tb[8];
+    uint32_t pend = 0u;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      tb[u] = tk[h + u];
+      if (lane + 32 * (h + u) < len) {
+        if ((uint32_t)tb[u] >= (uint32_t)p.vocab)
+          set_err(p.err, kErrBadToken);
+        else
+          pend |= 1u << u;
+      }
+    }
+    if (!insert_batch<8, S>(tab, list, &misc[0], l2, tb, pend, df)) set_err(p.err, kErrTable);
+  }
+  __syncwarp();
+  const int nnz = misc[0];
+  if (p.bag_write) {
+    for (int x = lane; x < nnz; x += 32) {
+      const S v = tab[list[x]];
+      p.bag_terms[o0 + x] = (int32_t)T::term(v);
+      p.bag_cnts[o0 + x] = (int32_t)T::count(v);
+    }
+    if (lane == 0) p.bag_n[d] = nnz;
+  }
+  return nnz;
 }
 
 // One document of <= kShortMax tokens (or any stored bag) by one warp, in the warp's shared
-// memory `base` (short_warp_bytes(kq)). The document's terms are either read from the stored
-// bag as they are walked, or built by hashing the tokens (all token loads in flight at once,
-// inserts in batches of 8) and found through the list of occupied slots. They are then walked
-// 32 at a time, each chunk's table values gathered while the previous chunk is worked on.
+// memory `base` (short_warp_bytes(kq, p.narrow), or bag_warp_bytes(kq) for a pass over stored
+// bags). The document's terms are either read from the stored bag as they are walked, or built
+// by hashing the tokens (all token loads in flight at once, inserts in batches of 8) and found
+// through the list of occupied slots. They are then walked 32 at a time, each chunk's table
+// values gathered while the previous chunk is worked on.
 template <int MODE>
 __device__ void warp_doc(const IngestParams& p, int64_t d, uint8_t* base, int kq, int lane, const Transposer& tr) {
   unsigned long long* num_q = reinterpret_cast<unsigned long long*>(base);
-  unsigned long long* tab = num_q + kq;
-  uint16_t* list = reinterpret_cast<uint16_t*>(tab + kShortSlots);
+  uint8_t* tab = reinterpret_cast<uint8_t*>(num_q + kq);
+  const bool narrow = p.narrow != 0;
+  uint16_t* list = reinterpret_cast<uint16_t*>(tab + (size_t)kShortSlots * (narrow ? 4 : 8));
   // [0] list size, [1] row count (right after the accumulators in a pass over stored bags)
   int32_t* misc = p.bag_read ? reinterpret_cast<int32_t*>(tab) : reinterpret_cast<int32_t*>(list + kShortMax);
   int64_t o0, len;
@@ -446,45 +519,13 @@ __device__ void warp_doc(const IngestParams& p, int64_t d, uint8_t* base, int kq
     misc[1] = 0;
   }
   int nnz = 0;
-  if (p.bag_read) {
+  if (p.bag_read)
     nnz = p.bag_n[d];  // the document's bag, built by an earlier pass, read as it is walked
-  } else {
-    const int l2 = log2_slots(len, 10);
-    const int ts = 1 << l2;
-    for (int s = lane; s < ts; s += 32) tab[s] = kEmpty64;
-    int32_t tk[kShortRegs];
-#pragma unroll
-    for (int u = 0; u < kShortRegs; ++u) tk[u] = lane + 32 * u < len ? __ldcs(p.tokens + o0 + lane + 32 * u) : -1;
-    __syncwarp();
-    int32_t* df = (MODE == kDF || MODE == kDFN) ? p.df : nullptr;
-#pragma unroll
-    for (int h = 0; h < kShortRegs; h += 8) {
-      if (32 * h >= len) break;  // warp-uniform
-      int32_t tb[8];
-      uint32_t pend = 0u;
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        tb[u] = tk[h + u];
-        if (lane + 32 * (h + u) < len) {
-          if ((uint32_t)tb[u] >= (uint32_t)p.vocab)
-            set_err(p.err, kErrBadToken);
-          else
-            pend |= 1u << u;
-        }
-      }
-      if (!insert_batch<8>(tab, list, &misc[0], l2, tb, pend, df)) set_err(p.err, kErrTable);
-    }
-    __syncwarp();
-    nnz = misc[0];
-    if (p.bag_write) {
-      for (int x = lane; x < nnz; x += 32) {
-        const unsigned long long v = tab[list[x]];
-        p.bag_terms[o0 + x] = (int32_t)(uint32_t)(v >> 32);
-        p.bag_cnts[o0 + x] = (int32_t)(uint32_t)v;
-      }
-      if (lane == 0) p.bag_n[d] = nnz;
-    }
-  }
+  else if (narrow)
+    nnz = hash_doc<MODE, uint32_t>(p, d, reinterpret_cast<uint32_t*>(tab), list, misc, o0, len, lane);
+  else
+    nnz = hash_doc<MODE, unsigned long long>(p, d, reinterpret_cast<unsigned long long*>(tab), list, misc, o0, len,
+                                             lane);
   Acc a{0ull, 0ull, 0u, 0u};
   float inv_norm = 0.f;
   if (MODE == kDENSE) inv_norm = inv_norm_of(p.dense.norm[d]);
@@ -498,10 +539,14 @@ __device__ void warp_doc(const IngestParams& p, int64_t d, uint8_t* base, int kq
       } else if (bag) {
         key = (uint32_t)__ldcs(p.bag_terms + o0 + x);
         c = (uint32_t)__ldcs(p.bag_cnts + o0 + x);
+      } else if (narrow) {
+        const uint32_t v = reinterpret_cast<const uint32_t*>(tab)[list[x]];
+        key = Slot<uint32_t>::term(v);
+        c = Slot<uint32_t>::count(v);
       } else {
-        const unsigned long long v = tab[list[x]];
-        key = (uint32_t)(v >> 32);
-        c = (uint32_t)v;
+        const unsigned long long v = reinterpret_cast<const unsigned long long*>(tab)[list[x]];
+        key = Slot<unsigned long long>::term(v);
+        c = Slot<unsigned long long>::count(v);
       }
     };
     uint32_t key, c;
