@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 #include <algorithm>
 #include <string>
+#include <type_traits>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
@@ -160,10 +161,12 @@ __global__ void __launch_bounds__(kWarpsShort * 32, MINB) k_ingest_short(IngestP
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kLongThreads, 1) k_ingest_long(IngestParams p) {
+// G groups of kGroupThreads threads; NARROW: the groups' tables have 32-bit slots.
+template <int MODE, int G, bool NARROW>
+__global__ void __launch_bounds__(G * kGroupThreads, 1) k_ingest_long(IngestParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int32_t s_next, s_huge;
+  constexpr int kThreads = G * kGroupThreads;
   const int g = threadIdx.x / kGroupThreads, gt = threadIdx.x % kGroupThreads;
   const int lane = threadIdx.x & 31;
   const int kq = ingest_kq<MODE>(p);
@@ -185,17 +188,18 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_ingest_long(IngestParams p)
     const int32_t it = s_next;
     __syncthreads();
     if (it >= n_huge) break;
-    team_doc<MODE>(p, p.long_list[it], smem, kq, kHugeSlots, kLongThreads, 0, threadIdx.x, tr);
+    team_doc<MODE>(p, p.long_list[it], smem, kq, kHugeSlots, kThreads, 0, threadIdx.x, tr);
   }
   // phase 2: the other long documents, one per group at a time
-  uint8_t* base = smem + long_group_bytes(kq) * g;
+  uint8_t* base = smem + long_group_bytes(kq, NARROW) * g;
   int32_t* slot = reinterpret_cast<int32_t*>(base + (size_t)kq * 8 + 16 + 64 * 4);  // misc[0] of the group
   while (true) {
     if (gt == 0) *slot = n_huge + atomicAdd(p.long_cursor, 1);
     team_sync(1 + g, kGroupThreads);
     const int32_t it = *slot;
     if (it >= n_long) break;
-    team_doc<MODE>(p, p.long_list[it], base, kq, kLongSlots, kGroupThreads, 1 + g, gt, tr);
+    team_doc<MODE, typename std::conditional<NARROW, uint32_t, unsigned long long>::type>(
+        p, p.long_list[it], base, kq, kLongSlots, kGroupThreads, 1 + g, gt, tr);
   }
 }
 
@@ -315,15 +319,35 @@ template <int MODE, int MINB>
 int short_grid(const mrc_ctx* ctx, size_t smem) {
   return ctx->num_sms * resident_ctas(k_ingest_short<MODE, MINB>, kWarpsShort * 32, smem);
 }
-template <int MODE>
+template <int MODE, bool NARROW>
 int long_grid(const mrc_ctx* ctx, size_t smem) {
-  return ctx->num_sms * resident_ctas(k_ingest_long<MODE>, kLongThreads, smem);
+  constexpr int G = long_groups(MODE, NARROW);
+  return ctx->num_sms * resident_ctas(k_ingest_long<MODE, G, NARROW>, G * kGroupThreads, smem);
 }
 
 size_t short_smem(int kq, bool bag, bool narrow) {
   return (size_t)kWarpsShort * (bag ? bag_warp_bytes(kq) : short_warp_bytes(kq, narrow));
 }
-size_t long_smem(int kq) { return std::max((size_t)kGroupsLong * long_group_bytes(kq), long_huge_bytes(kq)); }
+template <int MODE, bool NARROW>
+size_t long_smem(int kq) {
+  return std::max((size_t)long_groups(MODE, NARROW) * long_group_bytes(kq, NARROW), long_huge_bytes(kq));
+}
+
+// The long-document grid (persistent: as many CTAs as fit, at most `cap`), narrow or wide tables.
+template <int MODE, bool NARROW>
+cudaError_t launch_long_as(mrc_ctx* ctx, const IngestParams& p, int kq, int64_t cap) {
+  constexpr int G = long_groups(MODE, NARROW);
+  const size_t smem = long_smem<MODE, NARROW>(kq);
+  int grid = long_grid<MODE, NARROW>(ctx, smem);
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  if (cap < grid) grid = (int)cap;
+  k_ingest_long<MODE, G, NARROW><<<grid, G * kGroupThreads, smem, ctx->stream>>>(p);
+  return cudaGetLastError();
+}
+template <int MODE>
+cudaError_t launch_long(mrc_ctx* ctx, const IngestParams& p, int kq, int64_t cap) {
+  return p.narrow ? launch_long_as<MODE, true>(ctx, p, kq, cap) : launch_long_as<MODE, false>(ctx, p, kq, cap);
+}
 
 template <int MODE>
 cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const char* name, double bytes_per_token,
@@ -355,7 +379,7 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   p.err = d.err;
   p.narrow = narrow_slots(p.vocab) ? 1 : 0;
   const int kq = ingest_kq<MODE>(p);
-  const size_t s_smem = short_smem(kq, p.bag_read != 0, p.narrow != 0), l_smem = long_smem(kq);
+  const size_t s_smem = short_smem(kq, p.bag_read != 0, p.narrow != 0);
   const double tokens = (double)d.n_tokens;
   cudaEvent_t ev = nullptr;
   // The CTA path (longest documents first) is launched first; the warp path follows as a
@@ -365,14 +389,10 @@ cudaError_t run_ingest(mrc_ctx* ctx, const DocsDev& d, IngestParams p, const cha
   cudaStreamIsCapturing(ctx->stream, &cap);
   const bool overlap = cap == cudaStreamCaptureStatusNone && !ctx->timing;
   if (!p.bag_read) {  // a pass over stored bags takes every document in the warp path
-    int grid = long_grid<MODE>(ctx, l_smem);
-    if (grid <= 0) return cudaErrorInvalidConfiguration;
-    if (d.n_docs < grid) grid = (int)d.n_docs;
     std::string nm = std::string(name) + ".long";
     timing_begin(ctx, nm.c_str(), 0.0, 0.0, &ev);
-    k_ingest_long<MODE><<<grid, kLongThreads, l_smem, ctx->stream>>>(p);
+    e = launch_long<MODE>(ctx, p, kq, d.n_docs);
     timing_end(ctx, ev);
-    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   {
@@ -578,7 +598,7 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
   p.huge_cursor = counts + kCntHugeCursor;
   p.err = err;
   p.narrow = narrow_slots(p.vocab) ? 1 : 0;
-  const size_t s_smem = short_smem(k, false, p.narrow != 0), l_smem = long_smem(k);
+  const size_t s_smem = short_smem(k, false, p.narrow != 0);
   if (h[0] > 0) {
     int grid = short_grid<kSIG, 3>(ctx, s_smem);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
@@ -587,10 +607,8 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
     k_ingest_short<kSIG, 3><<<grid, kWarpsShort * 32, s_smem, ctx->stream>>>(p);
   }
   if (h[1] > 0) {
-    int grid = long_grid<kSIG>(ctx, l_smem);
-    if (grid <= 0) return cudaErrorInvalidConfiguration;
-    if (h[1] < grid) grid = h[1];
-    k_ingest_long<kSIG><<<grid, kLongThreads, l_smem, ctx->stream>>>(p);
+    e = launch_long<kSIG>(ctx, p, k, h[1]);
+    if (e != cudaSuccess) return e;
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -20,8 +20,7 @@ constexpr int kWarpsShort = 7;      // warps per CTA in the warp path (three CTA
 constexpr int kShortRegs = kShortMax / 32;  // tokens (then terms) per lane held in registers (warp path)
 constexpr int kGroupWarps = 4;      // warps per document group of the long-document path
 constexpr int kGroupThreads = kGroupWarps * 32;
-constexpr int kGroupsLong = 5;      // groups per CTA (one CTA per SM: five tables fill shared memory)
-constexpr int kLongThreads = kGroupsLong * kGroupThreads;
+constexpr int kGroupsLong = 5;      // groups per CTA with 64-bit tables (one CTA per SM: five fill shared memory)
 constexpr int kLongSlots = 4096;    // per-group table: documents with > 2048 tokens take several passes
 constexpr int kLongUnroll = 4;      // token loads per thread in flight (long-document path)
 constexpr float kFix = 4194304.0f;  // 2^22
@@ -119,14 +118,14 @@ __device__ __forceinline__ float inv_norm_of(unsigned long long norm_q) {
 // shared-memory counter, so later passes walk only occupied slots) and, with df, the term's
 // document frequency gets its 1. Returns false if a term found no slot.
 constexpr unsigned long long kEmpty64 = 0xFFFFFFFF00000000ull;
-// Warp-path tables of a vocabulary of fewer than kNarrowVocab term ids use 32-bit slots: the term
-// id above kSlotCountBits bits of count (a document of at most kShortMax tokens counts a term at
-// most 512 times), and all ones for a free slot (no term id reaches it). Half the shared memory
-// per warp, so more documents are in flight per SM.
-constexpr int kSlotCountBits = 10;
+// The tables of the warp path and of the four-warp groups use 32-bit slots when the vocabulary has
+// fewer than kNarrowVocab term ids: the term id above kSlotCountBits bits of count (those
+// documents have fewer than kHugeMin tokens, so no count reaches 2^11), and all ones for a free
+// slot (no term id reaches it). Half the shared memory per table, so more documents are in
+// flight per SM. The CTA-wide table of the longest documents keeps 64-bit slots.
+constexpr int kSlotCountBits = 11;
 constexpr uint32_t kEmpty32 = 0xFFFFFFFFu;
 constexpr int32_t kNarrowVocab = (1 << (32 - kSlotCountBits)) - 1;
-static_assert(kShortMax < (1 << kSlotCountBits), "a warp-path document's counts fit a 32-bit slot");
 template <typename S>
 struct Slot;
 template <>
@@ -598,8 +597,15 @@ constexpr int kCntClass = 8, kCntClassFill = 16, kCntWords = 32;
 constexpr int kHugeMin = 2048;       // documents this long take a whole CTA
 constexpr int kHugeSlots = 16384;    // the CTA-wide table
 static_assert(kHugeMin == (2 << (9 + 1)), "length classes 2 and up are the documents of kHugeMin tokens or more");
-__host__ __device__ __forceinline__ size_t long_group_bytes(int kq) {
-  return (size_t)kq * 8 + 16 + 64 * 4 + 16 + (size_t)kLongSlots * 8 + (size_t)kLongSlots * 2;
+static_assert(kHugeMin <= (1 << kSlotCountBits), "a group-path document's counts fit a 32-bit slot");
+__host__ __device__ __forceinline__ size_t long_group_bytes(int kq, bool narrow) {
+  return (size_t)kq * 8 + 16 + 64 * 4 + 16 + (size_t)kLongSlots * (narrow ? 4 : 8) + (size_t)kLongSlots * 2;
+}
+// Groups per CTA of the long-document path (one CTA per SM): five with 64-bit tables (shared
+// memory), with 32-bit ones eight (1,024 threads) in the passes that need at most 64 registers a
+// thread and seven (72 registers) in the signature pass.
+__host__ __device__ constexpr int long_groups(int mode, bool narrow) {
+  return !narrow ? kGroupsLong : (mode == kSIG ? 7 : 8);
 }
 __host__ __device__ __forceinline__ size_t long_huge_bytes(int kq) {
   return (size_t)kq * 8 + 16 + 64 * 4 + 16 + (size_t)kHugeSlots * 8 + (size_t)kHugeSlots * 2;
@@ -651,9 +657,10 @@ __device__ __forceinline__ void team_walk(const IngestParams& p, int n, int tw, 
 }
 
 // One long document by a team of `nthreads` threads (barrier `bar`) with a table of `slots`
-// 64-bit entries in `base`: accumulators, then hashing passes (or the stored bag) and the
+// entries of type S (64-bit, or 32-bit for documents of fewer than kHugeMin tokens of a
+// narrow vocabulary) in `base`: accumulators, then hashing passes (or the stored bag) and the
 // walks, then the document's outputs. Called by every thread of the team.
-template <int MODE>
+template <int MODE, typename S = unsigned long long>
 __device__ void team_doc(const IngestParams& p, int64_t d, uint8_t* base, int kq, int slots, int nthreads, int bar,
                          int tt, const Transposer& tr) {
   const int tw = tt >> 5, lane = tt & 31, nwarps = nthreads >> 5;
@@ -661,7 +668,7 @@ __device__ void team_doc(const IngestParams& p, int64_t d, uint8_t* base, int kq
   unsigned long long* norm_s = num_q + kq;  // [0] |d|^2, [1] of the bfloat16 weights
   uint32_t* P = reinterpret_cast<uint32_t*>(norm_s + 2);  // [64] Simhash column sums
   int32_t* misc = reinterpret_cast<int32_t*>(P + 64);     // [1] row count, [2] bag size, [3] list size
-  unsigned long long* tab = reinterpret_cast<unsigned long long*>(misc + 4);
+  S* tab = reinterpret_cast<S*>(misc + 4);
   uint16_t* list = reinterpret_cast<uint16_t*>(tab + slots);
   int64_t o0, len;
   doc_span(p, d, o0, len);
@@ -701,7 +708,7 @@ __device__ void team_doc(const IngestParams& p, int64_t d, uint8_t* base, int kq
     const bool walk = MODE != kDF || p.bag_write;
     for (uint32_t pass = 0; pass < passes; ++pass) {
       team_sync(bar, nthreads);
-      for (int sl = tt; sl < ts; sl += nthreads) tab[sl] = kEmpty64;
+      for (int sl = tt; sl < ts; sl += nthreads) tab[sl] = Slot<S>::kFree;
       if (tt == 0) misc[3] = 0;
       team_sync(bar, nthreads);
       for (int64_t x0 = tt; x0 < len; x0 += kLongUnroll * nthreads) {
@@ -729,9 +736,14 @@ __device__ void team_doc(const IngestParams& p, int64_t d, uint8_t* base, int kq
       if (walk) {
         const int n = misc[3];
         auto at = [&](int x, uint32_t& key, uint32_t& c) {
-          const unsigned long long v = x < n ? tab[list[x]] : kEmpty64;
-          key = (uint32_t)(v >> 32);
-          c = (uint32_t)v;
+          if (x < n) {
+            const S v = tab[list[x]];
+            key = Slot<S>::term(v);
+            c = Slot<S>::count(v);
+          } else {
+            key = kEmpty;
+            c = 0u;
+          }
         };
         team_walk<MODE>(p, n, tw, nwarps, lane, at, tr, num_q, a, d, inv_norm, &misc[1], o0,
                         p.bag_write ? &misc[2] : nullptr);

@@ -141,6 +141,29 @@ def test_signature_of_new_documents(torch, M, ctx, orc, corpus):
     idx.free()
 
 
+def test_wide_vocabulary_tables(torch, M, ctx, orc, corpus):
+    """A vocabulary of 2^22 term ids is too wide for the 32-bit table slots (21 bits of term id):
+    every path (warp, four-warp groups, whole CTA) then hashes into 64-bit slots. The index build
+    and the signature pass over tokens still match the oracle, with the mixed corpus's term ids
+    spread over the whole vocabulary."""
+    offs, toks = corpus
+    V = 1 << 22
+    toks = ((toks.astype(np.int64) * 838_861 + 12_345) % V).astype(np.int32)  # distinct ids stay distinct
+    assert toks.max() >= 1 << 21
+    p = Params(k=16)
+    ref = build_index(offs, toks, V, p, orc)
+    idx = M.mrc_build_index(ctx, dev(torch, offs), dev(torch, toks), V, mrc_params(M, p))
+    ex = M.mrc_index_export(ctx, idx)
+    assert np.array_equal(ex["df"].astype(np.int64), ref.df)
+    assert np.abs(ex["sig"].astype(np.float64) - ref.S).max() <= SIG_TOL
+    assert np.array_equal(ex["simhash"], ref.F)
+    S_ref, F_ref, _ = signature(ref, offs, toks, orc)
+    sig, sh = M.mrc_signature(ctx, idx, dev(torch, offs), dev(torch, toks))
+    assert np.abs(sig.cpu().numpy().astype(np.float64) - S_ref).max() <= SIG_TOL
+    assert np.array_equal(sh.cpu().numpy().view(np.uint64), F_ref)
+    idx.free()
+
+
 @pytest.mark.parametrize("k,tau", [(8, 0.9), (64, 0.9), (64, 0.6), (130, 0.8)])
 def test_match_allpairs_fp32(torch, M, ctx, orc, k, tau):
     c = synth.make_corpus("tiny")
