@@ -385,15 +385,37 @@ __device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsi
   const float nrm = sqrtf(u64_to_f32_rn(norm_q) * kInvFix);
   const float nrm16 = p.bf16w ? sqrtf(u64_to_f32_rn(norm16_q) * kInvFix) : 0.f;
   // raw signature s_p = t_p / |d|, t_p = num_p / |R_p|; the unit signature is s / |s|,
-  // computed exactly as the packing of stored raw signatures computes it
-  float ss = 0.f, ss16 = 0.f;
-  for (int q = lane; q < p.k; q += 32) {
+  // computed exactly as the packing of stored raw signatures computes it. The raw entries of
+  // the first kFinCache rounds (k <= 64) stay in registers for the second loop.
+  constexpr int kFinCache = 2;
+  auto raw = [&](int q) {
     const float t = u64_to_f32_rn(num_q[q]) * kInvFix * p.rinv[q];
-    const float sv = nrm > 0.f ? t / nrm : 0.f;
+    return nrm > 0.f ? t / nrm : 0.f;
+  };
+  auto raw16 = [&](int q) {
+    const float t16 = u64_to_f32_rn(num_q[p.k + q]) * kInvFix * p.rinv16[q];
+    return nrm16 > 0.f ? t16 / nrm16 : 0.f;
+  };
+  float svc[kFinCache], sv16c[kFinCache];
+  float ss = 0.f, ss16 = 0.f;
+#pragma unroll
+  for (int r = 0; r < kFinCache; ++r) {
+    const int q = lane + 32 * r;
+    svc[r] = sv16c[r] = 0.f;
+    if (q < p.k) {
+      svc[r] = raw(q);
+      ss += svc[r] * svc[r];
+      if (p.bf16w) {
+        sv16c[r] = raw16(q);
+        ss16 += sv16c[r] * sv16c[r];
+      }
+    }
+  }
+  for (int q = lane + 32 * kFinCache; q < p.k; q += 32) {
+    const float sv = raw(q);
     ss += sv * sv;
     if (p.bf16w) {
-      const float t16 = u64_to_f32_rn(num_q[p.k + q]) * kInvFix * p.rinv16[q];
-      const float sv16 = nrm16 > 0.f ? t16 / nrm16 : 0.f;
+      const float sv16 = raw16(q);
       ss16 += sv16 * sv16;
     }
   }
@@ -403,9 +425,17 @@ __device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsi
   if (p.bf16w) sn16 = sqrtf(warp_sum(ss16));
   const int width = max(p.k, max(p.sig.kp, p.sig.kp8));
   float q2 = 0.f;  // squared norm of the E4M3-quantized unit signature
-  for (int q = lane; q < width; q += 32) {
-    const float t = q < p.k ? u64_to_f32_rn(num_q[q]) * kInvFix * p.rinv[q] : 0.f;
-    const float sv = nrm > 0.f ? t / nrm : 0.f;
+  for (int q = lane, r = 0; q < width; q += 32, ++r) {
+    float sv = 0.f;
+    if (q < p.k) {
+      if (r < kFinCache) {
+#pragma unroll
+        for (int x = 0; x < kFinCache; ++x)
+          if (x == r) sv = svc[x];
+      } else {
+        sv = raw(q);
+      }
+    }
     const float u = (q < p.k && sn > 0.f) ? sv / sn : 0.f;
     if (q < p.k) {
       if (p.sig.sig) p.sig.sig[d * p.k + q] = sv;
@@ -421,8 +451,16 @@ __device__ void finalize_sig(const IngestParams& p, int64_t d, int64_t len, unsi
     if (q < p.sig.kp8 && p.sig.op_e4m3) {
       float u8 = u;
       if (p.bf16w) {
-        const float t16 = q < p.k ? u64_to_f32_rn(num_q[p.k + q]) * kInvFix * p.rinv16[q] : 0.f;
-        const float sv16 = nrm16 > 0.f ? t16 / nrm16 : 0.f;
+        float sv16 = 0.f;
+        if (q < p.k) {
+          if (r < kFinCache) {
+#pragma unroll
+            for (int x = 0; x < kFinCache; ++x)
+              if (x == r) sv16 = sv16c[x];
+          } else {
+            sv16 = raw16(q);
+          }
+        }
         u8 = (q < p.k && sn16 > 0.f) ? sv16 / sn16 : 0.f;
       }
       const __nv_fp8_storage_t e = __nv_cvt_float_to_fp8(u8 * kE4M3Scale, __NV_SATFINITE, __NV_E4M3);
