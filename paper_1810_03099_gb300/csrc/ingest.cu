@@ -136,7 +136,8 @@ __device__ uint64_t sha1_feature(uint32_t t, uint64_t seed) {
 // pass takes the short documents only (the long ones go to the group path).
 // MINB: CTAs per SM the register budget is cut for (3 with 64-bit tables, 4 with 32-bit ones; 5
 // for passes over stored bags, whose warps need little shared memory), so that as many
-// documents as the shared memory holds are in flight.
+// documents as the shared memory holds are in flight. It also names the way the kernel takes
+// (the one it is launched for): 5 stored bags, 4 32-bit tables, 3 64-bit tables.
 template <int MODE, int MINB>
 __global__ void __launch_bounds__(kWarpsShort * 32, MINB) k_ingest_short(IngestParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(kWarpsShort * 32, MINB) k_ingest_short(IngestP
     int32_t next = 0;
     if (lane == 0) next = atomicAdd(p.short_cursor, 1);
     const int64_t d = it < n_long ? p.long_list[it] : p.short_list[it - n_long];
-    warp_doc<MODE>(p, d, base, kq, lane, tr);
+    warp_doc<MODE, MINB == 5 ? kVarBag : (MINB == 4 ? kVarNarrow : kVarWide)>(p, d, base, kq, lane, tr);
     it = __shfl_sync(kFull, next, 0);
   }
   // This grid may start while the long-document grid (launched just before it) is still
@@ -600,11 +601,14 @@ cudaError_t launch_signature_scratch(mrc_ctx* ctx, const DocsDev& d, int32_t voc
   p.narrow = narrow_slots(p.vocab) ? 1 : 0;
   const size_t s_smem = short_smem(k, false, p.narrow != 0);
   if (h[0] > 0) {
-    int grid = short_grid<kSIG, 3>(ctx, s_smem);
+    int grid = p.narrow ? short_grid<kSIG, 4>(ctx, s_smem) : short_grid<kSIG, 3>(ctx, s_smem);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
     const int need = (h[0] + kWarpsShort - 1) / kWarpsShort;
     if (need < grid) grid = need;
-    k_ingest_short<kSIG, 3><<<grid, kWarpsShort * 32, s_smem, ctx->stream>>>(p);
+    if (p.narrow)
+      k_ingest_short<kSIG, 4><<<grid, kWarpsShort * 32, s_smem, ctx->stream>>>(p);
+    else
+      k_ingest_short<kSIG, 3><<<grid, kWarpsShort * 32, s_smem, ctx->stream>>>(p);
   }
   if (h[1] > 0) {
     e = launch_long<kSIG>(ctx, p, k, h[1]);

@@ -540,14 +540,19 @@ __device__ __forceinline__ int hash_doc(const IngestParams& p, int64_t d, S* tab
 // by hashing the tokens (all token loads in flight at once, inserts in batches of 8) and found
 // through the list of occupied slots. They are then walked 32 at a time, each chunk's table
 // values gathered while the previous chunk is worked on.
-template <int MODE>
+// V fixes at compile time which of the three ways the kernel takes (stored bags, 32-bit table,
+// 64-bit table), so that each kernel holds the code of one and its loops stay in the
+// instruction cache; kVarAny decides from p at run time.
+constexpr int kVarAny = 0, kVarBag = 1, kVarNarrow = 2, kVarWide = 3;
+template <int MODE, int V = kVarAny>
 __device__ void warp_doc(const IngestParams& p, int64_t d, uint8_t* base, int kq, int lane, const Transposer& tr) {
   unsigned long long* num_q = reinterpret_cast<unsigned long long*>(base);
   uint8_t* tab = reinterpret_cast<uint8_t*>(num_q + kq);
-  const bool narrow = p.narrow != 0;
+  const bool bag_read = V == kVarAny ? p.bag_read != 0 : V == kVarBag;
+  const bool narrow = V == kVarAny ? p.narrow != 0 : V == kVarNarrow;
   uint16_t* list = reinterpret_cast<uint16_t*>(tab + (size_t)kShortSlots * (narrow ? 4 : 8));
   // [0] list size, [1] row count (right after the accumulators in a pass over stored bags)
-  int32_t* misc = p.bag_read ? reinterpret_cast<int32_t*>(tab) : reinterpret_cast<int32_t*>(list + kShortMax);
+  int32_t* misc = bag_read ? reinterpret_cast<int32_t*>(tab) : reinterpret_cast<int32_t*>(list + kShortMax);
   int64_t o0, len;
   doc_span(p, d, o0, len);
   for (int q = lane; q < kq; q += 32) num_q[q] = 0ull;
@@ -556,7 +561,7 @@ __device__ void warp_doc(const IngestParams& p, int64_t d, uint8_t* base, int kq
     misc[1] = 0;
   }
   int nnz = 0;
-  if (p.bag_read)
+  if (bag_read)
     nnz = p.bag_n[d];  // the document's bag, built by an earlier pass, read as it is walked
   else if (narrow)
     nnz = hash_doc<MODE, uint32_t>(p, d, reinterpret_cast<uint32_t*>(tab), list, misc, o0, len, lane);
@@ -566,9 +571,9 @@ __device__ void warp_doc(const IngestParams& p, int64_t d, uint8_t* base, int kq
   Acc a{0ull, 0ull, 0u, 0u};
   float inv_norm = 0.f;
   if (MODE == kDENSE) inv_norm = inv_norm_of(p.dense.norm[d]);
-  if (MODE != kDF || p.bag_read) {
+  if (MODE != kDF || bag_read) {
     // term x: the bag's entry x, or the table slot the list's entry x names
-    const bool bag = p.bag_read != 0;
+    const bool bag = bag_read;
     auto term = [&](int x, uint32_t& key, uint32_t& c) {
       if (x >= nnz) {
         key = kEmpty;
