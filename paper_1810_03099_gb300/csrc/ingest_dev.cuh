@@ -504,14 +504,17 @@ __device__ __forceinline__ int hash_doc(const IngestParams& p, int64_t d, S* tab
   for (int u = 0; u < kShortRegs; ++u) tk[u] = lane + 32 * u < len ? __ldcs(p.tokens + o0 + lane + 32 * u) : -1;
   __syncwarp();
   int32_t* df = (MODE == kDF || MODE == kDFN) ? p.df : nullptr;
-#pragma unroll
+  // one copy of the batch insert for both batches (the tokens are selected, so they stay in
+  // registers): the loop body is large, and two copies of it cost instruction-cache misses
+  static_assert(kShortRegs == 16, "two batches of 8 tokens per lane");
+#pragma unroll 1
   for (int h = 0; h < kShortRegs; h += 8) {
     if (32 * h >= len) break;  // warp-uniform
     int32_t tb[8];
     uint32_t pend = 0u;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      tb[u] = tk[h + u];
+      tb[u] = h == 0 ? tk[u] : tk[8 + u];
       if (lane + 32 * (h + u) < len) {
         if ((uint32_t)tb[u] >= (uint32_t)p.vocab)
           set_err(p.err, kErrBadToken);
