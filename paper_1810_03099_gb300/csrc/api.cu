@@ -331,94 +331,6 @@ double reference_weight(const mrc_params& p, const float* idf, int32_t t) {
   return idf[t];
 }
 
-// Reference selection (Section IV): terms ranked by df descending, ids ascending within equal
-// df, zero-df terms dropped; REGION / ALL / DF1 pick the selection; partition p holds
-// selection positions [floor(pL/k), floor((p+1)L/k)), so position x lies in partition
-// floor(((x + 1) k - 1) / L). Writes part[t] (-1 for unselected terms) for every term and
-// returns L. The ranking is never materialised: with cnt[v] terms of df v, a term of df v that
-// is the s-th such term in id order has rank #{df > v} + s, so one pass in id order places
-// every term.
-// |R_p|^2 accumulates over the selected terms in term-id order.
-int64_t select_references(const int32_t* df, int32_t V, int64_t n_docs, const mrc_params& p, int32_t* part,
-                          const float* idf, std::vector<double>* rnorm2) {
-  const int64_t L = p.L < 0 ? 32ll * p.k : p.L;
-  rnorm2->assign(p.k, 0.0);
-  if (p.select_mode == MRC_SELECT_DF1) {
-    int64_t n = 0;
-    for (int32_t t = 0; t < V; ++t) n += (df[t] == 1 && n < L) ? 1 : 0;
-    int64_t x = 0;
-    for (int32_t t = 0; t < V; ++t) {
-      int32_t q = -1;
-      if (df[t] == 1 && x < n) {
-        q = (int32_t)(((x + 1) * p.k - 1) / n);
-        ++x;
-        const double r = reference_weight(p, idf, t);
-        (*rnorm2)[q] += r * r;
-      }
-      part[t] = q;
-    }
-    return n;
-  }
-  // scratch kept across calls (fresh allocations cost page faults)
-  static thread_local std::vector<int64_t> base, seen;
-  static thread_local std::vector<int32_t> cnt4;
-  static thread_local std::vector<uint8_t> band;
-  // df <= n_docs bounds the histogram; a pass for the largest df pays off only when the
-  // vocabulary is small next to the collection
-  int32_t maxdf = (int32_t)std::min<int64_t>(n_docs, INT32_MAX - 2);
-  if (n_docs > 4 * (int64_t)V) {
-    maxdf = 0;
-    for (int32_t t = 0; t < V; ++t) maxdf = std::max(maxdf, df[t]);
-  }
-  // histogram of df in four interleaved copies (a run of equal df values would otherwise
-  // chain every increment on the previous one)
-  const size_t M = (size_t)maxdf + 2;
-  cnt4.assign(4 * M, 0);
-  for (int32_t t = 0; t < V; ++t) cnt4[(size_t)(t & 3) * M + df[t]] += 1;
-  base.assign(M, 0);
-  int64_t above = 0;  // terms with df > v, for v from maxdf down
-  for (int32_t v = maxdf; v >= 1; --v) {
-    const int64_t c = (int64_t)cnt4[v] + cnt4[M + v] + cnt4[2 * M + v] + cnt4[3 * M + v];
-    base[v] = above;
-    above += c;
-  }
-  const int64_t ranked = above;  // terms with df >= 1
-  int64_t start = 0, end = ranked;
-  if (p.select_mode != MRC_SELECT_ALL) {
-    start = p.region_start;
-    if (start < 0) {
-      // first rank whose df <= N / 100: the number of terms with df > floor(N / 100)
-      const int64_t vcap = n_docs / 100;
-      start = vcap >= maxdf ? 0 : (vcap >= 1 ? base[vcap] : ranked);
-    }
-    start = std::min(start, ranked);
-    end = std::min(start + L, ranked);
-  }
-  const int64_t n = end - start;
-  // df values whose ranks [base[v], base[v] + count) meet the selection [start, end): only
-  // their terms need a running rank
-  band.assign(M, 0);
-  for (int32_t v = maxdf; v >= 1; --v) {
-    const int64_t c = (v > 1 ? base[v - 1] : ranked) - base[v];
-    band[v] = base[v] < end && base[v] + c > start;
-  }
-  seen.assign(M, 0);
-  for (int32_t t = 0; t < V; ++t) {
-    const int32_t v = df[t];
-    int32_t q = -1;
-    if (band[v]) {
-      const int64_t x = base[v] + seen[v]++ - start;
-      if (x >= 0 && x < n) {
-        q = (int32_t)(((x + 1) * p.k - 1) / n);
-        const double r = reference_weight(p, idf, t);
-        (*rnorm2)[q] += r * r;
-      }
-    }
-    part[t] = q;
-  }
-  return n;
-}
-
 // Index arrays come from the device's stream-ordered memory pool (kept, not returned to the
 // driver, between builds), so building and freeing indexes does not synchronise the device.
 void free_index_arrays(mrc_index* x) {
@@ -735,12 +647,11 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "df pass"));
   e = launch_idf(ctx, d.n_docs, x->df, vocab, params->weighting, x->idf, nullptr);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "idf"));
-  // References: REGION selection on the device when its df histogram is small (no host round
-  // trip between the passes); otherwise, and when a tie group overflows the device sort, on
-  // the host.
-  const bool dev_select = params->select_mode == MRC_SELECT_REGION &&
-                          d.n_docs + 2 <= std::max<int64_t>(4 * (int64_t)vocab, 1 << 20);
-  if (dev_select) {
+  // References (Section IV), on the device for every selection mode: the df histogram, the
+  // band of df values the selection meets, and the band's terms ranked by (df descending, id
+  // ascending); a band of more than 8,192 terms takes the general pass (a radix sort) after the
+  // call's one synchronisation.
+  {
     const size_t hb = sizeof(int32_t) * ((size_t)d.n_docs + 2);
     int32_t* hist = (int32_t*)ws_get(ctx, "sel.hist", hb, &st);
     int32_t* above = (int32_t*)ws_get(ctx, "sel.above", hb, &st);
@@ -750,44 +661,38 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
     if (st != MRC_OK) return bail(st);
     const bool tfidf = params->weighting == MRC_WEIGHT_TFIDF;
     const int64_t L = params->L < 0 ? 32ll * params->k : params->L;
-    e = launch_select_region(ctx, x->df, vocab, d.n_docs, L, params->region_start, tfidf ? x->idf : nullptr, 0,
-                             x->k, hist, above, sstate, keys, d_part, x->rnorm, x->rinv, x->rinv16);
+    e = launch_select_region(ctx, x->df, vocab, d.n_docs, L, params->region_start, params->select_mode,
+                             tfidf ? x->idf : nullptr, 0, x->k, hist, above, sstate, keys, d_part, x->rnorm, x->rinv,
+                             x->rinv16);
     if (e == cudaSuccess) e = launch_term_info(ctx, x->idf, d_part, vocab, tfidf, 0, x->tinfo);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "reference selection"));
-    mark_index_tables(ctx, x);
     // one synchronisation, before the signature pass: the error word of the df pass, the
     // selection state and |R_p|; the call then returns while the signature pass runs (it meets
     // only documents the df pass validated)
     char* hs = (char*)ctx->pinned + 1024;
-    e = cudaMemcpyAsync(hs, sstate, sizeof(long long) * device_selection_words(), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(hs + 128, x->rnorm, sizeof(double) * x->k, cudaMemcpyDeviceToHost, ctx->stream);
-    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "reading the selection"));
+    auto read_selection = [&]() {
+      cudaError_t r = cudaMemcpyAsync(hs, sstate, sizeof(long long) * device_selection_words(), cudaMemcpyDeviceToHost,
+                                      ctx->stream);
+      if (r == cudaSuccess)
+        r = cudaMemcpyAsync(hs + 128, x->rnorm, sizeof(double) * x->k, cudaMemcpyDeviceToHost, ctx->stream);
+      return r;
+    };
+    if ((e = read_selection()) != cudaSuccess) return bail(cuda_fail(ctx, e, "reading the selection"));
     if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);  // synchronises the stream
-    const long long* hss = (const long long*)hs;
-    if (hss[6] == 0) {
-      x->L_used = hss[1];
-      x->h_rnorm.assign((const double*)(hs + 128), (const double*)(hs + 128) + x->k);
-      if ((st = launch_index_signatures(ctx, x, d)) != MRC_OK) return bail(st);
-      mark_index_ready(ctx, x);
-      *out = x;
-      return MRC_OK;
+    if (((const long long*)hs)[6] != 0) {  // a band larger than the small path holds
+      void* gs = ws_get(ctx, "sel.general", select_general_bytes(vocab), &st);
+      if (st != MRC_OK) return bail(st);
+      e = launch_select_general(ctx, x->df, vocab, tfidf ? x->idf : nullptr, 0, x->k, sstate, gs, d_part, x->rnorm,
+                                x->rinv, x->rinv16);
+      if (e == cudaSuccess) e = launch_term_info(ctx, x->idf, d_part, vocab, tfidf, 0, x->tinfo);
+      if (e == cudaSuccess) e = read_selection();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "reference selection (general pass)"));
     }
+    const long long* hss = (const long long*)hs;
+    x->L_used = hss[1];
+    x->h_rnorm.assign((const double*)(hs + 128), (const double*)(hs + 128) + x->k);
   }
-  // host selection: df and idf read back to pinned staging, then the partition [vocab] and
-  // 1 / |R_p| [k] staged for the device tables
-  char* stage = (char*)host_ws(ctx, 12 * (size_t)vocab + 8 * (size_t)x->k + 64, &st);
-  if (!stage) return bail(st);
-  int32_t* h_df = (int32_t*)stage;
-  float* h_idf = (float*)(stage + 4 * (size_t)vocab);
-  e = cudaMemcpyAsync(h_df, x->df, sizeof(int32_t) * vocab, cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h_idf, x->idf, sizeof(float) * vocab, cudaMemcpyDeviceToHost, ctx->stream);
-  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "reading df"));
-  if ((st = check_err_word(ctx, d_err)) != MRC_OK) return bail(st);  // synchronises the stream
-  int32_t* part_stage = (int32_t*)(stage + 8 * (size_t)vocab);
-  x->L_used = select_references(h_df, vocab, d.n_docs, *params, part_stage, h_idf, &x->h_rnorm);
-  if ((st = upload_references(ctx, x, part_stage, (float*)(stage + 12 * (size_t)vocab), h_idf)) != MRC_OK)
-    return bail(st);
   mark_index_tables(ctx, x);
   if ((st = launch_index_signatures(ctx, x, d)) != MRC_OK) return bail(st);
   // The df pass already validated these documents (offsets, lengths, token ids) and the

@@ -185,18 +185,25 @@ struct DocsDev {
 };
 
 // select.cu
-// REGION reference selection on the device from df [V]: partition of every term into part
-// [V] (-1 unselected), |R_p| into rnorm [k] (double) and 1 / |R_p| into rinv [k]; idf NULL
-// under count weighting, bf16: weights rounded to bfloat16; rinv16 (may be NULL): 1 / |R_p| of
-// the bfloat16-rounded weights (the precision form's compare operands). Scratch: hist
-// and above [n_docs + 2] int32, state [device_selection_words()] int64, keys [8192] uint64.
-// state[5] = band size, state[6] = 1 if the band exceeded 8192 terms (part, rnorm and rinv
-// are then not written: select on the host), state[1] = L.
+// Reference selection on the device from df [V] (mode MRC_SELECT_*): partition of every term
+// into part [V] (-1 unselected), |R_p| into rnorm [k] (double) and 1 / |R_p| into rinv [k];
+// idf NULL under count weighting, bf16: weights rounded to bfloat16; rinv16 (may be NULL):
+// 1 / |R_p| of the bfloat16-rounded weights (the precision form's compare operands). Scratch:
+// hist and above [n_docs + 2] int32, state [device_selection_words()] int64, keys [8192]
+// uint64. state[5] = band size, state[6] = 1 if the band exceeded 8192 terms (part, rnorm and
+// rinv are then not written: run launch_select_general), state[1] = L.
 int64_t device_selection_words();
 cudaError_t launch_select_region(mrc_ctx* ctx, const int32_t* df, int32_t V, int64_t n_docs, int64_t L,
-                                 int64_t region_start, const float* idf, int32_t bf16, int32_t k, int32_t* hist,
-                                 int32_t* above, long long* state, unsigned long long* keys, int32_t* part,
-                                 double* rnorm, float* rinv, float* rinv16);
+                                 int64_t region_start, int32_t mode, const float* idf, int32_t bf16, int32_t k,
+                                 int32_t* hist, int32_t* above, long long* state, unsigned long long* keys,
+                                 int32_t* part, double* rnorm, float* rinv, float* rinv16);
+// The selection of a band of any size, after launch_select_region reported state[6] = 1 (a
+// no-op otherwise): same outputs, from the same state. scratch: select_general_bytes(V) bytes
+// of device memory.
+size_t select_general_bytes(int32_t V);
+cudaError_t launch_select_general(mrc_ctx* ctx, const int32_t* df, int32_t V, const float* idf, int32_t bf16,
+                                  int32_t k, long long* state, void* scratch, int32_t* part, double* rnorm,
+                                  float* rinv, float* rinv16);
 
 // ingest.cu
 cudaError_t launch_df(mrc_ctx* ctx, const DocsDev& d, int32_t* df, int32_t vocab);

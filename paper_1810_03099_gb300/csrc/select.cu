@@ -15,8 +15,17 @@
 //      weight by selection position,
 //   5. sums the reference norms |R_p| (one CTA, k_ref_norms; each partition summed by one
 //      thread in rank order, in double).
-// A band of more than kBandMax terms is reported in the status word; the caller then selects
-// on the host.
+// A band of more than kBandMax terms is reported in the status word; the caller then runs the
+// general pass (launch_select_general), which ranks any number of band terms:
+//   6. compacts the band terms in id order (k_band_compact),
+//   7. sorts them by df, descending, with a stable least-significant-digit radix sort on
+//      v_hi - df, 8 bits a pass (k_radix_hist, k_radix_scan, k_radix_scatter): ids stay
+//      ascending within each df, which is the ranking,
+//   8. assigns partitions and reference weights by selection position (k_select_assign) and
+//      sums the reference norms as step 5 does (k_ref_norms_wide).
+// All three selections (Section IV) are a contiguous range of that one ranking: REGION the
+// ranks [start, start + L); ALL every ranked term; DF1 the first L terms of df 1, which are the
+// last ranks, in id order.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -73,7 +82,7 @@ __global__ void __launch_bounds__(1024) k_df_hist(const int32_t* __restrict__ df
 // band of df values whose ranks meet it.
 __global__ void __launch_bounds__(kSelThreads, 1) k_sel_band(const int32_t* __restrict__ hist, int32_t* __restrict__ above,
                                                          int64_t n_docs, int64_t L, int64_t region_start,
-                                                         long long* __restrict__ state) {
+                                                         int32_t mode, long long* __restrict__ state) {
   __shared__ long long part[kSelThreads];
   __shared__ long long s_lo, s_hi;
   const int64_t maxdf = state[kSsMaxdf];
@@ -120,13 +129,19 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_sel_band(const int32_t* __re
   }
   __syncthreads();
   const int64_t ranked = above[0];
-  int64_t start = region_start;
-  if (start < 0) {
-    const int64_t vcap = n_docs / 100;  // first rank whose df <= N / 100
-    start = vcap >= maxdf ? 0 : (vcap >= 1 ? above[vcap] : ranked);
+  int64_t start = 0, end = ranked;  // ALL: every ranked term
+  if (mode == MRC_SELECT_REGION) {
+    start = region_start;
+    if (start < 0) {
+      const int64_t vcap = n_docs / 100;  // first rank whose df <= N / 100
+      start = vcap >= maxdf ? 0 : (vcap >= 1 ? above[vcap] : ranked);
+    }
+    start = min(start, ranked);
+    end = min(start + L, ranked);
+  } else if (mode == MRC_SELECT_DF1) {  // the terms of df 1 hold the last ranks, in id order
+    start = maxdf >= 1 ? above[1] : ranked;
+    end = min(start + L, ranked);
   }
-  start = min(start, ranked);
-  const int64_t end = min(start + L, ranked);
 #pragma unroll 4
   for (int64_t q = 0; q < per; ++q) {
     const int64_t v = v_top - q;
@@ -248,12 +263,223 @@ __global__ void __launch_bounds__(kSelThreads) k_ref_norms(const long long* __re
   }
 }
 
+// ---------------------------------------------------------------- general pass (any band size)
+constexpr int kRadixItems = 1024;  // items per CTA of the compaction and the radix passes
+constexpr int kRadixBits = 8;
+constexpr int kRadixDigits = 1 << kRadixBits;
+
+__device__ __forceinline__ bool general_needed(const long long* state) { return state[kSsStatus] == 1; }
+
+// Radix passes the band's keys v_hi - df need (0 when the band is one df value).
+__device__ __forceinline__ int radix_passes(const long long* state) {
+  const long long span = state[kSsVhi] - state[kSsVlo];
+  int bits = 0;
+  while (bits < 62 && (span >> bits) != 0) ++bits;
+  return (bits + kRadixBits - 1) / kRadixBits;
+}
+
+// Step 6a: per CTA of kRadixItems terms, the number of band terms.
+__global__ void __launch_bounds__(kRadixItems) k_band_count(const int32_t* __restrict__ df, int32_t V,
+                                                            const long long* __restrict__ state,
+                                                            int32_t* __restrict__ bcount) {
+  __shared__ int32_t s_n;
+  if (!general_needed(state)) return;
+  const long long v_lo = state[kSsVlo], v_hi = state[kSsVhi];
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * kRadixItems + threadIdx.x;
+  const bool in = t < V && df[t] >= v_lo && df[t] <= v_hi;
+  const unsigned b = __ballot_sync(kFull, in);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(&s_n, __popc(b));
+  __syncthreads();
+  if (threadIdx.x == 0) bcount[blockIdx.x] = s_n;
+}
+
+// Exclusive scan of n int32 counts in place by one CTA (thread i sums a contiguous run, the runs
+// are scanned by one warp, then written back); the total goes to *total.
+__global__ void __launch_bounds__(kSelThreads, 1) k_scan_counts(int32_t* __restrict__ c, int64_t n,
+                                                                const long long* __restrict__ state,
+                                                                long long* __restrict__ total) {
+  __shared__ long long part[kSelThreads];
+  if (!general_needed(state)) return;
+  const int64_t per = (n + kSelThreads - 1) / kSelThreads;
+  const int64_t a = min(n, (int64_t)threadIdx.x * per), b = min(n, a + per);
+  long long sum = 0;
+  for (int64_t x = a; x < b; ++x) sum += c[x];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    long long carry = 0;
+    for (int q = 0; q < kSelThreads; q += 32) {
+      const long long x = part[q + threadIdx.x];
+      long long incl = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(kFull, incl, o);
+        if ((int)threadIdx.x >= o) incl += y;
+      }
+      part[q + threadIdx.x] = carry + incl - x;
+      carry += __shfl_sync(kFull, incl, 31);
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+  }
+  __syncthreads();
+  long long run = part[threadIdx.x];
+  for (int64_t x = a; x < b; ++x) {
+    const int32_t v = c[x];
+    c[x] = (int32_t)run;
+    run += v;
+  }
+}
+
+// Step 6b: the band terms in id order: ids[pos] = t, keys[pos] = v_hi - df[t].
+__global__ void __launch_bounds__(kRadixItems) k_band_compact(const int32_t* __restrict__ df, int32_t V,
+                                                              const long long* __restrict__ state,
+                                                              const int32_t* __restrict__ boff,
+                                                              uint32_t* __restrict__ ids, uint32_t* __restrict__ keys) {
+  __shared__ int32_t s_warp[kRadixItems / 32];
+  if (!general_needed(state)) return;
+  const long long v_lo = state[kSsVlo], v_hi = state[kSsVhi];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t t = (int64_t)blockIdx.x * kRadixItems + threadIdx.x;
+  const int32_t d = t < V ? df[t] : 0;
+  const bool in = t < V && d >= v_lo && d <= v_hi;
+  const unsigned b = __ballot_sync(kFull, in);
+  if (lane == 0) s_warp[warp] = __popc(b);
+  __syncthreads();
+  if (warp == 0) {  // exclusive scan of the 32 warp counts
+    const int x = s_warp[lane];
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    s_warp[lane] = incl - x;
+  }
+  __syncthreads();
+  if (in) {
+    const int64_t pos = (int64_t)boff[blockIdx.x] + s_warp[warp] + __popc(b & ((1u << lane) - 1u));
+    if (pos < V) {  // a guard: the band holds at most V terms
+      ids[pos] = (uint32_t)t;
+      keys[pos] = (uint32_t)(v_hi - d);
+    }
+  }
+}
+
+// Step 7a: digit counts of one radix pass, digit-major: cnt[digit * nblk + block].
+__global__ void __launch_bounds__(kRadixItems) k_radix_hist(const uint32_t* __restrict__ keys,
+                                                            const long long* __restrict__ state,
+                                                            const long long* __restrict__ nband, int pass,
+                                                            int32_t* __restrict__ cnt, int64_t nblk) {
+  __shared__ int32_t s_cnt[kRadixDigits];
+  if (!general_needed(state) || pass >= radix_passes(state)) return;
+  const int64_t n = *nband;  // CTAs past the band's end write zero counts (the scan reads them all)
+  for (int x = threadIdx.x; x < kRadixDigits; x += kRadixItems) s_cnt[x] = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * kRadixItems + threadIdx.x;
+  if (i < n) atomicAdd(&s_cnt[(keys[i] >> (kRadixBits * pass)) & (kRadixDigits - 1)], 1);
+  __syncthreads();
+  for (int x = threadIdx.x; x < kRadixDigits; x += kRadixItems) cnt[(int64_t)x * nblk + blockIdx.x] = s_cnt[x];
+}
+
+// Step 7b: one stable radix pass. An item's place is the digit's offset for its block, plus the
+// items of the same digit in earlier warps of the block, plus those in earlier lanes of its warp.
+__global__ void __launch_bounds__(kRadixItems) k_radix_scatter(const uint32_t* __restrict__ keys,
+                                                               const uint32_t* __restrict__ ids,
+                                                               const long long* __restrict__ state,
+                                                               const long long* __restrict__ nband, int pass,
+                                                               const int32_t* __restrict__ off, int64_t nblk,
+                                                               uint32_t* __restrict__ keys_out,
+                                                               uint32_t* __restrict__ ids_out) {
+  __shared__ int32_t s_wc[kRadixItems / 32][kRadixDigits];  // per warp and digit: count, then prefix
+  if (!general_needed(state) || pass >= radix_passes(state)) return;
+  const int64_t n = *nband;
+  if ((int64_t)blockIdx.x * kRadixItems >= n) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int x = threadIdx.x; x < (kRadixItems / 32) * kRadixDigits; x += kRadixItems) (&s_wc[0][0])[x] = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * kRadixItems + threadIdx.x;
+  const bool valid = i < n;
+  const uint32_t key = valid ? keys[i] : 0u;
+  const uint32_t id = valid ? ids[i] : 0u;
+  const int dg = valid ? (int)((key >> (kRadixBits * pass)) & (kRadixDigits - 1)) : kRadixDigits;  // sentinel
+  const unsigned peers = __match_any_sync(kFull, dg);
+  const int in_warp = __popc(peers & ((1u << lane) - 1u));
+  if (valid && lane == __ffs(peers) - 1) s_wc[warp][dg] = __popc(peers);
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRadixDigits; d += kRadixItems) {  // exclusive scan over the warps
+    int run = 0;
+    for (int w = 0; w < kRadixItems / 32; ++w) {
+      const int c = s_wc[w][d];
+      s_wc[w][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    const int64_t pos = (int64_t)off[(int64_t)dg * nblk + blockIdx.x] + s_wc[warp][dg] + in_warp;
+    if (pos >= 0 && pos < n) {  // always so when the counts are consistent; a guard, not a branch taken
+      keys_out[pos] = key;
+      ids_out[pos] = id;
+    }
+  }
+}
+
+// Step 8a: the sorted band terms hold the ranks rank0, rank0 + 1, ...; those in [start, start + L)
+// get their partition and, at their selection position, their reference weight. ids_sorted is
+// buffer 0 or 1 of the ping-pong by the number of passes.
+__global__ void k_select_assign(const uint32_t* __restrict__ ids0, const uint32_t* __restrict__ ids1, int32_t V,
+                                const long long* __restrict__ state, const long long* __restrict__ nband,
+                                const float* __restrict__ idf, int32_t bf16, int32_t k, int32_t* __restrict__ part,
+                                float* __restrict__ rsel) {
+  if (!general_needed(state)) return;
+  const uint32_t* ids = (radix_passes(state) & 1) ? ids1 : ids0;
+  const int64_t n = *nband;
+  const long long rank0 = state[kSsRank0], start = state[kSsStart], L = state[kSsL];
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const long long pos = rank0 + r - start;
+    if (pos < 0 || pos >= L) continue;
+    const uint32_t t = ids[r];
+    if (t >= (uint32_t)V) continue;  // a guard: every sorted id is a term
+    part[t] = (int32_t)(((pos + 1) * k - 1) / L);
+    float w = 1.f;
+    if (idf) w = bf16 ? __bfloat162float(__float2bfloat16_rn(idf[t])) : idf[t];
+    rsel[pos] = w;
+  }
+}
+
+// Step 8b: k_ref_norms for a selection of any length (the weights read from global memory).
+__global__ void __launch_bounds__(kSelThreads) k_ref_norms_wide(const long long* __restrict__ state,
+                                                              const float* __restrict__ rsel, int32_t k,
+                                                              double* __restrict__ rnorm, float* __restrict__ rinv,
+                                                              float* __restrict__ rinv16) {
+  if (!general_needed(state)) return;
+  const long long L = state[kSsVhi] < 0 ? 0 : state[kSsL];
+  for (int q = threadIdx.x; q < k; q += kSelThreads) {
+    double s = 0.0, s16 = 0.0;
+    const long long p0 = q * L / k, p1 = (q + 1) * L / k;
+    for (long long pos = p0; pos < p1; ++pos) {
+      const float w = rsel[pos];
+      const double r = (double)w;
+      s += r * r;
+      const double r16 = (double)__bfloat162float(__float2bfloat16_rn(w));
+      s16 += r16 * r16;
+    }
+    const double nr = sqrt(s);
+    rnorm[q] = nr;
+    rinv[q] = nr > 0.0 ? (float)(1.0 / nr) : 0.f;
+    if (rinv16) rinv16[q] = s16 > 0.0 ? (float)(1.0 / sqrt(s16)) : 0.f;
+  }
+}
+
 }  // namespace
 
 int64_t device_selection_words() { return kSsWords; }
 
 cudaError_t launch_select_region(mrc_ctx* ctx, const int32_t* df, int32_t V, int64_t n_docs, int64_t L,
-                                 int64_t region_start, const float* idf, int32_t bf16, int32_t k, int32_t* hist,
+                                 int64_t region_start, int32_t mode, const float* idf, int32_t bf16, int32_t k,
+                                 int32_t* hist,
                                  int32_t* above, long long* state, unsigned long long* keys, int32_t* part,
                                  double* rnorm, float* rinv, float* rinv16) {
   if (V <= 0 || k <= 0) return cudaErrorInvalidValue;
@@ -272,7 +498,7 @@ cudaError_t launch_select_region(mrc_ctx* ctx, const int32_t* df, int32_t V, int
   }
   {
     KernelTimer kt(ctx, "select_band", 8.0 * (double)n_docs);
-    k_sel_band<<<1, kSelThreads, 0, ctx->stream>>>(hist, above, n_docs, L, region_start, state);
+    k_sel_band<<<1, kSelThreads, 0, ctx->stream>>>(hist, above, n_docs, L, region_start, mode, state);
   }
   {
     KernelTimer kt(ctx, "select_group", 4.0 * V);
@@ -287,6 +513,47 @@ cudaError_t launch_select_region(mrc_ctx* ctx, const int32_t* df, int32_t V, int
   }
   KernelTimer kt(ctx, "select_norms");
   k_ref_norms<<<1, kSelThreads, 0, ctx->stream>>>(state, rsel, k, rnorm, rinv, rinv16);
+  return cudaGetLastError();
+}
+
+size_t select_general_bytes(int32_t V) {
+  const size_t nblk = ((size_t)std::max(V, 1) + kRadixItems - 1) / kRadixItems;
+  return 5 * 4 * (size_t)std::max(V, 1) + 4 * (kRadixDigits + 1) * nblk + 256;
+}
+
+cudaError_t launch_select_general(mrc_ctx* ctx, const int32_t* df, int32_t V, const float* idf, int32_t bf16,
+                                  int32_t k, long long* state, void* scratch, int32_t* part, double* rnorm,
+                                  float* rinv, float* rinv16) {
+  if (V <= 0 || k <= 0) return cudaErrorInvalidValue;
+  const int64_t nblk = ((int64_t)V + kRadixItems - 1) / kRadixItems;
+  // scratch: ids and keys twice [V] (ping-pong), reference weights [V], digit counts
+  // [256 * nblk], per-CTA band counts [nblk], the band size
+  uint32_t* ids0 = static_cast<uint32_t*>(scratch);
+  uint32_t* keys0 = ids0 + V;
+  uint32_t* ids1 = keys0 + V;
+  uint32_t* keys1 = ids1 + V;
+  float* rsel = reinterpret_cast<float*>(keys1 + V);
+  int32_t* cnt = reinterpret_cast<int32_t*>(rsel + V);
+  int32_t* bcount = cnt + kRadixDigits * nblk;
+  long long* nband = reinterpret_cast<long long*>((reinterpret_cast<uintptr_t>(bcount + nblk) + 7) & ~uintptr_t(7));
+  KernelTimer kt(ctx, "select_general", 24.0 * V);
+  const unsigned g = (unsigned)nblk;
+  k_band_count<<<g, kRadixItems, 0, ctx->stream>>>(df, V, state, bcount);
+  k_scan_counts<<<1, kSelThreads, 0, ctx->stream>>>(bcount, nblk, state, nband);
+  k_band_compact<<<g, kRadixItems, 0, ctx->stream>>>(df, V, state, bcount, ids0, keys0);
+  // df < 2^31: at most four passes of 8 bits; each returns at once past the passes the band needs
+  for (int pass = 0; pass < 4; ++pass) {
+    const uint32_t* ki = (pass & 1) ? keys1 : keys0;
+    const uint32_t* ii = (pass & 1) ? ids1 : ids0;
+    uint32_t* ko = (pass & 1) ? keys0 : keys1;
+    uint32_t* io = (pass & 1) ? ids0 : ids1;
+    k_radix_hist<<<g, kRadixItems, 0, ctx->stream>>>(ki, state, nband, pass, cnt, nblk);
+    k_scan_counts<<<1, kSelThreads, 0, ctx->stream>>>(cnt, kRadixDigits * nblk, state, nullptr);
+    k_radix_scatter<<<g, kRadixItems, 0, ctx->stream>>>(ki, ii, state, nband, pass, cnt, nblk, ko, io);
+  }
+  k_select_assign<<<(unsigned)std::min<int64_t>(nblk * 4, 8 * ctx->num_sms), 256, 0, ctx->stream>>>(
+      ids0, ids1, V, state, nband, idf, bf16, k, part, rsel);
+  k_ref_norms_wide<<<1, kSelThreads, 0, ctx->stream>>>(state, rsel, k, rnorm, rinv, rinv16);
   return cudaGetLastError();
 }
 

@@ -112,6 +112,26 @@ def test_index_build_large_tie_group(torch, M, ctx, orc):
     idx.free()
 
 
+@pytest.mark.parametrize("p", [Params(k=64, mode=MODE_ALL), Params(k=32, mode=MODE_DF1, L=20000),
+                               Params(k=48, mode=MODE_REGION, L=20000), Params(k=16, mode=MODE_DF1, L=300)])
+def test_selection_of_wide_bands(torch, M, ctx, orc, p):
+    """Selections whose band of df values holds more than the 8,192 terms the small device path
+    sorts: ALL ranks 50,589 terms over 339 df values (two radix passes), DF1 takes from a df-1
+    group of 12,327 terms, REGION 20,000 terms over many values. The partitions, |R_p| and the
+    signatures match the oracle's ranking by (df descending, id ascending)."""
+    c = synth.make_corpus(synth.SPECS["tiny"].with_(n_docs=3000, vocab=60000))
+    V = c.vocab
+    ref = build_index(c.offsets, c.tokens, V, p, orc)
+    idx = M.mrc_build_index(ctx, dev(torch, c.offsets), dev(torch, c.tokens), V, mrc_params(M, p))
+    ex = M.mrc_index_export(ctx, idx)
+    assert idx.L_used == ref.L_used
+    assert np.array_equal(ex["part"], ref.part)
+    assert np.max(np.abs(ex["rnorm"] - ref.rnorm) / np.maximum(ref.rnorm, 1e-300)) < 1e-6
+    assert np.abs(ex["sig"].astype(np.float64) - ref.S).max() <= SIG_TOL
+    assert np.array_equal(ex["simhash"], ref.F)
+    idx.free()
+
+
 def test_signature_of_new_documents(torch, M, ctx, orc, corpus):
     offs, toks = corpus
     V = 5000
