@@ -165,9 +165,9 @@ mrc_status mrc_text_grams(mrc_ctx* ctx, int64_t n_docs, const int64_t* text_offs
 /*
  * Build a device-resident signature index over `corpus` (Sections III-IV):
  * term counts per document, document frequencies, idf (frozen for later
- * queries), reference selection and partitioning (REGION ranks the df band
- * it needs on the device; ALL and DF1 rank the vocabulary on the host after
- * one device-to-host copy of df), then every document's signature
+ * queries), reference selection and partitioning (on the device in every
+ * mode: the band of df values the selection meets is ranked by df, then id),
+ * then every document's signature
  * s_p(d) = cos(v(d), v(R_p)) (Eq. 1 against partition p), its unit-length
  * packed form for comparison, and its 64-bit Simhash (Section III).
  * vocab: number of term ids. The returned index must be freed with
