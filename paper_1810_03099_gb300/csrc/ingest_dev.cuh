@@ -29,9 +29,9 @@ constexpr float kInvFix = 1.0f / 4194304.0f;
 enum Mode { kDF = 0, kSIG = 1, kDENSE = 2, kDFN = 3 };
 
 __device__ __forceinline__ uint32_t slot_of(uint32_t t, int log2ts) { return (t * 0x9E3779B1u) >> (32 - log2ts); }
-__device__ __forceinline__ uint32_t pass_of(uint32_t t, uint32_t passes) {
-  return ((t * 0x85EBCA77u) >> 7) % passes;
-}
+// The hashing pass [0, passes) of term t (a document hashed in several passes keeps one hash
+// partition per pass): the high word of a second hash times passes, so no division.
+__device__ __forceinline__ uint32_t pass_of(uint32_t t, uint32_t passes) { return __umulhi(t * 0x85EBCA77u, passes); }
 
 // SplitMix64 (Steele, Lea, Flood 2014), one step from state (t XOR seed).
 __device__ __forceinline__ uint64_t feature_hash(uint32_t t, uint64_t seed) {
@@ -640,10 +640,16 @@ constexpr int kCntClass = 8, kCntClassFill = 16, kCntWords = 32;
 // tokens than half its table is hashed in several passes, each keeping the terms of one hash
 // partition (a second hash of the term id), so the table runs about half full. The list of
 // occupied slots has room for every slot.
-constexpr int kHugeMin = 2048;       // documents this long take a whole CTA
+constexpr int kHugeMin = 2048;       // documents this long take a whole CTA (64-bit tables)
 constexpr int kHugeSlots = 16384;    // the CTA-wide table
+// With 32-bit group tables the documents of kHugeMin tokens or more go to the groups too, each
+// into a table of kHugeGroupSlots 64-bit slots (their counts may need more than 11 bits) in the
+// same bytes as the group's 32-bit table, hashed in passes of kHugeGroupSlots / 2 terms.
+constexpr int kHugeGroupSlots = 2048;
 static_assert(kHugeMin == (2 << (9 + 1)), "length classes 2 and up are the documents of kHugeMin tokens or more");
 static_assert(kHugeMin <= (1 << kSlotCountBits), "a group-path document's counts fit a 32-bit slot");
+static_assert(kHugeGroupSlots * (8 + 2) <= kLongSlots * (4 + 2) && kHugeGroupSlots <= kLongSlots,
+              "a huge document's 64-bit table and slot list fit a 32-bit group's");
 __host__ __device__ __forceinline__ size_t long_group_bytes(int kq, bool narrow) {
   return (size_t)kq * 8 + 16 + 64 * 4 + 16 + (size_t)kLongSlots * (narrow ? 4 : 8) + (size_t)kLongSlots * 2;
 }
