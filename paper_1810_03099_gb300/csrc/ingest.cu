@@ -182,8 +182,14 @@ __global__ void __launch_bounds__(G * kGroupThreads, 1) k_ingest_long(IngestPara
   const int32_t n_huge = s_huge;
   // the warp path's grid may start on SMs this grid leaves (the two touch disjoint documents)
   asm volatile("griddepcontrol.launch_dependents;");
-  // phase 1 (64-bit group tables only): the huge documents, one per CTA at a time
-  while (!NARROW) {
+  // The huge documents go to the groups (32-bit group tables only) when there are at least
+  // four per CTA: then the pass is bound by throughput, and a whole CTA per document would leave
+  // most of its warps waiting on one document's chain (half the groups' tokens per second).
+  // With fewer, the longest document's latency bounds the pass, and a whole CTA takes it in
+  // one hashing pass where a group would need up to ten.
+  const bool huge_groups = NARROW && n_huge >= 4 * (int32_t)gridDim.x;
+  // phase 1: the huge documents, one per CTA at a time
+  while (!huge_groups) {
     if (threadIdx.x == 0) s_next = atomicAdd(p.huge_cursor, 1);
     __syncthreads();
     const int32_t it = s_next;
@@ -191,17 +197,16 @@ __global__ void __launch_bounds__(G * kGroupThreads, 1) k_ingest_long(IngestPara
     if (it >= n_huge) break;
     team_doc<MODE>(p, p.long_list[it], smem, kq, kHugeSlots, kThreads, 0, threadIdx.x, tr);
   }
-  // phase 2: the other long documents, one per group at a time; with 32-bit group tables the
-  // huge ones too, first (a whole CTA per document left most of its warps waiting on one
-  // document's chain: half the tokens per second of the groups)
+  // phase 2: the other long documents, one per group at a time (the huge ones first when the
+  // groups take them)
   uint8_t* base = smem + long_group_bytes(kq, NARROW) * g;
   int32_t* slot = reinterpret_cast<int32_t*>(base + (size_t)kq * 8 + 16 + 64 * 4);  // misc[0] of the group
   while (true) {
-    if (gt == 0) *slot = (NARROW ? 0 : n_huge) + atomicAdd(p.long_cursor, 1);
+    if (gt == 0) *slot = (huge_groups ? 0 : n_huge) + atomicAdd(p.long_cursor, 1);
     team_sync(1 + g, kGroupThreads);
     const int32_t it = *slot;
     if (it >= n_long) break;
-    if (NARROW && it < n_huge)
+    if (huge_groups && it < n_huge)
       team_doc<MODE, unsigned long long>(p, p.long_list[it], base, kq, kHugeGroupSlots, kGroupThreads, 1 + g, gt,
                                          tr);
     else
@@ -337,8 +342,7 @@ size_t short_smem(int kq, bool bag, bool narrow) {
 }
 template <int MODE, bool NARROW>
 size_t long_smem(int kq) {
-  const size_t groups = (size_t)long_groups(MODE, NARROW) * long_group_bytes(kq, NARROW);
-  return NARROW ? groups : std::max(groups, long_huge_bytes(kq));
+  return std::max((size_t)long_groups(MODE, NARROW) * long_group_bytes(kq, NARROW), long_huge_bytes(kq));
 }
 
 // The long-document grid (persistent: as many CTAs as fit, at most `cap`), narrow or wide tables.

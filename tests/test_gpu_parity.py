@@ -132,6 +132,29 @@ def test_selection_of_wide_bands(torch, M, ctx, orc, p):
     idx.free()
 
 
+def test_long_documents_in_groups(torch, M, ctx, orc):
+    """800 documents of 2,048 to 8,000 tokens: at least four per CTA, so with 32-bit tables the
+    four-warp groups take them, each into 2,048 64-bit slots hashed in two to eight passes. The
+    build and the signature pass over tokens match the oracle."""
+    c = synth.make_corpus(synth.SPECS["batch_queries"].with_(n_docs=800, vocab=5000, length_min=2048,
+                                                              length_max=8000))
+    V = c.vocab
+    lens = np.diff(c.offsets)
+    assert lens.min() >= 2048 and len(lens) >= 4 * 152
+    p = Params(k=32, mode=MODE_ALL)  # every term a reference (the default region is empty here)
+    ref = build_index(c.offsets, c.tokens, V, p, orc)
+    idx = M.mrc_build_index(ctx, dev(torch, c.offsets), dev(torch, c.tokens), V, mrc_params(M, p))
+    ex = M.mrc_index_export(ctx, idx)
+    assert np.array_equal(ex["df"].astype(np.int64), ref.df)
+    assert np.abs(ex["sig"].astype(np.float64) - ref.S).max() <= SIG_TOL
+    assert np.array_equal(ex["simhash"], ref.F)
+    S_ref, F_ref, _ = signature(ref, c.offsets, c.tokens, orc)
+    sig, sh = M.mrc_signature(ctx, idx, dev(torch, c.offsets), dev(torch, c.tokens))
+    assert np.abs(sig.cpu().numpy().astype(np.float64) - S_ref).max() <= SIG_TOL
+    assert np.array_equal(sh.cpu().numpy().view(np.uint64), F_ref)
+    idx.free()
+
+
 def test_signature_of_new_documents(torch, M, ctx, orc, corpus):
     offs, toks = corpus
     V = 5000
