@@ -206,7 +206,7 @@ const void* stage_in(mrc_ctx* ctx, const char* slot, const void* p, size_t bytes
 }
 
 struct Scope {
-  explicit Scope(mrc_ctx* c) : ctx(c) {
+  Scope(mrc_ctx* c, const char* name) : trace(name), ctx(c) {
     int cur = -1;
     cudaGetDevice(&cur);
     prev = cur;
@@ -215,6 +215,7 @@ struct Scope {
   ~Scope() {
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
   }
+  TraceRange trace;  // first constructed, last destroyed: the range covers the whole call
   mrc_ctx* ctx;
   int prev;
 };
@@ -607,7 +608,7 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
                            mrc_index** out) {
   if (!ctx || !out) return MRC_ERR_INVALID;
   *out = nullptr;
-  Scope scope(ctx);
+  Scope scope(ctx, __func__);
   std::string why;
   if (!valid_params(params, &why)) return fail(ctx, MRC_ERR_INVALID, why);
   if (vocab < 1) return fail(ctx, MRC_ERR_INVALID, "vocab must be >= 1");
@@ -706,7 +707,7 @@ mrc_status mrc_build_index(mrc_ctx* ctx, const mrc_docs* corpus, int32_t vocab, 
 mrc_status mrc_text_grams(mrc_ctx* ctx, int64_t n_docs, const int64_t* text_offsets, const uint8_t* text,
                           int64_t* gram_offsets, int32_t* grams, int64_t capacity, int64_t* n_grams) {
   if (!ctx) return MRC_ERR_INVALID;
-  Scope scope(ctx);
+  Scope scope(ctx, __func__);
   if (n_docs < 0 || !text_offsets || !gram_offsets || !n_grams || capacity < 0 || (capacity > 0 && !grams))
     return fail(ctx, MRC_ERR_INVALID, "mrc_text_grams: NULL pointer or negative size");
   if (n_docs >= (1ll << 40)) return fail(ctx, MRC_ERR_UNSUPPORTED, "too many documents");
@@ -761,7 +762,7 @@ mrc_status mrc_text_grams(mrc_ctx* ctx, int64_t n_docs, const int64_t* text_offs
 
 mrc_status mrc_signature(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float* sig, uint64_t* simhash) {
   if (!ctx || !index) return MRC_ERR_INVALID;
-  Scope scope(ctx);
+  Scope scope(ctx, __func__);
   wait_for_index(ctx, index);
   if (!docs) return fail(ctx, MRC_ERR_INVALID, "docs is NULL");
   if (docs->n_docs == 0) return MRC_OK;
@@ -794,7 +795,7 @@ mrc_status mrc_signature(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* d
 static mrc_status match_impl(mrc_ctx* ctx, const mrc_index* index, const float* query_sig, int64_t nq, float tau,
                       mrc_pair* pairs, int64_t capacity, int64_t* n_pairs, unsigned long long* d_total) {
   if (!ctx || !index) return MRC_ERR_INVALID;
-  Scope scope(ctx);
+  Scope scope(ctx, __func__);
   wait_for_index(ctx, index);
   if (capacity < 0) return fail(ctx, MRC_ERR_INVALID, "capacity < 0");
   if (query_sig && nq < 0) return fail(ctx, MRC_ERR_INVALID, "nq < 0");
@@ -909,7 +910,7 @@ static mrc_status match_impl(mrc_ctx* ctx, const mrc_index* index, const float* 
 static mrc_status cosine_impl(mrc_ctx* ctx, const mrc_index* index, const mrc_docs* docs, float tau, mrc_pair* pairs,
                        int64_t capacity, int64_t* n_pairs, unsigned long long* d_total) {
   if (!ctx || !index) return MRC_ERR_INVALID;
-  Scope scope(ctx);
+  Scope scope(ctx, __func__);
   wait_for_index_tables(ctx, index);  // idf and the term table only
   if (capacity < 0) return fail(ctx, MRC_ERR_INVALID, "capacity < 0");
   if (n_pairs) *n_pairs = 0;
@@ -1136,7 +1137,7 @@ static mrc_status simhash_impl(mrc_ctx* ctx, const uint64_t* a, int64_t na, cons
                         int32_t hamming_max, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs,
                         unsigned long long* d_total) {
   if (!ctx) return MRC_ERR_INVALID;
-  Scope scope(ctx);
+  Scope scope(ctx, __func__);
   if (na < 0 || (b && nb < 0) || capacity < 0 || (na > 0 && !a))
     return fail(ctx, MRC_ERR_INVALID, "simhash_match: bad sizes or NULL input");
   if (na >= (1ll << 31) || nb >= (1ll << 31)) return fail(ctx, MRC_ERR_UNSUPPORTED, "more than 2^31 fingerprints");
@@ -1198,7 +1199,7 @@ mrc_status mrc_simhash_index_build(mrc_ctx* ctx, const uint64_t* fps, int64_t n,
                                    mrc_simhash_index** out) {
   if (!ctx || !out) return MRC_ERR_INVALID;
   *out = nullptr;
-  Scope scope(ctx);
+  Scope scope(ctx, __func__);
   if (n < 0 || (n > 0 && !fps)) return fail(ctx, MRC_ERR_INVALID, "mrc_simhash_index_build: bad size or NULL input");
   if (n >= (1ll << 31) - 1) return fail(ctx, MRC_ERR_UNSUPPORTED, "more than 2^31 - 2 fingerprints");
   if (hamming_max < 0 || hamming_max > 15) return fail(ctx, MRC_ERR_INVALID, "hamming_max must be in [0, 15]");
@@ -1246,7 +1247,7 @@ mrc_status mrc_simhash_index_build(mrc_ctx* ctx, const uint64_t* fps, int64_t n,
 mrc_status mrc_simhash_index_match(mrc_ctx* ctx, const mrc_simhash_index* index, const uint64_t* queries, int64_t nq,
                                    int32_t hamming_max, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs) {
   if (!ctx) return MRC_ERR_INVALID;
-  Scope scope(ctx);
+  Scope scope(ctx, __func__);
   if (!index || (queries && nq < 0) || capacity < 0 || (!queries && nq != 0))
     return fail(ctx, MRC_ERR_INVALID, "mrc_simhash_index_match: bad sizes or NULL index");
   if (nq >= (1ll << 31)) return fail(ctx, MRC_ERR_UNSUPPORTED, "more than 2^31 queries");
@@ -1284,7 +1285,7 @@ void mrc_simhash_index_free(mrc_simhash_index* x) {
 
 mrc_status mrc_ctx_sync(mrc_ctx* ctx) {
   if (!ctx) return MRC_ERR_INVALID;
-  Scope scope(ctx);
+  Scope scope(ctx, __func__);
   int32_t* h = (int32_t*)((char*)ctx->pinned + 256);
   cudaError_t e = cudaMemcpyAsync(h, ctx->async_err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->async_err, 0, sizeof(int32_t), ctx->stream);
@@ -1309,7 +1310,7 @@ mrc_status mrc_index_get_info(const mrc_index* x, mrc_index_info* info) {
 mrc_status mrc_index_export(mrc_ctx* ctx, const mrc_index* x, float* sig, uint64_t* simhash, int32_t* df, float* idf,
                             int32_t* part, double* rnorm) {
   if (!ctx || !x) return MRC_ERR_INVALID;
-  Scope scope(ctx);
+  Scope scope(ctx, __func__);
   wait_for_index(ctx, x);
   const size_t n = (size_t)x->n_docs;
   auto cp = [&](void* dst, const void* src, size_t bytes) {
@@ -1352,7 +1353,7 @@ static const char kMagic[8] = {'M', 'R', 'C', 'I', 'D', 'X', '0', '1'};
 
 mrc_status mrc_index_save(mrc_ctx* ctx, const mrc_index* x, const char* path) {
   if (!ctx || !x || !path) return MRC_ERR_INVALID;
-  Scope scope(ctx);
+  Scope scope(ctx, __func__);
   // the copies below are plain ones: the index must be complete first
   wait_for_index(ctx, x);
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "waiting for the index");
@@ -1411,7 +1412,7 @@ mrc_status mrc_index_save(mrc_ctx* ctx, const mrc_index* x, const char* path) {
 mrc_status mrc_index_load(mrc_ctx* ctx, const char* path, mrc_index** out) {
   if (!ctx || !path || !out) return MRC_ERR_INVALID;
   *out = nullptr;
-  Scope scope(ctx);
+  Scope scope(ctx, __func__);
   FILE* f = std::fopen(path, "rb");
   if (!f) return fail(ctx, MRC_ERR_INVALID, std::string("cannot open ") + path);
   char magic[8];
@@ -1523,14 +1524,14 @@ mrc_status mrc_ctx_set_wait_limit(mrc_ctx* ctx, int64_t ns) {
 
 mrc_status mrc_measure_popc_rate(mrc_ctx* ctx, double* popc_per_s) {
   if (!ctx || !popc_per_s) return MRC_ERR_INVALID;
-  Scope scope(ctx);
+  Scope scope(ctx, __func__);
   const cudaError_t e = measure_popc_rate(ctx, popc_per_s);
   return e == cudaSuccess ? MRC_OK : cuda_fail(ctx, e, "POPC rate probe");
 }
 
 mrc_status mrc_measure_smem_atomic_rate(mrc_ctx* ctx, double* atomics_per_s) {
   if (!ctx || !atomics_per_s) return MRC_ERR_INVALID;
-  Scope scope(ctx);
+  Scope scope(ctx, __func__);
   const cudaError_t e = measure_smem_atomic_rate(ctx, atomics_per_s);
   return e == cudaSuccess ? MRC_OK : cuda_fail(ctx, e, "shared-memory atomic rate probe");
 }

@@ -373,6 +373,7 @@ extern "C" {
 
 mrc_status mrc_batch_create(mrc_ctx* ctx, const mrc_index* index, int64_t max_docs, int64_t max_tokens, float tau,
                             int64_t capacity, int32_t tile_n, mrc_batch** out) {
+  TraceRange trace(__func__);
   if (!ctx || !index || !out) return MRC_ERR_INVALID;
   *out = nullptr;
   if (max_docs < 1 || max_docs > (1 << 24) || max_tokens < 1 || capacity < 1)
@@ -454,6 +455,7 @@ mrc_status mrc_batch_create(mrc_ctx* ctx, const mrc_index* index, int64_t max_do
 }
 
 mrc_status mrc_batch_launch(mrc_batch* b, const mrc_docs* docs) {
+  TraceRange trace(__func__);
   if (!b || !docs) return MRC_ERR_INVALID;
   mrc_ctx* ctx = b->ctx;
   cudaSetDevice(ctx->device);
@@ -513,6 +515,7 @@ int32_t mrc_batch_poll(mrc_batch* b) {
 }
 
 mrc_status mrc_batch_wait(mrc_batch* b, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs, int64_t* query_offsets) {
+  TraceRange trace(__func__);
   if (!b) return MRC_ERR_INVALID;
   mrc_ctx* ctx = b->ctx;
   cudaSetDevice(ctx->device);
@@ -529,6 +532,7 @@ mrc_status mrc_batch_wait(mrc_batch* b, mrc_pair* pairs, int64_t capacity, int64
 
 mrc_status mrc_batch_attach_simhash(mrc_batch* b, const mrc_simhash_index* index, int32_t hamming_max,
                                     int64_t capacity) {
+  TraceRange trace(__func__);
   if (!b) return MRC_ERR_INVALID;
   mrc_ctx* ctx = b->ctx;
   cudaSetDevice(ctx->device);
@@ -557,6 +561,7 @@ mrc_status mrc_batch_attach_simhash(mrc_batch* b, const mrc_simhash_index* index
 
 mrc_status mrc_batch_hamming(mrc_batch* b, mrc_pair* pairs, int64_t capacity, int64_t* n_pairs,
                              int64_t* query_offsets) {
+  TraceRange trace(__func__);
   if (!b) return MRC_ERR_INVALID;
   mrc_ctx* ctx = b->ctx;
   if (n_pairs) *n_pairs = 0;
@@ -572,6 +577,7 @@ mrc_status mrc_batch_hamming(mrc_batch* b, mrc_pair* pairs, int64_t capacity, in
 }
 
 mrc_status mrc_batch_tune(mrc_batch* b, int32_t tile_n, int32_t ring, int32_t prefetch) {
+  TraceRange trace(__func__);
   if (!b) return MRC_ERR_INVALID;
   mrc_ctx* ctx = b->ctx;
   cudaSetDevice(ctx->device);

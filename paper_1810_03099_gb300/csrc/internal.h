@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <map>
@@ -9,6 +10,15 @@
 #include <vector>
 
 #include "mrc.h"
+
+// A named NVTX range over one C-ABI call, so that a timeline profiler shows the library's calls
+// around their kernels. Without a profiler attached the push and pop return at once.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 namespace mrc {
 
